@@ -1,0 +1,382 @@
+"""Benchmark: space-time DoFs/s to relative residual 1e-8 on GB300.
+
+Workload (default "square64"): heat equation on (0,1)^2 x (0,1), B-spline
+degree 2 in space and time, 64 x 64 knot spans, 256 time slabs x 2 time
+elements (4 194 304 space-time dofs), theta = 1, right-hand side from i.i.d.
+N(0,1) B-spline coefficients (seed 2), zero initial guess.  Solver: FGMRES(20)
+right-preconditioned by one time-multigrid V-cycle (damped block Jacobi,
+omega = 1/2, nu1 = nu2 = 1, slab inverses by real-Schur time transform + fast
+diagonalisation in space), to ||f - L u|| <= 1e-8 ||f||.
+
+One step = one whole solve with the right-hand side resident in HBM.  `value`
+is the mixed-precision method (FP32 V-cycle, FP64 outer residual and update);
+the plain FP64 method on the same workload is reported beside it.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (dim, spans, degree, slabs, ne, tol, seed)
+    "square64": (2, (64, 64), 2, 256, 2, 1e-8, 2),
+    "square128_p3": (2, (128, 128), 3, 1024, 2, 1e-8, 3),
+    "interval16": (1, (16,), 2, 8, 4, 1e-10, 1),
+}
+METRIC = "space-time DoFs/s to rel. residual 1e-8, mixed vs FP64 plain; serve p50/p99"
+UNIT = "DoFs/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg (runs in a child process, single-threaded BLAS)
+# ----------------------------------------------------------------------------
+
+def cpu_leg(args):
+    """Time the oracle's FGMRES + V-cycle solve on a bounded sample of the
+    workload: the same spatial grid, degree and slab size with fewer slabs."""
+    import numpy as np
+    from oracle import assemble as A
+    from oracle import solve as S
+    from paper_1802_09277_gb300 import inputs
+    d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
+    n_sample = args.sample_slabs
+    pr = A.Problem(d, spans, p, ne, n_sample, theta=1.0, T=float(n_sample) / N)
+    c = inputs.normal_coeffs(seed, pr.ndofs)
+    f = A.load_from_coeffs(pr, c)
+    H = S.Hierarchy(pr)
+    L = H.levels[0].L
+    reps, total, iters = 0, 0.0, 0
+    t_end = time.perf_counter() + args.cpu_seconds
+    while True:
+        t0 = time.perf_counter()
+        u, it, hist = S.fgmres(L, f, lambda v: S.vcycle(H, v), tol=tol, restart=20)
+        total += time.perf_counter() - t0
+        reps += 1
+        iters = it
+        if time.perf_counter() >= t_end or reps >= 50:
+            break
+    out = {"value": pr.ndofs * reps / total, "seconds_per_solve": total / reps,
+           "iterations": iters, "sample_dofs": pr.ndofs, "sample_slabs": n_sample,
+           "reps": reps}
+    print(json.dumps(out))
+
+
+def run_cpu_leg(workload, sample_slabs, seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--workload", workload,
+           "--sample-slabs", str(sample_slabs), "--cpu-seconds", str(seconds)]
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+    if res.returncode != 0:
+        raise RuntimeError("cpu leg failed: " + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = str(gpu_index)
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%s.csv" % self.idx)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.idx, "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def gpu_arm(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_1802_09277_gb300 import inputs, st
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
+    common = dict(ne_per_slab=ne, outer="fgmres", gmres_restart=20, max_it=300)
+    peaks, peak_src = load_peaks()
+
+    def make(prec):
+        return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, **common)
+
+    # rank r solves its own right-hand side (independent replicas)
+    c = torch.tensor(inputs.normal_coeffs(seed + 1000 * rank, 0 + make_len(d, spans, p, N, ne)),
+                     dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed_solves(solver, f, steps, warmup, profile=False):
+        u = torch.zeros_like(f)
+        for _ in range(warmup):
+            solver.solve(f, u, tol=tol)
+        times, infos = [], []
+        barrier()
+        torch.cuda.synchronize()
+        if profile:
+            solver.profile(True)
+        for _ in range(steps):
+            flush.fill_(1.0)  # L2 flush between timed iterations (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = solver.solve(f, u, tol=tol)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(info)
+        torch.cuda.synchronize()
+        prof = None
+        if profile:
+            prof = solver.profile_read()
+            solver.profile(False)
+        barrier()
+        return times, infos, u, prof
+
+    # --- mixed precision (headline) ---
+    sm = make("mixed_fp32")
+    f = torch.empty_like(c)
+    sm.load_coeffs(c, f)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    t_mixed, i_mixed, u_mixed, prof = timed_solves(sm, f, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    ms = sum(t_mixed) / len(t_mixed)
+    ms_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(tt.item())
+
+    # --- end to end through the public API with host buffers ---
+    f_host = f.cpu().pin_memory()
+    u_host = torch.empty_like(f_host).pin_memory()
+    f_dev = torch.empty_like(f)
+    u_dev = torch.zeros_like(f)
+    e2e_t = []
+    for k in range(args.warmup + max(2, args.steps // 2)):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f_dev.copy_(f_host, non_blocking=True)
+        sm.solve(f_dev, u_dev, tol=tol)
+        u_host.copy_(u_dev, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            e2e_t.append(e0.elapsed_time(e1))
+    e2e_ms = sum(e2e_t) / len(e2e_t)
+
+    # --- plain FP64 method on the same workload ---
+    s64 = make("fp64")
+    t64, i64, u64, _ = timed_solves(s64, f, max(1, args.steps // 2), 1)
+    ms64 = sum(t64) / len(t64)
+    rel_diff = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
+
+    # --- roofline of the dominant kernel class ---
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    pd = prof[dom]
+    per_launch_ms = pd["ms"] / max(pd["launches"], 1)
+    launches = sum(v["launches"] for v in prof.values())
+    ndofs = sm.ndofs
+    result = {
+        "ndofs": ndofs, "ms_mixed": ms, "ms_mixed_max": ms_max, "ms64": ms64,
+        "iters_mixed": i_mixed[-1]["iterations"], "res_mixed": i_mixed[-1]["rel_residual"],
+        "iters64": i64[-1]["iterations"], "res64": i64[-1]["rel_residual"],
+        "rel_diff_mixed_vs_fp64": rel_diff, "e2e_ms": e2e_ms, "bytes_h2d": f.numel() * 8,
+        "bytes_d2h": f.numel() * 8, "prof": prof, "dominant": dom,
+        "per_launch_ms": per_launch_ms, "launches": launches // max(args.steps, 1),
+        "launches_total": launches, "clocks": clk, "peaks": peaks, "peak_src": peak_src,
+    }
+    sm.close()
+    s64.close()
+    return result
+
+
+def make_len(d, spans, p, N, ne):
+    nx = 1
+    for s in spans:
+        nx *= s + p - 2
+    return N * (ne + p) * nx
+
+
+def roofline_entry(r):
+    peaks = r["peaks"]
+    dom = r["dominant"]
+    pd = r["prof"][dom]
+    secs = pd["ms"] / 1e3
+    clk_max = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    if dom in ("gemm32",):
+        # FP32 FMA on CUDA cores: 152 SMs x 128 lanes x 2 flop x max clock
+        peak = 152 * 128 * 2 * clk_max / 1e12
+        achieved = pd["flops"] / secs / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_note": "FP32 CUDA-core FMA rate from unit counts x max SM clock",
+                "per_launch_ms": r["per_launch_ms"], "launches": pd["launches"]}
+    achieved = pd["bytes"] / secs / 1e9
+    peak = peaks["hbm_gbs"]
+    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "peak_note": "%s hbm_gbs" % r["peak_src"],
+            "per_launch_ms": r["per_launch_ms"], "launches": pd["launches"]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="square64", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-leg", action="store_true")
+    ap.add_argument("--sample-slabs", type=int, default=8)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    if args.cpu_leg:
+        cpu_leg(args)
+        return
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
+    cfg = {"workload": args.workload, "domain": "unit %s" % {1: "interval", 2: "square", 3: "cube"}[d],
+           "spans": list(spans), "degree": p, "slabs": N, "time_elements_per_slab": ne,
+           "theta": 1.0, "tol": tol, "solver": "FGMRES(20) + 1 V-cycle, omega=0.5, nu=1/1",
+           "rhs": "N(0,1) B-spline coefficients, seed %d" % seed, "l2": "flushed between steps"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ncores = os.cpu_count()
+        r = run_cpu_leg(args.workload, args.sample_slabs, max(5.0, args.cpu_seconds))
+        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * r["seconds_per_solve"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": cfg,
+                "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "host_cores_available": ncores,
+                                 "sample": "%d of %d slabs (%d dofs), same grid/degree/slab size, "
+                                           "%d solves" % (r["sample_slabs"], N, r["sample_dofs"], r["reps"])},
+                "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = gpu_arm(args, rank, world)
+    if rank != 0:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+        return
+    ndofs = r["ndofs"]
+    value = ndofs * world / (r["ms_mixed_max"] / 1e3)
+    cpu = None
+    if not args.no_cpu and world == 1:
+        try:
+            cb = run_cpu_leg(args.workload, args.sample_slabs, args.cpu_seconds)
+            cpu = {"value": cb["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "host_cores_available": os.cpu_count(),
+                   "sample": "%d of %d slabs (%d dofs), same grid/degree/slab size, FGMRES + V-cycle "
+                             "with sparse-LU slab solves, %d solves" % (
+                                 cb["sample_slabs"], N, cb["sample_dofs"], cb["reps"])}
+        except Exception as e:  # the GPU number stands without it
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)[:200]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_mixed_max"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": cfg,
+        "iterations": r["iters_mixed"], "rel_residual": r["res_mixed"],
+        "fp64_plain": {"value": ndofs * world / (r["ms64"] / 1e3), "ms_per_step": r["ms64"],
+                       "iterations": r["iters64"], "rel_residual": r["res64"], "dtype": "f64"},
+        "mixed_vs_fp64_solution_rel_diff": r["rel_diff_mixed_vs_fp64"],
+        "roofline": roofline_entry(r),
+        "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                               "share": v["ms"] / max(1e-12, sum(x["ms"] for x in r["prof"].values()))}
+                           for k, v in r["prof"].items() if v["launches"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": ndofs * world / (r["e2e_ms"] / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": r["bytes_h2d"], "d2h_bytes_per_step": r["bytes_d2h"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

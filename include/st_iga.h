@@ -1,0 +1,208 @@
+/*
+ * st_iga.h -- C ABI of the GB300 space-time multigrid library (libst_iga.so).
+ *
+ * The library solves the linear system L_h u = f of the space-time
+ * discontinuous-Galerkin isogeometric (SUPG, "time-upwind") discretisation of
+ * the heat equation  d_t u - Laplace u = f  on (0,1)^d x (0,T), u = 0 on the
+ * spatial boundary, u(0) = 0 (Hofer, Langer, Neumueller, arXiv:1802.09277,
+ * Eq. 1.1 and Sec. 2.2-2.3).  L_h is block lower bidiagonal over N time slabs
+ * (Eq. 2.4): diagonal blocks A_n = K_t (x) M_x + M_t (x) K_x (Eq. 2.5, time
+ * matrices Eq. 2.6) and sub-diagonal blocks -B_n = -N_t (x) M_x.
+ *
+ * The solver is the time-parallel multigrid of Sec. 3.1: damped block-Jacobi
+ * smoothing u <- u + omega D^{-1} (f - L_h u), D = blockdiag(A_n), where each
+ * A_n^{-1} is applied through the factorisation of Eq. 3.1,
+ *   A^{-1} = (X (x) I) (Z (x) M_x + I (x) K_x)^{-1} (Y (x) I),  Y = (M_t X)^{-1},
+ * with (X, Z) the real Schur factors of M_t^{-1} K_t (Sec. 3.5, Eq. 3.5), and
+ * the spatial problems K_x + z M_x solved exactly by fast diagonalisation in
+ * the generalized eigenbasis of the 1D matrices (K1 U = M1 U Lambda,
+ * U^T M1 U = I).  Time coarsening merges slab pairs.  The V-cycle
+ * preconditions an FP64 FGMRES (or is iterated directly).
+ *
+ * Conventions for every entry point:
+ *  - Vectors are FP64 DEVICE pointers, owned by the caller, never freed or
+ *    retained by the library, laid out as v[rhs][slab][t][z][y][x] (x fastest;
+ *    unused axes have extent 1).  Length = st_sizes().n_dofs.
+ *  - All device work is enqueued on the handle's CUDA stream (st_setup /
+ *    st_set_stream).  Calls returning results to the host (st_solve's info,
+ *    st_last_error) synchronise that stream; the others do not.
+ *  - Every function returns ST_OK (0) or a negative ST_ERR_* code; the
+ *    message of the last failure on the calling thread is st_last_error().
+ *    No C++ exception crosses this interface.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef ST_IGA_H
+#define ST_IGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ST_OK                   0
+#define ST_ERR_INVALID_ARG     -1  /* bad pointer, size, option or geometry      */
+#define ST_ERR_OOM             -2  /* device allocation failed                   */
+#define ST_ERR_NOT_POSITIVE    -3  /* Re lambda(K_t, M_t) <= 0 (Sec. 3.2 remark: use smaller theta) */
+#define ST_ERR_ILL_CONDITIONED -4  /* a time or space factorisation failed its residual check */
+#define ST_ERR_NO_CONVERGENCE  -5  /* iteration cap reached above the tolerance  */
+#define ST_ERR_TIMEOUT         -6  /* a bounded device wait ran out              */
+#define ST_ERR_CUDA            -7  /* a CUDA runtime call failed                 */
+#define ST_ERR_OVER_BUDGET     -8  /* request exceeds the HBM budget             */
+#define ST_ERR_UNSUPPORTED     -9  /* valid but not built (e.g. degree > 3)      */
+
+/* geometry: the spatial domain (0,1)^d */
+#define ST_INTERVAL 1
+#define ST_SQUARE   2
+#define ST_CUBE     3
+
+/* precision of the multigrid preconditioner (the outer iteration is FP64) */
+#define ST_FP64        0  /* everything FP64                                  */
+#define ST_MIXED_FP32  1  /* V-cycle in FP32 (CUDA cores), FP64 outer          */
+#define ST_MIXED_TF32  2  /* V-cycle FP32, spatial transforms on TF32 tensor cores */
+#define ST_MIXED_BF16  3  /* V-cycle FP32, spatial transforms on BF16 tensor cores */
+
+/* outer iteration */
+#define ST_OUTER_FGMRES 0 /* FGMRES(restart), right-preconditioned by one V-cycle */
+#define ST_OUTER_MG     1 /* multigrid iteration u <- u + V(f - L u)             */
+
+typedef struct st_handle_s *st_handle;
+
+typedef struct {
+    double T;             /* final time (default 1)                              */
+    double theta;         /* SUPG parameter theta_n, all slabs (default 1)       */
+    double omega;         /* block-Jacobi damping (default 0.5, Sec. 3.1)        */
+    int ne_per_slab;      /* time elements per slab (default 2)                  */
+    int nu1, nu2;         /* pre/post smoothing steps (default 1, 1)             */
+    int precision;        /* ST_FP64 / ST_MIXED_*                                */
+    int outer;            /* ST_OUTER_FGMRES / ST_OUTER_MG                       */
+    int gmres_restart;    /* FGMRES restart length (default 20)                  */
+    int max_it;           /* outer iteration cap (default 200)                   */
+    int nrhs;             /* independent right-hand sides solved together (1)    */
+    size_t hbm_budget;    /* bytes the handle may allocate; 0 = unlimited        */
+} st_options;
+
+typedef struct {
+    int iterations;       /* outer iterations (V-cycles) taken                   */
+    int status;           /* ST_OK or ST_ERR_NO_CONVERGENCE                      */
+    double rel_residual;  /* max over rhs of ||f - L u||_2 / ||f||_2 (FP64)       */
+    double seconds;       /* wall time of the solve, host clock                 */
+} st_solve_info;
+
+/* Fill *opt with the defaults listed above. */
+void st_options_default(st_options *opt);
+
+/* Build a handle: B-spline bases (Sec. 2.1), the 1D matrices M1, K1 (after
+ * Eq. 2.5) and per multigrid level K_t, M_t (Eq. 2.6, theta*h frozen at the
+ * finest value on coarse levels), the real Schur factors of M_t^{-1} K_t with
+ * Y = (M_t X)^{-1} (Sec. 3.2, 3.5), the generalized eigenpairs of (K1, M1),
+ * and the time prolongation of two slabs onto one (Sec. 3.1); uploads them and
+ * allocates all device work buffers.
+ *   geometry : ST_INTERVAL / ST_SQUARE / ST_CUBE (d = 1, 2, 3)
+ *   degree   : B-spline degree p in space and time, 1..3
+ *   spans    : d knot-span counts (x, y, z), each >= 2; n = spans + p - 2
+ *              interior dofs per axis (Dirichlet ends removed)
+ *   slabs    : number N of time slabs, >= 1
+ *   opt      : options (NULL = defaults)
+ *   stream   : cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Errors: INVALID_ARG, UNSUPPORTED, NOT_POSITIVE (Re lambda <= 0 on some
+ * level), ILL_CONDITIONED, OVER_BUDGET, OOM, CUDA.  *out is NULL on error. */
+int st_setup(st_handle *out, int geometry, int degree, const int *spans,
+             int slabs, const st_options *opt, void *stream);
+
+/* Same as st_setup but builds only the host-side FP64 factors (no CUDA call,
+ * no device memory): st_sizes, st_time_factors, st_space_factors and
+ * st_time_prolongation work on such a handle, every entry point that touches
+ * device vectors returns ST_ERR_INVALID_ARG.  Usable on a machine without a
+ * GPU. */
+int st_setup_host(st_handle *out, int geometry, int degree, const int *spans,
+                  int slabs, const st_options *opt);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void st_destroy(st_handle h);
+
+/* Change the stream later calls enqueue on. */
+int st_set_stream(st_handle h, void *stream);
+
+/* Sizes: total dofs (all rhs), time dofs per slab N_t = ne + p, interior
+ * dofs per axis (3 entries, unused axes 1), number of multigrid levels and
+ * device bytes held by the handle.  Any output pointer may be NULL. */
+int st_sizes(st_handle h, int64_t *n_dofs, int *n_t, int *n_x_per_axis,
+             int *n_levels, size_t *device_bytes);
+
+/* y = L_h x (Eq. 2.4), matrix-free through the Kronecker factors of
+ * Eq. 2.5 (FP64).  x, y: device, n_dofs each, must not alias. */
+int st_apply(st_handle h, const double *x, double *y);
+
+/* r = f - L_h u (FP64).  u, f, r: device, n_dofs each; r must not alias u. */
+int st_residual(st_handle h, const double *u, const double *f, double *r);
+
+/* Load vector of a source given by its B-spline coefficients in the trial
+ * basis of every slab: f = (M_t (x) M_x) c, which is l_h(phi_i) of Sec. 2.3
+ * exactly (u0 = 0).  c, f: device, n_dofs each, must not alias. */
+int st_load_coeffs(st_handle h, const double *c, double *f);
+
+/* nsteps damped block-Jacobi steps on the finest level (Sec. 3.1):
+ * u <- u + omega D^{-1}(f - L_h u), A_n^{-1} applied through Eq. 3.1.
+ * Runs in the handle's precision (FP32 inside for the mixed modes, u and f
+ * stay FP64 at the interface).  u: in/out, f: in, device, n_dofs each. */
+int st_smooth(st_handle h, double *u, const double *f, int nsteps);
+
+/* One V-cycle on L_h u = f starting from u (in/out), precision as above. */
+int st_vcycle(st_handle h, double *u, const double *f);
+
+/* Solve L_h u = rhs to ||rhs - L_h u||_2 <= tol ||rhs||_2 per right-hand
+ * side with the outer iteration of opt.outer, zero initial guess when
+ * use_guess == 0 (else u holds the guess).  rhs, u: device, n_dofs.
+ * info may be NULL.  Returns ST_ERR_NO_CONVERGENCE (u holds the last
+ * iterate) when max_it is reached. */
+int st_solve(st_handle h, const double *rhs, double tol, double *u,
+             int use_guess, st_solve_info *info);
+
+/* Per-kernel-class device timing for measurement.  While enabled, every
+ * kernel launch of the handle is bracketed by CUDA events on the handle's
+ * stream and its algorithmic bytes and flops (counted from the launch sizes:
+ * each input and output vector once, the arithmetic of the method, no halo
+ * or tile overhead) are accumulated per class.  st_profile(h, 1) resets and
+ * starts, st_profile(h, 0) stops; both synchronise the stream.
+ * st_profile_read returns launches, summed device milliseconds, bytes and
+ * flops of one class; it synchronises the stream. */
+#define ST_PROF_STENCIL64 0  /* residual / operator / load vector, FP64      */
+#define ST_PROF_STENCIL32 1  /* residual + fused forward time transform, FP32 */
+#define ST_PROF_GEMM64    2  /* spatial transform (one axis), FP64           */
+#define ST_PROF_GEMM32    3  /* spatial transform (one axis), FP32           */
+#define ST_PROF_SHIFT     4  /* quasi-triangular shift solve per mode        */
+#define ST_PROF_UPDATE    5  /* backward time transform + damped update      */
+#define ST_PROF_TRANSFER  6  /* time restriction / prolongation             */
+#define ST_PROF_VECTOR    7  /* FGMRES vector kernels, precision conversion  */
+#define ST_PROF_NCLASS    8
+int st_profile(st_handle h, int enable);
+int st_profile_read(st_handle h, int cls, int64_t *launches, double *ms,
+                    double *bytes, double *flops);
+
+/* Host copies of the FP64 setup factors, for inspection and tests.
+ * Time factors of level lvl (0 = finest), each nt x nt row-major, nt <= 8:
+ * K_t, M_t, X (= Q, orthogonal), Z (quasi upper triangular Schur form),
+ * Y = (M_t X)^{-1}; any output may be NULL. */
+int st_time_factors(st_handle h, int lvl, int *nt, double *Kt, double *Mt,
+                    double *X, double *Z, double *Y);
+
+/* Host copies of the 1D space factors of axis a (0 = x): dense n x n M1, K1,
+ * the generalized eigenvectors U (columns, U^T M1 U = I) and eigenvalues. */
+int st_space_factors(st_handle h, int axis, int *n, double *M1, double *K1,
+                     double *U, double *lam);
+
+/* The time prolongation P_t (2 nt x nt, row-major) that expresses one coarse
+ * slab in the bases of the two fine slabs it merges (Sec. 3.1). */
+int st_time_prolongation(st_handle h, int *nt, double *Pt);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *st_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ST_IGA_H */

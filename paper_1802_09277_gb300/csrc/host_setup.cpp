@@ -1,0 +1,511 @@
+// Host-side FP64 setup: see host_setup.h.
+#include "host_setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+namespace st {
+namespace host {
+
+static const double kPi = 3.14159265358979323846;
+
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        // initial guess for the i-th root (descending), Newton on P_n
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= n; ++k) {  // three-term recurrence
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            double dz = p0 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[n - 1 - i] = z;
+        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+std::vector<double> open_knots(double a, double b, int nel, int p) {
+    std::vector<double> k;
+    for (int i = 0; i < p; ++i) k.push_back(a);
+    for (int e = 0; e <= nel; ++e) k.push_back(a + (b - a) * e / nel);
+    k.back() = b;
+    for (int i = 0; i < p; ++i) k.push_back(b);
+    return k;
+}
+
+// index s of the span [t_s, t_{s+1}) holding x (p <= s < nb); the right end
+// belongs to the last non-empty span
+static int find_span(const std::vector<double> &t, int p, double x) {
+    const int nb = (int)t.size() - p - 1;
+    if (x >= t[nb]) {
+        int s = nb - 1;
+        while (s > p && t[s] == t[s + 1]) --s;
+        return s;
+    }
+    int s = p;
+    while (s < nb - 1 && x >= t[s + 1]) ++s;
+    return s;
+}
+
+void eval_basis(const std::vector<double> &t, int p, double x, std::vector<double> &val,
+                std::vector<double> &der) {
+    const int nb = (int)t.size() - p - 1;
+    val.assign(nb, 0.0);
+    der.assign(nb, 0.0);
+    const int s = find_span(t, p, x);
+    // tri[k][r] = N_{s-k+r, k}(x), r = 0..k: the degree-k functions that do
+    // not vanish on span s, raised one degree at a time
+    double tri[16][16] = {{0.0}};
+    tri[0][0] = 1.0;
+    for (int k = 1; k <= p; ++k) {
+        for (int r = 0; r <= k; ++r) {
+            const int i = s - k + r;
+            double v = 0.0;
+            if (r >= 1) {  // N_{i,k-1} = tri[k-1][r-1]
+                const double den = t[i + k] - t[i];
+                if (den > 0.0) v += (x - t[i]) / den * tri[k - 1][r - 1];
+            }
+            if (r <= k - 1) {  // N_{i+1,k-1} = tri[k-1][r]
+                const double den = t[i + k + 1] - t[i + 1];
+                if (den > 0.0) v += (t[i + k + 1] - x) / den * tri[k - 1][r];
+            }
+            tri[k][r] = v;
+        }
+    }
+    for (int r = 0; r <= p; ++r) {
+        const int i = s - p + r;
+        val[i] = tri[p][r];
+        if (p == 0) continue;
+        double d = 0.0;
+        if (r >= 1) {
+            const double den = t[i + p] - t[i];
+            if (den > 0.0) d += p / den * tri[p - 1][r - 1];
+        }
+        if (r <= p - 1) {
+            const double den = t[i + p + 1] - t[i + 1];
+            if (den > 0.0) d -= p / den * tri[p - 1][r];
+        }
+        der[i] = d;
+    }
+}
+
+void space_matrices(int s, int p, Mat &M1, Mat &K1) {
+    const std::vector<double> t = open_knots(0.0, 1.0, s, p);
+    const int nb = s + p, n = nb - 2;
+    Mat Mf(nb * nb, 0.0), Kf(nb * nb, 0.0);
+    std::vector<double> gx, gw, v, d;
+    gauss_legendre(p + 2, gx, gw);
+    for (int e = 0; e < s; ++e) {
+        const double a = (double)e / s, b = (double)(e + 1) / s;
+        for (size_t q = 0; q < gx.size(); ++q) {
+            const double x = 0.5 * (b - a) * (gx[q] + 1.0) + a, w = 0.5 * (b - a) * gw[q];
+            eval_basis(t, p, x, v, d);
+            for (int i = 0; i < nb; ++i) {
+                if (v[i] == 0.0 && d[i] == 0.0) continue;
+                for (int j = 0; j < nb; ++j) {
+                    Mf[i * nb + j] += w * v[i] * v[j];
+                    Kf[i * nb + j] += w * d[i] * d[j];
+                }
+            }
+        }
+    }
+    M1.assign(n * n, 0.0);
+    K1.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            M1[i * n + j] = Mf[(i + 1) * nb + j + 1];
+            K1[i * n + j] = Kf[(i + 1) * nb + j + 1];
+        }
+}
+
+void time_matrices(double tau, int ne, int p, double delta, Mat &Kt, Mat &Mt) {
+    const std::vector<double> t = open_knots(0.0, tau, ne, p);
+    const int nt = ne + p;
+    Kt.assign(nt * nt, 0.0);
+    Mt.assign(nt * nt, 0.0);
+    std::vector<double> gx, gw, v, d;
+    gauss_legendre(p + 2, gx, gw);
+    for (int e = 0; e < ne; ++e) {
+        const double a = tau * e / ne, b = tau * (e + 1) / ne;
+        for (size_t q = 0; q < gx.size(); ++q) {
+            const double x = 0.5 * (b - a) * (gx[q] + 1.0) + a, w = 0.5 * (b - a) * gw[q];
+            eval_basis(t, p, x, v, d);
+            for (int i = 0; i < nt; ++i) {
+                const double test = v[i] + delta * d[i];  // psi_i + theta h psi_i'
+                for (int j = 0; j < nt; ++j) {
+                    Kt[i * nt + j] += w * d[j] * test;
+                    Mt[i * nt + j] += w * v[j] * test;
+                }
+            }
+        }
+    }
+    eval_basis(t, p, 0.0, v, d);  // upwind term psi_j(t_{n-1}) psi_i(t_{n-1})
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j) Kt[i * nt + j] += v[j] * v[i];
+}
+
+void time_prolongation(double tau, int ne, int p, Mat &Pt) {
+    const int nt = ne + p;
+    const std::vector<double> tc = open_knots(0.0, 2.0 * tau, ne, p);
+    Pt.assign(2 * nt * nt, 0.0);
+    std::vector<double> v, d;
+    for (int q = 0; q < 2; ++q) {
+        const std::vector<double> tf = open_knots(q * tau, (q + 1) * tau, ne, p);
+        Mat Bf(nt * nt), Bc(nt * nt);
+        for (int m = 0; m < nt; ++m) {
+            double g = 0.0;  // Greville abscissa of fine function m
+            for (int k = 1; k <= p; ++k) g += tf[m + k];
+            g = (p > 0) ? g / p : tf[m];
+            eval_basis(tf, p, g, v, d);
+            for (int a = 0; a < nt; ++a) Bf[m * nt + a] = v[a];
+            eval_basis(tc, p, g, v, d);
+            for (int b = 0; b < nt; ++b) Bc[m * nt + b] = v[b];
+        }
+        lu_solve(nt, nt, Bf, Bc);
+        for (int a = 0; a < nt; ++a)
+            for (int b = 0; b < nt; ++b) Pt[(q * nt + a) * nt + b] = Bc[a * nt + b];
+    }
+}
+
+bool lu_solve(int n, int m, Mat A, Mat &B) {
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(A[i * n + k]) > std::fabs(A[piv * n + k])) piv = i;
+        if (A[piv * n + k] == 0.0) return false;
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) std::swap(A[k * n + j], A[piv * n + j]);
+            for (int j = 0; j < m; ++j) std::swap(B[k * m + j], B[piv * m + j]);
+        }
+        for (int i = k + 1; i < n; ++i) {
+            const double l = A[i * n + k] / A[k * n + k];
+            if (l == 0.0) continue;
+            for (int j = k; j < n; ++j) A[i * n + j] -= l * A[k * n + j];
+            for (int j = 0; j < m; ++j) B[i * m + j] -= l * B[k * m + j];
+        }
+    }
+    for (int i = n - 1; i >= 0; --i)
+        for (int j = 0; j < m; ++j) {
+            double s = B[i * m + j];
+            for (int k = i + 1; k < n; ++k) s -= A[i * n + k] * B[k * m + j];
+            B[i * m + j] = s / A[i * n + i];
+        }
+    return true;
+}
+
+double frob(const Mat &A) {
+    double s = 0.0;
+    for (double a : A) s += a * a;
+    return std::sqrt(s);
+}
+
+Mat matmul(int n, const Mat &A, const Mat &B) {
+    Mat C(n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const double a = A[i * n + k];
+            for (int j = 0; j < n; ++j) C[i * n + j] += a * B[k * n + j];
+        }
+    return C;
+}
+
+double resid_norm(int n, const Mat &A, const Mat &B, const Mat &C) {
+    Mat P = matmul(n, A, B);
+    double s = 0.0;
+    for (int i = 0; i < n * n; ++i) s += (P[i] - C[i]) * (P[i] - C[i]);
+    return std::sqrt(s);
+}
+
+bool sym_gen_eig(int n, const Mat &K, const Mat &M, Mat &U, std::vector<double> &lam,
+                 std::string &err) {
+    // Cholesky M = L L^T (L lower)
+    Mat L(n * n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        double s = M[j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+        if (!(s > 0.0)) {
+            err = "space mass matrix is not positive definite";
+            return false;
+        }
+        L[j * n + j] = std::sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = M[i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = t / L[j * n + j];
+        }
+    }
+    // C = L^{-1} K L^{-T}: first W = L^{-1} K (forward substitution per column)
+    Mat W(K);
+    for (int c = 0; c < n; ++c)
+        for (int i = 0; i < n; ++i) {
+            double s = W[i * n + c];
+            for (int k = 0; k < i; ++k) s -= L[i * n + k] * W[k * n + c];
+            W[i * n + c] = s / L[i * n + i];
+        }
+    // C^T = L^{-1} W^T, and C is symmetric
+    Mat C(n * n);
+    for (int r = 0; r < n; ++r)
+        for (int i = 0; i < n; ++i) {
+            double s = W[r * n + i];
+            for (int k = 0; k < i; ++k) s -= L[i * n + k] * C[r * n + k];
+            C[r * n + i] = s / L[i * n + i];
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            const double a = 0.5 * (C[i * n + j] + C[j * n + i]);
+            C[i * n + j] = C[j * n + i] = a;
+        }
+    // cyclic Jacobi: C <- J^T C J until off-diagonal mass is negligible
+    Mat V(n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
+    const double cnorm = frob(C);
+    bool converged = (n == 1);
+    for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += C[i * n + j] * C[i * n + j];
+        if (std::sqrt(2.0 * off) <= 1e-17 * cnorm) {
+            converged = true;
+            break;
+        }
+        for (int pi = 0; pi < n - 1; ++pi)
+            for (int qi = pi + 1; qi < n; ++qi) {
+                const double apq = C[pi * n + qi];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double app = C[pi * n + pi], aqq = C[qi * n + qi];
+                const double th = (aqq - app) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // columns p, q
+                    const double ckp = C[k * n + pi], ckq = C[k * n + qi];
+                    C[k * n + pi] = c * ckp - s * ckq;
+                    C[k * n + qi] = s * ckp + c * ckq;
+                }
+                for (int k = 0; k < n; ++k) {  // rows p, q
+                    const double cpk = C[pi * n + k], cqk = C[qi * n + k];
+                    C[pi * n + k] = c * cpk - s * cqk;
+                    C[qi * n + k] = s * cpk + c * cqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[k * n + pi], vkq = V[k * n + qi];
+                    V[k * n + pi] = c * vkp - s * vkq;
+                    V[k * n + qi] = s * vkp + c * vkq;
+                }
+            }
+    }
+    if (!converged) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += C[i * n + j] * C[i * n + j];
+        if (std::sqrt(2.0 * off) > 1e-13 * cnorm) {
+            err = "Jacobi eigensolver did not converge";
+            return false;
+        }
+    }
+    // sort ascending, U = L^{-T} V
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return C[a * n + a] < C[b * n + b]; });
+    lam.resize(n);
+    U.assign(n * n, 0.0);
+    for (int c = 0; c < n; ++c) {
+        lam[c] = C[idx[c] * n + idx[c]];
+        for (int i = n - 1; i >= 0; --i) {  // back substitution with L^T
+            double s = V[i * n + idx[c]];
+            for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * U[k * n + c];
+            U[i * n + c] = s / L[i * n + i];
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Real Schur form
+// ---------------------------------------------------------------------------
+
+// Apply the reflector I - beta v v^T (v of length m, rows/cols k..k+m-1).
+static void reflect_rows(int n, Mat &H, int k, int m, const double *v, double beta, int c0, int c1) {
+    for (int j = c0; j <= c1; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += v[i] * H[(k + i) * n + j];
+        s *= beta;
+        for (int i = 0; i < m; ++i) H[(k + i) * n + j] -= s * v[i];
+    }
+}
+static void reflect_cols(int n, Mat &H, int k, int m, const double *v, double beta, int r0, int r1) {
+    for (int i = r0; i <= r1; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s += H[i * n + k + j] * v[j];
+        s *= beta;
+        for (int j = 0; j < m; ++j) H[i * n + k + j] -= s * v[j];
+    }
+}
+// v, beta with (I - beta v v^T) x = -sign(x0) ||x|| e1; returns false if x = 0
+static bool householder(int m, const double *x, double *v, double &beta) {
+    double nrm = 0.0;
+    for (int i = 0; i < m; ++i) nrm += x[i] * x[i];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0.0) return false;
+    const double alpha = (x[0] >= 0.0) ? -nrm : nrm;
+    for (int i = 0; i < m; ++i) v[i] = x[i];
+    v[0] -= alpha;
+    double vv = 0.0;
+    for (int i = 0; i < m; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) return false;
+    beta = 2.0 / vv;
+    return true;
+}
+
+// Rotate rows/cols k, k+1 by G = [[c, -s], [s, c]] : H <- G^T H G, Q <- Q G
+static void rotate(int n, Mat &H, Mat &Q, int k, double c, double s) {
+    for (int j = 0; j < n; ++j) {
+        const double a = H[k * n + j], b = H[(k + 1) * n + j];
+        H[k * n + j] = c * a + s * b;
+        H[(k + 1) * n + j] = -s * a + c * b;
+    }
+    for (int i = 0; i < n; ++i) {
+        const double a = H[i * n + k], b = H[i * n + k + 1];
+        H[i * n + k] = c * a + s * b;
+        H[i * n + k + 1] = -s * a + c * b;
+        const double qa = Q[i * n + k], qb = Q[i * n + k + 1];
+        Q[i * n + k] = c * qa + s * qb;
+        Q[i * n + k + 1] = -s * qa + c * qb;
+    }
+}
+
+bool real_schur(int n, const Mat &A, Mat &Q, Mat &T, std::vector<int> &blk, std::string &err) {
+    Mat H(A);
+    Q.assign(n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[i * n + i] = 1.0;
+    double v[16], x[16], beta;
+    // 1. Householder reduction to upper Hessenberg form
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;
+        for (int i = 0; i < m; ++i) x[i] = H[(k + 1 + i) * n + k];
+        if (!householder(m, x, v, beta)) continue;
+        reflect_rows(n, H, k + 1, m, v, beta, 0, n - 1);
+        reflect_cols(n, H, k + 1, m, v, beta, 0, n - 1);
+        reflect_cols(n, Q, k + 1, m, v, beta, 0, n - 1);
+        for (int i = k + 2; i < n; ++i) H[i * n + k] = 0.0;
+    }
+    // 2. Francis double-shift QR with deflation
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1, iter = 0;
+    while (hi >= 0) {
+        if (iter > 60 * n) {
+            err = "Francis QR iteration did not converge";
+            return false;
+        }
+        int lo = hi;  // start of the unreduced block ending at hi
+        while (lo > 0) {
+            const double sub = std::fabs(H[lo * n + lo - 1]);
+            double scale = std::fabs(H[(lo - 1) * n + lo - 1]) + std::fabs(H[lo * n + lo]);
+            if (scale == 0.0) scale = frob(H);
+            if (sub <= eps * scale) {
+                H[lo * n + lo - 1] = 0.0;
+                break;
+            }
+            --lo;
+        }
+        if (lo == hi) {  // 1x1 block converged
+            --hi;
+            iter = 0;
+            continue;
+        }
+        if (lo == hi - 1) {  // 2x2 block: split it if its eigenvalues are real
+            const int k = lo;
+            const double a = H[k * n + k], b = H[k * n + k + 1];
+            const double c = H[(k + 1) * n + k], d = H[(k + 1) * n + k + 1];
+            const double hd = 0.5 * (a - d), disc = hd * hd + b * c;
+            if (disc >= 0.0) {
+                const double r = std::sqrt(disc);
+                const double l1 = 0.5 * (a + d) + (hd >= 0 ? r : -r);  // larger |.| root
+                // eigenvector of [[a,b],[c,d]] for l1 as first rotation column
+                double e0 = b, e1 = l1 - a;
+                if (std::fabs(l1 - d) + std::fabs(c) > std::fabs(e0) + std::fabs(e1)) {
+                    e0 = l1 - d;
+                    e1 = c;
+                }
+                const double nr = std::hypot(e0, e1);
+                if (nr > 0.0) {
+                    rotate(n, H, Q, k, e0 / nr, e1 / nr);
+                    H[(k + 1) * n + k] = 0.0;
+                }
+            }
+            hi -= 2;
+            iter = 0;
+            continue;
+        }
+        // Francis double-shift step on the window lo..hi
+        ++iter;
+        double s = H[(hi - 1) * n + hi - 1] + H[hi * n + hi];
+        double t = H[(hi - 1) * n + hi - 1] * H[hi * n + hi] - H[(hi - 1) * n + hi] * H[hi * n + hi - 1];
+        if (iter % 11 == 0) {  // exceptional shift
+            const double w = std::fabs(H[hi * n + hi - 1]) + std::fabs(H[(hi - 1) * n + hi - 2]);
+            s = 1.5 * w;
+            t = w * w;
+        }
+        double X0 = H[lo * n + lo] * H[lo * n + lo] + H[lo * n + lo + 1] * H[(lo + 1) * n + lo] -
+                    s * H[lo * n + lo] + t;
+        double X1 = H[(lo + 1) * n + lo] * (H[lo * n + lo] + H[(lo + 1) * n + lo + 1] - s);
+        double X2 = H[(lo + 1) * n + lo] * H[(lo + 2) * n + lo + 1];
+        for (int k = lo; k <= hi - 2; ++k) {
+            x[0] = X0;
+            x[1] = X1;
+            x[2] = X2;
+            if (householder(3, x, v, beta)) {
+                const int r = std::max(lo, k - 1);
+                reflect_rows(n, H, k, 3, v, beta, r, n - 1);
+                const int rr = std::min(k + 3, hi);
+                reflect_cols(n, H, k, 3, v, beta, 0, rr);
+                reflect_cols(n, Q, k, 3, v, beta, 0, n - 1);
+            }
+            X0 = H[(k + 1) * n + k];
+            X1 = H[(k + 2) * n + k];
+            if (k < hi - 2) X2 = H[(k + 3) * n + k];
+        }
+        x[0] = X0;
+        x[1] = X1;
+        if (householder(2, x, v, beta)) {
+            reflect_rows(n, H, hi - 1, 2, v, beta, hi - 2, n - 1);
+            reflect_cols(n, H, hi - 1, 2, v, beta, 0, hi);
+            reflect_cols(n, Q, hi - 1, 2, v, beta, 0, n - 1);
+        }
+        for (int i = lo + 2; i <= hi; ++i)
+            for (int j = lo; j < i - 1; ++j) H[i * n + j] = 0.0;
+    }
+    T = H;
+    blk.assign(n, 0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+            if (i > j + 1) T[i * n + j] = 0.0;
+    for (int i = 1; i < n; ++i)
+        if (T[i * n + i - 1] != 0.0) blk[i] = 1;
+    for (int i = 1; i < n; ++i)
+        if (blk[i] && i >= 2 && blk[i - 1]) {
+            err = "Schur form has overlapping 2x2 blocks";
+            return false;
+        }
+    // residual check ||A Q - Q T|| <= tol ||A||
+    const double r = std::sqrt(std::pow(resid_norm(n, A, Q, matmul(n, Q, T)), 2));
+    if (!(r <= 1e-12 * std::max(1.0, frob(A)))) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "Schur residual %.3e too large", r);
+        err = buf;
+        return false;
+    }
+    return true;
+}
+
+}  // namespace host
+}  // namespace st

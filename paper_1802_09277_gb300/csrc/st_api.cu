@@ -1,0 +1,1009 @@
+// C ABI of the space-time multigrid library (see include/st_iga.h).
+//
+// Host orchestration: setup of the FP64 factors, device buffers, the damped
+// block-Jacobi smoothing step (Sec. 3.1 with A_n^{-1} through Eq. 3.1), the
+// time-coarsening V-cycle and the FP64 outer iteration (FGMRES or plain
+// multigrid iteration).  All arithmetic on vectors runs in the kernels of
+// kernels_*.cu on the handle's stream.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/st_iga.h"
+#include "host_setup.h"
+#include "st_internal.h"
+
+using namespace st;
+using host::Mat;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(...)                                                                          \
+    do {                                                                                 \
+        cudaError_t e_ = (__VA_ARGS__);                                                  \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(ST_ERR_CUDA, "%s failed: %s", #__VA_ARGS__, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKS(...)                       \
+    do {                               \
+        int s_ = (__VA_ARGS__);        \
+        if (s_ != ST_OK) return s_;    \
+    } while (0)
+
+struct LevelHost {
+    int nslab;  // slabs per problem
+    double tau;
+    Mat Kt, Mt, X, Z, Y;
+    std::vector<int> blk;
+};
+
+template <typename T>
+struct DevSpace {  // device copies of the 1D factors in one precision
+    Bands<T> bands{};
+    const T *U[3] = {nullptr, nullptr, nullptr};   // W = U  (forward, U^T applied)
+    const T *Ut[3] = {nullptr, nullptr, nullptr};  // W = U^T (inverse, U applied)
+    const T *lam[3] = {nullptr, nullptr, nullptr};
+};
+
+template <typename T>
+struct Work {  // multigrid vectors in the V-cycle precision
+    std::vector<T *> u, f;  // per level (level 0 entries only used in mixed mode)
+    T *w0 = nullptr, *w1 = nullptr;
+};
+
+}  // namespace
+
+struct st_handle_s {
+    int dim = 1, p = 1, N = 1, nt = 2, nrhs = 1, nlev = 1;
+    int spans[3] = {1, 1, 1};
+    int n[3] = {1, 1, 1};
+    st_options opt{};
+    cudaStream_t stream = nullptr;
+    Grid g{};
+    long long len = 0;  // dofs per rhs on level 0
+    bool host_only = false;
+    bool mixed = false;
+    // host factors
+    Mat M1[3], K1[3], U[3], Pt;
+    std::vector<double> lam[3];
+    std::vector<LevelHost> lv;
+    // device
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    DevSpace<double> s64;
+    DevSpace<float> s32;
+    Work<double> w64;
+    Work<float> w32;
+    // per-kernel-class profiling (CUDA events around each launch)
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes, flops;
+    };
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_next = 0;
+    std::vector<ProfRec> recs;
+    long long prof_n[ST_PROF_NCLASS] = {0};
+    double prof_ms[ST_PROF_NCLASS] = {0}, prof_bytes[ST_PROF_NCLASS] = {0},
+           prof_flops[ST_PROF_NCLASS] = {0};
+    // outer iteration
+    std::vector<double *> V, Zk;
+    double *partial = nullptr, *dots = nullptr;
+    int nblk_dot = 0;
+    int krylov_m = 0;
+};
+
+namespace {
+
+int dalloc(st_handle h, size_t bytes, void **out) {
+    if (h->opt.hbm_budget && h->bytes + bytes > h->opt.hbm_budget)
+        return fail(ST_ERR_OVER_BUDGET, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu used)",
+                    bytes, h->bytes, h->opt.hbm_budget);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ST_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    h->allocs.push_back(p);
+    h->bytes += bytes;
+    *out = p;
+    return ST_OK;
+}
+
+// ---- profiling --------------------------------------------------------------
+cudaEvent_t next_event(st_handle h) {
+    if (h->ev_next == h->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_next++];
+}
+
+// Fold completed records into the per-class totals.  Only called when the
+// handle's stream is idle (after a synchronisation).
+void prof_fold(st_handle h) {
+    for (const auto &r : h->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        h->prof_n[r.cls] += 1;
+        h->prof_ms[r.cls] += ms;
+        h->prof_bytes[r.cls] += r.bytes;
+        h->prof_flops[r.cls] += r.flops;
+    }
+    h->recs.clear();
+    h->ev_next = 0;
+}
+
+// Records [start, stop) events around one launch when profiling is on.
+struct KScope {
+    st_handle h;
+    int cls;
+    double bytes, flops;
+    cudaEvent_t a = nullptr;
+    KScope(st_handle h_, int c, double by, double fl) : h(h_), cls(c), bytes(by), flops(fl) {
+        if (h->prof_on && (a = next_event(h))) cudaEventRecord(a, h->stream);
+    }
+    ~KScope() {
+        if (!a) return;
+        cudaEvent_t b = next_event(h);
+        if (!b) return;
+        cudaEventRecord(b, h->stream);
+        h->recs.push_back({cls, a, b, bytes, flops});
+    }
+};
+
+template <typename T>
+constexpr int cls_of(int c64, int c32) { return sizeof(T) == 8 ? c64 : c32; }
+
+template <typename T>
+int upload(st_handle h, const std::vector<double> &src, const T **out) {
+    std::vector<T> tmp(src.begin(), src.end());
+    void *p;
+    CKS(dalloc(h, tmp.size() * sizeof(T), &p));
+    CK(cudaMemcpy(p, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice));
+    *out = static_cast<const T *>(p);
+    return ST_OK;
+}
+
+template <typename T>
+int upload_space(st_handle h, DevSpace<T> &ds, const std::vector<double> bandM[3],
+                 const std::vector<double> bandK[3]) {
+    for (int a = 0; a < h->dim; ++a) {
+        const int n = h->n[a];
+        CKS(upload<T>(h, bandM[a], &ds.bands.M[a]));
+        CKS(upload<T>(h, bandK[a], &ds.bands.K[a]));
+        CKS(upload<T>(h, h->U[a], &ds.U[a]));
+        Mat Ut(n * n);
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < n; ++k) Ut[k * n + i] = h->U[a][i * n + k];
+        CKS(upload<T>(h, Ut, &ds.Ut[a]));
+        CKS(upload<T>(h, h->lam[a], &ds.lam[a]));
+    }
+    for (int a = h->dim; a < 3; ++a) {
+        ds.bands.M[a] = ds.bands.K[a] = nullptr;
+        ds.U[a] = ds.Ut[a] = ds.lam[a] = nullptr;
+    }
+    return ST_OK;
+}
+
+template <typename T>
+int alloc_work(st_handle h, Work<T> &w, bool level0) {
+    const size_t e0 = (size_t)h->len * h->nrhs;
+    void *p;
+    CKS(dalloc(h, e0 * sizeof(T), &p));
+    w.w0 = (T *)p;
+    CKS(dalloc(h, e0 * sizeof(T), &p));
+    w.w1 = (T *)p;
+    w.u.assign(h->nlev, nullptr);
+    w.f.assign(h->nlev, nullptr);
+    for (int l = level0 ? 0 : 1; l < h->nlev; ++l) {
+        const size_t e = (size_t)h->lv[l].nslab * h->nt * h->g.nxyz * h->nrhs;
+        CKS(dalloc(h, e * sizeof(T), &p));
+        w.u[l] = (T *)p;
+        CKS(dalloc(h, e * sizeof(T), &p));
+        w.f[l] = (T *)p;
+    }
+    return ST_OK;
+}
+
+// ---- coefficient packing ----------------------------------------------------
+template <typename T>
+TimeCoefs<T> pack_time(st_handle h, int l, int mode, bool fuse_y) {
+    TimeCoefs<T> tc;
+    std::memset(&tc, 0, sizeof tc);
+    const int nt = h->nt;
+    const LevelHost &L = h->lv[l];
+    for (int i = 0; i < nt; ++i)
+        for (int j = 0; j < nt; ++j) {
+            if (mode == MODE_MASS) {
+                tc.CK[i * NTMAX + j] = (T)L.Mt[i * nt + j];
+                tc.CM[i * NTMAX + j] = T(0);
+            } else {
+                tc.CK[i * NTMAX + j] = (T)L.Kt[i * nt + j];
+                tc.CM[i * NTMAX + j] = (T)L.Mt[i * nt + j];
+            }
+            tc.Y[i * NTMAX + j] = (T)L.Y[i * nt + j];
+        }
+    tc.nt = nt;
+    tc.fuse_y = fuse_y ? 1 : 0;
+    tc.mode = mode;
+    return tc;
+}
+
+template <typename T>
+SchurCoefs<T> pack_schur(st_handle h, int l) {
+    SchurCoefs<T> sc;
+    std::memset(&sc, 0, sizeof sc);
+    const int nt = h->nt;
+    const LevelHost &L = h->lv[l];
+    for (int i = 0; i < nt; ++i) {
+        for (int j = 0; j < nt; ++j) {
+            sc.Z[i * NTMAX + j] = (T)L.Z[i * nt + j];
+            sc.X[i * NTMAX + j] = (T)L.X[i * nt + j];
+        }
+        sc.blk[i] = L.blk[i];
+    }
+    sc.nt = nt;
+    return sc;
+}
+
+template <typename T>
+ProlongCoefs<T> pack_prolong(st_handle h) {
+    ProlongCoefs<T> pc;
+    std::memset(&pc, 0, sizeof pc);
+    const int nt = h->nt;
+    for (int r = 0; r < 2 * nt; ++r)
+        for (int c = 0; c < nt; ++c) pc.P[r * NTMAX + c] = (T)h->Pt[r * nt + c];
+    pc.nt = nt;
+    return pc;
+}
+
+template <typename T>
+DevSpace<T> &space(st_handle h);
+template <>
+DevSpace<double> &space<double>(st_handle h) { return h->s64; }
+template <>
+DevSpace<float> &space<float>(st_handle h) { return h->s32; }
+template <typename T>
+Work<T> &work(st_handle h);
+template <>
+Work<double> &work<double>(st_handle h) { return h->w64; }
+template <>
+Work<float> &work<float>(st_handle h) { return h->w32; }
+
+// ---- operator pieces --------------------------------------------------------
+template <typename T>
+int stencil(st_handle h, int l, const T *u, const T *f, T *out, int mode, bool fuse_y, int slab0,
+            int nslabs) {
+    const TimeCoefs<T> tc = pack_time<T>(h, l, mode, fuse_y);
+    // algorithmic traffic: u and out once (+ f for the residual, + the
+    // coupling plane), flops of the sum-factorised applies on every plane
+    const double E = (double)nslabs * h->nt * h->g.nxyz;
+    const double planes_pt = (double)nslabs * (h->nt + (mode == MODE_MASS ? 0 : 1)) * h->g.nxyz;
+    const int W = 2 * h->p + 1;
+    const double fsp = 4.0 * W + (h->dim >= 2 ? 6.0 * W : 0) + (h->dim >= 3 ? 6.0 * W : 0);
+    const double bytes = sizeof(T) * (2.0 * E + (mode == MODE_RES ? E : 0.0) +
+                                      (mode == MODE_MASS ? 0.0 : (double)nslabs * h->g.nxyz));
+    const double flops = planes_pt * fsp + E * 4.0 * h->nt + (fuse_y ? E * 2.0 * h->nt : 0.0);
+    KScope ks(h, cls_of<T>(ST_PROF_STENCIL64, ST_PROF_STENCIL32), bytes, flops);
+    CK(launch_stencil<T>(u, f, out, space<T>(h).bands, h->g, tc, h->lv[l].nslab, slab0, nslabs,
+                         h->stream));
+    return ST_OK;
+}
+
+// out[..k..] = sum_i W[i][k] in[..i..] along every active axis (forward: W = U,
+// i.e. U^T applied; inverse: W = U^T).  Ping-pongs in -> t0 -> t1 -> t0;
+// *res is the buffer holding the result.
+template <typename T>
+int spatial(st_handle h, const T *in, T *t0, T *t1, const T *const W[3], long long planes, T **res) {
+    const long long nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
+    const double E = (double)planes * h->g.nxyz;
+    const int c = cls_of<T>(ST_PROF_GEMM64, ST_PROF_GEMM32);
+    {
+        KScope ks(h, c, sizeof(T) * (2.0 * E + nx * nx), 2.0 * E * nx);
+        CK(launch_gemm_strided<T>(1, (int)(planes * nz * ny), (int)nx, (int)nx, in, 0, nx, 1, W[0], 0,
+                                  nx, 1, t0, 0, nx, 1, h->stream));
+    }
+    *res = t0;
+    if (h->dim < 2) return ST_OK;
+    {
+        KScope ks(h, c, sizeof(T) * (2.0 * E + ny * ny), 2.0 * E * ny);
+        CK(launch_gemm_strided<T>((int)(planes * nz), (int)ny, (int)nx, (int)ny, W[1], 0, 1, ny, t0,
+                                  ny * nx, nx, 1, t1, ny * nx, nx, 1, h->stream));
+    }
+    *res = t1;
+    if (h->dim < 3) return ST_OK;
+    {
+        KScope ks(h, c, sizeof(T) * (2.0 * E + nz * nz), 2.0 * E * nz);
+        CK(launch_gemm_strided<T>((int)planes, (int)nz, (int)(ny * nx), (int)nz, W[2], 0, 1, nz, t1,
+                                  nz * ny * nx, ny * nx, 1, t0, nz * ny * nx, ny * nx, 1, h->stream));
+    }
+    *res = t0;
+    return ST_OK;
+}
+
+// Damped block-Jacobi step on slabs [s0, s0+ns) of level l:
+// u <- (overwrite ? 0 : u) + omega A^{-1} (f - L u)  (A^{-1} by Eq. 3.1 + FD)
+template <typename T>
+int smooth_range(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns, int overwrite) {
+    Work<T> &w = work<T>(h);
+    DevSpace<T> &ds = space<T>(h);
+    const long long sl = (long long)h->nt * h->g.nxyz;  // elements per slab
+    T *w0 = w.w0 + s0 * sl, *w1 = w.w1 + s0 * sl;
+    CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, true, s0, ns));
+    T *fw = nullptr, *bz = nullptr;
+    CKS(spatial<T>(h, w0, w1, w0, ds.U, (long long)ns * h->nt, &fw));
+    const SchurCoefs<T> sc = pack_schur<T>(h, l);
+    const double E = (double)ns * h->nt * h->g.nxyz;
+    {
+        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 2.0 * E, E * (h->nt + 2.0));
+        CK(launch_shift_solve<T>(fw, ds.lam[0], ds.lam[1], ds.lam[2], h->g, sc, ns, h->stream));
+    }
+    T *other = (fw == w0) ? w1 : w0;
+    CKS(spatial<T>(h, fw, other, fw, ds.Ut, (long long)ns * h->nt, &bz));
+    {
+        KScope ks(h, ST_PROF_UPDATE, sizeof(T) * (overwrite ? 2.0 : 3.0) * E, E * (2.0 * h->nt + 2.0));
+        CK(launch_update<T>(u + s0 * sl, bz, sc, omega, h->g, ns, overwrite, h->stream));
+    }
+    return ST_OK;
+}
+
+template <typename T>
+int smooth(st_handle h, int l, T *u, const T *f, T omega, int overwrite = 0) {
+    return smooth_range<T>(h, l, u, f, omega, 0, h->lv[l].nslab * h->nrhs, overwrite);
+}
+
+// Exact solve on the coarsest level: block forward substitution over its
+// slabs (a single damped step with omega = 1 when there is one slab).
+template <typename T>
+int coarse_solve(st_handle h, int l, T *u, const T *f) {
+    const int Nl = h->lv[l].nslab;
+    CK(launch_zero<T>(u, (long long)Nl * h->nrhs * h->nt * h->g.nxyz, h->stream));
+    if (Nl == 1) return smooth<T>(h, l, u, f, T(1), 1);
+    for (int r = 0; r < h->nrhs; ++r)
+        for (int s = 0; s < Nl; ++s) CKS(smooth_range<T>(h, l, u, f, T(1), r * Nl + s, 1, 0));
+    return ST_OK;
+}
+
+// One V-cycle on level l for L_l u = f starting from u (zero_init: u = 0).
+template <typename T>
+int vcycle(st_handle h, int l, T *u, const T *f, bool zero_init) {
+    const long long n_l = (long long)h->lv[l].nslab * h->nrhs * h->nt * h->g.nxyz;
+    if (l == h->nlev - 1) return coarse_solve<T>(h, l, u, f);
+    if (zero_init) CK(launch_zero<T>(u, n_l, h->stream));
+    const T omega = (T)h->opt.omega;
+    for (int k = 0; k < h->opt.nu1; ++k) CKS(smooth<T>(h, l, u, f, omega));
+    Work<T> &w = work<T>(h);
+    CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, false, 0, h->lv[l].nslab * h->nrhs));
+    const ProlongCoefs<T> pc = pack_prolong<T>(h);
+    const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
+    const double Ec = (double)nc * h->nt * h->g.nxyz;
+    {
+        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 3.0 * Ec, Ec * 4.0 * h->nt);
+        CK(launch_restrict<T>(w.w0, w.f[l + 1], pc, h->g, nc, h->stream));
+    }
+    CKS(vcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], true));
+    {
+        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 5.0 * Ec, Ec * 4.0 * h->nt);
+        CK(launch_prolong_add<T>(w.u[l + 1], u, pc, h->g, nc, h->stream));
+    }
+    for (int k = 0; k < h->opt.nu2; ++k) CKS(smooth<T>(h, l, u, f, omega));
+    return ST_OK;
+}
+
+int vaxpy(st_handle h, int nv, const double *const *xs, const double *coef, double *y) {
+    KScope ks(h, ST_PROF_VECTOR, 8.0 * (nv + 2) * h->len * h->nrhs, 2.0 * nv * h->len * h->nrhs);
+    CK(launch_multiaxpy(nv, xs, coef, h->nrhs, h->len, y, h->stream));
+    return ST_OK;
+}
+
+int vscale(st_handle h, const double *x, double *y, const double *a) {
+    KScope ks(h, ST_PROF_VECTOR, 16.0 * h->len * h->nrhs, 1.0 * h->len * h->nrhs);
+    CK(launch_scale(x, y, a, h->nrhs, h->len, h->stream));
+    return ST_OK;
+}
+
+template <typename Tin, typename Tout>
+int vconvert(st_handle h, const Tin *x, Tout *y) {
+    const double n = (double)h->len * h->nrhs;
+    KScope ks(h, ST_PROF_VECTOR, n * (sizeof(Tin) + sizeof(Tout)), 0.0);
+    CK(launch_convert<Tin, Tout>(x, y, (long long)n, h->stream));
+    return ST_OK;
+}
+
+// z = V-cycle(v) with zero initial guess, FP64 at the interface
+int precondition(st_handle h, const double *v, double *z) {
+    const long long n0 = h->len * h->nrhs;
+    if (!h->mixed) return vcycle<double>(h, 0, z, v, true);
+    Work<float> &w = h->w32;
+    CKS((vconvert<double, float>(h, v, w.f[0])));
+    CKS(vcycle<float>(h, 0, w.u[0], w.f[0], true));
+    CKS((vconvert<float, double>(h, w.u[0], z)));
+    (void)n0;
+    return ST_OK;
+}
+
+int check_ptr(st_handle h, const void *p, const char *name) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (h->host_only) return fail(ST_ERR_INVALID_ARG, "handle was built host-only");
+    if (!p) return fail(ST_ERR_INVALID_ARG, "null pointer '%s'", name);
+    return ST_OK;
+}
+
+int ensure_krylov(st_handle h) {
+    const int m = h->opt.gmres_restart;
+    if (h->krylov_m == m && !h->V.empty()) return ST_OK;
+    const size_t e0 = (size_t)h->len * h->nrhs;
+    void *p;
+    h->V.clear();
+    h->Zk.clear();
+    for (int i = 0; i <= m; ++i) {
+        CKS(dalloc(h, e0 * sizeof(double), &p));
+        h->V.push_back((double *)p);
+    }
+    for (int i = 0; i < m; ++i) {
+        CKS(dalloc(h, e0 * sizeof(double), &p));
+        h->Zk.push_back((double *)p);
+    }
+    h->krylov_m = m;
+    return ST_OK;
+}
+
+// per-rhs dots of vecs[0..nv) with w -> host out[v*nrhs + r]
+int dots(st_handle h, int nv, const double *const *vecs, const double *w, std::vector<double> &out) {
+    out.assign((size_t)nv * h->nrhs, 0.0);
+    for (int v0 = 0; v0 < nv; v0 += MAXV) {
+        const int cnt = std::min(MAXV, nv - v0);
+        {
+            KScope ks(h, ST_PROF_VECTOR, 8.0 * (cnt + 1) * h->len * h->nrhs,
+                      2.0 * cnt * h->len * h->nrhs);
+            CK(launch_multidot(cnt, vecs + v0, w, h->nrhs, h->len, h->partial, h->nblk_dot,
+                               h->dots, h->stream));
+        }
+        CK(cudaMemcpyAsync(out.data() + (size_t)v0 * h->nrhs, h->dots,
+                           sizeof(double) * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->recs.size() > 2048) prof_fold(h);
+    return ST_OK;
+}
+
+int norms(st_handle h, const double *x, std::vector<double> &nr) {
+    std::vector<double> d;
+    const double *v[1] = {x};
+    CKS(dots(h, 1, v, x, d));
+    nr.resize(h->nrhs);
+    for (int r = 0; r < h->nrhs; ++r) nr[r] = std::sqrt(std::max(0.0, d[r]));
+    return ST_OK;
+}
+
+int residual64(st_handle h, const double *u, const double *f, double *r) {
+    return stencil<double>(h, 0, u, f, r, MODE_RES, false, 0, h->N * h->nrhs);
+}
+
+int solve_mg(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
+    CKS(ensure_krylov(h));
+    double *r = h->V[0], *e = h->Zk[0];
+    std::vector<double> nf, nr;
+    CKS(norms(h, rhs, nf));
+    int it = 0;
+    double worst = 0.0;
+    for (;;) {
+        CKS(residual64(h, u, rhs, r));
+        CKS(norms(h, r, nr));
+        worst = 0.0;
+        for (int q = 0; q < h->nrhs; ++q) worst = std::max(worst, nf[q] > 0 ? nr[q] / nf[q] : 0.0);
+        if (worst <= tol || it >= h->opt.max_it) break;
+        CKS(precondition(h, r, e));
+        const double one[1] = {1.0};
+        std::vector<double> c(h->nrhs, 1.0);
+        const double *xs[1] = {e};
+        CKS(vaxpy(h, 1, xs, c.data(), u));
+        (void)one;
+        ++it;
+    }
+    info->iterations = it;
+    info->rel_residual = worst;
+    info->status = (worst <= tol) ? ST_OK : ST_ERR_NO_CONVERGENCE;
+    return ST_OK;
+}
+
+int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
+    CKS(ensure_krylov(h));
+    const int m = h->opt.gmres_restart, R = h->nrhs;
+    std::vector<double> nf, beta, hcol, h2;
+    CKS(norms(h, rhs, nf));
+    int total = 0;
+    double worst = 0.0;
+    std::vector<char> done(R, 0);
+    for (int q = 0; q < R; ++q) done[q] = !(nf[q] > 0);
+    while (true) {
+        CKS(residual64(h, u, rhs, h->V[0]));
+        CKS(norms(h, h->V[0], beta));
+        worst = 0.0;
+        for (int q = 0; q < R; ++q) {
+            const double rel = nf[q] > 0 ? beta[q] / nf[q] : 0.0;
+            worst = std::max(worst, rel);
+            done[q] = rel <= tol;
+        }
+        if (worst <= tol || total >= h->opt.max_it) break;
+        std::vector<double> sc(R);
+        for (int q = 0; q < R; ++q) sc[q] = beta[q] > 0 ? 1.0 / beta[q] : 0.0;
+        CKS(vscale(h, h->V[0], h->V[0], sc.data()));
+        // per-rhs Hessenberg (column-major (m+1) x m), Givens, rhs g
+        std::vector<double> H((size_t)R * (m + 1) * m, 0.0), cs((size_t)R * m), sn((size_t)R * m),
+            g((size_t)R * (m + 1), 0.0);
+        std::vector<int> kq(R, 0);
+        for (int q = 0; q < R; ++q) g[(size_t)q * (m + 1)] = beta[q];
+        std::vector<char> act(R);
+        for (int q = 0; q < R; ++q) act[q] = !done[q];
+        int j = 0;
+        for (; j < m; ++j) {
+            CKS(precondition(h, h->V[j], h->Zk[j]));
+            CKS(stencil<double>(h, 0, h->Zk[j], nullptr, h->V[j + 1], MODE_APPLY, false, 0,
+                                h->N * R));
+            // classical Gram-Schmidt, twice
+            std::vector<double> hsum((size_t)(j + 1) * R, 0.0);
+            for (int pass = 0; pass < 2; ++pass) {
+                CKS(dots(h, j + 1, h->V.data(), h->V[j + 1], hcol));
+                std::vector<double> neg(hcol.size());
+                for (size_t i = 0; i < hcol.size(); ++i) {
+                    neg[i] = -hcol[i];
+                    hsum[i] += hcol[i];
+                }
+                for (int v0 = 0; v0 <= j; v0 += MAXV) {
+                    const int cnt = std::min(MAXV, j + 1 - v0);
+                    CKS(vaxpy(h, cnt, h->V.data() + v0, neg.data() + (size_t)v0 * R, h->V[j + 1]));
+                }
+            }
+            std::vector<double> hn;
+            CKS(norms(h, h->V[j + 1], hn));
+            for (int q = 0; q < R; ++q) sc[q] = hn[q] > 0 ? 1.0 / hn[q] : 0.0;
+            CKS(vscale(h, h->V[j + 1], h->V[j + 1], sc.data()));
+            ++total;
+            bool all = true;
+            for (int q = 0; q < R; ++q) {
+                if (!act[q]) continue;
+                double *Hq = &H[(size_t)q * (m + 1) * m];
+                double *col = Hq + (size_t)j * (m + 1);
+                for (int i = 0; i <= j; ++i) col[i] = hsum[(size_t)i * R + q];
+                col[j + 1] = hn[q];
+                double *c = &cs[(size_t)q * m], *s = &sn[(size_t)q * m], *gq = &g[(size_t)q * (m + 1)];
+                for (int i = 0; i < j; ++i) {
+                    const double a = col[i], b = col[i + 1];
+                    col[i] = c[i] * a + s[i] * b;
+                    col[i + 1] = -s[i] * a + c[i] * b;
+                }
+                const double a = col[j], b = col[j + 1];
+                const double rad = std::hypot(a, b);
+                c[j] = rad > 0 ? a / rad : 1.0;
+                s[j] = rad > 0 ? b / rad : 0.0;
+                col[j] = rad;
+                col[j + 1] = 0.0;
+                gq[j + 1] = -s[j] * gq[j];
+                gq[j] = c[j] * gq[j];
+                kq[q] = j + 1;
+                if (std::fabs(gq[j + 1]) <= tol * nf[q] || hn[q] == 0.0) act[q] = 0;
+                if (act[q]) all = false;
+            }
+            if (all || total >= h->opt.max_it) break;
+        }
+        // u += Z y per rhs
+        const int kmax = *std::max_element(kq.begin(), kq.end());
+        std::vector<double> coef((size_t)kmax * R, 0.0);
+        for (int q = 0; q < R; ++q) {
+            const int k = kq[q];
+            const double *Hq = &H[(size_t)q * (m + 1) * m];
+            const double *gq = &g[(size_t)q * (m + 1)];
+            std::vector<double> y(k);
+            for (int i = k - 1; i >= 0; --i) {
+                double sacc = gq[i];
+                for (int c2 = i + 1; c2 < k; ++c2) sacc -= Hq[(size_t)c2 * (m + 1) + i] * y[c2];
+                y[i] = sacc / Hq[(size_t)i * (m + 1) + i];
+            }
+            for (int i = 0; i < k; ++i) coef[(size_t)i * R + q] = y[i];
+        }
+        for (int v0 = 0; v0 < kmax; v0 += MAXV) {
+            const int cnt = std::min(MAXV, kmax - v0);
+            CKS(vaxpy(h, cnt, h->Zk.data() + v0, coef.data() + (size_t)v0 * R, u));
+        }
+    }
+    info->iterations = total;
+    info->rel_residual = worst;
+    info->status = (worst <= tol) ? ST_OK : ST_ERR_NO_CONVERGENCE;
+    return ST_OK;
+}
+
+int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slabs,
+               const st_options *opt, void *stream) {
+    if (opt) h->opt = *opt; else st_options_default(&h->opt);
+    st_options &o = h->opt;
+    if (geometry < ST_INTERVAL || geometry > ST_CUBE) return fail(ST_ERR_INVALID_ARG, "geometry must be 1..3");
+    if (degree < 1) return fail(ST_ERR_INVALID_ARG, "degree must be >= 1");
+    if (degree > PMAX) return fail(ST_ERR_UNSUPPORTED, "degree %d > %d is not built", degree, PMAX);
+    if (!spans) return fail(ST_ERR_INVALID_ARG, "null spans");
+    if (slabs < 1) return fail(ST_ERR_INVALID_ARG, "slabs must be >= 1");
+    if (o.ne_per_slab < 1 || o.ne_per_slab + degree > NTMAX)
+        return fail(ST_ERR_UNSUPPORTED, "ne_per_slab + degree must be in [2, %d]", NTMAX);
+    if (!(o.T > 0) || !(o.theta >= 0) || !(o.omega > 0))
+        return fail(ST_ERR_INVALID_ARG, "T > 0, theta >= 0, omega > 0 required");
+    if (o.nu1 < 0 || o.nu2 < 0 || o.gmres_restart < 1 || o.gmres_restart > 256 || o.max_it < 0 ||
+        o.nrhs < 1 || o.nrhs > 32)
+        return fail(ST_ERR_INVALID_ARG, "bad nu1/nu2/gmres_restart/max_it/nrhs");
+    if (o.precision < ST_FP64 || o.precision > ST_MIXED_BF16)
+        return fail(ST_ERR_INVALID_ARG, "bad precision");
+    h->dim = geometry;
+    h->p = degree;
+    h->N = slabs;
+    h->nrhs = o.nrhs;
+    h->nt = o.ne_per_slab + degree;
+    h->mixed = o.precision != ST_FP64;
+    h->stream = (cudaStream_t)stream;
+    for (int a = 0; a < 3; ++a) {
+        h->spans[a] = (a < h->dim) ? spans[a] : 1;
+        if (a < h->dim && spans[a] < 2) return fail(ST_ERR_INVALID_ARG, "spans must be >= 2");
+        h->n[a] = (a < h->dim) ? spans[a] + degree - 2 : 1;
+        if (h->n[a] < 1) return fail(ST_ERR_INVALID_ARG, "no interior dofs on axis %d", a);
+    }
+    h->g.nx = h->n[0];
+    h->g.ny = h->n[1];
+    h->g.nz = h->n[2];
+    h->g.dim = h->dim;
+    h->g.p = degree;
+    h->g.nxyz = (long long)h->n[0] * h->n[1] * h->n[2];
+    h->len = (long long)slabs * h->nt * h->g.nxyz;
+    if (slabs > 65535 / h->nrhs) return fail(ST_ERR_UNSUPPORTED, "too many slabs x rhs");
+
+    // spatial factors
+    std::vector<double> bandM[3], bandK[3];
+    const int W = 2 * degree + 1;
+    for (int a = 0; a < h->dim; ++a) {
+        const int n = h->n[a];
+        host::space_matrices(h->spans[a], degree, h->M1[a], h->K1[a]);
+        std::string err;
+        if (!host::sym_gen_eig(n, h->K1[a], h->M1[a], h->U[a], h->lam[a], err))
+            return fail(ST_ERR_ILL_CONDITIONED, "space eigenproblem axis %d: %s", a, err.c_str());
+        // checks: K1 U = M1 U Lambda, U^T M1 U = I
+        Mat MU = host::matmul(n, h->M1[a], h->U[a]);
+        Mat KU = host::matmul(n, h->K1[a], h->U[a]);
+        double r1 = 0, r2 = 0;
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < n; ++k) {
+                r1 = std::max(r1, std::fabs(KU[i * n + k] - MU[i * n + k] * h->lam[a][k]));
+                double s = 0;
+                for (int j = 0; j < n; ++j) s += h->U[a][j * n + i] * MU[j * n + k];
+                r2 = std::max(r2, std::fabs(s - (i == k ? 1.0 : 0.0)));
+            }
+        if (r1 > 1e-9 * h->lam[a][n - 1] || r2 > 1e-9)
+            return fail(ST_ERR_ILL_CONDITIONED, "space eigen residuals %.2e %.2e", r1, r2);
+        bandM[a].assign((size_t)n * W, 0.0);
+        bandK[a].assign((size_t)n * W, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int oo = -degree; oo <= degree; ++oo) {
+                const int j = i + oo;
+                if (j < 0 || j >= n) continue;
+                bandM[a][(size_t)i * W + oo + degree] = h->M1[a][i * n + j];
+                bandK[a][(size_t)i * W + oo + degree] = h->K1[a][i * n + j];
+            }
+    }
+    // time factors per level (theta*h frozen at the finest value)
+    const double tau0 = o.T / slabs;
+    const double delta = o.theta * tau0 / o.ne_per_slab;
+    int Nl = slabs;
+    const int nt = h->nt;
+    for (;;) {
+        LevelHost L;
+        L.nslab = Nl;
+        L.tau = o.T / Nl;
+        host::time_matrices(L.tau, o.ne_per_slab, degree, delta, L.Kt, L.Mt);
+        Mat G = L.Kt;  // G = M_t^{-1} K_t
+        if (!host::lu_solve(nt, nt, L.Mt, G)) return fail(ST_ERR_NOT_POSITIVE, "M_t is singular");
+        std::string err;
+        if (!host::real_schur(nt, G, L.X, L.Z, L.blk, err))
+            return fail(ST_ERR_ILL_CONDITIONED, "real Schur: %s", err.c_str());
+        // Re lambda > 0 check (Sec. 3.2: a posteriori control of positivity)
+        for (int i = 0; i < nt; ++i) {
+            double re;
+            if (i + 1 < nt && L.blk[i + 1]) {
+                re = 0.5 * (L.Z[i * nt + i] + L.Z[(i + 1) * nt + i + 1]);
+                if (!(re > 0)) return fail(ST_ERR_NOT_POSITIVE, "Re lambda <= 0 on level with %d slabs (use a smaller theta)", Nl);
+                ++i;
+                continue;
+            }
+            re = L.Z[i * nt + i];
+            if (!(re > 0)) return fail(ST_ERR_NOT_POSITIVE, "Re lambda <= 0 on level with %d slabs (use a smaller theta)", Nl);
+        }
+        // Y = (M_t X)^{-1}
+        Mat MX = host::matmul(nt, L.Mt, L.X);
+        L.Y.assign(nt * nt, 0.0);
+        for (int i = 0; i < nt; ++i) L.Y[i * nt + i] = 1.0;
+        if (!host::lu_solve(nt, nt, MX, L.Y)) return fail(ST_ERR_ILL_CONDITIONED, "M_t X singular");
+        // check K_t X = M_t X Z
+        Mat KX = host::matmul(nt, L.Kt, L.X), MXZ = host::matmul(nt, MX, L.Z);
+        double rr = 0;
+        for (int i = 0; i < nt * nt; ++i) rr = std::max(rr, std::fabs(KX[i] - MXZ[i]));
+        if (rr > 1e-11 * std::max(1.0, host::frob(L.Kt)))
+            return fail(ST_ERR_ILL_CONDITIONED, "time factor residual %.2e", rr);
+        h->lv.push_back(L);
+        if (Nl % 2 != 0 || Nl == 1) break;
+        Nl /= 2;
+    }
+    h->nlev = (int)h->lv.size();
+    host::time_prolongation(tau0, o.ne_per_slab, degree, h->Pt);
+
+    if (h->host_only) return ST_OK;
+
+    // device data
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(ST_ERR_CUDA, "no CUDA device");
+    }
+    CKS(upload_space<double>(h, h->s64, bandM, bandK));
+    if (h->mixed) CKS(upload_space<float>(h, h->s32, bandM, bandK));
+    if (h->mixed) {
+        CKS(alloc_work<float>(h, h->w32, true));
+        // the FP64 outer residual needs no FP64 V-cycle buffers except scratch
+        void *p;
+        CKS(dalloc(h, (size_t)h->len * h->nrhs * sizeof(double), &p));
+        h->w64.w0 = (double *)p;
+    } else {
+        CKS(alloc_work<double>(h, h->w64, false));
+    }
+    h->nblk_dot = 304;
+    void *p;
+    CKS(dalloc(h, sizeof(double) * MAXV * h->nrhs * h->nblk_dot, &p));
+    h->partial = (double *)p;
+    CKS(dalloc(h, sizeof(double) * MAXV * h->nrhs, &p));
+    h->dots = (double *)p;
+    return ST_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void st_options_default(st_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->T = 1.0;
+    o->theta = 1.0;
+    o->omega = 0.5;
+    o->ne_per_slab = 2;
+    o->nu1 = 1;
+    o->nu2 = 1;
+    o->precision = ST_FP64;
+    o->outer = ST_OUTER_FGMRES;
+    o->gmres_restart = 20;
+    o->max_it = 200;
+    o->nrhs = 1;
+    o->hbm_budget = 0;
+}
+
+const char *st_last_error(void) { return g_err.c_str(); }
+
+static int setup_entry(st_handle *out, int geometry, int degree, const int *spans, int slabs,
+                       const st_options *opt, void *stream, bool host_only) {
+    if (!out) return fail(ST_ERR_INVALID_ARG, "null output handle");
+    *out = nullptr;
+    st_handle h = nullptr;
+    try {
+        h = new st_handle_s();
+        h->host_only = host_only;
+        const int rc = setup_impl(h, geometry, degree, spans, slabs, opt, stream);
+        if (rc != ST_OK) {
+            st_destroy(h);
+            return rc;
+        }
+    } catch (...) {
+        if (h) st_destroy(h);
+        return fail(ST_ERR_OOM, "host exception during setup");
+    }
+    *out = h;
+    g_err.clear();
+    return ST_OK;
+}
+
+int st_setup(st_handle *out, int geometry, int degree, const int *spans, int slabs,
+             const st_options *opt, void *stream) {
+    return setup_entry(out, geometry, degree, spans, slabs, opt, stream, false);
+}
+
+int st_setup_host(st_handle *out, int geometry, int degree, const int *spans, int slabs,
+                  const st_options *opt) {
+    return setup_entry(out, geometry, degree, spans, slabs, opt, nullptr, true);
+}
+
+void st_destroy(st_handle h) {
+    if (!h) return;
+    for (void *p : h->allocs) cudaFree(p);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+}
+
+int st_set_stream(st_handle h, void *stream) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    h->stream = (cudaStream_t)stream;
+    return ST_OK;
+}
+
+int st_sizes(st_handle h, int64_t *n_dofs, int *n_t, int *n_x, int *n_levels, size_t *bytes) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (n_dofs) *n_dofs = h->len * h->nrhs;
+    if (n_t) *n_t = h->nt;
+    if (n_x)
+        for (int a = 0; a < 3; ++a) n_x[a] = h->n[a];
+    if (n_levels) *n_levels = h->nlev;
+    if (bytes) *bytes = h->bytes;
+    return ST_OK;
+}
+
+int st_apply(st_handle h, const double *x, double *y) {
+    CKS(check_ptr(h, x, "x"));
+    CKS(check_ptr(h, y, "y"));
+    if ((const void *)x == (void *)y) return fail(ST_ERR_INVALID_ARG, "x and y alias");
+    return stencil<double>(h, 0, x, nullptr, y, MODE_APPLY, false, 0, h->N * h->nrhs);
+}
+
+int st_residual(st_handle h, const double *u, const double *f, double *r) {
+    CKS(check_ptr(h, u, "u"));
+    CKS(check_ptr(h, f, "f"));
+    CKS(check_ptr(h, r, "r"));
+    if ((const void *)u == (void *)r) return fail(ST_ERR_INVALID_ARG, "u and r alias");
+    return residual64(h, u, f, r);
+}
+
+int st_load_coeffs(st_handle h, const double *c, double *f) {
+    CKS(check_ptr(h, c, "c"));
+    CKS(check_ptr(h, f, "f"));
+    if ((const void *)c == (void *)f) return fail(ST_ERR_INVALID_ARG, "c and f alias");
+    return stencil<double>(h, 0, c, nullptr, f, MODE_MASS, false, 0, h->N * h->nrhs);
+}
+
+int st_smooth(st_handle h, double *u, const double *f, int nsteps) {
+    CKS(check_ptr(h, u, "u"));
+    CKS(check_ptr(h, f, "f"));
+    if (nsteps < 0) return fail(ST_ERR_INVALID_ARG, "nsteps < 0");
+    if (!h->mixed) {
+        for (int k = 0; k < nsteps; ++k) CKS(smooth<double>(h, 0, u, f, h->opt.omega));
+        return ST_OK;
+    }
+    const long long n0 = h->len * h->nrhs;
+    CK(launch_convert<double, float>(u, h->w32.u[0], n0, h->stream));
+    CK(launch_convert<double, float>(f, h->w32.f[0], n0, h->stream));
+    for (int k = 0; k < nsteps; ++k)
+        CKS(smooth<float>(h, 0, h->w32.u[0], h->w32.f[0], (float)h->opt.omega));
+    CK(launch_convert<float, double>(h->w32.u[0], u, n0, h->stream));
+    return ST_OK;
+}
+
+int st_vcycle(st_handle h, double *u, const double *f) {
+    CKS(check_ptr(h, u, "u"));
+    CKS(check_ptr(h, f, "f"));
+    if (!h->mixed) return vcycle<double>(h, 0, u, f, false);
+    const long long n0 = h->len * h->nrhs;
+    CK(launch_convert<double, float>(u, h->w32.u[0], n0, h->stream));
+    CK(launch_convert<double, float>(f, h->w32.f[0], n0, h->stream));
+    CKS(vcycle<float>(h, 0, h->w32.u[0], h->w32.f[0], false));
+    CK(launch_convert<float, double>(h->w32.u[0], u, n0, h->stream));
+    return ST_OK;
+}
+
+int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_guess,
+             st_solve_info *info) {
+    CKS(check_ptr(h, rhs, "rhs"));
+    CKS(check_ptr(h, u, "u"));
+    if ((const void *)rhs == (void *)u) return fail(ST_ERR_INVALID_ARG, "rhs and u alias");
+    if (!(tol > 0)) return fail(ST_ERR_INVALID_ARG, "tol must be > 0");
+    st_solve_info local;
+    if (!info) info = &local;
+    std::memset(info, 0, sizeof *info);
+    const auto t0 = std::chrono::steady_clock::now();
+    try {
+        if (!use_guess) CK(launch_zero<double>(u, h->len * h->nrhs, h->stream));
+        if (h->opt.outer == ST_OUTER_MG) CKS(solve_mg(h, rhs, tol, u, info));
+        else CKS(solve_fgmres(h, rhs, tol, u, info));
+        CK(cudaStreamSynchronize(h->stream));
+    } catch (...) {
+        return fail(ST_ERR_OOM, "host exception during solve");
+    }
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info->status != ST_OK)
+        return fail(info->status, "no convergence: rel. residual %.3e after %d iterations",
+                    info->rel_residual, info->iterations);
+    return ST_OK;
+}
+
+int st_profile(st_handle h, int enable) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (h->host_only) return fail(ST_ERR_INVALID_ARG, "handle was built host-only");
+    CK(cudaStreamSynchronize(h->stream));
+    prof_fold(h);
+    if (enable) {
+        for (int c = 0; c < ST_PROF_NCLASS; ++c) {
+            h->prof_n[c] = 0;
+            h->prof_ms[c] = h->prof_bytes[c] = h->prof_flops[c] = 0.0;
+        }
+    }
+    h->prof_on = enable != 0;
+    return ST_OK;
+}
+
+int st_profile_read(st_handle h, int cls, int64_t *launches, double *ms, double *bytes,
+                    double *flops) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (cls < 0 || cls >= ST_PROF_NCLASS) return fail(ST_ERR_INVALID_ARG, "bad kernel class");
+    if (!h->host_only) {
+        CK(cudaStreamSynchronize(h->stream));
+        prof_fold(h);
+    }
+    if (launches) *launches = h->prof_n[cls];
+    if (ms) *ms = h->prof_ms[cls];
+    if (bytes) *bytes = h->prof_bytes[cls];
+    if (flops) *flops = h->prof_flops[cls];
+    return ST_OK;
+}
+
+int st_time_factors(st_handle h, int lvl, int *nt, double *Kt, double *Mt, double *X, double *Z,
+                    double *Y) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (lvl < 0 || lvl >= h->nlev) return fail(ST_ERR_INVALID_ARG, "level out of range");
+    const LevelHost &L = h->lv[lvl];
+    const size_t b = sizeof(double) * h->nt * h->nt;
+    if (nt) *nt = h->nt;
+    if (Kt) std::memcpy(Kt, L.Kt.data(), b);
+    if (Mt) std::memcpy(Mt, L.Mt.data(), b);
+    if (X) std::memcpy(X, L.X.data(), b);
+    if (Z) std::memcpy(Z, L.Z.data(), b);
+    if (Y) std::memcpy(Y, L.Y.data(), b);
+    return ST_OK;
+}
+
+int st_space_factors(st_handle h, int axis, int *n, double *M1, double *K1, double *U, double *lam) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (axis < 0 || axis >= h->dim) return fail(ST_ERR_INVALID_ARG, "axis out of range");
+    const int nn = h->n[axis];
+    const size_t b = sizeof(double) * nn * nn;
+    if (n) *n = nn;
+    if (M1) std::memcpy(M1, h->M1[axis].data(), b);
+    if (K1) std::memcpy(K1, h->K1[axis].data(), b);
+    if (U) std::memcpy(U, h->U[axis].data(), b);
+    if (lam) std::memcpy(lam, h->lam[axis].data(), sizeof(double) * nn);
+    return ST_OK;
+}
+
+int st_time_prolongation(st_handle h, int *nt, double *Pt) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (nt) *nt = h->nt;
+    if (Pt) std::memcpy(Pt, h->Pt.data(), sizeof(double) * 2 * h->nt * h->nt);
+    return ST_OK;
+}
+
+}  // extern "C"

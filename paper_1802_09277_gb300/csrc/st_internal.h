@@ -1,0 +1,109 @@
+// Internal declarations shared by the CUDA translation units (not part of
+// the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace st {
+
+constexpr int NTMAX = 8;  // max time dofs per slab (ne + p)
+constexpr int PMAX = 3;   // max B-spline degree
+constexpr int MAXV = 32;  // max vectors in one multi-vector kernel call
+
+// Spatial grid: interior dofs per axis (unused axes 1), dimension, degree.
+struct Grid {
+    int nx, ny, nz;
+    int dim;
+    int p;
+    long long nxyz;
+};
+
+// Stencil output modes of the residual kernel
+enum StencilMode { MODE_RES = 0, MODE_APPLY = 1, MODE_MASS = 2 };
+
+// Per-launch time coefficients (row-major nt x nt), converted on the host to
+// the kernel's scalar type.
+template <typename T>
+struct TimeCoefs {
+    T CK[NTMAX * NTMAX];  // multiplies M_x u_j (K_t; M_t in MODE_MASS)
+    T CM[NTMAX * NTMAX];  // multiplies K_x u_j (M_t; 0 in MODE_MASS)
+    T Y[NTMAX * NTMAX];   // fused forward time transform (used if fuse_y)
+    int nt;
+    int fuse_y;
+    int mode;
+};
+
+// Quasi-triangular Schur factor for the shift solve, plus X for the update
+template <typename T>
+struct SchurCoefs {
+    T Z[NTMAX * NTMAX];
+    T X[NTMAX * NTMAX];
+    int blk[NTMAX];  // blk[i] = 1: row i is the second row of a 2x2 block
+    int nt;
+};
+
+template <typename T>
+struct ProlongCoefs {
+    T P[2 * NTMAX * NTMAX];  // (2nt x nt) row-major
+    int nt;
+};
+
+// Banded 1D matrices on the device: band[a][i][o+p] = Mat_a[i][i+o].
+template <typename T>
+struct Bands {
+    const T *M[3];
+    const T *K[3];
+};
+
+// ---- launchers (kernels_stencil.cu) ----
+template <typename T>
+cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands, const Grid &g,
+                           const TimeCoefs<T> &tc, int slabs_per_prob, int slab0, int nslabs,
+                           cudaStream_t s);
+
+// ---- launchers (kernels_transform.cu) ----
+// C[b][m][n] = sum_k A(b,m,k) B(b,k,n) with arbitrary strides
+template <typename T>
+cudaError_t launch_gemm_strided(int batch, int M, int N, int K, const T *A, long long sAb,
+                                long long sAm, long long sAk, const T *B, long long sBb,
+                                long long sBk, long long sBn, T *C, long long sCb, long long sCm,
+                                long long sCn, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_shift_solve(T *w, const T *lam0, const T *lam1, const T *lam2, const Grid &g,
+                               const SchurCoefs<T> &sc, long long nslabs, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_update(T *u, const T *z, const SchurCoefs<T> &sc, T omega, const Grid &g,
+                          long long nslabs, int overwrite, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_restrict(const T *rf, T *fc, const ProlongCoefs<T> &pc, const Grid &g,
+                            long long ncoarse, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_prolong_add(const T *ec, T *uf, const ProlongCoefs<T> &pc, const Grid &g,
+                               long long ncoarse, cudaStream_t s);
+
+// ---- vector kernels (kernels_vector.cu) ----
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin *x, Tout *y, long long n, cudaStream_t s);
+
+// partial[v][r][blk] = partial dot of vecs[v] and w over rhs r
+cudaError_t launch_multidot(int nv, const double *const *vecs, const double *w, int nrhs,
+                            long long len, double *partial, int nblk, double *out,
+                            cudaStream_t s);
+
+// y_r += sum_v coef[v][r] x_v  (per rhs r)
+cudaError_t launch_multiaxpy(int nv, const double *const *xs, const double *coef, int nrhs,
+                             long long len, double *y, cudaStream_t s);
+
+// y = a_r * x (per rhs), y may alias x
+cudaError_t launch_scale(const double *x, double *y, const double *a, int nrhs, long long len,
+                         cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_zero(T *x, long long n, cudaStream_t s);
+
+}  // namespace st

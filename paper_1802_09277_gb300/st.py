@@ -1,0 +1,239 @@
+"""Thin ctypes binding of the C ABI in include/st_iga.h (libst_iga.so).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Device vectors are torch tensors (float64, contiguous, on the
+CUDA device); their pointers are passed as-is.  The library is loaded
+in-tree from this package directory; ``load()`` raises if it is missing.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libst_iga.so")
+
+ST_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NOT_POSITIVE", -4: "ILL_CONDITIONED",
+          -5: "NO_CONVERGENCE", -6: "TIMEOUT", -7: "CUDA", -8: "OVER_BUDGET",
+          -9: "UNSUPPORTED"}
+GEOMETRY = {1: 1, 2: 2, 3: 3}
+PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
+OUTER = {"fgmres": 0, "mg": 1}
+
+# every symbol declared in include/st_iga.h
+SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",
+           "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_smooth", "st_vcycle",
+           "st_solve", "st_profile", "st_profile_read", "st_time_factors", "st_space_factors",
+           "st_time_prolongation", "st_last_error"]
+PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
+                "vector"]
+
+
+class StOptions(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_double), ("theta", ctypes.c_double), ("omega", ctypes.c_double),
+                ("ne_per_slab", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("precision", ctypes.c_int), ("outer", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("max_it", ctypes.c_int),
+                ("nrhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t)]
+
+
+class StSolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class StError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libst_iga.so (in-tree).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libst_iga.so is missing: run __graft_entry__.build() or "
+                           "python paper_1802_09277_gb300/build.py first")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
+    ip = ctypes.POINTER(ctypes.c_int)
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "st_options_default": (V, [ctypes.POINTER(StOptions)]),
+        "st_setup": (I, [ctypes.POINTER(P), I, I, ip, I, ctypes.POINTER(StOptions), P]),
+        "st_setup_host": (I, [ctypes.POINTER(P), I, I, ip, I, ctypes.POINTER(StOptions)]),
+        "st_destroy": (V, [P]),
+        "st_set_stream": (I, [P, P]),
+        "st_sizes": (I, [P, ctypes.POINTER(ctypes.c_int64), ip, ip, ip,
+                         ctypes.POINTER(ctypes.c_size_t)]),
+        "st_apply": (I, [P, P, P]),
+        "st_residual": (I, [P, P, P, P]),
+        "st_load_coeffs": (I, [P, P, P]),
+        "st_smooth": (I, [P, P, P, I]),
+        "st_vcycle": (I, [P, P, P]),
+        "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
+        "st_profile": (I, [P, I]),
+        "st_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]),
+        "st_time_factors": (I, [P, I, ip, dp, dp, dp, dp, dp]),
+        "st_space_factors": (I, [P, I, ip, dp, dp, dp, dp]),
+        "st_time_prolongation": (I, [P, ip, dp]),
+        "st_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != ST_OK:
+        raise StError(rc, _lib.st_last_error().decode())
+
+
+def options(**kw):
+    """st_options with defaults, overridden by keyword (precision/outer may be
+    given by name)."""
+    lib = load()
+    o = StOptions()
+    lib.st_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = PRECISION[v]
+        if k == "outer" and isinstance(v, str):
+            v = OUTER[v]
+        setattr(o, k, v)
+    return o
+
+
+def _dptr(t, n, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch tensor" % name)
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("%s must be a contiguous float64 CUDA tensor" % name)
+    if t.numel() != n:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), n))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One handle of the library: geometry 1/2/3 (interval/square/cube),
+    degree p, spans per axis, slabs; keyword options as in st_options.
+    host_only=True builds only the FP64 factors (no GPU needed)."""
+
+    def __init__(self, dim, degree, spans, slabs, host_only=False, stream=None, **opts):
+        lib = load()
+        self.dim = int(dim)
+        self.opt = options(**opts)
+        self._h = ctypes.c_void_p()
+        sp = (ctypes.c_int * 3)(*([int(s) for s in spans] + [1] * (3 - len(spans))))
+        if host_only:
+            rc = lib.st_setup_host(ctypes.byref(self._h), self.dim, int(degree), sp, int(slabs),
+                                   ctypes.byref(self.opt))
+        else:
+            if stream is None:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            rc = lib.st_setup(ctypes.byref(self._h), self.dim, int(degree), sp, int(slabs),
+                              ctypes.byref(self.opt), ctypes.c_void_p(stream))
+        _check(rc)
+        n = ctypes.c_int64()
+        nt = ctypes.c_int()
+        nx = (ctypes.c_int * 3)()
+        nl = ctypes.c_int()
+        nb = ctypes.c_size_t()
+        _check(lib.st_sizes(self._h, ctypes.byref(n), ctypes.byref(nt), nx, ctypes.byref(nl),
+                            ctypes.byref(nb)))
+        self.ndofs, self.nt, self.nx = n.value, nt.value, tuple(nx)
+        self.nlevels, self.device_bytes = nl.value, nb.value
+
+    def close(self):
+        if self._h:
+            _lib.st_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        _check(_lib.st_set_stream(self._h, ctypes.c_void_p(stream)))
+
+    def apply(self, x, y):
+        _check(_lib.st_apply(self._h, _dptr(x, self.ndofs, "x"), _dptr(y, self.ndofs, "y")))
+
+    def residual(self, u, f, r):
+        _check(_lib.st_residual(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f"),
+                                _dptr(r, self.ndofs, "r")))
+
+    def load_coeffs(self, c, f):
+        _check(_lib.st_load_coeffs(self._h, _dptr(c, self.ndofs, "c"), _dptr(f, self.ndofs, "f")))
+
+    def smooth(self, u, f, nsteps=1):
+        _check(_lib.st_smooth(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f"),
+                              int(nsteps)))
+
+    def vcycle(self, u, f):
+        _check(_lib.st_vcycle(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f")))
+
+    def solve(self, rhs, u, tol=1e-8, use_guess=False, check=True):
+        info = StSolveInfo()
+        rc = _lib.st_solve(self._h, _dptr(rhs, self.ndofs, "rhs"), float(tol),
+                           _dptr(u, self.ndofs, "u"), int(bool(use_guess)), ctypes.byref(info))
+        if check:
+            _check(rc)
+        return {"iterations": info.iterations, "status": info.status,
+                "rel_residual": info.rel_residual, "seconds": info.seconds, "rc": rc}
+
+    def profile(self, enable):
+        """Start (reset) or stop per-kernel-class event timing."""
+        _check(_lib.st_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{class: {launches, ms, bytes, flops}} accumulated since profile(True)."""
+        out = {}
+        for c, name in enumerate(PROF_CLASSES):
+            n = ctypes.c_int64()
+            ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            _check(_lib.st_profile_read(self._h, c, ctypes.byref(n), ctypes.byref(ms),
+                                        ctypes.byref(by), ctypes.byref(fl)))
+            out[name] = {"launches": n.value, "ms": ms.value, "bytes": by.value,
+                         "flops": fl.value}
+        return out
+
+    # host-side factor inspection -------------------------------------------
+    def time_factors(self, level=0):
+        import numpy as np
+        nt = self.nt
+        mats = [np.zeros((nt, nt)) for _ in range(5)]
+        ptrs = [m.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for m in mats]
+        k = ctypes.c_int()
+        _check(_lib.st_time_factors(self._h, int(level), ctypes.byref(k), *ptrs))
+        return dict(zip(["Kt", "Mt", "X", "Z", "Y"], mats))
+
+    def space_factors(self, axis=0):
+        import numpy as np
+        n = self.nx[axis]
+        M1, K1, U = (np.zeros((n, n)) for _ in range(3))
+        lam = np.zeros(n)
+        cp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        k = ctypes.c_int()
+        _check(_lib.st_space_factors(self._h, int(axis), ctypes.byref(k), cp(M1), cp(K1), cp(U),
+                                     cp(lam)))
+        return {"M1": M1, "K1": K1, "U": U, "lam": lam}
+
+    def time_prolongation(self):
+        import numpy as np
+        P = np.zeros((2 * self.nt, self.nt))
+        k = ctypes.c_int()
+        _check(_lib.st_time_prolongation(self._h, ctypes.byref(k),
+                                         P.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return P

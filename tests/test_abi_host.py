@@ -1,0 +1,125 @@
+"""CPU tests of the C ABI library: it loads, exports every declared symbol,
+and its host-side FP64 setup (no GPU) reproduces the oracle's matrices and
+satisfies the factorisation identities of Sec. 3.2-3.5 (arXiv:1802.09277)."""
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.linalg as sl
+
+from oracle import assemble as A
+from oracle import solve as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def st():
+    from paper_1802_09277_gb300 import build, st as stmod
+    if not os.path.exists(stmod.LIB_PATH):
+        build.build()
+    stmod.load()
+    return stmod
+
+
+def test_exports_every_declared_symbol(st):
+    hdr = open(os.path.join(ROOT, "include", "st_iga.h")).read()
+    declared = set(re.findall(r"\b(st_[a-z_]+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    lib = st.load()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(st.SYMBOLS)
+
+
+CASES = [(1, (16,), 2, 8, 4), (2, (8, 6), 3, 8, 2), (3, (5, 4, 6), 1, 4, 3),
+         (2, (64, 64), 2, 256, 2), (2, (10, 9), 1, 6, 5)]
+
+
+@pytest.mark.parametrize("d,spans,p,N,ne", CASES)
+def test_host_factors(st, d, spans, p, N, ne):
+    s = st.Solver(d, p, spans, N, host_only=True, ne_per_slab=ne)
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    assert s.ndofs == pr.ndofs and s.nt == pr.Nt
+    # time matrices on every level: theta*h frozen at the finest value
+    prl = pr
+    for lvl in range(s.nlevels):
+        tf = s.time_factors(lvl)
+        Kt, Mt = A.time_matrices(prl.tau, ne, p, prl.delta)
+        assert np.allclose(tf["Kt"], Kt, rtol=0, atol=1e-13 * np.abs(Kt).max())
+        assert np.allclose(tf["Mt"], Mt, rtol=0, atol=1e-13 * np.abs(Mt).max())
+        X, Z, Y = tf["X"], tf["Z"], tf["Y"]
+        nt = len(X)
+        # Eq. 3.1 ingredients: K_t X = M_t X Z, X orthogonal, Y = (M_t X)^{-1}
+        assert np.abs(Kt @ X - Mt @ X @ Z).max() <= 1e-12 * np.abs(Kt).max()
+        assert np.abs(X.T @ X - np.eye(nt)).max() <= 1e-13
+        assert np.abs(Y @ Mt @ X - np.eye(nt)).max() <= 1e-11
+        # quasi-triangular with 2x2 blocks only for complex pairs
+        assert np.all(np.tril(Z, -2) == 0)
+        for i in range(1, nt):
+            if Z[i, i - 1] != 0:
+                blk = Z[i - 1:i + 1, i - 1:i + 1]
+                assert np.iscomplex(np.linalg.eigvals(blk)).all()
+                assert i < 2 or Z[i - 1, i - 2] == 0
+        lam_t = np.linalg.eigvals(Z)
+        ref = sl.eigvals(Kt, Mt)
+        for v in ref:  # same spectrum as the generalized problem
+            assert np.min(np.abs(lam_t - v)) <= 1e-9 * max(1.0, abs(v))
+        assert lam_t.real.min() > 0  # Sec. 3.2: Re lambda > 0
+        if lvl + 1 < s.nlevels:
+            prl = prl.coarse()
+    # space factors: K1 U = M1 U Lambda, U^T M1 U = I
+    for a in range(d):
+        sf = s.space_factors(a)
+        M1, K1 = A.space_matrices(spans[a], p)
+        assert np.allclose(sf["M1"], M1, atol=1e-15) and np.allclose(sf["K1"], K1, atol=1e-12)
+        U, lam = sf["U"], sf["lam"]
+        assert np.abs(U.T @ M1 @ U - np.eye(len(U))).max() <= 1e-12
+        assert np.abs(K1 @ U - M1 @ U * lam).max() <= 1e-12 * lam.max()
+        assert np.allclose(lam, sl.eigh(K1, M1, eigvals_only=True), rtol=1e-10)
+    # time prolongation (collocation) equals the oracle's L2 projection
+    assert np.allclose(s.time_prolongation(), S.time_prolongation(pr.tau, ne, p), atol=1e-13)
+    s.close()
+
+
+def test_setup_errors(st):
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 0, (4, 4), 2, host_only=True)
+    assert e.value.code == -1
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 4, (4, 4), 2, host_only=True)
+    assert e.value.code == -9
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 2, (1, 4), 2, host_only=True)
+    assert e.value.code == -1
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 2, (4, 4), 0, host_only=True)
+    assert e.value.code == -1
+    with pytest.raises(st.StError) as e:
+        st.Solver(4, 2, (4, 4), 2, host_only=True)
+    assert e.value.code == -1
+
+
+def test_not_positive_guard(st):
+    """Sec. 3.2 remark: a negative Re lambda(K_t, M_t) is reported, so the
+    caller can take a smaller theta.  theta = 1e3 makes M_t indefinite."""
+    bad = None
+    for th in (30.0, 100.0, 1e3, 1e4):
+        Kt, Mt = A.time_matrices(1.0 / 2, 5, 3, th * 0.1)
+        if sl.eigvals(Kt, Mt).real.min() <= 0:
+            bad = th
+            break
+    assert bad is not None
+    with pytest.raises(st.StError) as e:
+        st.Solver(1, 3, (4,), 2, host_only=True, ne_per_slab=5, theta=bad)
+    assert e.value.code == -3
+
+
+def test_host_only_handle_rejects_device_calls(st):
+    s = st.Solver(1, 2, (6,), 2, host_only=True)
+    lib = st.load()
+    import ctypes
+    rc = lib.st_apply(s._h, ctypes.c_void_p(8), ctypes.c_void_p(16))
+    assert rc == -1
+    s.close()

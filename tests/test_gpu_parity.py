@@ -1,0 +1,257 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (FP64 rounding of sums of O(10)-O(100) terms, written per test):
+operator/load/residual 1e-13 relative to the largest output entry; one
+smoothing step and one V-cycle 1e-11 (the d spatial transforms and the time
+transforms add O(n) rounded terms each); FP64 solve 1e-10 (solved to 1e-12);
+mixed-precision solve 1e-8 (solved to 1e-10)."""
+import numpy as np
+import pytest
+
+from oracle import assemble as A
+from oracle import solve as S
+from paper_1802_09277_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def st():
+    import os
+    from paper_1802_09277_gb300 import build, st as stmod
+    if not os.path.exists(stmod.LIB_PATH):
+        build.build()
+    stmod.load()
+    assert torch.cuda.is_available()
+    return stmod
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# (d, spans, p, N, ne): several tiles per axis and ragged tails (tile sizes
+# are 128 (1D), 32x8 (2D), 16x8x4 (3D))
+CASES = [
+    (1, (16,), 2, 8, 4),       # the 1D manufactured-solution configuration
+    (1, (300,), 3, 3, 2),      # 1D, 3 x-tiles ragged, odd slab count
+    (2, (8, 6), 3, 5, 2),
+    (2, (37, 29), 2, 6, 2),    # 2 x-tiles, 4 y-tiles, ragged
+    (2, (20, 20), 1, 4, 5),    # p = 1, nt = 6
+    (3, (5, 4, 6), 1, 4, 3),
+    (3, (19, 11, 9), 2, 2, 2),  # 3D ragged in every axis
+    (3, (6, 6, 6), 3, 2, 2),
+]
+
+
+@pytest.mark.parametrize("d,spans,p,N,ne", CASES)
+def test_apply_residual_load_parity(st, d, spans, p, N, ne):
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    L = A.assemble_L(pr)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne)
+    x = inputs.uniform_vector(1, pr.ndofs)
+    f = inputs.uniform_vector(2, pr.ndofs)
+    y = torch.empty(pr.ndofs, dtype=torch.float64, device="cuda")
+    s.apply(dev(x), y)
+    assert relerr(host(y), L @ x) <= 1e-13
+    s.residual(dev(x), dev(f), y)
+    assert relerr(host(y), f - L @ x) <= 1e-13
+    s.load_coeffs(dev(x), y)
+    assert relerr(host(y), A.load_from_coeffs(pr, x)) <= 1e-13
+    s.close()
+
+
+@pytest.mark.parametrize("d,spans,p,N,ne", CASES)
+def test_smooth_step_parity(st, d, spans, p, N, ne):
+    """One damped block-Jacobi step (Sec. 3.1) with A^{-1} by Eq. 3.1 + fast
+    diagonalisation equals the oracle's step with sparse-LU slab solves."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    L = A.assemble_L(pr)
+    lev = S.Level(L, N, pr.Nt * pr.Nx)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne)
+    u0 = inputs.uniform_vector(3, pr.ndofs)
+    f = inputs.uniform_vector(4, pr.ndofs)
+    ref = S.jacobi_step(lev, u0, f, 0.5)
+    u = dev(u0)
+    s.smooth(u, dev(f), 1)
+    assert relerr(host(u), ref) <= 1e-11
+    ref2 = S.jacobi_step(lev, ref, f, 0.5)
+    s.smooth(u, dev(f), 1)
+    assert relerr(host(u), ref2) <= 1e-11
+    s.close()
+
+
+@pytest.mark.parametrize("d,spans,p,N,ne", [c for c in CASES if c[3] > 1])
+def test_vcycle_parity(st, d, spans, p, N, ne):
+    """One V-cycle (time coarsening, Galerkin coarse operators in the oracle,
+    frozen-delta rediscretisation on the GPU) from a nonzero start."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    H = S.Hierarchy(pr)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne)
+    u0 = inputs.uniform_vector(5, pr.ndofs)
+    f = inputs.uniform_vector(6, pr.ndofs)
+    ref = S.vcycle(H, f, u=u0.copy())
+    u = dev(u0)
+    s.vcycle(u, dev(f))
+    assert relerr(host(u), ref) <= 1e-11
+    # a second cycle must not depend on state left by the first
+    ref2 = S.vcycle(H, f, u=ref.copy())
+    s.vcycle(u, dev(f))
+    assert relerr(host(u), ref2) <= 1e-11
+    s.close()
+
+
+@pytest.mark.parametrize("outer", ["fgmres", "mg"])
+@pytest.mark.parametrize("d,spans,p,N,ne", CASES[:6])
+def test_solve_fp64_parity(st, outer, d, spans, p, N, ne):
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    c = inputs.normal_coeffs(7, pr.ndofs)
+    fr = A.load_from_coeffs(pr, c)
+    ud = S.direct(A.assemble_L(pr), fr)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer)
+    f = torch.empty(pr.ndofs, dtype=torch.float64, device="cuda")
+    s.load_coeffs(dev(c), f)
+    u = torch.zeros_like(f)
+    info = s.solve(f, u, tol=1e-12)
+    err = np.linalg.norm(host(u) - ud) / np.linalg.norm(ud)
+    assert info["rel_residual"] <= 1e-12
+    assert err <= 1e-10, (err, info)
+    s.close()
+
+
+@pytest.mark.parametrize("outer", ["fgmres", "mg"])
+@pytest.mark.parametrize("d,spans,p,N,ne", CASES[:6])
+def test_solve_mixed_parity(st, outer, d, spans, p, N, ne):
+    """FP32 V-cycle, FP64 outer residual and update: 1e-8 vs the oracle."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    c = inputs.normal_coeffs(8, pr.ndofs)
+    fr = A.load_from_coeffs(pr, c)
+    ud = S.direct(A.assemble_L(pr), fr)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer, precision="mixed_fp32")
+    f = dev(fr)
+    u = torch.zeros_like(f)
+    info = s.solve(f, u, tol=1e-10)
+    err = np.linalg.norm(host(u) - ud) / np.linalg.norm(ud)
+    assert err <= 1e-8, (err, info)
+    s.close()
+
+
+def test_manufactured_1d_solution(st):
+    """The 1D configuration: u = sin(pi x) sin(pi t), multigrid iteration to
+    1e-10; the GPU solution equals the oracle's direct solution."""
+    pr = A.Problem(1, (16,), 2, 4, 8, theta=1.0)
+    fr = A.manufactured_load(pr)
+    ud = S.direct(A.assemble_L(pr), fr)
+    s = st.Solver(1, 2, (16,), 8, ne_per_slab=4, outer="mg")
+    u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+    info = s.solve(dev(fr), u, tol=1e-10)
+    assert np.linalg.norm(host(u) - ud) <= 1e-9 * np.linalg.norm(ud)
+    assert info["iterations"] <= 40
+    s.close()
+
+
+def test_single_slab_exact_in_one_cycle(st):
+    pr = A.Problem(2, (9, 7), 2, 2, 1, theta=1.0)
+    fr = inputs.normal_coeffs(9, pr.ndofs)
+    ud = S.direct(A.assemble_L(pr), fr)
+    s = st.Solver(2, 2, (9, 7), 1, outer="mg")
+    u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+    info = s.solve(dev(fr), u, tol=1e-12)
+    assert info["iterations"] == 1
+    assert relerr(host(u), ud) <= 1e-12
+
+
+def test_multi_rhs_equals_single(st):
+    """nrhs independent problems solved together give each single solution."""
+    d, spans, p, N = 2, (12, 10), 2, 8
+    pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+    R = 3
+    fs = [inputs.normal_coeffs(20 + r, pr.ndofs) for r in range(R)]
+    sb = st.Solver(d, p, spans, N, nrhs=R)
+    assert sb.ndofs == R * pr.ndofs
+    u = torch.zeros(R * pr.ndofs, dtype=torch.float64, device="cuda")
+    sb.solve(dev(np.concatenate(fs)), u, tol=1e-12)
+    ub = host(u).reshape(R, -1)
+    L = A.assemble_L(pr)
+    for r in range(R):
+        ud = S.direct(L, fs[r])
+        assert np.linalg.norm(ub[r] - ud) <= 1e-10 * np.linalg.norm(ud)
+    # the operator is block diagonal over rhs
+    x = inputs.uniform_vector(30, R * pr.ndofs)
+    y = torch.empty_like(u)
+    sb.apply(dev(x), y)
+    yr = host(y).reshape(R, -1)
+    for r in range(R):
+        assert relerr(yr[r], L @ x[r * pr.ndofs:(r + 1) * pr.ndofs]) <= 1e-13
+
+
+def test_zero_rhs(st):
+    s = st.Solver(2, 2, (8, 8), 4)
+    f = torch.zeros(s.ndofs, dtype=torch.float64, device="cuda")
+    u = torch.ones_like(f)
+    info = s.solve(f, u, tol=1e-8)
+    assert info["iterations"] == 0
+    assert float(u.abs().max()) == 0.0
+
+
+def test_argument_errors(st):
+    s = st.Solver(1, 2, (6,), 2)
+    x = torch.zeros(s.ndofs, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        s.apply(x, torch.zeros(s.ndofs + 1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        s.apply(x, torch.zeros(s.ndofs, dtype=torch.float32, device="cuda"))
+    with pytest.raises(st.StError) as e:
+        s.apply(x, x)
+    assert e.value.code == -1
+    with pytest.raises(st.StError) as e:
+        s.solve(x, x, tol=1e-8)
+    assert e.value.code == -1
+
+
+def test_hbm_budget_refused(st):
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 2, (64, 64), 256, hbm_budget=1 << 20)
+    assert e.value.code == -8
+
+
+def test_full_size_2d_sampled(st):
+    """The 2D workload at full size (64x64 spans, p = 2, 256 slabs x 2
+    elements, 4.19 M dofs): st_apply checked slab by slab on sampled slabs,
+    and the FP64 solve's residual recomputed by the oracle on every slab."""
+    d, spans, p, N, ne = 2, (64, 64), 2, 256, 2
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    Ab, Bb = A.slab_blocks(pr)
+    m = pr.Nt * pr.Nx
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne)
+    x = inputs.uniform_vector(40, pr.ndofs)
+    y = torch.empty(pr.ndofs, dtype=torch.float64, device="cuda")
+    s.apply(dev(x), y)
+    yh = host(y)
+    X = x.reshape(N, m)
+    for n in (0, 1, 97, 255):
+        ref = Ab @ X[n] - (Bb @ X[n - 1] if n else 0.0)
+        assert relerr(yh[n * m:(n + 1) * m], ref) <= 1e-13
+    c = inputs.normal_coeffs(2, pr.ndofs)
+    f = torch.empty_like(y)
+    s.load_coeffs(dev(c), f)
+    u = torch.zeros_like(y)
+    info = s.solve(f, u, tol=1e-8)
+    U = host(u).reshape(N, m)
+    F = A.load_from_coeffs(pr, c).reshape(N, m)
+    res2 = 0.0
+    for n in range(N):
+        r = F[n] - Ab @ U[n] + (Bb @ U[n - 1] if n else 0.0)
+        res2 += float(r @ r)
+    rel = np.sqrt(res2) / np.linalg.norm(F)
+    assert rel <= 1.01e-8, (rel, info)
