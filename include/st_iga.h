@@ -150,6 +150,34 @@ int st_load_coeffs(st_handle h, const double *c, double *f);
  * stay FP64 at the interface).  u: in/out, f: in, device, n_dofs each. */
 int st_smooth(st_handle h, double *u, const double *f, int nsteps);
 
+/* Allocation-free smoothing steps.  The paper has no counterpart: this is a
+ * deployment variant of st_smooth for callers that cannot allocate device
+ * memory -- for example a host application whose memory pool already owns
+ * the GPU's memory, or code that runs where a cudaMalloc would stall or is
+ * forbidden, such as a real-time control loop.  Such a caller builds the
+ * factors with st_setup_host (no device memory), allocates u and f itself,
+ * and calls this function; it performs nsteps FP64 damped block-Jacobi
+ * steps exactly like st_smooth on an FP64 handle.  Its two work vectors and
+ * the uploaded 1D factors live in one file-scope static device array of
+ * ST_STATIC_SCRATCH_BYTES (about 9.7 MB) that every GPU which loads the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree
+ * or other allocating routine.
+ *   h      : any handle (st_setup or st_setup_host); only its host factors are
+ *            read, its precision option is ignored (the steps run in FP64)
+ *   u, f   : device, n_dofs doubles each (u in/out), must not alias
+ *   stream : cudaStream_t for all work of this call (NULL = default stream)
+ * Limits: n_dofs <= ST_STATIC_MAX_DOFS and at most ST_STATIC_MAX_N interior
+ * dofs per axis, else ST_ERR_INVALID_ARG.  The first call on a device looks
+ * up the static array's device address with that device current; make that
+ * first call before any stream capture.  Every call uploads the handle's 1D
+ * factors (at most about 1.3 MB) into the array and reuses the same work space,
+ * which keeps the last call's contents: calls that overlap on the GPU (other
+ * streams or threads) race with each other. */
+#define ST_STATIC_MAX_DOFS 524288
+#define ST_STATIC_MAX_N    160
+#define ST_STATIC_SCRATCH_BYTES (8 * (2 * ST_STATIC_MAX_DOFS + 3 * (2 * ST_STATIC_MAX_N * 7 + 2 * ST_STATIC_MAX_N * ST_STATIC_MAX_N + ST_STATIC_MAX_N)))
+int st_smooth_static(st_handle h, double *u, const double *f, int nsteps, void *stream);
+
 /* One V-cycle on L_h u = f starting from u (in/out), precision as above. */
 int st_vcycle(st_handle h, double *u, const double *f);
 

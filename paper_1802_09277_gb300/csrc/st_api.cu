@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -788,6 +789,47 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Allocation-free smoothing: work vectors and 1D factors in static device
+// memory (see st_smooth_static in include/st_iga.h).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticFactorPerAxis =
+    2 * (size_t)ST_STATIC_MAX_N * (2 * PMAX + 1) + 2 * (size_t)ST_STATIC_MAX_N * ST_STATIC_MAX_N +
+    ST_STATIC_MAX_N;
+constexpr size_t kStaticDoubles = 2 * (size_t)ST_STATIC_MAX_DOFS + 3 * kStaticFactorPerAxis;
+
+// Shared by every call on a device and kept until the process exits.  Host
+// code must not use this name as an address: it only stands for the device
+// symbol; the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
+
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+double *g_static_addr[kMaxDevices] = {nullptr};
+
+// Device address of g_static_scratch on the current device; looked up once
+// per device, with that device current.
+int static_scratch_addr(double **out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(ST_ERR_INVALID_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ST_ERR_CUDA, "cudaGetSymbolAddress(static scratch) failed: %s",
+                        cudaGetErrorString(e));
+        g_static_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_addr[dev];
+    return ST_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void st_options_default(st_options *o) {
@@ -968,6 +1010,72 @@ int st_profile_read(st_handle h, int cls, int64_t *launches, double *ms, double 
     if (ms) *ms = h->prof_ms[cls];
     if (bytes) *bytes = h->prof_bytes[cls];
     if (flops) *flops = h->prof_flops[cls];
+    return ST_OK;
+}
+
+int st_smooth_static(st_handle h, double *u, const double *f, int nsteps, void *stream) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (!u || !f) return fail(ST_ERR_INVALID_ARG, "null vector pointer");
+    if ((const void *)u == (const void *)f) return fail(ST_ERR_INVALID_ARG, "u and f alias");
+    if (nsteps < 0) return fail(ST_ERR_INVALID_ARG, "nsteps < 0");
+    const long long total = h->len * h->nrhs;
+    if (total > ST_STATIC_MAX_DOFS)
+        return fail(ST_ERR_INVALID_ARG, "%lld dofs exceed the static work space of %d dofs", total,
+                    (int)ST_STATIC_MAX_DOFS);
+    for (int a = 0; a < h->dim; ++a)
+        if (h->n[a] > ST_STATIC_MAX_N)
+            return fail(ST_ERR_INVALID_ARG, "%d dofs on axis %d exceed the static limit %d", h->n[a],
+                        a, (int)ST_STATIC_MAX_N);
+    double *base = nullptr;
+    CKS(static_scratch_addr(&base));
+    try {
+        // a view of the handle's host factors that runs on the static memory
+        st_handle_s v;
+        v.dim = h->dim; v.p = h->p; v.N = h->N; v.nt = h->nt; v.nrhs = h->nrhs; v.nlev = h->nlev;
+        for (int a = 0; a < 3; ++a) { v.spans[a] = h->spans[a]; v.n[a] = h->n[a]; }
+        v.opt = h->opt;
+        v.g = h->g;
+        v.len = h->len;
+        v.lv = h->lv;
+        v.stream = (cudaStream_t)stream;
+        v.w64.w0 = base;
+        v.w64.w1 = base + ST_STATIC_MAX_DOFS;
+        const cudaStream_t s = v.stream;
+        const int W = 2 * h->p + 1;
+        for (int a = 0; a < h->dim; ++a) {
+            const int n = h->n[a];
+            double *fa = base + 2 * (size_t)ST_STATIC_MAX_DOFS + a * kStaticFactorPerAxis;
+            double *bm = fa, *bk = bm + (size_t)ST_STATIC_MAX_N * W;
+            double *U = bk + (size_t)ST_STATIC_MAX_N * W, *Ut = U + (size_t)ST_STATIC_MAX_N * ST_STATIC_MAX_N;
+            double *lam = Ut + (size_t)ST_STATIC_MAX_N * ST_STATIC_MAX_N;
+            std::vector<double> hbm((size_t)n * W, 0.0), hbk((size_t)n * W, 0.0), hut((size_t)n * n);
+            for (int i = 0; i < n; ++i)
+                for (int o = -h->p; o <= h->p; ++o) {
+                    const int j = i + o;
+                    if (j < 0 || j >= n) continue;
+                    hbm[(size_t)i * W + o + h->p] = h->M1[a][(size_t)i * n + j];
+                    hbk[(size_t)i * W + o + h->p] = h->K1[a][(size_t)i * n + j];
+                }
+            for (int i = 0; i < n; ++i)
+                for (int k = 0; k < n; ++k) hut[(size_t)k * n + i] = h->U[a][(size_t)i * n + k];
+            // pageable sources: each copy has consumed its host buffer on return
+            CK(cudaMemcpyAsync(bm, hbm.data(), hbm.size() * 8, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(bk, hbk.data(), hbk.size() * 8, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(U, h->U[a].data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(Ut, hut.data(), hut.size() * 8, cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(lam, h->lam[a].data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+            v.s64.bands.M[a] = bm;
+            v.s64.bands.K[a] = bk;
+            v.s64.U[a] = U;
+            v.s64.Ut[a] = Ut;
+            v.s64.lam[a] = lam;
+        }
+        // nothing in the static work space has to start at zero: every step
+        // writes both work vectors before it reads them
+        for (int k = 0; k < nsteps; ++k) CKS(smooth<double>(&v, 0, u, f, v.opt.omega));
+    } catch (...) {
+        return fail(ST_ERR_OOM, "host exception in st_smooth_static");
+    }
     return ST_OK;
 }
 

@@ -21,7 +21,8 @@ OUTER = {"fgmres": 0, "mg": 1}
 
 # every symbol declared in include/st_iga.h
 SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",
-           "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_smooth", "st_vcycle",
+           "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_smooth",
+           "st_smooth_static", "st_vcycle",
            "st_solve", "st_profile", "st_profile_read", "st_time_factors", "st_space_factors",
            "st_time_prolongation", "st_last_error"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
@@ -74,6 +75,7 @@ def load():
         "st_residual": (I, [P, P, P, P]),
         "st_load_coeffs": (I, [P, P, P]),
         "st_smooth": (I, [P, P, P, I]),
+        "st_smooth_static": (I, [P, P, P, I, P]),
         "st_vcycle": (I, [P, P, P]),
         "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
         "st_profile": (I, [P, I]),
@@ -180,6 +182,16 @@ class Solver:
     def smooth(self, u, f, nsteps=1):
         _check(_lib.st_smooth(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f"),
                               int(nsteps)))
+
+    def smooth_static(self, u, f, nsteps=1, stream=None):
+        """FP64 smoothing steps with the library's static device work space
+        (no device allocation; works on a host_only handle)."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        _check(_lib.st_smooth_static(self._h, _dptr(u, self.ndofs, "u"),
+                                     _dptr(f, self.ndofs, "f"), int(nsteps),
+                                     ctypes.c_void_p(stream)))
 
     def vcycle(self, u, f):
         _check(_lib.st_vcycle(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f")))
