@@ -159,8 +159,9 @@ def gpu_arm(args, rank, world):
     common = dict(ne_per_slab=ne, outer="fgmres", gmres_restart=20, max_it=300)
     peaks, peak_src = load_peaks()
 
-    def make(prec):
-        return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, **common)
+    def make(prec, basis):
+        return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
+                         **common)
 
     # rank r solves its own right-hand side (independent replicas)
     c = torch.tensor(inputs.normal_coeffs(seed + 1000 * rank, 0 + make_len(d, spans, p, N, ne)),
@@ -199,7 +200,7 @@ def gpu_arm(args, rank, world):
         return times, infos, u, prof
 
     # --- mixed precision (headline) ---
-    sm = make("mixed_fp32")
+    sm = make(args.precision, args.basis)
     f = torch.empty_like(c)
     sm.load_coeffs(c, f)
     clocks = ClockSampler(dev.index)
@@ -233,10 +234,26 @@ def gpu_arm(args, rank, world):
             e2e_t.append(e0.elapsed_time(e1))
     e2e_ms = sum(e2e_t) / len(e2e_t)
 
-    # --- plain FP64 method on the same workload ---
-    s64 = make("fp64")
-    t64, i64, u64, _ = timed_solves(s64, f, max(1, args.steps // 2), 1)
-    ms64 = sum(t64) / len(t64)
+    # --- the other variants on the same workload (fewer steps, no profiling) ---
+    other = "nodal" if args.basis == "spectral" else "spectral"
+    variants = {}
+    u64 = None
+    for name, prec, basis in (("fp64_plain", "fp64", "nodal"), ("fp64_" + "spectral", "fp64", "spectral"),
+                              ("mixed_" + other, args.precision, other)):
+        if name in variants:
+            continue
+        sv = make(prec, basis)
+        tv, iv, uv, _ = timed_solves(sv, f, max(1, args.steps // 2), 1)
+        msv = sum(tv) / len(tv)
+        variants[name] = {"precision": prec, "basis": basis, "ms_per_step": msv,
+                          "value": sv.ndofs * world / (msv / 1e3),
+                          "iterations": iv[-1]["iterations"], "rel_residual": iv[-1]["rel_residual"]}
+        if name == "fp64_plain":
+            u64 = uv.clone()
+        sv.close()
+    ms64 = variants["fp64_plain"]["ms_per_step"]
+    i64 = [{"iterations": variants["fp64_plain"]["iterations"],
+            "rel_residual": variants["fp64_plain"]["rel_residual"]}]
     rel_diff = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
 
     # --- roofline of the dominant kernel class ---
@@ -253,9 +270,9 @@ def gpu_arm(args, rank, world):
         "bytes_d2h": f.numel() * 8, "prof": prof, "dominant": dom,
         "per_launch_ms": per_launch_ms, "launches": launches // max(args.steps, 1),
         "launches_total": launches, "clocks": clk, "peaks": peaks, "peak_src": peak_src,
+        "variants": variants,
     }
     sm.close()
-    s64.close()
     return result
 
 
@@ -272,7 +289,7 @@ def roofline_entry(r):
     pd = r["prof"][dom]
     secs = pd["ms"] / 1e3
     clk_max = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    if dom in ("gemm32",):
+    if dom in ("gemm32", "gemm64"):
         # FP32 FMA on CUDA cores: 152 SMs x 128 lanes x 2 flop x max clock
         peak = 152 * 128 * 2 * clk_max / 1e12
         achieved = pd["flops"] / secs / 1e12
@@ -298,6 +315,9 @@ def main():
     ap.add_argument("--sample-slabs", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--basis", default="spectral", choices=["spectral", "nodal"])
+    ap.add_argument("--precision", default="mixed_fp32",
+                    choices=["mixed_fp32", "mixed_tf32", "mixed_bf16", "fp64"])
     args = ap.parse_args()
 
     if args.cpu_leg:
@@ -310,6 +330,7 @@ def main():
     cfg = {"workload": args.workload, "domain": "unit %s" % {1: "interval", 2: "square", 3: "cube"}[d],
            "spans": list(spans), "degree": p, "slabs": N, "time_elements_per_slab": ne,
            "theta": 1.0, "tol": tol, "solver": "FGMRES(20) + 1 V-cycle, omega=0.5, nu=1/1",
+           "precision": args.precision, "vcycle_basis": args.basis,
            "rhs": "N(0,1) B-spline coefficients, seed %d" % seed, "l2": "flushed between steps"}
 
     if args.impl == "reference":
@@ -356,11 +377,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_mixed_max"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": cfg,
         "iterations": r["iters_mixed"], "rel_residual": r["res_mixed"],
         "fp64_plain": {"value": ndofs * world / (r["ms64"] / 1e3), "ms_per_step": r["ms64"],
-                       "iterations": r["iters64"], "rel_residual": r["res64"], "dtype": "f64"},
+                       "iterations": r["iters64"], "rel_residual": r["res64"], "dtype": "f64",
+                       "basis": "nodal"},
+        "variants": r["variants"],
         "mixed_vs_fp64_solution_rel_diff": r["rel_diff_mixed_vs_fp64"],
         "roofline": roofline_entry(r),
         "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),

@@ -64,6 +64,17 @@ extern "C" {
 #define ST_MIXED_TF32  2  /* V-cycle FP32, spatial transforms on TF32 tensor cores */
 #define ST_MIXED_BF16  3  /* V-cycle FP32, spatial transforms on BF16 tensor cores */
 
+/* basis of the V-cycle (both give the same iterates up to rounding) */
+#define ST_BASIS_NODAL    0 /* B-spline basis: every smoothing step computes the
+                               residual with the banded 1D matrices and applies
+                               A_n^{-1} by time transform, spatial transforms,
+                               shift solve, inverse transforms (Sec. 3.1, Eq. 3.1) */
+#define ST_BASIS_SPECTRAL 1 /* spatial eigenbasis: the spatial transforms are
+                               applied once on entry and once on exit of the
+                               V-cycle; they commute with the time-only
+                               coarsening and the block-Jacobi smoother, and in
+                               between every operator is pointwise in the mode */
+
 /* outer iteration */
 #define ST_OUTER_FGMRES 0 /* FGMRES(restart), right-preconditioned by one V-cycle */
 #define ST_OUTER_MG     1 /* multigrid iteration u <- u + V(f - L u)             */
@@ -82,6 +93,7 @@ typedef struct {
     int max_it;           /* outer iteration cap (default 200)                   */
     int nrhs;             /* independent right-hand sides solved together (1)    */
     size_t hbm_budget;    /* bytes the handle may allocate; 0 = unlimited        */
+    int basis;            /* ST_BASIS_NODAL (default) / ST_BASIS_SPECTRAL         */
 } st_options;
 
 typedef struct {

@@ -1,0 +1,252 @@
+// The time-multigrid V-cycle in the spatial eigenbasis (arXiv:1802.09277,
+// Sec. 3.1 smoother with A_n^{-1} from Eq. 3.1).
+//
+// With U^T M_x U = I and U^T K_x U = Lambda (U = U_z (x) U_y (x) U_x) the
+// slab operator becomes A^ = K_t (x) I + M_t (x) Lambda and the coupling
+// B^ = N_t (x) I: every spatial mode k (shift mu_k = sum over axes of the 1D
+// eigenvalues) carries an independent block lower-bidiagonal time problem
+// with diagonal blocks K_t + mu_k M_t = Y^{-1} (Z + mu_k I) X^{-1}.  Time
+// coarsening (P = P_t (x) I) and block Jacobi commute with the spatial
+// transform, so the V-cycle of the original basis equals
+// (I (x) U) V^(r^) with r^ = (I (x) U^T) r.  Here every kernel is pointwise in
+// the spatial mode; one thread owns one (slab, mode) pair and its N_t
+// coefficients, reading them with stride nxyz (coalesced across threads).
+//
+//  k_spec_smooth        one damped block-Jacobi step, out-of-place (Jacobi:
+//                       every slab sees the previous iterate of its
+//                       predecessor): r = f - A^ u + B^ u_prev,
+//                       u_out = u + omega X (Z + mu I)^{-1} Y r
+//  k_spec_res_restrict  residual of two fine slabs and their restriction
+//                       P_t^T onto the merged coarse slab
+//  k_spec_coarse        exact solve of a level by forward substitution over
+//                       its slabs: u_n = A^{-1} (f_n + B^ u_{n-1})
+#include "st_internal.h"
+
+namespace st {
+
+// r = f - (Kt + mu Mt) u + e_0 uprev  (in place into f's copy)
+template <typename T>
+__device__ __forceinline__ void spec_residual(const SpecCoefs<T> &c, T mu, const T *u, T uprev,
+                                              T *r) {
+    const int nt = c.nt;
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) {
+        if (i >= nt) break;
+        T a = r[i];
+#pragma unroll
+        for (int j = 0; j < NTMAX; ++j)
+            if (j < nt) a -= (c.Kt[i * NTMAX + j] + mu * c.Mt[i * NTMAX + j]) * u[j];
+        if (i == 0) a += uprev;
+        r[i] = a;
+    }
+}
+
+// v = X (Z + mu I)^{-1} Y r  =  (K_t + mu M_t)^{-1} r   (Eq. 3.1 per mode)
+template <typename T>
+__device__ __forceinline__ void spec_block_solve(const SpecCoefs<T> &c, T mu, const T *r, T *v) {
+    const int nt = c.nt;
+    T w[NTMAX], z[NTMAX];
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) {
+        T a = T(0);
+#pragma unroll
+        for (int j = 0; j < NTMAX; ++j)
+            if (j < nt) a += c.Y[i * NTMAX + j] * r[j];
+        w[i] = a;
+        z[i] = T(0);
+    }
+    bool skip = false;
+#pragma unroll
+    for (int i = NTMAX - 1; i >= 0; --i) {
+        if (i >= nt) continue;
+        if (skip) {
+            skip = false;
+            continue;
+        }
+        if (i >= 1 && c.blk[i]) {
+            T g1 = w[i - 1], g2 = w[i];
+#pragma unroll
+            for (int j = i + 1; j < NTMAX; ++j)
+                if (j < nt) {
+                    g1 -= c.Z[(i - 1) * NTMAX + j] * z[j];
+                    g2 -= c.Z[i * NTMAX + j] * z[j];
+                }
+            const T a = c.Z[(i - 1) * NTMAX + i - 1] + mu, b = c.Z[(i - 1) * NTMAX + i];
+            const T cc = c.Z[i * NTMAX + i - 1], d = c.Z[i * NTMAX + i] + mu;
+            const T det = a * d - b * cc;
+            z[i - 1] = (d * g1 - b * g2) / det;
+            z[i] = (a * g2 - cc * g1) / det;
+            skip = true;
+        } else {
+            T gg = w[i];
+#pragma unroll
+            for (int j = i + 1; j < NTMAX; ++j)
+                if (j < nt) gg -= c.Z[i * NTMAX + j] * z[j];
+            z[i] = gg / (c.Z[i * NTMAX + i] + mu);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) {
+        T a = T(0);
+#pragma unroll
+        for (int j = 0; j < NTMAX; ++j)
+            if (j < nt) a += c.X[i * NTMAX + j] * z[j];
+        v[i] = a;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T mode_shift(const Grid &g, const T *lam0, const T *lam1, const T *lam2,
+                                        long long k) {
+    const int kx = (int)(k % g.nx);
+    T mu = lam0[kx];
+    if (g.dim >= 2) mu += lam1[(int)((k / g.nx) % g.ny)];
+    if (g.dim >= 3) mu += lam2[(int)(k / ((long long)g.nx * g.ny))];
+    return mu;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_spec_smooth(const T *__restrict__ uin, T *__restrict__ uout, const T *__restrict__ f,
+                  const T *__restrict__ lam0, const T *__restrict__ lam1,
+                  const T *__restrict__ lam2, Grid g, const __grid_constant__ SpecCoefs<T> c,
+                  T omega, int slabs_per_prob, long long nslabs, int uin_zero) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nslabs * g.nxyz) return;
+    const long long slab = idx / g.nxyz, k = idx % g.nxyz;
+    const int nt = c.nt;
+    const long long base = slab * nt * g.nxyz + k;
+    const T mu = mode_shift(g, lam0, lam1, lam2, k);
+    T u[NTMAX], r[NTMAX], v[NTMAX];
+    T uprev = T(0);
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) {
+        u[i] = (i < nt && !uin_zero) ? uin[base + (long long)i * g.nxyz] : T(0);
+        r[i] = (i < nt) ? f[base + (long long)i * g.nxyz] : T(0);
+    }
+    if (!uin_zero && (slab % slabs_per_prob) != 0) uprev = uin[base - g.nxyz];
+    spec_residual(c, mu, u, uprev, r);
+    spec_block_solve(c, mu, r, v);
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i)
+        if (i < nt) uout[base + (long long)i * g.nxyz] = u[i] + omega * v[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_spec_res_restrict(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ fc,
+                        const T *__restrict__ lam0, const T *__restrict__ lam1,
+                        const T *__restrict__ lam2, Grid g, const __grid_constant__ SpecCoefs<T> c,
+                        const __grid_constant__ ProlongCoefs<T> pc, int slabs_per_prob,
+                        long long ncoarse) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ncoarse * g.nxyz) return;
+    const long long m = idx / g.nxyz, k = idx % g.nxyz;
+    const int nt = c.nt;
+    const T mu = mode_shift(g, lam0, lam1, lam2, k);
+    const long long a = 2 * m;  // first fine slab (same problem as a + 1)
+    const long long ba = a * nt * g.nxyz + k, bb = ba + (long long)nt * g.nxyz;
+    T ua[NTMAX], ub[NTMAX], ra[NTMAX], rb[NTMAX];
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) {
+        const bool in = i < nt;
+        ua[i] = in ? u[ba + (long long)i * g.nxyz] : T(0);
+        ub[i] = in ? u[bb + (long long)i * g.nxyz] : T(0);
+        ra[i] = in ? f[ba + (long long)i * g.nxyz] : T(0);
+        rb[i] = in ? f[bb + (long long)i * g.nxyz] : T(0);
+    }
+    const T uprev = ((a % slabs_per_prob) != 0) ? u[ba - g.nxyz] : T(0);
+    T ua_last = T(0);
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i)
+        if (i == nt - 1) ua_last = ua[i];
+    spec_residual(c, mu, ua, uprev, ra);
+    spec_residual(c, mu, ub, ua_last, rb);
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) {
+        if (i >= nt) break;
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < NTMAX; ++j)
+            if (j < nt) s += pc.P[j * NTMAX + i] * ra[j] + pc.P[(nt + j) * NTMAX + i] * rb[j];
+        fc[(m * nt + i) * g.nxyz + k] = s;
+    }
+}
+
+// grid over (problem, mode); sequential over the level's slabs
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_spec_coarse(T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ lam0,
+                  const T *__restrict__ lam1, const T *__restrict__ lam2, Grid g,
+                  const __grid_constant__ SpecCoefs<T> c, int slabs_per_prob, int nprob) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nprob * g.nxyz) return;
+    const long long prob = idx / g.nxyz, k = idx % g.nxyz;
+    const int nt = c.nt;
+    const T mu = mode_shift(g, lam0, lam1, lam2, k);
+    T prev = T(0);
+    for (int n = 0; n < slabs_per_prob; ++n) {
+        const long long base = ((prob * slabs_per_prob + n) * nt) * g.nxyz + k;
+        T r[NTMAX], v[NTMAX];
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i) r[i] = (i < nt) ? f[base + (long long)i * g.nxyz] : T(0);
+        r[0] += prev;
+        spec_block_solve(c, mu, r, v);
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i) {
+            if (i < nt) u[base + (long long)i * g.nxyz] = v[i];
+            if (i == nt - 1) prev = v[i];
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *const lam[3],
+                               const Grid &g, const SpecCoefs<T> &c, T omega, int slabs_per_prob,
+                               long long nslabs, int uin_zero, cudaStream_t s) {
+    const long long total = nslabs * g.nxyz;
+    if (total <= 0) return cudaSuccess;
+    k_spec_smooth<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        uin, uout, f, lam[0], lam[1], lam[2], g, c, omega, slabs_per_prob, nslabs, uin_zero);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *const lam[3],
+                                     const Grid &g, const SpecCoefs<T> &c,
+                                     const ProlongCoefs<T> &pc, int slabs_per_prob,
+                                     long long ncoarse, cudaStream_t s) {
+    const long long total = ncoarse * g.nxyz;
+    if (total <= 0) return cudaSuccess;
+    k_spec_res_restrict<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        u, f, fc, lam[0], lam[1], lam[2], g, c, pc, slabs_per_prob, ncoarse);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_coarse(T *u, const T *f, const T *const lam[3], const Grid &g,
+                               const SpecCoefs<T> &c, int slabs_per_prob, int nprob,
+                               cudaStream_t s) {
+    const long long total = (long long)nprob * g.nxyz;
+    if (total <= 0) return cudaSuccess;
+    k_spec_coarse<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        u, f, lam[0], lam[1], lam[2], g, c, slabs_per_prob, nprob);
+    return cudaGetLastError();
+}
+
+#define ST_INST(T)                                                                             \
+    template cudaError_t launch_spec_smooth<T>(const T *, T *, const T *, const T *const[3],   \
+                                               const Grid &, const SpecCoefs<T> &, T, int,     \
+                                               long long, int, cudaStream_t);                  \
+    template cudaError_t launch_spec_res_restrict<T>(const T *, const T *, T *,                \
+                                                     const T *const[3], const Grid &,          \
+                                                     const SpecCoefs<T> &,                     \
+                                                     const ProlongCoefs<T> &, int, long long,  \
+                                                     cudaStream_t);                            \
+    template cudaError_t launch_spec_coarse<T>(T *, const T *, const T *const[3], const Grid &, \
+                                               const SpecCoefs<T> &, int, int, cudaStream_t);
+ST_INST(double)
+ST_INST(float)
+#undef ST_INST
+
+}  // namespace st

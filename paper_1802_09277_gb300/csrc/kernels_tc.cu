@@ -1,0 +1,264 @@
+// Spatial fast-diagonalisation transforms on the 5th-generation tensor cores
+// (tcgen05, sm_100 family): one axis of out[..k..] = sum_i W[i][k] in[..i..]
+// (W = U for the forward transform U^T, W = U^T for the inverse), the dense
+// contraction inside A^{-1} = (X (x) U)(Z (x) I + I (x) Lambda)^{-1}(Y (x) U^T)
+// (Eq. 3.1 of arXiv:1802.09277 with fast diagonalisation in space).
+//
+// FP32 data in HBM; operands rounded to TF32 (cvt.rna) or BF16 while they are
+// staged into shared memory; FP32 accumulation in tensor memory.
+//
+// MODE_X (contracted axis contiguous):  D[k][c] = sum_i Wt[k][i] In[c][i]
+//     A = Wt (128 rows = output modes, n_out <= 128), B = 128 input rows
+//     c, D in TMEM with lane = k: out[c][k] is written by consecutive lanes.
+// MODE_S (contracted axis strided by `inner`): D[c][k] = sum_i In_c[i] Wt[k][i]
+//     A = 128 columns c = (outer, inner index), B = Wt (N = n_out padded to
+//     16, <= 256), lane = c: out[o][k][ci] is written by consecutive lanes.
+//
+// One CTA (128 threads) loops over 128-column tiles: all threads stage the
+// activation tile, thread 0 issues the MMAs and commits them to an
+// mbarrier, all threads wait (bounded) and drain TMEM with tcgen05.ld.
+#include <cuda_bf16.h>
+
+#include "st_internal.h"
+#include "tc_sm100.cuh"
+
+namespace st {
+
+namespace {
+
+constexpr int TC_THREADS = 128;
+constexpr int TC_COLS = 128;  // columns (GEMM rows of the activation operand) per tile
+constexpr uint32_t TC_MAX_POLLS = 1u << 24;
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// Store 16 bytes of operand data for row r, 16-byte chunk kc of a K-major tile
+// with R rows.  TF32: 4 values; BF16: 8 values.
+template <int KIND>
+__device__ __forceinline__ void stage16(unsigned char *tile, int R, int r, int kc, const float *v) {
+    uint4 q;
+    if (KIND == tc::FMT_TF32) {
+        q.x = to_tf32(v[0]);
+        q.y = to_tf32(v[1]);
+        q.z = to_tf32(v[2]);
+        q.w = to_tf32(v[3]);
+    } else {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        __nv_bfloat162 c = __floats2bfloat162_rn(v[4], v[5]);
+        __nv_bfloat162 d = __floats2bfloat162_rn(v[6], v[7]);
+        q.x = *reinterpret_cast<uint32_t *>(&a);
+        q.y = *reinterpret_cast<uint32_t *>(&b);
+        q.z = *reinterpret_cast<uint32_t *>(&c);
+        q.w = *reinterpret_cast<uint32_t *>(&d);
+    }
+    *reinterpret_cast<uint4 *>(tile + tc::kmajor_offset(R, r, kc * 16)) = q;
+}
+
+}  // namespace
+
+struct TcArgs {
+    const float *in;
+    float *out;
+    const float *wt;   // Wt[k][i] row-major, n_out x n_in (FP32)
+    int n_in, n_out;   // contracted / produced axis length
+    int k_pad;         // n_in padded to the MMA K step
+    int n_pad;         // MODE_S: n_out padded to 16
+    long long ncols;   // number of GEMM columns (input rows / (outer, inner) pairs)
+    long long inner;   // MODE_S: stride of the contracted axis
+    int *err;          // set to 1 if an mbarrier wait ran out
+};
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    constexpr int ESZ = (KIND == tc::FMT_TF32) ? 4 : 2;
+    constexpr int EPC = 16 / ESZ;  // elements per 16-byte chunk
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int KC = a.k_pad / EPC;  // 16-byte chunks per operand row
+    const int wrows = (MODE == 0) ? 128 : a.n_pad;
+    unsigned char *wtile = smem;
+    unsigned char *xtile = smem + (size_t)wrows * KC * 16;
+    const uint32_t tmem_cols = (MODE == 0) ? 128u : (a.n_pad <= 32 ? 32u : a.n_pad <= 64 ? 64u
+                                                   : a.n_pad <= 128 ? 128u : 256u);
+
+    // weight operand Wt[k][i] (zero padded), staged once
+    for (int t = tid; t < wrows * KC; t += TC_THREADS) {
+        const int r = t / KC, kc = t % KC;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < EPC; ++j) {
+            const int i = kc * EPC + j;
+            v[j] = (r < a.n_out && i < a.n_in) ? a.wt[(long long)r * a.n_in + i] : 0.f;
+        }
+        stage16<KIND>(wtile, wrows, r, kc, v);
+    }
+    if (tid == 0) tc::mbar_init(&mbar, 1);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = (MODE == 0) ? tc::make_idesc(KIND, 128, TC_COLS)
+                                       : tc::make_idesc(KIND, 128, a.n_pad);
+    const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
+    uint32_t phase = 0;
+    bool failed = false;
+
+    for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        const long long c0 = tile * TC_COLS;
+        // ---- stage the activation tile: 128 rows (columns c) x k_pad ----
+        if (MODE == 0) {
+            // lanes: 8 consecutive rows x 4 consecutive 16-byte chunks
+            for (int t = tid; t < TC_COLS * KC; t += TC_THREADS) {
+                const int grp = t / (8 * KC), rem = t % (8 * KC);
+                const int kc = rem / 8, r = grp * 8 + rem % 8;
+                const long long c = c0 + r;
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < EPC; ++j) {
+                    const int i = kc * EPC + j;
+                    v[j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
+                }
+                stage16<KIND>(xtile, TC_COLS, r, kc, v);
+            }
+        } else {
+            // lanes: consecutive columns (consecutive inner index), same chunk
+            for (int t = tid; t < TC_COLS * KC; t += TC_THREADS) {
+                const int kc = t / TC_COLS, r = t % TC_COLS;
+                const long long c = c0 + r;
+                const long long o = c / a.inner, ci = c % a.inner;
+                const float *src = a.in + o * a.n_in * a.inner + ci;
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < EPC; ++j) {
+                    const int i = kc * EPC + j;
+                    v[j] = (c < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
+                }
+                stage16<KIND>(xtile, TC_COLS, r, kc, v);
+            }
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        // ---- MMAs: K in 32-byte steps ----
+        if (tid == 0) {
+            const uint32_t wa = tc::smem_u32(wtile), xa = tc::smem_u32(xtile);
+            const uint32_t lbo_w = (uint32_t)wrows * 16, lbo_x = TC_COLS * 16;
+            const int steps = KC / 2;
+            for (int s = 0; s < steps; ++s) {
+                const uint64_t dw = tc::make_sdesc(wa + 2 * s * lbo_w, lbo_w, 128);
+                const uint64_t dx = tc::make_sdesc(xa + 2 * s * lbo_x, lbo_x, 128);
+                if (MODE == 0)
+                    tc::mma<KIND>(tmem, dw, dx, idesc, s > 0 ? 1u : 0u);
+                else
+                    tc::mma<KIND>(tmem, dx, dw, idesc, s > 0 ? 1u : 0u);
+            }
+            tc::commit(&mbar);
+        }
+        if (!tc::mbar_wait_bounded(&mbar, phase, TC_MAX_POLLS)) {
+            failed = true;
+            if (tid == 0) atomicExch(a.err, 1);
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (!failed) {
+            // ---- epilogue: TMEM -> registers -> global ----
+            const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+            if (MODE == 0) {
+                const int k = 32 * warp + lane;  // output mode of this lane
+                if (32 * warp < a.n_out) {
+                    for (int cc = 0; cc < TC_COLS; cc += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tmem + lane_base + cc, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const long long c = c0 + cc + j;
+                            if (k < a.n_out && c < a.ncols) a.out[c * a.n_out + k] = v[j];
+                        }
+                    }
+                }
+            } else {
+                const long long c = c0 + 32 * warp + lane;  // column of this lane
+                const long long o = c / a.inner, ci = c % a.inner;
+                float *dst = a.out + o * a.n_out * a.inner + ci;
+                for (int kk = 0; kk < a.n_pad; kk += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + lane_base + kk, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int k = kk + j;
+                        if (k < a.n_out && c < a.ncols) dst[(long long)k * a.inner] = v[j];
+                    }
+                }
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
+}
+
+template <int KIND, int MODE>
+static cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s, int nsm) {
+    constexpr int EPC = (KIND == tc::FMT_TF32) ? 4 : 8;
+    const int KC = a.k_pad / EPC;
+    const int wrows = (MODE == 0) ? 128 : a.n_pad;
+    const size_t smem = (size_t)(wrows + TC_COLS) * KC * 16;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_axis<KIND, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    // CTAs per SM limited so that their TMEM columns fit in 512
+    const int tmem_cols = (MODE == 0) ? 128 : (a.n_pad <= 32 ? 32 : a.n_pad <= 64 ? 64
+                                               : a.n_pad <= 128 ? 128 : 256);
+    int per_sm = 512 / tmem_cols;
+    const int by_smem = (int)((220 * 1024) / (smem + 1024));
+    if (by_smem < per_sm) per_sm = by_smem;
+    if (per_sm < 1) per_sm = 1;
+    const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
+    long long grid = (long long)nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid <= 0) return cudaSuccess;
+    k_tc_axis<KIND, MODE><<<(unsigned)grid, TC_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Returns cudaErrorNotSupported when the shape is outside what the kernel
+// covers (the caller then uses the CUDA-core transform).
+cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, const float *wt,
+                           int n_in, int n_out, long long ncols, long long inner, int *err,
+                           int nsm, cudaStream_t s) {
+    TcArgs a;
+    a.in = in;
+    a.out = out;
+    a.wt = wt;
+    a.n_in = n_in;
+    a.n_out = n_out;
+    const int kstep = (kind == tc::FMT_TF32) ? 8 : 16;
+    a.k_pad = (n_in + kstep - 1) / kstep * kstep;
+    a.n_pad = (n_out + 15) / 16 * 16;
+    a.ncols = ncols;
+    a.inner = inner;
+    a.err = err;
+    if (ncols <= 0) return cudaSuccess;
+    if (mode == 0 && n_out > 128) return cudaErrorNotSupported;
+    if (mode == 1 && a.n_pad > 256) return cudaErrorNotSupported;
+    if (kind == tc::FMT_TF32)
+        return mode == 0 ? launch_tc_t<tc::FMT_TF32, 0>(a, s, nsm) : launch_tc_t<tc::FMT_TF32, 1>(a, s, nsm);
+    return mode == 0 ? launch_tc_t<tc::FMT_BF16, 0>(a, s, nsm) : launch_tc_t<tc::FMT_BF16, 1>(a, s, nsm);
+}
+
+}  // namespace st

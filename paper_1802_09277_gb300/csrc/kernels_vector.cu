@@ -14,6 +14,7 @@ struct VecList {
 struct AxpyArgs {
     const double *x[MAXV];
     double coef[MAXV * NRHS_MAX];
+    double post[NRHS_MAX];  // y <- post_r * (y + sum_v coef x_v)
 };
 
 template <typename Tin, typename Tout>
@@ -54,39 +55,51 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// grid (nblk, nrhs), 256 threads; partial[(v*nrhs + r)*nblk + blk]
+// grid (nblk, nrhs), 256 threads; partial[(v*nrhs + r)*nblk + blk].
+// One pass over w: every thread keeps the nv running sums in registers.
 __global__ void __launch_bounds__(256)
     k_multidot_partial(int nv, const __grid_constant__ VecList vl, const double *__restrict__ w,
                        long long len, double *__restrict__ partial) {
-    __shared__ double red[8];
+    __shared__ double red[8][MAXV];
     const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
     const long long chunk = (len + nblk - 1) / nblk;
     const long long lo = blockIdx.x * chunk;
     const long long hi = (lo + chunk < len) ? lo + chunk : len;
-    const double *wr = w + (long long)r * len;
-    for (int v = 0; v < nv; ++v) {
-        const double *xr = vl.v[v] + (long long)r * len;
-        double s = 0.0;
-        for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += xr[i] * wr[i];
-        s = warp_sum(s);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < 8; ++q) t += red[q];
-            partial[((long long)v * nrhs + r) * nblk + blockIdx.x] = t;
-        }
-        __syncthreads();
+    const long long off = (long long)r * len;
+    double acc[MAXV];
+#pragma unroll
+    for (int v = 0; v < MAXV; ++v) acc[v] = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const double wi = w[off + i];
+#pragma unroll
+        for (int v = 0; v < MAXV; ++v)
+            if (v < nv) acc[v] += vl.v[v][off + i] * wi;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < MAXV; ++v) {
+        if (v >= nv) break;
+        const double t = warp_sum(acc[v]);
+        if (lane == 0) red[warp][v] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+        partial[((long long)threadIdx.x * nrhs + r) * nblk + blockIdx.x] = t;
     }
 }
 
+// one warp per output; lane-strided partial sums, then a fixed shuffle tree
 __global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, int count,
                                   double *__restrict__ out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x & 31;
     if (i >= count) return;
     double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += partial[(long long)i * nblk + b];
-    out[i] = t;
+    for (int b = lane; b < nblk; b += 32) t += partial[(long long)i * nblk + b];
+    t = warp_sum(t);
+    if (lane == 0) out[i] = t;
 }
 
 cudaError_t launch_multidot(int nv, const double *const *vecs, const double *w, int nrhs,
@@ -99,7 +112,7 @@ cudaError_t launch_multidot(int nv, const double *const *vecs, const double *w, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int count = nv * nrhs;
-    k_reduce_partials<<<(count + 127) / 128, 128, 0, s>>>(partial, nblk, count, out);
+    k_reduce_partials<<<(count + 3) / 4, 128, 0, s>>>(partial, nblk, count, out);
     return cudaGetLastError();
 }
 
@@ -111,19 +124,20 @@ __global__ void k_multiaxpy(int nv, const __grid_constant__ AxpyArgs aa, int nrh
         const int r = (int)(i / len);
         double acc = y[i];
         for (int v = 0; v < nv; ++v) acc += aa.coef[v * NRHS_MAX + r] * aa.x[v][i];
-        y[i] = acc;
+        y[i] = aa.post[r] * acc;
     }
 }
 
 cudaError_t launch_multiaxpy(int nv, const double *const *xs, const double *coef, int nrhs,
-                             long long len, double *y, cudaStream_t s) {
-    if (nv > MAXV || nrhs > NRHS_MAX) return cudaErrorInvalidValue;
-    if (nv <= 0) return cudaSuccess;
+                             long long len, double *y, cudaStream_t s, const double *post) {
+    if (nv > MAXV || nrhs > NRHS_MAX || nv < 0) return cudaErrorInvalidValue;
+    if (nv == 0 && !post) return cudaSuccess;
     AxpyArgs aa;
     for (int v = 0; v < nv; ++v) {
         aa.x[v] = xs[v];
         for (int r = 0; r < nrhs; ++r) aa.coef[v * NRHS_MAX + r] = coef[v * nrhs + r];
     }
+    for (int r = 0; r < nrhs; ++r) aa.post[r] = post ? post[r] : 1.0;
     long long blocks = ((long long)nrhs * len + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     k_multiaxpy<<<(unsigned)blocks, 256, 0, s>>>(nv, aa, nrhs, len, y);

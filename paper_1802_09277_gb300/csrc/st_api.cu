@@ -82,6 +82,8 @@ struct st_handle_s {
     long long len = 0;  // dofs per rhs on level 0
     bool host_only = false;
     bool mixed = false;
+    int nsm = 152;
+    int *tc_err = nullptr;  // device flag: a tensor-core kernel's bounded wait ran out
     // host factors
     Mat M1[3], K1[3], U[3], Pt;
     std::vector<double> lam[3];
@@ -287,6 +289,26 @@ ProlongCoefs<T> pack_prolong(st_handle h) {
 }
 
 template <typename T>
+SpecCoefs<T> pack_spec(st_handle h, int l) {
+    SpecCoefs<T> c;
+    std::memset(&c, 0, sizeof c);
+    const int nt = h->nt;
+    const LevelHost &L = h->lv[l];
+    for (int i = 0; i < nt; ++i) {
+        for (int j = 0; j < nt; ++j) {
+            c.Kt[i * NTMAX + j] = (T)L.Kt[i * nt + j];
+            c.Mt[i * NTMAX + j] = (T)L.Mt[i * nt + j];
+            c.Y[i * NTMAX + j] = (T)L.Y[i * nt + j];
+            c.Z[i * NTMAX + j] = (T)L.Z[i * nt + j];
+            c.X[i * NTMAX + j] = (T)L.X[i * nt + j];
+        }
+        c.blk[i] = L.blk[i];
+    }
+    c.nt = nt;
+    return c;
+}
+
+template <typename T>
 DevSpace<T> &space(st_handle h);
 template <>
 DevSpace<double> &space<double>(st_handle h) { return h->s64; }
@@ -321,31 +343,52 @@ int stencil(st_handle h, int l, const T *u, const T *f, T *out, int mode, bool f
 
 // out[..k..] = sum_i W[i][k] in[..i..] along every active axis (forward: W = U,
 // i.e. U^T applied; inverse: W = U^T).  Ping-pongs in -> t0 -> t1 -> t0;
-// *res is the buffer holding the result.
+// *res is the buffer holding the result.  FP32 transforms run on the tensor
+// cores in the TF32 / BF16 modes (CUDA cores for shapes the kernel does not
+// cover), everything else on CUDA cores.
 template <typename T>
-int spatial(st_handle h, const T *in, T *t0, T *t1, const T *const W[3], long long planes, T **res) {
+int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long long planes) {
+    DevSpace<T> &ds = space<T>(h);
     const long long nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
+    const long long n = (axis == 0) ? nx : (axis == 1) ? ny : nz;
     const double E = (double)planes * h->g.nxyz;
-    const int c = cls_of<T>(ST_PROF_GEMM64, ST_PROF_GEMM32);
-    {
-        KScope ks(h, c, sizeof(T) * (2.0 * E + nx * nx), 2.0 * E * nx);
-        CK(launch_gemm_strided<T>(1, (int)(planes * nz * ny), (int)nx, (int)nx, in, 0, nx, 1, W[0], 0,
-                                  nx, 1, t0, 0, nx, 1, h->stream));
+    const T *W = forward ? ds.U[axis] : ds.Ut[axis];
+    const long long inner = (axis == 0) ? 1 : (axis == 1) ? nx : nx * ny;
+    const long long outer = (long long)(E / (double)(n * inner) + 0.5);
+    const int prec = h->opt.precision;
+    if (sizeof(T) == 4 && (prec == ST_MIXED_TF32 || prec == ST_MIXED_BF16)) {
+        const float *Wt = (const float *)(forward ? ds.Ut[axis] : ds.U[axis]);
+        const int kind = (prec == ST_MIXED_TF32) ? 2 : 1;
+        const long long ncols = (axis == 0) ? outer : outer * inner;
+        KScope ks(h, ST_PROF_GEMM32, sizeof(T) * (2.0 * E + n * n), 2.0 * E * n);
+        const cudaError_t e = launch_tc_axis(kind, axis == 0 ? 0 : 1, (const float *)in,
+                                             (float *)out, Wt, (int)n, (int)n, ncols, inner,
+                                             h->tc_err, h->nsm, h->stream);
+        if (e == cudaSuccess) return ST_OK;
+        if (e != cudaErrorNotSupported) CK(e);
+        cudaGetLastError();
     }
+    KScope ks(h, cls_of<T>(ST_PROF_GEMM64, ST_PROF_GEMM32), sizeof(T) * (2.0 * E + n * n),
+              2.0 * E * n);
+    if (axis == 0) {
+        CK(launch_gemm_strided<T>(1, (int)outer, (int)nx, (int)nx, in, 0, nx, 1, W, 0, nx, 1, out,
+                                  0, nx, 1, h->stream));
+    } else {
+        CK(launch_gemm_strided<T>((int)outer, (int)n, (int)inner, (int)n, W, 0, 1, n, in,
+                                  n * inner, inner, 1, out, n * inner, inner, 1, h->stream));
+    }
+    return ST_OK;
+}
+
+template <typename T>
+int spatial(st_handle h, const T *in, T *t0, T *t1, bool forward, long long planes, T **res) {
+    CKS(axis_pass<T>(h, 0, in, t0, forward, planes));
     *res = t0;
     if (h->dim < 2) return ST_OK;
-    {
-        KScope ks(h, c, sizeof(T) * (2.0 * E + ny * ny), 2.0 * E * ny);
-        CK(launch_gemm_strided<T>((int)(planes * nz), (int)ny, (int)nx, (int)ny, W[1], 0, 1, ny, t0,
-                                  ny * nx, nx, 1, t1, ny * nx, nx, 1, h->stream));
-    }
+    CKS(axis_pass<T>(h, 1, t0, t1, forward, planes));
     *res = t1;
     if (h->dim < 3) return ST_OK;
-    {
-        KScope ks(h, c, sizeof(T) * (2.0 * E + nz * nz), 2.0 * E * nz);
-        CK(launch_gemm_strided<T>((int)planes, (int)nz, (int)(ny * nx), (int)nz, W[2], 0, 1, nz, t1,
-                                  nz * ny * nx, ny * nx, 1, t0, nz * ny * nx, ny * nx, 1, h->stream));
-    }
+    CKS(axis_pass<T>(h, 2, t1, t0, forward, planes));
     *res = t0;
     return ST_OK;
 }
@@ -360,7 +403,7 @@ int smooth_range(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns, 
     T *w0 = w.w0 + s0 * sl, *w1 = w.w1 + s0 * sl;
     CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, true, s0, ns));
     T *fw = nullptr, *bz = nullptr;
-    CKS(spatial<T>(h, w0, w1, w0, ds.U, (long long)ns * h->nt, &fw));
+    CKS(spatial<T>(h, w0, w1, w0, true, (long long)ns * h->nt, &fw));
     const SchurCoefs<T> sc = pack_schur<T>(h, l);
     const double E = (double)ns * h->nt * h->g.nxyz;
     {
@@ -368,7 +411,7 @@ int smooth_range(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns, 
         CK(launch_shift_solve<T>(fw, ds.lam[0], ds.lam[1], ds.lam[2], h->g, sc, ns, h->stream));
     }
     T *other = (fw == w0) ? w1 : w0;
-    CKS(spatial<T>(h, fw, other, fw, ds.Ut, (long long)ns * h->nt, &bz));
+    CKS(spatial<T>(h, fw, other, fw, false, (long long)ns * h->nt, &bz));
     {
         KScope ks(h, ST_PROF_UPDATE, sizeof(T) * (overwrite ? 2.0 : 3.0) * E, E * (2.0 * h->nt + 2.0));
         CK(launch_update<T>(u + s0 * sl, bz, sc, omega, h->g, ns, overwrite, h->stream));
@@ -419,9 +462,19 @@ int vcycle(st_handle h, int l, T *u, const T *f, bool zero_init) {
     return ST_OK;
 }
 
-int vaxpy(st_handle h, int nv, const double *const *xs, const double *coef, double *y) {
-    KScope ks(h, ST_PROF_VECTOR, 8.0 * (nv + 2) * h->len * h->nrhs, 2.0 * nv * h->len * h->nrhs);
-    CK(launch_multiaxpy(nv, xs, coef, h->nrhs, h->len, y, h->stream));
+// y_r = post_r (y_r + sum_v coef[v*R + r] x_v), in chunks of MAXV vectors
+int vaxpy(st_handle h, int nv, const double *const *xs, const double *coef, double *y,
+          const double *post = nullptr) {
+    const int R = h->nrhs;
+    int v0 = 0;
+    do {
+        const int cnt = std::min(MAXV, nv - v0);
+        const bool last = v0 + cnt >= nv;
+        KScope ks(h, ST_PROF_VECTOR, 8.0 * (cnt + 2) * h->len * R, 2.0 * cnt * h->len * R);
+        CK(launch_multiaxpy(cnt, xs + v0, coef + (size_t)v0 * R, R, h->len, y, h->stream,
+                            last ? post : nullptr));
+        v0 += cnt;
+    } while (v0 < nv);
     return ST_OK;
 }
 
@@ -439,9 +492,96 @@ int vconvert(st_handle h, const Tin *x, Tout *y) {
     return ST_OK;
 }
 
+// ---- the same V-cycle in the spatial eigenbasis -------------------------------
+// u, f are eigenbasis coefficients of level l; tmp is a free buffer of at
+// least the level's size.  Identical in exact arithmetic to vcycle() after
+// the transforms (I (x) U^T) on the residual and (I (x) U) on the result.
+template <typename T>
+int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
+    const int spp = h->lv[l].nslab;
+    const long long ns = (long long)spp * h->nrhs;
+    const double E = (double)ns * h->nt * h->g.nxyz;
+    const SpecCoefs<T> c = pack_spec<T>(h, l);
+    const T *const *lam = space<T>(h).lam;
+    const int nt = h->nt;
+    if (l == h->nlev - 1) {
+        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 2.0 * E, E * (5.0 * nt + 4.0));
+        CK(launch_spec_coarse<T>(u, f, lam, h->g, c, spp, h->nrhs, h->stream));
+        return ST_OK;
+    }
+    Work<T> &w = work<T>(h);
+    const T omega = (T)h->opt.omega;
+    T *cur = u, *oth = tmp;
+    bool zero = zero_init;
+    for (int k = 0; k < h->opt.nu1; ++k) {
+        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * (zero ? 2.0 : 3.0) * E, E * (7.0 * nt + 6.0));
+        CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, zero ? 1 : 0, h->stream));
+        std::swap(cur, oth);
+        zero = false;
+    }
+    if (zero) CK(launch_zero<T>(cur, (long long)E, h->stream));
+    const ProlongCoefs<T> pc = pack_prolong<T>(h);
+    const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
+    {
+        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 2.5 * E, E * (4.0 * nt + 2.0));
+        CK(launch_spec_res_restrict<T>(cur, f, w.f[l + 1], lam, h->g, c, pc, spp, nc, h->stream));
+    }
+    CKS(svcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], oth, true));
+    {
+        const double Ec = (double)nc * nt * h->g.nxyz;
+        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 5.0 * Ec, Ec * 4.0 * nt);
+        CK(launch_prolong_add<T>(w.u[l + 1], cur, pc, h->g, nc, h->stream));
+    }
+    for (int k = 0; k < h->opt.nu2; ++k) {
+        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 3.0 * E, E * (7.0 * nt + 6.0));
+        CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, 0, h->stream));
+        std::swap(cur, oth);
+    }
+    if (cur != u)
+        CK(cudaMemcpyAsync(u, cur, sizeof(T) * (size_t)E, cudaMemcpyDeviceToDevice, h->stream));
+    return ST_OK;
+}
+
+// z = (I (x) U) V^( (I (x) U^T) v ), FP64 at the interface
+template <typename T>
+int precondition_spectral(st_handle h, const double *v, double *z);
+
+template <>
+int precondition_spectral<double>(st_handle h, const double *v, double *z) {
+    Work<double> &w = h->w64;
+    DevSpace<double> &ds = h->s64;
+    const long long planes = (long long)h->N * h->nrhs * h->nt;
+    double *fh = nullptr, *e = nullptr;
+    CKS(spatial<double>(h, v, w.w0, w.w1, true, planes, &fh));
+    double *tmp = (fh == w.w0) ? w.w1 : w.w0;
+    CKS(svcycle<double>(h, 0, w.u[0], fh, tmp, true));
+    double *t0 = (h->dim % 2 == 1) ? z : w.w0, *t1 = (h->dim % 2 == 1) ? w.w0 : z;
+    CKS(spatial<double>(h, w.u[0], t0, t1, false, planes, &e));
+    if (e != z) CK(cudaMemcpyAsync(z, e, sizeof(double) * h->len * h->nrhs, cudaMemcpyDeviceToDevice, h->stream));
+    return ST_OK;
+}
+
 // z = V-cycle(v) with zero initial guess, FP64 at the interface
+int precondition_spectral_f32(st_handle h, const double *v, double *z) {
+    Work<float> &w = h->w32;
+    DevSpace<float> &ds = h->s32;
+    const long long planes = (long long)h->N * h->nrhs * h->nt;
+    CKS((vconvert<double, float>(h, v, w.w0)));
+    float *fh = nullptr, *e = nullptr;
+    CKS(spatial<float>(h, w.w0, w.w1, w.f[0], true, planes, &fh));
+    float *tmp = (fh == w.w1) ? w.w0 : w.w1;
+    CKS(svcycle<float>(h, 0, w.u[0], fh, tmp, true));
+    float *t0 = (fh == w.w0) ? w.w1 : w.w0;
+    float *t1 = (fh == w.f[0]) ? ((t0 == w.w0) ? w.w1 : w.w0) : w.f[0];
+    CKS(spatial<float>(h, w.u[0], t0, t1, false, planes, &e));
+    CKS((vconvert<float, double>(h, e, z)));
+    return ST_OK;
+}
+
 int precondition(st_handle h, const double *v, double *z) {
     const long long n0 = h->len * h->nrhs;
+    if (h->opt.basis == ST_BASIS_SPECTRAL)
+        return h->mixed ? precondition_spectral_f32(h, v, z) : precondition_spectral<double>(h, v, z);
     if (!h->mixed) return vcycle<double>(h, 0, z, v, true);
     Work<float> &w = h->w32;
     CKS((vconvert<double, float>(h, v, w.f[0])));
@@ -557,7 +697,7 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
         if (worst <= tol || total >= h->opt.max_it) break;
         std::vector<double> sc(R);
         for (int q = 0; q < R; ++q) sc[q] = beta[q] > 0 ? 1.0 / beta[q] : 0.0;
-        CKS(vscale(h, h->V[0], h->V[0], sc.data()));
+        CKS(vaxpy(h, 0, nullptr, nullptr, h->V[0], sc.data()));
         // per-rhs Hessenberg (column-major (m+1) x m), Givens, rhs g
         std::vector<double> H((size_t)R * (m + 1) * m, 0.0), cs((size_t)R * m), sn((size_t)R * m),
             g((size_t)R * (m + 1), 0.0);
@@ -570,24 +710,47 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
             CKS(precondition(h, h->V[j], h->Zk[j]));
             CKS(stencil<double>(h, 0, h->Zk[j], nullptr, h->V[j + 1], MODE_APPLY, false, 0,
                                 h->N * R));
-            // classical Gram-Schmidt, twice
-            std::vector<double> hsum((size_t)(j + 1) * R, 0.0);
-            for (int pass = 0; pass < 2; ++pass) {
-                CKS(dots(h, j + 1, h->V.data(), h->V[j + 1], hcol));
-                std::vector<double> neg(hcol.size());
-                for (size_t i = 0; i < hcol.size(); ++i) {
-                    neg[i] = -hcol[i];
-                    hsum[i] += hcol[i];
+            // classical Gram-Schmidt: one fused pass gives V^T w and w.w; a
+            // second pass runs only where ||w - V h|| < ||w|| / sqrt(2)
+            // (Kahan's "twice is enough" criterion)
+            std::vector<const double *> vw(h->V.begin(), h->V.begin() + j + 1);
+            vw.push_back(h->V[j + 1]);
+            CKS(dots(h, j + 2, vw.data(), h->V[j + 1], hcol));
+            std::vector<double> hsum((size_t)(j + 1) * R), neg((size_t)(j + 1) * R), rem2(R),
+                post(R);
+            bool reorth = false;
+            for (int q = 0; q < R; ++q) {
+                double hh = 0.0;
+                for (int i = 0; i <= j; ++i) {
+                    const double v = hcol[(size_t)i * R + q];
+                    hsum[(size_t)i * R + q] = v;
+                    neg[(size_t)i * R + q] = -v;
+                    hh += v * v;
                 }
-                for (int v0 = 0; v0 <= j; v0 += MAXV) {
-                    const int cnt = std::min(MAXV, j + 1 - v0);
-                    CKS(vaxpy(h, cnt, h->V.data() + v0, neg.data() + (size_t)v0 * R, h->V[j + 1]));
+                const double ww = hcol[(size_t)(j + 1) * R + q];
+                rem2[q] = ww - hh;
+                if (act[q] && rem2[q] < 0.5 * ww) reorth = true;
+            }
+            if (reorth) {
+                CKS(vaxpy(h, j + 1, h->V.data(), neg.data(), h->V[j + 1]));
+                CKS(dots(h, j + 2, vw.data(), h->V[j + 1], hcol));
+                for (int q = 0; q < R; ++q) {
+                    double hh = 0.0;
+                    for (int i = 0; i <= j; ++i) {
+                        const double v = hcol[(size_t)i * R + q];
+                        hsum[(size_t)i * R + q] += v;
+                        neg[(size_t)i * R + q] = -v;
+                        hh += v * v;
+                    }
+                    rem2[q] = hcol[(size_t)(j + 1) * R + q] - hh;
                 }
             }
-            std::vector<double> hn;
-            CKS(norms(h, h->V[j + 1], hn));
-            for (int q = 0; q < R; ++q) sc[q] = hn[q] > 0 ? 1.0 / hn[q] : 0.0;
-            CKS(vscale(h, h->V[j + 1], h->V[j + 1], sc.data()));
+            std::vector<double> hn(R);
+            for (int q = 0; q < R; ++q) {
+                hn[q] = std::sqrt(std::max(rem2[q], 0.0));
+                post[q] = hn[q] > 0 ? 1.0 / hn[q] : 0.0;
+            }
+            CKS(vaxpy(h, j + 1, h->V.data(), neg.data(), h->V[j + 1], post.data()));
             ++total;
             bool all = true;
             for (int q = 0; q < R; ++q) {
@@ -631,10 +794,7 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
             }
             for (int i = 0; i < k; ++i) coef[(size_t)i * R + q] = y[i];
         }
-        for (int v0 = 0; v0 < kmax; v0 += MAXV) {
-            const int cnt = std::min(MAXV, kmax - v0);
-            CKS(vaxpy(h, cnt, h->Zk.data() + v0, coef.data() + (size_t)v0 * R, u));
-        }
+        if (kmax > 0) CKS(vaxpy(h, kmax, h->Zk.data(), coef.data(), u));
     }
     info->iterations = total;
     info->rel_residual = worst;
@@ -660,6 +820,8 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         return fail(ST_ERR_INVALID_ARG, "bad nu1/nu2/gmres_restart/max_it/nrhs");
     if (o.precision < ST_FP64 || o.precision > ST_MIXED_BF16)
         return fail(ST_ERR_INVALID_ARG, "bad precision");
+    if (o.basis != ST_BASIS_NODAL && o.basis != ST_BASIS_SPECTRAL)
+        return fail(ST_ERR_INVALID_ARG, "bad basis");
     h->dim = geometry;
     h->p = degree;
     h->N = slabs;
@@ -767,6 +929,16 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         cudaGetLastError();
         return fail(ST_ERR_CUDA, "no CUDA device");
     }
+    {
+        int dev = 0, nsm = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        h->nsm = nsm > 0 ? nsm : 1;
+        void *pe;
+        CKS(dalloc(h, sizeof(int), &pe));
+        h->tc_err = (int *)pe;
+        CK(cudaMemset(h->tc_err, 0, sizeof(int)));
+    }
     CKS(upload_space<double>(h, h->s64, bandM, bandK));
     if (h->mixed) CKS(upload_space<float>(h, h->s32, bandM, bandK));
     if (h->mixed) {
@@ -776,7 +948,7 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         CKS(dalloc(h, (size_t)h->len * h->nrhs * sizeof(double), &p));
         h->w64.w0 = (double *)p;
     } else {
-        CKS(alloc_work<double>(h, h->w64, false));
+        CKS(alloc_work<double>(h, h->w64, true));
     }
     h->nblk_dot = 304;
     void *p;
@@ -847,6 +1019,7 @@ void st_options_default(st_options *o) {
     o->max_it = 200;
     o->nrhs = 1;
     o->hbm_budget = 0;
+    o->basis = ST_BASIS_NODAL;
 }
 
 const char *st_last_error(void) { return g_err.c_str(); }
@@ -949,6 +1122,17 @@ int st_smooth(st_handle h, double *u, const double *f, int nsteps) {
 int st_vcycle(st_handle h, double *u, const double *f) {
     CKS(check_ptr(h, u, "u"));
     CKS(check_ptr(h, f, "f"));
+    if (h->opt.basis == ST_BASIS_SPECTRAL) {
+        // the V-cycle is the affine iteration u + B (f - L u)
+        CKS(ensure_krylov(h));
+        CKS(residual64(h, u, f, h->V[0]));
+        CKS(precondition(h, h->V[0], h->Zk[0]));
+        const double one[1] = {1.0};
+        std::vector<double> c(h->nrhs, 1.0);
+        const double *xs[1] = {h->Zk[0]};
+        (void)one;
+        return vaxpy(h, 1, xs, c.data(), u);
+    }
     if (!h->mixed) return vcycle<double>(h, 0, u, f, false);
     const long long n0 = h->len * h->nrhs;
     CK(launch_convert<double, float>(u, h->w32.u[0], n0, h->stream));
@@ -973,6 +1157,12 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
         if (h->opt.outer == ST_OUTER_MG) CKS(solve_mg(h, rhs, tol, u, info));
         else CKS(solve_fgmres(h, rhs, tol, u, info));
         CK(cudaStreamSynchronize(h->stream));
+        int tc_err = 0;
+        CK(cudaMemcpy(&tc_err, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (tc_err) {
+            CK(cudaMemset(h->tc_err, 0, sizeof(int)));
+            return fail(ST_ERR_TIMEOUT, "a tensor-core transform's bounded wait ran out");
+        }
     } catch (...) {
         return fail(ST_ERR_OOM, "host exception during solve");
     }

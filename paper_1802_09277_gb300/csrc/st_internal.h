@@ -22,8 +22,8 @@ struct Grid {
 // Stencil output modes of the residual kernel
 enum StencilMode { MODE_RES = 0, MODE_APPLY = 1, MODE_MASS = 2 };
 
-// Per-launch time coefficients (row-major nt x nt), converted on the host to
-// the kernel's scalar type.
+// Per-launch time coefficients, row-major with row stride NTMAX, converted on
+// the host to the kernel's scalar type.
 template <typename T>
 struct TimeCoefs {
     T CK[NTMAX * NTMAX];  // multiplies M_x u_j (K_t; M_t in MODE_MASS)
@@ -40,6 +40,18 @@ struct SchurCoefs {
     T Z[NTMAX * NTMAX];
     T X[NTMAX * NTMAX];
     int blk[NTMAX];  // blk[i] = 1: row i is the second row of a 2x2 block
+    int nt;
+};
+
+// Time factors of one level for the eigenbasis (spectral) V-cycle
+template <typename T>
+struct SpecCoefs {
+    T Kt[NTMAX * NTMAX];
+    T Mt[NTMAX * NTMAX];
+    T Y[NTMAX * NTMAX];
+    T Z[NTMAX * NTMAX];
+    T X[NTMAX * NTMAX];
+    int blk[NTMAX];
     int nt;
 };
 
@@ -86,6 +98,29 @@ template <typename T>
 cudaError_t launch_prolong_add(const T *ec, T *uf, const ProlongCoefs<T> &pc, const Grid &g,
                                long long ncoarse, cudaStream_t s);
 
+// ---- tensor-core transforms (kernels_tc.cu) ----
+// kind: 2 = TF32, 1 = BF16; mode 0: contracted axis contiguous, 1: strided by
+// `inner`.  wt = W^T row-major (n_out x n_in).  cudaErrorNotSupported when the
+// shape is not covered.
+cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, const float *wt,
+                           int n_in, int n_out, long long ncols, long long inner, int *err,
+                           int nsm, cudaStream_t s);
+
+// ---- eigenbasis V-cycle kernels (kernels_spectral.cu) ----
+template <typename T>
+cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *const lam[3],
+                               const Grid &g, const SpecCoefs<T> &c, T omega, int slabs_per_prob,
+                               long long nslabs, int uin_zero, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *const lam[3],
+                                     const Grid &g, const SpecCoefs<T> &c,
+                                     const ProlongCoefs<T> &pc, int slabs_per_prob,
+                                     long long ncoarse, cudaStream_t s);
+template <typename T>
+cudaError_t launch_spec_coarse(T *u, const T *f, const T *const lam[3], const Grid &g,
+                               const SpecCoefs<T> &c, int slabs_per_prob, int nprob,
+                               cudaStream_t s);
+
 // ---- vector kernels (kernels_vector.cu) ----
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin *x, Tout *y, long long n, cudaStream_t s);
@@ -95,9 +130,10 @@ cudaError_t launch_multidot(int nv, const double *const *vecs, const double *w, 
                             long long len, double *partial, int nblk, double *out,
                             cudaStream_t s);
 
-// y_r += sum_v coef[v][r] x_v  (per rhs r)
+// y_r = post_r * (y_r + sum_v coef[v][r] x_v)  (per rhs r; post NULL = 1)
 cudaError_t launch_multiaxpy(int nv, const double *const *xs, const double *coef, int nrhs,
-                             long long len, double *y, cudaStream_t s);
+                             long long len, double *y, cudaStream_t s,
+                             const double *post = nullptr);
 
 // y = a_r * x (per rhs), y may alias x
 cudaError_t launch_scale(const double *x, double *y, const double *a, int nrhs, long long len,

@@ -1,0 +1,61 @@
+"""Run one library operation on a chosen problem, e.g. under ncu:
+
+  python paper_1802_09277_gb300/profile_case.py --dim 2 --spans 128 128 \
+      --degree 3 --slabs 512 --precision mixed_fp32 --op smooth --reps 2
+
+Operations: apply (FP64 operator), smooth (one damped block-Jacobi step in
+the handle's precision), vcycle, solve (to --tol).  Inputs are seeded
+synthetic vectors; the script prints the mean CUDA-event time per call.
+"""
+import argparse
+import os
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(HERE))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dim", type=int, default=2)
+    ap.add_argument("--spans", type=int, nargs="+", default=[128, 128])
+    ap.add_argument("--degree", type=int, default=3)
+    ap.add_argument("--slabs", type=int, default=512)
+    ap.add_argument("--ne", type=int, default=2)
+    ap.add_argument("--precision", default="mixed_fp32")
+    ap.add_argument("--op", default="smooth", choices=["apply", "smooth", "vcycle", "solve"])
+    ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    args = ap.parse_args()
+
+    import torch
+    from paper_1802_09277_gb300 import inputs, st
+
+    s = st.Solver(args.dim, args.degree, args.spans, args.slabs, ne_per_slab=args.ne,
+                  precision=args.precision)
+    n = s.ndofs
+    x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
+    f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times = []
+    for _ in range(args.reps):
+        ev[0].record()
+        if args.op == "apply":
+            s.apply(x, y)
+        elif args.op == "smooth":
+            s.smooth(x, f, 1)
+        elif args.op == "vcycle":
+            s.vcycle(x, f)
+        else:
+            s.solve(f, y, tol=args.tol)
+        ev[1].record()
+        ev[1].synchronize()
+        times.append(ev[0].elapsed_time(ev[1]))
+    print("op=%s dofs=%d precision=%s mean_ms=%.4f" % (args.op, n, args.precision,
+                                                      sum(times) / len(times)))
+    s.close()
+
+
+if __name__ == "__main__":
+    main()

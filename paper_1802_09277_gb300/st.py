@@ -18,6 +18,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NOT_POSITIVE", -4: "ILL_CONDITIONED
 GEOMETRY = {1: 1, 2: 2, 3: 3}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
 OUTER = {"fgmres": 0, "mg": 1}
+BASIS = {"nodal": 0, "spectral": 1}
 
 # every symbol declared in include/st_iga.h
 SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",
@@ -34,7 +35,7 @@ class StOptions(ctypes.Structure):
                 ("ne_per_slab", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("precision", ctypes.c_int), ("outer", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("max_it", ctypes.c_int),
-                ("nrhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t)]
+                ("nrhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("basis", ctypes.c_int)]
 
 
 class StSolveInfo(ctypes.Structure):
@@ -109,6 +110,8 @@ def options(**kw):
             v = PRECISION[v]
         if k == "outer" and isinstance(v, str):
             v = OUTER[v]
+        if k == "basis" and isinstance(v, str):
+            v = BASIS[v]
         setattr(o, k, v)
     return o
 

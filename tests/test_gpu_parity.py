@@ -91,13 +91,15 @@ def test_smooth_step_parity(st, d, spans, p, N, ne):
     s.close()
 
 
+@pytest.mark.parametrize("basis", ["nodal", "spectral"])
 @pytest.mark.parametrize("d,spans,p,N,ne", [c for c in CASES if c[3] > 1])
-def test_vcycle_parity(st, d, spans, p, N, ne):
+def test_vcycle_parity(st, basis, d, spans, p, N, ne):
     """One V-cycle (time coarsening, Galerkin coarse operators in the oracle,
-    frozen-delta rediscretisation on the GPU) from a nonzero start."""
+    frozen-delta rediscretisation on the GPU) from a nonzero start, in the
+    B-spline basis and in the spatial eigenbasis."""
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     H = S.Hierarchy(pr)
-    s = st.Solver(d, p, spans, N, ne_per_slab=ne)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, basis=basis)
     u0 = inputs.uniform_vector(5, pr.ndofs)
     f = inputs.uniform_vector(6, pr.ndofs)
     ref = S.vcycle(H, f, u=u0.copy())
@@ -111,14 +113,15 @@ def test_vcycle_parity(st, d, spans, p, N, ne):
     s.close()
 
 
+@pytest.mark.parametrize("basis", ["nodal", "spectral"])
 @pytest.mark.parametrize("outer", ["fgmres", "mg"])
 @pytest.mark.parametrize("d,spans,p,N,ne", CASES[:6])
-def test_solve_fp64_parity(st, outer, d, spans, p, N, ne):
+def test_solve_fp64_parity(st, basis, outer, d, spans, p, N, ne):
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     c = inputs.normal_coeffs(7, pr.ndofs)
     fr = A.load_from_coeffs(pr, c)
     ud = S.direct(A.assemble_L(pr), fr)
-    s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer, basis=basis)
     f = torch.empty(pr.ndofs, dtype=torch.float64, device="cuda")
     s.load_coeffs(dev(c), f)
     u = torch.zeros_like(f)
@@ -129,15 +132,17 @@ def test_solve_fp64_parity(st, outer, d, spans, p, N, ne):
     s.close()
 
 
+@pytest.mark.parametrize("basis", ["nodal", "spectral"])
 @pytest.mark.parametrize("outer", ["fgmres", "mg"])
 @pytest.mark.parametrize("d,spans,p,N,ne", CASES[:6])
-def test_solve_mixed_parity(st, outer, d, spans, p, N, ne):
+def test_solve_mixed_parity(st, basis, outer, d, spans, p, N, ne):
     """FP32 V-cycle, FP64 outer residual and update: 1e-8 vs the oracle."""
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     c = inputs.normal_coeffs(8, pr.ndofs)
     fr = A.load_from_coeffs(pr, c)
     ud = S.direct(A.assemble_L(pr), fr)
-    s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer, precision="mixed_fp32")
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer, precision="mixed_fp32",
+                  basis=basis)
     f = dev(fr)
     u = torch.zeros_like(f)
     info = s.solve(f, u, tol=1e-10)
@@ -171,13 +176,14 @@ def test_single_slab_exact_in_one_cycle(st):
     assert relerr(host(u), ud) <= 1e-12
 
 
-def test_multi_rhs_equals_single(st):
+@pytest.mark.parametrize("basis", ["nodal", "spectral"])
+def test_multi_rhs_equals_single(st, basis):
     """nrhs independent problems solved together give each single solution."""
     d, spans, p, N = 2, (12, 10), 2, 8
     pr = A.Problem(d, spans, p, 2, N, theta=1.0)
     R = 3
     fs = [inputs.normal_coeffs(20 + r, pr.ndofs) for r in range(R)]
-    sb = st.Solver(d, p, spans, N, nrhs=R)
+    sb = st.Solver(d, p, spans, N, nrhs=R, basis=basis)
     assert sb.ndofs == R * pr.ndofs
     u = torch.zeros(R * pr.ndofs, dtype=torch.float64, device="cuda")
     sb.solve(dev(np.concatenate(fs)), u, tol=1e-12)
@@ -255,3 +261,43 @@ def test_full_size_2d_sampled(st):
         res2 += float(r @ r)
     rel = np.sqrt(res2) / np.linalg.norm(F)
     assert rel <= 1.01e-8, (rel, info)
+
+
+TC_CASES = [(1, (16,), 2, 8, 4), (2, (37, 29), 2, 6, 2), (2, (20, 20), 1, 4, 5),
+            (3, (19, 11, 9), 2, 2, 2), (2, (64, 64), 2, 4, 2)]
+
+
+@pytest.mark.parametrize("prec,tol", [("mixed_tf32", 1e-2), ("mixed_bf16", 6e-2)])
+@pytest.mark.parametrize("d,spans,p,N,ne", TC_CASES)
+def test_vcycle_tensor_core_transforms(st, prec, tol, d, spans, p, N, ne):
+    """One V-cycle with the spatial transforms on the tensor cores (operands
+    rounded to TF32: 10-bit, BF16: 7-bit mantissa; FP32 accumulation) stays
+    within a rounding-level distance of the oracle's FP64 V-cycle."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    H = S.Hierarchy(pr)
+    f = inputs.uniform_vector(60, pr.ndofs)
+    ref = S.vcycle(H, f)
+    for basis in ("spectral", "nodal"):
+        s = st.Solver(d, p, spans, N, ne_per_slab=ne, precision=prec, basis=basis)
+        u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+        s.vcycle(u, dev(f))
+        assert relerr(host(u), ref) <= tol, (basis, relerr(host(u), ref))
+        s.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed_tf32", "mixed_bf16"])
+@pytest.mark.parametrize("d,spans,p,N,ne", TC_CASES)
+def test_solve_tensor_core_parity(st, prec, d, spans, p, N, ne):
+    """FGMRES with the tensor-core V-cycle reaches the oracle's solution to
+    1e-8: the FP64 outer residual recovers the accuracy of the TF32 / BF16
+    transforms."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    c = inputs.normal_coeffs(61, pr.ndofs)
+    fr = A.load_from_coeffs(pr, c)
+    ud = S.direct(A.assemble_L(pr), fr)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, precision=prec, basis="spectral")
+    u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+    info = s.solve(dev(fr), u, tol=1e-10)
+    err = np.linalg.norm(host(u) - ud) / np.linalg.norm(ud)
+    assert err <= 1e-8, (err, info)
+    s.close()
