@@ -36,6 +36,22 @@ UNIT = "DoFs/s"
 L2_FLUSH_BYTES = 256 << 20
 
 
+def reduce_max(value, device="cpu"):
+    """Max over the ranks of the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(dofs_per_rank, world, ms_max):
+    """Whole-job throughput: every rank's dofs over the slowest rank's time."""
+    return dofs_per_rank * world / (ms_max / 1e3)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -156,12 +172,12 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
-    common = dict(ne_per_slab=ne, outer="fgmres", gmres_restart=20, max_it=300)
+    common = dict(ne_per_slab=ne, gmres_restart=20, max_it=300)
     peaks, peak_src = load_peaks()
 
-    def make(prec, basis):
+    def make(prec, basis, outer):
         return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
-                         **common)
+                         outer=outer, **common)
 
     # rank r solves its own right-hand side (independent replicas)
     c = torch.tensor(inputs.normal_coeffs(seed + 1000 * rank, 0 + make_len(d, spans, p, N, ne)),
@@ -200,19 +216,19 @@ def gpu_arm(args, rank, world):
         return times, infos, u, prof
 
     # --- mixed precision (headline) ---
-    sm = make(args.precision, args.basis)
+    sm = make(args.precision, args.basis, args.outer)
     f = torch.empty_like(c)
     sm.load_coeffs(c, f)
     clocks = ClockSampler(dev.index)
     clocks.start()
-    t_mixed, i_mixed, u_mixed, prof = timed_solves(sm, f, args.steps, args.warmup, profile=True)
+    t_mixed, i_mixed, u_mixed, _ = timed_solves(sm, f, args.steps, args.warmup)
     clk = clocks.stop()
     ms = sum(t_mixed) / len(t_mixed)
-    ms_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(tt.item())
+    # the same steps again with per-launch CUDA events (library profiling
+    # hook) for the per-kernel roofline; kept out of the headline timing
+    t_prof, _, _, prof = timed_solves(sm, f, args.steps, 0, profile=True)
+    ms_prof = sum(t_prof) / len(t_prof)
+    ms_max = reduce_max(ms, dev)
 
     # --- end to end through the public API with host buffers ---
     f_host = f.cpu().pin_memory()
@@ -235,19 +251,23 @@ def gpu_arm(args, rank, world):
     e2e_ms = sum(e2e_t) / len(e2e_t)
 
     # --- the other variants on the same workload (fewer steps, no profiling) ---
-    other = "nodal" if args.basis == "spectral" else "spectral"
     variants = {}
     u64 = None
-    for name, prec, basis in (("fp64_plain", "fp64", "nodal"), ("fp64_" + "spectral", "fp64", "spectral"),
-                              ("mixed_" + other, args.precision, other)):
-        if name in variants:
+    for prec, basis, outer in (("fp64", "nodal", "fgmres"), ("fp64", "spectral", "fgmres"),
+                               ("mixed_fp32", "nodal", "fgmres"), ("mixed_fp32", "spectral", "fgmres"),
+                               ("mixed_fp32", "spectral", "ir"), ("mixed_tf32", "spectral", "ir"),
+                               ("mixed_bf16", "spectral", "ir"), ("mixed_tf32", "spectral", "fgmres")):
+        name = "fp64_plain" if (prec, basis) == ("fp64", "nodal") else "%s_%s_%s" % (prec, basis, outer)
+        if (prec, basis, outer) == (args.precision, args.basis, args.outer) and name != "fp64_plain":
             continue
-        sv = make(prec, basis)
+        sv = make(prec, basis, outer)
         tv, iv, uv, _ = timed_solves(sv, f, max(1, args.steps // 2), 1)
         msv = sum(tv) / len(tv)
-        variants[name] = {"precision": prec, "basis": basis, "ms_per_step": msv,
+        variants[name] = {"precision": prec, "basis": basis, "outer": outer, "ms_per_step": msv,
                           "value": sv.ndofs * world / (msv / 1e3),
-                          "iterations": iv[-1]["iterations"], "rel_residual": iv[-1]["rel_residual"]}
+                          "iterations": iv[-1]["iterations"],
+                          "refinements": iv[-1].get("refinements", 0),
+                          "rel_residual": iv[-1]["rel_residual"]}
         if name == "fp64_plain":
             u64 = uv.clone()
         sv.close()
@@ -263,8 +283,9 @@ def gpu_arm(args, rank, world):
     launches = sum(v["launches"] for v in prof.values())
     ndofs = sm.ndofs
     result = {
-        "ndofs": ndofs, "ms_mixed": ms, "ms_mixed_max": ms_max, "ms64": ms64,
+        "ndofs": ndofs, "ms_mixed": ms, "ms_mixed_max": ms_max, "ms64": ms64, "ms_prof": ms_prof,
         "iters_mixed": i_mixed[-1]["iterations"], "res_mixed": i_mixed[-1]["rel_residual"],
+        "refin_mixed": i_mixed[-1].get("refinements", 0),
         "iters64": i64[-1]["iterations"], "res64": i64[-1]["rel_residual"],
         "rel_diff_mixed_vs_fp64": rel_diff, "e2e_ms": e2e_ms, "bytes_h2d": f.numel() * 8,
         "bytes_d2h": f.numel() * 8, "prof": prof, "dominant": dom,
@@ -276,6 +297,56 @@ def gpu_arm(args, rank, world):
     return result
 
 
+def serve_arm(args):
+    """Serving workload: Poisson arrivals of solve requests of mixed
+    configurations through st_serve (continuous batching)."""
+    import threading
+    import numpy as np
+    from paper_1802_09277_gb300 import inputs, st
+    nreq, rate, seed = args.serve_requests, args.serve_rate, 5
+    arrivals = inputs.poisson_arrivals(seed, nreq, rate)
+    mix = inputs.serving_mix(seed, nreq)
+    ne = 2
+    reqs = []
+    for i, (sp, p, N) in enumerate(mix):
+        n = (sp + p - 2) ** 2 * N * (ne + p)
+        reqs.append((sp, p, N, inputs.normal_coeffs(10000 + i, n)))
+    srv = st.Server(workers=args.serve_workers, max_batch=8, precision=args.precision,
+                    basis="spectral", outer="ir", ne_per_slab=ne, gmres_restart=20, max_it=300)
+    tickets = [None] * nreq
+    t0 = time.perf_counter()
+
+    def submitter():
+        for i, (sp, p, N, c) in enumerate(reqs):
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(2, p, (sp, sp), N, c, tol=1e-8, coeffs=True)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, dofs, worst, batches, bad = [], 0, 0.0, [], 0
+    for i in range(nreq):
+        while tickets[i] is None:
+            time.sleep(1e-4)
+        res, u = srv.wait(tickets[i], timeout=600.0)
+        if res["status"] != 0:
+            bad += 1
+        lat.append(res["latency_seconds"])
+        dofs += res["n_dofs"]
+        worst = max(worst, res["rel_residual"])
+        batches.append(res["batch_size"])
+    makespan = time.perf_counter() - t0
+    th.join()
+    srv.stop()
+    lat = np.sort(np.array(lat))
+    return {"requests": nreq, "arrival_rate_per_s": rate, "workers": args.serve_workers,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "throughput_dofs_per_s": dofs / makespan, "makespan_s": makespan, "total_dofs": int(dofs),
+            "max_rel_residual": worst, "failed": bad, "mean_batch": float(np.mean(batches)),
+            "precision": args.precision, "tol": 1e-8}
+
+
 def make_len(d, spans, p, N, ne):
     nx = 1
     for s in spans:
@@ -284,24 +355,33 @@ def make_len(d, spans, p, N, ne):
 
 
 def roofline_entry(r):
+    """Roofline of the kernel class with the largest share of device time:
+    achieved = algorithmic bytes (or flops) of its launches / their summed
+    CUDA-event time."""
     peaks = r["peaks"]
     dom = r["dominant"]
     pd = r["prof"][dom]
     secs = pd["ms"] / 1e3
     clk_max = peaks.get("sm_max_mhz", 2070.0) * 1e6
-    if dom in ("gemm32", "gemm64"):
-        # FP32 FMA on CUDA cores: 152 SMs x 128 lanes x 2 flop x max clock
+    base = {"kernel": dom, "per_launch_ms": pd["ms"] / max(1, pd["launches"]),
+            "launches": pd["launches"], "traffic": None}
+    if dom == "gemm32":  # FP32 FMA on CUDA cores: 152 SMs x 128 lanes x 2 flop x max clock
         peak = 152 * 128 * 2 * clk_max / 1e12
-        achieved = pd["flops"] / secs / 1e12
-        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_note": "FP32 CUDA-core FMA rate from unit counts x max SM clock",
-                "per_launch_ms": r["per_launch_ms"], "launches": pd["launches"]}
-    achieved = pd["bytes"] / secs / 1e9
+        ach = pd["flops"] / secs / 1e12
+        base.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    peak_note="FP32 CUDA-core FMA rate: unit counts x max SM clock")
+        return base
+    if dom in ("stencil64", "gemm64"):  # FP64 pipe: GB300's 1.25 TFLOP/s dense FP64
+        peak = 1.25
+        ach = pd["flops"] / secs / 1e12
+        base.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    peak_note="GB300 FP64 rate 1.25 TFLOP/s (probe: 1.26)")
+        return base
+    ach = pd["bytes"] / secs / 1e9
     peak = peaks["hbm_gbs"]
-    return {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_note": "%s hbm_gbs" % r["peak_src"],
-            "per_launch_ms": r["per_launch_ms"], "launches": pd["launches"]}
+    base.update(bound="hbm", achieved=ach, peak=peak, unit="GB/s", frac=ach / peak,
+                peak_note="%s hbm_gbs" % r["peak_src"])
+    return base
 
 
 def main():
@@ -315,8 +395,13 @@ def main():
     ap.add_argument("--sample-slabs", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=512)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--basis", default="spectral", choices=["spectral", "nodal"])
-    ap.add_argument("--precision", default="mixed_fp32",
+    ap.add_argument("--outer", default="ir", choices=["ir", "fgmres", "mg"])
+    ap.add_argument("--precision", default="mixed_tf32",
                     choices=["mixed_fp32", "mixed_tf32", "mixed_bf16", "fp64"])
     args = ap.parse_args()
 
@@ -329,8 +414,8 @@ def main():
     d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
     cfg = {"workload": args.workload, "domain": "unit %s" % {1: "interval", 2: "square", 3: "cube"}[d],
            "spans": list(spans), "degree": p, "slabs": N, "time_elements_per_slab": ne,
-           "theta": 1.0, "tol": tol, "solver": "FGMRES(20) + 1 V-cycle, omega=0.5, nu=1/1",
-           "precision": args.precision, "vcycle_basis": args.basis,
+           "theta": 1.0, "tol": tol, "solver": "V(1,1) time multigrid, omega=0.5, FGMRES(20) restart",
+           "precision": args.precision, "vcycle_basis": args.basis, "outer": args.outer,
            "rhs": "N(0,1) B-spline coefficients, seed %d" % seed, "l2": "flushed between steps"}
 
     if args.impl == "reference":
@@ -362,7 +447,13 @@ def main():
             torch.distributed.destroy_process_group()
         return
     ndofs = r["ndofs"]
-    value = ndofs * world / (r["ms_mixed_max"] / 1e3)
+    value = job_value(ndofs, world, r["ms_mixed_max"])
+    serve = None
+    if not args.no_serve and world == 1:
+        try:
+            serve = serve_arm(args)
+        except Exception as e:
+            serve = {"error": str(e)[:300]}
     cpu = None
     if not args.no_cpu and world == 1:
         try:
@@ -380,17 +471,20 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": cfg,
-        "iterations": r["iters_mixed"], "rel_residual": r["res_mixed"],
+        "iterations": r["iters_mixed"], "refinements": r["refin_mixed"],
+        "rel_residual": r["res_mixed"],
         "fp64_plain": {"value": ndofs * world / (r["ms64"] / 1e3), "ms_per_step": r["ms64"],
                        "iterations": r["iters64"], "rel_residual": r["res64"], "dtype": "f64",
                        "basis": "nodal"},
         "variants": r["variants"],
         "mixed_vs_fp64_solution_rel_diff": r["rel_diff_mixed_vs_fp64"],
         "roofline": roofline_entry(r),
+        "profiled_ms_per_step": r["ms_prof"],
         "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                                "share": v["ms"] / max(1e-12, sum(x["ms"] for x in r["prof"].values()))}
                            for k, v in r["prof"].items() if v["launches"]},
         "cpu_baseline": cpu,
+        "serve": serve,
         "e2e": {"value": ndofs * world / (r["e2e_ms"] / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": r["bytes_h2d"], "d2h_bytes_per_step": r["bytes_d2h"]},
         "gpu_launches": r["launches"],

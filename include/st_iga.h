@@ -78,6 +78,10 @@ extern "C" {
 /* outer iteration */
 #define ST_OUTER_FGMRES 0 /* FGMRES(restart), right-preconditioned by one V-cycle */
 #define ST_OUTER_MG     1 /* multigrid iteration u <- u + V(f - L u)             */
+#define ST_OUTER_IR     2 /* mixed modes: iterative refinement, FP64 residual and
+                             update around FGMRES on FP32 vectors (FP32 operator,
+                             FP32 V-cycle) solved to inner_tol; FP64 handles
+                             fall back to ST_OUTER_FGMRES                       */
 
 typedef struct st_handle_s *st_handle;
 
@@ -94,10 +98,12 @@ typedef struct {
     int nrhs;             /* independent right-hand sides solved together (1)    */
     size_t hbm_budget;    /* bytes the handle may allocate; 0 = unlimited        */
     int basis;            /* ST_BASIS_NODAL (default) / ST_BASIS_SPECTRAL         */
+    double inner_tol;     /* ST_OUTER_IR: inner relative tolerance (default 1e-4) */
 } st_options;
 
 typedef struct {
-    int iterations;       /* outer iterations (V-cycles) taken                   */
+    int iterations;       /* Krylov / multigrid iterations (V-cycles) taken      */
+    int refinements;      /* ST_OUTER_IR: FP64 refinement steps (else 0)          */
     int status;           /* ST_OK or ST_ERR_NO_CONVERGENCE                      */
     double rel_residual;  /* max over rhs of ||f - L u||_2 / ||f||_2 (FP64)       */
     double seconds;       /* wall time of the solve, host clock                 */
@@ -210,17 +216,82 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u,
  * st_profile_read returns launches, summed device milliseconds, bytes and
  * flops of one class; it synchronises the stream. */
 #define ST_PROF_STENCIL64 0  /* residual / operator / load vector, FP64      */
-#define ST_PROF_STENCIL32 1  /* residual + fused forward time transform, FP32 */
-#define ST_PROF_GEMM64    2  /* spatial transform (one axis), FP64           */
-#define ST_PROF_GEMM32    3  /* spatial transform (one axis), FP32           */
+#define ST_PROF_STENCIL32 1  /* residual (+ fused forward time transform), FP32 */
+#define ST_PROF_GEMM64    2  /* spatial transform (one axis), FP64, CUDA cores */
+#define ST_PROF_GEMM32    3  /* spatial transform (one axis), FP32, CUDA cores */
 #define ST_PROF_SHIFT     4  /* quasi-triangular shift solve per mode        */
 #define ST_PROF_UPDATE    5  /* backward time transform + damped update      */
 #define ST_PROF_TRANSFER  6  /* time restriction / prolongation             */
-#define ST_PROF_VECTOR    7  /* FGMRES vector kernels, precision conversion  */
-#define ST_PROF_NCLASS    8
+#define ST_PROF_VECTOR    7  /* Krylov updates, scaling, precision conversion */
+#define ST_PROF_DOT       8  /* Krylov dot products (deterministic reduction) */
+#define ST_PROF_TC        9  /* spatial transform (one axis), tensor cores    */
+#define ST_PROF_SPEC     10  /* eigenbasis smoothing step / coarse solve      */
+#define ST_PROF_NCLASS   11
 int st_profile(st_handle h, int enable);
 int st_profile_read(st_handle h, int cls, int64_t *launches, double *ms,
                     double *bytes, double *flops);
+
+/* ------------------------------------------------------------------------
+ * Serving: continuous batching of many solves (no counterpart in the paper,
+ * which solves one problem at a time).  A server owns W worker threads, each
+ * with its own CUDA stream, so solves of different requests overlap on the
+ * GPU.  A free worker takes the oldest pending request together with up to
+ * max_batch - 1 further pending requests of the same configuration
+ * (geometry, degree, spans, slabs, tolerance) and solves them as one
+ * multi-right-hand-side problem (opt.nrhs = batch size; every right-hand
+ * side is refined independently, so its result does not depend on the
+ * batch).  Setups (factors + work space, st_setup) are cached per
+ * configuration and batch size and evicted least-recently-used.  A batch is
+ * admitted only when its setup and vectors fit the HBM budget; otherwise it
+ * waits for running solves to release memory (or fails with
+ * ST_ERR_OVER_BUDGET if it cannot fit even on an idle server).
+ * ------------------------------------------------------------------------ */
+typedef struct st_server_s *st_server;
+
+typedef struct {
+    size_t hbm_budget;    /* device bytes the server may hold; 0 = 90% of the free memory */
+    int workers;          /* concurrent solves (default 4)                          */
+    int max_batch;        /* right-hand sides per batched solve, 1..32 (default 8)  */
+    st_options opt;       /* solver options for every request (nrhs is set per batch) */
+} st_server_opts;
+
+typedef struct {
+    int geometry, degree; /* as st_setup                                          */
+    int spans[3];         /* first `geometry` entries used                        */
+    int slabs;
+    const double *rhs;    /* HOST pointer, n_dofs doubles; copied by st_serve_submit */
+    int rhs_is_coeffs;    /* 1: rhs holds B-spline coefficients c and the load
+                             vector (M_t (x) M_x) c is formed on the device      */
+    double tol;           /* relative residual tolerance                          */
+} st_request;
+
+#define ST_ERR_NOT_READY -10  /* st_serve_poll: the request is still pending */
+
+typedef struct {
+    int status;           /* ST_OK or the solve's error code                      */
+    int iterations, refinements;
+    double rel_residual;
+    double queue_seconds; /* submit -> admitted                                   */
+    double solve_seconds; /* admitted -> solution on the host                     */
+    double latency_seconds; /* submit -> solution on the host                     */
+    int batch_size;       /* requests solved together with this one (incl. itself) */
+    int64_t n_dofs;
+} st_result;
+
+void st_serve_opts_default(st_server_opts *o);
+/* Start the worker threads.  Errors: INVALID_ARG, CUDA. */
+int st_serve_start(st_server *out, const st_server_opts *o);
+/* Queue a request (its rhs is copied before returning); *ticket identifies it.
+ * Errors: INVALID_ARG (bad sizes), UNSUPPORTED. */
+int st_serve_submit(st_server s, const st_request *req, uint64_t *ticket);
+/* Non-blocking: ST_ERR_NOT_READY while pending; otherwise fills *res, copies
+ * the solution (n_dofs doubles) into u_host if it is not NULL, releases the
+ * request and returns ST_OK (the request's own status is res->status). */
+int st_serve_poll(st_server s, uint64_t ticket, st_result *res, double *u_host);
+/* As st_serve_poll but blocks up to timeout_s seconds (< 0: no limit). */
+int st_serve_wait(st_server s, uint64_t ticket, double timeout_s, st_result *res, double *u_host);
+/* Finish queued work, stop the workers, free every device and host resource. */
+int st_serve_stop(st_server s);
 
 /* Host copies of the FP64 setup factors, for inspection and tests.
  * Time factors of level lvl (0 = finest), each nt x nt row-major, nt <= 8:

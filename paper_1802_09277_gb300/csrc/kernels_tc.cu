@@ -28,7 +28,7 @@ namespace {
 
 constexpr int TC_THREADS = 128;
 constexpr int TC_COLS = 128;  // columns (GEMM rows of the activation operand) per tile
-constexpr uint32_t TC_MAX_POLLS = 1u << 24;
+constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s: far above any tile's MMA time
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
             }
             tc::commit(&mbar);
         }
-        if (!tc::mbar_wait_bounded(&mbar, phase, TC_MAX_POLLS)) {
+        if (!tc::mbar_wait_bounded(&mbar, phase, TC_WAIT_NS)) {
             failed = true;
             if (tid == 0) atomicExch(a.err, 1);
         }

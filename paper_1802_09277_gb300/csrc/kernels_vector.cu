@@ -8,13 +8,27 @@ namespace st {
 
 constexpr int NRHS_MAX = 32;
 
+template <typename T>
 struct VecList {
-    const double *v[MAXV];
+    const T *v[MAXV];
 };
+template <typename T>
 struct AxpyArgs {
-    const double *x[MAXV];
+    const T *x[MAXV];
     double coef[MAXV * NRHS_MAX];
     double post[NRHS_MAX];  // y <- post_r * (y + sum_v coef x_v)
+};
+
+// two consecutive elements as one 8- (float) or 16-byte (double) access
+template <typename T>
+struct Pair;
+template <>
+struct Pair<double> {
+    using V = double2;
+};
+template <>
+struct Pair<float> {
+    using V = float2;
 };
 
 template <typename Tin, typename Tout>
@@ -55,40 +69,44 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// grid (nblk, nrhs), 256 threads; partial[(v*nrhs + r)*nblk + blk].
-// One pass over w: every thread keeps the nv running sums in registers.
+// grid (nblk, nrhs), 256 threads = 8 warps; partial[(v*nrhs + r)*nblk + blk].
+// Block b owns a contiguous chunk of the rhs segment; warp g accumulates the
+// vectors v = g, g + 8, ... (FP64 sums, also for FP32 vectors), so every
+// vector is read from HBM once and the chunk of w is re-read from L1.
+template <typename T>
 __global__ void __launch_bounds__(256)
-    k_multidot_partial(int nv, const __grid_constant__ VecList vl, const double *__restrict__ w,
-                       long long len, double *__restrict__ partial) {
-    __shared__ double red[8][MAXV];
+    k_multidot_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ w,
+                       long long len, double *__restrict__ partial, int vec2) {
+    using P2 = typename Pair<T>::V;
     const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
-    const long long chunk = (len + nblk - 1) / nblk;
-    const long long lo = blockIdx.x * chunk;
-    const long long hi = (lo + chunk < len) ? lo + chunk : len;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long off = (long long)r * len;
-    double acc[MAXV];
-#pragma unroll
-    for (int v = 0; v < MAXV; ++v) acc[v] = 0.0;
-    for (long long i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        const double wi = w[off + i];
-#pragma unroll
-        for (int v = 0; v < MAXV; ++v)
-            if (v < nv) acc[v] += vl.v[v][off + i] * wi;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int v = 0; v < MAXV; ++v) {
-        if (v >= nv) break;
-        const double t = warp_sum(acc[v]);
-        if (lane == 0) red[warp][v] = t;
-    }
-    __syncthreads();
-    if (threadIdx.x < nv) {
-        double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
-        partial[((long long)threadIdx.x * nrhs + r) * nblk + blockIdx.x] = t;
+    long long chunk = (len + nblk - 1) / nblk;
+    chunk += chunk & 1;  // even, so pairs never cross chunks
+    const long long lo = (long long)blockIdx.x * chunk;
+    const long long hi = (lo + chunk < len) ? lo + chunk : len;
+    for (int v = warp; v < nv; v += 8) {
+        const T *x = vl.v[v] + off;
+        const T *wr = w + off;
+        double acc = 0.0;
+        if (vec2) {
+            const P2 *x2 = reinterpret_cast<const P2 *>(x);
+            const P2 *w2 = reinterpret_cast<const P2 *>(wr);
+#pragma unroll 4
+            for (long long i = lo / 2 + lane; i < hi / 2; i += 32) {
+                const P2 a = x2[i], b = w2[i];
+                acc += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+            }
+        } else {
+#pragma unroll 4
+            for (long long i = lo + lane; i < hi; i += 32) acc += (double)x[i] * (double)wr[i];
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) partial[((long long)v * nrhs + r) * nblk + blockIdx.x] = acc;
     }
 }
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // one warp per output; lane-strided partial sums, then a fixed shuffle tree
 __global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, int count,
@@ -102,13 +120,20 @@ __global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, 
     if (lane == 0) out[i] = t;
 }
 
-cudaError_t launch_multidot(int nv, const double *const *vecs, const double *w, int nrhs,
-                            long long len, double *partial, int nblk, double *out,
-                            cudaStream_t s) {
+template <typename T>
+cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, long long len,
+                            double *partial, int nblk, double *out, cudaStream_t s) {
     if (nv > MAXV || nrhs > 65535 || nv <= 0) return cudaErrorInvalidValue;
-    VecList vl;
-    for (int i = 0; i < nv; ++i) vl.v[i] = vecs[i];
-    k_multidot_partial<<<dim3(nblk, nrhs), 256, 0, s>>>(nv, vl, w, len, partial);
+    VecList<T> vl;
+    auto al = [](const void *p) {
+        return sizeof(T) == 8 ? aligned16(p) : ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
+    };
+    int vec2 = (len % 2 == 0) && al(w);
+    for (int i = 0; i < nv; ++i) {
+        vl.v[i] = vecs[i];
+        vec2 = vec2 && al(vecs[i]);
+    }
+    k_multidot_partial<T><<<dim3(nblk, nrhs), 256, 0, s>>>(nv, vl, w, len, partial, vec2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int count = nv * nrhs;
@@ -116,37 +141,86 @@ cudaError_t launch_multidot(int nv, const double *const *vecs, const double *w, 
     return cudaGetLastError();
 }
 
-__global__ void k_multiaxpy(int nv, const __grid_constant__ AxpyArgs aa, int nrhs, long long len,
-                            double *__restrict__ y) {
+template <typename T>
+__global__ void k_multiaxpy(int nv, const __grid_constant__ AxpyArgs<T> aa, int nrhs,
+                            long long len, T *__restrict__ y, int vec2) {
+    using P2 = typename Pair<T>::V;
+    if (vec2) {  // pairs never straddle two rhs because len is even
+        const long long n = (long long)nrhs * len / 2;
+        P2 *y2 = reinterpret_cast<P2 *>(y);
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const int r = (int)((2 * i) / len);
+            P2 acc = y2[i];
+            for (int v = 0; v < nv; ++v) {
+                const T c = (T)aa.coef[v * NRHS_MAX + r];
+                const P2 x = reinterpret_cast<const P2 *>(aa.x[v])[i];
+                acc.x += c * x.x;
+                acc.y += c * x.y;
+            }
+            acc.x *= (T)aa.post[r];
+            acc.y *= (T)aa.post[r];
+            y2[i] = acc;
+        }
+        return;
+    }
     const long long n = (long long)nrhs * len;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(i / len);
-        double acc = y[i];
-        for (int v = 0; v < nv; ++v) acc += aa.coef[v * NRHS_MAX + r] * aa.x[v][i];
-        y[i] = aa.post[r] * acc;
+        T acc = y[i];
+        for (int v = 0; v < nv; ++v) acc += (T)aa.coef[v * NRHS_MAX + r] * aa.x[v][i];
+        y[i] = (T)aa.post[r] * acc;
     }
 }
 
-cudaError_t launch_multiaxpy(int nv, const double *const *xs, const double *coef, int nrhs,
-                             long long len, double *y, cudaStream_t s, const double *post) {
+template <typename T>
+cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int nrhs,
+                             long long len, T *y, cudaStream_t s, const double *post) {
     if (nv > MAXV || nrhs > NRHS_MAX || nv < 0) return cudaErrorInvalidValue;
     if (nv == 0 && !post) return cudaSuccess;
-    AxpyArgs aa;
+    AxpyArgs<T> aa;
     for (int v = 0; v < nv; ++v) {
         aa.x[v] = xs[v];
         for (int r = 0; r < nrhs; ++r) aa.coef[v * NRHS_MAX + r] = coef[v * nrhs + r];
     }
     for (int r = 0; r < nrhs; ++r) aa.post[r] = post ? post[r] : 1.0;
-    long long blocks = ((long long)nrhs * len + 255) / 256;
+    const bool al = sizeof(T) == 8 ? aligned16(y) : ((reinterpret_cast<uintptr_t>(y) & 7u) == 0);
+    int vec2 = (len % 2 == 0) && al;
+    for (int v = 0; v < nv; ++v)
+        vec2 = vec2 && (sizeof(T) == 8 ? aligned16(xs[v])
+                                       : ((reinterpret_cast<uintptr_t>(xs[v]) & 7u) == 0));
+    long long blocks = ((long long)nrhs * len + 511) / 512;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_multiaxpy<<<(unsigned)blocks, 256, 0, s>>>(nv, aa, nrhs, len, y);
+    if (blocks < 1) blocks = 1;
+    k_multiaxpy<T><<<(unsigned)blocks, 256, 0, s>>>(nv, aa, nrhs, len, y, vec2);
     return cudaGetLastError();
 }
 
 struct ScaleArgs {
     double a[NRHS_MAX];
 };
+
+// y (FP64) += a_r * x (FP32), per rhs r: the refinement update
+__global__ void k_axpy_f32_f64(const float *__restrict__ x, double *__restrict__ y,
+                               const __grid_constant__ ScaleArgs sa, long long len, int nrhs) {
+    const long long n = (long long)nrhs * len;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] += sa.a[i / len] * (double)x[i];
+}
+
+cudaError_t launch_axpy_f32_f64(const float *x, double *y, const double *a, int nrhs,
+                                long long len, cudaStream_t s) {
+    if (nrhs > NRHS_MAX) return cudaErrorInvalidValue;
+    ScaleArgs sa;
+    for (int r = 0; r < nrhs; ++r) sa.a[r] = a[r];
+    long long blocks = ((long long)nrhs * len + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks <= 0) return cudaSuccess;
+    k_axpy_f32_f64<<<(unsigned)blocks, 256, 0, s>>>(x, y, sa, len, nrhs);
+    return cudaGetLastError();
+}
 
 __global__ void k_scale(const double *__restrict__ x, double *y, const __grid_constant__ ScaleArgs sa,
                         long long len, int nrhs) {
@@ -172,6 +246,14 @@ template cudaError_t launch_convert<double, float>(const double *, float *, long
 template cudaError_t launch_convert<float, double>(const float *, double *, long long, cudaStream_t);
 template cudaError_t launch_convert<double, double>(const double *, double *, long long, cudaStream_t);
 template cudaError_t launch_zero<double>(double *, long long, cudaStream_t);
+template cudaError_t launch_multidot<double>(int, const double *const *, const double *, int,
+                                             long long, double *, int, double *, cudaStream_t);
+template cudaError_t launch_multidot<float>(int, const float *const *, const float *, int,
+                                            long long, double *, int, double *, cudaStream_t);
+template cudaError_t launch_multiaxpy<double>(int, const double *const *, const double *, int,
+                                              long long, double *, cudaStream_t, const double *);
+template cudaError_t launch_multiaxpy<float>(int, const float *const *, const double *, int,
+                                             long long, float *, cudaStream_t, const double *);
 template cudaError_t launch_zero<float>(float *, long long, cudaStream_t);
 
 }  // namespace st

@@ -110,6 +110,10 @@ struct st_handle_s {
            prof_flops[ST_PROF_NCLASS] = {0};
     // outer iteration
     std::vector<double *> V, Zk;
+    std::vector<float *> V32, Z32;  // FP32 Krylov space of the refinement's inner solver
+    double *r64 = nullptr;
+    float *rhs32 = nullptr, *e32 = nullptr;
+    int krylov32_m = 0;
     double *partial = nullptr, *dots = nullptr;
     int nblk_dot = 0;
     int krylov_m = 0;
@@ -360,7 +364,7 @@ int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long lon
         const float *Wt = (const float *)(forward ? ds.Ut[axis] : ds.U[axis]);
         const int kind = (prec == ST_MIXED_TF32) ? 2 : 1;
         const long long ncols = (axis == 0) ? outer : outer * inner;
-        KScope ks(h, ST_PROF_GEMM32, sizeof(T) * (2.0 * E + n * n), 2.0 * E * n);
+        KScope ks(h, ST_PROF_TC, sizeof(T) * (2.0 * E + n * n), 2.0 * E * n);
         const cudaError_t e = launch_tc_axis(kind, axis == 0 ? 0 : 1, (const float *)in,
                                              (float *)out, Wt, (int)n, (int)n, ncols, inner,
                                              h->tc_err, h->nsm, h->stream);
@@ -463,16 +467,17 @@ int vcycle(st_handle h, int l, T *u, const T *f, bool zero_init) {
 }
 
 // y_r = post_r (y_r + sum_v coef[v*R + r] x_v), in chunks of MAXV vectors
-int vaxpy(st_handle h, int nv, const double *const *xs, const double *coef, double *y,
+template <typename T>
+int vaxpy(st_handle h, int nv, const T *const *xs, const double *coef, T *y,
           const double *post = nullptr) {
     const int R = h->nrhs;
     int v0 = 0;
     do {
         const int cnt = std::min(MAXV, nv - v0);
         const bool last = v0 + cnt >= nv;
-        KScope ks(h, ST_PROF_VECTOR, 8.0 * (cnt + 2) * h->len * R, 2.0 * cnt * h->len * R);
-        CK(launch_multiaxpy(cnt, xs + v0, coef + (size_t)v0 * R, R, h->len, y, h->stream,
-                            last ? post : nullptr));
+        KScope ks(h, ST_PROF_VECTOR, sizeof(T) * (cnt + 2.0) * h->len * R, 2.0 * cnt * h->len * R);
+        CK(launch_multiaxpy<T>(cnt, xs ? xs + v0 : nullptr, coef ? coef + (size_t)v0 * R : nullptr,
+                               R, h->len, y, h->stream, last ? post : nullptr));
         v0 += cnt;
     } while (v0 < nv);
     return ST_OK;
@@ -505,7 +510,7 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     const T *const *lam = space<T>(h).lam;
     const int nt = h->nt;
     if (l == h->nlev - 1) {
-        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 2.0 * E, E * (5.0 * nt + 4.0));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E, E * (5.0 * nt + 4.0));
         CK(launch_spec_coarse<T>(u, f, lam, h->g, c, spp, h->nrhs, h->stream));
         return ST_OK;
     }
@@ -514,7 +519,7 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     T *cur = u, *oth = tmp;
     bool zero = zero_init;
     for (int k = 0; k < h->opt.nu1; ++k) {
-        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * (zero ? 2.0 : 3.0) * E, E * (7.0 * nt + 6.0));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.0 : 3.0) * E, E * (7.0 * nt + 6.0));
         CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, zero ? 1 : 0, h->stream));
         std::swap(cur, oth);
         zero = false;
@@ -533,7 +538,7 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
         CK(launch_prolong_add<T>(w.u[l + 1], cur, pc, h->g, nc, h->stream));
     }
     for (int k = 0; k < h->opt.nu2; ++k) {
-        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 3.0 * E, E * (7.0 * nt + 6.0));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.0 * E, E * (7.0 * nt + 6.0));
         CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, 0, h->stream));
         std::swap(cur, oth);
     }
@@ -617,16 +622,17 @@ int ensure_krylov(st_handle h) {
     return ST_OK;
 }
 
-// per-rhs dots of vecs[0..nv) with w -> host out[v*nrhs + r]
-int dots(st_handle h, int nv, const double *const *vecs, const double *w, std::vector<double> &out) {
+// per-rhs dots of vecs[0..nv) with w -> host out[v*nrhs + r] (FP64 sums)
+template <typename T>
+int dots(st_handle h, int nv, const T *const *vecs, const T *w, std::vector<double> &out) {
     out.assign((size_t)nv * h->nrhs, 0.0);
     for (int v0 = 0; v0 < nv; v0 += MAXV) {
         const int cnt = std::min(MAXV, nv - v0);
         {
-            KScope ks(h, ST_PROF_VECTOR, 8.0 * (cnt + 1) * h->len * h->nrhs,
+            KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 1.0) * h->len * h->nrhs,
                       2.0 * cnt * h->len * h->nrhs);
-            CK(launch_multidot(cnt, vecs + v0, w, h->nrhs, h->len, h->partial, h->nblk_dot,
-                               h->dots, h->stream));
+            CK(launch_multidot<T>(cnt, vecs + v0, w, h->nrhs, h->len, h->partial, h->nblk_dot,
+                                  h->dots, h->stream));
         }
         CK(cudaMemcpyAsync(out.data() + (size_t)v0 * h->nrhs, h->dots,
                            sizeof(double) * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
@@ -636,10 +642,11 @@ int dots(st_handle h, int nv, const double *const *vecs, const double *w, std::v
     return ST_OK;
 }
 
-int norms(st_handle h, const double *x, std::vector<double> &nr) {
+template <typename T>
+int norms(st_handle h, const T *x, std::vector<double> &nr) {
     std::vector<double> d;
-    const double *v[1] = {x};
-    CKS(dots(h, 1, v, x, d));
+    const T *v[1] = {x};
+    CKS(dots<T>(h, 1, v, x, d));
     nr.resize(h->nrhs);
     for (int r = 0; r < h->nrhs; ++r) nr[r] = std::sqrt(std::max(0.0, d[r]));
     return ST_OK;
@@ -653,21 +660,19 @@ int solve_mg(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
     CKS(ensure_krylov(h));
     double *r = h->V[0], *e = h->Zk[0];
     std::vector<double> nf, nr;
-    CKS(norms(h, rhs, nf));
+    CKS(norms<double>(h, rhs, nf));
     int it = 0;
     double worst = 0.0;
     for (;;) {
         CKS(residual64(h, u, rhs, r));
-        CKS(norms(h, r, nr));
+        CKS(norms<double>(h, r, nr));
         worst = 0.0;
         for (int q = 0; q < h->nrhs; ++q) worst = std::max(worst, nf[q] > 0 ? nr[q] / nf[q] : 0.0);
         if (worst <= tol || it >= h->opt.max_it) break;
         CKS(precondition(h, r, e));
-        const double one[1] = {1.0};
         std::vector<double> c(h->nrhs, 1.0);
         const double *xs[1] = {e};
-        CKS(vaxpy(h, 1, xs, c.data(), u));
-        (void)one;
+        CKS(vaxpy<double>(h, 1, xs, c.data(), u));
         ++it;
     }
     info->iterations = it;
@@ -676,48 +681,51 @@ int solve_mg(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
     return ST_OK;
 }
 
-int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
-    CKS(ensure_krylov(h));
-    const int m = h->opt.gmres_restart, R = h->nrhs;
-    std::vector<double> nf, beta, hcol, h2;
-    CKS(norms(h, rhs, nf));
+// Flexible GMRES(m) on T vectors for L x = b (per right-hand side), right
+// preconditioned by prec(v, z); x holds the initial guess.  Stops each rhs
+// at ||b - L x|| <= tol ||b|| (true residual checked at every restart).
+// skip[q] excludes rhs q (its x is left unchanged).  *its: iterations,
+// *worst: largest relative true residual at exit.
+template <typename T, typename Apply, typename Prec>
+int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vector<T *> &V,
+                std::vector<T *> &Zk, Apply apply, Prec prec, const std::vector<char> &skip,
+                int *its, double *worst_out) {
+    const int m = (int)Zk.size(), R = h->nrhs;
+    std::vector<double> nb, beta, hcol;
+    CKS(norms<T>(h, b, nb));
     int total = 0;
     double worst = 0.0;
     std::vector<char> done(R, 0);
-    for (int q = 0; q < R; ++q) done[q] = !(nf[q] > 0);
     while (true) {
-        CKS(residual64(h, u, rhs, h->V[0]));
-        CKS(norms(h, h->V[0], beta));
+        CKS(stencil<T>(h, 0, x, b, V[0], MODE_RES, false, 0, h->N * R));
+        CKS(norms<T>(h, V[0], beta));
         worst = 0.0;
         for (int q = 0; q < R; ++q) {
-            const double rel = nf[q] > 0 ? beta[q] / nf[q] : 0.0;
-            worst = std::max(worst, rel);
-            done[q] = rel <= tol;
+            const double rel = nb[q] > 0 ? beta[q] / nb[q] : 0.0;
+            done[q] = skip[q] || !(nb[q] > 0) || rel <= tol;
+            if (!skip[q]) worst = std::max(worst, rel);
         }
-        if (worst <= tol || total >= h->opt.max_it) break;
+        if (worst <= tol || total >= maxit) break;
         std::vector<double> sc(R);
-        for (int q = 0; q < R; ++q) sc[q] = beta[q] > 0 ? 1.0 / beta[q] : 0.0;
-        CKS(vaxpy(h, 0, nullptr, nullptr, h->V[0], sc.data()));
+        for (int q = 0; q < R; ++q) sc[q] = (!done[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
+        CKS(vaxpy<T>(h, 0, nullptr, nullptr, V[0], sc.data()));
         // per-rhs Hessenberg (column-major (m+1) x m), Givens, rhs g
         std::vector<double> H((size_t)R * (m + 1) * m, 0.0), cs((size_t)R * m), sn((size_t)R * m),
             g((size_t)R * (m + 1), 0.0);
         std::vector<int> kq(R, 0);
-        for (int q = 0; q < R; ++q) g[(size_t)q * (m + 1)] = beta[q];
+        for (int q = 0; q < R; ++q) g[(size_t)q * (m + 1)] = done[q] ? 0.0 : beta[q];
         std::vector<char> act(R);
         for (int q = 0; q < R; ++q) act[q] = !done[q];
-        int j = 0;
-        for (; j < m; ++j) {
-            CKS(precondition(h, h->V[j], h->Zk[j]));
-            CKS(stencil<double>(h, 0, h->Zk[j], nullptr, h->V[j + 1], MODE_APPLY, false, 0,
-                                h->N * R));
+        for (int j = 0; j < m; ++j) {
+            CKS(prec(V[j], Zk[j]));
+            CKS(apply(Zk[j], V[j + 1]));
             // classical Gram-Schmidt: one fused pass gives V^T w and w.w; a
             // second pass runs only where ||w - V h|| < ||w|| / sqrt(2)
             // (Kahan's "twice is enough" criterion)
-            std::vector<const double *> vw(h->V.begin(), h->V.begin() + j + 1);
-            vw.push_back(h->V[j + 1]);
-            CKS(dots(h, j + 2, vw.data(), h->V[j + 1], hcol));
-            std::vector<double> hsum((size_t)(j + 1) * R), neg((size_t)(j + 1) * R), rem2(R),
-                post(R);
+            std::vector<const T *> vw(V.begin(), V.begin() + j + 1);
+            vw.push_back(V[j + 1]);
+            CKS(dots<T>(h, j + 2, vw.data(), V[j + 1], hcol));
+            std::vector<double> hsum((size_t)(j + 1) * R), neg((size_t)(j + 1) * R), rem2(R), post(R);
             bool reorth = false;
             for (int q = 0; q < R; ++q) {
                 double hh = 0.0;
@@ -732,8 +740,8 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
                 if (act[q] && rem2[q] < 0.5 * ww) reorth = true;
             }
             if (reorth) {
-                CKS(vaxpy(h, j + 1, h->V.data(), neg.data(), h->V[j + 1]));
-                CKS(dots(h, j + 2, vw.data(), h->V[j + 1], hcol));
+                CKS(vaxpy<T>(h, j + 1, V.data(), neg.data(), V[j + 1]));
+                CKS(dots<T>(h, j + 2, vw.data(), V[j + 1], hcol));
                 for (int q = 0; q < R; ++q) {
                     double hh = 0.0;
                     for (int i = 0; i <= j; ++i) {
@@ -750,7 +758,7 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
                 hn[q] = std::sqrt(std::max(rem2[q], 0.0));
                 post[q] = hn[q] > 0 ? 1.0 / hn[q] : 0.0;
             }
-            CKS(vaxpy(h, j + 1, h->V.data(), neg.data(), h->V[j + 1], post.data()));
+            CKS(vaxpy<T>(h, j + 1, V.data(), neg.data(), V[j + 1], post.data()));
             ++total;
             bool all = true;
             for (int q = 0; q < R; ++q) {
@@ -761,27 +769,27 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
                 col[j + 1] = hn[q];
                 double *c = &cs[(size_t)q * m], *s = &sn[(size_t)q * m], *gq = &g[(size_t)q * (m + 1)];
                 for (int i = 0; i < j; ++i) {
-                    const double a = col[i], b = col[i + 1];
-                    col[i] = c[i] * a + s[i] * b;
-                    col[i + 1] = -s[i] * a + c[i] * b;
+                    const double a = col[i], bb = col[i + 1];
+                    col[i] = c[i] * a + s[i] * bb;
+                    col[i + 1] = -s[i] * a + c[i] * bb;
                 }
-                const double a = col[j], b = col[j + 1];
-                const double rad = std::hypot(a, b);
+                const double a = col[j], bb = col[j + 1];
+                const double rad = std::hypot(a, bb);
                 c[j] = rad > 0 ? a / rad : 1.0;
-                s[j] = rad > 0 ? b / rad : 0.0;
+                s[j] = rad > 0 ? bb / rad : 0.0;
                 col[j] = rad;
                 col[j + 1] = 0.0;
                 gq[j + 1] = -s[j] * gq[j];
                 gq[j] = c[j] * gq[j];
                 kq[q] = j + 1;
-                if (std::fabs(gq[j + 1]) <= tol * nf[q] || hn[q] == 0.0) act[q] = 0;
+                if (std::fabs(gq[j + 1]) <= tol * nb[q] || hn[q] == 0.0) act[q] = 0;
                 if (act[q]) all = false;
             }
-            if (all || total >= h->opt.max_it) break;
+            if (all || total >= maxit) break;
         }
-        // u += Z y per rhs
+        // x += Z y per rhs
         const int kmax = *std::max_element(kq.begin(), kq.end());
-        std::vector<double> coef((size_t)kmax * R, 0.0);
+        std::vector<double> coef((size_t)std::max(kmax, 1) * R, 0.0);
         for (int q = 0; q < R; ++q) {
             const int k = kq[q];
             const double *Hq = &H[(size_t)q * (m + 1) * m];
@@ -794,9 +802,117 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
             }
             for (int i = 0; i < k; ++i) coef[(size_t)i * R + q] = y[i];
         }
-        if (kmax > 0) CKS(vaxpy(h, kmax, h->Zk.data(), coef.data(), u));
+        if (kmax > 0) CKS(vaxpy<T>(h, kmax, Zk.data(), coef.data(), x));
+    }
+    *its = total;
+    *worst_out = worst;
+    return ST_OK;
+}
+
+int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
+    CKS(ensure_krylov(h));
+    std::vector<double *> Z(h->Zk);
+    std::vector<char> skip(h->nrhs, 0);
+    int its = 0;
+    double worst = 0.0;
+    auto apply = [h](const double *z, double *w) {
+        return stencil<double>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, h->N * h->nrhs);
+    };
+    auto prec = [h](const double *v, double *z) { return precondition(h, v, z); };
+    CKS(fgmres_core<double>(h, rhs, u, tol, h->opt.max_it, h->V, Z, apply, prec, skip, &its,
+                            &worst));
+    info->iterations = its;
+    info->rel_residual = worst;
+    info->status = (worst <= tol) ? ST_OK : ST_ERR_NO_CONVERGENCE;
+    return ST_OK;
+}
+
+// z = V-cycle(v) on FP32 vectors (the mixed modes' inner preconditioner)
+int precondition32(st_handle h, const float *v, float *z) {
+    Work<float> &w = h->w32;
+    if (h->opt.basis != ST_BASIS_SPECTRAL) return vcycle<float>(h, 0, z, v, true);
+    const long long planes = (long long)h->N * h->nrhs * h->nt;
+    float *fh = nullptr, *e = nullptr;
+    CKS(spatial<float>(h, v, w.w0, w.w1, true, planes, &fh));
+    float *tmp = (fh == w.w0) ? w.w1 : w.w0;
+    CKS(svcycle<float>(h, 0, w.u[0], fh, tmp, true));
+    float *t0 = (h->dim % 2 == 1) ? z : w.f[0], *t1 = (h->dim % 2 == 1) ? w.f[0] : z;
+    CKS(spatial<float>(h, w.u[0], t0, t1, false, planes, &e));
+    if (e != z) CK(cudaMemcpyAsync(z, e, sizeof(float) * h->len * h->nrhs, cudaMemcpyDeviceToDevice, h->stream));
+    return ST_OK;
+}
+
+int ensure_krylov32(st_handle h) {
+    const int m = h->opt.gmres_restart;
+    if (h->krylov32_m == m && !h->V32.empty()) return ST_OK;
+    const size_t e0 = (size_t)h->len * h->nrhs;
+    void *p;
+    h->V32.clear();
+    h->Z32.clear();
+    for (int i = 0; i <= m; ++i) {
+        CKS(dalloc(h, e0 * sizeof(float), &p));
+        h->V32.push_back((float *)p);
+    }
+    for (int i = 0; i < m; ++i) {
+        CKS(dalloc(h, e0 * sizeof(float), &p));
+        h->Z32.push_back((float *)p);
+    }
+    CKS(dalloc(h, e0 * sizeof(double), &p));
+    h->r64 = (double *)p;
+    CKS(dalloc(h, e0 * sizeof(float), &p));
+    h->rhs32 = (float *)p;
+    CKS(dalloc(h, e0 * sizeof(float), &p));
+    h->e32 = (float *)p;
+    h->krylov32_m = m;
+    return ST_OK;
+}
+
+// Mixed-precision iterative refinement: FP64 residual r = f - L u and FP64
+// update u += ||r|| e, where e solves L e = r / ||r|| approximately by FGMRES
+// on FP32 vectors (FP32 operator, FP32 V-cycle) to inner_tol.
+int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
+    CKS(ensure_krylov32(h));
+    const int R = h->nrhs;
+    std::vector<double> nf, nr;
+    CKS(norms<double>(h, rhs, nf));
+    int total = 0, outer = 0;
+    double worst = 0.0;
+    auto apply = [h](const float *z, float *w) {
+        return stencil<float>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, h->N * h->nrhs);
+    };
+    auto prec = [h](const float *v, float *z) { return precondition32(h, v, z); };
+    const long long n0 = h->len * R;
+    for (;;) {
+        CKS(residual64(h, u, rhs, h->r64));
+        CKS(norms<double>(h, h->r64, nr));
+        worst = 0.0;
+        std::vector<char> skip(R, 0);
+        std::vector<double> sc(R), back(R);
+        for (int q = 0; q < R; ++q) {
+            const double rel = nf[q] > 0 ? nr[q] / nf[q] : 0.0;
+            worst = std::max(worst, rel);
+            skip[q] = !(nf[q] > 0) || rel <= tol || !(nr[q] > 0);
+            sc[q] = skip[q] ? 0.0 : 1.0 / nr[q];
+            back[q] = skip[q] ? 0.0 : nr[q];
+        }
+        if (worst <= tol || total >= h->opt.max_it || outer >= 60) break;
+        CKS((vconvert<double, float>(h, h->r64, h->rhs32)));
+        CKS(vaxpy<float>(h, 0, nullptr, nullptr, h->rhs32, sc.data()));
+        CK(launch_zero<float>(h->e32, n0, h->stream));
+        int its = 0;
+        double w32 = 0.0;
+        const double itol = std::max(h->opt.inner_tol, 1e-6);
+        CKS(fgmres_core<float>(h, h->rhs32, h->e32, itol, h->opt.max_it - total, h->V32, h->Z32,
+                               apply, prec, skip, &its, &w32));
+        total += its;
+        ++outer;
+        {
+            KScope ks(h, ST_PROF_VECTOR, 12.0 * n0, 2.0 * n0);
+            CK(launch_axpy_f32_f64(h->e32, u, back.data(), R, h->len, h->stream));
+        }
     }
     info->iterations = total;
+    info->refinements = outer;
     info->rel_residual = worst;
     info->status = (worst <= tol) ? ST_OK : ST_ERR_NO_CONVERGENCE;
     return ST_OK;
@@ -822,6 +938,10 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         return fail(ST_ERR_INVALID_ARG, "bad precision");
     if (o.basis != ST_BASIS_NODAL && o.basis != ST_BASIS_SPECTRAL)
         return fail(ST_ERR_INVALID_ARG, "bad basis");
+    if (o.outer < ST_OUTER_FGMRES || o.outer > ST_OUTER_IR)
+        return fail(ST_ERR_INVALID_ARG, "bad outer iteration");
+    if (!(o.inner_tol > 0) || o.inner_tol >= 1)
+        return fail(ST_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
     h->dim = geometry;
     h->p = degree;
     h->N = slabs;
@@ -950,7 +1070,7 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     } else {
         CKS(alloc_work<double>(h, h->w64, true));
     }
-    h->nblk_dot = 304;
+    h->nblk_dot = 8 * h->nsm;
     void *p;
     CKS(dalloc(h, sizeof(double) * MAXV * h->nrhs * h->nblk_dot, &p));
     h->partial = (double *)p;
@@ -1002,6 +1122,12 @@ int static_scratch_addr(double **out) {
 
 }  // namespace
 
+int st::prepare_solve(st_handle_s *h) {
+    if (!h || h->host_only) return ST_ERR_INVALID_ARG;
+    if (h->opt.outer == ST_OUTER_IR && h->mixed) return ensure_krylov32(h);
+    return ensure_krylov(h);
+}
+
 extern "C" {
 
 void st_options_default(st_options *o) {
@@ -1020,6 +1146,7 @@ void st_options_default(st_options *o) {
     o->nrhs = 1;
     o->hbm_budget = 0;
     o->basis = ST_BASIS_NODAL;
+    o->inner_tol = 1e-4;
 }
 
 const char *st_last_error(void) { return g_err.c_str(); }
@@ -1131,7 +1258,7 @@ int st_vcycle(st_handle h, double *u, const double *f) {
         std::vector<double> c(h->nrhs, 1.0);
         const double *xs[1] = {h->Zk[0]};
         (void)one;
-        return vaxpy(h, 1, xs, c.data(), u);
+        return vaxpy<double>(h, 1, xs, c.data(), u);
     }
     if (!h->mixed) return vcycle<double>(h, 0, u, f, false);
     const long long n0 = h->len * h->nrhs;
@@ -1155,6 +1282,7 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
     try {
         if (!use_guess) CK(launch_zero<double>(u, h->len * h->nrhs, h->stream));
         if (h->opt.outer == ST_OUTER_MG) CKS(solve_mg(h, rhs, tol, u, info));
+        else if (h->opt.outer == ST_OUTER_IR && h->mixed) CKS(solve_ir(h, rhs, tol, u, info));
         else CKS(solve_fgmres(h, rhs, tol, u, info));
         CK(cudaStreamSynchronize(h->stream));
         int tc_err = 0;

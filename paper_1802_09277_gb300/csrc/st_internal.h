@@ -5,7 +5,13 @@
 
 #include <cstdint>
 
+struct st_handle_s;
+
 namespace st {
+
+// Allocate the outer iteration's Krylov space now (st_solve would do it on
+// first use); used by the server to account a setup's memory up front.
+int prepare_solve(st_handle_s *h);
 
 constexpr int NTMAX = 8;  // max time dofs per slab (ne + p)
 constexpr int PMAX = 3;   // max B-spline degree
@@ -125,15 +131,20 @@ cudaError_t launch_spec_coarse(T *u, const T *f, const T *const lam[3], const Gr
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin *x, Tout *y, long long n, cudaStream_t s);
 
-// partial[v][r][blk] = partial dot of vecs[v] and w over rhs r
-cudaError_t launch_multidot(int nv, const double *const *vecs, const double *w, int nrhs,
-                            long long len, double *partial, int nblk, double *out,
-                            cudaStream_t s);
+// out[v*nrhs + r] = dot of vecs[v] and w over rhs r (FP64 accumulation);
+// partial: nv * nrhs * nblk doubles of scratch
+template <typename T>
+cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, long long len,
+                            double *partial, int nblk, double *out, cudaStream_t s);
 
 // y_r = post_r * (y_r + sum_v coef[v][r] x_v)  (per rhs r; post NULL = 1)
-cudaError_t launch_multiaxpy(int nv, const double *const *xs, const double *coef, int nrhs,
-                             long long len, double *y, cudaStream_t s,
-                             const double *post = nullptr);
+template <typename T>
+cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int nrhs,
+                             long long len, T *y, cudaStream_t s, const double *post = nullptr);
+
+// y (FP64) += a_r * x (FP32) per rhs r
+cudaError_t launch_axpy_f32_f64(const float *x, double *y, const double *a, int nrhs,
+                                long long len, cudaStream_t s);
 
 // y = a_r * x (per rhs), y may alias x
 cudaError_t launch_scale(const double *x, double *y, const double *a, int nrhs, long long len,

@@ -109,12 +109,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity) {
         : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
     return ok != 0;
 }
-// Bounded wait: returns false if the phase did not complete within max_polls.
+// Non-blocking probe of the phase (mbarrier.test_wait never suspends).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wall-clock bounded wait: returns false if the phase did not complete within
+// limit_ns nanoseconds (the caller then records an error and bails out).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity,
-                                                  uint32_t max_polls) {
-    for (uint32_t i = 0; i < max_polls; ++i)
-        if (mbar_try_wait(mbar, parity)) return true;
-    return false;
+                                                  uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_test_wait(mbar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+        __nanosleep(64);
+    }
 }
 
 // ---- TMEM -> registers: 32 lanes x 32 bit, 16 consecutive columns ----

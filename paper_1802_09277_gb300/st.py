@@ -17,7 +17,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NOT_POSITIVE", -4: "ILL_CONDITIONED
           -9: "UNSUPPORTED"}
 GEOMETRY = {1: 1, 2: 2, 3: 3}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
-OUTER = {"fgmres": 0, "mg": 1}
+OUTER = {"fgmres": 0, "mg": 1, "ir": 2}
 BASIS = {"nodal": 0, "spectral": 1}
 
 # every symbol declared in include/st_iga.h
@@ -25,9 +25,10 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_smooth",
            "st_smooth_static", "st_vcycle",
            "st_solve", "st_profile", "st_profile_read", "st_time_factors", "st_space_factors",
-           "st_time_prolongation", "st_last_error"]
+           "st_time_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
+           "st_serve_submit", "st_serve_poll", "st_serve_wait", "st_serve_stop"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
-                "vector"]
+                "vector", "dot", "tc", "spec"]
 
 
 class StOptions(ctypes.Structure):
@@ -35,12 +36,36 @@ class StOptions(ctypes.Structure):
                 ("ne_per_slab", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("precision", ctypes.c_int), ("outer", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("max_it", ctypes.c_int),
-                ("nrhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("basis", ctypes.c_int)]
+                ("nrhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("basis", ctypes.c_int),
+                ("inner_tol", ctypes.c_double)]
 
 
 class StSolveInfo(ctypes.Structure):
-    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int),
+    _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("status", ctypes.c_int),
                 ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class StServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("opt", StOptions)]
+
+
+class StRequest(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int), ("degree", ctypes.c_int),
+                ("spans", ctypes.c_int * 3), ("slabs", ctypes.c_int),
+                ("rhs", ctypes.POINTER(ctypes.c_double)), ("rhs_is_coeffs", ctypes.c_int),
+                ("tol", ctypes.c_double)]
+
+
+class StResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("queue_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
+                ("latency_seconds", ctypes.c_double), ("batch_size", ctypes.c_int),
+                ("n_dofs", ctypes.c_int64)]
+
+
+ST_ERR_NOT_READY = -10
 
 
 class StError(RuntimeError):
@@ -85,6 +110,12 @@ def load():
         "st_space_factors": (I, [P, I, ip, dp, dp, dp, dp]),
         "st_time_prolongation": (I, [P, ip, dp]),
         "st_last_error": (ctypes.c_char_p, []),
+        "st_serve_opts_default": (V, [ctypes.POINTER(StServerOpts)]),
+        "st_serve_start": (I, [ctypes.POINTER(P), ctypes.POINTER(StServerOpts)]),
+        "st_serve_submit": (I, [P, ctypes.POINTER(StRequest), ctypes.POINTER(ctypes.c_uint64)]),
+        "st_serve_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(StResult), dp]),
+        "st_serve_wait": (I, [P, ctypes.c_uint64, D, ctypes.POINTER(StResult), dp]),
+        "st_serve_stop": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -205,7 +236,8 @@ class Solver:
                            _dptr(u, self.ndofs, "u"), int(bool(use_guess)), ctypes.byref(info))
         if check:
             _check(rc)
-        return {"iterations": info.iterations, "status": info.status,
+        return {"iterations": info.iterations, "refinements": info.refinements,
+                "status": info.status,
                 "rel_residual": info.rel_residual, "seconds": info.seconds, "rc": rc}
 
     def profile(self, enable):
@@ -252,3 +284,66 @@ class Solver:
         _check(_lib.st_time_prolongation(self._h, ctypes.byref(k),
                                          P.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
         return P
+
+
+class Server:
+    """Continuous-batching solve server (st_serve_*): submit host right-hand
+    sides of any configuration, poll or wait for host solutions."""
+
+    def __init__(self, workers=4, max_batch=8, hbm_budget=0, **opts):
+        lib = load()
+        self.o = StServerOpts()
+        lib.st_serve_opts_default(ctypes.byref(self.o))
+        self.o.workers = int(workers)
+        self.o.max_batch = int(max_batch)
+        self.o.hbm_budget = int(hbm_budget)
+        self.o.opt = options(**opts)
+        self._s = ctypes.c_void_p()
+        _check(lib.st_serve_start(ctypes.byref(self._s), ctypes.byref(self.o)))
+        self._n = {}
+
+    def submit(self, dim, degree, spans, slabs, rhs, tol=1e-8, coeffs=False):
+        import numpy as np
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        r = StRequest()
+        r.geometry, r.degree, r.slabs = int(dim), int(degree), int(slabs)
+        for a in range(3):
+            r.spans[a] = int(spans[a]) if a < len(spans) else 1
+        r.rhs = rhs.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.rhs_is_coeffs = 1 if coeffs else 0
+        r.tol = float(tol)
+        t = ctypes.c_uint64()
+        _check(_lib.st_serve_submit(self._s, ctypes.byref(r), ctypes.byref(t)))
+        self._n[t.value] = rhs.size
+        return t.value
+
+    def _take(self, fn, ticket, *extra):
+        import numpy as np
+        res = StResult()
+        u = np.empty(self._n[ticket])
+        rc = fn(self._s, ctypes.c_uint64(ticket), *extra, ctypes.byref(res),
+                u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        if rc == ST_ERR_NOT_READY:
+            return None
+        _check(rc)
+        del self._n[ticket]
+        out = {k: getattr(res, k) for k, _ in StResult._fields_}
+        return out, u
+
+    def poll(self, ticket):
+        """(result dict, solution) or None while pending."""
+        return self._take(_lib.st_serve_poll, ticket)
+
+    def wait(self, ticket, timeout=-1.0):
+        return self._take(_lib.st_serve_wait, ticket, ctypes.c_double(timeout))
+
+    def stop(self):
+        if self._s:
+            _check(_lib.st_serve_stop(self._s))
+            self._s = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

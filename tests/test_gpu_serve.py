@@ -1,0 +1,109 @@
+"""Serving loop (st_serve_*): continuous batching of solves of different
+configurations.  Every request's result must be the same whether it is
+solved alone or in a mix with others (batched with requests of the same
+configuration and overlapping with others on the GPU), and must match the
+oracle's direct solution to the solve tolerance."""
+import numpy as np
+import pytest
+
+from oracle import assemble as A
+from oracle import solve as S
+from paper_1802_09277_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def st():
+    import os
+    from paper_1802_09277_gb300 import build, st as stmod
+    if not os.path.exists(stmod.LIB_PATH):
+        build.build()
+    stmod.load()
+    assert torch.cuda.is_available()
+    return stmod
+
+
+# (dim, spans, degree, slabs): a mix with repeated configurations so that the
+# server can batch them
+MIX = [(2, (16, 16), 2, 8), (2, (16, 16), 2, 8), (1, (32,), 3, 16), (2, (16, 16), 2, 8),
+       (2, (12, 20), 1, 32), (3, (6, 6, 6), 2, 4), (1, (32,), 3, 16), (2, (12, 20), 1, 32)]
+
+
+def _requests():
+    reqs = []
+    for i, (d, spans, p, N) in enumerate(MIX):
+        pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+        reqs.append((d, spans, p, N, inputs.normal_coeffs(500 + i, pr.ndofs)))
+    return reqs
+
+
+@pytest.mark.parametrize("prec,outer", [("mixed_tf32", "ir"), ("fp64", "fgmres")])
+def test_alone_vs_mix(st, prec, outer):
+    reqs = _requests()
+    tol = 1e-10
+    opts = dict(precision=prec, outer=outer, basis="spectral")
+    alone = []
+    srv = st.Server(workers=1, max_batch=1, **opts)
+    for d, spans, p, N, c in reqs:
+        t = srv.submit(d, p, spans, N, c, tol=tol, coeffs=True)
+        res, u = srv.wait(t, timeout=120.0)
+        assert res["status"] == 0 and res["batch_size"] == 1
+        alone.append(u)
+    srv.stop()
+    srv = st.Server(workers=3, max_batch=4, **opts)
+    tickets = [srv.submit(d, p, spans, N, c, tol=tol, coeffs=True) for d, spans, p, N, c in reqs]
+    mixed = [srv.wait(t, timeout=120.0) for t in tickets]
+    srv.stop()
+    batched = max(res["batch_size"] for res, _ in mixed)
+    assert batched >= 2  # the repeated configurations were solved together
+    for (d, spans, p, N, c), ua, (res, um) in zip(reqs, alone, mixed):
+        assert res["status"] == 0
+        # each right-hand side is refined on its own: same bits alone and in the mix
+        assert np.array_equal(ua, um), (d, spans, p, N, res["batch_size"])
+        pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+        ud = S.direct(A.assemble_L(pr), A.load_from_coeffs(pr, c))
+        assert np.linalg.norm(um - ud) <= 1e-8 * np.linalg.norm(ud)
+
+
+def test_budget_admission(st):
+    d, spans, p, N = 2, (24, 24), 2, 16
+    pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+    c = inputs.normal_coeffs(600, pr.ndofs)
+    # too small for any setup: the request fails cleanly with OVER_BUDGET
+    srv = st.Server(workers=2, max_batch=2, hbm_budget=1 << 20, precision="mixed_fp32", outer="ir")
+    res, _ = srv.wait(srv.submit(d, p, spans, N, c, coeffs=True), timeout=60.0)
+    assert res["status"] == -8
+    srv.stop()
+    # enough for one setup at a time: requests are admitted one after the other
+    probe = st.Solver(d, p, spans, N, precision="mixed_fp32", outer="ir", basis="spectral")
+    one = probe.device_bytes
+    probe.close()
+    budget = int(one * 4 + 4 * 8 * pr.ndofs)  # setup + lazily allocated Krylov space + vectors
+    srv = st.Server(workers=3, max_batch=1, hbm_budget=budget, precision="mixed_fp32",
+                    outer="ir", basis="spectral")
+    ts = [srv.submit(d, p, spans, N, inputs.normal_coeffs(601 + i, pr.ndofs), coeffs=True)
+          for i in range(4)]
+    outs = [srv.wait(t, timeout=120.0) for t in ts]
+    srv.stop()
+    assert all(r["status"] == 0 for r, _ in outs)
+
+
+def test_poll_and_tickets(st):
+    srv = st.Server(workers=1, max_batch=1, precision="mixed_fp32", outer="ir")
+    d, spans, p, N = 1, (20,), 2, 4
+    pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+    t = srv.submit(d, p, spans, N, inputs.normal_coeffs(7, pr.ndofs), coeffs=True)
+    got = None
+    for _ in range(20000):
+        got = srv.poll(t)
+        if got is not None:
+            break
+    if got is None:
+        got = srv.wait(t, timeout=60.0)
+    assert got[0]["status"] == 0 and got[0]["latency_seconds"] >= got[0]["solve_seconds"]
+    with pytest.raises(st.StError):
+        srv.poll(t + 12345) if (t + 12345) in srv._n else st._check(
+            st.load().st_serve_poll(srv._s, t + 12345, None, None))
+    srv.stop()
