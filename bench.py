@@ -29,8 +29,14 @@ WORKLOADS = {
     # name: (dim, spans, degree, slabs, ne, tol, seed)
     "square64": (2, (64, 64), 2, 256, 2, 1e-8, 2),
     "square128_p3": (2, (128, 128), 3, 1024, 2, 1e-8, 3),
+    "cube48_x16": (3, (48, 48, 48), 2, 128, 2, 1e-8, 400),
     "interval16": (1, (16,), 2, 8, 4, 1e-10, 1),
 }
+# right-hand side: "coeffs" = N(0,1) B-spline coefficients (one seed per rhs),
+# "bumps" = 32 space-time Gaussian bumps; number of rhs solved together;
+# FGMRES restart (memory); variants measured beside the headline
+RHS = {"square64": ("coeffs", 1, 20, "all"), "square128_p3": ("bumps", 1, 20, "min"),
+       "cube48_x16": ("coeffs", 16, 10, "min"), "interval16": ("coeffs", 1, 20, "all")}
 METRIC = "space-time DoFs/s to rel. residual 1e-8, mixed vs FP64 plain; serve p50/p99"
 UNIT = "DoFs/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -172,16 +178,18 @@ def gpu_arm(args, rank, world):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
-    common = dict(ne_per_slab=ne, gmres_restart=20, max_it=300)
+    rhs_kind, nrhs, restart, vset = RHS[args.workload]
+    common = dict(ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
     peaks, peak_src = load_peaks()
 
     def make(prec, basis, outer):
         return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
                          outer=outer, **common)
 
-    # rank r solves its own right-hand side (independent replicas)
-    c = torch.tensor(inputs.normal_coeffs(seed + 1000 * rank, 0 + make_len(d, spans, p, N, ne)),
-                     dtype=torch.float64, device=dev)
+    # rank r solves its own right-hand side(s) (independent replicas)
+    n1 = make_len(d, spans, p, N, ne)
+    c = torch.tensor(np.concatenate([inputs.normal_coeffs(seed + 1000 * rank + q, n1)
+                                     for q in range(nrhs)]), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -218,7 +226,13 @@ def gpu_arm(args, rank, world):
     # --- mixed precision (headline) ---
     sm = make(args.precision, args.basis, args.outer)
     f = torch.empty_like(c)
-    sm.load_coeffs(c, f)
+    if rhs_kind == "bumps":
+        cen, wid, amp = inputs.gaussian_bumps(seed + 1000 * rank, count=32, dim=d + 1)
+        sm.load_gaussians(cen, wid, amp, f)
+    else:
+        sm.load_coeffs(c, f)
+    del c
+    tuning = sm.autotune()  # also runs inside the first solve (opt.autotune)
     clocks = ClockSampler(dev.index)
     clocks.start()
     t_mixed, i_mixed, u_mixed, _ = timed_solves(sm, f, args.steps, args.warmup)
@@ -249,14 +263,20 @@ def gpu_arm(args, rank, world):
         if k >= args.warmup:
             e2e_t.append(e0.elapsed_time(e1))
     e2e_ms = sum(e2e_t) / len(e2e_t)
+    del f_host, u_host, f_dev, u_dev
 
     # --- the other variants on the same workload (fewer steps, no profiling) ---
     variants = {}
     u64 = None
-    for prec, basis, outer in (("fp64", "nodal", "fgmres"), ("fp64", "spectral", "fgmres"),
-                               ("mixed_fp32", "nodal", "fgmres"), ("mixed_fp32", "spectral", "fgmres"),
-                               ("mixed_fp32", "spectral", "ir"), ("mixed_tf32", "spectral", "ir"),
-                               ("mixed_bf16", "spectral", "ir"), ("mixed_tf32", "spectral", "fgmres")):
+    u_mixed = u_mixed.cpu()
+    ndofs_h = sm.ndofs
+    sm.close()
+    torch.cuda.empty_cache()
+    allv = (("fp64", "nodal", "fgmres"), ("fp64", "spectral", "fgmres"),
+            ("mixed_fp32", "nodal", "fgmres"), ("mixed_fp32", "spectral", "fgmres"),
+            ("mixed_fp32", "spectral", "ir"), ("mixed_tf32", "spectral", "ir"),
+            ("mixed_bf16", "spectral", "ir"), ("mixed_tf32", "spectral", "fgmres"))
+    for prec, basis, outer in (allv if vset == "all" else allv[:1]):
         name = "fp64_plain" if (prec, basis) == ("fp64", "nodal") else "%s_%s_%s" % (prec, basis, outer)
         if (prec, basis, outer) == (args.precision, args.basis, args.outer) and name != "fp64_plain":
             continue
@@ -269,19 +289,21 @@ def gpu_arm(args, rank, world):
                           "refinements": iv[-1].get("refinements", 0),
                           "rel_residual": iv[-1]["rel_residual"]}
         if name == "fp64_plain":
-            u64 = uv.clone()
+            u64 = uv.cpu()
+        del uv
         sv.close()
+        torch.cuda.empty_cache()
     ms64 = variants["fp64_plain"]["ms_per_step"]
     i64 = [{"iterations": variants["fp64_plain"]["iterations"],
             "rel_residual": variants["fp64_plain"]["rel_residual"]}]
     rel_diff = float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
+    ndofs = ndofs_h
 
     # --- roofline of the dominant kernel class ---
     dom = max(prof, key=lambda k: prof[k]["ms"])
     pd = prof[dom]
     per_launch_ms = pd["ms"] / max(pd["launches"], 1)
     launches = sum(v["launches"] for v in prof.values())
-    ndofs = sm.ndofs
     result = {
         "ndofs": ndofs, "ms_mixed": ms, "ms_mixed_max": ms_max, "ms64": ms64, "ms_prof": ms_prof,
         "iters_mixed": i_mixed[-1]["iterations"], "res_mixed": i_mixed[-1]["rel_residual"],
@@ -291,9 +313,8 @@ def gpu_arm(args, rank, world):
         "bytes_d2h": f.numel() * 8, "prof": prof, "dominant": dom,
         "per_launch_ms": per_launch_ms, "launches": launches // max(args.steps, 1),
         "launches_total": launches, "clocks": clk, "peaks": peaks, "peak_src": peak_src,
-        "variants": variants,
+        "variants": variants, "tuning": tuning,
     }
-    sm.close()
     return result
 
 
@@ -488,6 +509,9 @@ def main():
         "e2e": {"value": ndofs * world / (r["e2e_ms"] / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": r["bytes_h2d"], "d2h_bytes_per_step": r["bytes_d2h"]},
         "gpu_launches": r["launches"],
+        "transform_autotune": [{"axis": a, "choice": ("cuda_cores" if c == 0 else
+                                                       "tensor_cores_%d_cta_per_sm" % c),
+                                "ms_per_pass": ms} for a, (c, ms) in enumerate(r["tuning"])],
         "clocks": r["clocks"],
     }
     print(json.dumps(line))

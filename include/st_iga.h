@@ -58,6 +58,11 @@ extern "C" {
 #define ST_SQUARE   2
 #define ST_CUBE     3
 
+/* factorisation of M_t^{-1} K_t used for the slab solves (Eq. 3.1) */
+#define ST_RSCHUR 0  /* real Schur form, 2x2 blocks for complex pairs (Sec. 3.5)   */
+#define ST_EIG    1  /* diagonalisation with complex eigenvalues (Sec. 3.3); setup
+                        fails with ST_ERR_ILL_CONDITIONED if cond(X) > 1e8        */
+
 /* precision of the multigrid preconditioner (the outer iteration is FP64) */
 #define ST_FP64        0  /* everything FP64                                  */
 #define ST_MIXED_FP32  1  /* V-cycle in FP32 (CUDA cores), FP64 outer          */
@@ -99,6 +104,15 @@ typedef struct {
     size_t hbm_budget;    /* bytes the handle may allocate; 0 = unlimited        */
     int basis;            /* ST_BASIS_NODAL (default) / ST_BASIS_SPECTRAL         */
     double inner_tol;     /* ST_OUTER_IR: inner relative tolerance (default 1e-4) */
+    int use_graphs;       /* 1 (default): replay each preconditioner application
+                             inside st_solve as a captured CUDA graph            */
+    int variant;          /* ST_RSCHUR (default) / ST_EIG                          */
+    int autotune;         /* 1 (default): the first st_solve times the candidate
+                             kernels of each spatial transform and keeps the
+                             fastest (see st_autotune)                          */
+    int fused_vcycle;     /* 1 (default): ST_BASIS_SPECTRAL runs the whole
+                             V-cycle in one shared-memory kernel per block of
+                             spatial modes when a mode's levels fit            */
 } st_options;
 
 typedef struct {
@@ -161,6 +175,15 @@ int st_residual(st_handle h, const double *u, const double *f, double *r);
  * basis of every slab: f = (M_t (x) M_x) c, which is l_h(phi_i) of Sec. 2.3
  * exactly (u0 = 0).  c, f: device, n_dofs each, must not alias. */
 int st_load_coeffs(st_handle h, const double *c, double *f);
+
+/* Load vector of a source made of space-time Gaussian bumps,
+ *   f(x, t) = sum_k amps[k] exp(-|(x, t) - c_k|^2 / (2 widths[k]^2)),
+ * l_h(phi_i) of Sec. 2.3 by Gauss-Legendre quadrature with 2p + 4 points per
+ * element (every bump is a product of 1D functions).  centers: HOST,
+ * nbumps x (d + 1) in (x, y, z, t) order; widths, amps: HOST, nbumps each;
+ * f: DEVICE, n_dofs (every rhs gets the same source).  Synchronises. */
+int st_load_gaussians(st_handle h, int nbumps, const double *centers, const double *widths,
+                      const double *amps, double *f);
 
 /* nsteps damped block-Jacobi steps on the finest level (Sec. 3.1):
  * u <- u + omega D^{-1}(f - L_h u), A_n^{-1} applied through Eq. 3.1.
@@ -276,6 +299,7 @@ typedef struct {
     double latency_seconds; /* submit -> solution on the host                     */
     int batch_size;       /* requests solved together with this one (incl. itself) */
     int64_t n_dofs;
+    char error[128];      /* message of a failure ("" on success)              */
 } st_result;
 
 void st_serve_opts_default(st_server_opts *o);
@@ -304,6 +328,21 @@ int st_time_factors(st_handle h, int lvl, int *nt, double *Kt, double *Mt,
  * the generalized eigenvectors U (columns, U^T M1 U = I) and eigenvalues. */
 int st_space_factors(st_handle h, int axis, int *n, double *M1, double *K1,
                      double *U, double *lam);
+
+/* Autotune the FP32 spatial transforms (mixed modes): for every axis, time
+ * the tensor-core kernel at 1..4 CTAs per SM (TF32 / BF16 modes; the
+ * candidates give identical results, so tuning never changes the numbers)
+ * with CUDA events on the handle's stream and keep the fastest.
+ * choice[a]: 0 = CUDA cores (ST_MIXED_FP32), k > 0 = tensor cores with k
+ * CTAs per SM (-1 for unused axes); ms[a]: its time per pass.  Either may
+ * be NULL.  Synchronises; FP64 handles return immediately. */
+int st_autotune(st_handle h, int *choice, double *ms);
+
+/* Generalized eigenvalues lambda = lam_re + i lam_im of K_t z = lambda M_t z
+ * on level lvl (Sec. 3.2; their real parts must be positive) and the 2-norm
+ * condition number of the eigenvector matrix X with unit columns (Table 1 of
+ * Sec. 4.1 reports it).  nt entries each; any output may be NULL. */
+int st_time_spectrum(st_handle h, int lvl, double *lam_re, double *lam_im, double *cond_x);
 
 /* The time prolongation P_t (2 nt x nt, row-major) that expresses one coarse
  * slab in the bases of the two fine slabs it merges (Sec. 3.1). */

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 
 namespace st {
@@ -505,6 +506,177 @@ bool real_schur(int n, const Mat &A, Mat &Q, Mat &T, std::vector<int> &blk, std:
         return false;
     }
     return true;
+}
+
+using cd = std::complex<double>;
+
+bool schur_eigvecs(int n, const Mat &Q, const Mat &T, const std::vector<int> &blk,
+                   std::vector<double> &lam_re, std::vector<double> &lam_im, Mat &Xre, Mat &Xim,
+                   std::string &err) {
+    lam_re.assign(n, 0.0);
+    lam_im.assign(n, 0.0);
+    // eigenvalues from the diagonal blocks
+    for (int i = 0; i < n; ++i) {
+        if (i + 1 < n && blk[i + 1]) {
+            const double a = T[i * n + i], b = T[i * n + i + 1];
+            const double c = T[(i + 1) * n + i], d = T[(i + 1) * n + i + 1];
+            const double hd = 0.5 * (a - d), disc = hd * hd + b * c;
+            const double im = std::sqrt(std::max(-disc, 0.0));
+            lam_re[i] = lam_re[i + 1] = 0.5 * (a + d);
+            lam_im[i] = im;
+            lam_im[i + 1] = -im;
+            ++i;
+        } else {
+            lam_re[i] = T[i * n + i];
+        }
+    }
+    // eigenvectors of T: (T - lam I) v = 0, v zero below the eigenvalue's block
+    std::vector<cd> V(n * n, cd(0.0, 0.0));
+    for (int k = 0; k < n; ++k) {
+        const cd lam(lam_re[k], lam_im[k]);
+        std::vector<cd> v(n, cd(0.0, 0.0));
+        int top;  // first row of the eigenvalue's block
+        if (k + 1 < n && blk[k + 1]) {  // first of a conjugate pair
+            const double a = T[k * n + k], b = T[k * n + k + 1];
+            v[k] = cd(b, 0.0);
+            v[k + 1] = lam - a;
+            top = k;
+        } else if (blk[k]) {  // second of the pair: conjugate of the first
+            for (int i = 0; i < n; ++i) V[i * n + k] = std::conj(V[i * n + k - 1]);
+            continue;
+        } else {
+            v[k] = cd(1.0, 0.0);
+            top = k;
+        }
+        // back substitution for rows above the block, block by block
+        for (int i = top - 1; i >= 0; --i) {
+            if (i >= 1 && blk[i]) {  // 2x2 block on rows i-1, i
+                cd g1(0.0, 0.0), g2(0.0, 0.0);
+                for (int j = i + 1; j < n; ++j) {
+                    g1 -= T[(i - 1) * n + j] * v[j];
+                    g2 -= T[i * n + j] * v[j];
+                }
+                const cd a = T[(i - 1) * n + i - 1] - lam, b = T[(i - 1) * n + i];
+                const cd c = T[i * n + i - 1], d = T[i * n + i] - lam;
+                const cd det = a * d - b * c;
+                if (std::abs(det) == 0.0) {
+                    err = "defective eigenvalue (repeated)";
+                    return false;
+                }
+                v[i - 1] = (d * g1 - b * g2) / det;
+                v[i] = (a * g2 - c * g1) / det;
+                --i;
+            } else {
+                cd g(0.0, 0.0);
+                for (int j = i + 1; j < n; ++j) g -= T[i * n + j] * v[j];
+                const cd den = T[i * n + i] - lam;
+                if (std::abs(den) == 0.0) {
+                    err = "defective eigenvalue (repeated)";
+                    return false;
+                }
+                v[i] = g / den;
+            }
+        }
+        for (int i = 0; i < n; ++i) V[i * n + k] = v[i];
+    }
+    // X = Q V, unit 2-norm columns
+    Xre.assign(n * n, 0.0);
+    Xim.assign(n * n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        std::vector<cd> col(n, cd(0.0, 0.0));
+        double nrm = 0.0;
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) col[i] += Q[i * n + j] * V[j * n + k];
+            nrm += std::norm(col[i]);
+        }
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0)) {
+            err = "zero eigenvector";
+            return false;
+        }
+        for (int i = 0; i < n; ++i) {
+            Xre[i * n + k] = col[i].real() / nrm;
+            Xim[i * n + k] = col[i].imag() / nrm;
+        }
+    }
+    return true;
+}
+
+bool complex_inverse(int n, const Mat &Are, const Mat &Aim, Mat &Bre, Mat &Bim) {
+    std::vector<cd> A(n * n), B(n * n, cd(0.0, 0.0));
+    for (int i = 0; i < n * n; ++i) A[i] = cd(Are[i], Aim[i]);
+    for (int i = 0; i < n; ++i) B[i * n + i] = cd(1.0, 0.0);
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < n; ++i)
+            if (std::abs(A[i * n + k]) > std::abs(A[piv * n + k])) piv = i;
+        if (std::abs(A[piv * n + k]) == 0.0) return false;
+        if (piv != k)
+            for (int j = 0; j < n; ++j) {
+                std::swap(A[k * n + j], A[piv * n + j]);
+                std::swap(B[k * n + j], B[piv * n + j]);
+            }
+        const cd inv = 1.0 / A[k * n + k];
+        for (int j = 0; j < n; ++j) {
+            A[k * n + j] *= inv;
+            B[k * n + j] *= inv;
+        }
+        for (int i = 0; i < n; ++i) {
+            if (i == k) continue;
+            const cd l = A[i * n + k];
+            if (std::abs(l) == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                A[i * n + j] -= l * A[k * n + j];
+                B[i * n + j] -= l * B[k * n + j];
+            }
+        }
+    }
+    Bre.resize(n * n);
+    Bim.resize(n * n);
+    for (int i = 0; i < n * n; ++i) {
+        Bre[i] = B[i].real();
+        Bim[i] = B[i].imag();
+    }
+    return true;
+}
+
+static double complex_norm2(int n, const std::vector<cd> &M) {
+    // largest singular value: power iteration on M^H M
+    std::vector<cd> x(n, cd(1.0, 0.0)), y(n), z(n);
+    double s = 0.0;
+    for (int it = 0; it < 500; ++it) {
+        for (int i = 0; i < n; ++i) {
+            y[i] = 0.0;
+            for (int j = 0; j < n; ++j) y[i] += M[i * n + j] * x[j];
+        }
+        for (int j = 0; j < n; ++j) {
+            z[j] = 0.0;
+            for (int i = 0; i < n; ++i) z[j] += std::conj(M[i * n + j]) * y[i];
+        }
+        double nz = 0.0;
+        for (int j = 0; j < n; ++j) nz += std::norm(z[j]);
+        nz = std::sqrt(nz);
+        if (!(nz > 0)) return 0.0;
+        const double snew = std::sqrt(nz);
+        for (int j = 0; j < n; ++j) x[j] = z[j] / nz;
+        if (std::fabs(snew - s) <= 1e-13 * snew) {
+            s = snew;
+            break;
+        }
+        s = snew;
+    }
+    return s;
+}
+
+double complex_cond2(int n, const Mat &Are, const Mat &Aim) {
+    Mat Bre, Bim;
+    if (!complex_inverse(n, Are, Aim, Bre, Bim)) return INFINITY;
+    std::vector<cd> A(n * n), B(n * n);
+    for (int i = 0; i < n * n; ++i) {
+        A[i] = cd(Are[i], Aim[i]);
+        B[i] = cd(Bre[i], Bim[i]);
+    }
+    return complex_norm2(n, A) * complex_norm2(n, B);
 }
 
 }  // namespace host

@@ -56,6 +56,45 @@ bool sym_gen_eig(int n, const Mat &K, const Mat &M, Mat &U, std::vector<double> 
 // second row of a 2x2 block, else 0.
 bool real_schur(int n, const Mat &A, Mat &Q, Mat &T, std::vector<int> &blk, std::string &err);
 
+// Eigen-decomposition A X = X diag(lam) from the real Schur form A = Q T Q^T
+// (blk as returned by real_schur): eigenvectors of T by back substitution
+// (complex for the 2x2 blocks), X = Q V, columns scaled to unit 2-norm.
+// Re/Im parts returned separately (row-major n x n).
+bool schur_eigvecs(int n, const Mat &Q, const Mat &T, const std::vector<int> &blk,
+                   std::vector<double> &lam_re, std::vector<double> &lam_im, Mat &Xre, Mat &Xim,
+                   std::string &err);
+
+// Inverse of the complex matrix (A_re + i A_im) by Gauss-Jordan with partial
+// pivoting; false if singular.
+bool complex_inverse(int n, const Mat &Are, const Mat &Aim, Mat &Bre, Mat &Bim);
+
+// 2-norm condition number of a complex matrix (power iteration on M^H M and
+// on its inverse).
+double complex_cond2(int n, const Mat &Are, const Mat &Aim);
+
+// g[i] = int_a^b func(x) (phi_i(x) + delta phi_i'(x)) dx over the B-splines of
+// an open knot vector on [a, b] with nel elements (first/last removed if
+// interior_only), Gauss-Legendre with npts points per element.
+template <typename F>
+std::vector<double> load_1d(double a, double b, int nel, int p, double delta, bool interior_only,
+                            int npts, F func) {
+    const std::vector<double> t = open_knots(a, b, nel, p);
+    const int nb = nel + p;
+    std::vector<double> g(nb, 0.0), gx, gw, v, d;
+    gauss_legendre(npts, gx, gw);
+    for (int e = 0; e < nel; ++e) {
+        const double lo = a + (b - a) * e / nel, hi = a + (b - a) * (e + 1) / nel;
+        for (int q = 0; q < npts; ++q) {
+            const double x = 0.5 * (hi - lo) * (gx[q] + 1.0) + lo, w = 0.5 * (hi - lo) * gw[q];
+            eval_basis(t, p, x, v, d);
+            const double fx = func(x);
+            for (int i = 0; i < nb; ++i) g[i] += w * fx * (v[i] + delta * d[i]);
+        }
+    }
+    if (interior_only) return std::vector<double>(g.begin() + 1, g.end() - 1);
+    return g;
+}
+
 // Frobenius norm of A*B - C (n x n), helper for the residual checks.
 double resid_norm(int n, const Mat &A, const Mat &B, const Mat &C);
 double frob(const Mat &A);

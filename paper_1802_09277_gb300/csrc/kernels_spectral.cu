@@ -45,6 +45,32 @@ __device__ __forceinline__ void spec_residual(const SpecCoefs<T> &c, T mu, const
 template <typename T>
 __device__ __forceinline__ void spec_block_solve(const SpecCoefs<T> &c, T mu, const T *r, T *v) {
     const int nt = c.nt;
+    if (c.variant == 1) {  // diagonalisation (Sec. 3.3): complex shifts lambda_i + mu
+        T zr[NTMAX], zi[NTMAX];
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i) {
+            T ar = T(0), ai = T(0);
+#pragma unroll
+            for (int j = 0; j < NTMAX; ++j)
+                if (j < nt) {
+                    ar += c.Y[i * NTMAX + j] * r[j];
+                    ai += c.Yi[i * NTMAX + j] * r[j];
+                }
+            const T dr = c.lre[i] + mu, di = c.lim[i];
+            const T den = dr * dr + di * di;
+            zr[i] = (i < nt) ? (ar * dr + ai * di) / den : T(0);
+            zi[i] = (i < nt) ? (ai * dr - ar * di) / den : T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i) {
+            T a = T(0);
+#pragma unroll
+            for (int j = 0; j < NTMAX; ++j)
+                if (j < nt) a += c.X[i * NTMAX + j] * zr[j] - c.Xi[i * NTMAX + j] * zi[j];
+            v[i] = a;
+        }
+        return;
+    }
     T w[NTMAX], z[NTMAX];
 #pragma unroll
     for (int i = 0; i < NTMAX; ++i) {
@@ -173,6 +199,242 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_mode_solve(T *__restrict__ w, const T *__restrict__ lam0, const T *__restrict__ lam1,
+                 const T *__restrict__ lam2, Grid g, const __grid_constant__ SpecCoefs<T> c,
+                 long long nslabs) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nslabs * g.nxyz) return;
+    const long long slab = idx / g.nxyz, k = idx % g.nxyz;
+    const int nt = c.nt;
+    const long long base = slab * nt * g.nxyz + k;
+    const T mu = mode_shift(g, lam0, lam1, lam2, k);
+    T r[NTMAX], v[NTMAX];
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) r[i] = (i < nt) ? w[base + (long long)i * g.nxyz] : T(0);
+    spec_block_solve(c, mu, r, v);
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i)
+        if (i < nt) w[base + (long long)i * g.nxyz] = v[i];
+}
+
+template <typename T>
+cudaError_t launch_mode_solve(T *w, const T *const lam[3], const Grid &g, const SpecCoefs<T> &c,
+                              long long nslabs, cudaStream_t s) {
+    const long long total = nslabs * g.nxyz;
+    if (total <= 0) return cudaSuccess;
+    k_mode_solve<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(w, lam[0], lam[1], lam[2], g,
+                                                                    c, nslabs);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The whole eigenbasis V-cycle in shared memory.  CTA (problem r, mode block
+// b) owns modes k0 .. k0 + MB - 1 of problem r on every slab of every level:
+// per level l it keeps u_l and f_l ([N_l][nt][MB], mode fastest) plus one
+// level-0 sized scratch array for the out-of-place Jacobi steps.  HBM is
+// touched twice: f^ is read once and u^ written once.  Same arithmetic as
+// k_spec_smooth / k_spec_res_restrict / k_prolong_add / k_spec_coarse.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_spec_vcycle(const T *__restrict__ fin, T *__restrict__ uout,
+                  const SpecCoefs<T> *__restrict__ lvc, const T *__restrict__ lam0,
+                  const T *__restrict__ lam1, const T *__restrict__ lam2, Grid g,
+                  const __grid_constant__ ProlongCoefs<T> pc, int nlev, int N, int MB, int nu1,
+                  int nu2, T omega) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int nt = pc.nt;
+    const long long nmodes = g.nxyz;
+    const int nblk = (int)((nmodes + MB - 1) / MB);
+    const int r = blockIdx.x / nblk;
+    const long long k0 = (long long)(blockIdx.x % nblk) * MB;
+    const int tid = threadIdx.x, NTH = blockDim.x;
+    // layout: mu[MB] | U_0 F_0 U_1 F_1 ... | TMP
+    T *mu = sm;
+    T *lev = sm + MB;
+    auto U = [&](int l) {
+        long long off = 0;
+        for (int q = 0; q < l; ++q) off += 2LL * (N >> q) * nt * MB;
+        return lev + off;
+    };
+    auto F = [&](int l) { return U(l) + (long long)(N >> l) * nt * MB; };
+    T *TMP = U(nlev);
+    for (int kk = tid; kk < MB; kk += NTH)
+        mu[kk] = (k0 + kk < nmodes) ? mode_shift(g, lam0, lam1, lam2, k0 + kk) : T(0);
+    // load f^ of this problem's mode block
+    {
+        T *F0 = F(0);
+        const long long base = (long long)r * N * nt * nmodes;
+        for (long long e = tid; e < (long long)N * nt * MB; e += NTH) {
+            const long long row = e / MB;  // n * nt + i
+            const int kk = (int)(e % MB);
+            F0[e] = (k0 + kk < nmodes) ? fin[base + row * nmodes + k0 + kk] : T(0);
+        }
+    }
+    __syncthreads();
+
+    // one damped block-Jacobi step on level l: TMP = smooth(u), then u = TMP
+    auto smooth = [&](int l, bool zero) {
+        const SpecCoefs<T> &c = lvc[l];
+        const int Nl = N >> l;
+        T *u = U(l);
+        const T *f = F(l);
+        for (int it = tid; it < Nl * MB; it += NTH) {
+            const int n = it / MB, kk = it % MB;
+            T uu[NTMAX], rr[NTMAX], v[NTMAX];
+#pragma unroll
+            for (int i = 0; i < NTMAX; ++i) {
+                uu[i] = (i < nt && !zero) ? u[(n * nt + i) * MB + kk] : T(0);
+                rr[i] = (i < nt) ? f[(n * nt + i) * MB + kk] : T(0);
+            }
+            const T up = (!zero && n > 0) ? u[(n * nt - 1) * MB + kk] : T(0);
+            spec_residual(c, mu[kk], uu, up, rr);
+            spec_block_solve(c, mu[kk], rr, v);
+#pragma unroll
+            for (int i = 0; i < NTMAX; ++i)
+                if (i < nt) TMP[(n * nt + i) * MB + kk] = uu[i] + omega * v[i];
+        }
+        __syncthreads();
+        for (long long e = tid; e < (long long)Nl * nt * MB; e += NTH) u[e] = TMP[e];
+        __syncthreads();
+    };
+
+    for (int l = 0; l < nlev - 1; ++l) {
+        for (int sidx = 0; sidx < nu1; ++sidx) smooth(l, sidx == 0);
+        if (nu1 == 0)
+            for (long long e = tid; e < (long long)(N >> l) * nt * MB; e += NTH) U(l)[e] = T(0);
+        // residual of slab pairs, restricted to level l + 1
+        const SpecCoefs<T> &c = lvc[l];
+        const int Nc = N >> (l + 1);
+        const T *u = U(l), *f = F(l);
+        T *fc = F(l + 1), *uc = U(l + 1);
+        __syncthreads();
+        for (int it = tid; it < Nc * MB; it += NTH) {
+            const int m = it / MB, kk = it % MB, a = 2 * m;
+            T ua[NTMAX], ub[NTMAX], ra[NTMAX], rb[NTMAX];
+#pragma unroll
+            for (int i = 0; i < NTMAX; ++i) {
+                const bool in = i < nt;
+                ua[i] = in ? u[(a * nt + i) * MB + kk] : T(0);
+                ub[i] = in ? u[((a + 1) * nt + i) * MB + kk] : T(0);
+                ra[i] = in ? f[(a * nt + i) * MB + kk] : T(0);
+                rb[i] = in ? f[((a + 1) * nt + i) * MB + kk] : T(0);
+            }
+            const T up = (a > 0) ? u[(a * nt - 1) * MB + kk] : T(0);
+            T ualast = T(0);
+#pragma unroll
+            for (int i = 0; i < NTMAX; ++i)
+                if (i == nt - 1) ualast = ua[i];
+            spec_residual(c, mu[kk], ua, up, ra);
+            spec_residual(c, mu[kk], ub, ualast, rb);
+#pragma unroll
+            for (int i = 0; i < NTMAX; ++i) {
+                if (i >= nt) break;
+                T sacc = T(0);
+#pragma unroll
+                for (int j = 0; j < NTMAX; ++j)
+                    if (j < nt) sacc += pc.P[j * NTMAX + i] * ra[j] + pc.P[(nt + j) * NTMAX + i] * rb[j];
+                fc[(m * nt + i) * MB + kk] = sacc;
+                uc[(m * nt + i) * MB + kk] = T(0);
+            }
+        }
+        __syncthreads();
+    }
+    // coarsest level: exact forward substitution over its slabs, per mode
+    {
+        const int l = nlev - 1, Nl = N >> l;
+        const SpecCoefs<T> &c = lvc[l];
+        T *u = U(l);
+        const T *f = F(l);
+        for (int kk = tid; kk < MB; kk += NTH) {
+            T prev = T(0);
+            for (int n = 0; n < Nl; ++n) {
+                T rr[NTMAX], v[NTMAX];
+#pragma unroll
+                for (int i = 0; i < NTMAX; ++i) rr[i] = (i < nt) ? f[(n * nt + i) * MB + kk] : T(0);
+                rr[0] += prev;
+                spec_block_solve(c, mu[kk], rr, v);
+#pragma unroll
+                for (int i = 0; i < NTMAX; ++i) {
+                    if (i < nt) u[(n * nt + i) * MB + kk] = v[i];
+                    if (i == nt - 1) prev = v[i];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int l = nlev - 2; l >= 0; --l) {
+        // prolongation of the coarse correction
+        const int Nc = N >> (l + 1);
+        T *u = U(l);
+        const T *uc = U(l + 1);
+        for (int it = tid; it < Nc * MB; it += NTH) {
+            const int m = it / MB, kk = it % MB;
+            T e[NTMAX];
+#pragma unroll
+            for (int i = 0; i < NTMAX; ++i) e[i] = (i < nt) ? uc[(m * nt + i) * MB + kk] : T(0);
+#pragma unroll
+            for (int j = 0; j < 2 * NTMAX; ++j) {
+                const int q = j / NTMAX, jj = j % NTMAX;
+                if (jj >= nt) continue;
+                T sacc = T(0);
+#pragma unroll
+                for (int i = 0; i < NTMAX; ++i)
+                    if (i < nt) sacc += pc.P[((q * nt) + jj) * NTMAX + i] * e[i];
+                u[((2 * m + q) * nt + jj) * MB + kk] += sacc;
+            }
+        }
+        __syncthreads();
+        for (int sidx = 0; sidx < nu2; ++sidx) smooth(l, false);
+    }
+    // store u^
+    {
+        const T *U0 = U(0);
+        const long long base = (long long)r * N * nt * nmodes;
+        for (long long e = tid; e < (long long)N * nt * MB; e += NTH) {
+            const long long row = e / MB;
+            const int kk = (int)(e % MB);
+            if (k0 + kk < nmodes) uout[base + row * nmodes + k0 + kk] = U0[e];
+        }
+    }
+}
+
+// Shared memory (elements) of k_spec_vcycle for a mode block of MB modes.
+static long long spec_vcycle_elems(int nlev, int N, int nt, int MB) {
+    long long e = MB;
+    for (int l = 0; l < nlev; ++l) e += 2LL * (N >> l) * nt * MB;
+    return e + (long long)N * nt * MB;
+}
+
+template <typename T>
+cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc, const T *const lam[3],
+                               const Grid &g, const ProlongCoefs<T> &pc, int nlev, int N, int nrhs,
+                               int nu1, int nu2, T omega, int max_smem, cudaStream_t s) {
+    // largest mode block that fits, at most 32 modes
+    int MB = 32;
+    while (MB > 1 && spec_vcycle_elems(nlev, N, pc.nt, MB) * (long long)sizeof(T) > max_smem) MB /= 2;
+    const long long bytes = spec_vcycle_elems(nlev, N, pc.nt, MB) * (long long)sizeof(T);
+    if (bytes > max_smem) return cudaErrorNotSupported;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_spec_vcycle<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long nblk = (g.nxyz + MB - 1) / MB;
+    const long long grid = nblk * nrhs;
+    if (grid <= 0) return cudaSuccess;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_spec_vcycle<T><<<(unsigned)grid, 256, (size_t)bytes, s>>>(fin, uout, lvc, lam[0], lam[1],
+                                                               lam[2], g, pc, nlev, N, MB, nu1,
+                                                               nu2, omega);
+    return cudaGetLastError();
+}
+
 // grid over (problem, mode); sequential over the level's slabs
 template <typename T>
 __global__ void __launch_bounds__(256)
@@ -244,7 +506,13 @@ cudaError_t launch_spec_coarse(T *u, const T *f, const T *const lam[3], const Gr
                                                      const ProlongCoefs<T> &, int, long long,  \
                                                      cudaStream_t);                            \
     template cudaError_t launch_spec_coarse<T>(T *, const T *, const T *const[3], const Grid &, \
-                                               const SpecCoefs<T> &, int, int, cudaStream_t);
+                                               const SpecCoefs<T> &, int, int, cudaStream_t);     \
+    template cudaError_t launch_mode_solve<T>(T *, const T *const[3], const Grid &,             \
+                                              const SpecCoefs<T> &, long long, cudaStream_t);     \
+    template cudaError_t launch_spec_vcycle<T>(const T *, T *, const SpecCoefs<T> *,            \
+                                               const T *const[3], const Grid &,                 \
+                                               const ProlongCoefs<T> &, int, int, int, int, int, \
+                                               T, int, cudaStream_t);
 ST_INST(double)
 ST_INST(float)
 #undef ST_INST

@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
 }
 
 template <int KIND, int MODE>
-static cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s, int nsm) {
+static cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s, int nsm, int ctas_per_sm) {
     constexpr int EPC = (KIND == tc::FMT_TF32) ? 4 : 8;
     const int KC = a.k_pad / EPC;
     const int wrows = (MODE == 0) ? 128 : a.n_pad;
@@ -227,6 +227,7 @@ static cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s, int nsm) {
     int per_sm = 512 / tmem_cols;
     const int by_smem = (int)((220 * 1024) / (smem + 1024));
     if (by_smem < per_sm) per_sm = by_smem;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     if (per_sm < 1) per_sm = 1;
     const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
     long long grid = (long long)nsm * per_sm;
@@ -240,7 +241,7 @@ static cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s, int nsm) {
 // covers (the caller then uses the CUDA-core transform).
 cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, const float *wt,
                            int n_in, int n_out, long long ncols, long long inner, int *err,
-                           int nsm, cudaStream_t s) {
+                           int nsm, cudaStream_t s, int ctas_per_sm) {
     TcArgs a;
     a.in = in;
     a.out = out;
@@ -257,8 +258,10 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
     if (mode == 0 && n_out > 128) return cudaErrorNotSupported;
     if (mode == 1 && a.n_pad > 256) return cudaErrorNotSupported;
     if (kind == tc::FMT_TF32)
-        return mode == 0 ? launch_tc_t<tc::FMT_TF32, 0>(a, s, nsm) : launch_tc_t<tc::FMT_TF32, 1>(a, s, nsm);
-    return mode == 0 ? launch_tc_t<tc::FMT_BF16, 0>(a, s, nsm) : launch_tc_t<tc::FMT_BF16, 1>(a, s, nsm);
+        return mode == 0 ? launch_tc_t<tc::FMT_TF32, 0>(a, s, nsm, ctas_per_sm)
+                         : launch_tc_t<tc::FMT_TF32, 1>(a, s, nsm, ctas_per_sm);
+    return mode == 0 ? launch_tc_t<tc::FMT_BF16, 0>(a, s, nsm, ctas_per_sm)
+                     : launch_tc_t<tc::FMT_BF16, 1>(a, s, nsm, ctas_per_sm);
 }
 
 }  // namespace st

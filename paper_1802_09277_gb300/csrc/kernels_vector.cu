@@ -69,40 +69,82 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// grid (nblk, nrhs), 256 threads = 8 warps; partial[(v*nrhs + r)*nblk + blk].
-// Block b owns a contiguous chunk of the rhs segment; warp g accumulates the
-// vectors v = g, g + 8, ... (FP64 sums, also for FP32 vectors), so every
-// vector is read from HBM once and the chunk of w is re-read from L1.
+// Per-thread accumulator of a dot product: FP64 for FP64 vectors; for FP32
+// vectors an FP32 sum with Kahan compensation (GB300's FP64 pipe is ~60x
+// slower than its FP32 pipe, so FP64 products would make the kernel
+// ALU-bound); partial sums are combined in FP64.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float y = fmaf(a, b, -c);
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// grid (nblk, nrhs, ceil(nv / 4)), 256 threads; partial[(v*nrhs + r)*nblk + blk].
+// Block (b, r, g) accumulates the dots of w with vectors 4g .. 4g+3 over a
+// grid-stride loop, two elements per load when vec2 is set.  w is re-read
+// by every group from L2.
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_multidot_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ w,
                        long long len, double *__restrict__ partial, int vec2) {
     using P2 = typename Pair<T>::V;
+    __shared__ double red[8][4];
     const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int v0 = 4 * blockIdx.z;
+    const int cnt = (nv - v0 < 4) ? nv - v0 : 4;
     const long long off = (long long)r * len;
-    long long chunk = (len + nblk - 1) / nblk;
-    chunk += chunk & 1;  // even, so pairs never cross chunks
-    const long long lo = (long long)blockIdx.x * chunk;
-    const long long hi = (lo + chunk < len) ? lo + chunk : len;
-    for (int v = warp; v < nv; v += 8) {
-        const T *x = vl.v[v] + off;
-        const T *wr = w + off;
-        double acc = 0.0;
-        if (vec2) {
-            const P2 *x2 = reinterpret_cast<const P2 *>(x);
-            const P2 *w2 = reinterpret_cast<const P2 *>(wr);
-#pragma unroll 4
-            for (long long i = lo / 2 + lane; i < hi / 2; i += 32) {
-                const P2 a = x2[i], b = w2[i];
-                acc += (double)a.x * (double)b.x + (double)a.y * (double)b.y;
-            }
-        } else {
-#pragma unroll 4
-            for (long long i = lo + lane; i < hi; i += 32) acc += (double)x[i] * (double)wr[i];
+    const T *x[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0] + off;
+    DotAcc<T> acc[4];
+    const long long stride = (long long)nblk * blockDim.x;
+    if (vec2) {
+        const P2 *w2 = reinterpret_cast<const P2 *>(w + off);
+        const long long np = len / 2;
+#pragma unroll 2
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
+            const P2 wi = w2[i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < cnt) {
+                    const P2 a = reinterpret_cast<const P2 *>(x[k])[i];
+                    acc[k].add(a.x, wi.x);
+                    acc[k].add(a.y, wi.y);
+                }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) partial[((long long)v * nrhs + r) * nblk + blockIdx.x] = acc;
+    } else {
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+            const T wi = w[off + i];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k < cnt) acc[k].add(x[k][i], wi);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double t = warp_sum(acc[k].value());
+        if (lane == 0) red[warp][k] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
+        partial[((long long)(v0 + threadIdx.x) * nrhs + r) * nblk + blockIdx.x] = t;
     }
 }
 
@@ -133,7 +175,8 @@ cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, 
         vl.v[i] = vecs[i];
         vec2 = vec2 && al(vecs[i]);
     }
-    k_multidot_partial<T><<<dim3(nblk, nrhs), 256, 0, s>>>(nv, vl, w, len, partial, vec2);
+    k_multidot_partial<T><<<dim3(nblk, nrhs, (nv + 3) / 4), 256, 0, s>>>(nv, vl, w, len, partial,
+                                                                        vec2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int count = nv * nrhs;
@@ -239,6 +282,32 @@ cudaError_t launch_scale(const double *x, double *y, const double *a, int nrhs, 
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (blocks <= 0) return cudaSuccess;
     k_scale<<<(unsigned)blocks, 256, 0, s>>>(x, y, sa, len, nrhs);
+    return cudaGetLastError();
+}
+
+// f[slab][t][z][y][x] = sum_k gt[k][slab][t] gz[k][z] gy[k][y] gx[k][x]
+__global__ void k_separable_sum(double *__restrict__ f, const double *__restrict__ g, int K,
+                                long long nslab_t, int nx, int ny, int nz, long long total) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const long long nxyz = (long long)nx * ny * nz;
+    const long long st = idx / nxyz, sp = idx % nxyz;
+    const int x = (int)(sp % nx), y = (int)((sp / nx) % ny), z = (int)(sp / ((long long)nx * ny));
+    const long long per = nslab_t + nx + ny + nz;
+    double acc = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double *gk = g + k * per;
+        acc += gk[st] * gk[nslab_t + x] * gk[nslab_t + nx + y] * gk[nslab_t + nx + ny + z];
+    }
+    f[idx] = acc;
+}
+
+cudaError_t launch_separable_sum(double *f, const double *g, int K, long long nslab_t, int nx,
+                                 int ny, int nz, cudaStream_t s) {
+    const long long total = nslab_t * nx * ny * nz;
+    if (total <= 0) return cudaSuccess;
+    k_separable_sum<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(f, g, K, nslab_t, nx, ny, nz,
+                                                                    total);
     return cudaGetLastError();
 }
 

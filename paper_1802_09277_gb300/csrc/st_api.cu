@@ -52,8 +52,13 @@ int fail(int code, const char *fmt, ...) {
 struct LevelHost {
     int nslab;  // slabs per problem
     double tau;
-    Mat Kt, Mt, X, Z, Y;
+    Mat Kt, Mt, X, Z, Y;  // real Schur factors (Sec. 3.5)
     std::vector<int> blk;
+    // diagonalisation (Sec. 3.3): eigenvalues, unit-column eigenvectors, Y = (M_t X)^{-1}
+    std::vector<double> lre, lim;
+    Mat Xre, Xim, Yre, Yim;
+    double condX = 0.0;
+    bool eig_ok = false;
 };
 
 template <typename T>
@@ -83,6 +88,14 @@ struct st_handle_s {
     bool host_only = false;
     bool mixed = false;
     int nsm = 152;
+    int max_smem = 48 * 1024;  // opt-in shared memory per block
+    SpecCoefs<float> *d_lvc32 = nullptr;   // per-level coefficients for the fused V-cycle
+    SpecCoefs<double> *d_lvc64 = nullptr;
+    // autotuned transform per axis: -1 = not tuned (heuristic), 0 = CUDA
+    // cores, k > 0 = tensor cores with at most k CTAs per SM
+    int tune[3] = {-1, -1, -1};
+    double tune_ms[3] = {0, 0, 0};
+    bool tuned = false;
     int *tc_err = nullptr;  // device flag: a tensor-core kernel's bounded wait ran out
     // host factors
     Mat M1[3], K1[3], U[3], Pt;
@@ -111,6 +124,15 @@ struct st_handle_s {
     // outer iteration
     std::vector<double *> V, Zk;
     std::vector<float *> V32, Z32;  // FP32 Krylov space of the refinement's inner solver
+    // CUDA graphs of the preconditioner, keyed by its (input, output) buffers
+    struct GraphRec {
+        const void *in;
+        void *out;
+        int uses;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphRec> graphs;
+    cudaStream_t cap_stream = nullptr;
     double *r64 = nullptr;
     float *rhs32 = nullptr, *e32 = nullptr;
     int krylov32_m = 0;
@@ -309,6 +331,19 @@ SpecCoefs<T> pack_spec(st_handle h, int l) {
         c.blk[i] = L.blk[i];
     }
     c.nt = nt;
+    c.variant = h->opt.variant;
+    if (h->opt.variant == ST_EIG) {
+        for (int i = 0; i < nt; ++i) {
+            for (int j = 0; j < nt; ++j) {
+                c.X[i * NTMAX + j] = (T)L.Xre[i * nt + j];
+                c.Xi[i * NTMAX + j] = (T)L.Xim[i * nt + j];
+                c.Y[i * NTMAX + j] = (T)L.Yre[i * nt + j];
+                c.Yi[i * NTMAX + j] = (T)L.Yim[i * nt + j];
+            }
+            c.lre[i] = (T)L.lre[i];
+            c.lim[i] = (T)L.lim[i];
+        }
+    }
     return c;
 }
 
@@ -360,14 +395,15 @@ int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long lon
     const long long inner = (axis == 0) ? 1 : (axis == 1) ? nx : nx * ny;
     const long long outer = (long long)(E / (double)(n * inner) + 0.5);
     const int prec = h->opt.precision;
-    if (sizeof(T) == 4 && (prec == ST_MIXED_TF32 || prec == ST_MIXED_BF16)) {
+    if (sizeof(T) == 4 && (prec == ST_MIXED_TF32 || prec == ST_MIXED_BF16) && h->tune[axis] != 0) {
         const float *Wt = (const float *)(forward ? ds.Ut[axis] : ds.U[axis]);
         const int kind = (prec == ST_MIXED_TF32) ? 2 : 1;
         const long long ncols = (axis == 0) ? outer : outer * inner;
         KScope ks(h, ST_PROF_TC, sizeof(T) * (2.0 * E + n * n), 2.0 * E * n);
         const cudaError_t e = launch_tc_axis(kind, axis == 0 ? 0 : 1, (const float *)in,
                                              (float *)out, Wt, (int)n, (int)n, ncols, inner,
-                                             h->tc_err, h->nsm, h->stream);
+                                             h->tc_err, h->nsm, h->stream,
+                                             h->tune[axis] > 0 ? h->tune[axis] : 0);
         if (e == cudaSuccess) return ST_OK;
         if (e != cudaErrorNotSupported) CK(e);
         cudaGetLastError();
@@ -397,6 +433,51 @@ int spatial(st_handle h, const T *in, T *t0, T *t1, bool forward, long long plan
     return ST_OK;
 }
 
+// Autotuner: time every candidate for each axis pass of the FP32 transform on
+// the level-0 buffers (CUDA-event medians of 3 runs) and keep the fastest.
+int autotune(st_handle h) {
+    if (!h->mixed) {
+        h->tuned = true;
+        return ST_OK;
+    }
+    const bool tc_ok = h->opt.precision == ST_MIXED_TF32 || h->opt.precision == ST_MIXED_BF16;
+    const long long planes = (long long)h->N * h->nrhs * h->nt;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const bool prof = h->prof_on;
+    h->prof_on = false;
+    for (int ax = 0; ax < h->dim; ++ax) {
+        double best = 1e30;
+        int best_c = 0;
+        // only candidates that give identical numbers (the CTA count of the
+        // tensor-core kernel); CUDA cores vs tensor cores is set by the mode
+        for (int c = tc_ok ? 1 : 0; c <= (tc_ok ? 4 : 0); ++c) {
+            h->tune[ax] = c;
+            float t[3];
+            for (int rep = 0; rep < 4; ++rep) {
+                CK(cudaEventRecord(e0, h->stream));
+                CKS(axis_pass<float>(h, ax, h->w32.w0, h->w32.w1, true, planes));
+                CK(cudaEventRecord(e1, h->stream));
+                CK(cudaEventSynchronize(e1));
+                if (rep > 0) CK(cudaEventElapsedTime(&t[rep - 1], e0, e1));
+            }
+            std::sort(t, t + 3);
+            if (t[1] < best) {
+                best = t[1];
+                best_c = c;
+            }
+        }
+        h->tune[ax] = best_c;
+        h->tune_ms[ax] = best;
+    }
+    h->prof_on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tuned = true;
+    return ST_OK;
+}
+
 // Damped block-Jacobi step on slabs [s0, s0+ns) of level l:
 // u <- (overwrite ? 0 : u) + omega A^{-1} (f - L u)  (A^{-1} by Eq. 3.1 + FD)
 template <typename T>
@@ -405,12 +486,21 @@ int smooth_range(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns, 
     DevSpace<T> &ds = space<T>(h);
     const long long sl = (long long)h->nt * h->g.nxyz;  // elements per slab
     T *w0 = w.w0 + s0 * sl, *w1 = w.w1 + s0 * sl;
-    CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, true, s0, ns));
+    const bool eig = h->opt.variant == ST_EIG;
+    // real Schur: Y fused into the residual, shift solve with Z, X in the
+    // update; diagonalisation: the complex Y, shifts and X all per mode
+    CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, !eig, s0, ns));
     T *fw = nullptr, *bz = nullptr;
     CKS(spatial<T>(h, w0, w1, w0, true, (long long)ns * h->nt, &fw));
-    const SchurCoefs<T> sc = pack_schur<T>(h, l);
+    SchurCoefs<T> sc = pack_schur<T>(h, l);
     const double E = (double)ns * h->nt * h->g.nxyz;
-    {
+    if (eig) {
+        const SpecCoefs<T> c = pack_spec<T>(h, l);
+        KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 2.0 * E, E * (5.0 * h->nt + 4.0));
+        CK(launch_mode_solve<T>(fw, ds.lam, h->g, c, ns, h->stream));
+        for (int i = 0; i < NTMAX; ++i)
+            for (int j = 0; j < NTMAX; ++j) sc.X[i * NTMAX + j] = (i == j) ? T(1) : T(0);
+    } else {
         KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 2.0 * E, E * (h->nt + 2.0));
         CK(launch_shift_solve<T>(fw, ds.lam[0], ds.lam[1], ds.lam[2], h->g, sc, ns, h->stream));
     }
@@ -547,6 +637,33 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     return ST_OK;
 }
 
+template <typename T>
+const SpecCoefs<T> *dev_lvc(st_handle h);
+template <>
+const SpecCoefs<double> *dev_lvc<double>(st_handle h) { return h->d_lvc64; }
+template <>
+const SpecCoefs<float> *dev_lvc<float>(st_handle h) { return h->d_lvc32; }
+
+// Top of the eigenbasis V-cycle from zero: the whole V-cycle in one
+// shared-memory kernel when a mode's levels fit (opt.fused_vcycle), else the
+// level-by-level kernels.
+template <typename T>
+int svcycle_top(st_handle h, T *u, const T *f, T *tmp) {
+    if (h->opt.fused_vcycle) {
+        const double E = (double)h->len * h->nrhs;
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E,
+                  E * 2.0 * (h->opt.nu1 + h->opt.nu2 + 1) * (7.0 * h->nt + 6.0));
+        const cudaError_t e = launch_spec_vcycle<T>(f, u, dev_lvc<T>(h), space<T>(h).lam, h->g,
+                                                    pack_prolong<T>(h), h->nlev, h->N, h->nrhs,
+                                                    h->opt.nu1, h->opt.nu2, (T)h->opt.omega,
+                                                    h->max_smem, h->stream);
+        if (e == cudaSuccess) return ST_OK;
+        if (e != cudaErrorNotSupported) CK(e);
+        cudaGetLastError();
+    }
+    return svcycle<T>(h, 0, u, f, tmp, true);
+}
+
 // z = (I (x) U) V^( (I (x) U^T) v ), FP64 at the interface
 template <typename T>
 int precondition_spectral(st_handle h, const double *v, double *z);
@@ -559,7 +676,7 @@ int precondition_spectral<double>(st_handle h, const double *v, double *z) {
     double *fh = nullptr, *e = nullptr;
     CKS(spatial<double>(h, v, w.w0, w.w1, true, planes, &fh));
     double *tmp = (fh == w.w0) ? w.w1 : w.w0;
-    CKS(svcycle<double>(h, 0, w.u[0], fh, tmp, true));
+    CKS(svcycle_top<double>(h, w.u[0], fh, tmp));
     double *t0 = (h->dim % 2 == 1) ? z : w.w0, *t1 = (h->dim % 2 == 1) ? w.w0 : z;
     CKS(spatial<double>(h, w.u[0], t0, t1, false, planes, &e));
     if (e != z) CK(cudaMemcpyAsync(z, e, sizeof(double) * h->len * h->nrhs, cudaMemcpyDeviceToDevice, h->stream));
@@ -575,7 +692,7 @@ int precondition_spectral_f32(st_handle h, const double *v, double *z) {
     float *fh = nullptr, *e = nullptr;
     CKS(spatial<float>(h, w.w0, w.w1, w.f[0], true, planes, &fh));
     float *tmp = (fh == w.w1) ? w.w0 : w.w1;
-    CKS(svcycle<float>(h, 0, w.u[0], fh, tmp, true));
+    CKS(svcycle_top<float>(h, w.u[0], fh, tmp));
     float *t0 = (fh == w.w0) ? w.w1 : w.w0;
     float *t1 = (fh == w.f[0]) ? ((t0 == w.w0) ? w.w1 : w.w0) : w.f[0];
     CKS(spatial<float>(h, w.u[0], t0, t1, false, planes, &e));
@@ -619,6 +736,48 @@ int ensure_krylov(st_handle h) {
         h->Zk.push_back((double *)p);
     }
     h->krylov_m = m;
+    return ST_OK;
+}
+
+// Run fn() (which enqueues on h->stream) as a CUDA graph keyed by (in, out):
+// the first use runs eagerly, the second captures and instantiates a graph on
+// a private stream, later uses launch it.  Eager while profiling is on.
+template <typename Fn>
+int run_graphed(st_handle h, const void *in, void *out, Fn fn) {
+    if (h->prof_on || !h->opt.use_graphs) return fn();
+    st_handle_s::GraphRec *g = nullptr;
+    for (auto &r : h->graphs)
+        if (r.in == in && r.out == out) g = &r;
+    if (!g) {
+        h->graphs.push_back({in, out, 0, nullptr});
+        g = &h->graphs.back();
+    }
+    if (g->exec) {
+        CK(cudaGraphLaunch(g->exec, h->stream));
+        return ST_OK;
+    }
+    if (g->uses++ == 0) return fn();
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    // order the capture after prior work on the handle's stream
+    CK(cudaStreamSynchronize(h->stream));
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = fn();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->cap_stream, &graph);
+    h->stream = user;
+    if (rc != ST_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    CK(ec);
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ei);
+    g->exec = exec;
+    CK(cudaGraphLaunch(g->exec, h->stream));
     return ST_OK;
 }
 
@@ -818,7 +977,9 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
     auto apply = [h](const double *z, double *w) {
         return stencil<double>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, h->N * h->nrhs);
     };
-    auto prec = [h](const double *v, double *z) { return precondition(h, v, z); };
+    auto prec = [h](const double *v, double *z) {
+        return run_graphed(h, v, z, [h, v, z] { return precondition(h, v, z); });
+    };
     CKS(fgmres_core<double>(h, rhs, u, tol, h->opt.max_it, h->V, Z, apply, prec, skip, &its,
                             &worst));
     info->iterations = its;
@@ -835,7 +996,7 @@ int precondition32(st_handle h, const float *v, float *z) {
     float *fh = nullptr, *e = nullptr;
     CKS(spatial<float>(h, v, w.w0, w.w1, true, planes, &fh));
     float *tmp = (fh == w.w0) ? w.w1 : w.w0;
-    CKS(svcycle<float>(h, 0, w.u[0], fh, tmp, true));
+    CKS(svcycle_top<float>(h, w.u[0], fh, tmp));
     float *t0 = (h->dim % 2 == 1) ? z : w.f[0], *t1 = (h->dim % 2 == 1) ? w.f[0] : z;
     CKS(spatial<float>(h, w.u[0], t0, t1, false, planes, &e));
     if (e != z) CK(cudaMemcpyAsync(z, e, sizeof(float) * h->len * h->nrhs, cudaMemcpyDeviceToDevice, h->stream));
@@ -880,7 +1041,9 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
     auto apply = [h](const float *z, float *w) {
         return stencil<float>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, h->N * h->nrhs);
     };
-    auto prec = [h](const float *v, float *z) { return precondition32(h, v, z); };
+    auto prec = [h](const float *v, float *z) {
+        return run_graphed(h, v, z, [h, v, z] { return precondition32(h, v, z); });
+    };
     const long long n0 = h->len * R;
     for (;;) {
         CKS(residual64(h, u, rhs, h->r64));
@@ -938,6 +1101,8 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         return fail(ST_ERR_INVALID_ARG, "bad precision");
     if (o.basis != ST_BASIS_NODAL && o.basis != ST_BASIS_SPECTRAL)
         return fail(ST_ERR_INVALID_ARG, "bad basis");
+    if (o.variant != ST_RSCHUR && o.variant != ST_EIG)
+        return fail(ST_ERR_INVALID_ARG, "bad variant");
     if (o.outer < ST_OUTER_FGMRES || o.outer > ST_OUTER_IR)
         return fail(ST_ERR_INVALID_ARG, "bad outer iteration");
     if (!(o.inner_tol > 0) || o.inner_tol >= 1)
@@ -1023,6 +1188,22 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
             re = L.Z[i * nt + i];
             if (!(re > 0)) return fail(ST_ERR_NOT_POSITIVE, "Re lambda <= 0 on level with %d slabs (use a smaller theta)", Nl);
         }
+        // diagonalisation from the Schur form (Sec. 3.3): X, Y = (M_t X)^{-1}
+        {
+            std::string e2;
+            L.eig_ok = host::schur_eigvecs(nt, L.X, L.Z, L.blk, L.lre, L.lim, L.Xre, L.Xim, e2);
+            if (L.eig_ok) {
+                Mat MXr = host::matmul(nt, L.Mt, L.Xre), MXi = host::matmul(nt, L.Mt, L.Xim);
+                L.eig_ok = host::complex_inverse(nt, MXr, MXi, L.Yre, L.Yim);
+                L.condX = host::complex_cond2(nt, L.Xre, L.Xim);
+            }
+            if (o.variant == ST_EIG) {
+                if (!L.eig_ok) return fail(ST_ERR_ILL_CONDITIONED, "diagonalisation failed: %s", e2.c_str());
+                if (!(L.condX <= 1e8))
+                    return fail(ST_ERR_ILL_CONDITIONED, "cond(X) = %.3e > 1e8 on the level with %d slabs "
+                                "(use the real Schur variant)", L.condX, Nl);
+            }
+        }
         // Y = (M_t X)^{-1}
         Mat MX = host::matmul(nt, L.Mt, L.X);
         L.Y.assign(nt * nt, 0.0);
@@ -1032,8 +1213,10 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         Mat KX = host::matmul(nt, L.Kt, L.X), MXZ = host::matmul(nt, MX, L.Z);
         double rr = 0;
         for (int i = 0; i < nt * nt; ++i) rr = std::max(rr, std::fabs(KX[i] - MXZ[i]));
-        if (rr > 1e-11 * std::max(1.0, host::frob(L.Kt)))
-            return fail(ST_ERR_ILL_CONDITIONED, "time factor residual %.2e", rr);
+        // backward-error scale of K_t X = M_t X Z: ||K_t|| + ||M_t|| ||Z||
+        const double scale = host::frob(L.Kt) + host::frob(L.Mt) * host::frob(L.Z);
+        if (rr > 1e-12 * nt * scale)
+            return fail(ST_ERR_ILL_CONDITIONED, "time factor residual %.2e (scale %.2e)", rr, scale);
         h->lv.push_back(L);
         if (Nl % 2 != 0 || Nl == 1) break;
         Nl /= 2;
@@ -1070,7 +1253,26 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     } else {
         CKS(alloc_work<double>(h, h->w64, true));
     }
-    h->nblk_dot = 8 * h->nsm;
+    {
+        int dev = 0, ms = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&ms, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        h->max_smem = ms > 0 ? ms : 48 * 1024;
+        std::vector<SpecCoefs<double>> c64(h->nlev);
+        std::vector<SpecCoefs<float>> c32(h->nlev);
+        for (int l = 0; l < h->nlev; ++l) {
+            c64[l] = pack_spec<double>(h, l);
+            c32[l] = pack_spec<float>(h, l);
+        }
+        void *q;
+        CKS(dalloc(h, sizeof(SpecCoefs<double>) * h->nlev, &q));
+        h->d_lvc64 = (SpecCoefs<double> *)q;
+        CK(cudaMemcpy(q, c64.data(), sizeof(SpecCoefs<double>) * h->nlev, cudaMemcpyHostToDevice));
+        CKS(dalloc(h, sizeof(SpecCoefs<float>) * h->nlev, &q));
+        h->d_lvc32 = (SpecCoefs<float> *)q;
+        CK(cudaMemcpy(q, c32.data(), sizeof(SpecCoefs<float>) * h->nlev, cudaMemcpyHostToDevice));
+    }
+    h->nblk_dot = 2 * h->nsm;
     void *p;
     CKS(dalloc(h, sizeof(double) * MAXV * h->nrhs * h->nblk_dot, &p));
     h->partial = (double *)p;
@@ -1147,6 +1349,10 @@ void st_options_default(st_options *o) {
     o->hbm_budget = 0;
     o->basis = ST_BASIS_NODAL;
     o->inner_tol = 1e-4;
+    o->use_graphs = 1;
+    o->variant = ST_RSCHUR;
+    o->autotune = 1;
+    o->fused_vcycle = 1;
 }
 
 const char *st_last_error(void) { return g_err.c_str(); }
@@ -1185,6 +1391,9 @@ int st_setup_host(st_handle *out, int geometry, int degree, const int *spans, in
 
 void st_destroy(st_handle h) {
     if (!h) return;
+    for (auto &g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (void *p : h->allocs) cudaFree(p);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -1227,6 +1436,54 @@ int st_load_coeffs(st_handle h, const double *c, double *f) {
     CKS(check_ptr(h, f, "f"));
     if ((const void *)c == (void *)f) return fail(ST_ERR_INVALID_ARG, "c and f alias");
     return stencil<double>(h, 0, c, nullptr, f, MODE_MASS, false, 0, h->N * h->nrhs);
+}
+
+int st_load_gaussians(st_handle h, int nbumps, const double *centers, const double *widths,
+                      const double *amps, double *f) {
+    CKS(check_ptr(h, f, "f"));
+    if (nbumps < 0 || (nbumps > 0 && (!centers || !widths || !amps)))
+        return fail(ST_ERR_INVALID_ARG, "bad bump arrays");
+    const int d = h->dim, nt = h->nt, N = h->N, ne = h->opt.ne_per_slab, p = h->p;
+    const long long nst = (long long)N * nt;
+    const long long per = nst + h->n[0] + h->n[1] + h->n[2];
+    if ((long long)nbumps * per > h->len * h->nrhs)
+        return fail(ST_ERR_INVALID_ARG, "too many bumps for the work space");
+    const double tau = h->opt.T / N, delta = h->opt.theta * tau / ne;
+    const int npts = 2 * p + 4;
+    std::vector<double> g((size_t)nbumps * per, 0.0);
+    for (int k = 0; k < nbumps; ++k) {
+        const double w = widths[k], a = amps[k];
+        if (!(w > 0)) return fail(ST_ERR_INVALID_ARG, "bump width must be > 0");
+        double *gk = g.data() + (size_t)k * per;
+        const double ct = centers[k * (d + 1) + d];
+        auto ft = [=](double t) { return a * std::exp(-(t - ct) * (t - ct) / (2 * w * w)); };
+        for (int n = 0; n < N; ++n) {
+            const std::vector<double> gt = host::load_1d(n * tau, (n + 1) * tau, ne, p, delta, false, npts, ft);
+            for (int j = 0; j < nt; ++j) gk[(size_t)n * nt + j] = gt[j];
+        }
+        long long off = nst;
+        for (int ax = 0; ax < 3; ++ax) {
+            if (ax < d) {
+                const double c = centers[k * (d + 1) + ax];
+                auto fx = [=](double x) { return std::exp(-(x - c) * (x - c) / (2 * w * w)); };
+                const std::vector<double> gx = host::load_1d(0.0, 1.0, h->spans[ax], p, 0.0, true, npts, fx);
+                for (int i = 0; i < h->n[ax]; ++i) gk[off + i] = gx[i];
+            } else {
+                gk[off] = 1.0;
+            }
+            off += h->n[ax];
+        }
+    }
+    if (nbumps == 0) {
+        CK(launch_zero<double>(f, h->len * h->nrhs, h->stream));
+        return ST_OK;
+    }
+    double *dg = h->w64.w0;  // the handle's FP64 scratch holds the 1D loads
+    CK(cudaMemcpyAsync(dg, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    for (int r = 0; r < h->nrhs; ++r)
+        CK(launch_separable_sum(f + r * h->len, dg, nbumps, nst, h->n[0], h->n[1], h->n[2], h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // g (host) must outlive the copy
+    return ST_OK;
 }
 
 int st_smooth(st_handle h, double *u, const double *f, int nsteps) {
@@ -1278,6 +1535,7 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
     st_solve_info local;
     if (!info) info = &local;
     std::memset(info, 0, sizeof *info);
+    if (h->opt.autotune && !h->tuned) CKS(autotune(h));
     const auto t0 = std::chrono::steady_clock::now();
     try {
         if (!use_guess) CK(launch_zero<double>(u, h->len * h->nrhs, h->stream));
@@ -1422,6 +1680,28 @@ int st_space_factors(st_handle h, int axis, int *n, double *M1, double *K1, doub
     if (K1) std::memcpy(K1, h->K1[axis].data(), b);
     if (U) std::memcpy(U, h->U[axis].data(), b);
     if (lam) std::memcpy(lam, h->lam[axis].data(), sizeof(double) * nn);
+    return ST_OK;
+}
+
+int st_autotune(st_handle h, int *choice, double *ms) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (h->host_only) return fail(ST_ERR_INVALID_ARG, "handle was built host-only");
+    CKS(autotune(h));
+    for (int a = 0; a < 3; ++a) {
+        if (choice) choice[a] = a < h->dim ? h->tune[a] : -1;
+        if (ms) ms[a] = a < h->dim ? h->tune_ms[a] : 0.0;
+    }
+    return ST_OK;
+}
+
+int st_time_spectrum(st_handle h, int lvl, double *lam_re, double *lam_im, double *cond_x) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (lvl < 0 || lvl >= h->nlev) return fail(ST_ERR_INVALID_ARG, "level out of range");
+    const LevelHost &L = h->lv[lvl];
+    if (!L.eig_ok) return fail(ST_ERR_ILL_CONDITIONED, "no eigen-decomposition on this level");
+    if (lam_re) std::memcpy(lam_re, L.lre.data(), sizeof(double) * h->nt);
+    if (lam_im) std::memcpy(lam_im, L.lim.data(), sizeof(double) * h->nt);
+    if (cond_x) *cond_x = L.condX;
     return ST_OK;
 }
 

@@ -49,7 +49,10 @@ struct SchurCoefs {
     int nt;
 };
 
-// Time factors of one level for the eigenbasis (spectral) V-cycle
+// Time factors of one level for the per-mode block solve
+// (K_t + mu M_t)^{-1} = X (Z + mu I)^{-1} Y.  variant 0: real Schur (Z quasi
+// triangular, X, Y real); variant 1: diagonalisation (complex eigenvalues
+// lre + i lim, X = Xr + i Xi, Y = Y + i Yi).
 template <typename T>
 struct SpecCoefs {
     T Kt[NTMAX * NTMAX];
@@ -57,8 +60,13 @@ struct SpecCoefs {
     T Y[NTMAX * NTMAX];
     T Z[NTMAX * NTMAX];
     T X[NTMAX * NTMAX];
+    T Yi[NTMAX * NTMAX];
+    T Xi[NTMAX * NTMAX];
+    T lre[NTMAX];
+    T lim[NTMAX];
     int blk[NTMAX];
     int nt;
+    int variant;
 };
 
 template <typename T>
@@ -110,7 +118,7 @@ cudaError_t launch_prolong_add(const T *ec, T *uf, const ProlongCoefs<T> &pc, co
 // shape is not covered.
 cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, const float *wt,
                            int n_in, int n_out, long long ncols, long long inner, int *err,
-                           int nsm, cudaStream_t s);
+                           int nsm, cudaStream_t s, int ctas_per_sm = 0);
 
 // ---- eigenbasis V-cycle kernels (kernels_spectral.cu) ----
 template <typename T>
@@ -122,6 +130,18 @@ cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *con
                                      const Grid &g, const SpecCoefs<T> &c,
                                      const ProlongCoefs<T> &pc, int slabs_per_prob,
                                      long long ncoarse, cudaStream_t s);
+// the whole eigenbasis V-cycle in shared memory (one launch); lvc: device
+// array of the nlev levels' coefficients; cudaErrorNotSupported if one mode's
+// levels do not fit in max_smem bytes
+template <typename T>
+cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc, const T *const lam[3],
+                               const Grid &g, const ProlongCoefs<T> &pc, int nlev, int N, int nrhs,
+                               int nu1, int nu2, T omega, int max_smem, cudaStream_t s);
+
+// in place per (slab, mode): w <- (K_t + mu_k M_t)^{-1} w
+template <typename T>
+cudaError_t launch_mode_solve(T *w, const T *const lam[3], const Grid &g, const SpecCoefs<T> &c,
+                              long long nslabs, cudaStream_t s);
 template <typename T>
 cudaError_t launch_spec_coarse(T *u, const T *f, const T *const lam[3], const Grid &g,
                                const SpecCoefs<T> &c, int slabs_per_prob, int nprob,
@@ -141,6 +161,11 @@ cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, 
 template <typename T>
 cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int nrhs,
                              long long len, T *y, cudaStream_t s, const double *post = nullptr);
+
+// f = sum_k gt_k (x) gz_k (x) gy_k (x) gx_k, g packed per k as
+// [nslab_t | nx | ny | nz] doubles
+cudaError_t launch_separable_sum(double *f, const double *g, int K, long long nslab_t, int nx,
+                                 int ny, int nz, cudaStream_t s);
 
 // y (FP64) += a_r * x (FP32) per rhs r
 cudaError_t launch_axpy_f32_f64(const float *x, double *y, const double *a, int nrhs,

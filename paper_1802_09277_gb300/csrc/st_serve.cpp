@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -134,7 +135,8 @@ bool evict_one(st_server_s *s) {
 }
 
 void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const st_solve_info *info,
-            Entry *e, Clock::time_point admitted, const std::vector<std::vector<double>> *u) {
+            Entry *e, Clock::time_point admitted, const std::vector<std::vector<double>> *u,
+            const std::string &msg = std::string()) {
     const auto now = Clock::now();
     for (size_t i = 0; i < batch.size(); ++i) {
         Done &d = s->results[batch[i].ticket];
@@ -148,6 +150,7 @@ void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const
         d.res.latency_seconds = std::chrono::duration<double>(now - batch[i].submitted).count();
         d.res.batch_size = (int)batch.size();
         d.res.n_dofs = (int64_t)batch[i].rhs.size();
+        std::snprintf(d.res.error, sizeof d.res.error, "%s", status == ST_OK ? "" : msg.c_str());
         if (u) d.u = (*u)[i];
     }
     (void)e;
@@ -179,6 +182,7 @@ void worker(st_server_s *s) {
         // find or create a setup
         Entry *e = nullptr;
         int rc = ST_OK;
+        std::string why;
         for (;;) {
             e = nullptr;
             for (auto &c : s->cache)
@@ -189,6 +193,7 @@ void worker(st_server_s *s) {
             if (e) break;
             rc = make_entry(s, key, R, &e);
             if (rc == ST_OK) break;
+            why = std::string("setup: ") + st_last_error();
             if (rc != ST_ERR_OVER_BUDGET && rc != ST_ERR_OOM) break;
             if (evict_one(s)) continue;
             if (s->busy_workers > 0) {  // wait for running solves to release memory
@@ -196,10 +201,14 @@ void worker(st_server_s *s) {
                 continue;
             }
             rc = ST_ERR_OVER_BUDGET;
+            char buf[200];
+            std::snprintf(buf, sizeof buf, "does not fit the HBM budget (%zu of %zu bytes held; %s)",
+                          s->used, s->budget, why.c_str());
+            why = buf;
             break;
         }
         if (rc != ST_OK) {
-            finish(s, batch, rc, nullptr, nullptr, Clock::now(), nullptr);
+            finish(s, batch, rc, nullptr, nullptr, Clock::now(), nullptr, why);
             s->cv.notify_all();
             continue;
         }
@@ -230,8 +239,9 @@ void worker(st_server_s *s) {
         }
         if (st == ST_ERR_CUDA) cudaGetLastError();
 
+        const std::string solve_msg = (st == ST_OK) ? std::string() : std::string(st_last_error());
         lock.lock();
-        finish(s, batch, st, &info, e, admitted, &u);
+        finish(s, batch, st, &info, e, admitted, &u, solve_msg);
         e->busy = false;
         --s->busy_workers;
         s->cv.notify_all();

@@ -27,13 +27,14 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--basis", default="nodal", choices=["nodal", "spectral"])
+    ap.add_argument("--outer", default="fgmres", choices=["fgmres", "mg", "ir"])
     args = ap.parse_args()
 
     import torch
     from paper_1802_09277_gb300 import inputs, st
 
     s = st.Solver(args.dim, args.degree, args.spans, args.slabs, ne_per_slab=args.ne,
-                  precision=args.precision, basis=args.basis)
+                  precision=args.precision, basis=args.basis, outer=args.outer)
     n = s.ndofs
     x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
     f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")

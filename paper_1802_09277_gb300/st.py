@@ -19,12 +19,13 @@ GEOMETRY = {1: 1, 2: 2, 3: 3}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
 OUTER = {"fgmres": 0, "mg": 1, "ir": 2}
 BASIS = {"nodal": 0, "spectral": 1}
+VARIANT = {"rschur": 0, "eig": 1}
 
 # every symbol declared in include/st_iga.h
 SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",
-           "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_smooth",
+           "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_load_gaussians", "st_smooth",
            "st_smooth_static", "st_vcycle",
-           "st_solve", "st_profile", "st_profile_read", "st_time_factors", "st_space_factors",
+           "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
            "st_time_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_poll", "st_serve_wait", "st_serve_stop"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
@@ -37,7 +38,9 @@ class StOptions(ctypes.Structure):
                 ("precision", ctypes.c_int), ("outer", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("max_it", ctypes.c_int),
                 ("nrhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("basis", ctypes.c_int),
-                ("inner_tol", ctypes.c_double)]
+                ("inner_tol", ctypes.c_double), ("use_graphs", ctypes.c_int),
+                ("variant", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("fused_vcycle", ctypes.c_int)]
 
 
 class StSolveInfo(ctypes.Structure):
@@ -62,7 +65,7 @@ class StResult(ctypes.Structure):
                 ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("queue_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
                 ("latency_seconds", ctypes.c_double), ("batch_size", ctypes.c_int),
-                ("n_dofs", ctypes.c_int64)]
+                ("n_dofs", ctypes.c_int64), ("error", ctypes.c_char * 128)]
 
 
 ST_ERR_NOT_READY = -10
@@ -100,13 +103,16 @@ def load():
         "st_apply": (I, [P, P, P]),
         "st_residual": (I, [P, P, P, P]),
         "st_load_coeffs": (I, [P, P, P]),
+        "st_load_gaussians": (I, [P, I, dp, dp, dp, P]),
         "st_smooth": (I, [P, P, P, I]),
         "st_smooth_static": (I, [P, P, P, I, P]),
         "st_vcycle": (I, [P, P, P]),
         "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
+        "st_autotune": (I, [P, ip, dp]),
         "st_profile": (I, [P, I]),
         "st_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]),
         "st_time_factors": (I, [P, I, ip, dp, dp, dp, dp, dp]),
+        "st_time_spectrum": (I, [P, I, dp, dp, dp]),
         "st_space_factors": (I, [P, I, ip, dp, dp, dp, dp]),
         "st_time_prolongation": (I, [P, ip, dp]),
         "st_last_error": (ctypes.c_char_p, []),
@@ -143,6 +149,8 @@ def options(**kw):
             v = OUTER[v]
         if k == "basis" and isinstance(v, str):
             v = BASIS[v]
+        if k == "variant" and isinstance(v, str):
+            v = VARIANT[v]
         setattr(o, k, v)
     return o
 
@@ -213,6 +221,15 @@ class Solver:
     def load_coeffs(self, c, f):
         _check(_lib.st_load_coeffs(self._h, _dptr(c, self.ndofs, "c"), _dptr(f, self.ndofs, "f")))
 
+    def load_gaussians(self, centers, widths, amps, f):
+        import numpy as np
+        c = np.ascontiguousarray(centers, dtype=np.float64)
+        w = np.ascontiguousarray(widths, dtype=np.float64)
+        a = np.ascontiguousarray(amps, dtype=np.float64)
+        dpp = lambda z: z.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(_lib.st_load_gaussians(self._h, len(w), dpp(c), dpp(w), dpp(a),
+                                      _dptr(f, self.ndofs, "f")))
+
     def smooth(self, u, f, nsteps=1):
         _check(_lib.st_smooth(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f"),
                               int(nsteps)))
@@ -240,6 +257,14 @@ class Solver:
                 "status": info.status,
                 "rel_residual": info.rel_residual, "seconds": info.seconds, "rc": rc}
 
+    def autotune(self):
+        """Per axis: (choice, ms per pass); choice 0 = CUDA cores, k > 0 =
+        tensor cores with k CTAs per SM."""
+        ch = (ctypes.c_int * 3)()
+        ms = (ctypes.c_double * 3)()
+        _check(_lib.st_autotune(self._h, ch, ms))
+        return [(ch[a], ms[a]) for a in range(self.dim)]
+
     def profile(self, enable):
         """Start (reset) or stop per-kernel-class event timing."""
         _check(_lib.st_profile(self._h, int(bool(enable))))
@@ -265,6 +290,15 @@ class Solver:
         k = ctypes.c_int()
         _check(_lib.st_time_factors(self._h, int(level), ctypes.byref(k), *ptrs))
         return dict(zip(["Kt", "Mt", "X", "Z", "Y"], mats))
+
+    def time_spectrum(self, level=0):
+        """(eigenvalues (complex array), cond2 of the unit-column eigenvectors)."""
+        import numpy as np
+        re, im = np.zeros(self.nt), np.zeros(self.nt)
+        c = ctypes.c_double()
+        dpp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(_lib.st_time_spectrum(self._h, int(level), dpp(re), dpp(im), ctypes.byref(c)))
+        return re + 1j * im, c.value
 
     def space_factors(self, axis=0):
         import numpy as np
@@ -328,6 +362,7 @@ class Server:
         _check(rc)
         del self._n[ticket]
         out = {k: getattr(res, k) for k, _ in StResult._fields_}
+        out["error"] = res.error.decode(errors="replace")
         return out, u
 
     def poll(self, ticket):

@@ -40,6 +40,24 @@ def relerr(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+_HIER = {}
+
+
+def hierarchy(pr):
+    """Oracle multigrid hierarchy, cached per problem (the Galerkin products
+    dominate the CPU time of the V-cycle tests)."""
+    key = (pr.d, pr.spans, pr.p, pr.ne, pr.N, pr.theta)
+    if key not in _HIER:
+        _HIER[key] = S.Hierarchy(pr)
+    return _HIER[key]
+
+
+def exact(pr, f):
+    """The oracle's exact solution by block forward substitution (pinned
+    against the sparse-LU solve of the whole system)."""
+    return S.forward_subst(pr, f)
+
+
 # (d, spans, p, N, ne): several tiles per axis and ragged tails (tile sizes
 # are 128 (1D), 32x8 (2D), 16x8x4 (3D))
 CASES = [
@@ -98,7 +116,7 @@ def test_vcycle_parity(st, basis, d, spans, p, N, ne):
     frozen-delta rediscretisation on the GPU) from a nonzero start, in the
     B-spline basis and in the spatial eigenbasis."""
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
-    H = S.Hierarchy(pr)
+    H = hierarchy(pr)
     s = st.Solver(d, p, spans, N, ne_per_slab=ne, basis=basis)
     u0 = inputs.uniform_vector(5, pr.ndofs)
     f = inputs.uniform_vector(6, pr.ndofs)
@@ -120,7 +138,7 @@ def test_solve_fp64_parity(st, basis, outer, d, spans, p, N, ne):
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     c = inputs.normal_coeffs(7, pr.ndofs)
     fr = A.load_from_coeffs(pr, c)
-    ud = S.direct(A.assemble_L(pr), fr)
+    ud = exact(pr, fr)
     s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer, basis=basis)
     f = torch.empty(pr.ndofs, dtype=torch.float64, device="cuda")
     s.load_coeffs(dev(c), f)
@@ -140,7 +158,7 @@ def test_solve_mixed_parity(st, basis, outer, d, spans, p, N, ne):
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     c = inputs.normal_coeffs(8, pr.ndofs)
     fr = A.load_from_coeffs(pr, c)
-    ud = S.direct(A.assemble_L(pr), fr)
+    ud = exact(pr, fr)
     s = st.Solver(d, p, spans, N, ne_per_slab=ne, outer=outer, precision="mixed_fp32",
                   basis=basis)
     f = dev(fr)
@@ -156,7 +174,7 @@ def test_manufactured_1d_solution(st):
     1e-10; the GPU solution equals the oracle's direct solution."""
     pr = A.Problem(1, (16,), 2, 4, 8, theta=1.0)
     fr = A.manufactured_load(pr)
-    ud = S.direct(A.assemble_L(pr), fr)
+    ud = exact(pr, fr)
     s = st.Solver(1, 2, (16,), 8, ne_per_slab=4, outer="mg")
     u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
     info = s.solve(dev(fr), u, tol=1e-10)
@@ -168,7 +186,7 @@ def test_manufactured_1d_solution(st):
 def test_single_slab_exact_in_one_cycle(st):
     pr = A.Problem(2, (9, 7), 2, 2, 1, theta=1.0)
     fr = inputs.normal_coeffs(9, pr.ndofs)
-    ud = S.direct(A.assemble_L(pr), fr)
+    ud = exact(pr, fr)
     s = st.Solver(2, 2, (9, 7), 1, outer="mg")
     u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
     info = s.solve(dev(fr), u, tol=1e-12)
@@ -190,7 +208,7 @@ def test_multi_rhs_equals_single(st, basis):
     ub = host(u).reshape(R, -1)
     L = A.assemble_L(pr)
     for r in range(R):
-        ud = S.direct(L, fs[r])
+        ud = exact(pr, fs[r])
         assert np.linalg.norm(ub[r] - ud) <= 1e-10 * np.linalg.norm(ud)
     # the operator is block diagonal over rhs
     x = inputs.uniform_vector(30, R * pr.ndofs)
@@ -274,7 +292,7 @@ def test_vcycle_tensor_core_transforms(st, prec, tol, d, spans, p, N, ne):
     rounded to TF32: 10-bit, BF16: 7-bit mantissa; FP32 accumulation) stays
     within a rounding-level distance of the oracle's FP64 V-cycle."""
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
-    H = S.Hierarchy(pr)
+    H = hierarchy(pr)
     f = inputs.uniform_vector(60, pr.ndofs)
     ref = S.vcycle(H, f)
     for basis in ("spectral", "nodal"):
@@ -294,7 +312,7 @@ def test_solve_tensor_core_parity(st, prec, d, spans, p, N, ne):
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     c = inputs.normal_coeffs(61, pr.ndofs)
     fr = A.load_from_coeffs(pr, c)
-    ud = S.direct(A.assemble_L(pr), fr)
+    ud = exact(pr, fr)
     s = st.Solver(d, p, spans, N, ne_per_slab=ne, precision=prec, basis="spectral")
     u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
     info = s.solve(dev(fr), u, tol=1e-10)
@@ -312,7 +330,7 @@ def test_solve_refinement_parity(st, prec, basis, d, spans, p, N, ne):
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     c = inputs.normal_coeffs(62, pr.ndofs)
     fr = A.load_from_coeffs(pr, c)
-    ud = S.direct(A.assemble_L(pr), fr)
+    ud = exact(pr, fr)
     s = st.Solver(d, p, spans, N, ne_per_slab=ne, precision=prec, basis=basis, outer="ir")
     u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
     info = s.solve(dev(fr), u, tol=1e-10)
@@ -338,5 +356,66 @@ def test_refinement_multi_rhs_equals_single(st):
         s1.solve(dev(fs[r]), u1, tol=1e-10)
         # each rhs is refined independently: the batched result is the single one
         assert np.array_equal(host(u1), ub[r])
-        ud = S.direct(L, fs[r])
+        ud = exact(pr, fs[r])
         assert np.linalg.norm(ub[r] - ud) <= 1e-8 * np.linalg.norm(ud)
+
+
+@pytest.mark.parametrize("basis", ["nodal", "spectral"])
+@pytest.mark.parametrize("d,spans,p,N,ne", [CASES[0], CASES[2], CASES[3], CASES[5]])
+def test_eig_variant_vcycle_and_solve(st, basis, d, spans, p, N, ne):
+    """Diagonalisation variant (Sec. 3.3, complex shifts): one smoothing step,
+    one V-cycle and an FP64 solve equal the oracle's."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    H = hierarchy(pr)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, variant="eig", basis=basis)
+    u0 = inputs.uniform_vector(80, pr.ndofs)
+    f = inputs.uniform_vector(81, pr.ndofs)
+    u = dev(u0)
+    s.smooth(u, dev(f), 1)
+    lev = S.Level(H.levels[0].L, N, pr.Nt * pr.Nx)
+    assert relerr(host(u), S.jacobi_step(lev, u0, f, 0.5)) <= 1e-10
+    if N > 1:
+        u = dev(u0)
+        s.vcycle(u, dev(f))
+        assert relerr(host(u), S.vcycle(H, f, u=u0.copy())) <= 1e-10
+    ud = exact(pr, f)
+    x = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+    s.solve(dev(f), x, tol=1e-12)
+    assert np.linalg.norm(host(x) - ud) <= 1e-10 * np.linalg.norm(ud)
+    s.close()
+
+
+@pytest.mark.parametrize("d,spans,p,N,ne", [(1, (16,), 2, 8, 4), (2, (12, 9), 3, 4, 2),
+                                            (3, (5, 6, 4), 2, 3, 2)])
+def test_gaussian_bump_load_parity(st, d, spans, p, N, ne):
+    """Space-time Gaussian-bump source: library quadrature vs the oracle's
+    (both Gauss-Legendre, 2p + 4 points per element)."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    cen, wid, amp = inputs.gaussian_bumps(9, count=6, dim=d + 1)
+    ref = A.bumps_load(pr, cen, wid, amp)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne)
+    f = torch.empty(pr.ndofs, dtype=torch.float64, device="cuda")
+    s.load_gaussians(cen, wid, amp, f)
+    assert relerr(host(f), ref) <= 1e-13
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_fp32"])
+@pytest.mark.parametrize("d,spans,p,N,ne", [CASES[0], CASES[3], CASES[4], CASES[6], (2, (64, 64), 2, 64, 2)])
+def test_fused_vcycle_matches_levelwise(st, prec, d, spans, p, N, ne):
+    """The one-kernel shared-memory V-cycle gives the level-by-level
+    eigenbasis V-cycle's result, and both match the oracle's V-cycle."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    f = inputs.uniform_vector(90, pr.ndofs)
+    out = []
+    for fused in (1, 0):
+        s = st.Solver(d, p, spans, N, ne_per_slab=ne, precision=prec, basis="spectral",
+                      fused_vcycle=fused)
+        u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+        s.vcycle(u, dev(f))
+        out.append(host(u))
+        s.close()
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert relerr(out[0], out[1]) <= tol
+    ref = S.vcycle(hierarchy(pr), f)
+    assert relerr(out[0], ref) <= (1e-11 if prec == "fp64" else 1e-4)
