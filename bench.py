@@ -182,9 +182,10 @@ def gpu_arm(args, rank, world):
     common = dict(ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
     peaks, peak_src = load_peaks()
 
-    def make(prec, basis, outer):
+    def make(prec, basis, outer, fused=None):
         return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
-                         outer=outer, **common)
+                         outer=outer, fused_vcycle=args.fused if fused is None else fused,
+                         **common)
 
     # rank r solves its own right-hand side(s) (independent replicas)
     n1 = make_len(d, spans, p, N, ne)
@@ -276,14 +277,19 @@ def gpu_arm(args, rank, world):
             ("mixed_fp32", "nodal", "fgmres"), ("mixed_fp32", "spectral", "fgmres"),
             ("mixed_fp32", "spectral", "ir"), ("mixed_tf32", "spectral", "ir"),
             ("mixed_bf16", "spectral", "ir"), ("mixed_tf32", "spectral", "fgmres"))
-    for prec, basis, outer in (allv if vset == "all" else allv[:1]):
+    allv = [v + (args.fused,) for v in allv]
+    allv.append((args.precision, args.basis, args.outer, 1 - args.fused))
+    for prec, basis, outer, fz in (allv if vset == "all" else [allv[0], allv[-1]]):
         name = "fp64_plain" if (prec, basis) == ("fp64", "nodal") else "%s_%s_%s" % (prec, basis, outer)
-        if (prec, basis, outer) == (args.precision, args.basis, args.outer) and name != "fp64_plain":
+        if fz != args.fused:
+            name += "_fused" if fz else "_levelwise"
+        elif (prec, basis, outer) == (args.precision, args.basis, args.outer) and name != "fp64_plain":
             continue
-        sv = make(prec, basis, outer)
+        sv = make(prec, basis, outer, fz)
         tv, iv, uv, _ = timed_solves(sv, f, max(1, args.steps // 2), 1)
         msv = sum(tv) / len(tv)
-        variants[name] = {"precision": prec, "basis": basis, "outer": outer, "ms_per_step": msv,
+        variants[name] = {"precision": prec, "basis": basis, "outer": outer, "fused_vcycle": fz,
+                          "ms_per_step": msv,
                           "value": sv.ndofs * world / (msv / 1e3),
                           "iterations": iv[-1]["iterations"],
                           "refinements": iv[-1].get("refinements", 0),
@@ -424,6 +430,8 @@ def main():
     ap.add_argument("--outer", default="ir", choices=["ir", "fgmres", "mg"])
     ap.add_argument("--precision", default="mixed_tf32",
                     choices=["mixed_fp32", "mixed_tf32", "mixed_bf16", "fp64"])
+    ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
+                    help="eigenbasis V-cycle as one shared-memory kernel (1) or level by level (0)")
     args = ap.parse_args()
 
     if args.cpu_leg:
@@ -437,6 +445,7 @@ def main():
            "spans": list(spans), "degree": p, "slabs": N, "time_elements_per_slab": ne,
            "theta": 1.0, "tol": tol, "solver": "V(1,1) time multigrid, omega=0.5, FGMRES(20) restart",
            "precision": args.precision, "vcycle_basis": args.basis, "outer": args.outer,
+           "fused_vcycle": args.fused,
            "rhs": "N(0,1) B-spline coefficients, seed %d" % seed, "l2": "flushed between steps"}
 
     if args.impl == "reference":

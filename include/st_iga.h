@@ -110,7 +110,8 @@ typedef struct {
     int autotune;         /* 1 (default): the first st_solve times the candidate
                              kernels of each spatial transform and keeps the
                              fastest (see st_autotune)                          */
-    int fused_vcycle;     /* 1 (default): ST_BASIS_SPECTRAL runs the whole
+    int fused_vcycle;     /* 0 (default): ST_BASIS_SPECTRAL runs the V-cycle
+                             level by level (one launch per step); 1: the whole
                              V-cycle in one shared-memory kernel per block of
                              spatial modes when a mode's levels fit            */
 } st_options;

@@ -20,6 +20,8 @@
 //                       P_t^T onto the merged coarse slab
 //  k_spec_coarse        exact solve of a level by forward substitution over
 //                       its slabs: u_n = A^{-1} (f_n + B^ u_{n-1})
+#include <cstring>
+
 #include "st_internal.h"
 
 namespace st {
@@ -229,30 +231,77 @@ cudaError_t launch_mode_solve(T *w, const T *const lam[3], const Grid &g, const 
     return cudaGetLastError();
 }
 
+// The eigenbasis operator L^ = blockbidiag(K_t + mu M_t, -N_t):
+// res = 1: out = f - L^ u, else out = L^ u  (pointwise per (slab, mode))
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_spec_op(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out,
+              const T *__restrict__ lam0, const T *__restrict__ lam1, const T *__restrict__ lam2,
+              Grid g, const __grid_constant__ SpecCoefs<T> c, int slabs_per_prob, long long nslabs,
+              int res) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= nslabs * g.nxyz) return;
+    const long long slab = idx / g.nxyz, k = idx % g.nxyz;
+    const int nt = c.nt;
+    const long long base = slab * nt * g.nxyz + k;
+    const T mu = mode_shift(g, lam0, lam1, lam2, k);
+    T uu[NTMAX], r[NTMAX];
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i) {
+        uu[i] = (i < nt) ? u[base + (long long)i * g.nxyz] : T(0);
+        r[i] = (i < nt && res) ? f[base + (long long)i * g.nxyz] : T(0);
+    }
+    const T up = ((slab % slabs_per_prob) != 0) ? u[base - g.nxyz] : T(0);
+    spec_residual(c, mu, uu, up, r);
+#pragma unroll
+    for (int i = 0; i < NTMAX; ++i)
+        if (i < nt) out[base + (long long)i * g.nxyz] = res ? r[i] : -r[i];
+}
+
+template <typename T>
+cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *const lam[3], const Grid &g,
+                           const SpecCoefs<T> &c, int slabs_per_prob, long long nslabs, int res,
+                           cudaStream_t s) {
+    const long long total = nslabs * g.nxyz;
+    if (total <= 0) return cudaSuccess;
+    k_spec_op<T><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(u, f, out, lam[0], lam[1], lam[2],
+                                                                g, c, slabs_per_prob, nslabs, res);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // The whole eigenbasis V-cycle in shared memory.  CTA (problem r, mode block
 // b) owns modes k0 .. k0 + MB - 1 of problem r on every slab of every level:
-// per level l it keeps u_l and f_l ([N_l][nt][MB], mode fastest) plus one
-// level-0 sized scratch array for the out-of-place Jacobi steps.  HBM is
-// touched twice: f^ is read once and u^ written once.  Same arithmetic as
-// k_spec_smooth / k_spec_res_restrict / k_prolong_add / k_spec_coarse.
+// per level l it keeps u_l and f_l as [nt][N_l][MB] (mode fastest, so a
+// warp's 32 consecutive (slab, mode) items hit 32 consecutive words), plus
+// one level-0 sized scratch array for the out-of-place Jacobi steps.  All
+// levels' time coefficients arrive as one __grid_constant__ parameter block
+// (constant-bank operands).  HBM is touched twice: f^ read once, u^ written
+// once.  Same arithmetic as k_spec_smooth / k_spec_res_restrict /
+// k_prolong_add / k_spec_coarse.
 // ---------------------------------------------------------------------------
+template <typename T>
+struct FusedParams {
+    static constexpr int LMAX = sizeof(T) == 4 ? 16 : 8;
+    SpecCoefs<T> lv[LMAX];
+    ProlongCoefs<T> pc;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256)
     k_spec_vcycle(const T *__restrict__ fin, T *__restrict__ uout,
-                  const SpecCoefs<T> *__restrict__ lvc, const T *__restrict__ lam0,
-                  const T *__restrict__ lam1, const T *__restrict__ lam2, Grid g,
-                  const __grid_constant__ ProlongCoefs<T> pc, int nlev, int N, int MB, int nu1,
-                  int nu2, T omega) {
+                  const __grid_constant__ FusedParams<T> P, const T *__restrict__ lam0,
+                  const T *__restrict__ lam1, const T *__restrict__ lam2, Grid g, int nlev, int N,
+                  int MB, int nu1, int nu2, T omega) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
-    const int nt = pc.nt;
+    const int nt = P.pc.nt;
     const long long nmodes = g.nxyz;
     const int nblk = (int)((nmodes + MB - 1) / MB);
     const int r = blockIdx.x / nblk;
     const long long k0 = (long long)(blockIdx.x % nblk) * MB;
     const int tid = threadIdx.x, NTH = blockDim.x;
-    // layout: mu[MB] | U_0 F_0 U_1 F_1 ... | TMP
+    // layout: mu[MB] | U_0 F_0 U_1 F_1 ... | TMP, each [nt][N_l][MB]
     T *mu = sm;
     T *lev = sm + MB;
     auto U = [&](int l) {
@@ -262,23 +311,24 @@ __global__ void __launch_bounds__(256)
     };
     auto F = [&](int l) { return U(l) + (long long)(N >> l) * nt * MB; };
     T *TMP = U(nlev);
+    // element (i, n, kk) of a level with Nl slabs
+#define SV_IDX(i, n, kk, Nl) (((long long)(i) * (Nl) + (n)) * MB + (kk))
     for (int kk = tid; kk < MB; kk += NTH)
         mu[kk] = (k0 + kk < nmodes) ? mode_shift(g, lam0, lam1, lam2, k0 + kk) : T(0);
-    // load f^ of this problem's mode block
-    {
+    {  // load f^ of this problem's mode block
         T *F0 = F(0);
         const long long base = (long long)r * N * nt * nmodes;
         for (long long e = tid; e < (long long)N * nt * MB; e += NTH) {
-            const long long row = e / MB;  // n * nt + i
-            const int kk = (int)(e % MB);
-            F0[e] = (k0 + kk < nmodes) ? fin[base + row * nmodes + k0 + kk] : T(0);
+            const long long row = e / MB;  // n * nt + i in global order
+            const int kk = (int)(e % MB), n = (int)(row / nt), i = (int)(row % nt);
+            F0[SV_IDX(i, n, kk, N)] = (k0 + kk < nmodes) ? fin[base + row * nmodes + k0 + kk] : T(0);
         }
     }
     __syncthreads();
 
     // one damped block-Jacobi step on level l: TMP = smooth(u), then u = TMP
     auto smooth = [&](int l, bool zero) {
-        const SpecCoefs<T> &c = lvc[l];
+        const SpecCoefs<T> &c = P.lv[l];
         const int Nl = N >> l;
         T *u = U(l);
         const T *f = F(l);
@@ -287,15 +337,15 @@ __global__ void __launch_bounds__(256)
             T uu[NTMAX], rr[NTMAX], v[NTMAX];
 #pragma unroll
             for (int i = 0; i < NTMAX; ++i) {
-                uu[i] = (i < nt && !zero) ? u[(n * nt + i) * MB + kk] : T(0);
-                rr[i] = (i < nt) ? f[(n * nt + i) * MB + kk] : T(0);
+                uu[i] = (i < nt && !zero) ? u[SV_IDX(i, n, kk, Nl)] : T(0);
+                rr[i] = (i < nt) ? f[SV_IDX(i, n, kk, Nl)] : T(0);
             }
-            const T up = (!zero && n > 0) ? u[(n * nt - 1) * MB + kk] : T(0);
+            const T up = (!zero && n > 0) ? u[SV_IDX(nt - 1, n - 1, kk, Nl)] : T(0);
             spec_residual(c, mu[kk], uu, up, rr);
             spec_block_solve(c, mu[kk], rr, v);
 #pragma unroll
             for (int i = 0; i < NTMAX; ++i)
-                if (i < nt) TMP[(n * nt + i) * MB + kk] = uu[i] + omega * v[i];
+                if (i < nt) TMP[SV_IDX(i, n, kk, Nl)] = uu[i] + omega * v[i];
         }
         __syncthreads();
         for (long long e = tid; e < (long long)Nl * nt * MB; e += NTH) u[e] = TMP[e];
@@ -306,24 +356,24 @@ __global__ void __launch_bounds__(256)
         for (int sidx = 0; sidx < nu1; ++sidx) smooth(l, sidx == 0);
         if (nu1 == 0)
             for (long long e = tid; e < (long long)(N >> l) * nt * MB; e += NTH) U(l)[e] = T(0);
+        __syncthreads();
         // residual of slab pairs, restricted to level l + 1
-        const SpecCoefs<T> &c = lvc[l];
-        const int Nc = N >> (l + 1);
+        const SpecCoefs<T> &c = P.lv[l];
+        const int Nl = N >> l, Nc = N >> (l + 1);
         const T *u = U(l), *f = F(l);
         T *fc = F(l + 1), *uc = U(l + 1);
-        __syncthreads();
         for (int it = tid; it < Nc * MB; it += NTH) {
             const int m = it / MB, kk = it % MB, a = 2 * m;
             T ua[NTMAX], ub[NTMAX], ra[NTMAX], rb[NTMAX];
 #pragma unroll
             for (int i = 0; i < NTMAX; ++i) {
                 const bool in = i < nt;
-                ua[i] = in ? u[(a * nt + i) * MB + kk] : T(0);
-                ub[i] = in ? u[((a + 1) * nt + i) * MB + kk] : T(0);
-                ra[i] = in ? f[(a * nt + i) * MB + kk] : T(0);
-                rb[i] = in ? f[((a + 1) * nt + i) * MB + kk] : T(0);
+                ua[i] = in ? u[SV_IDX(i, a, kk, Nl)] : T(0);
+                ub[i] = in ? u[SV_IDX(i, a + 1, kk, Nl)] : T(0);
+                ra[i] = in ? f[SV_IDX(i, a, kk, Nl)] : T(0);
+                rb[i] = in ? f[SV_IDX(i, a + 1, kk, Nl)] : T(0);
             }
-            const T up = (a > 0) ? u[(a * nt - 1) * MB + kk] : T(0);
+            const T up = (a > 0) ? u[SV_IDX(nt - 1, a - 1, kk, Nl)] : T(0);
             T ualast = T(0);
 #pragma unroll
             for (int i = 0; i < NTMAX; ++i)
@@ -336,17 +386,17 @@ __global__ void __launch_bounds__(256)
                 T sacc = T(0);
 #pragma unroll
                 for (int j = 0; j < NTMAX; ++j)
-                    if (j < nt) sacc += pc.P[j * NTMAX + i] * ra[j] + pc.P[(nt + j) * NTMAX + i] * rb[j];
-                fc[(m * nt + i) * MB + kk] = sacc;
-                uc[(m * nt + i) * MB + kk] = T(0);
+                    if (j < nt)
+                        sacc += P.pc.P[j * NTMAX + i] * ra[j] + P.pc.P[(nt + j) * NTMAX + i] * rb[j];
+                fc[SV_IDX(i, m, kk, Nc)] = sacc;
+                uc[SV_IDX(i, m, kk, Nc)] = T(0);
             }
         }
         __syncthreads();
     }
-    // coarsest level: exact forward substitution over its slabs, per mode
-    {
+    {  // coarsest level: exact forward substitution over its slabs, per mode
         const int l = nlev - 1, Nl = N >> l;
-        const SpecCoefs<T> &c = lvc[l];
+        const SpecCoefs<T> &c = P.lv[l];
         T *u = U(l);
         const T *f = F(l);
         for (int kk = tid; kk < MB; kk += NTH) {
@@ -354,12 +404,12 @@ __global__ void __launch_bounds__(256)
             for (int n = 0; n < Nl; ++n) {
                 T rr[NTMAX], v[NTMAX];
 #pragma unroll
-                for (int i = 0; i < NTMAX; ++i) rr[i] = (i < nt) ? f[(n * nt + i) * MB + kk] : T(0);
+                for (int i = 0; i < NTMAX; ++i) rr[i] = (i < nt) ? f[SV_IDX(i, n, kk, Nl)] : T(0);
                 rr[0] += prev;
                 spec_block_solve(c, mu[kk], rr, v);
 #pragma unroll
                 for (int i = 0; i < NTMAX; ++i) {
-                    if (i < nt) u[(n * nt + i) * MB + kk] = v[i];
+                    if (i < nt) u[SV_IDX(i, n, kk, Nl)] = v[i];
                     if (i == nt - 1) prev = v[i];
                 }
             }
@@ -368,14 +418,14 @@ __global__ void __launch_bounds__(256)
     }
     for (int l = nlev - 2; l >= 0; --l) {
         // prolongation of the coarse correction
-        const int Nc = N >> (l + 1);
+        const int Nl = N >> l, Nc = N >> (l + 1);
         T *u = U(l);
         const T *uc = U(l + 1);
         for (int it = tid; it < Nc * MB; it += NTH) {
             const int m = it / MB, kk = it % MB;
             T e[NTMAX];
 #pragma unroll
-            for (int i = 0; i < NTMAX; ++i) e[i] = (i < nt) ? uc[(m * nt + i) * MB + kk] : T(0);
+            for (int i = 0; i < NTMAX; ++i) e[i] = (i < nt) ? uc[SV_IDX(i, m, kk, Nc)] : T(0);
 #pragma unroll
             for (int j = 0; j < 2 * NTMAX; ++j) {
                 const int q = j / NTMAX, jj = j % NTMAX;
@@ -383,23 +433,23 @@ __global__ void __launch_bounds__(256)
                 T sacc = T(0);
 #pragma unroll
                 for (int i = 0; i < NTMAX; ++i)
-                    if (i < nt) sacc += pc.P[((q * nt) + jj) * NTMAX + i] * e[i];
-                u[((2 * m + q) * nt + jj) * MB + kk] += sacc;
+                    if (i < nt) sacc += P.pc.P[((q * nt) + jj) * NTMAX + i] * e[i];
+                u[SV_IDX(jj, 2 * m + q, kk, Nl)] += sacc;
             }
         }
         __syncthreads();
         for (int sidx = 0; sidx < nu2; ++sidx) smooth(l, false);
     }
-    // store u^
-    {
+    {  // store u^
         const T *U0 = U(0);
         const long long base = (long long)r * N * nt * nmodes;
         for (long long e = tid; e < (long long)N * nt * MB; e += NTH) {
             const long long row = e / MB;
-            const int kk = (int)(e % MB);
-            if (k0 + kk < nmodes) uout[base + row * nmodes + k0 + kk] = U0[e];
+            const int kk = (int)(e % MB), n = (int)(row / nt), i = (int)(row % nt);
+            if (k0 + kk < nmodes) uout[base + row * nmodes + k0 + kk] = U0[SV_IDX(i, n, kk, N)];
         }
     }
+#undef SV_IDX
 }
 
 // Shared memory (elements) of k_spec_vcycle for a mode block of MB modes.
@@ -410,13 +460,19 @@ static long long spec_vcycle_elems(int nlev, int N, int nt, int MB) {
 }
 
 template <typename T>
-cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc, const T *const lam[3],
-                               const Grid &g, const ProlongCoefs<T> &pc, int nlev, int N, int nrhs,
-                               int nu1, int nu2, T omega, int max_smem, cudaStream_t s) {
-    // largest mode block that fits, at most 32 modes
+cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc_host,
+                               const T *const lam[3], const Grid &g, const ProlongCoefs<T> &pc,
+                               int nlev, int N, int nrhs, int nu1, int nu2, T omega, int max_smem,
+                               int nsm, cudaStream_t s) {
+    if (nlev > FusedParams<T>::LMAX) return cudaErrorNotSupported;
+    // the mode block: at most 32 modes, small enough for two CTAs per SM
+    // when there are enough blocks to fill the GPU
     int MB = 32;
-    while (MB > 1 && spec_vcycle_elems(nlev, N, pc.nt, MB) * (long long)sizeof(T) > max_smem) MB /= 2;
-    const long long bytes = spec_vcycle_elems(nlev, N, pc.nt, MB) * (long long)sizeof(T);
+    const long long cap2 = (long long)(max_smem / 2 - 1024);
+    while (MB > 1 && (spec_vcycle_elems(nlev, N, pc.nt, MB) * (long long)sizeof(T) > cap2 ||
+                      (g.nxyz + MB - 1) / MB * nrhs < 2LL * nsm))
+        MB /= 2;
+    long long bytes = spec_vcycle_elems(nlev, N, pc.nt, MB) * (long long)sizeof(T);
     if (bytes > max_smem) return cudaErrorNotSupported;
     static bool attr = false;
     if (!attr) {
@@ -425,13 +481,16 @@ cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc, c
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    FusedParams<T> P;
+    memset(&P, 0, sizeof P);
+    for (int l = 0; l < nlev; ++l) P.lv[l] = lvc_host[l];
+    P.pc = pc;
     const long long nblk = (g.nxyz + MB - 1) / MB;
     const long long grid = nblk * nrhs;
     if (grid <= 0) return cudaSuccess;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_spec_vcycle<T><<<(unsigned)grid, 256, (size_t)bytes, s>>>(fin, uout, lvc, lam[0], lam[1],
-                                                               lam[2], g, pc, nlev, N, MB, nu1,
-                                                               nu2, omega);
+    k_spec_vcycle<T><<<(unsigned)grid, 256, (size_t)bytes, s>>>(fin, uout, P, lam[0], lam[1], lam[2],
+                                                               g, nlev, N, MB, nu1, nu2, omega);
     return cudaGetLastError();
 }
 
@@ -509,10 +568,13 @@ cudaError_t launch_spec_coarse(T *u, const T *f, const T *const lam[3], const Gr
                                                const SpecCoefs<T> &, int, int, cudaStream_t);     \
     template cudaError_t launch_mode_solve<T>(T *, const T *const[3], const Grid &,             \
                                               const SpecCoefs<T> &, long long, cudaStream_t);     \
+    template cudaError_t launch_spec_op<T>(const T *, const T *, T *, const T *const[3],        \
+                                           const Grid &, const SpecCoefs<T> &, int, long long,  \
+                                           int, cudaStream_t);                                  \
     template cudaError_t launch_spec_vcycle<T>(const T *, T *, const SpecCoefs<T> *,            \
                                                const T *const[3], const Grid &,                 \
                                                const ProlongCoefs<T> &, int, int, int, int, int, \
-                                               T, int, cudaStream_t);
+                                               T, int, int, cudaStream_t);
 ST_INST(double)
 ST_INST(float)
 #undef ST_INST

@@ -27,7 +27,7 @@ struct TileShape<1> {
 };
 template <>
 struct TileShape<2> {
-    static constexpr int TX = 32, TY = 8, TZ = 1;
+    static constexpr int TX = 32, TY = 16, TZ = 1;
 };
 template <>
 struct TileShape<3> {
@@ -126,16 +126,22 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
             S[e] = v;
         }
         __syncthreads();
-        // x-pass: A = M1x u, B = K1x u
+        // x-pass: A = M1x u, B = K1x u (the coupling plane needs only M_x u)
+        const bool mass_only = jj < 0;
         for (int e = tid; e < SZ * SY * TX; e += NTH) {
             const int ex = e % TX, row = e / TX;  // row = sz*SY + sy
             const T *srow = S + row * SX + ex;
             T a = T(0), b = T(0);
+            if (mass_only) {
 #pragma unroll
-            for (int o = 0; o < W; ++o) {
-                const T sv = srow[o];
-                a += bMx[ex * W + o] * sv;
-                b += bKx[ex * W + o] * sv;
+                for (int o = 0; o < W; ++o) a += bMx[ex * W + o] * srow[o];
+            } else {
+#pragma unroll
+                for (int o = 0; o < W; ++o) {
+                    const T sv = srow[o];
+                    a += bMx[ex * W + o] * sv;
+                    b += bKx[ex * W + o] * sv;
+                }
             }
             A[e] = a;
             B[e] = b;
@@ -148,13 +154,19 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
             for (int e = tid; e < SZ * TY * TX; e += NTH) {
                 const int ex = e % TX, ey = (e / TX) % TY, sz = e / (TX * TY);
                 T aa = T(0), ss = T(0);
+                if (mass_only) {
 #pragma unroll
-                for (int o = 0; o < W; ++o) {
-                    const int idx = (sz * SY + ey + o) * TX + ex;
-                    const T av = A[idx], bv = B[idx];
-                    const T my = bMy[ey * W + o], ky = bKy[ey * W + o];
-                    aa += my * av;
-                    ss += ky * av + my * bv;
+                    for (int o = 0; o < W; ++o)
+                        aa += bMy[ey * W + o] * A[(sz * SY + ey + o) * TX + ex];
+                } else {
+#pragma unroll
+                    for (int o = 0; o < W; ++o) {
+                        const int idx = (sz * SY + ey + o) * TX + ex;
+                        const T av = A[idx], bv = B[idx];
+                        const T my = bMy[ey * W + o], ky = bKy[ey * W + o];
+                        aa += my * av;
+                        ss += ky * av + my * bv;
+                    }
                 }
                 AA[e] = aa;
                 SS[e] = ss;

@@ -5,7 +5,10 @@
 // (Eq. 3.1 of arXiv:1802.09277 with fast diagonalisation in space).
 //
 // FP32 data in HBM; operands rounded to TF32 (cvt.rna) or BF16 while they are
-// staged into shared memory; FP32 accumulation in tensor memory.
+// staged into shared memory; FP32 accumulation in tensor memory.  KIND_TF32X3
+// splits each operand x = hi + lo (hi = tf32(x), lo = tf32(x - hi)) and
+// accumulates hi*hi + hi*lo + lo*hi: three TF32 MMAs per K step for a product
+// as accurate as FP32 arithmetic (the lo*lo term is below FP32 rounding).
 //
 // MODE_X (contracted axis contiguous):  D[k][c] = sum_i Wt[k][i] In[c][i]
 //     A = Wt (128 rows = output modes, n_out <= 128), B = 128 input rows
@@ -29,6 +32,14 @@ namespace {
 constexpr int TC_THREADS = 128;
 constexpr int TC_COLS = 128;  // columns (GEMM rows of the activation operand) per tile
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s: far above any tile's MMA time
+constexpr int KIND_TF32X3 = 3;  // split TF32 (see above); MMA format TF32
+
+template <int KIND>
+struct KindTraits {
+    static constexpr int FMT = (KIND == KIND_TF32X3) ? tc::FMT_TF32 : KIND;
+    static constexpr int ESZ = (FMT == tc::FMT_TF32) ? 4 : 2;  // bytes per element
+    static constexpr int NSPLIT = (KIND == KIND_TF32X3) ? 2 : 1;
+};
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -37,10 +48,27 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 }
 
 // Store 16 bytes of operand data for row r, 16-byte chunk kc of a K-major tile
-// with R rows.  TF32: 4 values; BF16: 8 values.
+// with R rows.  TF32: 4 values; BF16: 8 values; split TF32: 4 hi values in
+// `tile` and 4 lo values at the same offset in `tile + lo_off`.
 template <int KIND>
-__device__ __forceinline__ void stage16(unsigned char *tile, int R, int r, int kc, const float *v) {
+__device__ __forceinline__ void stage16(unsigned char *tile, int R, int r, int kc, const float *v,
+                                        size_t lo_off = 0) {
     uint4 q;
+    if (KIND == KIND_TF32X3) {
+        uint4 l;
+        q.x = to_tf32(v[0]);
+        q.y = to_tf32(v[1]);
+        q.z = to_tf32(v[2]);
+        q.w = to_tf32(v[3]);
+        l.x = to_tf32(v[0] - __uint_as_float(q.x));
+        l.y = to_tf32(v[1] - __uint_as_float(q.y));
+        l.z = to_tf32(v[2] - __uint_as_float(q.z));
+        l.w = to_tf32(v[3] - __uint_as_float(q.w));
+        const uint32_t off = tc::kmajor_offset(R, r, kc * 16);
+        *reinterpret_cast<uint4 *>(tile + off) = q;
+        *reinterpret_cast<uint4 *>(tile + lo_off + off) = l;
+        return;
+    }
     if (KIND == tc::FMT_TF32) {
         q.x = to_tf32(v[0]);
         q.y = to_tf32(v[1]);
@@ -78,13 +106,15 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    constexpr int ESZ = (KIND == tc::FMT_TF32) ? 4 : 2;
-    constexpr int EPC = 16 / ESZ;  // elements per 16-byte chunk
+    using KT = KindTraits<KIND>;
+    constexpr int EPC = 16 / KT::ESZ;  // elements per 16-byte chunk
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KC = a.k_pad / EPC;  // 16-byte chunks per operand row
     const int wrows = (MODE == 0) ? 128 : a.n_pad;
+    // [W hi | W lo] [X hi | X lo] (lo parts only for the split kind)
+    const size_t wbytes = (size_t)wrows * KC * 16, xbytes = (size_t)TC_COLS * KC * 16;
     unsigned char *wtile = smem;
-    unsigned char *xtile = smem + (size_t)wrows * KC * 16;
+    unsigned char *xtile = smem + KT::NSPLIT * wbytes;
     const uint32_t tmem_cols = (MODE == 0) ? 128u : (a.n_pad <= 32 ? 32u : a.n_pad <= 64 ? 64u
                                                    : a.n_pad <= 128 ? 128u : 256u);
 
@@ -97,7 +127,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
             const int i = kc * EPC + j;
             v[j] = (r < a.n_out && i < a.n_in) ? a.wt[(long long)r * a.n_in + i] : 0.f;
         }
-        stage16<KIND>(wtile, wrows, r, kc, v);
+        stage16<KIND>(wtile, wrows, r, kc, v, wbytes);
     }
     if (tid == 0) tc::mbar_init(&mbar, 1);
     if (warp == 0) tc::tmem_alloc(&tmem_base, tmem_cols);
@@ -105,8 +135,8 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = (MODE == 0) ? tc::make_idesc(KIND, 128, TC_COLS)
-                                       : tc::make_idesc(KIND, 128, a.n_pad);
+    const uint32_t idesc = (MODE == 0) ? tc::make_idesc(KT::FMT, 128, TC_COLS)
+                                       : tc::make_idesc(KT::FMT, 128, a.n_pad);
     const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
     uint32_t phase = 0;
     bool failed = false;
@@ -126,7 +156,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
                     const int i = kc * EPC + j;
                     v[j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
                 }
-                stage16<KIND>(xtile, TC_COLS, r, kc, v);
+                stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
             }
         } else {
             // lanes: consecutive columns (consecutive inner index), same chunk
@@ -141,7 +171,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
                     const int i = kc * EPC + j;
                     v[j] = (c < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
                 }
-                stage16<KIND>(xtile, TC_COLS, r, kc, v);
+                stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
             }
         }
         tc::fence_proxy_async_smem();
@@ -153,13 +183,21 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
             const uint32_t wa = tc::smem_u32(wtile), xa = tc::smem_u32(xtile);
             const uint32_t lbo_w = (uint32_t)wrows * 16, lbo_x = TC_COLS * 16;
             const int steps = KC / 2;
+            // split kind: (hi, hi), (hi, lo), (lo, hi) per K step
+            constexpr int NPROD = (KT::NSPLIT == 2) ? 3 : 1;
             for (int s = 0; s < steps; ++s) {
-                const uint64_t dw = tc::make_sdesc(wa + 2 * s * lbo_w, lbo_w, 128);
-                const uint64_t dx = tc::make_sdesc(xa + 2 * s * lbo_x, lbo_x, 128);
-                if (MODE == 0)
-                    tc::mma<KIND>(tmem, dw, dx, idesc, s > 0 ? 1u : 0u);
-                else
-                    tc::mma<KIND>(tmem, dx, dw, idesc, s > 0 ? 1u : 0u);
+#pragma unroll
+                for (int q = 0; q < NPROD; ++q) {
+                    const uint32_t wo = (q == 2) ? (uint32_t)wbytes : 0u;
+                    const uint32_t xo = (q == 1) ? (uint32_t)xbytes : 0u;
+                    const uint64_t dw = tc::make_sdesc(wa + wo + 2 * s * lbo_w, lbo_w, 128);
+                    const uint64_t dx = tc::make_sdesc(xa + xo + 2 * s * lbo_x, lbo_x, 128);
+                    const uint32_t acc = (s > 0 || q > 0) ? 1u : 0u;
+                    if (MODE == 0)
+                        tc::mma<KT::FMT>(tmem, dw, dx, idesc, acc);
+                    else
+                        tc::mma<KT::FMT>(tmem, dx, dw, idesc, acc);
+                }
             }
             tc::commit(&mbar);
         }
@@ -209,11 +247,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
 
 template <int KIND, int MODE>
 static cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s, int nsm, int ctas_per_sm) {
-    constexpr int EPC = (KIND == tc::FMT_TF32) ? 4 : 8;
+    using KT = KindTraits<KIND>;
+    constexpr int EPC = 16 / KT::ESZ;
     const int KC = a.k_pad / EPC;
     const int wrows = (MODE == 0) ? 128 : a.n_pad;
-    const size_t smem = (size_t)(wrows + TC_COLS) * KC * 16;
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)KT::NSPLIT * (wrows + TC_COLS) * KC * 16;
+    if (smem > 200 * 1024) return cudaErrorNotSupported;  // the caller uses CUDA cores
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_axis<KIND, MODE>,
@@ -248,7 +287,7 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
     a.wt = wt;
     a.n_in = n_in;
     a.n_out = n_out;
-    const int kstep = (kind == tc::FMT_TF32) ? 8 : 16;
+    const int kstep = (kind == tc::FMT_BF16) ? 16 : 8;
     a.k_pad = (n_in + kstep - 1) / kstep * kstep;
     a.n_pad = (n_out + 15) / 16 * 16;
     a.ncols = ncols;
@@ -257,6 +296,9 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
     if (ncols <= 0) return cudaSuccess;
     if (mode == 0 && n_out > 128) return cudaErrorNotSupported;
     if (mode == 1 && a.n_pad > 256) return cudaErrorNotSupported;
+    if (kind == KIND_TF32X3)
+        return mode == 0 ? launch_tc_t<KIND_TF32X3, 0>(a, s, nsm, ctas_per_sm)
+                         : launch_tc_t<KIND_TF32X3, 1>(a, s, nsm, ctas_per_sm);
     if (kind == tc::FMT_TF32)
         return mode == 0 ? launch_tc_t<tc::FMT_TF32, 0>(a, s, nsm, ctas_per_sm)
                          : launch_tc_t<tc::FMT_TF32, 1>(a, s, nsm, ctas_per_sm);

@@ -89,8 +89,8 @@ struct st_handle_s {
     bool mixed = false;
     int nsm = 152;
     int max_smem = 48 * 1024;  // opt-in shared memory per block
-    SpecCoefs<float> *d_lvc32 = nullptr;   // per-level coefficients for the fused V-cycle
-    SpecCoefs<double> *d_lvc64 = nullptr;
+    std::vector<SpecCoefs<float>> lvc32;   // per-level coefficients for the fused V-cycle
+    std::vector<SpecCoefs<double>> lvc64;
     // autotuned transform per axis: -1 = not tuned (heuristic), 0 = CUDA
     // cores, k > 0 = tensor cores with at most k CTAs per SM
     int tune[3] = {-1, -1, -1};
@@ -386,7 +386,8 @@ int stencil(st_handle h, int l, const T *u, const T *f, T *out, int mode, bool f
 // cores in the TF32 / BF16 modes (CUDA cores for shapes the kernel does not
 // cover), everything else on CUDA cores.
 template <typename T>
-int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long long planes) {
+int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long long planes,
+              bool full32 = false) {
     DevSpace<T> &ds = space<T>(h);
     const long long nx = h->g.nx, ny = h->g.ny, nz = h->g.nz;
     const long long n = (axis == 0) ? nx : (axis == 1) ? ny : nz;
@@ -397,7 +398,8 @@ int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long lon
     const int prec = h->opt.precision;
     if (sizeof(T) == 4 && (prec == ST_MIXED_TF32 || prec == ST_MIXED_BF16) && h->tune[axis] != 0) {
         const float *Wt = (const float *)(forward ? ds.Ut[axis] : ds.U[axis]);
-        const int kind = (prec == ST_MIXED_TF32) ? 2 : 1;
+        // full32: split TF32 on the tensor cores, as accurate as FP32
+        const int kind = full32 ? 3 : (prec == ST_MIXED_TF32) ? 2 : 1;
         const long long ncols = (axis == 0) ? outer : outer * inner;
         KScope ks(h, ST_PROF_TC, sizeof(T) * (2.0 * E + n * n), 2.0 * E * n);
         const cudaError_t e = launch_tc_axis(kind, axis == 0 ? 0 : 1, (const float *)in,
@@ -421,14 +423,15 @@ int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long lon
 }
 
 template <typename T>
-int spatial(st_handle h, const T *in, T *t0, T *t1, bool forward, long long planes, T **res) {
-    CKS(axis_pass<T>(h, 0, in, t0, forward, planes));
+int spatial(st_handle h, const T *in, T *t0, T *t1, bool forward, long long planes, T **res,
+            bool full32 = false) {
+    CKS(axis_pass<T>(h, 0, in, t0, forward, planes, full32));
     *res = t0;
     if (h->dim < 2) return ST_OK;
-    CKS(axis_pass<T>(h, 1, t0, t1, forward, planes));
+    CKS(axis_pass<T>(h, 1, t0, t1, forward, planes, full32));
     *res = t1;
     if (h->dim < 3) return ST_OK;
-    CKS(axis_pass<T>(h, 2, t1, t0, forward, planes));
+    CKS(axis_pass<T>(h, 2, t1, t0, forward, planes, full32));
     *res = t0;
     return ST_OK;
 }
@@ -640,9 +643,9 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
 template <typename T>
 const SpecCoefs<T> *dev_lvc(st_handle h);
 template <>
-const SpecCoefs<double> *dev_lvc<double>(st_handle h) { return h->d_lvc64; }
+const SpecCoefs<double> *dev_lvc<double>(st_handle h) { return h->lvc64.data(); }
 template <>
-const SpecCoefs<float> *dev_lvc<float>(st_handle h) { return h->d_lvc32; }
+const SpecCoefs<float> *dev_lvc<float>(st_handle h) { return h->lvc32.data(); }
 
 // Top of the eigenbasis V-cycle from zero: the whole V-cycle in one
 // shared-memory kernel when a mode's levels fit (opt.fused_vcycle), else the
@@ -656,7 +659,7 @@ int svcycle_top(st_handle h, T *u, const T *f, T *tmp) {
         const cudaError_t e = launch_spec_vcycle<T>(f, u, dev_lvc<T>(h), space<T>(h).lam, h->g,
                                                     pack_prolong<T>(h), h->nlev, h->N, h->nrhs,
                                                     h->opt.nu1, h->opt.nu2, (T)h->opt.omega,
-                                                    h->max_smem, h->stream);
+                                                    h->max_smem, h->nsm, h->stream);
         if (e == cudaSuccess) return ST_OK;
         if (e != cudaErrorNotSupported) CK(e);
         cudaGetLastError();
@@ -845,9 +848,9 @@ int solve_mg(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
 // at ||b - L x|| <= tol ||b|| (true residual checked at every restart).
 // skip[q] excludes rhs q (its x is left unchanged).  *its: iterations,
 // *worst: largest relative true residual at exit.
-template <typename T, typename Apply, typename Prec>
+template <typename T, typename Apply, typename Res, typename Prec>
 int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vector<T *> &V,
-                std::vector<T *> &Zk, Apply apply, Prec prec, const std::vector<char> &skip,
+                std::vector<T *> &Zk, Apply apply, Res resid, Prec prec, const std::vector<char> &skip,
                 int *its, double *worst_out) {
     const int m = (int)Zk.size(), R = h->nrhs;
     std::vector<double> nb, beta, hcol;
@@ -856,7 +859,7 @@ int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vecto
     double worst = 0.0;
     std::vector<char> done(R, 0);
     while (true) {
-        CKS(stencil<T>(h, 0, x, b, V[0], MODE_RES, false, 0, h->N * R));
+        CKS(resid(x, b, V[0]));
         CKS(norms<T>(h, V[0], beta));
         worst = 0.0;
         for (int q = 0; q < R; ++q) {
@@ -980,8 +983,11 @@ int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve
     auto prec = [h](const double *v, double *z) {
         return run_graphed(h, v, z, [h, v, z] { return precondition(h, v, z); });
     };
-    CKS(fgmres_core<double>(h, rhs, u, tol, h->opt.max_it, h->V, Z, apply, prec, skip, &its,
-                            &worst));
+    auto resid = [h](const double *x, const double *b, double *r) {
+        return stencil<double>(h, 0, x, b, r, MODE_RES, false, 0, h->N * h->nrhs);
+    };
+    CKS(fgmres_core<double>(h, rhs, u, tol, h->opt.max_it, h->V, Z, apply, resid, prec, skip,
+                            &its, &worst));
     info->iterations = its;
     info->rel_residual = worst;
     info->status = (worst <= tol) ? ST_OK : ST_ERR_NO_CONVERGENCE;
@@ -1038,11 +1044,30 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
     CKS(norms<double>(h, rhs, nf));
     int total = 0, outer = 0;
     double worst = 0.0;
-    auto apply = [h](const float *z, float *w) {
-        return stencil<float>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, h->N * h->nrhs);
+    const bool eig_basis = h->opt.basis == ST_BASIS_SPECTRAL;
+    const SpecCoefs<float> c0 = pack_spec<float>(h, 0);
+    const long long nsl = (long long)h->N * R;
+    // B-spline basis: FP32 stencil operator, V-cycle with its transforms;
+    // eigenbasis: pointwise operator L^, V-cycle without transforms
+    auto apply = [h, eig_basis, c0, nsl](const float *z, float *w) {
+        if (!eig_basis)
+            return stencil<float>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, (int)nsl);
+        const double E = (double)nsl * h->nt * h->g.nxyz;
+        KScope ks(h, ST_PROF_SPEC, 4.0 * 2.25 * E, E * (4.0 * h->nt + 2.0));
+        CK(launch_spec_op<float>(z, nullptr, w, h->s32.lam, h->g, c0, h->N, nsl, 0, h->stream));
+        return (int)ST_OK;
     };
-    auto prec = [h](const float *v, float *z) {
-        return run_graphed(h, v, z, [h, v, z] { return precondition32(h, v, z); });
+    auto resid = [h, eig_basis, c0, nsl](const float *x, const float *b, float *r) {
+        if (!eig_basis) return stencil<float>(h, 0, x, b, r, MODE_RES, false, 0, (int)nsl);
+        const double E = (double)nsl * h->nt * h->g.nxyz;
+        KScope ks(h, ST_PROF_SPEC, 4.0 * 3.25 * E, E * (4.0 * h->nt + 2.0));
+        CK(launch_spec_op<float>(x, b, r, h->s32.lam, h->g, c0, h->N, nsl, 1, h->stream));
+        return (int)ST_OK;
+    };
+    auto prec = [h, eig_basis](const float *v, float *z) {
+        if (!eig_basis)
+            return run_graphed(h, v, z, [h, v, z] { return precondition32(h, v, z); });
+        return run_graphed(h, v, z, [h, v, z] { return svcycle_top<float>(h, z, v, h->w32.w0); });
     };
     const long long n0 = h->len * R;
     for (;;) {
@@ -1061,17 +1086,31 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
         if (worst <= tol || total >= h->opt.max_it || outer >= 60) break;
         CKS((vconvert<double, float>(h, h->r64, h->rhs32)));
         CKS(vaxpy<float>(h, 0, nullptr, nullptr, h->rhs32, sc.data()));
+        const long long planes = (long long)h->N * R * h->nt;
+        // the two transforms around each inner solve run at full FP32
+        // accuracy: their error bounds what one refinement step can gain
+        if (eig_basis) {  // r^ = (I (x) U^T) r, into rhs32
+            float *rh = nullptr;
+            CKS(spatial<float>(h, h->rhs32, h->w32.w0, h->w32.w1, true, planes, &rh, true));
+            CK(cudaMemcpyAsync(h->rhs32, rh, sizeof(float) * n0, cudaMemcpyDeviceToDevice, h->stream));
+        }
         CK(launch_zero<float>(h->e32, n0, h->stream));
         int its = 0;
         double w32 = 0.0;
         const double itol = std::max(h->opt.inner_tol, 1e-6);
         CKS(fgmres_core<float>(h, h->rhs32, h->e32, itol, h->opt.max_it - total, h->V32, h->Z32,
-                               apply, prec, skip, &its, &w32));
+                               apply, resid, prec, skip, &its, &w32));
         total += its;
         ++outer;
+        const float *corr = h->e32;
+        if (eig_basis) {  // e = (I (x) U) e^
+            float *eb = nullptr;
+            CKS(spatial<float>(h, h->e32, h->w32.w0, h->w32.w1, false, planes, &eb, true));
+            corr = eb;
+        }
         {
             KScope ks(h, ST_PROF_VECTOR, 12.0 * n0, 2.0 * n0);
-            CK(launch_axpy_f32_f64(h->e32, u, back.data(), R, h->len, h->stream));
+            CK(launch_axpy_f32_f64(corr, u, back.data(), R, h->len, h->stream));
         }
     }
     info->iterations = total;
@@ -1258,19 +1297,12 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&ms, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         h->max_smem = ms > 0 ? ms : 48 * 1024;
-        std::vector<SpecCoefs<double>> c64(h->nlev);
-        std::vector<SpecCoefs<float>> c32(h->nlev);
+        h->lvc64.resize(h->nlev);
+        h->lvc32.resize(h->nlev);
         for (int l = 0; l < h->nlev; ++l) {
-            c64[l] = pack_spec<double>(h, l);
-            c32[l] = pack_spec<float>(h, l);
+            h->lvc64[l] = pack_spec<double>(h, l);
+            h->lvc32[l] = pack_spec<float>(h, l);
         }
-        void *q;
-        CKS(dalloc(h, sizeof(SpecCoefs<double>) * h->nlev, &q));
-        h->d_lvc64 = (SpecCoefs<double> *)q;
-        CK(cudaMemcpy(q, c64.data(), sizeof(SpecCoefs<double>) * h->nlev, cudaMemcpyHostToDevice));
-        CKS(dalloc(h, sizeof(SpecCoefs<float>) * h->nlev, &q));
-        h->d_lvc32 = (SpecCoefs<float> *)q;
-        CK(cudaMemcpy(q, c32.data(), sizeof(SpecCoefs<float>) * h->nlev, cudaMemcpyHostToDevice));
     }
     h->nblk_dot = 2 * h->nsm;
     void *p;
@@ -1352,7 +1384,7 @@ void st_options_default(st_options *o) {
     o->use_graphs = 1;
     o->variant = ST_RSCHUR;
     o->autotune = 1;
-    o->fused_vcycle = 1;
+    o->fused_vcycle = 0;
 }
 
 const char *st_last_error(void) { return g_err.c_str(); }

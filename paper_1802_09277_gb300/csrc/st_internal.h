@@ -113,7 +113,8 @@ cudaError_t launch_prolong_add(const T *ec, T *uf, const ProlongCoefs<T> &pc, co
                                long long ncoarse, cudaStream_t s);
 
 // ---- tensor-core transforms (kernels_tc.cu) ----
-// kind: 2 = TF32, 1 = BF16; mode 0: contracted axis contiguous, 1: strided by
+// kind: 2 = TF32, 1 = BF16, 3 = split TF32 (hi*hi + hi*lo + lo*hi, FP32
+// accuracy); mode 0: contracted axis contiguous, 1: strided by
 // `inner`.  wt = W^T row-major (n_out x n_in).  cudaErrorNotSupported when the
 // shape is not covered.
 cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, const float *wt,
@@ -130,13 +131,21 @@ cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *con
                                      const Grid &g, const SpecCoefs<T> &c,
                                      const ProlongCoefs<T> &pc, int slabs_per_prob,
                                      long long ncoarse, cudaStream_t s);
-// the whole eigenbasis V-cycle in shared memory (one launch); lvc: device
-// array of the nlev levels' coefficients; cudaErrorNotSupported if one mode's
-// levels do not fit in max_smem bytes
+// the whole eigenbasis V-cycle in shared memory (one launch); lvc_host: HOST
+// array of the nlev levels' coefficients (passed as a kernel parameter
+// block); cudaErrorNotSupported if one mode's levels do not fit in max_smem
+// bytes or there are too many levels
 template <typename T>
-cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc, const T *const lam[3],
-                               const Grid &g, const ProlongCoefs<T> &pc, int nlev, int N, int nrhs,
-                               int nu1, int nu2, T omega, int max_smem, cudaStream_t s);
+cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc_host,
+                               const T *const lam[3], const Grid &g, const ProlongCoefs<T> &pc,
+                               int nlev, int N, int nrhs, int nu1, int nu2, T omega, int max_smem,
+                               int nsm, cudaStream_t s);
+
+// eigenbasis operator: res = 1: out = f - L^ u; res = 0: out = L^ u
+template <typename T>
+cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *const lam[3], const Grid &g,
+                           const SpecCoefs<T> &c, int slabs_per_prob, long long nslabs, int res,
+                           cudaStream_t s);
 
 // in place per (slab, mode): w <- (K_t + mu_k M_t)^{-1} w
 template <typename T>

@@ -190,7 +190,10 @@ void worker(st_server_s *s) {
                     e = c.get();
                     break;
                 }
-            if (e) break;
+            if (e) {  // a cached setup (possibly freed while this worker waited)
+                rc = ST_OK;
+                break;
+            }
             rc = make_entry(s, key, R, &e);
             if (rc == ST_OK) break;
             why = std::string("setup: ") + st_last_error();

@@ -28,13 +28,15 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--basis", default="nodal", choices=["nodal", "spectral"])
     ap.add_argument("--outer", default="fgmres", choices=["fgmres", "mg", "ir"])
+    ap.add_argument("--fused", type=int, default=0, choices=[0, 1])
     args = ap.parse_args()
 
     import torch
     from paper_1802_09277_gb300 import inputs, st
 
     s = st.Solver(args.dim, args.degree, args.spans, args.slabs, ne_per_slab=args.ne,
-                  precision=args.precision, basis=args.basis, outer=args.outer)
+                  precision=args.precision, basis=args.basis, outer=args.outer,
+                  fused_vcycle=args.fused)
     n = s.ndofs
     x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
     f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")

@@ -94,7 +94,8 @@ def test_budget_admission(st):
           for i in range(4)]
     outs = [srv.wait(t, timeout=120.0) for t in ts]
     srv.stop()
-    assert all(r["status"] == 0 for r, _ in outs), ([r for r, _ in outs], budget, one)
+    assert all(r["status"] == 0 for r, _ in outs), (
+        [(r["status"], r["error"]) for r, _ in outs], budget, one)
 
 
 def test_poll_and_tickets(st):
