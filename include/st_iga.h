@@ -250,7 +250,8 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u,
 #define ST_PROF_DOT       8  /* Krylov dot products (deterministic reduction) */
 #define ST_PROF_TC        9  /* spatial transform (one axis), tensor cores    */
 #define ST_PROF_SPEC     10  /* eigenbasis smoothing step / coarse solve      */
-#define ST_PROF_NCLASS   11
+#define ST_PROF_STENCILDF 11 /* refinement residual, double-float on FP64 data */
+#define ST_PROF_NCLASS   12
 int st_profile(st_handle h, int enable);
 int st_profile_read(st_handle h, int cls, int64_t *launches, double *ms,
                     double *bytes, double *flops);

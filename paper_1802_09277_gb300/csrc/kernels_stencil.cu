@@ -15,9 +15,22 @@
 // tile plus a halo of p is staged in shared memory, then reduced axis by
 // axis: x-pass (M1x, K1x), y-pass, z-pass; the 2p+1 band coefficients of the
 // tile's rows are staged once per CTA.
+//
+// Storage type T (FP64 or FP32 in HBM) and compute type C are separate: the
+// FP64-accurate residual of the mixed-precision refinement computes in
+// double-float (C = dfloat) on FP64 data, converting on load and store.
 #include "st_internal.h"
 
 namespace st {
+
+template <typename C, typename T>
+__device__ __forceinline__ C to_c(T x) {
+    return C(x);
+}
+template <typename T, typename C>
+__device__ __forceinline__ T from_c(C x) {
+    return (T)x;
+}
 
 template <int DIM>
 struct TileShape;
@@ -34,7 +47,7 @@ struct TileShape<3> {
     static constexpr int TX = 16, TY = 8, TZ = 4;
 };
 
-template <typename T, int P, int DIM>
+template <typename T, int P, int DIM>  // T: compute type
 struct StencilSmem {
     using TS = TileShape<DIM>;
     static constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
@@ -49,28 +62,28 @@ struct StencilSmem {
     static constexpr int threads = TX * TY;
 };
 
-template <typename T, int P, int DIM>
-__global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
+template <typename T, typename C, int P, int DIM>
+__global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
     k_stencil(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out, Bands<T> bands,
-              Grid g, const __grid_constant__ TimeCoefs<T> tc, int slabs_per_prob, int slab0, int tiles_x, int tiles_y) {
-    using SM = StencilSmem<T, P, DIM>;
+              Grid g, const __grid_constant__ TimeCoefs<C> tc, int slabs_per_prob, int slab0, int tiles_x, int tiles_y) {
+    using SM = StencilSmem<C, P, DIM>;
     constexpr int TX = SM::TX, TY = SM::TY, TZ = SM::TZ;
     constexpr int HX = SM::HX, HY = SM::HY, HZ = SM::HZ;
     constexpr int SX = SM::SX, SY = SM::SY, SZ = SM::SZ, W = SM::W;
     constexpr int NTH = SM::threads;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *S = reinterpret_cast<T *>(smem_raw);
-    T *A = S + SM::nS;
-    T *B = A + SM::nA;
-    T *AA = B + SM::nA;
-    T *SS = AA + SM::nAA;
-    T *bMx = SS + SM::nAA;
-    T *bKx = bMx + TX * W;
-    T *bMy = bKx + TX * W;
-    T *bKy = bMy + TY * W;
-    T *bMz = bKy + TY * W;
-    T *bKz = bMz + TZ * W;
+    C *S = reinterpret_cast<C *>(smem_raw);
+    C *A = S + SM::nS;
+    C *B = A + SM::nA;
+    C *AA = B + SM::nA;
+    C *SS = AA + SM::nAA;
+    C *bMx = SS + SM::nAA;
+    C *bKx = bMx + TX * W;
+    C *bMy = bKx + TX * W;
+    C *bKy = bMy + TY * W;
+    C *bMz = bKy + TY * W;
+    C *bKz = bMz + TZ * W;
 
     const int tid = threadIdx.x;
     const int tile = blockIdx.x;
@@ -85,30 +98,30 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
     // stage the band rows of this tile (zero outside the grid)
     for (int e = tid; e < TX * W; e += NTH) {
         const int gx = x0 + e / W;
-        bMx[e] = (gx < nx) ? bands.M[0][(long long)gx * W + e % W] : T(0);
-        bKx[e] = (gx < nx) ? bands.K[0][(long long)gx * W + e % W] : T(0);
+        bMx[e] = (gx < nx) ? to_c<C>(bands.M[0][(long long)gx * W + e % W]) : C(0);
+        bKx[e] = (gx < nx) ? to_c<C>(bands.K[0][(long long)gx * W + e % W]) : C(0);
     }
     if (DIM >= 2)
         for (int e = tid; e < TY * W; e += NTH) {
             const int gy = y0 + e / W;
-            bMy[e] = (gy < ny) ? bands.M[1][(long long)gy * W + e % W] : T(0);
-            bKy[e] = (gy < ny) ? bands.K[1][(long long)gy * W + e % W] : T(0);
+            bMy[e] = (gy < ny) ? to_c<C>(bands.M[1][(long long)gy * W + e % W]) : C(0);
+            bKy[e] = (gy < ny) ? to_c<C>(bands.K[1][(long long)gy * W + e % W]) : C(0);
         }
     if (DIM >= 3)
         for (int e = tid; e < TZ * W; e += NTH) {
             const int gz = z0 + e / W;
-            bMz[e] = (gz < nz) ? bands.M[2][(long long)gz * W + e % W] : T(0);
-            bKz[e] = (gz < nz) ? bands.K[2][(long long)gz * W + e % W] : T(0);
+            bMz[e] = (gz < nz) ? to_c<C>(bands.M[2][(long long)gz * W + e % W]) : C(0);
+            bKz[e] = (gz < nz) ? to_c<C>(bands.K[2][(long long)gz * W + e % W]) : C(0);
         }
 
     const int tx = tid % TX, ty = tid / TX;
-    T acc[TZ][NTMAX];
-    T mprev[TZ];
+    C acc[TZ][NTMAX];
+    C mprev[TZ];
 #pragma unroll
     for (int a = 0; a < TZ; ++a) {
-        mprev[a] = T(0);
+        mprev[a] = C(0);
 #pragma unroll
-        for (int i = 0; i < NTMAX; ++i) acc[a][i] = T(0);
+        for (int i = 0; i < NTMAX; ++i) acc[a][i] = C(0);
     }
 
     const T *uslab = u + (long long)slab * nt * nxyz;
@@ -120,9 +133,9 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
         for (int e = tid; e < SZ * SY * SX; e += NTH) {
             const int sx = e % SX, sy = (e / SX) % SY, sz = e / (SX * SY);
             const int gx = x0 + sx - HX, gy = y0 + sy - HY, gz = z0 + sz - HZ;
-            T v = T(0);
+            C v = C(0);
             if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-                v = plane[((long long)gz * ny + gy) * nx + gx];
+                v = to_c<C>(plane[((long long)gz * ny + gy) * nx + gx]);
             S[e] = v;
         }
         __syncthreads();
@@ -130,15 +143,15 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
         const bool mass_only = jj < 0;
         for (int e = tid; e < SZ * SY * TX; e += NTH) {
             const int ex = e % TX, row = e / TX;  // row = sz*SY + sy
-            const T *srow = S + row * SX + ex;
-            T a = T(0), b = T(0);
+            const C *srow = S + row * SX + ex;
+            C a = C(0), b = C(0);
             if (mass_only) {
 #pragma unroll
                 for (int o = 0; o < W; ++o) a += bMx[ex * W + o] * srow[o];
             } else {
 #pragma unroll
                 for (int o = 0; o < W; ++o) {
-                    const T sv = srow[o];
+                    const C sv = srow[o];
                     a += bMx[ex * W + o] * sv;
                     b += bKx[ex * W + o] * sv;
                 }
@@ -147,13 +160,13 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
             B[e] = b;
         }
         __syncthreads();
-        const T *pm;
-        const T *pk;
+        const C *pm;
+        const C *pk;
         if (DIM >= 2) {
             // y-pass: AA = M1y A, SS = K1y A + M1y B
             for (int e = tid; e < SZ * TY * TX; e += NTH) {
                 const int ex = e % TX, ey = (e / TX) % TY, sz = e / (TX * TY);
-                T aa = T(0), ss = T(0);
+                C aa = C(0), ss = C(0);
                 if (mass_only) {
 #pragma unroll
                     for (int o = 0; o < W; ++o)
@@ -162,8 +175,8 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
 #pragma unroll
                     for (int o = 0; o < W; ++o) {
                         const int idx = (sz * SY + ey + o) * TX + ex;
-                        const T av = A[idx], bv = B[idx];
-                        const T my = bMy[ey * W + o], ky = bKy[ey * W + o];
+                        const C av = A[idx], bv = B[idx];
+                        const C my = bMy[ey * W + o], ky = bKy[ey * W + o];
                         aa += my * av;
                         ss += ky * av + my * bv;
                     }
@@ -181,14 +194,14 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
         // z-pass and accumulation into this thread's output points
 #pragma unroll
         for (int a = 0; a < TZ; ++a) {
-            T m, k;
+            C m, k;
             if (DIM >= 3) {
-                m = T(0);
-                k = T(0);
+                m = C(0);
+                k = C(0);
 #pragma unroll
                 for (int o = 0; o < W; ++o) {
                     const int idx = ((a + o) * TY + ty) * TX + tx;
-                    const T mz = bMz[a * W + o], kz = bKz[a * W + o];
+                    const C mz = bMz[a * W + o], kz = bKz[a * W + o];
                     m += mz * pm[idx];
                     k += kz * pm[idx] + mz * pk[idx];
                 }
@@ -215,16 +228,16 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
         if (gz >= nz) break;
         const long long sp = ((long long)gz * ny + gy) * nx + gx;
         const long long base = (long long)slab * nt * nxyz + sp;
-        T r[NTMAX];
+        C r[NTMAX];
 #pragma unroll
         for (int i = 0; i < NTMAX; ++i) {
             if (i >= nt) {
-                r[i] = T(0);
+                r[i] = C(0);
                 continue;
             }
-            T v = acc[a][i];
+            C v = acc[a][i];
             if (tc.mode == MODE_RES) {
-                v = f[base + (long long)i * nxyz] - v;
+                v = to_c<C>(f[base + (long long)i * nxyz]) - v;
                 if (i == 0) v += mprev[a];
             } else if (tc.mode == MODE_APPLY) {
                 if (i == 0) v -= mprev[a];
@@ -235,28 +248,28 @@ __global__ void __launch_bounds__(StencilSmem<T, P, DIM>::threads)
 #pragma unroll
             for (int i = 0; i < NTMAX; ++i) {
                 if (i >= nt) break;
-                T w = T(0);
+                C w = C(0);
 #pragma unroll
                 for (int j = 0; j < NTMAX; ++j)
                     if (j < nt) w += tc.Y[i * NTMAX + j] * r[j];
-                out[base + (long long)i * nxyz] = w;
+                out[base + (long long)i * nxyz] = from_c<T>(w);
             }
         } else {
 #pragma unroll
             for (int i = 0; i < NTMAX; ++i)
-                if (i < nt) out[base + (long long)i * nxyz] = r[i];
+                if (i < nt) out[base + (long long)i * nxyz] = from_c<T>(r[i]);
         }
     }
 }
 
-template <typename T, int P, int DIM>
+template <typename T, typename C, int P, int DIM>
 static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<T> &bands,
-                                    const Grid &g, const TimeCoefs<T> &tc, int slabs_per_prob,
+                                    const Grid &g, const TimeCoefs<C> &tc, int slabs_per_prob,
                                     int slab0, int nslabs, cudaStream_t s) {
-    using SM = StencilSmem<T, P, DIM>;
+    using SM = StencilSmem<C, P, DIM>;
     static bool attr_set = false;  // per device-less process; attribute is per function
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil<T, P, DIM>,
+        cudaError_t e = cudaFuncSetAttribute(k_stencil<T, C, P, DIM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)SM::bytes);
         if (e != cudaSuccess) return e;
@@ -268,19 +281,19 @@ static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<
     if (nslabs <= 0) return cudaSuccess;
     if (nslabs > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)(tx * ty * tz), (unsigned)nslabs);
-    k_stencil<T, P, DIM><<<grid, SM::threads, SM::bytes, s>>>(u, f, out, bands, g, tc,
-                                                              slabs_per_prob, slab0, tx, ty);
+    k_stencil<T, C, P, DIM><<<grid, SM::threads, SM::bytes, s>>>(u, f, out, bands, g, tc,
+                                                                 slabs_per_prob, slab0, tx, ty);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, typename C>
 cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands, const Grid &g,
-                           const TimeCoefs<T> &tc, int slabs_per_prob, int slab0, int nslabs,
+                           const TimeCoefs<C> &tc, int slabs_per_prob, int slab0, int nslabs,
                            cudaStream_t s) {
 #define ST_CASE(PP, DD)                                                                         \
     if (g.p == PP && g.dim == DD)                                                               \
-        return launch_stencil_t<T, PP, DD>(u, f, out, bands, g, tc, slabs_per_prob, slab0, nslabs, \
-                                           s);
+        return launch_stencil_t<T, C, PP, DD>(u, f, out, bands, g, tc, slabs_per_prob, slab0,   \
+                                              nslabs, s);
     ST_CASE(1, 1)
     ST_CASE(2, 1)
     ST_CASE(3, 1)
@@ -294,11 +307,17 @@ cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands
     return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_stencil<double>(const double *, const double *, double *,
-                                            const Bands<double> &, const Grid &,
-                                            const TimeCoefs<double> &, int, int, int, cudaStream_t);
-template cudaError_t launch_stencil<float>(const float *, const float *, float *,
-                                           const Bands<float> &, const Grid &,
-                                           const TimeCoefs<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_stencil<double, double>(const double *, const double *, double *,
+                                                    const Bands<double> &, const Grid &,
+                                                    const TimeCoefs<double> &, int, int, int,
+                                                    cudaStream_t);
+template cudaError_t launch_stencil<float, float>(const float *, const float *, float *,
+                                                  const Bands<float> &, const Grid &,
+                                                  const TimeCoefs<float> &, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t launch_stencil<double, dfloat>(const double *, const double *, double *,
+                                                    const Bands<double> &, const Grid &,
+                                                    const TimeCoefs<dfloat> &, int, int, int,
+                                                    cudaStream_t);
 
 }  // namespace st

@@ -67,6 +67,7 @@ struct DevSpace {  // device copies of the 1D factors in one precision
     const T *U[3] = {nullptr, nullptr, nullptr};   // W = U  (forward, U^T applied)
     const T *Ut[3] = {nullptr, nullptr, nullptr};  // W = U^T (inverse, U applied)
     const T *lam[3] = {nullptr, nullptr, nullptr};
+    const T *mu = nullptr;  // per spatial mode k: the shift sum over axes of lambda_axis
 };
 
 template <typename T>
@@ -239,6 +240,17 @@ int upload_space(st_handle h, DevSpace<T> &ds, const std::vector<double> bandM[3
         ds.bands.M[a] = ds.bands.K[a] = nullptr;
         ds.U[a] = ds.Ut[a] = ds.lam[a] = nullptr;
     }
+    // mu_k = lambda_x[kx] + lambda_y[ky] + lambda_z[kz], k = (kz * ny + ky) * nx + kx
+    std::vector<double> mu((size_t)h->n[0] * h->n[1] * h->n[2]);
+    for (int kz = 0; kz < h->n[2]; ++kz)
+        for (int ky = 0; ky < h->n[1]; ++ky)
+            for (int kx = 0; kx < h->n[0]; ++kx) {
+                double m = h->lam[0][kx];
+                if (h->dim >= 2) m += h->lam[1][ky];
+                if (h->dim >= 3) m += h->lam[2][kz];
+                mu[((size_t)kz * h->n[1] + ky) * h->n[0] + kx] = m;
+            }
+    CKS(upload<T>(h, mu, &ds.mu));
     return ST_OK;
 }
 
@@ -500,7 +512,7 @@ int smooth_range(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns, 
     if (eig) {
         const SpecCoefs<T> c = pack_spec<T>(h, l);
         KScope ks(h, ST_PROF_SHIFT, sizeof(T) * 2.0 * E, E * (5.0 * h->nt + 4.0));
-        CK(launch_mode_solve<T>(fw, ds.lam, h->g, c, ns, h->stream));
+        CK(launch_mode_solve<T>(fw, ds.mu, h->g, c, ns, h->stream));
         for (int i = 0; i < NTMAX; ++i)
             for (int j = 0; j < NTMAX; ++j) sc.X[i * NTMAX + j] = (i == j) ? T(1) : T(0);
     } else {
@@ -600,7 +612,7 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     const long long ns = (long long)spp * h->nrhs;
     const double E = (double)ns * h->nt * h->g.nxyz;
     const SpecCoefs<T> c = pack_spec<T>(h, l);
-    const T *const *lam = space<T>(h).lam;
+    const T *lam = space<T>(h).mu;
     const int nt = h->nt;
     if (l == h->nlev - 1) {
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E, E * (5.0 * nt + 4.0));
@@ -611,26 +623,38 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     const T omega = (T)h->opt.omega;
     T *cur = u, *oth = tmp;
     bool zero = zero_init;
-    for (int k = 0; k < h->opt.nu1; ++k) {
+    const ProlongCoefs<T> pc = pack_prolong<T>(h);
+    const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
+    // pre-smoothing; the last step runs fused with the residual and the
+    // restriction (k_spec_down), the first post-smoothing step with the
+    // prolongation (k_spec_up)
+    for (int k = 0; k + 1 < h->opt.nu1; ++k) {
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.0 : 3.0) * E, E * (7.0 * nt + 6.0));
         CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, zero ? 1 : 0, h->stream));
         std::swap(cur, oth);
         zero = false;
     }
-    if (zero) CK(launch_zero<T>(cur, (long long)E, h->stream));
-    const ProlongCoefs<T> pc = pack_prolong<T>(h);
-    const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
-    {
+    if (h->opt.nu1 >= 1) {
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.5 : 3.5) * E, E * (14.0 * nt + 12.0));
+        CK(launch_spec_down<T>(zero ? nullptr : cur, oth, f, w.f[l + 1], lam, h->g, c, pc, omega,
+                               spp, nc, h->stream));
+        std::swap(cur, oth);
+    } else {
+        if (zero) CK(launch_zero<T>(cur, (long long)E, h->stream));
         KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 2.5 * E, E * (4.0 * nt + 2.0));
         CK(launch_spec_res_restrict<T>(cur, f, w.f[l + 1], lam, h->g, c, pc, spp, nc, h->stream));
     }
     CKS(svcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], oth, true));
-    {
+    if (h->opt.nu2 >= 1) {
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.5 * E, E * (9.0 * nt + 6.0));
+        CK(launch_spec_up<T>(w.u[l + 1], cur, oth, f, lam, h->g, c, pc, omega, spp, nc, h->stream));
+        std::swap(cur, oth);
+    } else {
         const double Ec = (double)nc * nt * h->g.nxyz;
         KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 5.0 * Ec, Ec * 4.0 * nt);
         CK(launch_prolong_add<T>(w.u[l + 1], cur, pc, h->g, nc, h->stream));
     }
-    for (int k = 0; k < h->opt.nu2; ++k) {
+    for (int k = 1; k < h->opt.nu2; ++k) {
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.0 * E, E * (7.0 * nt + 6.0));
         CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, 0, h->stream));
         std::swap(cur, oth);
@@ -656,7 +680,7 @@ int svcycle_top(st_handle h, T *u, const T *f, T *tmp) {
         const double E = (double)h->len * h->nrhs;
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E,
                   E * 2.0 * (h->opt.nu1 + h->opt.nu2 + 1) * (7.0 * h->nt + 6.0));
-        const cudaError_t e = launch_spec_vcycle<T>(f, u, dev_lvc<T>(h), space<T>(h).lam, h->g,
+        const cudaError_t e = launch_spec_vcycle<T>(f, u, dev_lvc<T>(h), space<T>(h).mu, h->g,
                                                     pack_prolong<T>(h), h->nlev, h->N, h->nrhs,
                                                     h->opt.nu1, h->opt.nu2, (T)h->opt.omega,
                                                     h->max_smem, h->nsm, h->stream);
@@ -818,6 +842,22 @@ int residual64(st_handle h, const double *u, const double *f, double *r) {
     return stencil<double>(h, 0, u, f, r, MODE_RES, false, 0, h->N * h->nrhs);
 }
 
+// The refinement residual r = f - L u of the mixed modes on FP64 data in
+// double-float arithmetic (about 48 significant bits, far below the FP32
+// inner solve's error) instead of FP64, which runs at 1/64 of the FP32 rate.
+int residual_df(st_handle h, const double *u, const double *f, double *r) {
+    const TimeCoefs<dfloat> tc = pack_time<dfloat>(h, 0, MODE_RES, false);
+    const double E = (double)h->N * h->nrhs * h->nt * h->g.nxyz;
+    const double planes_pt = (double)h->N * h->nrhs * (h->nt + 1) * h->g.nxyz;
+    const int W = 2 * h->p + 1;
+    const double fsp = 4.0 * W + (h->dim >= 2 ? 6.0 * W : 0) + (h->dim >= 3 ? 6.0 * W : 0);
+    KScope ks(h, ST_PROF_STENCILDF, 8.0 * (3.0 * E + (double)h->N * h->nrhs * h->g.nxyz),
+              planes_pt * fsp + E * 4.0 * h->nt);
+    CK((launch_stencil<double, dfloat>(u, f, r, space<double>(h).bands, h->g, tc, h->lv[0].nslab,
+                                       0, h->N * h->nrhs, h->stream)));
+    return ST_OK;
+}
+
 int solve_mg(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
     CKS(ensure_krylov(h));
     double *r = h->V[0], *e = h->Zk[0];
@@ -882,39 +922,51 @@ int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vecto
             CKS(prec(V[j], Zk[j]));
             CKS(apply(Zk[j], V[j + 1]));
             // classical Gram-Schmidt: one fused pass gives V^T w and w.w; a
-            // second pass runs only where ||w - V h|| < ||w|| / sqrt(2)
-            // (Kahan's "twice is enough" criterion)
+            // second pass runs only where ||w - V h||^2 < ||w||^2 / 2 (Kahan's
+            // "twice is enough" criterion; a looser one lets the FGMRES
+            // residual estimate drift from the true residual in FP32).  The
+            // decision is taken per right-hand side (a rhs that needs no
+            // second pass gets zero coefficients and keeps its first-pass
+            // values), so a batch gives each rhs its single-rhs result.
             std::vector<const T *> vw(V.begin(), V.begin() + j + 1);
             vw.push_back(V[j + 1]);
             CKS(dots<T>(h, j + 2, vw.data(), V[j + 1], hcol));
             std::vector<double> hsum((size_t)(j + 1) * R), neg((size_t)(j + 1) * R), rem2(R), post(R);
+            std::vector<char> rq(R, 0);
             bool reorth = false;
             for (int q = 0; q < R; ++q) {
                 double hh = 0.0;
                 for (int i = 0; i <= j; ++i) {
                     const double v = hcol[(size_t)i * R + q];
                     hsum[(size_t)i * R + q] = v;
-                    neg[(size_t)i * R + q] = -v;
                     hh += v * v;
                 }
                 const double ww = hcol[(size_t)(j + 1) * R + q];
                 rem2[q] = ww - hh;
-                if (act[q] && rem2[q] < 0.5 * ww) reorth = true;
+                rq[q] = act[q] && rem2[q] < 0.5 * ww;
+                reorth = reorth || rq[q];
+                for (int i = 0; i <= j; ++i)
+                    neg[(size_t)i * R + q] = rq[q] ? -hsum[(size_t)i * R + q] : 0.0;
             }
             if (reorth) {
                 CKS(vaxpy<T>(h, j + 1, V.data(), neg.data(), V[j + 1]));
                 CKS(dots<T>(h, j + 2, vw.data(), V[j + 1], hcol));
                 for (int q = 0; q < R; ++q) {
+                    if (!rq[q]) continue;
                     double hh = 0.0;
                     for (int i = 0; i <= j; ++i) {
                         const double v = hcol[(size_t)i * R + q];
                         hsum[(size_t)i * R + q] += v;
-                        neg[(size_t)i * R + q] = -v;
                         hh += v * v;
                     }
                     rem2[q] = hcol[(size_t)(j + 1) * R + q] - hh;
                 }
             }
+            // the remaining projection: the second pass's coefficients where
+            // it ran, else the first pass's
+            for (int q = 0; q < R; ++q)
+                for (int i = 0; i <= j; ++i)
+                    neg[(size_t)i * R + q] = rq[q] ? -hcol[(size_t)i * R + q] : -hsum[(size_t)i * R + q];
             std::vector<double> hn(R);
             for (int q = 0; q < R; ++q) {
                 hn[q] = std::sqrt(std::max(rem2[q], 0.0));
@@ -1054,14 +1106,14 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
             return stencil<float>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, (int)nsl);
         const double E = (double)nsl * h->nt * h->g.nxyz;
         KScope ks(h, ST_PROF_SPEC, 4.0 * 2.25 * E, E * (4.0 * h->nt + 2.0));
-        CK(launch_spec_op<float>(z, nullptr, w, h->s32.lam, h->g, c0, h->N, nsl, 0, h->stream));
+        CK(launch_spec_op<float>(z, nullptr, w, h->s32.mu, h->g, c0, h->N, nsl, 0, h->stream));
         return (int)ST_OK;
     };
     auto resid = [h, eig_basis, c0, nsl](const float *x, const float *b, float *r) {
         if (!eig_basis) return stencil<float>(h, 0, x, b, r, MODE_RES, false, 0, (int)nsl);
         const double E = (double)nsl * h->nt * h->g.nxyz;
         KScope ks(h, ST_PROF_SPEC, 4.0 * 3.25 * E, E * (4.0 * h->nt + 2.0));
-        CK(launch_spec_op<float>(x, b, r, h->s32.lam, h->g, c0, h->N, nsl, 1, h->stream));
+        CK(launch_spec_op<float>(x, b, r, h->s32.mu, h->g, c0, h->N, nsl, 1, h->stream));
         return (int)ST_OK;
     };
     auto prec = [h, eig_basis](const float *v, float *z) {
@@ -1071,7 +1123,7 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
     };
     const long long n0 = h->len * R;
     for (;;) {
-        CKS(residual64(h, u, rhs, h->r64));
+        CKS(residual_df(h, u, rhs, h->r64));
         CKS(norms<double>(h, h->r64, nr));
         worst = 0.0;
         std::vector<char> skip(R, 0);

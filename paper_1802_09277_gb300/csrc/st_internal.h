@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "dfloat.h"
+
 #include <cstdint>
 
 struct st_handle_s;
@@ -83,9 +85,10 @@ struct Bands {
 };
 
 // ---- launchers (kernels_stencil.cu) ----
-template <typename T>
+// T: data type in HBM; C: arithmetic (T itself, or dfloat on FP64 data)
+template <typename T, typename C = T>
 cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands, const Grid &g,
-                           const TimeCoefs<T> &tc, int slabs_per_prob, int slab0, int nslabs,
+                           const TimeCoefs<C> &tc, int slabs_per_prob, int slab0, int nslabs,
                            cudaStream_t s);
 
 // ---- launchers (kernels_transform.cu) ----
@@ -123,36 +126,47 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
 
 // ---- eigenbasis V-cycle kernels (kernels_spectral.cu) ----
 template <typename T>
-cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *const lam[3],
+cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *mu,
                                const Grid &g, const SpecCoefs<T> &c, T omega, int slabs_per_prob,
                                long long nslabs, int uin_zero, cudaStream_t s);
 template <typename T>
-cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *const lam[3],
+cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *mu,
                                      const Grid &g, const SpecCoefs<T> &c,
                                      const ProlongCoefs<T> &pc, int slabs_per_prob,
                                      long long ncoarse, cudaStream_t s);
+// last pre-smoothing step + residual + restriction (uin == nullptr: zero
+// incoming iterate); writes the smoothed slabs to uout and P_t^T r to fc
+template <typename T>
+cudaError_t launch_spec_down(const T *uin, T *uout, const T *f, T *fc, const T *mu,
+                             const Grid &g, const SpecCoefs<T> &c, const ProlongCoefs<T> &pc,
+                             T omega, int slabs_per_prob, long long ncoarse, cudaStream_t s);
+// uout = smooth(uin + P e) on the fine slabs of ncoarse coarse slabs
+template <typename T>
+cudaError_t launch_spec_up(const T *ec, const T *uin, T *uout, const T *f, const T *mu,
+                           const Grid &g, const SpecCoefs<T> &c, const ProlongCoefs<T> &pc,
+                           T omega, int slabs_per_prob, long long ncoarse, cudaStream_t s);
 // the whole eigenbasis V-cycle in shared memory (one launch); lvc_host: HOST
 // array of the nlev levels' coefficients (passed as a kernel parameter
 // block); cudaErrorNotSupported if one mode's levels do not fit in max_smem
 // bytes or there are too many levels
 template <typename T>
 cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc_host,
-                               const T *const lam[3], const Grid &g, const ProlongCoefs<T> &pc,
+                               const T *mu, const Grid &g, const ProlongCoefs<T> &pc,
                                int nlev, int N, int nrhs, int nu1, int nu2, T omega, int max_smem,
                                int nsm, cudaStream_t s);
 
 // eigenbasis operator: res = 1: out = f - L^ u; res = 0: out = L^ u
 template <typename T>
-cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *const lam[3], const Grid &g,
+cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *mu, const Grid &g,
                            const SpecCoefs<T> &c, int slabs_per_prob, long long nslabs, int res,
                            cudaStream_t s);
 
 // in place per (slab, mode): w <- (K_t + mu_k M_t)^{-1} w
 template <typename T>
-cudaError_t launch_mode_solve(T *w, const T *const lam[3], const Grid &g, const SpecCoefs<T> &c,
+cudaError_t launch_mode_solve(T *w, const T *mu, const Grid &g, const SpecCoefs<T> &c,
                               long long nslabs, cudaStream_t s);
 template <typename T>
-cudaError_t launch_spec_coarse(T *u, const T *f, const T *const lam[3], const Grid &g,
+cudaError_t launch_spec_coarse(T *u, const T *f, const T *mu, const Grid &g,
                                const SpecCoefs<T> &c, int slabs_per_prob, int nprob,
                                cudaStream_t s);
 

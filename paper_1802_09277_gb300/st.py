@@ -29,7 +29,7 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_time_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_poll", "st_serve_wait", "st_serve_stop"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
-                "vector", "dot", "tc", "spec"]
+                "vector", "dot", "tc", "spec", "stencil_df"]
 
 
 class StOptions(ctypes.Structure):
