@@ -1,0 +1,481 @@
+// Level kernels of the eigenbasis time-multigrid V-cycle (arXiv:1802.09277,
+// Sec. 3.1: damped block-Jacobi smoother, time coarsening by slab pairs, with
+// the slab inverse of Eq. 3.1 applied per spatial mode).
+//
+// In the spatial eigenbasis the slab block of mode k is the N_t x N_t matrix
+// A_k = K_t + mu_k M_t, with A_k^{-1} = X (Z + mu_k I)^{-1} Y (Eq. 3.1 for one
+// mode).  k_mode_inverse forms these inverses once per level in FP64 with the
+// Schur-form block solve and stores them in the V-cycle precision as
+// inv[(i * N_t + j) * nxyz + k] (mode fastest: a warp reads 32 consecutive
+// words per entry).  The level kernels apply them as dense N_t x N_t products
+// and use A_k^{-1} A_k = I to drop the residual from the smoothing step:
+//
+//   u_new = u + w A^{-1} (f - A u + e_0 u_prev) = (1 - w) u + w A^{-1} (f + e_0 u_prev)
+//
+// and, from a zero iterate (u = u_prev = 0, so A u_new = w f), the residual of
+// the smoothed iterate is r = f - A u_new + e_0 u_prev,new = (1 - w) f +
+// e_0 u_prev,new.  (e_0 u_prev is the coupling -B^ u_{n-1} = N_t u_{n-1}:
+// the last time dof of the previous slab enters the first equation.)
+//
+// One thread per spatial mode (x of a 2D grid) and slab or slab pair (y, z);
+// every kernel is a template on N_t so that all loops have exact length.
+//
+//  k_lv_smooth        one damped block-Jacobi step, out of place
+//  k_lv_down          the last pre-smoothing step, the residual of the new
+//                     iterate and its restriction P_t^T (slab pairs)
+//  k_lv_up            prolongation u + P_t e and the first post-smoothing step
+//  k_lv_coarse        exact solve of the coarsest level: forward substitution
+//                     u_n = A^{-1} (f_n + e_0 u_{n-1, last}) over its slabs
+//  k_lv_res_restrict  residual and restriction without smoothing (nu1 = 0)
+//  k_lv_op            the eigenbasis operator L^ (or f - L^ u) pointwise
+#include "spec_common.cuh"
+
+namespace st {
+
+namespace {
+
+template <typename T, int NT>
+__device__ __forceinline__ void load_inv(const T *__restrict__ inv, long long S, int k,
+                                         T (&m)[NT * NT]) {
+#pragma unroll
+    for (int e = 0; e < NT * NT; ++e) m[e] = inv[(long long)e * S + k];
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void matvec(const T (&m)[NT * NT], const T (&r)[NT], T (&v)[NT]) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        T a = T(0);
+#pragma unroll
+        for (int j = 0; j < NT; ++j) a += m[i * NT + j] * r[j];
+        v[i] = a;
+    }
+}
+
+// last row of A^{-1} times r
+template <typename T, int NT>
+__device__ __forceinline__ T lastrow(const T (&m)[NT * NT], const T (&r)[NT]) {
+    T a = T(0);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) a += m[(NT - 1) * NT + j] * r[j];
+    return a;
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void load_col(const T *__restrict__ x, long long base, long long S,
+                                         T (&v)[NT]) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) v[i] = x[base + (long long)i * S];
+}
+
+template <typename T, int NT>
+__device__ __forceinline__ void store_col(T *__restrict__ x, long long base, long long S,
+                                          const T (&v)[NT]) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) x[base + (long long)i * S] = v[i];
+}
+
+// r = f - (K_t + mu M_t) u + e_0 uprev
+template <typename T, int NT>
+__device__ __forceinline__ void op_residual(const SpecCoefs<T> &c, T mu, const T (&u)[NT],
+                                            T uprev, T (&r)[NT]) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        T a = r[i];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) a -= (c.Kt[i * NTMAX + j] + mu * c.Mt[i * NTMAX + j]) * u[j];
+        if (i == 0) a += uprev;
+        r[i] = a;
+    }
+}
+
+// fc = P_t^T [ra; rb]
+template <typename T, int NT>
+__device__ __forceinline__ void restrict_pair(const ProlongCoefs<T> &pc, const T (&ra)[NT],
+                                              const T (&rb)[NT], T (&fc)[NT]) {
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        T s = T(0);
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+            s += pc.P[j * NTMAX + i] * ra[j] + pc.P[(NT + j) * NTMAX + i] * rb[j];
+        fc[i] = s;
+    }
+}
+
+}  // namespace
+
+// inv[(i nt + j) S + k] = (A_k^{-1})_{ij}: column j is the block solve of e_j
+template <typename TO>
+__global__ void __launch_bounds__(256)
+    k_mode_inverse(TO *__restrict__ inv, const double *__restrict__ mu_tab, Grid g,
+                   const __grid_constant__ SpecCoefs<double> c) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= g.nxyz) return;
+    const long long S = g.nxyz;
+    const int nt = c.nt;
+    const double mu = mu_tab[k];
+    for (int j = 0; j < nt; ++j) {
+        double r[NTMAX], v[NTMAX];
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i) r[i] = (i == j) ? 1.0 : 0.0;
+        spec_block_solve(c, mu, r, v);
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i)
+            if (i < nt) inv[((long long)i * nt + j) * S + k] = (TO)v[i];
+    }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(256)
+    k_lv_smooth(const T *__restrict__ uin, T *__restrict__ uout, const T *__restrict__ f,
+                const T *__restrict__ inv, long long S, T omega, int spp, long long nslabs,
+                int zero) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = slab_index();
+    if (k >= S || n >= nslabs) return;
+    const long long base = n * NT * S + k;
+    T m[NT * NT], r[NT], v[NT];
+    load_inv<T, NT>(inv, S, k, m);
+    load_col<T, NT>(f, base, S, r);
+    if (zero) {
+        matvec<T, NT>(m, r, v);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) v[i] *= omega;
+    } else {
+        T u[NT];
+        load_col<T, NT>(uin, base, S, u);
+        if (((int)n % spp) != 0) r[0] += uin[base - S];
+        matvec<T, NT>(m, r, v);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) v[i] = (T(1) - omega) * u[i] + omega * v[i];
+    }
+    store_col<T, NT>(uout, base, S, v);
+}
+
+template <typename T, int NT, bool ZERO>
+__global__ void __launch_bounds__(256)
+    k_lv_down(const T *__restrict__ uin, T *__restrict__ uout, const T *__restrict__ f,
+              T *__restrict__ fc, const T *__restrict__ inv, const T *__restrict__ mu_tab,
+              long long S, const __grid_constant__ SpecCoefs<T> c,
+              const __grid_constant__ ProlongCoefs<T> pc, T omega, int spp, long long ncoarse) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long mc = slab_index();
+    if (k >= S || mc >= ncoarse) return;
+    const long long a = 2 * mc;
+    const bool first = ((int)a % spp) == 0;
+    const long long ba = a * NT * S + k, bb = ba + (long long)NT * S;
+    T m[NT * NT];
+    load_inv<T, NT>(inv, S, k, m);
+    // the new last entry of slab a - 1 (its old one is what slabs a sees)
+    T new_prev = T(0), old_prev = T(0);
+    if (!first) {
+        const long long bp = ba - (long long)NT * S;
+        T rp[NT];
+        load_col<T, NT>(f, bp, S, rp);
+        if (!ZERO) {
+            old_prev = uin[bp + (long long)(NT - 1) * S];
+            if (((int)a - 1) % spp != 0) rp[0] += uin[bp - S];
+            new_prev = (T(1) - omega) * old_prev + omega * lastrow<T, NT>(m, rp);
+        } else {
+            new_prev = omega * lastrow<T, NT>(m, rp);
+        }
+    }
+    T fa[NT], fb[NT], ua[NT], ub[NT];
+    load_col<T, NT>(f, ba, S, fa);
+    load_col<T, NT>(f, bb, S, fb);
+    if (ZERO) {
+        matvec<T, NT>(m, fa, ua);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) ua[i] *= omega;
+        matvec<T, NT>(m, fb, ub);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) ub[i] *= omega;
+        store_col<T, NT>(uout, ba, S, ua);
+        store_col<T, NT>(uout, bb, S, ub);
+        // residual of the smoothed iterate from zero: (1 - w) f + e_0 u_prev,new
+        T ra[NT], rb[NT], out[NT];
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            ra[i] = (T(1) - omega) * fa[i];
+            rb[i] = (T(1) - omega) * fb[i];
+        }
+        ra[0] += new_prev;
+        rb[0] += ua[NT - 1];
+        restrict_pair<T, NT>(pc, ra, rb, out);
+        store_col<T, NT>(fc, mc * NT * S + k, S, out);
+    } else {
+        T oa[NT], ob[NT], r[NT];
+        load_col<T, NT>(uin, ba, S, oa);
+        load_col<T, NT>(uin, bb, S, ob);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) r[i] = fa[i];
+        r[0] += old_prev;
+        matvec<T, NT>(m, r, ua);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) ua[i] = (T(1) - omega) * oa[i] + omega * ua[i];
+#pragma unroll
+        for (int i = 0; i < NT; ++i) r[i] = fb[i];
+        r[0] += oa[NT - 1];
+        matvec<T, NT>(m, r, ub);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) ub[i] = (T(1) - omega) * ob[i] + omega * ub[i];
+        store_col<T, NT>(uout, ba, S, ua);
+        store_col<T, NT>(uout, bb, S, ub);
+        // residual of the smoothed iterate, formed directly
+        const T mu = mu_tab[k];
+        T out[NT];
+        op_residual<T, NT>(c, mu, ua, new_prev, fa);
+        op_residual<T, NT>(c, mu, ub, ua[NT - 1], fb);
+        restrict_pair<T, NT>(pc, fa, fb, out);
+        store_col<T, NT>(fc, mc * NT * S + k, S, out);
+    }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(256)
+    k_lv_up(const T *__restrict__ ec, const T *__restrict__ uin, T *__restrict__ uout,
+            const T *__restrict__ f, const T *__restrict__ inv, long long S,
+            const __grid_constant__ ProlongCoefs<T> pc, T omega, int spp, long long ncoarse) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long mc = slab_index();
+    if (k >= S || mc >= ncoarse) return;
+    const long long a = 2 * mc;
+    const long long ba = a * NT * S + k, bb = ba + (long long)NT * S;
+    T e[NT], ua[NT], ub[NT];
+    load_col<T, NT>(ec, mc * NT * S + k, S, e);
+    load_col<T, NT>(uin, ba, S, ua);
+    load_col<T, NT>(uin, bb, S, ub);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        T pa = T(0), pb = T(0);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            pa += pc.P[j * NTMAX + i] * e[i];
+            pb += pc.P[(NT + j) * NTMAX + i] * e[i];
+        }
+        ua[j] += pa;
+        ub[j] += pb;
+    }
+    T uprev = T(0);
+    if (((int)a % spp) != 0) {  // corrected last entry of slab a - 1, from coarse slab mc - 1
+        T ep[NT];
+        load_col<T, NT>(ec, (mc - 1) * NT * S + k, S, ep);
+        T pl = T(0);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) pl += pc.P[(2 * NT - 1) * NTMAX + i] * ep[i];
+        uprev = uin[ba - S] + pl;
+    }
+    T m[NT * NT], r[NT], v[NT];
+    load_inv<T, NT>(inv, S, k, m);
+    load_col<T, NT>(f, ba, S, r);
+    r[0] += uprev;
+    matvec<T, NT>(m, r, v);
+    const T a_last = ua[NT - 1];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) v[i] = (T(1) - omega) * ua[i] + omega * v[i];
+    store_col<T, NT>(uout, ba, S, v);
+    load_col<T, NT>(f, bb, S, r);
+    r[0] += a_last;
+    matvec<T, NT>(m, r, v);
+#pragma unroll
+    for (int i = 0; i < NT; ++i) v[i] = (T(1) - omega) * ub[i] + omega * v[i];
+    store_col<T, NT>(uout, bb, S, v);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(256)
+    k_lv_coarse(T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ inv, long long S,
+                int spp, long long nprob) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long q = slab_index();
+    if (k >= S || q >= nprob) return;
+    T m[NT * NT];
+    load_inv<T, NT>(inv, S, k, m);
+    T prev = T(0);
+    for (int n = 0; n < spp; ++n) {
+        const long long base = ((q * spp + n) * NT) * S + k;
+        T r[NT], v[NT];
+        load_col<T, NT>(f, base, S, r);
+        r[0] += prev;
+        matvec<T, NT>(m, r, v);
+        store_col<T, NT>(u, base, S, v);
+        prev = v[NT - 1];
+    }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(256)
+    k_lv_res_restrict(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ fc,
+                      const T *__restrict__ mu_tab, long long S,
+                      const __grid_constant__ SpecCoefs<T> c,
+                      const __grid_constant__ ProlongCoefs<T> pc, int spp, long long ncoarse) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long mc = slab_index();
+    if (k >= S || mc >= ncoarse) return;
+    const long long a = 2 * mc;
+    const long long ba = a * NT * S + k, bb = ba + (long long)NT * S;
+    const T mu = mu_tab[k];
+    T ua[NT], ub[NT], ra[NT], rb[NT], out[NT];
+    load_col<T, NT>(u, ba, S, ua);
+    load_col<T, NT>(u, bb, S, ub);
+    load_col<T, NT>(f, ba, S, ra);
+    load_col<T, NT>(f, bb, S, rb);
+    const T uprev = (((int)a % spp) != 0) ? u[ba - S] : T(0);
+    op_residual<T, NT>(c, mu, ua, uprev, ra);
+    op_residual<T, NT>(c, mu, ub, ua[NT - 1], rb);
+    restrict_pair<T, NT>(pc, ra, rb, out);
+    store_col<T, NT>(fc, mc * NT * S + k, S, out);
+}
+
+// res = 1: out = f - L^ u, else out = L^ u
+template <typename T, int NT>
+__global__ void __launch_bounds__(256)
+    k_lv_op(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out,
+            const T *__restrict__ mu_tab, long long S, const __grid_constant__ SpecCoefs<T> c,
+            int spp, long long nslabs, int res) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = slab_index();
+    if (k >= S || n >= nslabs) return;
+    const long long base = n * NT * S + k;
+    const T mu = mu_tab[k];
+    T uu[NT], r[NT];
+    load_col<T, NT>(u, base, S, uu);
+    if (res) {
+        load_col<T, NT>(f, base, S, r);
+    } else {
+#pragma unroll
+        for (int i = 0; i < NT; ++i) r[i] = T(0);
+    }
+    const T up = (((int)n % spp) != 0) ? u[base - S] : T(0);
+    op_residual<T, NT>(c, mu, uu, up, r);
+    if (!res) {
+#pragma unroll
+        for (int i = 0; i < NT; ++i) r[i] = -r[i];
+    }
+    store_col<T, NT>(out, base, S, r);
+}
+
+// ---- launchers: dispatch on N_t ----
+#define ST_NT_DISPATCH(nt, CALL)          \
+    switch (nt) {                         \
+        case 2: { constexpr int NT = 2; CALL; break; } \
+        case 3: { constexpr int NT = 3; CALL; break; } \
+        case 4: { constexpr int NT = 4; CALL; break; } \
+        case 5: { constexpr int NT = 5; CALL; break; } \
+        case 6: { constexpr int NT = 6; CALL; break; } \
+        case 7: { constexpr int NT = 7; CALL; break; } \
+        case 8: { constexpr int NT = 8; CALL; break; } \
+        default: return cudaErrorNotSupported;         \
+    }
+
+template <typename TO>
+cudaError_t launch_mode_inverse(TO *inv, const double *mu64, const Grid &g,
+                                const SpecCoefs<double> &c, cudaStream_t s) {
+    if (g.nxyz <= 0) return cudaSuccess;
+    const ModeLaunch L = mode_launch(g.nxyz, 1);
+    k_mode_inverse<TO><<<L.grid, L.block, 0, s>>>(inv, mu64, g, c);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *inv, const Grid &g,
+                               int nt, T omega, int spp, long long nslabs, int uin_zero,
+                               cudaStream_t s) {
+    if (nslabs <= 0 || g.nxyz <= 0) return cudaSuccess;
+    const ModeLaunch L = mode_launch(g.nxyz, nslabs);
+    ST_NT_DISPATCH(nt, (k_lv_smooth<T, NT><<<L.grid, L.block, 0, s>>>(
+                           uin, uout, f, inv, g.nxyz, omega, spp, nslabs, uin_zero)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_down(const T *uin, T *uout, const T *f, T *fc, const T *inv,
+                             const T *mu, const Grid &g, const SpecCoefs<T> &c,
+                             const ProlongCoefs<T> &pc, T omega, int spp, long long ncoarse,
+                             cudaStream_t s) {
+    if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
+    const ModeLaunch L = mode_launch(g.nxyz, ncoarse);
+    if (uin) {
+        ST_NT_DISPATCH(c.nt, (k_lv_down<T, NT, false><<<L.grid, L.block, 0, s>>>(
+                                 uin, uout, f, fc, inv, mu, g.nxyz, c, pc, omega, spp, ncoarse)));
+    } else {
+        ST_NT_DISPATCH(c.nt, (k_lv_down<T, NT, true><<<L.grid, L.block, 0, s>>>(
+                                 uin, uout, f, fc, inv, mu, g.nxyz, c, pc, omega, spp, ncoarse)));
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_up(const T *ec, const T *uin, T *uout, const T *f, const T *inv,
+                           const Grid &g, const ProlongCoefs<T> &pc, T omega, int spp,
+                           long long ncoarse, cudaStream_t s) {
+    if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
+    const ModeLaunch L = mode_launch(g.nxyz, ncoarse);
+    ST_NT_DISPATCH(pc.nt, (k_lv_up<T, NT><<<L.grid, L.block, 0, s>>>(
+                              ec, uin, uout, f, inv, g.nxyz, pc, omega, spp, ncoarse)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_coarse(T *u, const T *f, const T *inv, const Grid &g, int nt, int spp,
+                               int nprob, cudaStream_t s) {
+    if (nprob <= 0 || g.nxyz <= 0) return cudaSuccess;
+    const ModeLaunch L = mode_launch(g.nxyz, nprob);
+    ST_NT_DISPATCH(nt, (k_lv_coarse<T, NT><<<L.grid, L.block, 0, s>>>(u, f, inv, g.nxyz, spp,
+                                                                       (long long)nprob)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *mu, const Grid &g,
+                                     const SpecCoefs<T> &c, const ProlongCoefs<T> &pc, int spp,
+                                     long long ncoarse, cudaStream_t s) {
+    if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
+    const ModeLaunch L = mode_launch(g.nxyz, ncoarse);
+    ST_NT_DISPATCH(c.nt, (k_lv_res_restrict<T, NT><<<L.grid, L.block, 0, s>>>(
+                             u, f, fc, mu, g.nxyz, c, pc, spp, ncoarse)));
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *mu, const Grid &g,
+                           const SpecCoefs<T> &c, int spp, long long nslabs, int res,
+                           cudaStream_t s) {
+    if (nslabs <= 0 || g.nxyz <= 0) return cudaSuccess;
+    const ModeLaunch L = mode_launch(g.nxyz, nslabs);
+    ST_NT_DISPATCH(c.nt, (k_lv_op<T, NT><<<L.grid, L.block, 0, s>>>(u, f, out, mu, g.nxyz, c,
+                                                                      spp, nslabs, res)));
+    return cudaGetLastError();
+}
+#undef ST_NT_DISPATCH
+
+template cudaError_t launch_mode_inverse<double>(double *, const double *, const Grid &,
+                                                 const SpecCoefs<double> &, cudaStream_t);
+template cudaError_t launch_mode_inverse<float>(float *, const double *, const Grid &,
+                                                const SpecCoefs<double> &, cudaStream_t);
+#define ST_INST(T)                                                                              \
+    template cudaError_t launch_spec_smooth<T>(const T *, T *, const T *, const T *,            \
+                                               const Grid &, int, T, int, long long, int,       \
+                                               cudaStream_t);                                   \
+    template cudaError_t launch_spec_down<T>(const T *, T *, const T *, T *, const T *,         \
+                                             const T *, const Grid &, const SpecCoefs<T> &,     \
+                                             const ProlongCoefs<T> &, T, int, long long,        \
+                                             cudaStream_t);                                     \
+    template cudaError_t launch_spec_up<T>(const T *, const T *, T *, const T *, const T *,     \
+                                           const Grid &, const ProlongCoefs<T> &, T, int,       \
+                                           long long, cudaStream_t);                            \
+    template cudaError_t launch_spec_coarse<T>(T *, const T *, const T *, const Grid &, int,    \
+                                               int, int, cudaStream_t);                         \
+    template cudaError_t launch_spec_res_restrict<T>(const T *, const T *, T *, const T *,      \
+                                                     const Grid &, const SpecCoefs<T> &,        \
+                                                     const ProlongCoefs<T> &, int, long long,   \
+                                                     cudaStream_t);                             \
+    template cudaError_t launch_spec_op<T>(const T *, const T *, T *, const T *, const Grid &,  \
+                                           const SpecCoefs<T> &, int, long long, int,           \
+                                           cudaStream_t);
+ST_INST(double)
+ST_INST(float)
+#undef ST_INST
+
+}  // namespace st

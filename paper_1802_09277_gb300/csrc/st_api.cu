@@ -92,6 +92,9 @@ struct st_handle_s {
     int max_smem = 48 * 1024;  // opt-in shared memory per block
     std::vector<SpecCoefs<float>> lvc32;   // per-level coefficients for the fused V-cycle
     std::vector<SpecCoefs<double>> lvc64;
+    // per level: the per-mode slab inverses of the eigenbasis V-cycle
+    std::vector<float *> inv32;
+    std::vector<double *> inv64;
     // autotuned transform per axis: -1 = not tuned (heuristic), 0 = CUDA
     // cores, k > 0 = tensor cores with at most k CTAs per SM
     int tune[3] = {-1, -1, -1};
@@ -602,6 +605,30 @@ int vconvert(st_handle h, const Tin *x, Tout *y) {
     return ST_OK;
 }
 
+template <typename T>
+std::vector<T *> &inv_tabs(st_handle h);
+template <>
+std::vector<double *> &inv_tabs<double>(st_handle h) { return h->inv64; }
+template <>
+std::vector<float *> &inv_tabs<float>(st_handle h) { return h->inv32; }
+
+// The per-mode slab inverses (K_t + mu_k M_t)^{-1} of every level (Eq. 3.1
+// per spatial mode), formed once in FP64 and kept in precision T.
+template <typename T>
+int ensure_inv(st_handle h) {
+    std::vector<T *> &tabs = inv_tabs<T>(h);
+    if ((int)tabs.size() == h->nlev) return ST_OK;
+    tabs.assign(h->nlev, nullptr);
+    const size_t e = (size_t)h->nt * h->nt * (size_t)h->g.nxyz;
+    for (int l = 0; l < h->nlev; ++l) {
+        void *p;
+        CKS(dalloc(h, e * sizeof(T), &p));
+        tabs[l] = (T *)p;
+        CK(launch_mode_inverse<T>(tabs[l], h->s64.mu, h->g, pack_spec<double>(h, l), h->stream));
+    }
+    return ST_OK;
+}
+
 // ---- the same V-cycle in the spatial eigenbasis -------------------------------
 // u, f are eigenbasis coefficients of level l; tmp is a free buffer of at
 // least the level's size.  Identical in exact arithmetic to vcycle() after
@@ -614,9 +641,12 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     const SpecCoefs<T> c = pack_spec<T>(h, l);
     const T *lam = space<T>(h).mu;
     const int nt = h->nt;
+    CKS(ensure_inv<T>(h));
+    const T *inv = inv_tabs<T>(h)[l];
     if (l == h->nlev - 1) {
-        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E, E * (5.0 * nt + 4.0));
-        CK(launch_spec_coarse<T>(u, f, lam, h->g, c, spp, h->nrhs, h->stream));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * (2.0 * E + nt * nt * h->g.nxyz),
+                  E * 2.0 * nt);
+        CK(launch_spec_coarse<T>(u, f, inv, h->g, nt, spp, h->nrhs, h->stream));
         return ST_OK;
     }
     Work<T> &w = work<T>(h);
@@ -629,15 +659,17 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     // restriction (k_spec_down), the first post-smoothing step with the
     // prolongation (k_spec_up)
     for (int k = 0; k + 1 < h->opt.nu1; ++k) {
-        KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.0 : 3.0) * E, E * (7.0 * nt + 6.0));
-        CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, zero ? 1 : 0, h->stream));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.0 : 3.0) * E, E * (2.0 * nt + 3.0));
+        CK(launch_spec_smooth<T>(cur, oth, f, inv, h->g, nt, omega, spp, ns, zero ? 1 : 0,
+                                 h->stream));
         std::swap(cur, oth);
         zero = false;
     }
     if (h->opt.nu1 >= 1) {
-        KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.5 : 3.5) * E, E * (14.0 * nt + 12.0));
-        CK(launch_spec_down<T>(zero ? nullptr : cur, oth, f, w.f[l + 1], lam, h->g, c, pc, omega,
-                               spp, nc, h->stream));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.5 : 3.5) * E,
+                  E * (zero ? 4.0 * nt + 4.0 : 8.0 * nt + 8.0));
+        CK(launch_spec_down<T>(zero ? nullptr : cur, oth, f, w.f[l + 1], inv, lam, h->g, c, pc,
+                               omega, spp, nc, h->stream));
         std::swap(cur, oth);
     } else {
         if (zero) CK(launch_zero<T>(cur, (long long)E, h->stream));
@@ -646,8 +678,8 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     }
     CKS(svcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], oth, true));
     if (h->opt.nu2 >= 1) {
-        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.5 * E, E * (9.0 * nt + 6.0));
-        CK(launch_spec_up<T>(w.u[l + 1], cur, oth, f, lam, h->g, c, pc, omega, spp, nc, h->stream));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.5 * E, E * (4.0 * nt + 4.0));
+        CK(launch_spec_up<T>(w.u[l + 1], cur, oth, f, inv, h->g, pc, omega, spp, nc, h->stream));
         std::swap(cur, oth);
     } else {
         const double Ec = (double)nc * nt * h->g.nxyz;
@@ -655,8 +687,8 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
         CK(launch_prolong_add<T>(w.u[l + 1], cur, pc, h->g, nc, h->stream));
     }
     for (int k = 1; k < h->opt.nu2; ++k) {
-        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.0 * E, E * (7.0 * nt + 6.0));
-        CK(launch_spec_smooth<T>(cur, oth, f, lam, h->g, c, omega, spp, ns, 0, h->stream));
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.0 * E, E * (2.0 * nt + 3.0));
+        CK(launch_spec_smooth<T>(cur, oth, f, inv, h->g, nt, omega, spp, ns, 0, h->stream));
         std::swap(cur, oth);
     }
     if (cur != u)
@@ -1356,6 +1388,8 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
             h->lvc32[l] = pack_spec<float>(h, l);
         }
     }
+    // the eigenbasis V-cycle's per-mode inverses, in its working precision
+    if (o.basis == ST_BASIS_SPECTRAL) CKS(h->mixed ? ensure_inv<float>(h) : ensure_inv<double>(h));
     h->nblk_dot = 2 * h->nsm;
     void *p;
     CKS(dalloc(h, sizeof(double) * MAXV * h->nrhs * h->nblk_dot, &p));

@@ -125,26 +125,44 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
                            int nsm, cudaStream_t s, int ctas_per_sm = 0);
 
 // ---- eigenbasis V-cycle kernels (kernels_spectral.cu) ----
+// ---- eigenbasis level kernels (kernels_modes.cu) ----
+// inv: per-mode slab inverses of one level, inv[(i nt + j) nxyz + k]
+// = ((K_t + mu_k M_t)^{-1})_{ij}; built by launch_mode_inverse from the FP64
+// factors.  spp: slabs per problem on the level (slab pairs never straddle).
+template <typename TO>
+cudaError_t launch_mode_inverse(TO *inv, const double *mu64, const Grid &g,
+                                const SpecCoefs<double> &c, cudaStream_t s);
+// uout = (1 - omega) uin + omega A^{-1} (f + e_0 uin_prev) (uin_zero: uin = 0)
 template <typename T>
-cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *mu,
-                               const Grid &g, const SpecCoefs<T> &c, T omega, int slabs_per_prob,
-                               long long nslabs, int uin_zero, cudaStream_t s);
-template <typename T>
-cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *mu,
-                                     const Grid &g, const SpecCoefs<T> &c,
-                                     const ProlongCoefs<T> &pc, int slabs_per_prob,
-                                     long long ncoarse, cudaStream_t s);
+cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *inv, const Grid &g,
+                               int nt, T omega, int spp, long long nslabs, int uin_zero,
+                               cudaStream_t s);
 // last pre-smoothing step + residual + restriction (uin == nullptr: zero
 // incoming iterate); writes the smoothed slabs to uout and P_t^T r to fc
 template <typename T>
-cudaError_t launch_spec_down(const T *uin, T *uout, const T *f, T *fc, const T *mu,
-                             const Grid &g, const SpecCoefs<T> &c, const ProlongCoefs<T> &pc,
-                             T omega, int slabs_per_prob, long long ncoarse, cudaStream_t s);
+cudaError_t launch_spec_down(const T *uin, T *uout, const T *f, T *fc, const T *inv,
+                             const T *mu, const Grid &g, const SpecCoefs<T> &c,
+                             const ProlongCoefs<T> &pc, T omega, int spp, long long ncoarse,
+                             cudaStream_t s);
 // uout = smooth(uin + P e) on the fine slabs of ncoarse coarse slabs
 template <typename T>
-cudaError_t launch_spec_up(const T *ec, const T *uin, T *uout, const T *f, const T *mu,
-                           const Grid &g, const SpecCoefs<T> &c, const ProlongCoefs<T> &pc,
-                           T omega, int slabs_per_prob, long long ncoarse, cudaStream_t s);
+cudaError_t launch_spec_up(const T *ec, const T *uin, T *uout, const T *f, const T *inv,
+                           const Grid &g, const ProlongCoefs<T> &pc, T omega, int spp,
+                           long long ncoarse, cudaStream_t s);
+// exact solve of the coarsest level (forward substitution over its slabs)
+template <typename T>
+cudaError_t launch_spec_coarse(T *u, const T *f, const T *inv, const Grid &g, int nt, int spp,
+                               int nprob, cudaStream_t s);
+// residual of slab pairs restricted onto the coarse slabs (no smoothing)
+template <typename T>
+cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *mu, const Grid &g,
+                                     const SpecCoefs<T> &c, const ProlongCoefs<T> &pc, int spp,
+                                     long long ncoarse, cudaStream_t s);
+// res = 1: out = f - L^ u, else out = L^ u
+template <typename T>
+cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *mu, const Grid &g,
+                           const SpecCoefs<T> &c, int spp, long long nslabs, int res,
+                           cudaStream_t s);
 // the whole eigenbasis V-cycle in shared memory (one launch); lvc_host: HOST
 // array of the nlev levels' coefficients (passed as a kernel parameter
 // block); cudaErrorNotSupported if one mode's levels do not fit in max_smem
@@ -155,20 +173,10 @@ cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc_ho
                                int nlev, int N, int nrhs, int nu1, int nu2, T omega, int max_smem,
                                int nsm, cudaStream_t s);
 
-// eigenbasis operator: res = 1: out = f - L^ u; res = 0: out = L^ u
-template <typename T>
-cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *mu, const Grid &g,
-                           const SpecCoefs<T> &c, int slabs_per_prob, long long nslabs, int res,
-                           cudaStream_t s);
-
 // in place per (slab, mode): w <- (K_t + mu_k M_t)^{-1} w
 template <typename T>
 cudaError_t launch_mode_solve(T *w, const T *mu, const Grid &g, const SpecCoefs<T> &c,
                               long long nslabs, cudaStream_t s);
-template <typename T>
-cudaError_t launch_spec_coarse(T *u, const T *f, const T *mu, const Grid &g,
-                               const SpecCoefs<T> &c, int slabs_per_prob, int nprob,
-                               cudaStream_t s);
 
 // ---- vector kernels (kernels_vector.cu) ----
 template <typename Tin, typename Tout>
