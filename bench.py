@@ -320,6 +320,7 @@ def gpu_arm(args, rank, world):
         "per_launch_ms": per_launch_ms, "launches": launches // max(args.steps, 1),
         "launches_total": launches, "clocks": clk, "peaks": peaks, "peak_src": peak_src,
         "variants": variants, "tuning": tuning,
+        "traffic_key": (args.workload, args.precision, args.basis, args.outer),
     }
     return result
 
@@ -381,6 +382,14 @@ def make_len(d, spans, p, N, ne):
     return N * (ne + p) * nx
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean
+# over the class's launches in one solve, ncu with its default cache flush
+# between launches) for (workload, precision, basis, outer, kernel class);
+# the capture is summarised in the profiles/ file named beside it.  An entry
+# is removed whenever a kernel of the class changes.
+TRAFFIC = {}
+
+
 def roofline_entry(r):
     """Roofline of the kernel class with the largest share of device time:
     achieved = algorithmic bytes (or flops) of its launches / their summed
@@ -390,8 +399,12 @@ def roofline_entry(r):
     pd = r["prof"][dom]
     secs = pd["ms"] / 1e3
     clk_max = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    tr = TRAFFIC.get(r["traffic_key"] + (dom,))
     base = {"kernel": dom, "per_launch_ms": pd["ms"] / max(1, pd["launches"]),
-            "launches": pd["launches"], "traffic": None}
+            "launches": pd["launches"], "traffic": tr[0] if tr else None,
+            "algorithmic_bytes_per_launch": pd["bytes"] / max(1, pd["launches"])}
+    if tr:
+        base["traffic_source"] = tr[1]
     if dom == "gemm32":  # FP32 FMA on CUDA cores: 152 SMs x 128 lanes x 2 flop x max clock
         peak = 152 * 128 * 2 * clk_max / 1e12
         ach = pd["flops"] / secs / 1e12

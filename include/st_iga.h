@@ -62,6 +62,8 @@ extern "C" {
 #define ST_RSCHUR 0  /* real Schur form, 2x2 blocks for complex pairs (Sec. 3.5)   */
 #define ST_EIG    1  /* diagonalisation with complex eigenvalues (Sec. 3.3); setup
                         fails with ST_ERR_ILL_CONDITIONED if cond(X) > 1e8        */
+#define ST_CSCHUR 2  /* complex Schur form, triangular solve with complex shifts
+                        (Sec. 3.4, Algorithm 1)                                   */
 
 /* precision of the multigrid preconditioner (the outer iteration is FP64) */
 #define ST_FP64        0  /* everything FP64                                  */

@@ -679,5 +679,72 @@ double complex_cond2(int n, const Mat &Are, const Mat &Aim) {
     return complex_norm2(n, A) * complex_norm2(n, B);
 }
 
+// Complex Schur form from the real one: each 2x2 block B of T (a complex pair
+// lambda, conj(lambda)) is made upper triangular by the unitary 2x2 matrix
+// G = [g, g_perp] whose first column is the unit eigenvector g of B for
+// lambda; T <- G^H T G and Q <- Q G on the two rows / columns of the block.
+// The blocks are disjoint, so the updates commute.  A = Q T Q^H with T
+// complex upper triangular (diagonal = the eigenvalues) and Q unitary.
+bool complex_schur(int n, const Mat &Q, const Mat &T, const std::vector<int> &blk, Mat &Qre,
+                   Mat &Qim, Mat &Tre, Mat &Tim, std::string &err) {
+    using C = std::complex<double>;
+    std::vector<C> q(n * n), t(n * n);
+    for (int i = 0; i < n * n; ++i) {
+        q[i] = Q[i];
+        t[i] = T[i];
+    }
+    for (int i = 1; i < n; ++i) {
+        if (!blk[i]) continue;
+        const int r0 = i - 1, r1 = i;
+        const double a = T[r0 * n + r0], b = T[r0 * n + r1], c = T[r1 * n + r0], d = T[r1 * n + r1];
+        const double disc = (a - d) * (a - d) + 4.0 * b * c;
+        if (!(disc < 0)) {
+            err = "2x2 Schur block with real eigenvalues";
+            return false;
+        }
+        const C lam(0.5 * (a + d), 0.5 * std::sqrt(-disc));
+        // (B - lambda I) v = 0: v = (b, lambda - a), or (lambda - d, c)
+        C v0(b, 0.0), v1 = lam - a;
+        if (std::abs(v0) + std::abs(v1) < std::abs(lam - d) + std::abs(c)) {
+            v0 = lam - d;
+            v1 = C(c, 0.0);
+        }
+        const double nv = std::sqrt(std::norm(v0) + std::norm(v1));
+        if (!(nv > 0)) {
+            err = "degenerate 2x2 Schur block";
+            return false;
+        }
+        v0 /= nv;
+        v1 /= nv;
+        // G = [[v0, -conj(v1)], [v1, conj(v0)]]
+        const C g00 = v0, g01 = -std::conj(v1), g10 = v1, g11 = std::conj(v0);
+        for (int row = 0; row < n; ++row) {  // columns r0, r1 of T and Q times G
+            const C t0 = t[row * n + r0], t1 = t[row * n + r1];
+            t[row * n + r0] = t0 * g00 + t1 * g10;
+            t[row * n + r1] = t0 * g01 + t1 * g11;
+            const C q0 = q[row * n + r0], q1 = q[row * n + r1];
+            q[row * n + r0] = q0 * g00 + q1 * g10;
+            q[row * n + r1] = q0 * g01 + q1 * g11;
+        }
+        for (int col = 0; col < n; ++col) {  // rows r0, r1 of T times G^H
+            const C t0 = t[r0 * n + col], t1 = t[r1 * n + col];
+            t[r0 * n + col] = std::conj(g00) * t0 + std::conj(g10) * t1;
+            t[r1 * n + col] = std::conj(g01) * t0 + std::conj(g11) * t1;
+        }
+        t[r1 * n + r0] = 0.0;  // eliminated (rounding residue)
+    }
+    Qre.assign(n * n, 0.0);
+    Qim.assign(n * n, 0.0);
+    Tre.assign(n * n, 0.0);
+    Tim.assign(n * n, 0.0);
+    for (int i = 0; i < n * n; ++i) {
+        Qre[i] = q[i].real();
+        Qim[i] = q[i].imag();
+        Tre[i] = t[i].real();
+        Tim[i] = t[i].imag();
+    }
+    return true;
+}
+
 }  // namespace host
 }  // namespace st

@@ -64,6 +64,12 @@ bool schur_eigvecs(int n, const Mat &Q, const Mat &T, const std::vector<int> &bl
                    std::vector<double> &lam_re, std::vector<double> &lam_im, Mat &Xre, Mat &Xim,
                    std::string &err);
 
+// Complex Schur form A = Q_c T_c Q_c^H (Sec. 3.4) from the real Schur form
+// A = Q T Q^T: every 2x2 block is triangularised by a 2x2 unitary rotation.
+// T_c is upper triangular with the eigenvalues on its diagonal.
+bool complex_schur(int n, const Mat &Q, const Mat &T, const std::vector<int> &blk, Mat &Qre,
+                   Mat &Qim, Mat &Tre, Mat &Tim, std::string &err);
+
 // Inverse of the complex matrix (A_re + i A_im) by Gauss-Jordan with partial
 // pivoting; false if singular.
 bool complex_inverse(int n, const Mat &Are, const Mat &Aim, Mat &Bre, Mat &Bim);

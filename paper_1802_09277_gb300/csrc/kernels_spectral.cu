@@ -64,7 +64,8 @@ cudaError_t launch_mode_solve(T *w, const T *mu, const Grid &g, const SpecCoefs<
 // ---------------------------------------------------------------------------
 template <typename T>
 struct FusedParams {
-    static constexpr int LMAX = sizeof(T) == 4 ? 16 : 8;
+    // levels that fit the 32 KB kernel-parameter space
+    static constexpr int LMAX = sizeof(T) == 4 ? 12 : 6;
     SpecCoefs<T> lv[LMAX];
     ProlongCoefs<T> pc;
 };

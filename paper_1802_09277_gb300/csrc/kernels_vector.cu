@@ -15,8 +15,20 @@ struct VecList {
 template <typename T>
 struct AxpyArgs {
     const T *x[MAXV];
-    double coef[MAXV * NRHS_MAX];
-    double post[NRHS_MAX];  // y <- post_r * (y + sum_v coef x_v)
+    T coef[MAXV * NRHS_MAX];  // rounded to T on the host
+    T post[NRHS_MAX];         // y <- post_r * (y + sum_v coef x_v)
+};
+
+// two outputs sharing the vectors x_v (the delayed Gram-Schmidt step):
+//   y1 <- post1_r * (y1 + sum_v c1 x_v)
+//   y2 <- post2_r * (y2 + c21_r * y1_old + sum_v c2 x_v)
+template <typename T>
+struct Axpy2Args {
+    const T *x[MAXV];
+    T c1[MAXV * NRHS_MAX];
+    T c2[MAXV * NRHS_MAX];
+    T c21[NRHS_MAX];
+    T post1[NRHS_MAX], post2[NRHS_MAX];
 };
 
 // two consecutive elements as one 8- (float) or 16-byte (double) access
@@ -79,6 +91,7 @@ template <>
 struct DotAcc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ void add1(double p) { s += p; }
     __device__ __forceinline__ double value() const { return s; }
 };
 template <>
@@ -90,7 +103,44 @@ struct DotAcc<float> {
         c = (t - s) - y;
         s = t;
     }
+    __device__ __forceinline__ void add1(float p) {  // add p (Kahan)
+        const float y = p - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Reduction of the per-thread accumulators across a warp and the CTA.  For
+// FP32 data the Kahan pairs (s, -c) are summed as double-float numbers (FP32
+// operations only): an FP64 shuffle tree per accumulator costs more than the
+// whole streaming loop on GB300's FP64 pipe.
+template <typename T>
+struct Red;
+template <>
+struct Red<double> {
+    using V = double;
+    static __device__ __forceinline__ V of(const DotAcc<double> &a) { return a.value(); }
+    static __device__ __forceinline__ V zero() { return 0.0; }
+    static __device__ __forceinline__ V add(V a, V b) { return a + b; }
+    static __device__ __forceinline__ V warp(V v) { return warp_sum(v); }
+    static __device__ __forceinline__ double out(V v) { return v; }
+};
+template <>
+struct Red<float> {
+    using V = dfloat;
+    static __device__ __forceinline__ V of(const DotAcc<float> &a) { return dfloat(a.s, -a.c); }
+    static __device__ __forceinline__ V zero() { return dfloat(0.f, 0.f); }
+    static __device__ __forceinline__ V add(V a, V b) { return df_add(a, b); }
+    static __device__ __forceinline__ V warp(V v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            v = df_add(v, dfloat(__shfl_xor_sync(0xffffffffu, v.hi, o),
+                                 __shfl_xor_sync(0xffffffffu, v.lo, o)));
+        return v;
+    }
+    static __device__ __forceinline__ double out(V v) { return (double)v; }
 };
 
 // grid (nblk, nrhs, ceil(nv / 4)), 256 threads; partial[(v*nrhs + r)*nblk + blk].
@@ -102,7 +152,7 @@ __global__ void __launch_bounds__(256)
     k_multidot_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ w,
                        long long len, double *__restrict__ partial, int vec2) {
     using P2 = typename Pair<T>::V;
-    __shared__ double red[8][4];
+    __shared__ typename Red<T>::V red[8][4];
     const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
     const int v0 = 4 * blockIdx.z;
     const int cnt = (nv - v0 < 4) ? nv - v0 : 4;
@@ -134,17 +184,19 @@ __global__ void __launch_bounds__(256)
                 if (k < cnt) acc[k].add(x[k][i], wi);
         }
     }
+    using RD = Red<T>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const double t = warp_sum(acc[k].value());
+        if (k >= cnt) break;
+        const typename RD::V t = RD::warp(RD::of(acc[k]));
         if (lane == 0) red[warp][k] = t;
     }
     __syncthreads();
     if (threadIdx.x < cnt) {
-        double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x];
-        partial[((long long)(v0 + threadIdx.x) * nrhs + r) * nblk + blockIdx.x] = t;
+        typename RD::V t = RD::zero();
+        for (int q = 0; q < 8; ++q) t = RD::add(t, red[q][threadIdx.x]);
+        partial[((long long)(v0 + threadIdx.x) * nrhs + r) * nblk + blockIdx.x] = RD::out(t);
     }
 }
 
@@ -184,37 +236,206 @@ cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, 
     return cudaGetLastError();
 }
 
+// grid (blocks, nrhs): block row r handles right-hand side r (no index division)
 template <typename T>
-__global__ void k_multiaxpy(int nv, const __grid_constant__ AxpyArgs<T> aa, int nrhs,
-                            long long len, T *__restrict__ y, int vec2) {
+__global__ void __launch_bounds__(256)
+    k_multiaxpy(int nv, const __grid_constant__ AxpyArgs<T> aa, long long len,
+                T *__restrict__ y, int vec2) {
     using P2 = typename Pair<T>::V;
-    if (vec2) {  // pairs never straddle two rhs because len is even
-        const long long n = (long long)nrhs * len / 2;
-        P2 *y2 = reinterpret_cast<P2 *>(y);
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x) {
-            const int r = (int)((2 * i) / len);
+    const int r = blockIdx.y;
+    const long long off = (long long)r * len;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const T post = aa.post[r];
+    if (vec2) {  // off is even because len is
+        const long long n = len / 2;
+        P2 *y2 = reinterpret_cast<P2 *>(y + off);
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
             P2 acc = y2[i];
             for (int v = 0; v < nv; ++v) {
-                const T c = (T)aa.coef[v * NRHS_MAX + r];
-                const P2 x = reinterpret_cast<const P2 *>(aa.x[v])[i];
+                const T c = aa.coef[v * NRHS_MAX + r];
+                const P2 x = reinterpret_cast<const P2 *>(aa.x[v] + off)[i];
                 acc.x += c * x.x;
                 acc.y += c * x.y;
             }
-            acc.x *= (T)aa.post[r];
-            acc.y *= (T)aa.post[r];
+            acc.x *= post;
+            acc.y *= post;
             y2[i] = acc;
         }
         return;
     }
-    const long long n = (long long)nrhs * len;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(i / len);
-        T acc = y[i];
-        for (int v = 0; v < nv; ++v) acc += (T)aa.coef[v * NRHS_MAX + r] * aa.x[v][i];
-        y[i] = (T)aa.post[r] * acc;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        T acc = y[off + i];
+        for (int v = 0; v < nv; ++v) acc += aa.coef[v * NRHS_MAX + r] * aa.x[v][off + i];
+        y[off + i] = post * acc;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_axpy2(int nv, const __grid_constant__ Axpy2Args<T> aa, long long len, T *__restrict__ y1,
+            T *__restrict__ y2, int write1) {
+    const int r = blockIdx.y;
+    const long long off = (long long)r * len;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const T p1 = aa.post1[r], p2 = aa.post2[r], c21 = aa.c21[r];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        const T a1o = y1[off + i];
+        T a1 = a1o, a2 = y2[off + i] + c21 * a1o;
+        for (int v = 0; v < nv; ++v) {
+            const T x = aa.x[v][off + i];
+            a1 += aa.c1[v * NRHS_MAX + r] * x;
+            a2 += aa.c2[v * NRHS_MAX + r] * x;
+        }
+        if (write1) y1[off + i] = p1 * a1;
+        y2[off + i] = p2 * a2;
+    }
+}
+
+// grid (nblk, nrhs, ceil(nv / GV)): the dots of vectors GV g .. GV g + GV - 1
+// with two targets t1, t2 in one pass; partial[((v * 2 + t) * nrhs + r) * nblk + blk].
+// vec4: 16-byte loads (len a multiple of 4, 16-byte aligned vectors); each
+// thread forms the 4-term products of a chunk in T and adds them into its
+// accumulator (Kahan-compensated in FP32), so the compensation runs once per
+// 4 elements.
+template <typename T>
+struct Quad;
+template <>
+struct Quad<float> {
+    using V = float4;
+};
+template <>
+struct Quad<double> {
+    using V = double4_32a;
+};
+
+// one CTA's share of the Gram products for CNT vectors (compile-time count:
+// every load of an iteration is issued before the arithmetic that uses it)
+template <typename T, int CNT>
+__device__ __forceinline__ void gram2_body(const T *const *x, const T *__restrict__ t1,
+                                           const T *__restrict__ t2, long long len, int vec4,
+                                           DotAcc<T> *a1, DotAcc<T> *a2) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec4) {
+        using Q = typename Quad<T>::V;
+        const long long nq = len / 4;
+        const Q *q1 = reinterpret_cast<const Q *>(t1);
+        const Q *q2 = reinterpret_cast<const Q *>(t2);
+#pragma unroll 2
+        for (long long i = i0; i < nq; i += stride) {
+            Q xv[CNT];
+            const Q u1 = q1[i], u2 = q2[i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) xv[k] = reinterpret_cast<const Q *>(x[k])[i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) {
+                a1[k].add1(xv[k].x * u1.x + xv[k].y * u1.y + xv[k].z * u1.z + xv[k].w * u1.w);
+                a2[k].add1(xv[k].x * u2.x + xv[k].y * u2.y + xv[k].z * u2.z + xv[k].w * u2.w);
+            }
+        }
+    } else {
+        for (long long i = i0; i < len; i += stride) {
+            T xv[CNT];
+            const T u1 = t1[i], u2 = t2[i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) xv[k] = x[k][i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) {
+                a1[k].add(xv[k], u1);
+                a2[k].add(xv[k], u2);
+            }
+        }
+    }
+}
+
+template <typename T, int GV>
+__global__ void __launch_bounds__(256)
+    k_gram2_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ t1,
+                    const T *__restrict__ t2, long long len, double *__restrict__ partial,
+                    int vec4) {
+    __shared__ typename Red<T>::V red[8][2 * GV];
+    const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
+    const int v0 = GV * blockIdx.z;
+    const int cnt = (nv - v0 < GV) ? nv - v0 : GV;
+    const long long off = (long long)r * len;
+    const T *x[GV];
+#pragma unroll
+    for (int k = 0; k < GV; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0] + off;
+    DotAcc<T> a1[GV], a2[GV];
+    static_assert(GV == 4, "the count dispatch below covers GV = 4");
+    switch (cnt) {  // uniform across the grid row
+        case 1: gram2_body<T, 1>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
+        case 2: gram2_body<T, 2>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
+        case 3: gram2_body<T, 3>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
+        default: gram2_body<T, 4>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
+    }
+    using RD = Red<T>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < GV; ++k) {
+        if (k >= cnt) break;
+        const typename RD::V s1 = RD::warp(RD::of(a1[k])), s2 = RD::warp(RD::of(a2[k]));
+        if (lane == 0) {
+            red[warp][2 * k] = s1;
+            red[warp][2 * k + 1] = s2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * cnt) {
+        typename RD::V t = RD::zero();
+        for (int q = 0; q < 8; ++q) t = RD::add(t, red[q][threadIdx.x]);
+        const int v = v0 + threadIdx.x / 2, which = threadIdx.x % 2;
+        partial[((long long)(2 * v + which) * nrhs + r) * nblk + blockIdx.x] = RD::out(t);
+    }
+}
+
+template <typename T>
+cudaError_t launch_gram2(int nv, const T *const *vecs, const T *t1, const T *t2, int nrhs,
+                         long long len, double *partial, int nblk, double *out, cudaStream_t s) {
+    if (nv > MAXV || nrhs > 65535 || nv <= 0) return cudaErrorInvalidValue;
+    VecList<T> vl;
+    // 4-element loads need the vectors aligned to 4 elements (16 or 32 bytes)
+    const uintptr_t am = 4 * sizeof(T) - 1;
+    auto al4 = [am](const void *p) { return (reinterpret_cast<uintptr_t>(p) & am) == 0; };
+    int vec4 = (len % 4 == 0) && al4(t1) && al4(t2);
+    for (int i = 0; i < nv; ++i) {
+        vl.v[i] = vecs[i];
+        vec4 = vec4 && al4(vecs[i]);
+    }
+    constexpr int GV = 4;
+    k_gram2_partial<T, GV><<<dim3(nblk, nrhs, (nv + GV - 1) / GV), 256, 0, s>>>(
+        nv, vl, t1, t2, len, partial, vec4);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int count = 2 * nv * nrhs;
+    k_reduce_partials<<<(count + 3) / 4, 128, 0, s>>>(partial, nblk, count, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_axpy2(int nv, const T *const *xs, const double *c1, const double *c2,
+                         const double *c21, const double *post1, const double *post2, int nrhs,
+                         long long len, T *y1, T *y2, int write1, cudaStream_t s) {
+    if (nv > MAXV || nrhs > NRHS_MAX || nv < 0) return cudaErrorInvalidValue;
+    Axpy2Args<T> aa;
+    for (int v = 0; v < nv; ++v) {
+        aa.x[v] = xs[v];
+        for (int r = 0; r < nrhs; ++r) {
+            aa.c1[v * NRHS_MAX + r] = (T)c1[v * nrhs + r];
+            aa.c2[v * NRHS_MAX + r] = (T)c2[v * nrhs + r];
+        }
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        aa.c21[r] = (T)c21[r];
+        aa.post1[r] = (T)post1[r];
+        aa.post2[r] = (T)post2[r];
+    }
+    long long bx = (len + 255) / 256;
+    const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
+    if (bx > cap) bx = cap;
+    if (bx < 1) bx = 1;
+    k_axpy2<T><<<dim3((unsigned)bx, (unsigned)nrhs), 256, 0, s>>>(nv, aa, len, y1, y2, write1);
+    return cudaGetLastError();
 }
 
 template <typename T>
@@ -225,18 +446,19 @@ cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int
     AxpyArgs<T> aa;
     for (int v = 0; v < nv; ++v) {
         aa.x[v] = xs[v];
-        for (int r = 0; r < nrhs; ++r) aa.coef[v * NRHS_MAX + r] = coef[v * nrhs + r];
+        for (int r = 0; r < nrhs; ++r) aa.coef[v * NRHS_MAX + r] = (T)coef[v * nrhs + r];
     }
-    for (int r = 0; r < nrhs; ++r) aa.post[r] = post ? post[r] : 1.0;
+    for (int r = 0; r < nrhs; ++r) aa.post[r] = post ? (T)post[r] : T(1);
     const bool al = sizeof(T) == 8 ? aligned16(y) : ((reinterpret_cast<uintptr_t>(y) & 7u) == 0);
     int vec2 = (len % 2 == 0) && al;
     for (int v = 0; v < nv; ++v)
         vec2 = vec2 && (sizeof(T) == 8 ? aligned16(xs[v])
                                        : ((reinterpret_cast<uintptr_t>(xs[v]) & 7u) == 0));
-    long long blocks = ((long long)nrhs * len + 511) / 512;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks < 1) blocks = 1;
-    k_multiaxpy<T><<<(unsigned)blocks, 256, 0, s>>>(nv, aa, nrhs, len, y, vec2);
+    long long bx = (len + 511) / 512;
+    const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
+    if (bx > cap) bx = cap;
+    if (bx < 1) bx = 1;
+    k_multiaxpy<T><<<dim3((unsigned)bx, (unsigned)nrhs), 256, 0, s>>>(nv, aa, len, y, vec2);
     return cudaGetLastError();
 }
 
@@ -324,5 +546,18 @@ template cudaError_t launch_multiaxpy<double>(int, const double *const *, const 
 template cudaError_t launch_multiaxpy<float>(int, const float *const *, const double *, int,
                                              long long, float *, cudaStream_t, const double *);
 template cudaError_t launch_zero<float>(float *, long long, cudaStream_t);
+template cudaError_t launch_gram2<float>(int, const float *const *, const float *, const float *,
+                                         int, long long, double *, int, double *, cudaStream_t);
+template cudaError_t launch_gram2<double>(int, const double *const *, const double *,
+                                          const double *, int, long long, double *, int,
+                                          double *, cudaStream_t);
+template cudaError_t launch_axpy2<float>(int, const float *const *, const double *,
+                                         const double *, const double *, const double *,
+                                         const double *, int, long long, float *, float *, int,
+                                         cudaStream_t);
+template cudaError_t launch_axpy2<double>(int, const double *const *, const double *,
+                                          const double *, const double *, const double *,
+                                          const double *, int, long long, double *, double *,
+                                          int, cudaStream_t);
 
 }  // namespace st

@@ -32,6 +32,48 @@ __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 template <typename T>
 __device__ __forceinline__ void spec_block_solve(const SpecCoefs<T> &c, T mu, const T *r, T *v) {
     const int nt = c.nt;
+    if (c.variant == 2) {  // complex Schur (Sec. 3.4, Algorithm 1): complex triangular Z
+        T wr[NTMAX], wi[NTMAX], zr[NTMAX], zi[NTMAX];
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i) {
+            T ar = T(0), ai = T(0);
+#pragma unroll
+            for (int j = 0; j < NTMAX; ++j)
+                if (j < nt) {
+                    ar += c.Y[i * NTMAX + j] * r[j];
+                    ai += c.Yi[i * NTMAX + j] * r[j];
+                }
+            wr[i] = ar;
+            wi[i] = ai;
+            zr[i] = T(0);
+            zi[i] = T(0);
+        }
+        // back substitution (Z + mu I) z = w, complex
+#pragma unroll
+        for (int i = NTMAX - 1; i >= 0; --i) {
+            if (i >= nt) continue;
+            T gr = wr[i], gi = wi[i];
+#pragma unroll
+            for (int j = i + 1; j < NTMAX; ++j)
+                if (j < nt) {
+                    gr -= c.Z[i * NTMAX + j] * zr[j] - c.Zi[i * NTMAX + j] * zi[j];
+                    gi -= c.Z[i * NTMAX + j] * zi[j] + c.Zi[i * NTMAX + j] * zr[j];
+                }
+            const T dr = c.Z[i * NTMAX + i] + mu, di = c.Zi[i * NTMAX + i];
+            const T rden = recip(dr * dr + di * di);
+            zr[i] = (gr * dr + gi * di) * rden;
+            zi[i] = (gi * dr - gr * di) * rden;
+        }
+#pragma unroll
+        for (int i = 0; i < NTMAX; ++i) {
+            T a = T(0);
+#pragma unroll
+            for (int j = 0; j < NTMAX; ++j)
+                if (j < nt) a += c.X[i * NTMAX + j] * zr[j] - c.Xi[i * NTMAX + j] * zi[j];
+            v[i] = a;
+        }
+        return;
+    }
     if (c.variant == 1) {  // diagonalisation (Sec. 3.3): complex shifts lambda_i + mu
         T zr[NTMAX], zi[NTMAX];
 #pragma unroll

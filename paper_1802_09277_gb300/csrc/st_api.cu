@@ -59,6 +59,9 @@ struct LevelHost {
     Mat Xre, Xim, Yre, Yim;
     double condX = 0.0;
     bool eig_ok = false;
+    // complex Schur form (Sec. 3.4): K_t Q_c = M_t Q_c T_c, T_c upper
+    // triangular, Q_c unitary; Y_c = (M_t Q_c)^{-1}
+    Mat Qcre, Qcim, Tcre, Tcim, Ycre, Ycim;
 };
 
 template <typename T>
@@ -347,6 +350,17 @@ SpecCoefs<T> pack_spec(st_handle h, int l) {
     }
     c.nt = nt;
     c.variant = h->opt.variant;
+    if (h->opt.variant == ST_CSCHUR) {
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < nt; ++j) {
+                c.X[i * NTMAX + j] = (T)L.Qcre[i * nt + j];
+                c.Xi[i * NTMAX + j] = (T)L.Qcim[i * nt + j];
+                c.Y[i * NTMAX + j] = (T)L.Ycre[i * nt + j];
+                c.Yi[i * NTMAX + j] = (T)L.Ycim[i * nt + j];
+                c.Z[i * NTMAX + j] = (T)L.Tcre[i * nt + j];
+                c.Zi[i * NTMAX + j] = (T)L.Tcim[i * nt + j];
+            }
+    }
     if (h->opt.variant == ST_EIG) {
         for (int i = 0; i < nt; ++i) {
             for (int j = 0; j < nt; ++j) {
@@ -504,9 +518,10 @@ int smooth_range(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns, 
     DevSpace<T> &ds = space<T>(h);
     const long long sl = (long long)h->nt * h->g.nxyz;  // elements per slab
     T *w0 = w.w0 + s0 * sl, *w1 = w.w1 + s0 * sl;
-    const bool eig = h->opt.variant == ST_EIG;
+    const bool eig = h->opt.variant != ST_RSCHUR;
     // real Schur: Y fused into the residual, shift solve with Z, X in the
-    // update; diagonalisation: the complex Y, shifts and X all per mode
+    // update; diagonalisation and complex Schur: the complex Y, the shifted
+    // diagonal or triangular solve and X all per mode
     CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, !eig, s0, ns));
     T *fw = nullptr, *bz = nullptr;
     CKS(spatial<T>(h, w0, w1, w0, true, (long long)ns * h->nt, &fw));
@@ -870,6 +885,27 @@ int norms(st_handle h, const T *x, std::vector<double> &nr) {
     return ST_OK;
 }
 
+// out[(v * 2 + t) * nrhs + r]: dots of vecs[v] with t1 (t = 0) and t2 (t = 1)
+template <typename T>
+int gram2s(st_handle h, int nv, const T *const *vecs, const T *t1, const T *t2,
+           std::vector<double> &out) {
+    out.assign((size_t)2 * nv * h->nrhs, 0.0);
+    for (int v0 = 0; v0 < nv; v0 += MAXV) {
+        const int cnt = std::min(MAXV, nv - v0);
+        {
+            KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 2.0) * h->len * h->nrhs,
+                      4.0 * cnt * h->len * h->nrhs);
+            CK(launch_gram2<T>(cnt, vecs + v0, t1, t2, h->nrhs, h->len, h->partial, h->nblk_dot,
+                               h->dots, h->stream));
+        }
+        CK(cudaMemcpyAsync(out.data() + (size_t)2 * v0 * h->nrhs, h->dots,
+                           sizeof(double) * 2 * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->recs.size() > 2048) prof_fold(h);
+    return ST_OK;
+}
+
 int residual64(st_handle h, const double *u, const double *f, double *r) {
     return stencil<double>(h, 0, u, f, r, MODE_RES, false, 0, h->N * h->nrhs);
 }
@@ -1055,6 +1091,209 @@ int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vecto
     return ST_OK;
 }
 
+// Flexible GMRES(m) with classical Gram-Schmidt and DELAYED
+// reorthogonalisation (the low-synchronisation scheme of Swirydowicz et al.,
+// "Low synchronization Gram-Schmidt and GMRES algorithms", and Bielich et
+// al., "Low-synch Gram-Schmidt with delayed reorthogonalization for Krylov
+// solvers"): basis vector j enters step j once-orthogonalised (q~_j); one
+// Gram pass over [q_0 .. q_{j-1}, q~_j, w] with the two targets q~_j and
+// w = A M^{-1} q~_j gives both the second pass of q~_j (a = Q^T q~_j,
+// rho = sqrt(q~_j.q~_j - |a|^2), q_j = (q~_j - Q a) / rho) and the first pass
+// of w (b = Q^T w, s_j = q_j^T w = (q~_j.w - a.b) / rho); one two-output
+// update writes q_j and q~_{j+1} = (w - Q b - q_j s_j) / nu.  Column j - 1 of
+// the Hessenberg matrix is completed one step late: w_{j-1}'s remainder
+// nu q~_j = nu (Q a + rho q_j) adds nu a to its entries and nu rho below
+// them.  Any vector may be preconditioned in FGMRES (A Z = Q H holds for the
+// z actually used), so preconditioning q~_j instead of q_j is exact.  One
+// host synchronisation and two passes over the basis per step (CGS2 takes
+// two synchronisations and four passes).  Every decision is taken per
+// right-hand side, so a batch gives each rhs its single-rhs result.
+template <typename T, class Apply, class Res, class Prec>
+int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vector<T *> &V,
+                 std::vector<T *> &Zk, Apply apply, Res resid, Prec prec,
+                 const std::vector<char> &skip, int *its, double *worst_out) {
+    const int m = (int)Zk.size(), R = h->nrhs;
+    const size_t ld = (size_t)m + 1;
+    std::vector<double> nb, beta, G;
+    CKS(norms<T>(h, b, nb));
+    int total = 0;
+    double worst = 0.0;
+    std::vector<char> done(R, 0);
+    while (true) {
+        CKS(resid(x, b, V[0]));
+        CKS(norms<T>(h, V[0], beta));
+        worst = 0.0;
+        for (int q = 0; q < R; ++q) {
+            const double rel = nb[q] > 0 ? beta[q] / nb[q] : 0.0;
+            done[q] = skip[q] || !(nb[q] > 0) || rel <= tol;
+            if (!skip[q]) worst = std::max(worst, rel);
+        }
+        if (worst <= tol || total >= maxit) break;
+        {
+            std::vector<double> sc(R);
+            for (int q = 0; q < R; ++q) sc[q] = (!done[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
+            CKS(vaxpy<T>(h, 0, nullptr, nullptr, V[0], sc.data()));
+        }
+        std::vector<double> H((size_t)R * ld * m, 0.0), cs((size_t)R * m), sn((size_t)R * m),
+            g((size_t)R * ld, 0.0), nu(R, 0.0);
+        std::vector<int> kq(R, 0);
+        std::vector<char> act(R), pend(R, 0);
+        for (int q = 0; q < R; ++q) {
+            g[(size_t)q * ld] = done[q] ? 0.0 : beta[q];
+            act[q] = !done[q];
+        }
+        // complete column col of rhs q with the second pass (a, rho) of the
+        // vector below it, rotate it and update the residual estimate
+        auto finish_col = [&](int q, int col, const double *a, double rho) {
+            double *c = &H[(size_t)q * ld * m + (size_t)col * ld];
+            for (int i = 0; i <= col; ++i) c[i] += nu[q] * a[i];
+            c[col + 1] = nu[q] * rho;
+            double *cq = &cs[(size_t)q * m], *sq = &sn[(size_t)q * m], *gq = &g[(size_t)q * ld];
+            for (int i = 0; i < col; ++i) {
+                const double x0 = c[i], x1 = c[i + 1];
+                c[i] = cq[i] * x0 + sq[i] * x1;
+                c[i + 1] = -sq[i] * x0 + cq[i] * x1;
+            }
+            const double rad = std::hypot(c[col], c[col + 1]);
+            cq[col] = rad > 0 ? c[col] / rad : 1.0;
+            sq[col] = rad > 0 ? c[col + 1] / rad : 0.0;
+            c[col] = rad;
+            c[col + 1] = 0.0;
+            gq[col + 1] = -sq[col] * gq[col];
+            gq[col] = cq[col] * gq[col];
+            kq[q] = col + 1;
+            pend[q] = 0;
+            if (std::fabs(gq[col + 1]) <= tol * nb[q] || rho == 0.0) act[q] = 0;
+        };
+        // residual estimate if the pending column were completed with a = 0, rho = 1
+        auto provisional = [&](int q, int col) {
+            std::vector<double> c(&H[(size_t)q * ld * m + (size_t)col * ld],
+                                  &H[(size_t)q * ld * m + (size_t)col * ld] + col + 2);
+            c[col + 1] = nu[q];
+            const double *cq = &cs[(size_t)q * m], *sq = &sn[(size_t)q * m];
+            for (int i = 0; i < col; ++i) {
+                const double x0 = c[i], x1 = c[i + 1];
+                c[i] = cq[i] * x0 + sq[i] * x1;
+                c[i + 1] = -sq[i] * x0 + cq[i] * x1;
+            }
+            const double rad = std::hypot(c[col], c[col + 1]);
+            const double s = rad > 0 ? c[col + 1] / rad : 0.0;
+            return std::fabs(s * g[(size_t)q * ld + col]);
+        };
+        for (int j = 0;; ++j) {
+            // (A) rhs whose pending column already meets the tolerance (or
+            // every pending rhs at the end of the cycle): second pass only
+            const bool last = (j == m) || total >= maxit;
+            std::vector<char> fin(R, 0);
+            bool anyfin = false;
+            for (int q = 0; q < R; ++q)
+                if (act[q] && pend[q] && (last || provisional(q, j - 1) <= tol * nb[q])) {
+                    fin[q] = 1;
+                    anyfin = true;
+                }
+            if (anyfin) {
+                std::vector<const T *> vw(V.begin(), V.begin() + j + 1);
+                CKS(dots<T>(h, j + 1, vw.data(), V[j], G));
+                std::vector<double> c1((size_t)j * R, 0.0), p1(R, 1.0), a(j);
+                for (int q = 0; q < R; ++q) {
+                    if (!fin[q]) continue;
+                    double aa = 0.0;
+                    for (int i = 0; i < j; ++i) {
+                        a[i] = G[(size_t)i * R + q];
+                        aa += a[i] * a[i];
+                    }
+                    const double rho = std::sqrt(std::max(G[(size_t)j * R + q] - aa, 0.0));
+                    finish_col(q, j - 1, a.data(), rho);
+                    if (act[q] && rho > 0) {  // continues: q~_j becomes q_j
+                        for (int i = 0; i < j; ++i) c1[(size_t)i * R + q] = -a[i];
+                        p1[q] = 1.0 / rho;
+                    }
+                }
+                CKS(vaxpy<T>(h, j, V.data(), c1.data(), V[j], p1.data()));
+            }
+            bool any = false;
+            for (int q = 0; q < R; ++q) any = any || act[q];
+            if (!any || last) break;
+            // (B) the step: z_j = M^{-1} q~_j, w = A z_j
+            CKS(prec(V[j], Zk[j]));
+            CKS(apply(Zk[j], V[j + 1]));
+            // (C) one Gram pass, targets q~_j and w
+            CKS(gram2s<T>(h, j + 2, V.data(), V[j], V[j + 1], G));
+            std::vector<double> c1((size_t)j * R, 0.0), c2((size_t)j * R, 0.0), c21(R, 0.0),
+                p1(R, 1.0), p2(R, 1.0), a(j), bb(j);
+            int write1 = 0;
+            for (int q = 0; q < R; ++q) {
+                if (!act[q]) continue;
+                double aa = 0.0, ab = 0.0, b2 = 0.0;
+                for (int i = 0; i < j; ++i) {
+                    a[i] = pend[q] ? G[((size_t)2 * i) * R + q] : 0.0;
+                    bb[i] = G[((size_t)2 * i + 1) * R + q];
+                    aa += a[i] * a[i];
+                    ab += a[i] * bb[i];
+                    b2 += bb[i] * bb[i];
+                }
+                const double d = G[((size_t)2 * j) * R + q];
+                const double cw = G[((size_t)2 * j + 1) * R + q];
+                const double e = G[((size_t)2 * (j + 1) + 1) * R + q];
+                double rho = 1.0;
+                if (pend[q]) {
+                    rho = std::sqrt(std::max(d - aa, 0.0));
+                    finish_col(q, j - 1, a.data(), rho);
+                    if (!act[q]) continue;  // converged at column j - 1
+                    write1 = 1;
+                    for (int i = 0; i < j; ++i) c1[(size_t)i * R + q] = -a[i];
+                    p1[q] = 1.0 / rho;
+                }
+                const double sj = (cw - ab) / rho;
+                double *col = &H[(size_t)q * ld * m + (size_t)j * ld];
+                for (int i = 0; i < j; ++i) col[i] = bb[i];
+                col[j] = sj;
+                // |w - Q b - q_j s_j| by Pythagoras; only a scale, the exact
+                // norm enters through the next second pass
+                const double r2 = e - b2 - sj * sj;
+                if (!(e > 0)) {  // w = 0: the Krylov space is invariant
+                    nu[q] = 0.0;
+                    kq[q] = j;
+                    act[q] = 0;
+                    continue;
+                }
+                const double nq = std::sqrt(std::max(r2, 1e-10 * e));
+                for (int i = 0; i < j; ++i) c2[(size_t)i * R + q] = -(bb[i] - a[i] * sj / rho);
+                c21[q] = -sj / rho;
+                p2[q] = 1.0 / nq;
+                nu[q] = nq;
+                pend[q] = 1;
+            }
+            {
+                KScope ks(h, ST_PROF_VECTOR, sizeof(T) * (j + 2.0 + 2.0) * h->len * R,
+                          4.0 * (j + 1) * h->len * R);
+                CK(launch_axpy2<T>(j, V.data(), c1.data(), c2.data(), c21.data(), p1.data(),
+                                   p2.data(), R, h->len, V[j], V[j + 1], write1, h->stream));
+            }
+            ++total;
+        }
+        // x += Z y per rhs
+        const int kmax = *std::max_element(kq.begin(), kq.end());
+        std::vector<double> coef((size_t)std::max(kmax, 1) * R, 0.0);
+        for (int q = 0; q < R; ++q) {
+            const int k = kq[q];
+            const double *Hq = &H[(size_t)q * ld * m];
+            const double *gq = &g[(size_t)q * ld];
+            std::vector<double> y(k);
+            for (int i = k - 1; i >= 0; --i) {
+                double sacc = gq[i];
+                for (int c2i = i + 1; c2i < k; ++c2i) sacc -= Hq[(size_t)c2i * ld + i] * y[c2i];
+                y[i] = sacc / Hq[(size_t)i * ld + i];
+            }
+            for (int i = 0; i < k; ++i) coef[(size_t)i * R + q] = y[i];
+        }
+        if (kmax > 0) CKS(vaxpy<T>(h, kmax, Zk.data(), coef.data(), x));
+    }
+    *its = total;
+    *worst_out = worst;
+    return ST_OK;
+}
+
 int solve_fgmres(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
     CKS(ensure_krylov(h));
     std::vector<double *> Z(h->Zk);
@@ -1124,8 +1363,18 @@ int ensure_krylov32(st_handle h) {
 int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
     CKS(ensure_krylov32(h));
     const int R = h->nrhs;
-    std::vector<double> nf, nr;
-    CKS(norms<double>(h, rhs, nf));
+    std::vector<double> nf(R), nr(R), g0;
+    // ||f|| and ||u|| in one pass: from a zero initial guess the first
+    // residual is f itself
+    {
+        const double *fu[2] = {rhs, u};
+        CKS(gram2s<double>(h, 2, fu, rhs, u, g0));
+    }
+    bool u_zero = true;
+    for (int q = 0; q < R; ++q) {
+        nf[q] = std::sqrt(std::max(0.0, g0[(size_t)0 * R + q]));
+        u_zero = u_zero && g0[(size_t)3 * R + q] == 0.0;
+    }
     int total = 0, outer = 0;
     double worst = 0.0;
     const bool eig_basis = h->opt.basis == ST_BASIS_SPECTRAL;
@@ -1154,9 +1403,15 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
         return run_graphed(h, v, z, [h, v, z] { return svcycle_top<float>(h, z, v, h->w32.w0); });
     };
     const long long n0 = h->len * R;
-    for (;;) {
-        CKS(residual_df(h, u, rhs, h->r64));
-        CKS(norms<double>(h, h->r64, nr));
+    for (bool first = true;; first = false) {
+        if (first && u_zero) {
+            CK(cudaMemcpyAsync(h->r64, rhs, sizeof(double) * h->len * R, cudaMemcpyDeviceToDevice,
+                               h->stream));
+            nr = nf;
+        } else {
+            CKS(residual_df(h, u, rhs, h->r64));
+            CKS(norms<double>(h, h->r64, nr));
+        }
         worst = 0.0;
         std::vector<char> skip(R, 0);
         std::vector<double> sc(R), back(R);
@@ -1182,8 +1437,8 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
         int its = 0;
         double w32 = 0.0;
         const double itol = std::max(h->opt.inner_tol, 1e-6);
-        CKS(fgmres_core<float>(h, h->rhs32, h->e32, itol, h->opt.max_it - total, h->V32, h->Z32,
-                               apply, resid, prec, skip, &its, &w32));
+        CKS(fgmres_dcgs2<float>(h, h->rhs32, h->e32, itol, h->opt.max_it - total, h->V32,
+                                h->Z32, apply, resid, prec, skip, &its, &w32));
         total += its;
         ++outer;
         const float *corr = h->e32;
@@ -1224,7 +1479,7 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         return fail(ST_ERR_INVALID_ARG, "bad precision");
     if (o.basis != ST_BASIS_NODAL && o.basis != ST_BASIS_SPECTRAL)
         return fail(ST_ERR_INVALID_ARG, "bad basis");
-    if (o.variant != ST_RSCHUR && o.variant != ST_EIG)
+    if (o.variant != ST_RSCHUR && o.variant != ST_EIG && o.variant != ST_CSCHUR)
         return fail(ST_ERR_INVALID_ARG, "bad variant");
     if (o.outer < ST_OUTER_FGMRES || o.outer > ST_OUTER_IR)
         return fail(ST_ERR_INVALID_ARG, "bad outer iteration");
@@ -1327,6 +1582,26 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
                                 "(use the real Schur variant)", L.condX, Nl);
             }
         }
+        // complex Schur form (Sec. 3.4) from the real one, Y_c = (M_t Q_c)^{-1}
+        if (o.variant == ST_CSCHUR) {
+            std::string e3;
+            if (!host::complex_schur(nt, L.X, L.Z, L.blk, L.Qcre, L.Qcim, L.Tcre, L.Tcim, e3))
+                return fail(ST_ERR_ILL_CONDITIONED, "complex Schur: %s", e3.c_str());
+            Mat MQr = host::matmul(nt, L.Mt, L.Qcre), MQi = host::matmul(nt, L.Mt, L.Qcim);
+            if (!host::complex_inverse(nt, MQr, MQi, L.Ycre, L.Ycim))
+                return fail(ST_ERR_ILL_CONDITIONED, "M_t Q_c singular");
+            // K_t Q_c = M_t Q_c T_c
+            Mat KQr = host::matmul(nt, L.Kt, L.Qcre), KQi = host::matmul(nt, L.Kt, L.Qcim);
+            Mat A1 = host::matmul(nt, MQr, L.Tcre), A2 = host::matmul(nt, MQi, L.Tcim);
+            Mat B1 = host::matmul(nt, MQr, L.Tcim), B2 = host::matmul(nt, MQi, L.Tcre);
+            double rc = 0.0;
+            for (int i = 0; i < nt * nt; ++i)
+                rc = std::max(rc, std::max(std::fabs(KQr[i] - (A1[i] - A2[i])),
+                                           std::fabs(KQi[i] - (B1[i] + B2[i]))));
+            const double sc = host::frob(L.Kt) + host::frob(L.Mt) * (host::frob(L.Tcre) + host::frob(L.Tcim));
+            if (!(rc <= 1e-12 * nt * sc))
+                return fail(ST_ERR_ILL_CONDITIONED, "complex Schur residual %.3e", rc);
+        }
         // Y = (M_t X)^{-1}
         Mat MX = host::matmul(nt, L.Mt, L.X);
         L.Y.assign(nt * nt, 0.0);
@@ -1390,11 +1665,11 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     }
     // the eigenbasis V-cycle's per-mode inverses, in its working precision
     if (o.basis == ST_BASIS_SPECTRAL) CKS(h->mixed ? ensure_inv<float>(h) : ensure_inv<double>(h));
-    h->nblk_dot = 2 * h->nsm;
+    h->nblk_dot = 3 * h->nsm;  // the dot kernels are register-limited to 3 CTAs per SM
     void *p;
-    CKS(dalloc(h, sizeof(double) * MAXV * h->nrhs * h->nblk_dot, &p));
+    CKS(dalloc(h, sizeof(double) * 2 * MAXV * h->nrhs * h->nblk_dot, &p));
     h->partial = (double *)p;
-    CKS(dalloc(h, sizeof(double) * MAXV * h->nrhs, &p));
+    CKS(dalloc(h, sizeof(double) * 2 * MAXV * h->nrhs, &p));
     h->dots = (double *)p;
     return ST_OK;
 }

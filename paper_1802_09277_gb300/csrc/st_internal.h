@@ -64,6 +64,7 @@ struct SpecCoefs {
     T X[NTMAX * NTMAX];
     T Yi[NTMAX * NTMAX];
     T Xi[NTMAX * NTMAX];
+    T Zi[NTMAX * NTMAX];  // complex Schur variant: imaginary part of Z
     T lre[NTMAX];
     T lim[NTMAX];
     int blk[NTMAX];
@@ -189,6 +190,16 @@ cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, 
                             double *partial, int nblk, double *out, cudaStream_t s);
 
 // y_r = post_r * (y_r + sum_v coef[v][r] x_v)  (per rhs r; post NULL = 1)
+// out[(v * 2 + t) * nrhs + r] = dot of vecs[v] with target t (t1, t2) over rhs r
+template <typename T>
+cudaError_t launch_gram2(int nv, const T *const *vecs, const T *t1, const T *t2, int nrhs,
+                         long long len, double *partial, int nblk, double *out, cudaStream_t s);
+// y1 <- post1 (y1 + sum_v c1[v] x_v);  y2 <- post2 (y2 + c21 y1_old + sum_v c2[v] x_v)
+// (coefficients [v * nrhs + r], per rhs r); write1 = 0 leaves y1 untouched
+template <typename T>
+cudaError_t launch_axpy2(int nv, const T *const *xs, const double *c1, const double *c2,
+                         const double *c21, const double *post1, const double *post2, int nrhs,
+                         long long len, T *y1, T *y2, int write1, cudaStream_t s);
 template <typename T>
 cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int nrhs,
                              long long len, T *y, cudaStream_t s, const double *post = nullptr);

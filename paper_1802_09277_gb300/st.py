@@ -19,7 +19,7 @@ GEOMETRY = {1: 1, 2: 2, 3: 3}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
 OUTER = {"fgmres": 0, "mg": 1, "ir": 2}
 BASIS = {"nodal": 0, "spectral": 1}
-VARIANT = {"rschur": 0, "eig": 1}
+VARIANT = {"rschur": 0, "eig": 1, "cschur": 2}
 
 # every symbol declared in include/st_iga.h
 SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",

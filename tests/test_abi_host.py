@@ -178,3 +178,18 @@ def test_eig_variant_factors(st):
             assert np.min(np.abs(lam - v)) <= 1e-9 * max(1.0, abs(v))
         assert 1.0 <= c < 1e8
     s.close()
+
+
+@pytest.mark.parametrize("p,theta,ne", [(1, 1.0, 4), (2, 1.0, 2), (3, 1.0, 2), (3, 0.1, 5), (2, 0.01, 6)])
+def test_complex_schur_variant_setup(st, p, theta, ne):
+    """Complex Schur variant (Sec. 3.4): setup forms K_t Q_c = M_t Q_c T_c with
+    T_c upper triangular from the real Schur form and checks its residual; the
+    spectrum is the generalized one (scipy) on every level."""
+    s = st.Solver(1, p, (8,), 8, host_only=True, ne_per_slab=ne, theta=theta, variant="cschur")
+    for lvl in range(s.nlevels):
+        tf = s.time_factors(lvl)
+        lam, _ = s.time_spectrum(lvl)
+        ref = sl.eigvals(tf["Kt"], tf["Mt"])
+        for v in ref:
+            assert np.min(np.abs(lam - v)) <= 1e-9 * max(1.0, abs(v))
+    s.close()

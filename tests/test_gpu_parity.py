@@ -386,12 +386,14 @@ def test_refinement_multi_rhs_equals_single(st):
 
 @pytest.mark.parametrize("basis", ["nodal", "spectral"])
 @pytest.mark.parametrize("d,spans,p,N,ne", [CASES[0], CASES[2], CASES[3], CASES[5]])
-def test_eig_variant_vcycle_and_solve(st, basis, d, spans, p, N, ne):
-    """Diagonalisation variant (Sec. 3.3, complex shifts): one smoothing step,
-    one V-cycle and an FP64 solve equal the oracle's."""
+@pytest.mark.parametrize("variant", ["eig", "cschur"])
+def test_eig_variant_vcycle_and_solve(st, variant, basis, d, spans, p, N, ne):
+    """Diagonalisation variant (Sec. 3.3, complex shifts) and complex Schur
+    variant (Sec. 3.4, Algorithm 1: complex triangular solve): one smoothing
+    step, one V-cycle and an FP64 solve equal the oracle's."""
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     H = hierarchy(pr)
-    s = st.Solver(d, p, spans, N, ne_per_slab=ne, variant="eig", basis=basis)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, variant=variant, basis=basis)
     u0 = inputs.uniform_vector(80, pr.ndofs)
     f = inputs.uniform_vector(81, pr.ndofs)
     u = dev(u0)
