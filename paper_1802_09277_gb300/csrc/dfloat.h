@@ -36,6 +36,42 @@ __device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
     return dfloat(hi, __fsub_rn(e, __fsub_rn(hi, p)));
 }
 
+// double -> (hi, lo) by bit manipulation (integer and FP32 operations only):
+// hi = the sign, exponent and leading 23 fraction bits (truncated), lo = the
+// remaining 29 fraction bits scaled by ulp(hi).  Outside |d| in
+// [2^-100, 2^127) (and for zero) it falls back to the FP64 conversion.
+__device__ __forceinline__ dfloat df_from_double(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
+    const int e = (int)((h32 >> 20) & 0x7ffu);
+    const int ef = e - 1023 + 127;  // float exponent field of hi
+    if (ef < 24 || ef > 254) return dfloat(d);
+    const unsigned sign = h32 & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)ef << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29));
+    // ulp(hi) * 2^-29 = 2^(ef - 127 - 23 - 29), built as a float (ef - 52 >= 1 is not
+    // guaranteed, so scale in two steps)
+    const float s1 = __uint_as_float((unsigned)(ef - 23) << 23);  // 2^(ef - 127 - 23)
+    const float lo = __fmul_rn(__fmul_rn(__uint2float_rn(l32 & 0x1fffffffu), 0x1p-29f), s1);
+    return dfloat(hi, sign ? -lo : lo);
+}
+
+// (hi, lo) -> double: each float widened exactly by bit manipulation, one FP64 add
+__device__ __forceinline__ double df_widen(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned ex = (u >> 23) & 0xffu;
+    if (ex == 0u && (u & 0x7fffffffu) == 0u)  // +-0
+        return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+    if (ex == 0u || ex == 0xffu) return (double)x;  // subnormal, inf / nan
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ex - 127u + 1023u) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ double df_to_double(dfloat a) {
+    return __dadd_rn(df_widen(a.hi), df_widen(a.lo));
+}
+
 __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) { return df_add(a, b); }
 __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return df_add(a, -b); }

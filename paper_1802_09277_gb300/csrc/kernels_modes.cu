@@ -356,6 +356,131 @@ __global__ void __launch_bounds__(256)
     store_col<T, NT>(out, base, S, r);
 }
 
+// The coarse end of the V-cycle, levels l0 .. L (N_{l0} <= TAIL_SLABS slabs
+// per problem, nu1 = nu2 = 1, zero initial iterate on every level), in one
+// launch: one thread per (spatial mode, rhs) runs the sub-cycle sequentially
+// over its slabs with the level vectors in thread-local memory (an
+// interleaved, L1-resident per-thread array), the same steps as k_lv_down /
+// k_lv_coarse / k_lv_up: the Jacobi steps see the previous slab's iterate
+// from before the step, which the sequential sweep keeps in a register.
+constexpr int TAIL_SLABS = 16;
+template <typename T>
+struct TailArgs {
+    const T *inv[16];  // per-mode inverses of levels l0 .. L
+    int nlev;          // L - l0 + 1
+};
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(128)
+    k_lv_tail(const T *__restrict__ fin, T *__restrict__ uout, const __grid_constant__ TailArgs<T> ta,
+              const __grid_constant__ ProlongCoefs<T> pc, long long S, int n0, T omega) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long q = slab_index();  // right-hand side
+    if (k >= S) return;
+    constexpr int CAP = 2 * TAIL_SLABS * NT;  // slabs of all tail levels, per vector
+    T f[CAP], u[CAP];
+    int off[16];
+    {
+        int o = 0;
+        for (int l = 0; l < ta.nlev; ++l) {
+            off[l] = o;
+            o += (n0 >> l) * NT;
+        }
+    }
+    const long long gbase = q * n0 * NT * S + k;
+    for (int e = 0; e < n0 * NT; ++e) f[e] = fin[gbase + (long long)e * S];
+    // down: the smoothing step from zero, residual, restriction
+    for (int l = 0; l + 1 < ta.nlev; ++l) {
+        const int N = n0 >> l;
+        T m[NT * NT];
+        load_inv<T, NT>(ta.inv[l], S, k, m);
+        T *fl = f + off[l], *ul = u + off[l], *fc = f + off[l + 1];
+        T prev = T(0);  // new last entry of the slab before the pair
+        for (int mc = 0; mc < N / 2; ++mc) {
+            T fa[NT], fb[NT], ua[NT], ub[NT], ra[NT], rb[NT], out[NT];
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                fa[i] = fl[(2 * mc) * NT + i];
+                fb[i] = fl[(2 * mc + 1) * NT + i];
+            }
+            matvec<T, NT>(m, fa, ua);
+            matvec<T, NT>(m, fb, ub);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                ua[i] *= omega;
+                ub[i] *= omega;
+                ra[i] = (T(1) - omega) * fa[i];
+                rb[i] = (T(1) - omega) * fb[i];
+                ul[(2 * mc) * NT + i] = ua[i];
+                ul[(2 * mc + 1) * NT + i] = ub[i];
+            }
+            ra[0] += prev;
+            rb[0] += ua[NT - 1];
+            prev = ub[NT - 1];
+            restrict_pair<T, NT>(pc, ra, rb, out);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) fc[mc * NT + i] = out[i];
+        }
+    }
+    {  // coarsest level: forward substitution
+        const int l = ta.nlev - 1, N = n0 >> l;
+        T m[NT * NT];
+        load_inv<T, NT>(ta.inv[l], S, k, m);
+        T prev = T(0);
+        for (int n = 0; n < N; ++n) {
+            T r[NT], v[NT];
+#pragma unroll
+            for (int i = 0; i < NT; ++i) r[i] = f[off[l] + n * NT + i];
+            r[0] += prev;
+            matvec<T, NT>(m, r, v);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) u[off[l] + n * NT + i] = v[i];
+            prev = v[NT - 1];
+        }
+    }
+    // up: prolongation of the coarse correction and the smoothing step
+    for (int l = ta.nlev - 2; l >= 0; --l) {
+        const int N = n0 >> l;
+        T m[NT * NT];
+        load_inv<T, NT>(ta.inv[l], S, k, m);
+        const T *fl = f + off[l], *uc = u + off[l + 1];
+        T *ul = u + off[l];
+        T prev = T(0);  // corrected (not yet smoothed) last entry of the slab before
+        for (int mc = 0; mc < N / 2; ++mc) {
+            T e[NT], ua[NT], ub[NT], r[NT], v[NT];
+#pragma unroll
+            for (int i = 0; i < NT; ++i) e[i] = uc[mc * NT + i];
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                T pa = T(0), pb = T(0);
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    pa += pc.P[j * NTMAX + i] * e[i];
+                    pb += pc.P[(NT + j) * NTMAX + i] * e[i];
+                }
+                ua[j] = ul[(2 * mc) * NT + j] + pa;
+                ub[j] = ul[(2 * mc + 1) * NT + j] + pb;
+            }
+#pragma unroll
+            for (int i = 0; i < NT; ++i) r[i] = fl[(2 * mc) * NT + i];
+            r[0] += prev;
+            matvec<T, NT>(m, r, v);
+            const T a_last = ua[NT - 1];
+            prev = ub[NT - 1];
+#pragma unroll
+            for (int i = 0; i < NT; ++i) ul[(2 * mc) * NT + i] = (T(1) - omega) * ua[i] + omega * v[i];
+#pragma unroll
+            for (int i = 0; i < NT; ++i) r[i] = fl[(2 * mc + 1) * NT + i];
+            r[0] += a_last;
+            matvec<T, NT>(m, r, v);
+#pragma unroll
+            for (int i = 0; i < NT; ++i)
+                ul[(2 * mc + 1) * NT + i] = (T(1) - omega) * ub[i] + omega * v[i];
+        }
+    }
+    for (int e = 0; e < n0 * NT; ++e) uout[gbase + (long long)e * S] = u[e];
+}
+
 // ---- launchers: dispatch on N_t ----
 #define ST_NT_DISPATCH(nt, CALL)          \
     switch (nt) {                         \
@@ -448,6 +573,26 @@ cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *mu, const Gr
                                                                       spp, nslabs, res)));
     return cudaGetLastError();
 }
+// the sub-cycle of levels l0 .. L in one launch; cudaErrorNotSupported when
+// n0 > TAIL_SLABS or more than 16 levels
+template <typename T>
+cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nlev,
+                             const Grid &g, const ProlongCoefs<T> &pc, T omega, int n0, int nrhs,
+                             cudaStream_t s) {
+    if (n0 > TAIL_SLABS || nlev > 16 || nlev < 1 || (n0 >> (nlev - 1)) < 1) return cudaErrorNotSupported;
+    if (g.nxyz <= 0 || nrhs <= 0) return cudaSuccess;
+    TailArgs<T> ta;
+    for (int l = 0; l < nlev; ++l) ta.inv[l] = inv[l];
+    ta.nlev = nlev;
+    ModeLaunch L = mode_launch(g.nxyz, nrhs);
+    if (L.block.x > 128) {  // smaller CTAs: more SMs share the few modes
+        L.block.x = 128;
+        L.grid.x = (unsigned)((g.nxyz + 127) / 128);
+    }
+    ST_NT_DISPATCH(pc.nt, (k_lv_tail<T, NT><<<L.grid, L.block, 0, s>>>(fin, uout, ta, pc, g.nxyz,
+                                                                        n0, omega)));
+    return cudaGetLastError();
+}
 #undef ST_NT_DISPATCH
 
 template cudaError_t launch_mode_inverse<double>(double *, const double *, const Grid &,
@@ -455,6 +600,8 @@ template cudaError_t launch_mode_inverse<double>(double *, const double *, const
 template cudaError_t launch_mode_inverse<float>(float *, const double *, const Grid &,
                                                 const SpecCoefs<double> &, cudaStream_t);
 #define ST_INST(T)                                                                              \
+    template cudaError_t launch_spec_tail<T>(const T *, T *, const T *const *, int, const Grid &, \
+                                             const ProlongCoefs<T> &, T, int, int, cudaStream_t);   \
     template cudaError_t launch_spec_smooth<T>(const T *, T *, const T *, const T *,            \
                                                const Grid &, int, T, int, long long, int,       \
                                                cudaStream_t);                                   \

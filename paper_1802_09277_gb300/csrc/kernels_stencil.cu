@@ -31,6 +31,16 @@ template <typename T, typename C>
 __device__ __forceinline__ T from_c(C x) {
     return (T)x;
 }
+// FP64 data in double-float arithmetic: split and widen without FP64-rate
+// conversions (GB300 runs FP64 at 1/64 of the FP32 rate)
+template <>
+__device__ __forceinline__ dfloat to_c<dfloat, double>(double x) {
+    return df_from_double(x);
+}
+template <>
+__device__ __forceinline__ double from_c<double, dfloat>(dfloat x) {
+    return df_to_double(x);
+}
 
 template <int DIM>
 struct TileShape;

@@ -131,6 +131,25 @@ def test_vcycle_parity(st, basis, d, spans, p, N, ne):
     s.close()
 
 
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 2), (0, 1), (1, 0), (2, 1)])
+@pytest.mark.parametrize("d,spans,p,N,ne", [(1, (16,), 2, 64, 2), (2, (6, 5), 2, 32, 2),
+                                            (2, (7, 6), 3, 12, 2)])
+def test_vcycle_levels_and_tail_parity(st, nu1, nu2, d, spans, p, N, ne):
+    """Eigenbasis V-cycle with more than 16 slabs (level-wise kernels above
+    the one-launch coarse tail), and with nu1, nu2 other than 1 (general
+    smoothing-step kernels, no tail), against the oracle's V(nu1, nu2)."""
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    H = hierarchy(pr)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, basis="spectral", nu1=nu1, nu2=nu2)
+    u0 = inputs.uniform_vector(15, pr.ndofs)
+    f = inputs.uniform_vector(16, pr.ndofs)
+    ref = S.vcycle(H, f, nu1=nu1, nu2=nu2, u=u0.copy())
+    u = dev(u0)
+    s.vcycle(u, dev(f))
+    assert relerr(host(u), ref) <= 1e-11
+    s.close()
+
+
 @pytest.mark.parametrize("basis", ["nodal", "spectral"])
 @pytest.mark.parametrize("outer", ["fgmres", "mg"])
 @pytest.mark.parametrize("d,spans,p,N,ne", CASES[:6])
