@@ -21,9 +21,12 @@
 // every kernel is a template on N_t so that all loops have exact length.
 //
 //  k_lv_smooth        one damped block-Jacobi step, out of place
-//  k_lv_down          the last pre-smoothing step, the residual of the new
-//                     iterate and its restriction P_t^T (slab pairs)
+//  k_lv_down0         from a zero iterate: the smoothing step, the residual of
+//                     the new iterate and its restriction P_t^T (two slab pairs
+//                     per thread)
+//  k_lv_down          the same from a given iterate (the last of nu1 > 1 steps)
 //  k_lv_up            prolongation u + P_t e and the first post-smoothing step
+//                     (two slab pairs per thread)
 //  k_lv_coarse        exact solve of the coarsest level: forward substitution
 //                     u_n = A^{-1} (f_n + e_0 u_{n-1, last}) over its slabs
 //  k_lv_res_restrict  residual and restriction without smoothing (nu1 = 0)
@@ -232,55 +235,124 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <typename T, int NT>
+// Pre-smoothing from zero + residual + restriction for PP consecutive slab
+// pairs of one mode per thread: the mode's inverse is loaded once for all of
+// them, and the new last entry of the slab before pair q > 0 is the previous
+// pair's (the same arithmetic as k_lv_down<.., true>).
+template <typename T, int NT, int PP>
 __global__ void __launch_bounds__(256)
-    k_lv_up(const T *__restrict__ ec, const T *__restrict__ uin, T *__restrict__ uout,
-            const T *__restrict__ f, const T *__restrict__ inv, long long S,
-            const __grid_constant__ ProlongCoefs<T> pc, T omega, int spp, long long ncoarse) {
+    k_lv_down0(T *__restrict__ uout, const T *__restrict__ f, T *__restrict__ fc,
+               const T *__restrict__ inv, long long S, const __grid_constant__ ProlongCoefs<T> pc,
+               T omega, int spp, long long ncoarse) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const long long mc = slab_index();
-    if (k >= S || mc >= ncoarse) return;
-    const long long a = 2 * mc;
-    const long long ba = a * NT * S + k, bb = ba + (long long)NT * S;
-    T e[NT], ua[NT], ub[NT];
-    load_col<T, NT>(ec, mc * NT * S + k, S, e);
-    load_col<T, NT>(uin, ba, S, ua);
-    load_col<T, NT>(uin, bb, S, ub);
+    const long long mc0 = slab_index() * PP;
+    if (k >= S || mc0 >= ncoarse) return;
+    T m[NT * NT];
+    load_inv<T, NT>(inv, S, k, m);
+    T carried = T(0);
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-        T pa = T(0), pb = T(0);
+    for (int q = 0; q < PP; ++q) {
+        const long long mc = mc0 + q;
+        if (mc >= ncoarse) break;
+        const long long a = 2 * mc;
+        const long long ba = a * NT * S + k, bb = ba + (long long)NT * S;
+        T new_prev = T(0);
+        if (((int)a % spp) != 0) {
+            if (q > 0) {
+                new_prev = carried;
+            } else {
+                T rp[NT];
+                load_col<T, NT>(f, ba - (long long)NT * S, S, rp);
+                new_prev = omega * lastrow<T, NT>(m, rp);
+            }
+        }
+        T fa[NT], fb[NT], ua[NT], ub[NT];
+        load_col<T, NT>(f, ba, S, fa);
+        load_col<T, NT>(f, bb, S, fb);
+        matvec<T, NT>(m, fa, ua);
+        matvec<T, NT>(m, fb, ub);
+        T ra[NT], rb[NT], out[NT];
 #pragma unroll
         for (int i = 0; i < NT; ++i) {
-            pa += pc.P[j * NTMAX + i] * e[i];
-            pb += pc.P[(NT + j) * NTMAX + i] * e[i];
+            ua[i] *= omega;
+            ub[i] *= omega;
+            ra[i] = (T(1) - omega) * fa[i];
+            rb[i] = (T(1) - omega) * fb[i];
         }
-        ua[j] += pa;
-        ub[j] += pb;
+        store_col<T, NT>(uout, ba, S, ua);
+        store_col<T, NT>(uout, bb, S, ub);
+        ra[0] += new_prev;
+        rb[0] += ua[NT - 1];
+        carried = ub[NT - 1];
+        restrict_pair<T, NT>(pc, ra, rb, out);
+        store_col<T, NT>(fc, mc * NT * S + k, S, out);
     }
-    T uprev = T(0);
-    if (((int)a % spp) != 0) {  // corrected last entry of slab a - 1, from coarse slab mc - 1
-        T ep[NT];
-        load_col<T, NT>(ec, (mc - 1) * NT * S + k, S, ep);
-        T pl = T(0);
-#pragma unroll
-        for (int i = 0; i < NT; ++i) pl += pc.P[(2 * NT - 1) * NTMAX + i] * ep[i];
-        uprev = uin[ba - S] + pl;
-    }
-    T m[NT * NT], r[NT], v[NT];
+}
+
+// Prolongation + first post-smoothing step for PP consecutive slab pairs of
+// one mode per thread (Jacobi: each slab sees its predecessor corrected but
+// not yet smoothed): the corrected last
+// entry of the slab before pair q > 0 is the previous pair's.
+template <typename T, int NT, int PP>
+__global__ void __launch_bounds__(256)
+    k_lv_up(const T *__restrict__ ec, const T *__restrict__ uin, T *__restrict__ uout,
+             const T *__restrict__ f, const T *__restrict__ inv, long long S,
+             const __grid_constant__ ProlongCoefs<T> pc, T omega, int spp, long long ncoarse) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long mc0 = slab_index() * PP;
+    if (k >= S || mc0 >= ncoarse) return;
+    T m[NT * NT];
     load_inv<T, NT>(inv, S, k, m);
-    load_col<T, NT>(f, ba, S, r);
-    r[0] += uprev;
-    matvec<T, NT>(m, r, v);
-    const T a_last = ua[NT - 1];
+    T carried = T(0);
 #pragma unroll
-    for (int i = 0; i < NT; ++i) v[i] = (T(1) - omega) * ua[i] + omega * v[i];
-    store_col<T, NT>(uout, ba, S, v);
-    load_col<T, NT>(f, bb, S, r);
-    r[0] += a_last;
-    matvec<T, NT>(m, r, v);
+    for (int q = 0; q < PP; ++q) {
+        const long long mc = mc0 + q;
+        if (mc >= ncoarse) break;
+        const long long a = 2 * mc;
+        const long long ba = a * NT * S + k, bb = ba + (long long)NT * S;
+        T e[NT], ua[NT], ub[NT], fa[NT], fb[NT];
+        load_col<T, NT>(ec, mc * NT * S + k, S, e);
+        load_col<T, NT>(uin, ba, S, ua);
+        load_col<T, NT>(uin, bb, S, ub);
+        load_col<T, NT>(f, ba, S, fa);
+        load_col<T, NT>(f, bb, S, fb);
 #pragma unroll
-    for (int i = 0; i < NT; ++i) v[i] = (T(1) - omega) * ub[i] + omega * v[i];
-    store_col<T, NT>(uout, bb, S, v);
+        for (int j = 0; j < NT; ++j) {
+            T pa = T(0), pb = T(0);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                pa += pc.P[j * NTMAX + i] * e[i];
+                pb += pc.P[(NT + j) * NTMAX + i] * e[i];
+            }
+            ua[j] += pa;
+            ub[j] += pb;
+        }
+        T uprev = T(0);
+        if (((int)a % spp) != 0) {
+            if (q > 0) {
+                uprev = carried;
+            } else {
+                T ep[NT];
+                load_col<T, NT>(ec, (mc - 1) * NT * S + k, S, ep);
+                T pl = T(0);
+#pragma unroll
+                for (int i = 0; i < NT; ++i) pl += pc.P[(2 * NT - 1) * NTMAX + i] * ep[i];
+                uprev = uin[ba - S] + pl;
+            }
+        }
+        carried = ub[NT - 1];
+        T v[NT];
+        fa[0] += uprev;
+        matvec<T, NT>(m, fa, v);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) v[i] = (T(1) - omega) * ua[i] + omega * v[i];
+        store_col<T, NT>(uout, ba, S, v);
+        fb[0] += ua[NT - 1];
+        matvec<T, NT>(m, fb, v);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) v[i] = (T(1) - omega) * ub[i] + omega * v[i];
+        store_col<T, NT>(uout, bb, S, v);
+    }
 }
 
 template <typename T, int NT>
@@ -360,7 +432,7 @@ __global__ void __launch_bounds__(256)
 // per problem, nu1 = nu2 = 1, zero initial iterate on every level), in one
 // launch: one thread per (spatial mode, rhs) runs the sub-cycle sequentially
 // over its slabs with the level vectors in thread-local memory (an
-// interleaved, L1-resident per-thread array), the same steps as k_lv_down /
+// interleaved, L1-resident per-thread array), the same steps as k_lv_down0 /
 // k_lv_coarse / k_lv_up: the Jacobi steps see the previous slab's iterate
 // from before the step, which the sequential sweep keeps in a register.
 constexpr int TAIL_SLABS = 16;
@@ -524,9 +596,10 @@ cudaError_t launch_spec_down(const T *uin, T *uout, const T *f, T *fc, const T *
     if (uin) {
         ST_NT_DISPATCH(c.nt, (k_lv_down<T, NT, false><<<L.grid, L.block, 0, s>>>(
                                  uin, uout, f, fc, inv, mu, g.nxyz, c, pc, omega, spp, ncoarse)));
-    } else {
-        ST_NT_DISPATCH(c.nt, (k_lv_down<T, NT, true><<<L.grid, L.block, 0, s>>>(
-                                 uin, uout, f, fc, inv, mu, g.nxyz, c, pc, omega, spp, ncoarse)));
+    } else {  // from zero: two slab pairs per thread
+        const ModeLaunch L2 = mode_launch(g.nxyz, (ncoarse + 1) / 2);
+        ST_NT_DISPATCH(c.nt, (k_lv_down0<T, NT, 2><<<L2.grid, L2.block, 0, s>>>(
+                                 uout, f, fc, inv, g.nxyz, pc, omega, spp, ncoarse)));
     }
     return cudaGetLastError();
 }
@@ -536,8 +609,8 @@ cudaError_t launch_spec_up(const T *ec, const T *uin, T *uout, const T *f, const
                            const Grid &g, const ProlongCoefs<T> &pc, T omega, int spp,
                            long long ncoarse, cudaStream_t s) {
     if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
-    const ModeLaunch L = mode_launch(g.nxyz, ncoarse);
-    ST_NT_DISPATCH(pc.nt, (k_lv_up<T, NT><<<L.grid, L.block, 0, s>>>(
+    const ModeLaunch L = mode_launch(g.nxyz, (ncoarse + 1) / 2);  // two slab pairs per thread
+    ST_NT_DISPATCH(pc.nt, (k_lv_up<T, NT, 2><<<L.grid, L.block, 0, s>>>(
                               ec, uin, uout, f, inv, g.nxyz, pc, omega, spp, ncoarse)));
     return cudaGetLastError();
 }

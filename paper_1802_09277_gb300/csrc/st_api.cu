@@ -206,6 +206,8 @@ struct KScope {
     KScope(st_handle h_, int c, double by, double fl) : h(h_), cls(c), bytes(by), flops(fl) {
         if (h->prof_on && (a = next_event(h))) cudaEventRecord(a, h->stream);
     }
+    // nothing was launched in the scope: record nothing
+    void cancel() { a = nullptr; }
     ~KScope() {
         if (!a) return;
         cudaEvent_t b = next_event(h);
@@ -438,6 +440,7 @@ int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long lon
         if (e == cudaSuccess) return ST_OK;
         if (e != cudaErrorNotSupported) CK(e);
         cudaGetLastError();
+        ks.cancel();
     }
     KScope ks(h, cls_of<T>(ST_PROF_GEMM64, ST_PROF_GEMM32), sizeof(T) * (2.0 * E + n * n),
               2.0 * E * n);
