@@ -418,6 +418,13 @@ def roofline_entry(r):
         base.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                     peak_note="FP32 CUDA-core FMA rate: unit counts x max SM clock")
         return base
+    if dom == "stencil_df":  # double-float on the FP32 pipe: 15 FP32 instructions per 2-flop FMA
+        peak = 152 * 128 * clk_max * 2 / 15 / 1e12
+        ach = pd["flops"] / secs / 1e12
+        base.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    peak_note="FP32 lane rate x max SM clock x 2 flops / 15 instructions per "
+                              "double-float multiply-add")
+        return base
     if dom in ("stencil64", "gemm64"):  # FP64 pipe: GB300's 1.25 TFLOP/s dense FP64
         peak = 1.25
         ach = pd["flops"] / secs / 1e12

@@ -72,6 +72,21 @@ __device__ __forceinline__ double df_to_double(dfloat a) {
     return __dadd_rn(df_widen(a.hi), df_widen(a.lo));
 }
 
+// acc + a * b in one step: the leading product's exact error by FMA, the
+// cross terms added to it, one TwoSum with the accumulator, renormalisation
+__device__ __forceinline__ dfloat df_fma(dfloat acc, dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    float t = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    t = __fadd_rn(t, __fadd_rn(acc.lo, e));
+    const float hi = __fadd_rn(s, t);
+    return dfloat(hi, __fsub_rn(t, __fsub_rn(hi, s)));
+}
+
 __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) { return df_add(a, b); }
 __device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return df_add(a, -b); }

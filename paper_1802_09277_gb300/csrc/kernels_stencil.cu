@@ -31,6 +31,17 @@ template <typename T, typename C>
 __device__ __forceinline__ T from_c(C x) {
     return (T)x;
 }
+// acc + x * y: contracted to one FMA in FP32 / FP64, the fused double-float
+// multiply-add for dfloat
+template <typename C>
+__device__ __forceinline__ C madd(C acc, C x, C y) {
+    return acc + x * y;
+}
+template <>
+__device__ __forceinline__ dfloat madd<dfloat>(dfloat acc, dfloat x, dfloat y) {
+    return df_fma(acc, x, y);
+}
+
 // FP64 data in double-float arithmetic: split and widen without FP64-rate
 // conversions (GB300 runs FP64 at 1/64 of the FP32 rate)
 template <>
@@ -157,13 +168,13 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
             C a = C(0), b = C(0);
             if (mass_only) {
 #pragma unroll
-                for (int o = 0; o < W; ++o) a += bMx[ex * W + o] * srow[o];
+                for (int o = 0; o < W; ++o) a = madd(a, bMx[ex * W + o], srow[o]);
             } else {
 #pragma unroll
                 for (int o = 0; o < W; ++o) {
                     const C sv = srow[o];
-                    a += bMx[ex * W + o] * sv;
-                    b += bKx[ex * W + o] * sv;
+                    a = madd(a, bMx[ex * W + o], sv);
+                    b = madd(b, bKx[ex * W + o], sv);
                 }
             }
             A[e] = a;
@@ -180,15 +191,15 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
                 if (mass_only) {
 #pragma unroll
                     for (int o = 0; o < W; ++o)
-                        aa += bMy[ey * W + o] * A[(sz * SY + ey + o) * TX + ex];
+                        aa = madd(aa, bMy[ey * W + o], A[(sz * SY + ey + o) * TX + ex]);
                 } else {
 #pragma unroll
                     for (int o = 0; o < W; ++o) {
                         const int idx = (sz * SY + ey + o) * TX + ex;
                         const C av = A[idx], bv = B[idx];
                         const C my = bMy[ey * W + o], ky = bKy[ey * W + o];
-                        aa += my * av;
-                        ss += ky * av + my * bv;
+                        aa = madd(aa, my, av);
+                        ss = madd(madd(ss, ky, av), my, bv);
                     }
                 }
                 AA[e] = aa;
@@ -212,8 +223,8 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
                 for (int o = 0; o < W; ++o) {
                     const int idx = ((a + o) * TY + ty) * TX + tx;
                     const C mz = bMz[a * W + o], kz = bKz[a * W + o];
-                    m += mz * pm[idx];
-                    k += kz * pm[idx] + mz * pk[idx];
+                    m = madd(m, mz, pm[idx]);
+                    k = madd(madd(k, kz, pm[idx]), mz, pk[idx]);
                 }
             } else {
                 m = pm[ty * TX + tx];
@@ -224,7 +235,7 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
             } else {
 #pragma unroll
                 for (int i = 0; i < NTMAX; ++i)
-                    if (i < nt) acc[a][i] += tc.CK[i * NTMAX + jj] * m + tc.CM[i * NTMAX + jj] * k;
+                    if (i < nt) acc[a][i] = madd(madd(acc[a][i], tc.CK[i * NTMAX + jj], m), tc.CM[i * NTMAX + jj], k);
             }
         }
     }
@@ -261,7 +272,7 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
                 C w = C(0);
 #pragma unroll
                 for (int j = 0; j < NTMAX; ++j)
-                    if (j < nt) w += tc.Y[i * NTMAX + j] * r[j];
+                    if (j < nt) w = madd(w, tc.Y[i * NTMAX + j], r[j]);
                 out[base + (long long)i * nxyz] = from_c<T>(w);
             }
         } else {
