@@ -96,10 +96,30 @@ struct TcArgs {
     int n_in, n_out;   // contracted / produced axis length
     int k_pad;         // n_in padded to the MMA K step
     int n_pad;         // MODE_S: n_out padded to 16
+    int kch;           // 16-byte K chunks staged at a time (even; = all of K when it fits)
+    int mh;            // MODE_X: 128-row halves of the output modes (1 or 2)
     long long ncols;   // number of GEMM columns (input rows / (outer, inner) pairs)
     long long inner;   // MODE_S: stride of the contracted axis
     int *err;          // set to 1 if an mbarrier wait ran out
 };
+
+// Stage 16-byte chunks [k0, k0 + kcs) of the weight operand (rows = output
+// modes, zero padded) as a K-major tile of wrows rows.
+template <int KIND>
+__device__ __forceinline__ void stage_w(const TcArgs &a, unsigned char *wtile, int wrows, int k0,
+                                        int kcs, size_t lo_off) {
+    constexpr int EPC = 16 / KindTraits<KIND>::ESZ;
+    for (int t = threadIdx.x; t < wrows * kcs; t += TC_THREADS) {
+        const int r = t / kcs, kc = t % kcs;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < EPC; ++j) {
+            const int i = (k0 + kc) * EPC + j;
+            v[j] = (r < a.n_out && i < a.n_in) ? a.wt[(long long)r * a.n_in + i] : 0.f;
+        }
+        stage16<KIND>(wtile, wrows, r, kc, v, lo_off);
+    }
+}
 
 template <int KIND, int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ TcArgs a) {
@@ -110,25 +130,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
     constexpr int EPC = 16 / KT::ESZ;  // elements per 16-byte chunk
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KC = a.k_pad / EPC;  // 16-byte chunks per operand row
-    const int wrows = (MODE == 0) ? 128 : a.n_pad;
-    // [W hi | W lo] [X hi | X lo] (lo parts only for the split kind)
-    const size_t wbytes = (size_t)wrows * KC * 16, xbytes = (size_t)TC_COLS * KC * 16;
+    const int kch = a.kch;         // chunks staged at a time
+    const int nchunk = (KC + kch - 1) / kch;
+    const int mh = (MODE == 0) ? a.mh : 1;
+    const int wrows = (MODE == 0) ? 128 * mh : a.n_pad;
+    // [W hi | W lo] [X hi | X lo] (lo parts only for the split kind), kch chunks each
+    const size_t wbytes = (size_t)wrows * kch * 16, xbytes = (size_t)TC_COLS * kch * 16;
     unsigned char *wtile = smem;
     unsigned char *xtile = smem + KT::NSPLIT * wbytes;
-    const uint32_t tmem_cols = (MODE == 0) ? 128u : (a.n_pad <= 32 ? 32u : a.n_pad <= 64 ? 64u
-                                                   : a.n_pad <= 128 ? 128u : 256u);
+    const uint32_t tmem_cols = (MODE == 0) ? (uint32_t)(TC_COLS * mh)
+                                           : (a.n_pad <= 32 ? 32u : a.n_pad <= 64 ? 64u
+                                              : a.n_pad <= 128 ? 128u : 256u);
 
-    // weight operand Wt[k][i] (zero padded), staged once
-    for (int t = tid; t < wrows * KC; t += TC_THREADS) {
-        const int r = t / KC, kc = t % KC;
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < EPC; ++j) {
-            const int i = kc * EPC + j;
-            v[j] = (r < a.n_out && i < a.n_in) ? a.wt[(long long)r * a.n_in + i] : 0.f;
-        }
-        stage16<KIND>(wtile, wrows, r, kc, v, wbytes);
-    }
+    // the whole weight operand fits: staged once for all column tiles
+    if (nchunk == 1) stage_w<KIND>(a, wtile, wrows, 0, KC, wbytes);
     if (tid == 0) tc::mbar_init(&mbar, 1);
     if (warp == 0) tc::tmem_alloc(&tmem_base, tmem_cols);
     tc::fence_before_sync();
@@ -143,79 +158,95 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
 
     for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
         const long long c0 = tile * TC_COLS;
-        // ---- stage the activation tile: 128 rows (columns c) x k_pad ----
-        if (MODE == 0) {
-            // lanes: 8 consecutive rows x 4 consecutive 16-byte chunks
-            for (int t = tid; t < TC_COLS * KC; t += TC_THREADS) {
-                const int grp = t / (8 * KC), rem = t % (8 * KC);
-                const int kc = rem / 8, r = grp * 8 + rem % 8;
-                const long long c = c0 + r;
-                float v[8];
+        for (int ch = 0; ch < nchunk && !failed; ++ch) {
+            const int k0 = ch * kch;
+            const int kcs = (KC - k0 < kch) ? KC - k0 : kch;  // even: KC and kch are
+            if (nchunk > 1) stage_w<KIND>(a, wtile, wrows, k0, kcs, wbytes);
+            // ---- stage the activation chunk: 128 rows (columns c) x kcs ----
+            if (MODE == 0) {
+                // lanes: 8 consecutive rows x 4 consecutive 16-byte chunks
+                for (int t = tid; t < TC_COLS * kcs; t += TC_THREADS) {
+                    const int grp = t / (8 * kcs), rem = t % (8 * kcs);
+                    const int kc = rem / 8, r = grp * 8 + rem % 8;
+                    const long long c = c0 + r;
+                    float v[8];
 #pragma unroll
-                for (int j = 0; j < EPC; ++j) {
-                    const int i = kc * EPC + j;
-                    v[j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
+                    for (int j = 0; j < EPC; ++j) {
+                        const int i = (k0 + kc) * EPC + j;
+                        v[j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
+                    }
+                    stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
                 }
-                stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
-            }
-        } else {
-            // lanes: consecutive columns (consecutive inner index), same chunk
-            for (int t = tid; t < TC_COLS * KC; t += TC_THREADS) {
-                const int kc = t / TC_COLS, r = t % TC_COLS;
-                const long long c = c0 + r;
-                const long long o = c / a.inner, ci = c % a.inner;
-                const float *src = a.in + o * a.n_in * a.inner + ci;
-                float v[8];
+            } else {
+                // lanes: consecutive columns (consecutive inner index), same chunk
+                for (int t = tid; t < TC_COLS * kcs; t += TC_THREADS) {
+                    const int kc = t / TC_COLS, r = t % TC_COLS;
+                    const long long c = c0 + r;
+                    const long long o = c / a.inner, ci = c % a.inner;
+                    const float *src = a.in + o * a.n_in * a.inner + ci;
+                    float v[8];
 #pragma unroll
-                for (int j = 0; j < EPC; ++j) {
-                    const int i = kc * EPC + j;
-                    v[j] = (c < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
-                }
-                stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
-            }
-        }
-        tc::fence_proxy_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        // ---- MMAs: K in 32-byte steps ----
-        if (tid == 0) {
-            const uint32_t wa = tc::smem_u32(wtile), xa = tc::smem_u32(xtile);
-            const uint32_t lbo_w = (uint32_t)wrows * 16, lbo_x = TC_COLS * 16;
-            const int steps = KC / 2;
-            // split kind: (hi, hi), (hi, lo), (lo, hi) per K step
-            constexpr int NPROD = (KT::NSPLIT == 2) ? 3 : 1;
-            for (int s = 0; s < steps; ++s) {
-#pragma unroll
-                for (int q = 0; q < NPROD; ++q) {
-                    const uint32_t wo = (q == 2) ? (uint32_t)wbytes : 0u;
-                    const uint32_t xo = (q == 1) ? (uint32_t)xbytes : 0u;
-                    const uint64_t dw = tc::make_sdesc(wa + wo + 2 * s * lbo_w, lbo_w, 128);
-                    const uint64_t dx = tc::make_sdesc(xa + xo + 2 * s * lbo_x, lbo_x, 128);
-                    const uint32_t acc = (s > 0 || q > 0) ? 1u : 0u;
-                    if (MODE == 0)
-                        tc::mma<KT::FMT>(tmem, dw, dx, idesc, acc);
-                    else
-                        tc::mma<KT::FMT>(tmem, dx, dw, idesc, acc);
+                    for (int j = 0; j < EPC; ++j) {
+                        const int i = (k0 + kc) * EPC + j;
+                        v[j] = (c < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
+                    }
+                    stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
                 }
             }
-            tc::commit(&mbar);
+            tc::fence_proxy_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            // ---- MMAs over the chunk: K in 32-byte steps ----
+            if (tid == 0) {
+                const uint32_t wa = tc::smem_u32(wtile), xa = tc::smem_u32(xtile);
+                const uint32_t lbo_w = (uint32_t)wrows * 16, lbo_x = TC_COLS * 16;
+                const int steps = kcs / 2;
+                // split kind: (hi, hi), (hi, lo), (lo, hi) per K step
+                constexpr int NPROD = (KT::NSPLIT == 2) ? 3 : 1;
+                for (int s = 0; s < steps; ++s) {
+#pragma unroll
+                    for (int q = 0; q < NPROD; ++q) {
+                        const uint32_t wo = (q == 2) ? (uint32_t)wbytes : 0u;
+                        const uint32_t xo = (q == 1) ? (uint32_t)xbytes : 0u;
+                        const uint64_t dx = tc::make_sdesc(xa + xo + 2 * s * lbo_x, lbo_x, 128);
+                        const uint32_t acc = (ch > 0 || s > 0 || q > 0) ? 1u : 0u;
+                        if (MODE == 0) {
+                            // output modes 128h .. 128h + 127: rows 128h.. of the weight
+                            // tile (16 core-matrix groups of 128 bytes further), TMEM
+                            // columns 128h ..
+                            for (int h = 0; h < mh; ++h) {
+                                const uint64_t dw = tc::make_sdesc(
+                                    wa + wo + 2 * s * lbo_w + (uint32_t)h * 2048u, lbo_w, 128);
+                                tc::mma<KT::FMT>(tmem + (uint32_t)(h * TC_COLS), dw, dx, idesc, acc);
+                            }
+                        } else {
+                            const uint64_t dw = tc::make_sdesc(wa + wo + 2 * s * lbo_w, lbo_w, 128);
+                            tc::mma<KT::FMT>(tmem, dx, dw, idesc, acc);
+                        }
+                    }
+                }
+                tc::commit(&mbar);
+            }
+            // the MMAs have read the chunk before it is overwritten or the
+            // accumulator is read
+            if (!tc::mbar_wait_bounded(&mbar, phase, TC_WAIT_NS)) {
+                failed = true;
+                if (tid == 0) atomicExch(a.err, 1);
+            }
+            phase ^= 1u;
+            tc::fence_after_sync();
         }
-        if (!tc::mbar_wait_bounded(&mbar, phase, TC_WAIT_NS)) {
-            failed = true;
-            if (tid == 0) atomicExch(a.err, 1);
-        }
-        phase ^= 1u;
-        tc::fence_after_sync();
         if (!failed) {
             // ---- epilogue: TMEM -> registers -> global ----
             const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
             if (MODE == 0) {
-                const int k = 32 * warp + lane;  // output mode of this lane
-                if (32 * warp < a.n_out) {
+                for (int h = 0; h < mh; ++h) {
+                    const int k = 128 * h + 32 * warp + lane;  // output mode of this lane
+                    if (128 * h + 32 * warp >= a.n_out) continue;
                     for (int cc = 0; cc < TC_COLS; cc += 16) {
                         float v[16];
-                        tc::tmem_ld16(tmem + lane_base + cc, v);
+                        tc::tmem_ld16(tmem + lane_base + (uint32_t)(h * TC_COLS + cc), v);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const long long c = c0 + cc + j;
@@ -245,24 +276,37 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
     if (warp == 0) tc::tmem_dealloc(tmem, tmem_cols);
 }
 
+constexpr size_t TC_SMEM_MAX = 200 * 1024;
+
 template <int KIND, int MODE>
-static cudaError_t launch_tc_t(const TcArgs &a, cudaStream_t s, int nsm, int ctas_per_sm) {
+static cudaError_t launch_tc_t(TcArgs a, cudaStream_t s, int nsm, int ctas_per_sm) {
     using KT = KindTraits<KIND>;
     constexpr int EPC = 16 / KT::ESZ;
     const int KC = a.k_pad / EPC;
-    const int wrows = (MODE == 0) ? 128 : a.n_pad;
-    const size_t smem = (size_t)KT::NSPLIT * (wrows + TC_COLS) * KC * 16;
-    if (smem > 200 * 1024) return cudaErrorNotSupported;  // the caller uses CUDA cores
+    const int wrows = (MODE == 0) ? 128 * a.mh : a.n_pad;
+    // stage the whole K when it fits, else the largest even number of chunks
+    const size_t per_chunk = (size_t)KT::NSPLIT * (wrows + TC_COLS) * 16;
+    int kch = KC;
+    if (per_chunk * KC > TC_SMEM_MAX) {  // balanced even chunks under the limit
+        const int kmax = (int)(TC_SMEM_MAX / per_chunk) & ~1;
+        if (kmax < 2) return cudaErrorNotSupported;  // the caller uses CUDA cores
+        const int nch = (KC + kmax - 1) / kmax;
+        kch = (((KC + nch - 1) / nch) + 1) & ~1;
+    }
+    a.kch = kch;
+    const size_t smem = per_chunk * kch;
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_axis<KIND, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)TC_SMEM_MAX);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     // CTAs per SM limited so that their TMEM columns fit in 512
-    const int tmem_cols = (MODE == 0) ? 128 : (a.n_pad <= 32 ? 32 : a.n_pad <= 64 ? 64
-                                               : a.n_pad <= 128 ? 128 : 256);
+    const int tmem_cols = (MODE == 0) ? TC_COLS * a.mh
+                                      : (a.n_pad <= 32 ? 32 : a.n_pad <= 64 ? 64
+                                         : a.n_pad <= 128 ? 128 : 256);
     int per_sm = 512 / tmem_cols;
     const int by_smem = (int)((220 * 1024) / (smem + 1024));
     if (by_smem < per_sm) per_sm = by_smem;
@@ -294,8 +338,10 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
     a.inner = inner;
     a.err = err;
     if (ncols <= 0) return cudaSuccess;
-    if (mode == 0 && n_out > 128) return cudaErrorNotSupported;
+    if (mode == 0 && n_out > 256) return cudaErrorNotSupported;
     if (mode == 1 && a.n_pad > 256) return cudaErrorNotSupported;
+    a.mh = (mode == 0 && n_out > 128) ? 2 : 1;
+    a.kch = 0;
     if (kind == KIND_TF32X3)
         return mode == 0 ? launch_tc_t<KIND_TF32X3, 0>(a, s, nsm, ctas_per_sm)
                          : launch_tc_t<KIND_TF32X3, 1>(a, s, nsm, ctas_per_sm);

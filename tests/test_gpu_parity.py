@@ -300,8 +300,12 @@ def test_full_size_2d_sampled(st):
     assert rel <= 1.01e-8, (rel, info)
 
 
+# the last two: more than 128 modes on the contiguous axis (two 128-row
+# accumulator halves) and on the strided axis, with the contraction staged in
+# K chunks where the whole of it does not fit in shared memory
 TC_CASES = [(1, (16,), 2, 8, 4), (2, (37, 29), 2, 6, 2), (2, (20, 20), 1, 4, 5),
-            (3, (19, 11, 9), 2, 2, 2), (2, (64, 64), 2, 4, 2)]
+            (3, (19, 11, 9), 2, 2, 2), (2, (64, 64), 2, 4, 2), (2, (130, 20), 2, 4, 2),
+            (2, (20, 150), 3, 4, 2)]
 
 
 @pytest.mark.parametrize("prec,tol", [("mixed_tf32", 1e-2), ("mixed_bf16", 6e-2)])
@@ -359,7 +363,8 @@ def test_solve_refinement_parity(st, prec, basis, d, spans, p, N, ne):
     s.close()
 
 
-@pytest.mark.parametrize("d,spans,p,N,ne", [CASES[3], (2, (64, 64), 2, 8, 2), (3, (10, 9, 8), 2, 4, 2)])
+@pytest.mark.parametrize("d,spans,p,N,ne", [CASES[3], (2, (64, 64), 2, 8, 2), (3, (10, 9, 8), 2, 4, 2),
+                                            (2, (130, 20), 2, 4, 2), (2, (20, 150), 3, 4, 2)])
 def test_split_tf32_transforms_keep_fp32_refinement(st, d, spans, p, N, ne):
     """In the eigenbasis refinement only the two spatial transforms around
     each inner solve leave the eigenbasis; on the tensor cores they run as
