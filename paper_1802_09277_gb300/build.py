@@ -3,7 +3,7 @@
 Each translation unit under ``csrc/`` is compiled in parallel into
 ``_build/`` and linked into ``paper_1802_09277_gb300/libst_iga.so``.  A unit
 is recompiled only when it, or any header under ``csrc/`` or ``include/``,
-is newer than its object file.
+is newer than its object file (headers: csrc/*.h, csrc/*.cuh, include/*.h).
 """
 import concurrent.futures as cf
 import glob
@@ -27,7 +27,8 @@ def _sources():
 
 
 def _headers_mtime():
-    hs = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
+    hs = (glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+          glob.glob(os.path.join(ROOT, "include", "*.h")))
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 

@@ -1,0 +1,349 @@
+// Matrix-free slab operator of the space-time system (Eq. 2.4, Eq. 2.5 of
+// arXiv:1802.09277), sum-factorised over the banded 1D B-spline matrices.
+//
+// For every slab n and spatial point, with m_j = M_x u_{n,j} and
+// k_j = K_x u_{n,j} (M_x = M1z(x)M1y(x)M1x, K_x = sum over axes of K1 in one
+// slot) and the coupling plane m_prev = M_x u_{n-1,nt-1} (B_n = N_t (x) M_x,
+// N_t = e_1 e_nt^T for open knots):
+//   MODE_RES  : r_i = f_i - sum_j (Kt[i][j] m_j + Mt[i][j] k_j) + [i==0] m_prev
+//   MODE_APPLY: y_i =       sum_j (Kt[i][j] m_j + Mt[i][j] k_j) - [i==0] m_prev
+//   MODE_MASS : y_i =       sum_j  Mt[i][j] m_j                  (load vector)
+// optionally followed by the forward time transform w = Y r (the first step
+// of applying A_n^{-1} through Eq. 3.1).
+//
+// One CTA owns one slab and one spatial tile (all time planes).  Each plane
+// tile plus a halo of p is staged in shared memory, then reduced axis by
+// axis: x-pass (M1x, K1x), y-pass, z-pass; the 2p+1 band coefficients of the
+// tile's rows are staged once per CTA.
+//
+// Storage type T (FP64 or FP32 in HBM) and compute type C are separate: the
+// FP64-accurate residual of the mixed-precision refinement computes in
+// double-float (C = dfloat) on FP64 data, converting on load and store.
+#pragma once
+#include <type_traits>
+
+#include "st_internal.h"
+
+namespace st {
+
+template <typename C, typename T>
+__device__ __forceinline__ C to_c(T x) {
+    return C(x);
+}
+template <typename T, typename C>
+__device__ __forceinline__ T from_c(C x) {
+    return (T)x;
+}
+// acc + x * y: contracted to one FMA in FP32 / FP64, the fused double-float
+// multiply-add for dfloat
+template <typename C>
+__device__ __forceinline__ C madd(C acc, C x, C y) {
+    return acc + x * y;
+}
+template <>
+__device__ __forceinline__ dfloat madd<dfloat>(dfloat acc, dfloat x, dfloat y) {
+    return df_fma(acc, x, y);
+}
+
+// FP64 data in double-float arithmetic: split and widen without FP64-rate
+// conversions (GB300 runs FP64 at 1/64 of the FP32 rate)
+template <>
+__device__ __forceinline__ dfloat to_c<dfloat, double>(double x) {
+    return df_from_double(x);
+}
+template <>
+__device__ __forceinline__ double from_c<double, dfloat>(dfloat x) {
+    return df_to_double(x);
+}
+
+template <int DIM>
+struct TileShape;
+template <>
+struct TileShape<1> {
+    static constexpr int TX = 128, TY = 1, TZ = 1;
+};
+template <>
+struct TileShape<2> {
+    static constexpr int TX = 32, TY = 16, TZ = 1;
+};
+template <>
+struct TileShape<3> {
+    static constexpr int TX = 16, TY = 8, TZ = 4;
+};
+
+template <typename T, int P, int DIM>  // T: compute type
+struct StencilSmem {
+    using TS = TileShape<DIM>;
+    static constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
+    static constexpr int HX = P, HY = (DIM >= 2) ? P : 0, HZ = (DIM >= 3) ? P : 0;
+    static constexpr int SX = TX + 2 * HX, SY = TY + 2 * HY, SZ = TZ + 2 * HZ;
+    static constexpr int W = 2 * P + 1;
+    static constexpr int nS = SZ * SY * SX;
+    static constexpr int nA = SZ * SY * TX;
+    static constexpr int nAA = SZ * TY * TX;
+    static constexpr int nBand = 2 * W * (TX + TY + TZ);
+    // the staged plane S and the y-pass results AA, SS are never live at the
+    // same time (a barrier separates the z-pass reads from the next staging)
+    static constexpr int nR1 = (nS > 2 * nAA) ? nS : 2 * nAA;
+    static constexpr size_t bytes = sizeof(T) * (nR1 + 2 * nA + nBand);
+    static constexpr int threads = TX * TY;
+};
+
+// NTC > 0: N_t fixed at compile time (exact-length loops, fewer registers
+// for the N_t x TZ accumulators); NTC = 0: N_t from tc.nt, loops over NTMAX
+template <typename T, typename C, int P, int DIM, int NTC = 0>
+__global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
+    k_stencil(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out, Bands<T> bands,
+              Grid g, const __grid_constant__ TimeCoefs<C> tc, int slabs_per_prob, int slab0, int tiles_x, int tiles_y) {
+    using SM = StencilSmem<C, P, DIM>;
+    constexpr int TX = SM::TX, TY = SM::TY, TZ = SM::TZ;
+    constexpr int HX = SM::HX, HY = SM::HY, HZ = SM::HZ;
+    constexpr int SX = SM::SX, SY = SM::SY, SZ = SM::SZ, W = SM::W;
+    constexpr int NTH = SM::threads;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *S = reinterpret_cast<C *>(smem_raw);
+    C *AA = S;
+    C *SS = AA + SM::nAA;
+    C *A = S + SM::nR1;
+    C *B = A + SM::nA;
+    C *bMx = B + SM::nA;
+    C *bKx = bMx + TX * W;
+    C *bMy = bKx + TX * W;
+    C *bKy = bMy + TY * W;
+    C *bMz = bKy + TY * W;
+    C *bKz = bMz + TZ * W;
+
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % tiles_x) * TX;
+    const int y0 = ((tile / tiles_x) % tiles_y) * TY;
+    const int z0 = (tile / (tiles_x * tiles_y)) * TZ;
+    const int slab = slab0 + blockIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long nxyz = g.nxyz;
+    constexpr int NL = NTC > 0 ? NTC : NTMAX;
+    const int nt = NTC > 0 ? NTC : tc.nt;
+
+    // stage the band rows of this tile (zero outside the grid)
+    for (int e = tid; e < TX * W; e += NTH) {
+        const int gx = x0 + e / W;
+        bMx[e] = (gx < nx) ? to_c<C>(bands.M[0][(long long)gx * W + e % W]) : C(0);
+        bKx[e] = (gx < nx) ? to_c<C>(bands.K[0][(long long)gx * W + e % W]) : C(0);
+    }
+    if (DIM >= 2)
+        for (int e = tid; e < TY * W; e += NTH) {
+            const int gy = y0 + e / W;
+            bMy[e] = (gy < ny) ? to_c<C>(bands.M[1][(long long)gy * W + e % W]) : C(0);
+            bKy[e] = (gy < ny) ? to_c<C>(bands.K[1][(long long)gy * W + e % W]) : C(0);
+        }
+    if (DIM >= 3)
+        for (int e = tid; e < TZ * W; e += NTH) {
+            const int gz = z0 + e / W;
+            bMz[e] = (gz < nz) ? to_c<C>(bands.M[2][(long long)gz * W + e % W]) : C(0);
+            bKz[e] = (gz < nz) ? to_c<C>(bands.K[2][(long long)gz * W + e % W]) : C(0);
+        }
+
+    const int tx = tid % TX, ty = tid / TX;
+    C acc[TZ][NL];
+    C mprev[TZ];
+#pragma unroll
+    for (int a = 0; a < TZ; ++a) {
+        mprev[a] = C(0);
+#pragma unroll
+        for (int i = 0; i < NL; ++i) acc[a][i] = C(0);
+    }
+
+    const T *uslab = u + (long long)slab * nt * nxyz;
+    const bool has_prev = (tc.mode != MODE_MASS) && (slab % slabs_per_prob) != 0;
+
+    for (int jj = has_prev ? -1 : 0; jj < nt; ++jj) {
+        const T *plane = (jj < 0) ? uslab - nxyz : uslab + (long long)jj * nxyz;
+        __syncthreads();
+        for (int e = tid; e < SZ * SY * SX; e += NTH) {
+            const int sx = e % SX, sy = (e / SX) % SY, sz = e / (SX * SY);
+            const int gx = x0 + sx - HX, gy = y0 + sy - HY, gz = z0 + sz - HZ;
+            C v = C(0);
+            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+                v = to_c<C>(plane[((long long)gz * ny + gy) * nx + gx]);
+            S[e] = v;
+        }
+        __syncthreads();
+        // x-pass: A = M1x u, B = K1x u (the coupling plane needs only M_x u)
+        const bool mass_only = jj < 0;
+        for (int e = tid; e < SZ * SY * TX; e += NTH) {
+            const int ex = e % TX, row = e / TX;  // row = sz*SY + sy
+            const C *srow = S + row * SX + ex;
+            C a = C(0), b = C(0);
+            if (mass_only) {
+#pragma unroll
+                for (int o = 0; o < W; ++o) a = madd(a, bMx[ex * W + o], srow[o]);
+            } else {
+#pragma unroll
+                for (int o = 0; o < W; ++o) {
+                    const C sv = srow[o];
+                    a = madd(a, bMx[ex * W + o], sv);
+                    b = madd(b, bKx[ex * W + o], sv);
+                }
+            }
+            A[e] = a;
+            B[e] = b;
+        }
+        __syncthreads();
+        const C *pm;
+        const C *pk;
+        if (DIM >= 2) {
+            // y-pass: AA = M1y A, SS = K1y A + M1y B
+            for (int e = tid; e < SZ * TY * TX; e += NTH) {
+                const int ex = e % TX, ey = (e / TX) % TY, sz = e / (TX * TY);
+                C aa = C(0), ss = C(0);
+                if (mass_only) {
+#pragma unroll
+                    for (int o = 0; o < W; ++o)
+                        aa = madd(aa, bMy[ey * W + o], A[(sz * SY + ey + o) * TX + ex]);
+                } else {
+#pragma unroll
+                    for (int o = 0; o < W; ++o) {
+                        const int idx = (sz * SY + ey + o) * TX + ex;
+                        const C av = A[idx], bv = B[idx];
+                        const C my = bMy[ey * W + o], ky = bKy[ey * W + o];
+                        aa = madd(aa, my, av);
+                        ss = madd(madd(ss, ky, av), my, bv);
+                    }
+                }
+                AA[e] = aa;
+                SS[e] = ss;
+            }
+            __syncthreads();
+            pm = AA;
+            pk = SS;
+        } else {
+            pm = A;
+            pk = B;
+        }
+        // z-pass and accumulation into this thread's output points
+#pragma unroll
+        for (int a = 0; a < TZ; ++a) {
+            C m, k;
+            if (DIM >= 3) {
+                m = C(0);
+                k = C(0);
+#pragma unroll
+                for (int o = 0; o < W; ++o) {
+                    const int idx = ((a + o) * TY + ty) * TX + tx;
+                    const C mz = bMz[a * W + o], kz = bKz[a * W + o];
+                    m = madd(m, mz, pm[idx]);
+                    k = madd(madd(k, kz, pm[idx]), mz, pk[idx]);
+                }
+            } else {
+                m = pm[ty * TX + tx];
+                k = pk[ty * TX + tx];
+            }
+            if (jj < 0) {
+                mprev[a] = m;
+            } else {
+#pragma unroll
+                for (int i = 0; i < NL; ++i)
+                    if (i < nt) acc[a][i] = madd(madd(acc[a][i], tc.CK[i * NTMAX + jj], m), tc.CM[i * NTMAX + jj], k);
+            }
+        }
+    }
+
+    // epilogue
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (gx >= nx || gy >= ny) return;
+#pragma unroll
+    for (int a = 0; a < TZ; ++a) {
+        const int gz = z0 + a;
+        if (gz >= nz) break;
+        const long long sp = ((long long)gz * ny + gy) * nx + gx;
+        const long long base = (long long)slab * nt * nxyz + sp;
+        C r[NL];
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            if (i >= nt) {
+                r[i] = C(0);
+                continue;
+            }
+            C v = acc[a][i];
+            if (tc.mode == MODE_RES) {
+                v = to_c<C>(f[base + (long long)i * nxyz]) - v;
+                if (i == 0) v += mprev[a];
+            } else if (tc.mode == MODE_APPLY) {
+                if (i == 0) v -= mprev[a];
+            }
+            r[i] = v;
+        }
+        if (tc.fuse_y) {
+#pragma unroll
+            for (int i = 0; i < NL; ++i) {
+                if (i >= nt) break;
+                C w = C(0);
+#pragma unroll
+                for (int j = 0; j < NL; ++j)
+                    if (j < nt) w = madd(w, tc.Y[i * NTMAX + j], r[j]);
+                out[base + (long long)i * nxyz] = from_c<T>(w);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NL; ++i)
+                if (i < nt) out[base + (long long)i * nxyz] = from_c<T>(r[i]);
+        }
+    }
+}
+
+template <typename T, typename C, int P, int DIM, int NTC = 0>
+static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<T> &bands,
+                                    const Grid &g, const TimeCoefs<C> &tc, int slabs_per_prob,
+                                    int slab0, int nslabs, cudaStream_t s) {
+    using SM = StencilSmem<C, P, DIM>;
+    static bool attr_set = false;  // per device-less process; attribute is per function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_stencil<T, C, P, DIM, NTC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SM::bytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int tx = (g.nx + SM::TX - 1) / SM::TX;
+    const int ty = (g.ny + SM::TY - 1) / SM::TY;
+    const int tz = (g.nz + SM::TZ - 1) / SM::TZ;
+    if (nslabs <= 0) return cudaSuccess;
+    if (nslabs > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)(tx * ty * tz), (unsigned)nslabs);
+    k_stencil<T, C, P, DIM, NTC><<<grid, SM::threads, SM::bytes, s>>>(u, f, out, bands, g, tc,
+                                                                      slabs_per_prob, slab0, tx, ty);
+    return cudaGetLastError();
+}
+
+template <typename T, typename C>
+cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands, const Grid &g,
+                           const TimeCoefs<C> &tc, int slabs_per_prob, int slab0, int nslabs,
+                           cudaStream_t s) {
+#define ST_NT(PP, DD, N)                                                                        \
+    if (tc.nt == N)                                                                             \
+        return launch_stencil_t<T, C, PP, DD, N>(u, f, out, bands, g, tc, slabs_per_prob, slab0, \
+                                                 nslabs, s);
+#define ST_CASE(PP, DD)                                                                         \
+    if (g.p == PP && g.dim == DD) {                                                             \
+        if constexpr (std::is_same<C, dfloat>::value) {                                         \
+            ST_NT(PP, DD, 3) ST_NT(PP, DD, 4) ST_NT(PP, DD, 5) ST_NT(PP, DD, 6)                  \
+        }                                                                                       \
+        return launch_stencil_t<T, C, PP, DD>(u, f, out, bands, g, tc, slabs_per_prob, slab0,   \
+                                              nslabs, s);                                       \
+    }
+    ST_CASE(1, 1)
+    ST_CASE(2, 1)
+    ST_CASE(3, 1)
+    ST_CASE(1, 2)
+    ST_CASE(2, 2)
+    ST_CASE(3, 2)
+    ST_CASE(1, 3)
+    ST_CASE(2, 3)
+    ST_CASE(3, 3)
+#undef ST_CASE
+#undef ST_NT
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace st
