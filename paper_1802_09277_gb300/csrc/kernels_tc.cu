@@ -29,7 +29,7 @@ namespace st {
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lane quarter w % 4
 constexpr int TC_COLS = 128;  // columns (GEMM rows of the activation operand) per tile
 constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s: far above any tile's MMA time
 constexpr int KIND_TF32X3 = 3;  // split TF32 (see above); MMA format TF32
@@ -109,8 +109,10 @@ template <int KIND>
 __device__ __forceinline__ void stage_w(const TcArgs &a, unsigned char *wtile, int wrows, int k0,
                                         int kcs, size_t lo_off) {
     constexpr int EPC = 16 / KindTraits<KIND>::ESZ;
+    // consecutive lanes take consecutive rows: their 16-byte stores are
+    // contiguous in the core-matrix layout (no shared-memory bank conflicts)
     for (int t = threadIdx.x; t < wrows * kcs; t += TC_THREADS) {
-        const int r = t / kcs, kc = t % kcs;
+        const int kc = t / wrows, r = t % wrows;
         float v[8];
 #pragma unroll
         for (int j = 0; j < EPC; ++j) {
@@ -239,12 +241,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
         }
         if (!failed) {
             // ---- epilogue: TMEM -> registers -> global ----
-            const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+            // warp w reads TMEM lanes 32 (w % 4) ..; warps w and w + 4 split the columns
+            const int wq = warp & 3, wh = warp >> 2;
+            const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
             if (MODE == 0) {
                 for (int h = 0; h < mh; ++h) {
-                    const int k = 128 * h + 32 * warp + lane;  // output mode of this lane
-                    if (128 * h + 32 * warp >= a.n_out) continue;
-                    for (int cc = 0; cc < TC_COLS; cc += 16) {
+                    const int k = 128 * h + 32 * wq + lane;  // output mode of this lane
+                    if (128 * h + 32 * wq >= a.n_out) continue;
+                    for (int cc = wh * (TC_COLS / 2); cc < (wh + 1) * (TC_COLS / 2); cc += 16) {
                         float v[16];
                         tc::tmem_ld16(tmem + lane_base + (uint32_t)(h * TC_COLS + cc), v);
 #pragma unroll
@@ -255,10 +259,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
                     }
                 }
             } else {
-                const long long c = c0 + 32 * warp + lane;  // column of this lane
+                const long long c = c0 + 32 * wq + lane;  // column of this lane
                 const long long o = c / a.inner, ci = c % a.inner;
                 float *dst = a.out + o * a.n_out * a.inner + ci;
-                for (int kk = 0; kk < a.n_pad; kk += 16) {
+                const int nk = a.n_pad / 16;  // 16-column groups, split between the warp pair
+                for (int kk = 16 * ((nk * wh) / 2); kk < 16 * ((nk * (wh + 1)) / 2); kk += 16) {
                     float v[16];
                     tc::tmem_ld16(tmem + lane_base + kk, v);
 #pragma unroll
