@@ -98,6 +98,7 @@ struct TcArgs {
     int n_pad;         // MODE_S: n_out padded to 16
     int kch;           // 16-byte K chunks staged at a time (even; = all of K when it fits)
     int mh;            // MODE_X: 128-row halves of the output modes (1 or 2)
+    int vec4;          // MODE_X: rows start on 16-byte boundaries (n_in % 4 == 0, aligned in)
     long long ncols;   // number of GEMM columns (input rows / (outer, inner) pairs)
     long long inner;   // MODE_S: stride of the contracted axis
     int *err;          // set to 1 if an mbarrier wait ran out
@@ -172,10 +173,23 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
                     const int kc = rem / 8, r = grp * 8 + rem % 8;
                     const long long c = c0 + r;
                     float v[8];
+                    const int i0 = (k0 + kc) * EPC;
+                    if (a.vec4 && c < a.ncols && i0 + EPC <= a.n_in) {
+                        // whole 16-byte groups of the row: vector loads
 #pragma unroll
-                    for (int j = 0; j < EPC; ++j) {
-                        const int i = (k0 + kc) * EPC + j;
-                        v[j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
+                        for (int j = 0; j < EPC; j += 4) {
+                            const float4 q = *reinterpret_cast<const float4 *>(a.in + c * a.n_in + i0 + j);
+                            v[j] = q.x;
+                            v[j + 1] = q.y;
+                            v[j + 2] = q.z;
+                            v[j + 3] = q.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < EPC; ++j) {
+                            const int i = i0 + j;
+                            v[j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
+                        }
                     }
                     stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
                 }
@@ -347,6 +361,7 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
     if (mode == 1 && a.n_pad > 256) return cudaErrorNotSupported;
     a.mh = (mode == 0 && n_out > 128) ? 2 : 1;
     a.kch = 0;
+    a.vec4 = (mode == 0 && n_in % 4 == 0 && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) ? 1 : 0;
     if (kind == KIND_TF32X3)
         return mode == 0 ? launch_tc_t<KIND_TF32X3, 0>(a, s, nsm, ctas_per_sm)
                          : launch_tc_t<KIND_TF32X3, 1>(a, s, nsm, ctas_per_sm);
