@@ -303,11 +303,19 @@ static cudaError_t launch_tc_t(TcArgs a, cudaStream_t s, int nsm, int ctas_per_s
     constexpr int EPC = 16 / KT::ESZ;
     const int KC = a.k_pad / EPC;
     const int wrows = (MODE == 0) ? 128 * a.mh : a.n_pad;
-    // stage the whole K when it fits, else the largest even number of chunks
+    // stage the whole K when it fits (in the shared memory of one CTA, or of
+    // one of ctas_per_sm CTAs when that is asked for), else balanced even
+    // chunks under that limit
     const size_t per_chunk = (size_t)KT::NSPLIT * (wrows + TC_COLS) * 16;
+    size_t limit = TC_SMEM_MAX;
+    if (ctas_per_sm > 1) {  // (a share too small for two chunks falls back to one CTA's
+                            // limit: the tensor cores keep the transform either way)
+        const size_t share = (size_t)(220 * 1024) / ctas_per_sm - 1024;
+        if (share < limit && share >= 2 * per_chunk) limit = share;
+    }
     int kch = KC;
-    if (per_chunk * KC > TC_SMEM_MAX) {  // balanced even chunks under the limit
-        const int kmax = (int)(TC_SMEM_MAX / per_chunk) & ~1;
+    if (per_chunk * KC > limit) {
+        const int kmax = (int)(limit / per_chunk) & ~1;
         if (kmax < 2) return cudaErrorNotSupported;  // the caller uses CUDA cores
         const int nch = (KC + kmax - 1) / kmax;
         kch = (((KC + nch - 1) / nch) + 1) & ~1;

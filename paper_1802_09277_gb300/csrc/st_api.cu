@@ -101,6 +101,8 @@ struct st_handle_s {
     // autotuned transform per axis: -1 = not tuned (heuristic), 0 = CUDA
     // cores, k > 0 = tensor cores with at most k CTAs per SM
     int tune[3] = {-1, -1, -1};
+    // the same for the split-TF32 (FP32-accurate) transforms of the refinement
+    int tune3[3] = {-1, -1, -1};
     double tune_ms[3] = {0, 0, 0};
     bool tuned = false;
     int *tc_err = nullptr;  // device flag: a tensor-core kernel's bounded wait ran out
@@ -436,7 +438,8 @@ int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long lon
         const cudaError_t e = launch_tc_axis(kind, axis == 0 ? 0 : 1, (const float *)in,
                                              (float *)out, Wt, (int)n, (int)n, ncols, inner,
                                              h->tc_err, h->nsm, h->stream,
-                                             h->tune[axis] > 0 ? h->tune[axis] : 0);
+                                             full32 ? (h->tune3[axis] > 0 ? h->tune3[axis] : 0)
+                                                    : (h->tune[axis] > 0 ? h->tune[axis] : 0));
         if (e == cudaSuccess) return ST_OK;
         if (e != cudaErrorNotSupported) CK(e);
         cudaGetLastError();
@@ -505,6 +508,28 @@ int autotune(st_handle h) {
         }
         h->tune[ax] = best_c;
         h->tune_ms[ax] = best;
+        if (!tc_ok) continue;
+        // the split-TF32 kind: CTAs per SM (its contraction is then staged in
+        // K chunks small enough for that many CTAs; same numbers either way)
+        double best3 = 1e30;
+        int best3_c = 1;
+        for (int c = 1; c <= 4; ++c) {
+            h->tune3[ax] = c;
+            float t[3];
+            for (int rep = 0; rep < 4; ++rep) {
+                CK(cudaEventRecord(e0, h->stream));
+                CKS(axis_pass<float>(h, ax, h->w32.w0, h->w32.w1, true, planes, true));
+                CK(cudaEventRecord(e1, h->stream));
+                CK(cudaEventSynchronize(e1));
+                if (rep > 0) CK(cudaEventElapsedTime(&t[rep - 1], e0, e1));
+            }
+            std::sort(t, t + 3);
+            if (t[1] < best3) {
+                best3 = t[1];
+                best3_c = c;
+            }
+        }
+        h->tune3[ax] = best3_c;
     }
     h->prof_on = prof;
     cudaEventDestroy(e0);
