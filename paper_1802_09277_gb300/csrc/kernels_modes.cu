@@ -156,7 +156,12 @@ __global__ void __launch_bounds__(256)
     store_col<T, NT>(uout, base, S, v);
 }
 
-template <typename T, int NT, bool ZERO>
+// The last of nu1 > 1 pre-smoothing steps (from a given iterate), the
+// residual of the new iterate and its restriction, one slab pair per thread.
+// Jacobi: the smoothed slabs see their predecessors' OLD iterates; the
+// residual needs the NEW last entry of slab a - 1, which the thread
+// recomputes (one more block product instead of a pass over HBM).
+template <typename T, int NT>
 __global__ void __launch_bounds__(256)
     k_lv_down(const T *__restrict__ uin, T *__restrict__ uout, const T *__restrict__ f,
               T *__restrict__ fc, const T *__restrict__ inv, const T *__restrict__ mu_tab,
@@ -170,75 +175,47 @@ __global__ void __launch_bounds__(256)
     const long long ba = a * NT * S + k, bb = ba + (long long)NT * S;
     T m[NT * NT];
     load_inv<T, NT>(inv, S, k, m);
-    // the new last entry of slab a - 1 (its old one is what slabs a sees)
     T new_prev = T(0), old_prev = T(0);
     if (!first) {
         const long long bp = ba - (long long)NT * S;
         T rp[NT];
         load_col<T, NT>(f, bp, S, rp);
-        if (!ZERO) {
-            old_prev = uin[bp + (long long)(NT - 1) * S];
-            if (((int)a - 1) % spp != 0) rp[0] += uin[bp - S];
-            new_prev = (T(1) - omega) * old_prev + omega * lastrow<T, NT>(m, rp);
-        } else {
-            new_prev = omega * lastrow<T, NT>(m, rp);
-        }
+        old_prev = uin[bp + (long long)(NT - 1) * S];
+        if (((int)a - 1) % spp != 0) rp[0] += uin[bp - S];
+        new_prev = (T(1) - omega) * old_prev + omega * lastrow<T, NT>(m, rp);
     }
-    T fa[NT], fb[NT], ua[NT], ub[NT];
+    T fa[NT], fb[NT], ua[NT], ub[NT], oa[NT], ob[NT], r[NT];
     load_col<T, NT>(f, ba, S, fa);
     load_col<T, NT>(f, bb, S, fb);
-    if (ZERO) {
-        matvec<T, NT>(m, fa, ua);
+    load_col<T, NT>(uin, ba, S, oa);
+    load_col<T, NT>(uin, bb, S, ob);
 #pragma unroll
-        for (int i = 0; i < NT; ++i) ua[i] *= omega;
-        matvec<T, NT>(m, fb, ub);
+    for (int i = 0; i < NT; ++i) r[i] = fa[i];
+    r[0] += old_prev;
+    matvec<T, NT>(m, r, ua);
 #pragma unroll
-        for (int i = 0; i < NT; ++i) ub[i] *= omega;
-        store_col<T, NT>(uout, ba, S, ua);
-        store_col<T, NT>(uout, bb, S, ub);
-        // residual of the smoothed iterate from zero: (1 - w) f + e_0 u_prev,new
-        T ra[NT], rb[NT], out[NT];
+    for (int i = 0; i < NT; ++i) ua[i] = (T(1) - omega) * oa[i] + omega * ua[i];
 #pragma unroll
-        for (int i = 0; i < NT; ++i) {
-            ra[i] = (T(1) - omega) * fa[i];
-            rb[i] = (T(1) - omega) * fb[i];
-        }
-        ra[0] += new_prev;
-        rb[0] += ua[NT - 1];
-        restrict_pair<T, NT>(pc, ra, rb, out);
-        store_col<T, NT>(fc, mc * NT * S + k, S, out);
-    } else {
-        T oa[NT], ob[NT], r[NT];
-        load_col<T, NT>(uin, ba, S, oa);
-        load_col<T, NT>(uin, bb, S, ob);
+    for (int i = 0; i < NT; ++i) r[i] = fb[i];
+    r[0] += oa[NT - 1];
+    matvec<T, NT>(m, r, ub);
 #pragma unroll
-        for (int i = 0; i < NT; ++i) r[i] = fa[i];
-        r[0] += old_prev;
-        matvec<T, NT>(m, r, ua);
-#pragma unroll
-        for (int i = 0; i < NT; ++i) ua[i] = (T(1) - omega) * oa[i] + omega * ua[i];
-#pragma unroll
-        for (int i = 0; i < NT; ++i) r[i] = fb[i];
-        r[0] += oa[NT - 1];
-        matvec<T, NT>(m, r, ub);
-#pragma unroll
-        for (int i = 0; i < NT; ++i) ub[i] = (T(1) - omega) * ob[i] + omega * ub[i];
-        store_col<T, NT>(uout, ba, S, ua);
-        store_col<T, NT>(uout, bb, S, ub);
-        // residual of the smoothed iterate, formed directly
-        const T mu = mu_tab[k];
-        T out[NT];
-        op_residual<T, NT>(c, mu, ua, new_prev, fa);
-        op_residual<T, NT>(c, mu, ub, ua[NT - 1], fb);
-        restrict_pair<T, NT>(pc, fa, fb, out);
-        store_col<T, NT>(fc, mc * NT * S + k, S, out);
-    }
+    for (int i = 0; i < NT; ++i) ub[i] = (T(1) - omega) * ob[i] + omega * ub[i];
+    store_col<T, NT>(uout, ba, S, ua);
+    store_col<T, NT>(uout, bb, S, ub);
+    // residual of the smoothed iterate, formed directly
+    const T mu = mu_tab[k];
+    T out[NT];
+    op_residual<T, NT>(c, mu, ua, new_prev, fa);
+    op_residual<T, NT>(c, mu, ub, ua[NT - 1], fb);
+    restrict_pair<T, NT>(pc, fa, fb, out);
+    store_col<T, NT>(fc, mc * NT * S + k, S, out);
 }
 
 // Pre-smoothing from zero + residual + restriction for PP consecutive slab
 // pairs of one mode per thread: the mode's inverse is loaded once for all of
 // them, and the new last entry of the slab before pair q > 0 is the previous
-// pair's (the same arithmetic as k_lv_down<.., true>).
+// pair's (from zero, so A u_new = w f and the residual is (1 - w) f + e_0 u_prev,new).
 template <typename T, int NT, int PP>
 __global__ void __launch_bounds__(256)
     k_lv_down0(T *__restrict__ uout, const T *__restrict__ f, T *__restrict__ fc,
@@ -594,7 +571,7 @@ cudaError_t launch_spec_down(const T *uin, T *uout, const T *f, T *fc, const T *
     if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
     const ModeLaunch L = mode_launch(g.nxyz, ncoarse);
     if (uin) {
-        ST_NT_DISPATCH(c.nt, (k_lv_down<T, NT, false><<<L.grid, L.block, 0, s>>>(
+        ST_NT_DISPATCH(c.nt, (k_lv_down<T, NT><<<L.grid, L.block, 0, s>>>(
                                  uin, uout, f, fc, inv, mu, g.nxyz, c, pc, omega, spp, ncoarse)));
     } else {  // from zero: two slab pairs per thread
         const ModeLaunch L2 = mode_launch(g.nxyz, (ncoarse + 1) / 2);
