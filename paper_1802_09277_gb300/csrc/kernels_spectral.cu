@@ -253,12 +253,10 @@ cudaError_t launch_spec_vcycle(const T *fin, T *uout, const SpecCoefs<T> *lvc_ho
         MB /= 2;
     long long bytes = spec_vcycle_elems(nlev, N, pc.nt, MB) * (long long)sizeof(T);
     if (bytes > max_smem) return cudaErrorNotSupported;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_spec_vcycle<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e = smem_attr_once((const void *)k_spec_vcycle<T>, max_smem, attr);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     FusedParams<T> P;
     memset(&P, 0, sizeof P);

@@ -322,13 +322,11 @@ static cudaError_t launch_tc_t(TcArgs a, cudaStream_t s, int nsm, int ctas_per_s
     }
     a.kch = kch;
     const size_t smem = per_chunk * kch;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_axis<KIND, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)TC_SMEM_MAX);
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e =
+            smem_attr_once((const void *)k_tc_axis<KIND, MODE>, (int)TC_SMEM_MAX, attr);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     // CTAs per SM limited so that their TMEM columns fit in 512
     const int tmem_cols = (MODE == 0) ? TC_COLS * a.mh

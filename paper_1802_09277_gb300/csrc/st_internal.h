@@ -5,11 +5,27 @@
 
 #include "dfloat.h"
 
+#include <atomic>
 #include <cstdint>
 
 struct st_handle_s;
 
 namespace st {
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` once per device
+// (the attribute belongs to the function on the current device; bit d of
+// `done` records device d), safe to call from several threads.
+inline cudaError_t smem_attr_once(const void *func, int bytes,
+                                  std::atomic<unsigned long long> &done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 // Allocate the outer iteration's Krylov space now (st_solve would do it on
 // first use); used by the server to account a setup's memory up front.

@@ -297,13 +297,11 @@ static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<
                                     const Grid &g, const TimeCoefs<C> &tc, int slabs_per_prob,
                                     int slab0, int nslabs, cudaStream_t s) {
     using SM = StencilSmem<C, P, DIM>;
-    static bool attr_set = false;  // per device-less process; attribute is per function
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_stencil<T, C, P, DIM, NTC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SM::bytes);
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e =
+            smem_attr_once((const void *)k_stencil<T, C, P, DIM, NTC>, (int)SM::bytes, attr);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const int tx = (g.nx + SM::TX - 1) / SM::TX;
     const int ty = (g.ny + SM::TY - 1) / SM::TY;
