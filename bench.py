@@ -19,6 +19,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -120,10 +121,12 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, path=None):
         self.idx = str(gpu_index)
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%s.csv" % self.idx)
+        self.keep = path is not None
+        self.path = path or os.path.join(tempfile.gettempdir(),
+                                         "st_bench_clocks_%d_%s.csv" % (os.getpid(), self.idx))
 
     def start(self):
         try:
@@ -158,6 +161,11 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+        if not self.keep:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         sm.sort()
@@ -234,7 +242,7 @@ def gpu_arm(args, rank, world):
         sm.load_coeffs(c, f)
     del c
     tuning = sm.autotune()  # also runs inside the first solve (opt.autotune)
-    clocks = ClockSampler(dev.index)
+    clocks = ClockSampler(dev.index, args.clocks_csv)
     clocks.start()
     t_mixed, i_mixed, u_mixed, _ = timed_solves(sm, f, args.steps, args.warmup)
     clk = clocks.stop()
@@ -450,6 +458,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--clocks-csv", default=None,
+                    help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-workers", type=int, default=4)
