@@ -15,6 +15,10 @@ What it computes (Hofer, Langer, Neumueller, arXiv:1802.09277):
   block-Jacobi smoother of Sec. 3.1 with sparse-LU slab solves, a time-only
   V-cycle that merges slab pairs with Galerkin coarse operators, the
   plain multigrid iteration and right-preconditioned FGMRES.
+* ``minres``   -- the inexact spatial solves of Sec. 3.3-3.5: the real Schur
+  form with standardised 2x2 blocks, the symmetric block systems and
+  preconditioners of Theorems 3.2/3.3, preconditioned MinRes, and the slab
+  solve of Eq. 3.1 / Algorithm 1 with MinRes block solves.
 
 Every function is written from the paper's definitions and is deliberately
 slow: no blocking, no fusion, no fast diagonalisation.  Every function is
