@@ -82,6 +82,23 @@ extern "C" {
                                coarsening and the block-Jacobi smoother, and in
                                between every operator is pointwise in the mode */
 
+/* spatial solves K_x + z M_x inside each slab inverse of the B-spline-basis
+ * V-cycle (option spatial_solver) */
+#define ST_SPATIAL_FD     0 /* exact: fast diagonalisation in the generalized
+                               eigenbasis of the 1D matrices (default)       */
+#define ST_SPATIAL_MINRES 1 /* inexact (Sec. 3.5, Theorem 3.3): the real Schur
+                               form's 2x2 blocks are standardised to
+                               [[alpha, beta1], [beta2, alpha]]; Algorithm 1
+                               runs over its diagonal blocks from the last to
+                               the first, every 2x2 block's spatial system
+                               solved by MinRes preconditioned by Theorem
+                               3.3's block-diagonal P (P^{-1} by fast
+                               diagonalisation) to minres_tol, every 1x1
+                               block (SPD, its own preconditioner) by one
+                               application of P^{-1}.  Needs ST_BASIS_NODAL
+                               and ST_RSCHUR; the V-cycle is then inexact, so
+                               pair it with ST_OUTER_FGMRES (flexible)       */
+
 /* outer iteration */
 #define ST_OUTER_FGMRES 0 /* FGMRES(restart), right-preconditioned by one V-cycle */
 #define ST_OUTER_MG     1 /* multigrid iteration u <- u + V(f - L u)             */
@@ -116,6 +133,17 @@ typedef struct {
                              level by level (one launch per step); 1: the whole
                              V-cycle in one shared-memory kernel per block of
                              spatial modes when a mode's levels fit            */
+    int spatial_solver;   /* ST_SPATIAL_FD (default) / ST_SPATIAL_MINRES         */
+    double minres_tol;    /* ST_SPATIAL_MINRES: reduction of ||r||_{P^{-1}} per
+                             block solve (default 1e-4, the inner tolerance of
+                             the paper's multigrid runs, Sec. 4.4)            */
+    int minres_maxit;     /* ST_SPATIAL_MINRES: MinRes steps per block solve;
+                             0 (default) = the count after which the MinRes
+                             bound for cond(P^{-1} A) <= sqrt 2 guarantees
+                             minres_tol, 2 ceil(ln(tol/2) / ln(3 - 2 sqrt 2))
+                             (12 for 1e-4).  Systems that converge earlier
+                             stop updating; the steps always run, so the
+                             smoother replays as one CUDA graph             */
 } st_options;
 
 typedef struct {
@@ -222,6 +250,36 @@ int st_smooth(st_handle h, double *u, const double *f, int nsteps);
 #define ST_STATIC_SCRATCH_BYTES (8 * (2 * ST_STATIC_MAX_DOFS + 3 * (2 * ST_STATIC_MAX_N * 7 + 2 * ST_STATIC_MAX_N * ST_STATIC_MAX_N + ST_STATIC_MAX_N)))
 int st_smooth_static(st_handle h, double *u, const double *f, int nsteps, void *stream);
 
+/* Inexact spatial block solve of Sec. 3.5 (Theorem 3.3) on the handle's
+ * spatial grid, in FP64 whatever the handle's precision: for nsys
+ * independent right-hand sides
+ *   [[K_x + alpha M_x, beta1 M_x], [beta2 M_x, K_x + alpha M_x]] [x; y] = [f; g]
+ * is rescaled to the symmetric indefinite matrix
+ *   Abar = [[|beta2| Kc, -beta1 |beta2| M_x], [|beta1| beta2 M_x, -|beta1| Kc]],
+ *   Kc = K_x + alpha M_x, acting on [x; -y] with right-hand side
+ *   [|beta2| f; |beta1| g], and solved by MinRes preconditioned by
+ *   P = diag(|beta2| (K_x + s M_x), |beta1| (K_x + s M_x)),
+ *   s = alpha + sqrt|beta1 beta2| (cond(P^{-1} Abar) <= sqrt 2), with P^{-1}
+ * applied by fast diagonalisation.  A complex shift alpha + i beta
+ * (Theorem 3.2, Sec. 3.3/3.4) is the case beta1 = -beta, beta2 = beta:
+ * (K_x + (alpha + i beta) M_x)(x + i y) = f + i g.
+ *   alpha > 0, beta1 * beta2 < 0 (a complex pair), else ST_ERR_INVALID_ARG
+ *   f      : device, nsys x 2 x n_x doubles ([sys][f then g][x fastest],
+ *            n_x = spatial dofs), not modified
+ *   u      : device, same layout: x then y of every system (output; must not
+ *            alias f)
+ *   tol    : stop a system once ||r_k||_{P^{-1}} <= tol ||r_0||_{P^{-1}}
+ *            (zero initial guess)
+ *   maxit  : step cap per system (0 = the bound's count for tol, as minres_tol)
+ *   iters, relres : host arrays of nsys (may be NULL): steps taken and the
+ *            final ||r_k||_{P^{-1}} / ||r_0||_{P^{-1}} of each system
+ * 1 <= nsys <= 32767.  Allocates and frees its own work space (9 vectors of
+ * the batch), synchronises the handle's stream, and returns
+ * ST_ERR_NO_CONVERGENCE (u holds the last iterates) when a system stopped at
+ * maxit above tol. */
+int st_block_minres(st_handle h, double alpha, double beta1, double beta2, const double *f,
+                    double *u, int nsys, double tol, int maxit, int *iters, double *relres);
+
 /* One V-cycle on L_h u = f starting from u (in/out), precision as above. */
 int st_vcycle(st_handle h, double *u, const double *f);
 
@@ -253,7 +311,11 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u,
 #define ST_PROF_TC        9  /* spatial transform (one axis), tensor cores    */
 #define ST_PROF_SPEC     10  /* eigenbasis smoothing step / coarse solve      */
 #define ST_PROF_STENCILDF 11 /* refinement residual, double-float on FP64 data */
-#define ST_PROF_NCLASS   12
+#define ST_PROF_MINRES   12  /* MinRes block solves: dots, Lanczos and update
+                                vectors, rotations, preconditioner scaling,
+                                gathers / scatters (its operator applications
+                                and transforms count in their own classes)  */
+#define ST_PROF_NCLASS   13
 int st_profile(st_handle h, int enable);
 int st_profile_read(st_handle h, int cls, int64_t *launches, double *ms,
                     double *bytes, double *flops);

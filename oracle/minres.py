@@ -223,3 +223,19 @@ def minres_bound_iterations(tol, kappa=np.sqrt(2.0)):
     is at most tol (the two-interval Chebyshev bound)."""
     q = (kappa - 1.0) / (kappa + 1.0)
     return 2 * int(np.ceil(np.log(tol / 2.0) / np.log(q)))
+
+
+def jacobi_step_minres(prob, u, f, omega=0.5, tol=1e-4):
+    """One damped block-Jacobi step of Sec. 3.1, u + omega D^{-1} (f - L u),
+    with every slab inverse applied by ``slab_solve_minres`` (inexact, the
+    smoother of the paper's multigrid runs with MinRes block solves).
+    Returns (new u, max MinRes iterations over the slabs)."""
+    L = assemble.assemble_L(prob)
+    r = (np.asarray(f, float) - L @ u).reshape(prob.N, -1)
+    out = np.array(u, dtype=float).reshape(prob.N, -1).copy()
+    itmax = 0
+    for n in range(prob.N):
+        z, it = slab_solve_minres(prob, r[n], tol=tol)
+        out[n] += omega * z
+        itmax = max(itmax, it)
+    return out.reshape(-1), itmax

@@ -508,6 +508,21 @@ bool real_schur(int n, const Mat &A, Mat &Q, Mat &T, std::vector<int> &blk, std:
     return true;
 }
 
+void standardize_schur(int n, Mat &Q, Mat &T, const std::vector<int> &blk) {
+    for (int k = 0; k + 1 < n; ++k) {
+        if (!blk[k + 1]) continue;
+        const double a = T[k * n + k], b = T[k * n + k + 1];
+        const double c = T[(k + 1) * n + k], d = T[(k + 1) * n + k + 1];
+        const double t = 0.5 * std::atan2(d - a, b + c);
+        rotate(n, T, Q, k, std::cos(t), std::sin(t));
+        const double al = 0.5 * (T[k * n + k] + T[(k + 1) * n + k + 1]);
+        T[k * n + k] = T[(k + 1) * n + k + 1] = al;
+        // rows below the block stay zero up to rounding of the rotation
+        for (int i = k + 2; i < n; ++i) T[i * n + k] = T[i * n + k + 1] = 0.0;
+        ++k;
+    }
+}
+
 using cd = std::complex<double>;
 
 bool schur_eigvecs(int n, const Mat &Q, const Mat &T, const std::vector<int> &blk,

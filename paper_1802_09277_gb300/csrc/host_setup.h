@@ -56,6 +56,12 @@ bool sym_gen_eig(int n, const Mat &K, const Mat &M, Mat &U, std::vector<double> 
 // second row of a 2x2 block, else 0.
 bool real_schur(int n, const Mat &A, Mat &Q, Mat &T, std::vector<int> &blk, std::string &err);
 
+// Rotate every 2x2 block of a real Schur form (Q, T) to the standard form
+// [[alpha, beta1], [beta2, alpha]] (Sec. 3.5): T <- G^T T G, Q <- Q G with G
+// the rotation by t = atan2(d - a, b + c) / 2 for the block [[a, b], [c, d]]
+// (the diagonal difference of G^T B G is cos 2t (a - d) + sin 2t (b + c)).
+void standardize_schur(int n, Mat &Q, Mat &T, const std::vector<int> &blk);
+
 // Eigen-decomposition A X = X diag(lam) from the real Schur form A = Q T Q^T
 // (blk as returned by real_schur): eigenvectors of T by back substitution
 // (complex for the 2x2 blocks), X = Q V, columns scaled to unit 2-norm.

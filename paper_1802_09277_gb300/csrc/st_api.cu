@@ -79,6 +79,21 @@ struct Work {  // multigrid vectors in the V-cycle precision
     T *w0 = nullptr, *w1 = nullptr;
 };
 
+// Work space of the MinRes block solves (ST_SPATIAL_MINRES): compact batches
+// [sys][comp][n_x] of up to `cap` systems with two components, the slab
+// solution of Algorithm 1 (nt planes per slab), chunk partials and states.
+template <typename T>
+struct MrWork {
+    T *q = nullptr, *qp = nullptr, *t = nullptr, *p = nullptr;  // Lanczos vectors
+    T *d1 = nullptr, *d2 = nullptr, *x = nullptr;                // directions, iterate
+    T *z0 = nullptr, *z1 = nullptr;                              // preconditioner ping-pong
+    T *zs = nullptr;                                             // slab-layout solution
+    double *partA = nullptr, *partB = nullptr;
+    MrState *st = nullptr;
+    int *count = nullptr;
+    long long cap = 0;  // systems
+};
+
 }  // namespace
 
 struct st_handle_s {
@@ -117,6 +132,8 @@ struct st_handle_s {
     DevSpace<float> s32;
     Work<double> w64;
     Work<float> w32;
+    MrWork<double> mr64;
+    MrWork<float> mr32;
     // per-kernel-class profiling (CUDA events around each launch)
     struct ProfRec {
         int cls;
@@ -538,10 +555,256 @@ int autotune(st_handle h) {
     return ST_OK;
 }
 
+// ---- inexact spatial solves (ST_SPATIAL_MINRES, Sec. 3.5) ---------------------
+template <typename T>
+MrWork<T> &mrwork(st_handle h);
+template <>
+MrWork<double> &mrwork<double>(st_handle h) { return h->mr64; }
+template <>
+MrWork<float> &mrwork<float>(st_handle h) { return h->mr32; }
+
+// Steps after which the MinRes bound 2 q^floor(k/2), q = (sqrt2 - 1)/(sqrt2 + 1),
+// for a spectrum of P^{-1} A inside [-1, -1/sqrt2] u [1/sqrt2, 1]
+// (Theorems 3.2/3.3) falls to tol.
+int minres_bound_steps(double tol) {
+    const double q = 3.0 - 2.0 * std::sqrt(2.0);
+    return 2 * (int)std::ceil(std::log(tol / 2.0) / std::log(q));
+}
+
+// Nine batch vectors of cap systems with two components, the slab-layout
+// solution, partials and states, by `alloc` (the handle's budgeted
+// allocator, or plain device memory for a one-off solve).
+template <typename T, typename Alloc>
+int alloc_mr(st_handle h, MrWork<T> &w, long long cap, bool with_slabs, Alloc alloc) {
+    const size_t e = (size_t)cap * 2 * h->g.nxyz;
+    void *p;
+    T **vecs[9] = {&w.q, &w.qp, &w.t, &w.p, &w.d1, &w.d2, &w.x, &w.z0, &w.z1};
+    for (T **v : vecs) {
+        CKS(alloc(e * sizeof(T), &p));
+        *v = (T *)p;
+    }
+    if (with_slabs) {
+        CKS(alloc((size_t)cap * h->nt * h->g.nxyz * sizeof(T), &p));
+        w.zs = (T *)p;
+    }
+    CKS(alloc(sizeof(double) * cap * MR_MAX_CHUNKS, &p));
+    w.partA = (double *)p;
+    CKS(alloc(sizeof(double) * cap * MR_MAX_CHUNKS, &p));
+    w.partB = (double *)p;
+    CKS(alloc(sizeof(MrState) * cap, &p));
+    w.st = (MrState *)p;
+    CKS(alloc(sizeof(int), &p));
+    w.count = (int *)p;
+    w.cap = cap;
+    return ST_OK;
+}
+
+// z = P^{-1} in for nsys systems of c components, P = diag(pw_c (K_x + shift M_x)):
+// forward spatial transforms, the eigenbasis scaling, inverse transforms
+// (FP32-accurate transforms in the mixed modes, so that P^{-1} stays
+// symmetric to working precision).  *res is the buffer holding z (z0 or z1).
+template <typename T>
+int precond_fd(st_handle h, const T *in, T *z0, T *z1, T **res, int nsys, int c, double shift,
+               double pw0, double pw1) {
+    const long long planes = (long long)nsys * c;
+    T *fw = nullptr;
+    CKS(spatial<T>(h, in, z0, z1, true, planes, &fw, true));
+    {
+        const double E = (double)planes * h->g.nxyz;
+        KScope ks(h, ST_PROF_MINRES, sizeof(T) * (2.0 * E + h->g.nxyz), 2.0 * E);
+        CK(launch_fd_scale<T>(fw, space<T>(h).mu, shift, pw0, pw1, c, h->g.nxyz, nsys, h->stream));
+    }
+    T *other = (fw == z0) ? z1 : z0;
+    CKS(spatial<T>(h, fw, other, fw, false, planes, res, true));
+    return ST_OK;
+}
+
+// Algorithmic bytes and flops of one sum-factorised operator application on
+// `planes` spatial planes without coupling plane (ntp planes per system).
+inline void op_counts(st_handle h, double planes, int ntp, int tsize, double *bytes,
+                      double *flops) {
+    const int W = 2 * h->p + 1;
+    const double fsp = 4.0 * W + (h->dim >= 2 ? 6.0 * W : 0) + (h->dim >= 3 ? 6.0 * W : 0);
+    const double E = planes * h->g.nxyz;
+    *bytes = tsize * 2.0 * E;
+    *flops = E * fsp + E * 4.0 * ntp;
+}
+
+struct BlockCoef {
+    double alpha, beta1, beta2;  // the standardised block [[alpha, beta1], [beta2, alpha]]
+};
+
+// Preconditioned MinRes (Theorem 3.3) on nsys systems whose scaled
+// right-hand sides [|beta2| f; |beta1| g] are in w.q (zero initial guess);
+// the iterate [x; -y] is in w.x on return.  `steps` MinRes steps run, a
+// system that has converged stops updating; early: after every step read
+// the number of running systems and stop when none is left (never during a
+// stream capture).
+template <typename T>
+int block_minres(st_handle h, MrWork<T> &w, const BlockCoef &bc, int nsys, double tol, int steps,
+                 bool early) {
+    const long long m = h->g.nxyz, len = 2 * m;
+    const int chunks = mr_dot_chunks(len);
+    const double a1 = std::fabs(bc.beta2), a2 = std::fabs(bc.beta1);
+    const double shift = bc.alpha + std::sqrt(a1 * a2);
+    const cudaStream_t s = h->stream;
+    const double E = (double)nsys * len;
+    // Abar as a two-plane operator: y_i = sum_j CK[i][j] M_x u_j + CM[i][j] K_x u_j
+    TimeCoefs<T> tc;
+    std::memset(&tc, 0, sizeof tc);
+    tc.CK[0] = (T)(a1 * bc.alpha);
+    tc.CK[1] = (T)(-bc.beta1 * a1);
+    tc.CK[NTMAX] = (T)(a2 * bc.beta2);
+    tc.CK[NTMAX + 1] = (T)(-a2 * bc.alpha);
+    tc.CM[0] = (T)a1;
+    tc.CM[NTMAX + 1] = (T)(-a2);
+    tc.nt = 2;
+    tc.fuse_y = 0;
+    tc.mode = MODE_APPLY;
+    double ob, of;
+    op_counts(h, 2.0 * nsys, 2, sizeof(T), &ob, &of);
+    T *z = nullptr;
+    CKS(precond_fd<T>(h, w.q, w.z0, w.z1, &z, nsys, 2, shift, a1, a2));
+    {
+        KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * E, 2.0 * E);
+        CK(launch_seg_dot<T>(w.q, z, w.partB, len, nsys, s));
+    }
+    {
+        KScope ks(h, ST_PROF_MINRES, 8.0 * chunks * nsys, 0.0);
+        CK(launch_mr_init(w.partB, chunks, w.st, nsys, s));
+    }
+    {
+        KScope ks(h, ST_PROF_MINRES, sizeof(T) * 8.0 * E, 2.0 * E);
+        CK(launch_mr_init_vec<T>(w.q, w.p, z, w.qp, w.d1, w.d2, w.x, w.st, len, nsys, s));
+    }
+    T *q = w.q, *qp = w.qp, *t = w.t, *d1 = w.d1, *d2 = w.d2;
+    for (int k = 0; k < steps; ++k) {
+        {
+            KScope ks(h, cls_of<T>(ST_PROF_STENCIL64, ST_PROF_STENCIL32), ob, of);
+            CK(launch_stencil<T>(w.p, nullptr, t, space<T>(h).bands, h->g, tc, 1, 0, nsys, s));
+        }
+        {
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * E, 2.0 * E);
+            CK(launch_seg_dot<T>(w.p, t, w.partA, len, nsys, s));
+        }
+        {
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 4.0 * E, 4.0 * E);
+            CK(launch_mr_lanczos<T>(t, q, qp, w.partA, chunks, w.st, len, nsys, s));
+        }
+        CKS(precond_fd<T>(h, t, w.z0, w.z1, &z, nsys, 2, shift, a1, a2));
+        {
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * E, 2.0 * E);
+            CK(launch_seg_dot<T>(t, z, w.partB, len, nsys, s));
+        }
+        {
+            KScope ks(h, ST_PROF_MINRES, 16.0 * chunks * nsys, 20.0 * nsys);
+            CK(launch_mr_givens(w.partA, w.partB, chunks, w.st, tol, nsys, s));
+        }
+        {
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 10.0 * E, 8.0 * E);
+            CK(launch_mr_update<T>(w.p, z, t, d1, d2, w.x, w.st, len, nsys, s));
+        }
+        // the new direction is in d2; q_{k+1} is in t
+        std::swap(d1, d2);
+        T *free_q = qp;
+        qp = q;
+        q = t;
+        t = free_q;
+        if (early) {
+            int left = 0;
+            CK(launch_mr_count(w.st, nsys, w.count, s));
+            CK(cudaMemcpyAsync(&left, w.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (left == 0) break;
+        }
+    }
+    return ST_OK;
+}
+
+// Damped block-Jacobi step on slabs [s0, s0+ns) of level l with the inexact
+// spatial solves of Sec. 3.5: w = (Y (x) I)(f - L u) (fused into the
+// residual); Algorithm 1 on (Z (x) M_x + I (x) K_x) z = w over the
+// standardised real Schur form Z, from the last diagonal block to the
+// first: g_B = w_B - sum over the solved blocks j of Z_Bj M_x z_j (one
+// operator application with those entries of Z), then a 1x1 block by one
+// application of (K_x + Z_bb M_x)^{-1}, a 2x2 block by MinRes; finally
+// u <- (overwrite ? 0 : u) + omega (X (x) I) z.
+template <typename T>
+int smooth_range_minres(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns,
+                        int overwrite) {
+    Work<T> &w = work<T>(h);
+    MrWork<T> &mw = mrwork<T>(h);
+    if (ns > mw.cap)
+        return fail(ST_ERR_INVALID_ARG, "MinRes batch of %d slabs exceeds its work space (%lld)",
+                    ns, mw.cap);
+    const int nt = h->nt;
+    const long long m = h->g.nxyz, sl = (long long)nt * m;
+    const LevelHost &L = h->lv[l];
+    const cudaStream_t s = h->stream;
+    const double tol = h->opt.minres_tol;
+    const int steps = h->opt.minres_maxit > 0 ? h->opt.minres_maxit : minres_bound_steps(tol);
+    CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, true, s0, ns));
+    T *W = w.w0 + s0 * sl, *G = w.w1 + s0 * sl, *Zs = mw.zs;
+    {
+        KScope ks(h, ST_PROF_MINRES, sizeof(T) * (double)ns * sl, 0.0);
+        CK(launch_zero<T>(Zs, ns * sl, s));
+    }
+    double ob, of;
+    op_counts(h, (double)ns * nt, nt, sizeof(T), &ob, &of);
+    bool first = true;
+    for (int i = nt - 1; i >= 0;) {
+        const int c = (i >= 1 && L.blk[i]) ? 2 : 1;
+        const int b = i - c + 1;
+        const T *src = W;
+        if (!first) {
+            TimeCoefs<T> tc;
+            std::memset(&tc, 0, sizeof tc);
+            for (int r = b; r < b + c; ++r)
+                for (int j = b + c; j < nt; ++j) tc.CK[r * NTMAX + j] = (T)L.Z[r * nt + j];
+            tc.nt = nt;
+            tc.fuse_y = 0;
+            tc.mode = MODE_RES;
+            KScope ks(h, cls_of<T>(ST_PROF_STENCIL64, ST_PROF_STENCIL32), ob * 1.5, of);
+            CK(launch_stencil<T>(Zs, W, G, space<T>(h).bands, h->g, tc, 1, 0, ns, s));
+            src = G;
+        }
+        first = false;
+        const double Eb = (double)ns * c * m;
+        if (c == 1) {
+            {
+                KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+                CK(launch_mr_gather<T>(src, mw.q, b, 1, nt, m, 1.0, 1.0, ns, s));
+            }
+            T *z = nullptr;
+            CKS(precond_fd<T>(h, mw.q, mw.z0, mw.z1, &z, ns, 1, L.Z[b * nt + b], 1.0, 1.0));
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+            CK(launch_mr_scatter<T>(z, Zs, b, 1, nt, m, 1.0, 1.0, ns, s));
+        } else {
+            const BlockCoef bc{L.Z[b * nt + b], L.Z[b * nt + b + 1], L.Z[(b + 1) * nt + b]};
+            {
+                KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+                CK(launch_mr_gather<T>(src, mw.q, b, 2, nt, m, std::fabs(bc.beta2),
+                                       std::fabs(bc.beta1), ns, s));
+            }
+            CKS(block_minres<T>(h, mw, bc, ns, tol, steps, false));
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+            CK(launch_mr_scatter<T>(mw.x, Zs, b, 2, nt, m, 1.0, -1.0, ns, s));
+        }
+        i = b - 1;
+    }
+    const SchurCoefs<T> sc = pack_schur<T>(h, l);
+    const double E = (double)ns * sl;
+    KScope ks(h, ST_PROF_UPDATE, sizeof(T) * (overwrite ? 2.0 : 3.0) * E, E * (2.0 * nt + 2.0));
+    CK(launch_update<T>(u + s0 * sl, Zs, sc, omega, h->g, ns, overwrite, s));
+    return ST_OK;
+}
+
 // Damped block-Jacobi step on slabs [s0, s0+ns) of level l:
 // u <- (overwrite ? 0 : u) + omega A^{-1} (f - L u)  (A^{-1} by Eq. 3.1 + FD)
 template <typename T>
 int smooth_range(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns, int overwrite) {
+    if (h->opt.spatial_solver == ST_SPATIAL_MINRES)
+        return smooth_range_minres<T>(h, l, u, f, omega, s0, ns, overwrite);
     Work<T> &w = work<T>(h);
     DevSpace<T> &ds = space<T>(h);
     const long long sl = (long long)h->nt * h->g.nxyz;  // elements per slab
@@ -1523,6 +1786,17 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         return fail(ST_ERR_INVALID_ARG, "bad outer iteration");
     if (!(o.inner_tol > 0) || o.inner_tol >= 1)
         return fail(ST_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
+    if (o.spatial_solver != ST_SPATIAL_FD && o.spatial_solver != ST_SPATIAL_MINRES)
+        return fail(ST_ERR_INVALID_ARG, "bad spatial_solver");
+    if (o.spatial_solver == ST_SPATIAL_MINRES) {
+        if (o.basis != ST_BASIS_NODAL || o.variant != ST_RSCHUR)
+            return fail(ST_ERR_UNSUPPORTED, "MinRes spatial solves are built for the B-spline "
+                        "basis with the real Schur variant");
+        if (!(o.minres_tol > 0) || o.minres_tol >= 1 || o.minres_maxit < 0 || o.minres_maxit > 1000)
+            return fail(ST_ERR_INVALID_ARG, "minres_tol must be in (0, 1), minres_maxit in [0, 1000]");
+        if ((long long)slabs * o.nrhs > 32767)
+            return fail(ST_ERR_UNSUPPORTED, "MinRes spatial solves take at most 32767 slabs x rhs");
+    }
     h->dim = geometry;
     h->p = degree;
     h->N = slabs;
@@ -1592,6 +1866,8 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         std::string err;
         if (!host::real_schur(nt, G, L.X, L.Z, L.blk, err))
             return fail(ST_ERR_ILL_CONDITIONED, "real Schur: %s", err.c_str());
+        // MinRes block solves need the standard 2x2 blocks of Sec. 3.5
+        if (o.spatial_solver == ST_SPATIAL_MINRES) host::standardize_schur(nt, L.X, L.Z, L.blk);
         // Re lambda > 0 check (Sec. 3.2: a posteriori control of positivity)
         for (int i = 0; i < nt; ++i) {
             double re;
@@ -1689,6 +1965,12 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     } else {
         CKS(alloc_work<double>(h, h->w64, true));
     }
+    if (o.spatial_solver == ST_SPATIAL_MINRES) {
+        auto budgeted = [h](size_t b, void **p) { return dalloc(h, b, p); };
+        const long long cap = (long long)slabs * o.nrhs;
+        CKS(h->mixed ? alloc_mr<float>(h, h->mr32, cap, true, budgeted)
+                     : alloc_mr<double>(h, h->mr64, cap, true, budgeted));
+    }
     {
         int dev = 0, ms = 0;
         CK(cudaGetDevice(&dev));
@@ -1784,6 +2066,9 @@ void st_options_default(st_options *o) {
     o->variant = ST_RSCHUR;
     o->autotune = 1;
     o->fused_vcycle = 0;
+    o->spatial_solver = ST_SPATIAL_FD;
+    o->minres_tol = 1e-4;
+    o->minres_maxit = 0;
 }
 
 const char *st_last_error(void) { return g_err.c_str(); }
@@ -1931,6 +2216,56 @@ int st_smooth(st_handle h, double *u, const double *f, int nsteps) {
     for (int k = 0; k < nsteps; ++k)
         CKS(smooth<float>(h, 0, h->w32.u[0], h->w32.f[0], (float)h->opt.omega));
     CK(launch_convert<float, double>(h->w32.u[0], u, n0, h->stream));
+    return ST_OK;
+}
+
+int st_block_minres(st_handle h, double alpha, double beta1, double beta2, const double *f,
+                    double *u, int nsys, double tol, int maxit, int *iters, double *relres) {
+    CKS(check_ptr(h, f, "f"));
+    CKS(check_ptr(h, u, "u"));
+    if ((const void *)f == (const void *)u) return fail(ST_ERR_INVALID_ARG, "f and u alias");
+    if (nsys < 1 || nsys > 32767) return fail(ST_ERR_INVALID_ARG, "nsys must be in [1, 32767]");
+    if (!(alpha > 0) || !(beta1 * beta2 < 0))
+        return fail(ST_ERR_INVALID_ARG, "need alpha > 0 and beta1 * beta2 < 0 (a complex pair)");
+    if (!(tol > 0) || tol >= 1 || maxit < 0 || maxit > 100000)
+        return fail(ST_ERR_INVALID_ARG, "tol must be in (0, 1), maxit in [0, 100000]");
+    const int steps = maxit > 0 ? maxit : minres_bound_steps(tol);
+    // one-off work space in plain device memory, released on every return
+    struct Tmp {
+        std::vector<void *> p;
+        ~Tmp() {
+            for (void *q : p) cudaFree(q);
+        }
+    } tmp;
+    auto plain = [&tmp](size_t b, void **out) {
+        void *q = nullptr;
+        const cudaError_t e = cudaMalloc(&q, b ? b : 16);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ST_ERR_OOM, "cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+        }
+        tmp.p.push_back(q);
+        *out = q;
+        return ST_OK;
+    };
+    MrWork<double> w;
+    CKS(alloc_mr<double>(h, w, nsys, false, plain));
+    const long long m = h->g.nxyz;
+    const BlockCoef bc{alpha, beta1, beta2};
+    CK(launch_mr_gather<double>(f, w.q, 0, 2, 2, m, std::fabs(beta2), std::fabs(beta1), nsys,
+                                h->stream));
+    CKS(block_minres<double>(h, w, bc, nsys, tol, steps, true));
+    CK(launch_mr_scatter<double>(w.x, u, 0, 2, 2, m, 1.0, -1.0, nsys, h->stream));
+    std::vector<MrState> hs(nsys);
+    CK(cudaMemcpyAsync(hs.data(), w.st, sizeof(MrState) * nsys, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    bool ok = true;
+    for (int i = 0; i < nsys; ++i) {
+        if (iters) iters[i] = hs[i].iters;
+        if (relres) relres[i] = hs[i].relres;
+        if (!(hs[i].relres <= tol)) ok = false;
+    }
+    if (!ok) return fail(ST_ERR_NO_CONVERGENCE, "MinRes stopped at %d steps above tol %.3e", steps, tol);
     return ST_OK;
 }
 

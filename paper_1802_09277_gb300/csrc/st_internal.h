@@ -244,4 +244,49 @@ cudaError_t launch_scale(const double *x, double *y, const double *a, int nrhs, 
 template <typename T>
 cudaError_t launch_zero(T *x, long long n, cudaStream_t s);
 
+// ---- preconditioned MinRes on spatial block systems (kernels_minres.cu) ----
+// Per-system scalars of the iteration (one thread per system updates them).
+struct MrState {
+    double beta1;           // ||r_0||_{P^{-1}}
+    double eta;             // signed ||r_k||_{P^{-1}} of the QR recurrence
+    double bk;              // beta_k of the Lanczos process
+    double c1, s1, c2, s2;  // rotations k-1 and k-2
+    double cd, cdel, ceps, cx;  // this step: 1/rho, delta, eps, c * eta_{k-1}
+    double invb;            // 1 / beta_{k+1} (0 once the system stopped)
+    double relres;          // ||r_k||_{P^{-1}} / ||r_0||_{P^{-1}}
+    int active;             // still iterating
+    int upd;                // this step updates the iterate
+    int iters;              // steps taken
+    int pad;
+};
+constexpr int MR_MAX_CHUNKS = 32;
+// CTAs per system of the dot kernel for a system of len elements
+int mr_dot_chunks(long long len);
+template <typename T>
+cudaError_t launch_seg_dot(const T *a, const T *b, double *part, long long len, int nsys,
+                           cudaStream_t s);
+cudaError_t launch_mr_init(const double *partB, int chunks, MrState *st, int nsys, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mr_init_vec(T *q, T *p, const T *z, T *qp, T *d1, T *d2, T *x,
+                               const MrState *st, long long len, int nsys, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mr_lanczos(T *t, const T *q, const T *qp, const double *partA, int chunks,
+                              const MrState *st, long long len, int nsys, cudaStream_t s);
+cudaError_t launch_mr_givens(const double *partA, const double *partB, int chunks, MrState *st,
+                             double tol, int nsys, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mr_update(T *p, const T *z, T *t, const T *d1, T *d2, T *x, const MrState *st,
+                             long long len, int nsys, cudaStream_t s);
+// w[sys][comp][k] /= pw_comp (mu_k + shift)  (pw (K_x + shift M_x) inverted in the eigenbasis)
+template <typename T>
+cudaError_t launch_fd_scale(T *w, const T *mu, double shift, double pw0, double pw1, int c,
+                            long long m, int nsys, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mr_gather(const T *src, T *dst, int row0, int c, int nt, long long m, double sc0,
+                             double sc1, int nsys, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mr_scatter(const T *src, T *dst, int row0, int c, int nt, long long m,
+                              double sg0, double sg1, int nsys, cudaStream_t s);
+cudaError_t launch_mr_count(const MrState *st, int nsys, int *count, cudaStream_t s);
+
 }  // namespace st

@@ -15,21 +15,25 @@ ST_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NOT_POSITIVE", -4: "ILL_CONDITIONED",
           -5: "NO_CONVERGENCE", -6: "TIMEOUT", -7: "CUDA", -8: "OVER_BUDGET",
           -9: "UNSUPPORTED"}
+ST_ERR_INVALID_ARG = -1
+ST_ERR_NO_CONVERGENCE = -5
+ST_ERR_UNSUPPORTED = -9
 GEOMETRY = {1: 1, 2: 2, 3: 3}
 PRECISION = {"fp64": 0, "mixed_fp32": 1, "mixed_tf32": 2, "mixed_bf16": 3}
 OUTER = {"fgmres": 0, "mg": 1, "ir": 2}
 BASIS = {"nodal": 0, "spectral": 1}
 VARIANT = {"rschur": 0, "eig": 1, "cschur": 2}
+SPATIAL = {"fd": 0, "minres": 1}
 
 # every symbol declared in include/st_iga.h
 SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",
            "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_load_gaussians", "st_smooth",
-           "st_smooth_static", "st_vcycle",
+           "st_smooth_static", "st_block_minres", "st_vcycle",
            "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
            "st_time_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_poll", "st_serve_wait", "st_serve_stop"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
-                "vector", "dot", "tc", "spec", "stencil_df"]
+                "vector", "dot", "tc", "spec", "stencil_df", "minres"]
 
 
 class StOptions(ctypes.Structure):
@@ -40,7 +44,8 @@ class StOptions(ctypes.Structure):
                 ("nrhs", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("basis", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("use_graphs", ctypes.c_int),
                 ("variant", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("fused_vcycle", ctypes.c_int)]
+                ("fused_vcycle", ctypes.c_int), ("spatial_solver", ctypes.c_int),
+                ("minres_tol", ctypes.c_double), ("minres_maxit", ctypes.c_int)]
 
 
 class StSolveInfo(ctypes.Structure):
@@ -106,6 +111,7 @@ def load():
         "st_load_gaussians": (I, [P, I, dp, dp, dp, P]),
         "st_smooth": (I, [P, P, P, I]),
         "st_smooth_static": (I, [P, P, P, I, P]),
+        "st_block_minres": (I, [P, D, D, D, P, P, I, D, I, ip, dp]),
         "st_vcycle": (I, [P, P, P]),
         "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
         "st_autotune": (I, [P, ip, dp]),
@@ -151,6 +157,8 @@ def options(**kw):
             v = BASIS[v]
         if k == "variant" and isinstance(v, str):
             v = VARIANT[v]
+        if k == "spatial_solver" and isinstance(v, str):
+            v = SPATIAL[v]
         setattr(o, k, v)
     return o
 
@@ -243,6 +251,25 @@ class Solver:
         _check(_lib.st_smooth_static(self._h, _dptr(u, self.ndofs, "u"),
                                      _dptr(f, self.ndofs, "f"), int(nsteps),
                                      ctypes.c_void_p(stream)))
+
+    def block_minres(self, alpha, beta1, beta2, f, u, tol=1e-10, maxit=0, check=True):
+        """MinRes on nsys spatial 2x2 block systems (Theorem 3.3; a complex
+        shift alpha + i beta is beta1 = -beta, beta2 = beta).  f, u: float64
+        CUDA tensors of nsys * 2 * n_x elements ([sys][f, g][space]).
+        Returns (iterations, relative P^{-1}-residuals, return code) per system."""
+        import numpy as np
+        m = int(np.prod(self.nx))
+        nsys = f.numel() // (2 * m)
+        if nsys * 2 * m != f.numel() or nsys < 1:
+            raise ValueError("f must hold nsys * 2 * n_x elements")
+        its = (ctypes.c_int * nsys)()
+        rel = (ctypes.c_double * nsys)()
+        rc = _lib.st_block_minres(self._h, float(alpha), float(beta1), float(beta2),
+                                  _dptr(f, nsys * 2 * m, "f"), _dptr(u, nsys * 2 * m, "u"),
+                                  int(nsys), float(tol), int(maxit), its, rel)
+        if check:
+            _check(rc)
+        return np.array(its[:]), np.array(rel[:]), rc
 
     def vcycle(self, u, f):
         _check(_lib.st_vcycle(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f")))

@@ -193,3 +193,53 @@ def test_complex_schur_variant_setup(st, p, theta, ne):
         for v in ref:
             assert np.min(np.abs(lam - v)) <= 1e-9 * max(1.0, abs(v))
     s.close()
+
+
+@pytest.mark.parametrize("p,theta,ne", [(2, 1.0, 2), (3, 0.1, 4), (1, 0.1, 4)])
+def test_minres_standardised_schur_factors(st, p, theta, ne):
+    """ST_SPATIAL_MINRES: the real Schur form's 2x2 blocks are rotated to
+    [[alpha, beta1], [beta2, alpha]] (Sec. 3.5) with alpha > 0 and
+    beta1 beta2 < 0; X stays orthogonal, K_t X = M_t X Z, Y M_t X = I, and
+    the blocks carry the generalized eigenvalues (scipy) on every level."""
+    s = st.Solver(2, p, (6, 5), 8, host_only=True, ne_per_slab=ne, theta=theta,
+                  spatial_solver="minres")
+    for lvl in range(s.nlevels):
+        tf = s.time_factors(lvl)
+        Kt, Mt, X, Z, Y = tf["Kt"], tf["Mt"], tf["X"], tf["Z"], tf["Y"]
+        n = Kt.shape[0]
+        assert np.allclose(X.T @ X, np.eye(n), atol=1e-12)
+        assert np.allclose(Kt @ X, Mt @ X @ Z, atol=1e-10 * np.abs(Kt).max())
+        assert np.allclose(Y @ Mt @ X, np.eye(n), atol=1e-10)
+        lam = sl.eigvals(Kt, Mt)
+        i, npairs = 0, 0
+        while i < n:
+            if i + 1 < n and Z[i + 1, i] != 0.0:
+                a, b1, b2 = Z[i, i], Z[i, i + 1], Z[i + 1, i]
+                assert Z[i + 1, i + 1] == a and a > 0 and b1 * b2 < 0
+                assert np.all(Z[i + 2:, i:i + 2] == 0.0)
+                w = np.sqrt(abs(b1 * b2))
+                assert np.min(np.abs(lam - (a + 1j * w))) <= 1e-9 * abs(a + 1j * w)
+                npairs += 1
+                i += 2
+            else:
+                assert np.min(np.abs(lam - Z[i, i])) <= 1e-9 * abs(Z[i, i])
+                i += 1
+        assert npairs >= 1
+    s.close()
+
+
+def test_minres_option_errors(st):
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 2, (6, 6), 4, host_only=True, spatial_solver="minres", basis="spectral")
+    assert e.value.code == st.ST_ERR_UNSUPPORTED
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 2, (6, 6), 4, host_only=True, spatial_solver="minres", variant="eig")
+    assert e.value.code == st.ST_ERR_UNSUPPORTED
+    for kw in [dict(minres_tol=0.0), dict(minres_tol=1.0), dict(minres_maxit=-2)]:
+        with pytest.raises(st.StError) as e:
+            st.Solver(2, 2, (6, 6), 4, host_only=True, spatial_solver="minres", **kw)
+        assert e.value.code == st.ST_ERR_INVALID_ARG
+    with pytest.raises(st.StError):
+        st.Solver(2, 2, (6, 6), 4, host_only=True, spatial_solver=7)
+    # the FD default ignores the MinRes fields
+    st.Solver(2, 2, (6, 6), 4, host_only=True, minres_tol=0.0).close()

@@ -305,3 +305,21 @@ def test_slab_solve_minres_inexact_error_scales_with_tolerance():
         errs.append(np.linalg.norm(got - exact) / np.linalg.norm(exact))
     assert errs[0] > errs[1] > errs[2]
     assert errs[1] <= 1e-2 and errs[2] <= 1e-4
+
+
+def test_jacobi_step_minres_tight_tolerance_is_exact_step():
+    """With a tight inner tolerance the inexact smoother is the exact damped
+    block-Jacobi step of Sec. 3.1 (sparse-LU slab solves)."""
+    from oracle import solve as S
+    prob = A.Problem(2, (8, 6), 3, 2, 5, theta=1.0)
+    L = A.assemble_L(prob)
+    lev = S.Level(L, prob.N, prob.Nt * prob.Nx)
+    rng = np.random.default_rng(12)
+    u0, f = rng.standard_normal(prob.ndofs), rng.standard_normal(prob.ndofs)
+    ref = S.jacobi_step(lev, u0, f, 0.5)
+    got, it = MR.jacobi_step_minres(prob, u0, f, 0.5, tol=1e-13)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    got4, it4 = MR.jacobi_step_minres(prob, u0, f, 0.5, tol=1e-4)
+    err = np.abs(got4 - ref).max() / np.abs(ref).max()
+    assert 1e-8 < err < 1e-3
+    assert it4 <= MR.minres_bound_iterations(1e-4) < it
