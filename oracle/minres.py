@@ -28,6 +28,11 @@ common factor |beta|.  The systems are solved by MinRes preconditioned by P.
   block back substitution of Algorithm 1 over the real Schur form (each
   block's spatial system by MinRes, the 1x1 blocks, which are SPD with P
   equal to the matrix itself, by one solve with P), time transform X.
+* ``complex_factors``, ``slab_solve_minres_complex`` -- the same with the
+  diagonalisation (Sec. 3.3) or the complex Schur form (Sec. 3.4): complex
+  time transforms, complex shifts solved in Theorem 3.2's form.
+* ``jacobi_step_minres``   -- the damped block-Jacobi step with these slab
+  solves.
 
 P is applied here by a sparse LU of K_x + s M_x; the tolerance is a reduction
 of the P^{-1}-norm of the residual, the quantity MinRes minimises.
@@ -225,17 +230,71 @@ def minres_bound_iterations(tol, kappa=np.sqrt(2.0)):
     return 2 * int(np.ceil(np.log(tol / 2.0) / np.log(q)))
 
 
-def jacobi_step_minres(prob, u, f, omega=0.5, tol=1e-4):
+def complex_factors(Kt, Mt, variant):
+    """Complex factors of Eq. 3.1, K_t X = M_t X T, Y = (M_t X)^{-1}:
+    variant "eig" (Sec. 3.3): T = diag(lambda), X the eigenvectors of the
+    pencil (K_t, M_t); variant "cschur" (Sec. 3.4): the complex Schur form
+    M_t^{-1} K_t = Q T Q^H, X = Q unitary, T upper triangular."""
+    if variant == "eig":
+        lam, X = sla.eig(Kt, Mt)
+        T = np.diag(lam)
+    elif variant == "cschur":
+        T, X = sla.schur(np.linalg.solve(Mt, Kt).astype(complex), output="complex")
+    else:
+        raise ValueError(variant)
+    Y = np.linalg.inv(Mt @ X)
+    return T, X, Y
+
+
+def slab_solve_minres_complex(prob, r, variant, tol=1e-4, maxit=500):
+    """A_n^{-1} r by Eq. 3.1 with complex factors (``complex_factors``):
+    w = (Y (x) I) r, then Algorithm 1 from the last row to the first,
+
+        g_i = w_i - sum_{j > i} T_ij M_x z_j,   (K_x + lambda_i M_x) z_i = g_i,
+
+    each complex shift lambda_i = alpha + i beta solved by MinRes in Theorem
+    3.2's form (the 2x2 real block with beta1 = -beta, beta2 = beta); a real
+    eigenvalue (|beta| <= 1e-13 |lambda|) by a direct solve of its real and
+    imaginary parts.  The diagonalisation has no back substitution (T is
+    diagonal).  Returns (Re (X (x) I) z, max MinRes iterations)."""
+    Mx, Kx = assemble.spatial_operators(prob)
+    Kt, Mt = assemble.time_matrices(prob.tau, prob.ne, prob.p, prob.delta)
+    T, X, Y = complex_factors(Kt, Mt, variant)
+    nt, m = prob.Nt, prob.Nx
+    w = Y @ np.asarray(r, float).reshape(nt, m)
+    z = np.zeros((nt, m), dtype=complex)
+    itmax = 0
+    for i in reversed(range(nt)):
+        g = w[i].copy()
+        for j in range(i + 1, nt):
+            g -= T[i, j] * (Mx @ z[j])
+        lam = T[i, i]
+        if abs(lam.imag) <= 1e-13 * abs(lam):
+            lu = spla.splu(sp.csc_matrix(Kx + lam.real * Mx))
+            z[i] = lu.solve(g.real) + 1j * lu.solve(g.imag)
+        else:
+            x, y, it = block_solve(Kx, Mx, lam.real, -lam.imag, lam.imag, g.real, g.imag,
+                                   tol=tol, maxit=maxit)
+            z[i] = x + 1j * y
+            itmax = max(itmax, it)
+    return (X @ z).real.reshape(-1), itmax
+
+
+def jacobi_step_minres(prob, u, f, omega=0.5, tol=1e-4, variant="rschur"):
     """One damped block-Jacobi step of Sec. 3.1, u + omega D^{-1} (f - L u),
-    with every slab inverse applied by ``slab_solve_minres`` (inexact, the
-    smoother of the paper's multigrid runs with MinRes block solves).
-    Returns (new u, max MinRes iterations over the slabs)."""
+    with every slab inverse applied by ``slab_solve_minres`` (variant
+    "rschur") or ``slab_solve_minres_complex`` ("eig", "cschur") -- inexact,
+    the smoothers of the paper's multigrid runs with MinRes block solves
+    (Table 4).  Returns (new u, max MinRes iterations over the slabs)."""
     L = assemble.assemble_L(prob)
     r = (np.asarray(f, float) - L @ u).reshape(prob.N, -1)
     out = np.array(u, dtype=float).reshape(prob.N, -1).copy()
     itmax = 0
     for n in range(prob.N):
-        z, it = slab_solve_minres(prob, r[n], tol=tol)
+        if variant == "rschur":
+            z, it = slab_solve_minres(prob, r[n], tol=tol)
+        else:
+            z, it = slab_solve_minres_complex(prob, r[n], variant, tol=tol)
         out[n] += omega * z
         itmax = max(itmax, it)
     return out.reshape(-1), itmax

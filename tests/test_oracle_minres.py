@@ -323,3 +323,33 @@ def test_jacobi_step_minres_tight_tolerance_is_exact_step():
     err = np.abs(got4 - ref).max() / np.abs(ref).max()
     assert 1e-8 < err < 1e-3
     assert it4 <= MR.minres_bound_iterations(1e-4) < it
+
+
+@pytest.mark.parametrize("variant", ["eig", "cschur"])
+@pytest.mark.parametrize("d,spans,p,ne,theta", [(1, (12,), 2, 2, 1.0), (2, (6, 5), 2, 2, 1.0),
+                                                (2, (5, 4), 3, 2, 0.1)])
+def test_complex_slab_solve_minres_matches_lu(variant, d, spans, p, ne, theta):
+    """Eq. 3.1 with the diagonalisation / complex Schur factors and Theorem
+    3.2's MinRes for every complex shift equals the sparse-LU slab solve at a
+    tight tolerance; the factors satisfy K_t X = M_t X T, Y M_t X = I."""
+    prob = A.Problem(d, spans, p, ne, 4, theta=theta)
+    Kt, Mt = A.time_matrices(prob.tau, prob.ne, prob.p, prob.delta)
+    T, X, Y = MR.complex_factors(Kt, Mt, variant)
+    n = Kt.shape[0]
+    assert np.allclose(Kt @ X, Mt @ X @ T, atol=1e-10 * np.abs(Kt).max())
+    assert np.allclose(Y @ Mt @ X, np.eye(n), atol=1e-9)
+    assert np.allclose(np.tril(T, -1), 0.0)
+    if variant == "cschur":
+        assert np.allclose(X.conj().T @ X, np.eye(n), atol=1e-12)
+    else:
+        assert np.allclose(T, np.diag(np.diag(T)))
+    assert np.any(np.abs(np.diag(T).imag) > 1e-3)
+    Ab, _ = A.slab_blocks(prob)
+    r = np.random.default_rng(13).standard_normal(prob.Nt * prob.Nx)
+    exact = spla.spsolve(sp.csc_matrix(Ab), r)
+    got, it = MR.slab_solve_minres_complex(prob, r, variant, tol=1e-13)
+    assert np.linalg.norm(got - exact) <= 1e-9 * np.linalg.norm(exact)
+    assert it >= 2
+    got4, _ = MR.slab_solve_minres_complex(prob, r, variant, tol=1e-4)
+    err = np.linalg.norm(got4 - exact) / np.linalg.norm(exact)
+    assert 1e-9 < err < 1e-2
