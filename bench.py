@@ -190,10 +190,10 @@ def gpu_arm(args, rank, world):
     common = dict(ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
     peaks, peak_src = load_peaks()
 
-    def make(prec, basis, outer, fused=None, spatial="fd"):
+    def make(prec, basis, outer, fused=None, spatial="fd", variant="rschur"):
         return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
                          outer=outer, fused_vcycle=args.fused if fused is None else fused,
-                         spatial_solver=spatial, **common)
+                         spatial_solver=spatial, variant=variant, **common)
 
     # rank r solves its own right-hand side(s) (independent replicas)
     n1 = make_len(d, spans, p, N, ne)
@@ -285,26 +285,28 @@ def gpu_arm(args, rank, world):
             ("mixed_fp32", "nodal", "fgmres"), ("mixed_fp32", "spectral", "fgmres"),
             ("mixed_fp32", "spectral", "ir"), ("mixed_tf32", "spectral", "ir"),
             ("mixed_bf16", "spectral", "ir"), ("mixed_tf32", "spectral", "fgmres"))
-    allv = [v + (args.fused, "fd") for v in allv]
-    # the inexact spatial solves (MinRes block solves inside the B-spline-basis smoother)
-    allv.append(("mixed_fp32", "nodal", "fgmres", args.fused, "minres"))
-    allv.append((args.precision, args.basis, args.outer, 1 - args.fused, "fd"))
+    allv = [v + (args.fused, "fd", "rschur") for v in allv]
+    # the inexact spatial solves (MinRes block solves inside the B-spline-basis
+    # smoother) with the three factorisations of Table 4
+    for fac in ("rschur", "eig", "cschur"):
+        allv.append(("mixed_fp32", "nodal", "fgmres", args.fused, "minres", fac))
+    allv.append((args.precision, args.basis, args.outer, 1 - args.fused, "fd", "rschur"))
     chosen = {"all": allv, "min": [allv[0], allv[-1]], "none": []}[vset]
-    for prec, basis, outer, fz, spatial in chosen:
+    for prec, basis, outer, fz, spatial, fac in chosen:
         name = "fp64_plain" if (prec, basis, spatial) == ("fp64", "nodal", "fd") else \
             "%s_%s_%s" % (prec, basis, outer)
         if spatial != "fd":
-            name += "_" + spatial
+            name += "_" + spatial + ("" if fac == "rschur" else "_" + fac)
         if fz != args.fused:
             name += "_fused" if fz else "_levelwise"
         elif (prec, basis, outer, spatial) == (args.precision, args.basis, args.outer, "fd") \
                 and name != "fp64_plain":
             continue
-        sv = make(prec, basis, outer, fz, spatial)
+        sv = make(prec, basis, outer, fz, spatial, fac)
         tv, iv, uv, _ = timed_solves(sv, f, max(1, args.steps // 2), 1)
         msv = sum(tv) / len(tv)
         variants[name] = {"precision": prec, "basis": basis, "outer": outer, "fused_vcycle": fz,
-                          "spatial_solver": spatial,
+                          "spatial_solver": spatial, "variant": fac,
                           "ms_per_step": msv,
                           "value": sv.ndofs * world / (msv / 1e3),
                           "iterations": iv[-1]["iterations"],

@@ -86,18 +86,25 @@ extern "C" {
  * V-cycle (option spatial_solver) */
 #define ST_SPATIAL_FD     0 /* exact: fast diagonalisation in the generalized
                                eigenbasis of the 1D matrices (default)       */
-#define ST_SPATIAL_MINRES 1 /* inexact (Sec. 3.5, Theorem 3.3): the real Schur
-                               form's 2x2 blocks are standardised to
-                               [[alpha, beta1], [beta2, alpha]]; Algorithm 1
-                               runs over its diagonal blocks from the last to
-                               the first, every 2x2 block's spatial system
-                               solved by MinRes preconditioned by Theorem
-                               3.3's block-diagonal P (P^{-1} by fast
-                               diagonalisation) to minres_tol, every 1x1
-                               block (SPD, its own preconditioner) by one
-                               application of P^{-1}.  Needs ST_BASIS_NODAL
-                               and ST_RSCHUR; the V-cycle is then inexact, so
-                               pair it with ST_OUTER_FGMRES (flexible)       */
+#define ST_SPATIAL_MINRES 1 /* inexact (Sec. 3.3-3.5, Theorems 3.2/3.3).
+                               ST_RSCHUR: the real Schur form's 2x2 blocks
+                               are standardised to [[alpha, beta1], [beta2,
+                               alpha]]; Algorithm 1 runs over its diagonal
+                               blocks from the last to the first, every 2x2
+                               block's spatial system solved by MinRes
+                               preconditioned by Theorem 3.3's block-diagonal
+                               P (P^{-1} by fast diagonalisation) to
+                               minres_tol, every 1x1 block (SPD, its own
+                               preconditioner) by one application of P^{-1}.
+                               ST_EIG / ST_CSCHUR: complex time transforms
+                               (real and imaginary parts as separate
+                               vectors), Algorithm 1 over the rows of the
+                               diagonal / upper triangular T, every complex
+                               shift alpha + i beta by MinRes in Theorem 3.2's
+                               form (twice the work of ST_RSCHUR: a conjugate
+                               pair is two complex solves).  Needs
+                               ST_BASIS_NODAL; the V-cycle is then inexact,
+                               so pair it with ST_OUTER_FGMRES (flexible)   */
 
 /* outer iteration */
 #define ST_OUTER_FGMRES 0 /* FGMRES(restart), right-preconditioned by one V-cycle */

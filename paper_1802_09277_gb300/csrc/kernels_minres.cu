@@ -205,31 +205,32 @@ __global__ void __launch_bounds__(MR_THREADS)
         wp[e] = ipw * wp[e] / (mu[e] + shift);
 }
 
-// dst[sys][comp][:] = scale_comp * src[sys][row0 + comp][:]  (src: nt planes per slab)
+// dst[sys][comp][:] = scale_comp * src_comp[sys][row_comp][:]  (sources: nt
+// planes per slab; component 1 may come from another vector or row)
 template <typename T>
 __global__ void __launch_bounds__(MR_THREADS)
-    k_mr_gather(const T *__restrict__ src, T *__restrict__ dst, int row0, int c, int nt,
-                long long m, T sc0, T sc1) {
+    k_mr_gather(const T *__restrict__ src0, int row0, const T *__restrict__ src1, int row1,
+                T *__restrict__ dst, int c, int nt, long long m, T sc0, T sc1) {
     const int plane = blockIdx.y;
     const int sys = plane / c, comp = plane - sys * c;
     const T sc = comp == 0 ? sc0 : sc1;
-    const T *sp = src + ((long long)sys * nt + row0 + comp) * m;
+    const T *sp = (comp == 0 ? src0 : src1) + ((long long)sys * nt + (comp == 0 ? row0 : row1)) * m;
     T *dp = dst + (long long)plane * m;
     for (long long e = (long long)blockIdx.x * MR_THREADS + threadIdx.x; e < m;
          e += (long long)gridDim.x * MR_THREADS)
         dp[e] = sc * sp[e];
 }
 
-// dst[sys][row0 + comp][:] = sign_comp * src[sys][comp][:]
+// dst_comp[sys][row_comp][:] = sign_comp * src[sys][comp][:]
 template <typename T>
 __global__ void __launch_bounds__(MR_THREADS)
-    k_mr_scatter(const T *__restrict__ src, T *__restrict__ dst, int row0, int c, int nt,
-                 long long m, T sg0, T sg1) {
+    k_mr_scatter(const T *__restrict__ src, T *__restrict__ dst0, int row0, T *__restrict__ dst1,
+                 int row1, int c, int nt, long long m, T sg0, T sg1) {
     const int plane = blockIdx.y;
     const int sys = plane / c, comp = plane - sys * c;
     const T sg = comp == 0 ? sg0 : sg1;
     const T *sp = src + (long long)plane * m;
-    T *dp = dst + ((long long)sys * nt + row0 + comp) * m;
+    T *dp = (comp == 0 ? dst0 : dst1) + ((long long)sys * nt + (comp == 0 ? row0 : row1)) * m;
     for (long long e = (long long)blockIdx.x * MR_THREADS + threadIdx.x; e < m;
          e += (long long)gridDim.x * MR_THREADS)
         dp[e] = sg * sp[e];
@@ -330,24 +331,29 @@ cudaError_t launch_fd_scale(T *w, const T *mu, double shift, double pw0, double 
 }
 
 template <typename T>
-cudaError_t launch_mr_gather(const T *src, T *dst, int row0, int c, int nt, long long m, double sc0,
-                             double sc1, int nsys, cudaStream_t s) {
+cudaError_t launch_mr_gather(const T *src0, int row0, const T *src1, int row1, T *dst, int c,
+                             int nt, long long m, double sc0, double sc1, int nsys,
+                             cudaStream_t s) {
     if (nsys <= 0 || m <= 0) return cudaSuccess;
-    if (c < 1 || c > 2 || row0 < 0 || row0 + c > nt || !grid_y_ok((long long)nsys * c))
+    if (c < 1 || c > 2 || row0 < 0 || row0 >= nt || (c == 2 && (row1 < 0 || row1 >= nt)) ||
+        !grid_y_ok((long long)nsys * c))
         return cudaErrorInvalidValue;
     dim3 grid(grid_x(m, 64), (unsigned)(nsys * c));
-    k_mr_gather<T><<<grid, MR_THREADS, 0, s>>>(src, dst, row0, c, nt, m, (T)sc0, (T)sc1);
+    k_mr_gather<T><<<grid, MR_THREADS, 0, s>>>(src0, row0, c == 2 ? src1 : src0, row1, dst, c, nt,
+                                               m, (T)sc0, (T)sc1);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_mr_scatter(const T *src, T *dst, int row0, int c, int nt, long long m,
-                              double sg0, double sg1, int nsys, cudaStream_t s) {
+cudaError_t launch_mr_scatter(const T *src, T *dst0, int row0, T *dst1, int row1, int c, int nt,
+                              long long m, double sg0, double sg1, int nsys, cudaStream_t s) {
     if (nsys <= 0 || m <= 0) return cudaSuccess;
-    if (c < 1 || c > 2 || row0 < 0 || row0 + c > nt || !grid_y_ok((long long)nsys * c))
+    if (c < 1 || c > 2 || row0 < 0 || row0 >= nt || (c == 2 && (row1 < 0 || row1 >= nt)) ||
+        !grid_y_ok((long long)nsys * c))
         return cudaErrorInvalidValue;
     dim3 grid(grid_x(m, 64), (unsigned)(nsys * c));
-    k_mr_scatter<T><<<grid, MR_THREADS, 0, s>>>(src, dst, row0, c, nt, m, (T)sg0, (T)sg1);
+    k_mr_scatter<T><<<grid, MR_THREADS, 0, s>>>(src, dst0, row0, c == 2 ? dst1 : dst0, row1, c, nt,
+                                                m, (T)sg0, (T)sg1);
     return cudaGetLastError();
 }
 
@@ -367,10 +373,10 @@ cudaError_t launch_mr_count(const MrState *st, int nsys, int *count, cudaStream_
                                              const MrState *, long long, int, cudaStream_t);    \
     template cudaError_t launch_fd_scale<T>(T *, const T *, double, double, double, int,         \
                                             long long, int, cudaStream_t);                      \
-    template cudaError_t launch_mr_gather<T>(const T *, T *, int, int, int, long long, double,   \
-                                             double, int, cudaStream_t);                        \
-    template cudaError_t launch_mr_scatter<T>(const T *, T *, int, int, int, long long, double,  \
-                                              double, int, cudaStream_t);
+    template cudaError_t launch_mr_gather<T>(const T *, int, const T *, int, T *, int, int,      \
+                                             long long, double, double, int, cudaStream_t);     \
+    template cudaError_t launch_mr_scatter<T>(const T *, T *, int, T *, int, int, int, long long, \
+                                              double, double, int, cudaStream_t);
 ST_MR_INST(double)
 ST_MR_INST(float)
 #undef ST_MR_INST

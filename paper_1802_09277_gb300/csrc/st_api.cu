@@ -88,6 +88,9 @@ struct MrWork {
     T *d1 = nullptr, *d2 = nullptr, *x = nullptr;                // directions, iterate
     T *z0 = nullptr, *z1 = nullptr;                              // preconditioner ping-pong
     T *zs = nullptr;                                             // slab-layout solution
+    // complex time factors: imaginary part of the solution, of w, and the
+    // real / imaginary right-hand sides of Algorithm 1
+    T *zi = nullptr, *wi = nullptr, *g0 = nullptr, *g1 = nullptr;
     double *partA = nullptr, *partB = nullptr;
     MrState *st = nullptr;
     int *count = nullptr;
@@ -584,8 +587,12 @@ int alloc_mr(st_handle h, MrWork<T> &w, long long cap, bool with_slabs, Alloc al
         *v = (T *)p;
     }
     if (with_slabs) {
-        CKS(alloc((size_t)cap * h->nt * h->g.nxyz * sizeof(T), &p));
-        w.zs = (T *)p;
+        T **slabv[5] = {&w.zs, &w.zi, &w.wi, &w.g0, &w.g1};
+        const int nslabv = h->opt.variant == ST_RSCHUR ? 1 : 5;
+        for (int k = 0; k < nslabv; ++k) {
+            CKS(alloc((size_t)cap * h->nt * h->g.nxyz * sizeof(T), &p));
+            *slabv[k] = (T *)p;
+        }
     }
     CKS(alloc(sizeof(double) * cap * MR_MAX_CHUNKS, &p));
     w.partA = (double *)p;
@@ -721,6 +728,124 @@ int block_minres(st_handle h, MrWork<T> &w, const BlockCoef &bc, int nsys, doubl
     return ST_OK;
 }
 
+// The MinRes smoothing step with complex time factors (ST_EIG, Sec. 3.3;
+// ST_CSCHUR, Sec. 3.4): w = (Y (x) I)(f - L u) in real and imaginary parts
+// (two residual passes, Re Y and Im Y fused); Algorithm 1 over the rows of
+// the upper triangular T from the last to the first,
+//   g_i = w_i - sum_{j>i} T_ij M_x z_j   (four real operator passes when row i
+//   of T has entries right of the diagonal; none for the diagonalisation),
+// each complex shift lambda_i = alpha + i beta solved by MinRes in Theorem
+// 3.2's form (beta1 = -beta, beta2 = beta, iterate [x; -y] for z_i = x + i y),
+// a real one by one application of (K_x + lambda_i M_x)^{-1} to both parts;
+// u <- (overwrite ? 0 : u) + omega Re((X (x) I) z) = ... + omega ((Re X) z_re - (Im X) z_im).
+template <typename T>
+int smooth_range_minres_cplx(st_handle h, int l, T *u, const T *f, T omega, int s0, int ns,
+                             int overwrite) {
+    Work<T> &w = work<T>(h);
+    MrWork<T> &mw = mrwork<T>(h);
+    const int nt = h->nt;
+    const long long m = h->g.nxyz, sl = (long long)nt * m;
+    const LevelHost &L = h->lv[l];
+    const bool eig = h->opt.variant == ST_EIG;
+    const Mat &Yr = eig ? L.Yre : L.Ycre, &Yi = eig ? L.Yim : L.Ycim;
+    const Mat &Xr = eig ? L.Xre : L.Qcre, &Xi = eig ? L.Xim : L.Qcim;
+    Mat Tr((size_t)nt * nt, 0.0), Ti((size_t)nt * nt, 0.0);
+    if (eig) {
+        for (int i = 0; i < nt; ++i) {
+            Tr[i * nt + i] = L.lre[i];
+            Ti[i * nt + i] = L.lim[i];
+        }
+    } else {
+        Tr = L.Tcre;
+        Ti = L.Tcim;
+    }
+    const cudaStream_t s = h->stream;
+    const double tol = h->opt.minres_tol;
+    const int steps = h->opt.minres_maxit > 0 ? h->opt.minres_maxit : minres_bound_steps(tol);
+    const DevSpace<T> &ds = space<T>(h);
+    double ob, of;
+    op_counts(h, (double)ns * nt, nt, sizeof(T), &ob, &of);
+    {
+        TimeCoefs<T> tc = pack_time<T>(h, l, MODE_RES, true);
+        for (int part = 0; part < 2; ++part) {
+            const Mat &Yp = part ? Yi : Yr;
+            for (int i = 0; i < nt; ++i)
+                for (int j = 0; j < nt; ++j) tc.Y[i * NTMAX + j] = (T)Yp[i * nt + j];
+            KScope ks(h, cls_of<T>(ST_PROF_STENCIL64, ST_PROF_STENCIL32), ob * 1.5, of);
+            CK(launch_stencil<T>(u, f, part ? mw.wi : w.w0, ds.bands, h->g, tc, L.nslab, s0, ns,
+                                 s));
+        }
+    }
+    T *Wr = w.w0 + s0 * sl, *Wi = mw.wi + s0 * sl, *Gt = w.w1 + s0 * sl;
+    T *Zr = mw.zs, *Zi = mw.zi, *Gr = mw.g0, *Gi = mw.g1;
+    {
+        KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * ns * sl, 0.0);
+        CK(launch_zero<T>(Zr, ns * sl, s));
+        CK(launch_zero<T>(Zi, ns * sl, s));
+    }
+    // out = fin - sign * C_{i, j>i} M_x zin on row i (other rows: fin)
+    auto pass = [&](int i, const T *zin, const T *fin, T *out, const Mat &C, double sign) -> int {
+        TimeCoefs<T> t2;
+        std::memset(&t2, 0, sizeof t2);
+        for (int j = i + 1; j < nt; ++j) t2.CK[i * NTMAX + j] = (T)(sign * C[i * nt + j]);
+        t2.nt = nt;
+        t2.fuse_y = 0;
+        t2.mode = MODE_RES;
+        KScope ks(h, cls_of<T>(ST_PROF_STENCIL64, ST_PROF_STENCIL32), ob * 1.5, of);
+        CK(launch_stencil<T>(zin, fin, out, ds.bands, h->g, t2, 1, 0, ns, s));
+        return ST_OK;
+    };
+    const double Eb = (double)ns * 2 * m;
+    for (int i = nt - 1; i >= 0; --i) {
+        const T *sr = Wr, *si = Wi;
+        bool upper = false;
+        for (int j = i + 1; j < nt; ++j)
+            if (Tr[i * nt + j] != 0.0 || Ti[i * nt + j] != 0.0) upper = true;
+        if (upper) {
+            CKS(pass(i, Zr, Wr, Gt, Tr, 1.0));   // w_re - Re T M z_re
+            CKS(pass(i, Zi, Gt, Gr, Ti, -1.0));  //      + Im T M z_im
+            CKS(pass(i, Zi, Wi, Gt, Tr, 1.0));   // w_im - Re T M z_im
+            CKS(pass(i, Zr, Gt, Gi, Ti, 1.0));   //      - Im T M z_re
+            sr = Gr;
+            si = Gi;
+        }
+        const double al = Tr[i * nt + i], be = Ti[i * nt + i];
+        if (be != 0.0) {
+            const BlockCoef bc{al, -be, be};
+            {
+                KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+                CK(launch_mr_gather<T>(sr, i, si, i, mw.q, 2, nt, m, std::fabs(be), std::fabs(be),
+                                       ns, s));
+            }
+            CKS(block_minres<T>(h, mw, bc, ns, tol, steps, false));
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+            CK(launch_mr_scatter<T>(mw.x, Zr, i, Zi, i, 2, nt, m, 1.0, -1.0, ns, s));
+        } else {
+            {
+                KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+                CK(launch_mr_gather<T>(sr, i, si, i, mw.q, 2, nt, m, 1.0, 1.0, ns, s));
+            }
+            T *z = nullptr;
+            CKS(precond_fd<T>(h, mw.q, mw.z0, mw.z1, &z, ns, 2, al, 1.0, 1.0));
+            KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
+            CK(launch_mr_scatter<T>(z, Zr, i, Zi, i, 2, nt, m, 1.0, 1.0, ns, s));
+        }
+    }
+    SchurCoefs<T> sc;
+    std::memset(&sc, 0, sizeof sc);
+    sc.nt = nt;
+    const double E = (double)ns * sl;
+    for (int part = 0; part < 2; ++part) {
+        const Mat &Xp = part ? Xi : Xr;
+        for (int i = 0; i < nt; ++i)
+            for (int j = 0; j < nt; ++j) sc.X[i * NTMAX + j] = (T)((part ? -1.0 : 1.0) * Xp[i * nt + j]);
+        KScope ks(h, ST_PROF_UPDATE, sizeof(T) * 3.0 * E, E * (2.0 * nt + 2.0));
+        CK(launch_update<T>(u + s0 * sl, part ? Zi : Zr, sc, omega, h->g, ns, part ? 0 : overwrite,
+                            s));
+    }
+    return ST_OK;
+}
+
 // Damped block-Jacobi step on slabs [s0, s0+ns) of level l with the inexact
 // spatial solves of Sec. 3.5: w = (Y (x) I)(f - L u) (fused into the
 // residual); Algorithm 1 on (Z (x) M_x + I (x) K_x) z = w over the
@@ -737,6 +862,8 @@ int smooth_range_minres(st_handle h, int l, T *u, const T *f, T omega, int s0, i
     if (ns > mw.cap)
         return fail(ST_ERR_INVALID_ARG, "MinRes batch of %d slabs exceeds its work space (%lld)",
                     ns, mw.cap);
+    if (h->opt.variant != ST_RSCHUR)
+        return smooth_range_minres_cplx<T>(h, l, u, f, omega, s0, ns, overwrite);
     const int nt = h->nt;
     const long long m = h->g.nxyz, sl = (long long)nt * m;
     const LevelHost &L = h->lv[l];
@@ -773,22 +900,22 @@ int smooth_range_minres(st_handle h, int l, T *u, const T *f, T omega, int s0, i
         if (c == 1) {
             {
                 KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
-                CK(launch_mr_gather<T>(src, mw.q, b, 1, nt, m, 1.0, 1.0, ns, s));
+                CK(launch_mr_gather<T>(src, b, src, b, mw.q, 1, nt, m, 1.0, 1.0, ns, s));
             }
             T *z = nullptr;
             CKS(precond_fd<T>(h, mw.q, mw.z0, mw.z1, &z, ns, 1, L.Z[b * nt + b], 1.0, 1.0));
             KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
-            CK(launch_mr_scatter<T>(z, Zs, b, 1, nt, m, 1.0, 1.0, ns, s));
+            CK(launch_mr_scatter<T>(z, Zs, b, Zs, b, 1, nt, m, 1.0, 1.0, ns, s));
         } else {
             const BlockCoef bc{L.Z[b * nt + b], L.Z[b * nt + b + 1], L.Z[(b + 1) * nt + b]};
             {
                 KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
-                CK(launch_mr_gather<T>(src, mw.q, b, 2, nt, m, std::fabs(bc.beta2),
+                CK(launch_mr_gather<T>(src, b, src, b + 1, mw.q, 2, nt, m, std::fabs(bc.beta2),
                                        std::fabs(bc.beta1), ns, s));
             }
             CKS(block_minres<T>(h, mw, bc, ns, tol, steps, false));
             KScope ks(h, ST_PROF_MINRES, sizeof(T) * 2.0 * Eb, Eb);
-            CK(launch_mr_scatter<T>(mw.x, Zs, b, 2, nt, m, 1.0, -1.0, ns, s));
+            CK(launch_mr_scatter<T>(mw.x, Zs, b, Zs, b + 1, 2, nt, m, 1.0, -1.0, ns, s));
         }
         i = b - 1;
     }
@@ -1789,9 +1916,8 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     if (o.spatial_solver != ST_SPATIAL_FD && o.spatial_solver != ST_SPATIAL_MINRES)
         return fail(ST_ERR_INVALID_ARG, "bad spatial_solver");
     if (o.spatial_solver == ST_SPATIAL_MINRES) {
-        if (o.basis != ST_BASIS_NODAL || o.variant != ST_RSCHUR)
-            return fail(ST_ERR_UNSUPPORTED, "MinRes spatial solves are built for the B-spline "
-                        "basis with the real Schur variant");
+        if (o.basis != ST_BASIS_NODAL)
+            return fail(ST_ERR_UNSUPPORTED, "MinRes spatial solves are built for the B-spline basis");
         if (!(o.minres_tol > 0) || o.minres_tol >= 1 || o.minres_maxit < 0 || o.minres_maxit > 1000)
             return fail(ST_ERR_INVALID_ARG, "minres_tol must be in (0, 1), minres_maxit in [0, 1000]");
         if ((long long)slabs * o.nrhs > 32767)
@@ -2252,10 +2378,10 @@ int st_block_minres(st_handle h, double alpha, double beta1, double beta2, const
     CKS(alloc_mr<double>(h, w, nsys, false, plain));
     const long long m = h->g.nxyz;
     const BlockCoef bc{alpha, beta1, beta2};
-    CK(launch_mr_gather<double>(f, w.q, 0, 2, 2, m, std::fabs(beta2), std::fabs(beta1), nsys,
+    CK(launch_mr_gather<double>(f, 0, f, 1, w.q, 2, 2, m, std::fabs(beta2), std::fabs(beta1), nsys,
                                 h->stream));
     CKS(block_minres<double>(h, w, bc, nsys, tol, steps, true));
-    CK(launch_mr_scatter<double>(w.x, u, 0, 2, 2, m, 1.0, -1.0, nsys, h->stream));
+    CK(launch_mr_scatter<double>(w.x, u, 0, u, 1, 2, 2, m, 1.0, -1.0, nsys, h->stream));
     std::vector<MrState> hs(nsys);
     CK(cudaMemcpyAsync(hs.data(), w.st, sizeof(MrState) * nsys, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));

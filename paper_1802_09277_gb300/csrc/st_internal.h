@@ -281,12 +281,14 @@ cudaError_t launch_mr_update(T *p, const T *z, T *t, const T *d1, T *d2, T *x, c
 template <typename T>
 cudaError_t launch_fd_scale(T *w, const T *mu, double shift, double pw0, double pw1, int c,
                             long long m, int nsys, cudaStream_t s);
+// compact batch <-> slab vectors (nt planes per slab): component 0 at row0 of
+// src0 / dst0, component 1 (c = 2) at row1 of src1 / dst1, scaled / signed
 template <typename T>
-cudaError_t launch_mr_gather(const T *src, T *dst, int row0, int c, int nt, long long m, double sc0,
-                             double sc1, int nsys, cudaStream_t s);
+cudaError_t launch_mr_gather(const T *src0, int row0, const T *src1, int row1, T *dst, int c,
+                             int nt, long long m, double sc0, double sc1, int nsys, cudaStream_t s);
 template <typename T>
-cudaError_t launch_mr_scatter(const T *src, T *dst, int row0, int c, int nt, long long m,
-                              double sg0, double sg1, int nsys, cudaStream_t s);
+cudaError_t launch_mr_scatter(const T *src, T *dst0, int row0, T *dst1, int row1, int c, int nt,
+                              long long m, double sg0, double sg1, int nsys, cudaStream_t s);
 cudaError_t launch_mr_count(const MrState *st, int nsys, int *count, cudaStream_t s);
 
 }  // namespace st

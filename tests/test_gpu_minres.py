@@ -1,5 +1,6 @@
-"""GPU parity of the inexact spatial solves (Sec. 3.5, Theorems 3.2/3.3,
-Algorithm 1 of arXiv:1802.09277) against the CPU oracle, through the C ABI.
+"""GPU parity of the inexact spatial solves (Sec. 3.3-3.5, Theorems 3.2/3.3,
+Algorithm 1 of arXiv:1802.09277) against the CPU oracle, through the C ABI,
+for the real Schur, diagonalisation and complex Schur factorisations.
 
 Tolerances: a block solve to 1e-10 in FP64 agrees with the oracle's MinRes
 (same iteration, its preconditioner by sparse LU instead of fast
@@ -134,15 +135,21 @@ SMOOTH_CASES = [
 ]
 
 
+VARIANTS = ["rschur", "eig", "cschur"]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("d,spans,p,N,ne", SMOOTH_CASES)
-def test_minres_smoother_tight_tolerance_is_exact(st, d, spans, p, N, ne):
+def test_minres_smoother_tight_tolerance_is_exact(st, variant, d, spans, p, N, ne):
     """With minres_tol 1e-13 the smoothing step (Algorithm 1 over the
-    standardised real Schur form, MinRes block solves) equals the oracle's
-    exact step with sparse-LU slab solves."""
+    standardised real Schur form, or over the complex triangular / diagonal
+    factor with Theorem 3.2's complex shifts, MinRes block solves) equals the
+    oracle's exact step with sparse-LU slab solves."""
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     L = A.assemble_L(pr)
     lev = S.Level(L, N, pr.Nt * pr.Nx)
-    s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres", minres_tol=1e-13)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres", minres_tol=1e-13,
+                  variant=variant)
     u0 = inputs.uniform_vector(3, pr.ndofs)
     f = inputs.uniform_vector(4, pr.ndofs)
     ref = S.jacobi_step(lev, u0, f, 0.5)
@@ -152,18 +159,19 @@ def test_minres_smoother_tight_tolerance_is_exact(st, d, spans, p, N, ne):
     s.close()
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("d,spans,p,N,ne", SMOOTH_CASES)
-def test_minres_smoother_default_tolerance(st, d, spans, p, N, ne):
+def test_minres_smoother_default_tolerance(st, variant, d, spans, p, N, ne):
     """At the default inner tolerance 1e-4 the step is inexact to the same
-    order as the oracle's own inexact step."""
+    order as the oracle's own inexact step with the same factorisation."""
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     L = A.assemble_L(pr)
     lev = S.Level(L, N, pr.Nt * pr.Nx)
-    s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres")
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres", variant=variant)
     u0 = inputs.uniform_vector(3, pr.ndofs)
     f = inputs.uniform_vector(4, pr.ndofs)
     ref = S.jacobi_step(lev, u0, f, 0.5)
-    ora, _ = MR.jacobi_step_minres(pr, u0, f, 0.5, tol=1e-4)
+    ora, _ = MR.jacobi_step_minres(pr, u0, f, 0.5, tol=1e-4, variant=variant)
     u = dev(u0)
     s.smooth(u, dev(f), 1)
     err = relerr(host(u), ref)
@@ -172,19 +180,21 @@ def test_minres_smoother_default_tolerance(st, d, spans, p, N, ne):
     s.close()
 
 
-def test_minres_smoother_multi_rhs_equals_single(st):
+@pytest.mark.parametrize("variant", ["rschur", "cschur"])
+def test_minres_smoother_multi_rhs_equals_single(st, variant):
     d, spans, p, N, ne = 2, (9, 7), 2, 4, 2
     pr = A.Problem(d, spans, p, ne, N)
     f1 = inputs.uniform_vector(31, pr.ndofs)
     f2 = inputs.uniform_vector(32, pr.ndofs)
     outs = []
     for f in (f1, f2):
-        s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres")
+        s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres", variant=variant)
         u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
         s.smooth(u, dev(f), 2)
         outs.append(host(u))
         s.close()
-    s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres", nrhs=2)
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres", nrhs=2,
+                  variant=variant)
     u = torch.zeros(2 * pr.ndofs, dtype=torch.float64, device="cuda")
     s.smooth(u, dev(np.concatenate([f1, f2])), 2)
     both = host(u)
@@ -216,8 +226,31 @@ def test_minres_vcycle_solve(st, precision, d, spans, p, N, ne):
     assert np.array_equal(res[0], res[1])
 
 
-def test_minres_rejects_other_bases(st):
-    for kw in [dict(basis="spectral"), dict(variant="eig"), dict(variant="cschur"),
+@pytest.mark.parametrize("variant", ["eig", "cschur"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed_fp32"])
+def test_minres_complex_factors_solve(st, variant, precision):
+    """Table 4's diagonalisation and complex Schur smoothers with MinRes
+    (Theorem 3.2's complex shifts) precondition FGMRES to 1e-8 and the exact
+    solution, in the same number of iterations as the real Schur one (+-1)."""
+    d, spans, p, N, ne = 2, (12, 10), 2, 8, 2
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    f = inputs.uniform_vector(8, pr.ndofs)
+    ref = S.forward_subst(pr, f)
+    its = {}
+    for v in ("rschur", variant):
+        s = st.Solver(d, p, spans, N, ne_per_slab=ne, spatial_solver="minres", variant=v,
+                      precision=precision, outer="fgmres")
+        u = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+        info = s.solve(dev(f), u, tol=1e-8)
+        assert info["rel_residual"] <= 1e-8
+        assert relerr(host(u), ref) <= (1e-6 if precision == "fp64" else 1e-5)
+        its[v] = info["iterations"]
+        s.close()
+    assert abs(its[variant] - its["rschur"]) <= 1
+
+
+def test_minres_rejects_other_bases_and_bad_options(st):
+    for kw in [dict(basis="spectral"), dict(basis="spectral", variant="eig"),
                dict(minres_tol=0.0), dict(minres_tol=1.5), dict(minres_maxit=-1)]:
         with pytest.raises(st.StError):
             st.Solver(2, 2, (6, 6), 4, spatial_solver="minres", **kw)
