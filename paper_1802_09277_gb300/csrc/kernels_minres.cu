@@ -10,8 +10,8 @@
 // strides over its elements, so per-system scalars are read once per thread
 // and no division by the system length is needed.  Scalars of the iteration
 // (Lanczos coefficients, Givens rotations, the residual norm) live in one
-// MrState per system on the device and are updated by one thread per system,
-// so the whole iteration runs without host synchronisation.
+// MrState per system on the device (two buffers, swapped every step), so the
+// whole iteration runs without host synchronisation.
 #include "st_internal.h"
 
 namespace st {
@@ -117,19 +117,11 @@ __global__ void __launch_bounds__(MR_THREADS)
 
 // New column (beta_k, alpha_k, beta_{k+1}) of the tridiagonal matrix: apply
 // the two previous rotations, choose the one that annihilates beta_{k+1},
-// and record the coefficients of the direction and iterate updates.
-__global__ void k_mr_givens(const double *__restrict__ partA, const double *__restrict__ partB,
-                            int chunks, MrState *__restrict__ st, double tol, int nsys) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= nsys) return;
-    MrState q = st[s];
+// and record the coefficients of the direction and iterate updates
+// (alpha = p_k . A p_k, b2 = beta_{k+1}^2).
+__device__ MrState mr_rotate(MrState q, double alpha, double b2, double tol) {
     q.upd = 0;
-    if (!q.active) {
-        st[s] = q;
-        return;
-    }
-    const double alpha = part_sum(partA, chunks, s);
-    const double b2 = part_sum(partB, chunks, s);
+    if (!q.active) return q;
     const double bn = b2 > 0.0 ? sqrt(b2) : 0.0;
     const double eps = q.s2 * q.bk;
     const double dbar = q.c2 * q.bk;
@@ -138,8 +130,7 @@ __global__ void k_mr_givens(const double *__restrict__ partA, const double *__re
     const double rho = hypot(gbar, bn);
     if (!(rho > 0.0)) {  // breakdown: keep the current iterate
         q.active = 0;
-        st[s] = q;
-        return;
+        return q;
     }
     const double c = gbar / rho, sn = bn / rho;
     q.cd = 1.0 / rho;
@@ -161,22 +152,36 @@ __global__ void k_mr_givens(const double *__restrict__ partA, const double *__re
     q.c1 = c;
     q.s1 = sn;
     q.bk = bn;
-    st[s] = q;
+    return q;
 }
 
+// One MinRes step's rotation and vector update.  Thread 0 of every CTA of a
+// system forms the new state from st_in and the chunk partials (the same
+// fixed-order sums in every CTA); CTA 0 stores it in st_out (a second state
+// buffer, so no CTA reads a state another one has already replaced).  Then
 // d_k = (p_k - delta d_{k-1} - eps d_{k-2}) / rho (written over d_{k-2}),
 // x += c eta d_k; if the system goes on: q_{k+1} = t / beta_{k+1} (in place),
-// p_{k+1} = P^{-1} t / beta_{k+1} (over p_k)
+// p_{k+1} = P^{-1} t / beta_{k+1} (over p_k).
 template <typename T>
 __global__ void __launch_bounds__(MR_THREADS)
-    k_mr_update(T *__restrict__ p, const T *__restrict__ z, T *__restrict__ t,
-                const T *__restrict__ d1, T *__restrict__ d2, T *__restrict__ x,
-                const MrState *__restrict__ st, long long len) {
+    k_mr_step(T *__restrict__ p, const T *__restrict__ z, T *__restrict__ t,
+              const T *__restrict__ d1, T *__restrict__ d2, T *__restrict__ x,
+              const double *__restrict__ partA, const double *__restrict__ partB, int chunks,
+              const MrState *__restrict__ st_in, MrState *__restrict__ st_out, double tol,
+              long long len) {
+    __shared__ MrState sh;
     const int sys = blockIdx.y;
-    if (!st[sys].upd) return;
-    const T cd = (T)st[sys].cd, cdel = (T)st[sys].cdel, ceps = (T)st[sys].ceps;
-    const T cx = (T)st[sys].cx, ib = (T)st[sys].invb;
-    const bool go_on = st[sys].active != 0;
+    if (threadIdx.x == 0) {
+        const MrState q = mr_rotate(st_in[sys], part_sum(partA, chunks, sys),
+                                    part_sum(partB, chunks, sys), tol);
+        sh = q;
+        if (blockIdx.x == 0) st_out[sys] = q;
+    }
+    __syncthreads();
+    if (!sh.upd) return;
+    const T cd = (T)sh.cd, cdel = (T)sh.cdel, ceps = (T)sh.ceps;
+    const T cx = (T)sh.cx, ib = (T)sh.invb;
+    const bool go_on = sh.active != 0;
     const long long off = (long long)sys * len;
     for (long long e = (long long)blockIdx.x * MR_THREADS + threadIdx.x; e < len;
          e += (long long)gridDim.x * MR_THREADS) {
@@ -301,20 +306,15 @@ cudaError_t launch_mr_lanczos(T *t, const T *q, const T *qp, const double *partA
     return cudaGetLastError();
 }
 
-cudaError_t launch_mr_givens(const double *partA, const double *partB, int chunks, MrState *st,
-                             double tol, int nsys, cudaStream_t s) {
-    if (nsys <= 0) return cudaSuccess;
-    k_mr_givens<<<(nsys + 127) / 128, 128, 0, s>>>(partA, partB, chunks, st, tol, nsys);
-    return cudaGetLastError();
-}
-
 template <typename T>
-cudaError_t launch_mr_update(T *p, const T *z, T *t, const T *d1, T *d2, T *x, const MrState *st,
-                             long long len, int nsys, cudaStream_t s) {
+cudaError_t launch_mr_step(T *p, const T *z, T *t, const T *d1, T *d2, T *x, const double *partA,
+                           const double *partB, int chunks, const MrState *st_in, MrState *st_out,
+                           double tol, long long len, int nsys, cudaStream_t s) {
     if (nsys <= 0 || len <= 0) return cudaSuccess;
-    if (!grid_y_ok(nsys)) return cudaErrorInvalidValue;
+    if (!grid_y_ok(nsys) || st_in == st_out) return cudaErrorInvalidValue;
     dim3 grid(grid_x(len, 64), (unsigned)nsys);
-    k_mr_update<T><<<grid, MR_THREADS, 0, s>>>(p, z, t, d1, d2, x, st, len);
+    k_mr_step<T><<<grid, MR_THREADS, 0, s>>>(p, z, t, d1, d2, x, partA, partB, chunks, st_in,
+                                             st_out, tol, len);
     return cudaGetLastError();
 }
 
@@ -369,8 +369,9 @@ cudaError_t launch_mr_count(const MrState *st, int nsys, int *count, cudaStream_
                                                const MrState *, long long, int, cudaStream_t);  \
     template cudaError_t launch_mr_lanczos<T>(T *, const T *, const T *, const double *, int,    \
                                               const MrState *, long long, int, cudaStream_t);   \
-    template cudaError_t launch_mr_update<T>(T *, const T *, T *, const T *, T *, T *,           \
-                                             const MrState *, long long, int, cudaStream_t);    \
+    template cudaError_t launch_mr_step<T>(T *, const T *, T *, const T *, T *, T *,             \
+                                           const double *, const double *, int, const MrState *, \
+                                           MrState *, double, long long, int, cudaStream_t);    \
     template cudaError_t launch_fd_scale<T>(T *, const T *, double, double, double, int,         \
                                             long long, int, cudaStream_t);                      \
     template cudaError_t launch_mr_gather<T>(const T *, int, const T *, int, T *, int, int,      \

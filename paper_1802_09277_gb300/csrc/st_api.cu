@@ -92,7 +92,7 @@ struct MrWork {
     // real / imaginary right-hand sides of Algorithm 1
     T *zi = nullptr, *wi = nullptr, *g0 = nullptr, *g1 = nullptr;
     double *partA = nullptr, *partB = nullptr;
-    MrState *st = nullptr;
+    MrState *st = nullptr, *st2 = nullptr;  // current state, the next step's
     int *count = nullptr;
     long long cap = 0;  // systems
 };
@@ -600,6 +600,8 @@ int alloc_mr(st_handle h, MrWork<T> &w, long long cap, bool with_slabs, Alloc al
     w.partB = (double *)p;
     CKS(alloc(sizeof(MrState) * cap, &p));
     w.st = (MrState *)p;
+    CKS(alloc(sizeof(MrState) * cap, &p));
+    w.st2 = (MrState *)p;
     CKS(alloc(sizeof(int), &p));
     w.count = (int *)p;
     w.cap = cap;
@@ -704,12 +706,10 @@ int block_minres(st_handle h, MrWork<T> &w, const BlockCoef &bc, int nsys, doubl
             CK(launch_seg_dot<T>(t, z, w.partB, len, nsys, s));
         }
         {
-            KScope ks(h, ST_PROF_MINRES, 16.0 * chunks * nsys, 20.0 * nsys);
-            CK(launch_mr_givens(w.partA, w.partB, chunks, w.st, tol, nsys, s));
-        }
-        {
             KScope ks(h, ST_PROF_MINRES, sizeof(T) * 10.0 * E, 8.0 * E);
-            CK(launch_mr_update<T>(w.p, z, t, d1, d2, w.x, w.st, len, nsys, s));
+            CK(launch_mr_step<T>(w.p, z, t, d1, d2, w.x, w.partA, w.partB, chunks, w.st, w.st2,
+                                 tol, len, nsys, s));
+            std::swap(w.st, w.st2);
         }
         // the new direction is in d2; q_{k+1} is in t
         std::swap(d1, d2);

@@ -272,11 +272,12 @@ cudaError_t launch_mr_init_vec(T *q, T *p, const T *z, T *qp, T *d1, T *d2, T *x
 template <typename T>
 cudaError_t launch_mr_lanczos(T *t, const T *q, const T *qp, const double *partA, int chunks,
                               const MrState *st, long long len, int nsys, cudaStream_t s);
-cudaError_t launch_mr_givens(const double *partA, const double *partB, int chunks, MrState *st,
-                             double tol, int nsys, cudaStream_t s);
+// rotation of every system (state st_in -> st_out) fused with its direction,
+// iterate and normalisation update
 template <typename T>
-cudaError_t launch_mr_update(T *p, const T *z, T *t, const T *d1, T *d2, T *x, const MrState *st,
-                             long long len, int nsys, cudaStream_t s);
+cudaError_t launch_mr_step(T *p, const T *z, T *t, const T *d1, T *d2, T *x, const double *partA,
+                           const double *partB, int chunks, const MrState *st_in, MrState *st_out,
+                           double tol, long long len, int nsys, cudaStream_t s);
 // w[sys][comp][k] /= pw_comp (mu_k + shift)  (pw (K_x + shift M_x) inverted in the eigenbasis)
 template <typename T>
 cudaError_t launch_fd_scale(T *w, const T *mu, double shift, double pw0, double pw1, int c,
