@@ -81,6 +81,13 @@ class Problem:
         return Problem(self.d, self.spans, self.p, self.ne, self.N // 2,
                        self.theta, self.T, self.delta)
 
+    def space_coarse(self):
+        """The next coarser level in space: every axis' spans halved, the
+        same slabs and time discretisation."""
+        assert all(s % 2 == 0 for s in self.spans)
+        return Problem(self.d, tuple(s // 2 for s in self.spans), self.p, self.ne, self.N,
+                       self.theta, self.T, self.delta)
+
 
 # ----------------------------------------------------------------------------
 # 1D matrices

@@ -11,7 +11,11 @@ Test infrastructure only (see ``oracle/__init__.py``).
   number of elements) expressed in the two fine slabs' bases.  The coarse
   spline space is nested in the broken fine space, so the L2 projection onto
   each fine slab reproduces it exactly.
-* ``Hierarchy``        -- levels with Galerkin coarse operators P^T L P.
+* ``space_prolongation_1d``, ``space_prolongation`` -- P_x: the coarse
+  spatial B-splines (spans halved) in the fine basis (knot insertion).
+* ``Hierarchy``        -- levels with Galerkin coarse operators P^T L P,
+  coarsening in time (slab pairs) or, above a parabolic ratio tau / h^2, in
+  space.
 * ``vcycle``, ``mg_solve``, ``fgmres`` -- the V-cycle, the plain multigrid
   iteration and right-preconditioned flexible GMRES.
 
@@ -96,24 +100,69 @@ def prolongation(prob):
     return sp.block_diag([blk] * (prob.N // 2), format="csr")
 
 
-class Hierarchy:
-    """Levels 0 (finest) .. J (one slab) with Galerkin operators."""
+def space_prolongation_1d(s, p):
+    """P_x of shape (n_f, n_c): the interior B-splines of s/2 spans on (0,1)
+    expressed in the interior B-splines of s spans.  The coarse space is
+    nested in the fine one (the fine knots are the coarse knots plus the
+    midpoints), so the L2 projection with the fine mass matrix reproduces it
+    exactly; the fine quadrature integrates the products exactly."""
+    assert s % 2 == 0
+    kf = bspline.open_knots(0.0, 1.0, s, p)
+    kc = bspline.open_knots(0.0, 1.0, s // 2, p)
+    x, w = bspline.element_quadrature(kf, p + 2)
+    Bf = bspline.basis(kf, p, x)[:, 1:-1]
+    Bc = bspline.basis(kc, p, x)[:, 1:-1]
+    Mff = Bf.T @ (w[:, None] * Bf)
+    Mfc = Bf.T @ (w[:, None] * Bc)
+    return np.linalg.solve(Mff, Mfc)
 
-    def __init__(self, prob, min_slabs=1):
+
+def space_prolongation(prob):
+    """P = I_{N N_t} (x) P_z (x) P_y (x) P_x: maps the level with every
+    axis' spans halved (same slabs) to prob's level (space coarsening)."""
+    mats = [space_prolongation_1d(s, prob.p) for s in prob.spans]
+    Px = assemble._kron_all(mats)
+    return sp.kron(sp.identity(prob.N * prob.Nt, format="csr"), Px, format="csr")
+
+
+def space_time_ratio(prob):
+    """tau / h_x^2 with h_x the largest spatial element size (the parabolic
+    ratio that decides between coarsening in time and in space)."""
+    return prob.tau * min(prob.spans) ** 2
+
+
+class Hierarchy:
+    """Levels 0 (finest) .. J with Galerkin operators.  Each coarsening step
+    merges slab pairs (time), or -- when space_ratio > 0 and the level's
+    tau / h_x^2 exceeds it (diffusion-dominated slabs) -- halves every spatial
+    axis' spans (space; Sec. 3.1's multigrid coarsens in space and time, the
+    rule is not given in the paper; the coarse level keeps at least min_spans
+    spans per axis); it stops at one slab or when neither applies.  kinds[l]
+    is "t" or "x" for the step from level l to l + 1."""
+
+    def __init__(self, prob, min_slabs=1, space_ratio=0.0, min_spans=2):
         self.probs = [prob]
         self.levels = []
         self.P = []
+        self.kinds = []
         L = assemble.assemble_L(prob)
-        m = prob.Nt * prob.Nx
         while True:
             pr = self.probs[-1]
-            self.levels.append(Level(L, pr.N, m))
-            if pr.N <= min_slabs or pr.N % 2:
+            self.levels.append(Level(L, pr.N, pr.Nt * pr.Nx))
+            space_ok = all(s % 2 == 0 and s // 2 >= min_spans for s in pr.spans)
+            if space_ratio > 0 and space_time_ratio(pr) > space_ratio and space_ok:
+                P = space_prolongation(pr)
+                nxt = pr.space_coarse()
+                self.kinds.append("x")
+            elif pr.N > min_slabs and pr.N % 2 == 0:
+                P = prolongation(pr)
+                nxt = pr.coarse()
+                self.kinds.append("t")
+            else:
                 break
-            P = prolongation(pr)
             self.P.append(P)
             L = (P.T @ L @ P).tocsr()
-            self.probs.append(pr.coarse())
+            self.probs.append(nxt)
         self.coarse_lu = spla.splu(sp.csc_matrix(self.levels[-1].L))
 
 

@@ -368,3 +368,51 @@ def test_multigrid_and_fgmres_converge_to_direct(d, spans, p, N):
     u2, it2, _ = S.fgmres(H.levels[0].L, f, lambda v: S.vcycle(H, v), tol=1e-11)
     assert it2 <= it
     assert np.linalg.norm(u2 - ud) <= 1e-9 * np.linalg.norm(ud)
+
+
+# --------------------------------------------------------------------------
+# Space coarsening (Sec. 3.1 coarsens in space and time)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("s", [4, 8, 14])
+def test_space_prolongation_reproduces_coarse_functions(p, s):
+    """P_x expresses every interior coarse B-spline (s/2 spans) exactly in the
+    interior fine ones (s spans): evaluated at random points, B_c = B_f P_x."""
+    Px = S.space_prolongation_1d(s, p)
+    x = np.random.default_rng(p * 100 + s).uniform(0.0, 1.0, 200)
+    Bf = bs.basis(bs.open_knots(0.0, 1.0, s, p), p, x)[:, 1:-1]
+    Bc = bs.basis(bs.open_knots(0.0, 1.0, s // 2, p), p, x)[:, 1:-1]
+    assert Px.shape == (s + p - 2, s // 2 + p - 2)
+    assert np.allclose(Bf @ Px, Bc, atol=1e-12)
+
+
+@pytest.mark.parametrize("d,spans,p", [(1, (8,), 2), (2, (8, 6), 2), (2, (4, 8), 3), (3, (4, 4, 6), 1)])
+def test_galerkin_space_coarse_operator_is_rediscretisation(d, spans, p):
+    """Nested spatial spaces: P^T L P with the space prolongation equals L
+    assembled on the grid with halved spans (same slabs, same delta)."""
+    pr = A.Problem(d, spans, p, 2, 3, theta=1.0)
+    P = S.space_prolongation(pr)
+    Lc = (P.T @ A.assemble_L(pr) @ P).toarray()
+    ref = A.assemble_L(pr.space_coarse()).toarray()
+    assert np.abs(Lc - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_space_time_hierarchy_rule_and_convergence():
+    """Above tau / h^2 = 1 the hierarchy coarsens in space first (diffusion-
+    dominated slabs), then in time; the multigrid iteration converges to the
+    direct solution, in fewer iterations than with time-only coarsening, and
+    its coarsest level is much smaller."""
+    pr = A.Problem(1, (64,), 2, 2, 16, theta=1.0)
+    assert S.space_time_ratio(pr) == pytest.approx(256.0)
+    f = inputs.uniform_vector(4, pr.ndofs)
+    ref = S.direct(A.assemble_L(pr), f)
+    Ht = S.Hierarchy(pr)
+    Hx = S.Hierarchy(pr, space_ratio=1.0)
+    assert "".join(Ht.kinds) == "tttt"
+    assert "".join(Hx.kinds) == "xxxxtxttt"
+    ut, it_t, _ = S.mg_solve(Ht, f, tol=1e-8)
+    ux, it_x, _ = S.mg_solve(Hx, f, tol=1e-8)
+    assert np.linalg.norm(ux - ref) <= 1e-6 * np.linalg.norm(ref)
+    assert it_x < it_t
+    assert Hx.levels[-1].L.shape[0] * 10 < Ht.levels[-1].L.shape[0]
