@@ -190,10 +190,11 @@ def gpu_arm(args, rank, world):
     common = dict(ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
     peaks, peak_src = load_peaks()
 
-    def make(prec, basis, outer, fused=None, spatial="fd", variant="rschur"):
+    def make(prec, basis, outer, fused=None, spatial="fd", variant="rschur", space_ratio=0.0):
         return st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
                          outer=outer, fused_vcycle=args.fused if fused is None else fused,
-                         spatial_solver=spatial, variant=variant, **common)
+                         spatial_solver=spatial, variant=variant, space_ratio=space_ratio,
+                         **common)
 
     # rank r solves its own right-hand side(s) (independent replicas)
     n1 = make_len(d, spans, p, N, ne)
@@ -296,28 +297,34 @@ def gpu_arm(args, rank, world):
             ("mixed_fp32", "nodal", "fgmres"), ("mixed_fp32", "spectral", "fgmres"),
             ("mixed_fp32", "spectral", "ir"), ("mixed_tf32", "spectral", "ir"),
             ("mixed_bf16", "spectral", "ir"), ("mixed_tf32", "spectral", "fgmres"))
-    allv = [v + (args.fused, "fd", "rschur") for v in allv]
+    allv = [v + (args.fused, "fd", "rschur", 0.0) for v in allv]
     # the inexact spatial solves (MinRes block solves inside the B-spline-basis
     # smoother) with the three factorisations of Table 4
     for fac in ("rschur", "eig", "cschur"):
-        allv.append(("mixed_fp32", "nodal", "fgmres", args.fused, "minres", fac))
-    allv.append((args.precision, args.basis, args.outer, 1 - args.fused, "fd", "rschur"))
+        allv.append(("mixed_fp32", "nodal", "fgmres", args.fused, "minres", fac, 0.0))
+    # space-time coarsening of the B-spline-basis V-cycle (space while tau/h^2 > 1)
+    allv.append(("mixed_fp32", "nodal", "fgmres", args.fused, "fd", "rschur", 1.0))
+    allv.append((args.precision, args.basis, args.outer, 1 - args.fused, "fd", "rschur", 0.0))
     chosen = {"all": allv, "min": [allv[0], allv[-1]], "none": []}[vset]
-    for prec, basis, outer, fz, spatial, fac in chosen:
-        name = "fp64_plain" if (prec, basis, spatial) == ("fp64", "nodal", "fd") else \
-            "%s_%s_%s" % (prec, basis, outer)
+    for prec, basis, outer, fz, spatial, fac, sratio in chosen:
+        name = "fp64_plain" if (prec, basis, spatial, sratio) == ("fp64", "nodal", "fd", 0.0) \
+            else "%s_%s_%s" % (prec, basis, outer)
         if spatial != "fd":
             name += "_" + spatial + ("" if fac == "rschur" else "_" + fac)
+        if sratio > 0:
+            name += "_spacetime"
         if fz != args.fused:
             name += "_fused" if fz else "_levelwise"
-        elif (prec, basis, outer, spatial) == (args.precision, args.basis, args.outer, "fd") \
-                and name != "fp64_plain":
+        elif (prec, basis, outer, spatial, sratio) == (args.precision, args.basis, args.outer,
+                                                       "fd", 0.0) and name != "fp64_plain":
             continue
-        sv, sv_setup_ms = timed_make(prec, basis, outer, fz, spatial, fac)
+        sv, sv_setup_ms = timed_make(prec, basis, outer, fz, spatial, fac, sratio)
         tv, iv, uv, _ = timed_solves(sv, f, max(1, args.steps // 2), 1)
         msv = sum(tv) / len(tv)
         variants[name] = {"precision": prec, "basis": basis, "outer": outer, "fused_vcycle": fz,
-                          "spatial_solver": spatial, "variant": fac, "setup_ms": sv_setup_ms,
+                          "spatial_solver": spatial, "variant": fac, "space_ratio": sratio,
+                          "levels": "".join(k for _, _, k in sv.level_shapes()[1:]),
+                          "setup_ms": sv_setup_ms,
                           "ms_per_step": msv,
                           "value": sv.ndofs * world / (msv / 1e3),
                           "iterations": iv[-1]["iterations"],

@@ -151,6 +151,18 @@ typedef struct {
                              (12 for 1e-4).  Systems that converge earlier
                              stop updating; the steps always run, so the
                              smoother replays as one CUDA graph             */
+    double space_ratio;   /* 0 (default): coarsen in time only (slab pairs).
+                             > 0 (ST_BASIS_NODAL): before merging slabs, halve
+                             every axis' spans while the level's
+                             tau / h_x^2 (slab length over the square of the
+                             largest element) exceeds space_ratio and the
+                             spans stay even and >= 4 (Sec. 3.1's multigrid
+                             coarsens in space and time; the rule is ours):
+                             space levels keep the slabs, prolongation
+                             P = I (x) P_z (x) P_y (x) P_x by B-spline knot
+                             insertion, restriction P^T, coarse operators
+                             rediscretised on the coarse grid (= Galerkin,
+                             the spaces are nested)                          */
 } st_options;
 
 typedef struct {
@@ -420,6 +432,12 @@ int st_time_spectrum(st_handle h, int lvl, double *lam_re, double *lam_im, doubl
 /* The time prolongation P_t (2 nt x nt, row-major) that expresses one coarse
  * slab in the bases of the two fine slabs it merges (Sec. 3.1). */
 int st_time_prolongation(st_handle h, int *nt, double *Pt);
+
+/* Shape of multigrid level lvl (0 = finest): slabs per right-hand side,
+ * knot spans per axis (spans[3], unused axes 1) and whether the level was
+ * obtained from the previous one by halving the spans (*space_step = 1) or
+ * by merging slab pairs (0; level 0: 0).  Any output may be NULL. */
+int st_level_shape(st_handle h, int lvl, int *slabs, int *spans, int *space_step);
 
 /* Message of the last failure on the calling thread ("" if none). */
 const char *st_last_error(void);

@@ -129,6 +129,29 @@ void space_matrices(int s, int p, Mat &M1, Mat &K1) {
         }
 }
 
+void space_prolongation(int s, int p, Mat &Px) {
+    // interior functions: fine n_f = s + p - 2 on s spans, coarse n_c on s/2;
+    // a coarse interior B-spline vanishes at both ends, so it is a combination
+    // of the fine interior ones; collocation at their Greville abscissae
+    // (Schoenberg-Whitney: the collocation matrix is nonsingular) finds it
+    const std::vector<double> tf = open_knots(0.0, 1.0, s, p);
+    const std::vector<double> tc = open_knots(0.0, 1.0, s / 2, p);
+    const int nf = s + p - 2, nc = s / 2 + p - 2;
+    Mat Bf((size_t)nf * nf), Bc((size_t)nf * nc);
+    std::vector<double> v, d;
+    for (int m = 0; m < nf; ++m) {
+        double g = 0.0;  // Greville abscissa of fine function m + 1
+        for (int k = 1; k <= p; ++k) g += tf[m + 1 + k];
+        g = (p > 0) ? g / p : tf[m + 1];
+        eval_basis(tf, p, g, v, d);
+        for (int a = 0; a < nf; ++a) Bf[(size_t)m * nf + a] = v[a + 1];
+        eval_basis(tc, p, g, v, d);
+        for (int b = 0; b < nc; ++b) Bc[(size_t)m * nc + b] = v[b + 1];
+    }
+    lu_solve(nf, nc, Bf, Bc);
+    Px = Bc;
+}
+
 void time_matrices(double tau, int ne, int p, double delta, Mat &Kt, Mat &Mt) {
     const std::vector<double> t = open_knots(0.0, tau, ne, p);
     const int nt = ne + p;

@@ -32,6 +32,10 @@ void eval_basis(const std::vector<double> &knots, int p, double x,
 // spans, degree p, first and last basis function removed: n = s + p - 2.
 void space_matrices(int s, int p, Mat &M1, Mat &K1);
 
+// Px (n_f x n_c, row-major): the interior B-splines of s/2 spans on (0,1)
+// in the interior B-splines of s spans (s even; nested spaces, so exact).
+void space_prolongation(int s, int p, Mat &Px);
+
 // K_t, M_t (Eq. 2.6) on one slab of length tau with ne elements, SUPG
 // weight delta = theta*h: nt = ne + p.
 void time_matrices(double tau, int ne, int p, double delta, Mat &Kt, Mat &Mt);

@@ -209,6 +209,20 @@ __global__ void k_update(T *__restrict__ u, const T *__restrict__ z,
     }
 }
 
+// y += x (the space prolongation's correction)
+template <typename T>
+__global__ void k_add(T *__restrict__ y, const T *__restrict__ x, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] += x[i];
+}
+
+template <typename T>
+cudaError_t launch_add(T *y, const T *x, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_add<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, n);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_update(T *u, const T *z, const SchurCoefs<T> &sc, T omega, const Grid &g,
                           long long nslabs, int overwrite, cudaStream_t s) {
@@ -305,7 +319,8 @@ cudaError_t launch_prolong_add(const T *ec, T *uf, const ProlongCoefs<T> &pc, co
     template cudaError_t launch_restrict<T>(const T *, T *, const ProlongCoefs<T> &,            \
                                             const Grid &, long long, cudaStream_t);             \
     template cudaError_t launch_prolong_add<T>(const T *, T *, const ProlongCoefs<T> &,         \
-                                               const Grid &, long long, cudaStream_t);
+                                               const Grid &, long long, cudaStream_t);         \
+    template cudaError_t launch_add<T>(T *, const T *, long long, cudaStream_t);
 ST_INST(double)
 ST_INST(float)
 #undef ST_INST

@@ -51,6 +51,8 @@ int fail(int code, const char *fmt, ...) {
 
 struct LevelHost {
     int nslab;  // slabs per problem
+    int sp = 0;          // index of the level's spatial grid (st_handle_s::ls)
+    bool xstep = false;  // obtained from the previous level by halving the spans
     double tau;
     Mat Kt, Mt, X, Z, Y;  // real Schur factors (Sec. 3.5)
     std::vector<int> blk;
@@ -97,6 +99,21 @@ struct MrWork {
     long long cap = 0;  // systems
 };
 
+// One spatial grid of the multigrid hierarchy: 1D factors per axis (K1 U =
+// M1 U Lambda, U^T M1 U = I), their bands, and -- when a coarser grid follows
+// -- the 1D prolongations Pc[a] (this grid's n x the coarser grid's n) that
+// express the coarser B-splines in this grid's (knot insertion).
+struct LevelSpace {
+    int spans[3] = {1, 1, 1}, n[3] = {1, 1, 1};
+    Grid g{};
+    Mat M1[3], K1[3], U[3], Pc[3];
+    std::vector<double> lam[3], bandM[3], bandK[3];
+    DevSpace<double> s64;
+    DevSpace<float> s32;
+    const double *P64[3] = {nullptr, nullptr, nullptr};
+    const float *P32[3] = {nullptr, nullptr, nullptr};
+};
+
 }  // namespace
 
 struct st_handle_s {
@@ -137,6 +154,8 @@ struct st_handle_s {
     Work<float> w32;
     MrWork<double> mr64;
     MrWork<float> mr32;
+    std::vector<LevelSpace> ls;   // spatial grids, finest first
+    void *xtmp = nullptr;         // scratch of level-0 size for space transfers
     // per-kernel-class profiling (CUDA events around each launch)
     struct ProfRec {
         int cls;
@@ -253,34 +272,80 @@ int upload(st_handle h, const std::vector<double> &src, const T **out) {
 }
 
 template <typename T>
-int upload_space(st_handle h, DevSpace<T> &ds, const std::vector<double> bandM[3],
-                 const std::vector<double> bandK[3]) {
+int upload_space(st_handle h, DevSpace<T> &ds, const LevelSpace &S) {
     for (int a = 0; a < h->dim; ++a) {
-        const int n = h->n[a];
-        CKS(upload<T>(h, bandM[a], &ds.bands.M[a]));
-        CKS(upload<T>(h, bandK[a], &ds.bands.K[a]));
-        CKS(upload<T>(h, h->U[a], &ds.U[a]));
+        const int n = S.n[a];
+        CKS(upload<T>(h, S.bandM[a], &ds.bands.M[a]));
+        CKS(upload<T>(h, S.bandK[a], &ds.bands.K[a]));
+        CKS(upload<T>(h, S.U[a], &ds.U[a]));
         Mat Ut(n * n);
         for (int i = 0; i < n; ++i)
-            for (int k = 0; k < n; ++k) Ut[k * n + i] = h->U[a][i * n + k];
+            for (int k = 0; k < n; ++k) Ut[k * n + i] = S.U[a][i * n + k];
         CKS(upload<T>(h, Ut, &ds.Ut[a]));
-        CKS(upload<T>(h, h->lam[a], &ds.lam[a]));
+        CKS(upload<T>(h, S.lam[a], &ds.lam[a]));
     }
     for (int a = h->dim; a < 3; ++a) {
         ds.bands.M[a] = ds.bands.K[a] = nullptr;
         ds.U[a] = ds.Ut[a] = ds.lam[a] = nullptr;
     }
     // mu_k = lambda_x[kx] + lambda_y[ky] + lambda_z[kz], k = (kz * ny + ky) * nx + kx
-    std::vector<double> mu((size_t)h->n[0] * h->n[1] * h->n[2]);
-    for (int kz = 0; kz < h->n[2]; ++kz)
-        for (int ky = 0; ky < h->n[1]; ++ky)
-            for (int kx = 0; kx < h->n[0]; ++kx) {
-                double m = h->lam[0][kx];
-                if (h->dim >= 2) m += h->lam[1][ky];
-                if (h->dim >= 3) m += h->lam[2][kz];
-                mu[((size_t)kz * h->n[1] + ky) * h->n[0] + kx] = m;
+    std::vector<double> mu((size_t)S.n[0] * S.n[1] * S.n[2]);
+    for (int kz = 0; kz < S.n[2]; ++kz)
+        for (int ky = 0; ky < S.n[1]; ++ky)
+            for (int kx = 0; kx < S.n[0]; ++kx) {
+                double m = S.lam[0][kx];
+                if (h->dim >= 2) m += S.lam[1][ky];
+                if (h->dim >= 3) m += S.lam[2][kz];
+                mu[((size_t)kz * S.n[1] + ky) * S.n[0] + kx] = m;
             }
     CKS(upload<T>(h, mu, &ds.mu));
+    return ST_OK;
+}
+
+// Spatial factors of the grid with the given spans: M1, K1, the generalized
+// eigenpairs (checked), the bands of M1 and K1.
+int build_space(st_handle h, const int spans[3], LevelSpace &S) {
+    const int degree = h->p;
+    const int W = 2 * degree + 1;
+    for (int a = 0; a < 3; ++a) {
+        S.spans[a] = (a < h->dim) ? spans[a] : 1;
+        S.n[a] = (a < h->dim) ? spans[a] + degree - 2 : 1;
+    }
+    S.g.nx = S.n[0];
+    S.g.ny = S.n[1];
+    S.g.nz = S.n[2];
+    S.g.dim = h->dim;
+    S.g.p = degree;
+    S.g.nxyz = (long long)S.n[0] * S.n[1] * S.n[2];
+    for (int a = 0; a < h->dim; ++a) {
+        const int n = S.n[a];
+        host::space_matrices(S.spans[a], degree, S.M1[a], S.K1[a]);
+        std::string err;
+        if (!host::sym_gen_eig(n, S.K1[a], S.M1[a], S.U[a], S.lam[a], err))
+            return fail(ST_ERR_ILL_CONDITIONED, "space eigenproblem axis %d: %s", a, err.c_str());
+        // checks: K1 U = M1 U Lambda, U^T M1 U = I
+        Mat MU = host::matmul(n, S.M1[a], S.U[a]);
+        Mat KU = host::matmul(n, S.K1[a], S.U[a]);
+        double r1 = 0, r2 = 0;
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < n; ++k) {
+                r1 = std::max(r1, std::fabs(KU[i * n + k] - MU[i * n + k] * S.lam[a][k]));
+                double sum = 0;
+                for (int j = 0; j < n; ++j) sum += S.U[a][j * n + i] * MU[j * n + k];
+                r2 = std::max(r2, std::fabs(sum - (i == k ? 1.0 : 0.0)));
+            }
+        if (r1 > 1e-9 * S.lam[a][n - 1] || r2 > 1e-9)
+            return fail(ST_ERR_ILL_CONDITIONED, "space eigen residuals %.2e %.2e", r1, r2);
+        S.bandM[a].assign((size_t)n * W, 0.0);
+        S.bandK[a].assign((size_t)n * W, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int oo = -degree; oo <= degree; ++oo) {
+                const int j = i + oo;
+                if (j < 0 || j >= n) continue;
+                S.bandM[a][(size_t)i * W + oo + degree] = S.M1[a][i * n + j];
+                S.bandK[a][(size_t)i * W + oo + degree] = S.K1[a][i * n + j];
+            }
+    }
     return ST_OK;
 }
 
@@ -295,7 +360,7 @@ int alloc_work(st_handle h, Work<T> &w, bool level0) {
     w.u.assign(h->nlev, nullptr);
     w.f.assign(h->nlev, nullptr);
     for (int l = level0 ? 0 : 1; l < h->nlev; ++l) {
-        const size_t e = (size_t)h->lv[l].nslab * h->nt * h->g.nxyz * h->nrhs;
+        const size_t e = (size_t)h->lv[l].nslab * h->nt * h->ls[h->lv[l].sp].g.nxyz * h->nrhs;
         CKS(dalloc(h, e * sizeof(T), &p));
         w.u[l] = (T *)p;
         CKS(dalloc(h, e * sizeof(T), &p));
@@ -982,8 +1047,75 @@ int coarse_solve(st_handle h, int l, T *u, const T *f) {
 }
 
 // One V-cycle on level l for L_l u = f starting from u (zero_init: u = 0).
+// Makes level l's spatial grid and factors the handle's current ones for the
+// scope (every operator, transform and smoother reads h->g and the DevSpace
+// of its precision); restores the previous ones on exit.
+struct LevelCtx {
+    st_handle h;
+    Grid g;
+    DevSpace<double> s64;
+    DevSpace<float> s32;
+    LevelCtx(st_handle h_, int l) : h(h_), g(h_->g), s64(h_->s64), s32(h_->s32) {
+        const LevelSpace &S = h->ls[h->lv[l].sp];
+        h->g = S.g;
+        h->s64 = S.s64;
+        h->s32 = S.s32;
+    }
+    ~LevelCtx() {
+        h->g = g;
+        h->s64 = s64;
+        h->s32 = s32;
+    }
+};
+
+template <typename T>
+const T *const *prolong_mats(const LevelSpace &S);
+template <>
+const double *const *prolong_mats<double>(const LevelSpace &S) { return S.P64; }
+template <>
+const float *const *prolong_mats<float>(const LevelSpace &S) { return S.P32; }
+
+// Space transfer between level l (grid F) and level l + 1 (F's spans halved)
+// for `planes` time planes: restriction out = (P_z^T (x) P_y^T (x) P_x^T) in
+// (fine -> coarse), prolongation out = (P_z (x) P_y (x) P_x) in (coarse ->
+// fine), with the 1D knot-insertion matrices P_a of F; one strided GEMM per
+// axis, intermediates in t0 / t1, the last axis writes `out`.
+template <typename T>
+int space_transfer(st_handle h, int l, const T *in, T *t0, T *t1, T *out, bool restr,
+                   long long planes) {
+    const LevelSpace &F = h->ls[h->lv[l].sp], &Cs = h->ls[h->lv[l + 1].sp];
+    const T *const *P = prolong_mats<T>(F);
+    long long cur[3];
+    for (int a = 0; a < 3; ++a) cur[a] = restr ? F.n[a] : Cs.n[a];
+    const T *src = in;
+    for (int a = 0; a < h->dim; ++a) {
+        const int nf = F.n[a], nc = Cs.n[a];
+        const int nin = restr ? nf : nc, nout = restr ? nc : nf;
+        long long inner = 1, outer = planes;
+        for (int b = 0; b < a; ++b) inner *= cur[b];
+        for (int b = a + 1; b < 3; ++b) outer *= cur[b];
+        T *dst = (a == h->dim - 1) ? out : ((a % 2 == 0) ? t0 : t1);
+        const double E = (double)outer * inner * (nin + nout);
+        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * E, 2.0 * (double)outer * inner * nin * nout);
+        if (a == 0) {
+            // dst[o][j] = sum_k src[o][k] W[k][j]; W[k][j] = P[k][j] (restr), P[j][k] (prolong)
+            CK(launch_gemm_strided<T>(1, (int)outer, nout, nin, src, 0, nin, 1, P[a], 0,
+                                      restr ? nc : 1, restr ? 1 : nc, dst, 0, nout, 1, h->stream));
+        } else {
+            // dst[o][j][i] = sum_k W[k][j] src[o][k][i]
+            CK(launch_gemm_strided<T>((int)outer, nout, (int)inner, nin, P[a], 0, restr ? 1 : nc,
+                                      restr ? nc : 1, src, (long long)nin * inner, inner, 1, dst,
+                                      (long long)nout * inner, inner, 1, h->stream));
+        }
+        cur[a] = nout;
+        src = dst;
+    }
+    return ST_OK;
+}
+
 template <typename T>
 int vcycle(st_handle h, int l, T *u, const T *f, bool zero_init) {
+    LevelCtx ctx(h, l);
     const long long n_l = (long long)h->lv[l].nslab * h->nrhs * h->nt * h->g.nxyz;
     if (l == h->nlev - 1) return coarse_solve<T>(h, l, u, f);
     if (zero_init) CK(launch_zero<T>(u, n_l, h->stream));
@@ -991,17 +1123,27 @@ int vcycle(st_handle h, int l, T *u, const T *f, bool zero_init) {
     for (int k = 0; k < h->opt.nu1; ++k) CKS(smooth<T>(h, l, u, f, omega));
     Work<T> &w = work<T>(h);
     CKS(stencil<T>(h, l, u, f, w.w0, MODE_RES, false, 0, h->lv[l].nslab * h->nrhs));
-    const ProlongCoefs<T> pc = pack_prolong<T>(h);
-    const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
-    const double Ec = (double)nc * h->nt * h->g.nxyz;
-    {
-        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 3.0 * Ec, Ec * 4.0 * h->nt);
-        CK(launch_restrict<T>(w.w0, w.f[l + 1], pc, h->g, nc, h->stream));
-    }
-    CKS(vcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], true));
-    {
-        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 5.0 * Ec, Ec * 4.0 * h->nt);
-        CK(launch_prolong_add<T>(w.u[l + 1], u, pc, h->g, nc, h->stream));
+    if (h->lv[l + 1].xstep) {  // space coarsening: same slabs, spans halved
+        const long long planes = (long long)h->lv[l].nslab * h->nrhs * h->nt;
+        T *xt = static_cast<T *>(h->xtmp);
+        CKS(space_transfer<T>(h, l, w.w0, w.w1, xt, w.f[l + 1], true, planes));
+        CKS(vcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], true));
+        CKS(space_transfer<T>(h, l, w.u[l + 1], w.w1, xt, w.w0, false, planes));
+        KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 3.0 * n_l, 1.0 * n_l);
+        CK(launch_add<T>(u, w.w0, n_l, h->stream));
+    } else {
+        const ProlongCoefs<T> pc = pack_prolong<T>(h);
+        const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
+        const double Ec = (double)nc * h->nt * h->g.nxyz;
+        {
+            KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 3.0 * Ec, Ec * 4.0 * h->nt);
+            CK(launch_restrict<T>(w.w0, w.f[l + 1], pc, h->g, nc, h->stream));
+        }
+        CKS(vcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], true));
+        {
+            KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 5.0 * Ec, Ec * 4.0 * h->nt);
+            CK(launch_prolong_add<T>(w.u[l + 1], u, pc, h->g, nc, h->stream));
+        }
     }
     for (int k = 0; k < h->opt.nu2; ++k) CKS(smooth<T>(h, l, u, f, omega));
     return ST_OK;
@@ -1915,6 +2057,9 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         return fail(ST_ERR_INVALID_ARG, "inner_tol must be in (0, 1)");
     if (o.spatial_solver != ST_SPATIAL_FD && o.spatial_solver != ST_SPATIAL_MINRES)
         return fail(ST_ERR_INVALID_ARG, "bad spatial_solver");
+    if (!(o.space_ratio >= 0)) return fail(ST_ERR_INVALID_ARG, "space_ratio must be >= 0");
+    if (o.space_ratio > 0 && o.basis != ST_BASIS_NODAL)
+        return fail(ST_ERR_UNSUPPORTED, "space coarsening is built for the B-spline basis");
     if (o.spatial_solver == ST_SPATIAL_MINRES) {
         if (o.basis != ST_BASIS_NODAL)
             return fail(ST_ERR_UNSUPPORTED, "MinRes spatial solves are built for the B-spline basis");
@@ -1945,117 +2090,128 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     h->len = (long long)slabs * h->nt * h->g.nxyz;
     if (slabs > 65535 / h->nrhs) return fail(ST_ERR_UNSUPPORTED, "too many slabs x rhs");
 
-    // spatial factors
-    std::vector<double> bandM[3], bandK[3];
-    const int W = 2 * degree + 1;
+    // spatial factors of the finest grid (level 0); coarser grids are added
+    // below when the hierarchy coarsens in space
+    h->ls.clear();
+    h->ls.emplace_back();
+    CKS(build_space(h, h->spans, h->ls[0]));
     for (int a = 0; a < h->dim; ++a) {
-        const int n = h->n[a];
-        host::space_matrices(h->spans[a], degree, h->M1[a], h->K1[a]);
-        std::string err;
-        if (!host::sym_gen_eig(n, h->K1[a], h->M1[a], h->U[a], h->lam[a], err))
-            return fail(ST_ERR_ILL_CONDITIONED, "space eigenproblem axis %d: %s", a, err.c_str());
-        // checks: K1 U = M1 U Lambda, U^T M1 U = I
-        Mat MU = host::matmul(n, h->M1[a], h->U[a]);
-        Mat KU = host::matmul(n, h->K1[a], h->U[a]);
-        double r1 = 0, r2 = 0;
-        for (int i = 0; i < n; ++i)
-            for (int k = 0; k < n; ++k) {
-                r1 = std::max(r1, std::fabs(KU[i * n + k] - MU[i * n + k] * h->lam[a][k]));
-                double s = 0;
-                for (int j = 0; j < n; ++j) s += h->U[a][j * n + i] * MU[j * n + k];
-                r2 = std::max(r2, std::fabs(s - (i == k ? 1.0 : 0.0)));
-            }
-        if (r1 > 1e-9 * h->lam[a][n - 1] || r2 > 1e-9)
-            return fail(ST_ERR_ILL_CONDITIONED, "space eigen residuals %.2e %.2e", r1, r2);
-        bandM[a].assign((size_t)n * W, 0.0);
-        bandK[a].assign((size_t)n * W, 0.0);
-        for (int i = 0; i < n; ++i)
-            for (int oo = -degree; oo <= degree; ++oo) {
-                const int j = i + oo;
-                if (j < 0 || j >= n) continue;
-                bandM[a][(size_t)i * W + oo + degree] = h->M1[a][i * n + j];
-                bandK[a][(size_t)i * W + oo + degree] = h->K1[a][i * n + j];
-            }
+        h->M1[a] = h->ls[0].M1[a];
+        h->K1[a] = h->ls[0].K1[a];
+        h->U[a] = h->ls[0].U[a];
+        h->lam[a] = h->ls[0].lam[a];
     }
     // time factors per level (theta*h frozen at the finest value)
     const double tau0 = o.T / slabs;
     const double delta = o.theta * tau0 / o.ne_per_slab;
     int Nl = slabs;
     const int nt = h->nt;
+    bool space_step = false;
     for (;;) {
-        LevelHost L;
-        L.nslab = Nl;
-        L.tau = o.T / Nl;
-        host::time_matrices(L.tau, o.ne_per_slab, degree, delta, L.Kt, L.Mt);
-        Mat G = L.Kt;  // G = M_t^{-1} K_t
-        if (!host::lu_solve(nt, nt, L.Mt, G)) return fail(ST_ERR_NOT_POSITIVE, "M_t is singular");
-        std::string err;
-        if (!host::real_schur(nt, G, L.X, L.Z, L.blk, err))
-            return fail(ST_ERR_ILL_CONDITIONED, "real Schur: %s", err.c_str());
-        // MinRes block solves need the standard 2x2 blocks of Sec. 3.5
-        if (o.spatial_solver == ST_SPATIAL_MINRES) host::standardize_schur(nt, L.X, L.Z, L.blk);
-        // Re lambda > 0 check (Sec. 3.2: a posteriori control of positivity)
-        for (int i = 0; i < nt; ++i) {
-            double re;
-            if (i + 1 < nt && L.blk[i + 1]) {
-                re = 0.5 * (L.Z[i * nt + i] + L.Z[(i + 1) * nt + i + 1]);
+        if (space_step) {  // same slabs and time factors, spatial grid halved
+            LevelHost L = h->lv.back();
+            L.sp = (int)h->ls.size() - 1;
+            L.xstep = true;
+            h->lv.push_back(L);
+        } else {
+            LevelHost L;
+            L.nslab = Nl;
+            L.sp = (int)h->ls.size() - 1;
+            L.tau = o.T / Nl;
+            host::time_matrices(L.tau, o.ne_per_slab, degree, delta, L.Kt, L.Mt);
+            Mat G = L.Kt;  // G = M_t^{-1} K_t
+            if (!host::lu_solve(nt, nt, L.Mt, G)) return fail(ST_ERR_NOT_POSITIVE, "M_t is singular");
+            std::string err;
+            if (!host::real_schur(nt, G, L.X, L.Z, L.blk, err))
+                return fail(ST_ERR_ILL_CONDITIONED, "real Schur: %s", err.c_str());
+            // MinRes block solves need the standard 2x2 blocks of Sec. 3.5
+            if (o.spatial_solver == ST_SPATIAL_MINRES) host::standardize_schur(nt, L.X, L.Z, L.blk);
+            // Re lambda > 0 check (Sec. 3.2: a posteriori control of positivity)
+            for (int i = 0; i < nt; ++i) {
+                double re;
+                if (i + 1 < nt && L.blk[i + 1]) {
+                    re = 0.5 * (L.Z[i * nt + i] + L.Z[(i + 1) * nt + i + 1]);
+                    if (!(re > 0)) return fail(ST_ERR_NOT_POSITIVE, "Re lambda <= 0 on level with %d slabs (use a smaller theta)", Nl);
+                    ++i;
+                    continue;
+                }
+                re = L.Z[i * nt + i];
                 if (!(re > 0)) return fail(ST_ERR_NOT_POSITIVE, "Re lambda <= 0 on level with %d slabs (use a smaller theta)", Nl);
-                ++i;
-                continue;
             }
-            re = L.Z[i * nt + i];
-            if (!(re > 0)) return fail(ST_ERR_NOT_POSITIVE, "Re lambda <= 0 on level with %d slabs (use a smaller theta)", Nl);
-        }
-        // diagonalisation from the Schur form (Sec. 3.3): X, Y = (M_t X)^{-1}
-        {
-            std::string e2;
-            L.eig_ok = host::schur_eigvecs(nt, L.X, L.Z, L.blk, L.lre, L.lim, L.Xre, L.Xim, e2);
-            if (L.eig_ok) {
-                Mat MXr = host::matmul(nt, L.Mt, L.Xre), MXi = host::matmul(nt, L.Mt, L.Xim);
-                L.eig_ok = host::complex_inverse(nt, MXr, MXi, L.Yre, L.Yim);
-                L.condX = host::complex_cond2(nt, L.Xre, L.Xim);
+            // diagonalisation from the Schur form (Sec. 3.3): X, Y = (M_t X)^{-1}
+            {
+                std::string e2;
+                L.eig_ok = host::schur_eigvecs(nt, L.X, L.Z, L.blk, L.lre, L.lim, L.Xre, L.Xim, e2);
+                if (L.eig_ok) {
+                    Mat MXr = host::matmul(nt, L.Mt, L.Xre), MXi = host::matmul(nt, L.Mt, L.Xim);
+                    L.eig_ok = host::complex_inverse(nt, MXr, MXi, L.Yre, L.Yim);
+                    L.condX = host::complex_cond2(nt, L.Xre, L.Xim);
+                }
+                if (o.variant == ST_EIG) {
+                    if (!L.eig_ok) return fail(ST_ERR_ILL_CONDITIONED, "diagonalisation failed: %s", e2.c_str());
+                    if (!(L.condX <= 1e8))
+                        return fail(ST_ERR_ILL_CONDITIONED, "cond(X) = %.3e > 1e8 on the level with %d slabs "
+                                    "(use the real Schur variant)", L.condX, Nl);
+                }
             }
-            if (o.variant == ST_EIG) {
-                if (!L.eig_ok) return fail(ST_ERR_ILL_CONDITIONED, "diagonalisation failed: %s", e2.c_str());
-                if (!(L.condX <= 1e8))
-                    return fail(ST_ERR_ILL_CONDITIONED, "cond(X) = %.3e > 1e8 on the level with %d slabs "
-                                "(use the real Schur variant)", L.condX, Nl);
+            // complex Schur form (Sec. 3.4) from the real one, Y_c = (M_t Q_c)^{-1}
+            if (o.variant == ST_CSCHUR) {
+                std::string e3;
+                if (!host::complex_schur(nt, L.X, L.Z, L.blk, L.Qcre, L.Qcim, L.Tcre, L.Tcim, e3))
+                    return fail(ST_ERR_ILL_CONDITIONED, "complex Schur: %s", e3.c_str());
+                Mat MQr = host::matmul(nt, L.Mt, L.Qcre), MQi = host::matmul(nt, L.Mt, L.Qcim);
+                if (!host::complex_inverse(nt, MQr, MQi, L.Ycre, L.Ycim))
+                    return fail(ST_ERR_ILL_CONDITIONED, "M_t Q_c singular");
+                // K_t Q_c = M_t Q_c T_c
+                Mat KQr = host::matmul(nt, L.Kt, L.Qcre), KQi = host::matmul(nt, L.Kt, L.Qcim);
+                Mat A1 = host::matmul(nt, MQr, L.Tcre), A2 = host::matmul(nt, MQi, L.Tcim);
+                Mat B1 = host::matmul(nt, MQr, L.Tcim), B2 = host::matmul(nt, MQi, L.Tcre);
+                double rc = 0.0;
+                for (int i = 0; i < nt * nt; ++i)
+                    rc = std::max(rc, std::max(std::fabs(KQr[i] - (A1[i] - A2[i])),
+                                               std::fabs(KQi[i] - (B1[i] + B2[i]))));
+                const double sc = host::frob(L.Kt) + host::frob(L.Mt) * (host::frob(L.Tcre) + host::frob(L.Tcim));
+                if (!(rc <= 1e-12 * nt * sc))
+                    return fail(ST_ERR_ILL_CONDITIONED, "complex Schur residual %.3e", rc);
             }
+            // Y = (M_t X)^{-1}
+            Mat MX = host::matmul(nt, L.Mt, L.X);
+            L.Y.assign(nt * nt, 0.0);
+            for (int i = 0; i < nt; ++i) L.Y[i * nt + i] = 1.0;
+            if (!host::lu_solve(nt, nt, MX, L.Y)) return fail(ST_ERR_ILL_CONDITIONED, "M_t X singular");
+            // check K_t X = M_t X Z
+            Mat KX = host::matmul(nt, L.Kt, L.X), MXZ = host::matmul(nt, MX, L.Z);
+            double rr = 0;
+            for (int i = 0; i < nt * nt; ++i) rr = std::max(rr, std::fabs(KX[i] - MXZ[i]));
+            // backward-error scale of K_t X = M_t X Z: ||K_t|| + ||M_t|| ||Z||
+            const double scale = host::frob(L.Kt) + host::frob(L.Mt) * host::frob(L.Z);
+            if (rr > 1e-12 * nt * scale)
+                return fail(ST_ERR_ILL_CONDITIONED, "time factor residual %.2e (scale %.2e)", rr, scale);
+            h->lv.push_back(L);
         }
-        // complex Schur form (Sec. 3.4) from the real one, Y_c = (M_t Q_c)^{-1}
-        if (o.variant == ST_CSCHUR) {
-            std::string e3;
-            if (!host::complex_schur(nt, L.X, L.Z, L.blk, L.Qcre, L.Qcim, L.Tcre, L.Tcim, e3))
-                return fail(ST_ERR_ILL_CONDITIONED, "complex Schur: %s", e3.c_str());
-            Mat MQr = host::matmul(nt, L.Mt, L.Qcre), MQi = host::matmul(nt, L.Mt, L.Qcim);
-            if (!host::complex_inverse(nt, MQr, MQi, L.Ycre, L.Ycim))
-                return fail(ST_ERR_ILL_CONDITIONED, "M_t Q_c singular");
-            // K_t Q_c = M_t Q_c T_c
-            Mat KQr = host::matmul(nt, L.Kt, L.Qcre), KQi = host::matmul(nt, L.Kt, L.Qcim);
-            Mat A1 = host::matmul(nt, MQr, L.Tcre), A2 = host::matmul(nt, MQi, L.Tcim);
-            Mat B1 = host::matmul(nt, MQr, L.Tcim), B2 = host::matmul(nt, MQi, L.Tcre);
-            double rc = 0.0;
-            for (int i = 0; i < nt * nt; ++i)
-                rc = std::max(rc, std::max(std::fabs(KQr[i] - (A1[i] - A2[i])),
-                                           std::fabs(KQi[i] - (B1[i] + B2[i]))));
-            const double sc = host::frob(L.Kt) + host::frob(L.Mt) * (host::frob(L.Tcre) + host::frob(L.Tcim));
-            if (!(rc <= 1e-12 * nt * sc))
-                return fail(ST_ERR_ILL_CONDITIONED, "complex Schur residual %.3e", rc);
+        // next step: halve the spans while the slabs are diffusion-dominated
+        // (tau / h_x^2 above opt.space_ratio; h_x = the largest element),
+        // else merge slab pairs; stop at one slab
+        const LevelSpace &S = h->ls.back();
+        int smin = S.spans[0];
+        bool halvable = true;
+        for (int a = 0; a < h->dim; ++a) {
+            smin = std::min(smin, S.spans[a]);
+            if (S.spans[a] % 2 != 0 || S.spans[a] / 2 < 2) halvable = false;
         }
-        // Y = (M_t X)^{-1}
-        Mat MX = host::matmul(nt, L.Mt, L.X);
-        L.Y.assign(nt * nt, 0.0);
-        for (int i = 0; i < nt; ++i) L.Y[i * nt + i] = 1.0;
-        if (!host::lu_solve(nt, nt, MX, L.Y)) return fail(ST_ERR_ILL_CONDITIONED, "M_t X singular");
-        // check K_t X = M_t X Z
-        Mat KX = host::matmul(nt, L.Kt, L.X), MXZ = host::matmul(nt, MX, L.Z);
-        double rr = 0;
-        for (int i = 0; i < nt * nt; ++i) rr = std::max(rr, std::fabs(KX[i] - MXZ[i]));
-        // backward-error scale of K_t X = M_t X Z: ||K_t|| + ||M_t|| ||Z||
-        const double scale = host::frob(L.Kt) + host::frob(L.Mt) * host::frob(L.Z);
-        if (rr > 1e-12 * nt * scale)
-            return fail(ST_ERR_ILL_CONDITIONED, "time factor residual %.2e (scale %.2e)", rr, scale);
-        h->lv.push_back(L);
+        const double ratio = (o.T / Nl) * (double)smin * smin;
+        if (o.space_ratio > 0 && ratio > o.space_ratio && halvable) {
+            int cs[3] = {1, 1, 1};
+            for (int a = 0; a < h->dim; ++a) cs[a] = S.spans[a] / 2;
+            LevelSpace C;
+            CKS(build_space(h, cs, C));
+            LevelSpace &F = h->ls.back();
+            for (int a = 0; a < h->dim; ++a) host::space_prolongation(F.spans[a], degree, F.Pc[a]);
+            h->ls.push_back(std::move(C));
+            space_step = true;
+            continue;
+        }
+        space_step = false;
         if (Nl % 2 != 0 || Nl == 1) break;
         Nl /= 2;
     }
@@ -2080,8 +2236,22 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         h->tc_err = (int *)pe;
         CK(cudaMemset(h->tc_err, 0, sizeof(int)));
     }
-    CKS(upload_space<double>(h, h->s64, bandM, bandK));
-    if (h->mixed) CKS(upload_space<float>(h, h->s32, bandM, bandK));
+    for (size_t k = 0; k < h->ls.size(); ++k) {
+        LevelSpace &S = h->ls[k];
+        CKS(upload_space<double>(h, S.s64, S));
+        if (h->mixed) CKS(upload_space<float>(h, S.s32, S));
+        for (int a = 0; a < h->dim && k + 1 < h->ls.size(); ++a) {
+            CKS(upload<double>(h, S.Pc[a], &S.P64[a]));
+            if (h->mixed) CKS(upload<float>(h, S.Pc[a], &S.P32[a]));
+        }
+    }
+    h->s64 = h->ls[0].s64;
+    if (h->mixed) h->s32 = h->ls[0].s32;
+    if (h->ls.size() > 1) {
+        void *px;
+        CKS(dalloc(h, (size_t)h->len * h->nrhs * (h->mixed ? sizeof(float) : sizeof(double)), &px));
+        h->xtmp = px;
+    }
     if (h->mixed) {
         CKS(alloc_work<float>(h, h->w32, true));
         // the FP64 outer residual needs no FP64 V-cycle buffers except scratch
@@ -2195,6 +2365,7 @@ void st_options_default(st_options *o) {
     o->spatial_solver = ST_SPATIAL_FD;
     o->minres_tol = 1e-4;
     o->minres_maxit = 0;
+    o->space_ratio = 0.0;
 }
 
 const char *st_last_error(void) { return g_err.c_str(); }
@@ -2601,6 +2772,17 @@ int st_time_prolongation(st_handle h, int *nt, double *Pt) {
     if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
     if (nt) *nt = h->nt;
     if (Pt) std::memcpy(Pt, h->Pt.data(), sizeof(double) * 2 * h->nt * h->nt);
+    return ST_OK;
+}
+
+int st_level_shape(st_handle h, int lvl, int *slabs, int *spans, int *space_step) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (lvl < 0 || lvl >= h->nlev) return fail(ST_ERR_INVALID_ARG, "level %d out of range", lvl);
+    const LevelHost &L = h->lv[lvl];
+    if (slabs) *slabs = L.nslab;
+    if (spans)
+        for (int a = 0; a < 3; ++a) spans[a] = h->ls[L.sp].spans[a];
+    if (space_step) *space_step = L.xstep ? 1 : 0;
     return ST_OK;
 }
 

@@ -131,6 +131,9 @@ cudaError_t launch_restrict(const T *rf, T *fc, const ProlongCoefs<T> &pc, const
 template <typename T>
 cudaError_t launch_prolong_add(const T *ec, T *uf, const ProlongCoefs<T> &pc, const Grid &g,
                                long long ncoarse, cudaStream_t s);
+// y += x
+template <typename T>
+cudaError_t launch_add(T *y, const T *x, long long n, cudaStream_t s);
 
 // ---- tensor-core transforms (kernels_tc.cu) ----
 // kind: 2 = TF32, 1 = BF16, 3 = split TF32 (hi*hi + hi*lo + lo*hi, FP32

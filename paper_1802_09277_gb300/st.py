@@ -30,7 +30,7 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_load_gaussians", "st_smooth",
            "st_smooth_static", "st_block_minres", "st_vcycle",
            "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
-           "st_time_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
+           "st_time_prolongation", "st_level_shape", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_poll", "st_serve_wait", "st_serve_stop"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
                 "vector", "dot", "tc", "spec", "stencil_df", "minres"]
@@ -45,7 +45,8 @@ class StOptions(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("use_graphs", ctypes.c_int),
                 ("variant", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("fused_vcycle", ctypes.c_int), ("spatial_solver", ctypes.c_int),
-                ("minres_tol", ctypes.c_double), ("minres_maxit", ctypes.c_int)]
+                ("minres_tol", ctypes.c_double), ("minres_maxit", ctypes.c_int),
+                ("space_ratio", ctypes.c_double)]
 
 
 class StSolveInfo(ctypes.Structure):
@@ -113,6 +114,7 @@ def load():
         "st_smooth_static": (I, [P, P, P, I, P]),
         "st_block_minres": (I, [P, D, D, D, P, P, I, D, I, ip, dp]),
         "st_vcycle": (I, [P, P, P]),
+        "st_level_shape": (I, [P, I, ip, ip, ip]),
         "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
         "st_autotune": (I, [P, ip, dp]),
         "st_profile": (I, [P, I]),
@@ -337,6 +339,18 @@ class Solver:
         _check(_lib.st_space_factors(self._h, int(axis), ctypes.byref(k), cp(M1), cp(K1), cp(U),
                                      cp(lam)))
         return {"M1": M1, "K1": K1, "U": U, "lam": lam}
+
+    def level_shapes(self):
+        """[(slabs, spans (d entries), 'x' | 't' | '-') per level]: the step
+        from the previous level ('-' on level 0)."""
+        out = []
+        for lvl in range(self.nlevels):
+            n = ctypes.c_int()
+            sp = (ctypes.c_int * 3)()
+            x = ctypes.c_int()
+            _check(_lib.st_level_shape(self._h, lvl, ctypes.byref(n), sp, ctypes.byref(x)))
+            out.append((n.value, tuple(sp[:self.dim]), "-" if lvl == 0 else ("x" if x.value else "t")))
+        return out
 
     def time_prolongation(self):
         import numpy as np

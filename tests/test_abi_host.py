@@ -242,3 +242,27 @@ def test_minres_option_errors(st):
         st.Solver(2, 2, (6, 6), 4, host_only=True, spatial_solver=7)
     # the FD default ignores the MinRes fields
     st.Solver(2, 2, (6, 6), 4, host_only=True, minres_tol=0.0).close()
+
+
+@pytest.mark.parametrize("d,spans,p,N,ratio", [(1, (64,), 2, 16, 1.0), (2, (16, 16), 2, 16, 1.0),
+                                               (2, (16, 12), 3, 8, 4.0), (1, (32,), 2, 64, 0.0),
+                                               (3, (8, 8, 8), 1, 8, 2.0), (1, (6,), 2, 4, 1.0)])
+def test_space_time_hierarchy_matches_oracle(st, d, spans, p, N, ratio):
+    """The library's coarsening schedule (space while tau / h_x^2 exceeds
+    space_ratio and the spans halve, else slab pairs) is the oracle's."""
+    pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+    H = S.Hierarchy(pr, space_ratio=ratio)
+    s = st.Solver(d, p, spans, N, host_only=True, space_ratio=ratio)
+    shapes = s.level_shapes()
+    assert [k for _, _, k in shapes[1:]] == H.kinds
+    assert [(n, sp) for n, sp, _ in shapes] == [(q.N, q.spans) for q in H.probs]
+    s.close()
+
+
+def test_space_ratio_option_errors(st):
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 2, (8, 8), 4, host_only=True, space_ratio=1.0, basis="spectral")
+    assert e.value.code == st.ST_ERR_UNSUPPORTED
+    with pytest.raises(st.StError) as e:
+        st.Solver(2, 2, (8, 8), 4, host_only=True, space_ratio=-1.0)
+    assert e.value.code == st.ST_ERR_INVALID_ARG
