@@ -404,7 +404,8 @@ int st_serve_stop(st_server s);
 
 /* Host copies of the FP64 setup factors, for inspection and tests.
  * Time factors of level lvl (0 = finest), each nt x nt row-major, nt <= 8:
- * K_t, M_t, X (= Q, orthogonal), Z (quasi upper triangular Schur form),
+ * K_t, M_t, X (= Q, orthogonal), Z (quasi upper triangular Schur form; with
+ * ST_SPATIAL_MINRES its 2x2 blocks are standardised to [[a, b1], [b2, a]]),
  * Y = (M_t X)^{-1}; any output may be NULL. */
 int st_time_factors(st_handle h, int lvl, int *nt, double *Kt, double *Mt,
                     double *X, double *Z, double *Y);

@@ -36,6 +36,7 @@ def main():
     ap.add_argument("--spatial-solver", default="fd", choices=["fd", "minres"])
     ap.add_argument("--minres-tol", type=float, default=1e-4)
     ap.add_argument("--theta", type=float, default=1.0)
+    ap.add_argument("--space-ratio", type=float, default=0.0)
     args = ap.parse_args()
 
     import torch
@@ -47,7 +48,7 @@ def main():
     s = st.Solver(args.dim, args.degree, args.spans, args.slabs, ne_per_slab=args.ne,
                   precision=args.precision, basis=args.basis, outer=args.outer,
                   fused_vcycle=args.fused, spatial_solver=args.spatial_solver,
-                  minres_tol=args.minres_tol, theta=args.theta)
+                  minres_tol=args.minres_tol, theta=args.theta, space_ratio=args.space_ratio)
     n = s.ndofs
     x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
     f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")
@@ -67,8 +68,14 @@ def main():
         ev[1].record()
         ev[1].synchronize()
         times.append(ev[0].elapsed_time(ev[1]))
-    print("op=%s dofs=%d precision=%s mean_ms=%.4f" % (args.op, n, args.precision,
-                                                      sum(times) / len(times)))
+    extra = ""
+    if args.op == "solve":
+        u = torch.zeros_like(f)
+        info = s.solve(f, u, tol=args.tol)
+        levels = "".join(k for _, _, k in s.level_shapes()[1:])
+        extra = " iterations=%d levels=%s min_ms=%.4f" % (info["iterations"], levels, min(times))
+    print("op=%s dofs=%d precision=%s mean_ms=%.4f%s" % (args.op, n, args.precision,
+                                                        sum(times) / len(times), extra))
     s.close()
 
 
