@@ -31,6 +31,7 @@
 //                     u_n = A^{-1} (f_n + e_0 u_{n-1, last}) over its slabs
 //  k_lv_res_restrict  residual and restriction without smoothing (nu1 = 0)
 //  k_lv_op            the eigenbasis operator L^ (or f - L^ u) pointwise
+#include "pdl.cuh"
 #include "spec_common.cuh"
 
 namespace st {
@@ -134,6 +135,8 @@ __global__ void __launch_bounds__(256)
     k_lv_smooth(const T *__restrict__ uin, T *__restrict__ uout, const T *__restrict__ f,
                 const T *__restrict__ inv, long long S, T omega, int spp, long long nslabs,
                 int zero) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = slab_index();
     if (k >= S || n >= nslabs) return;
@@ -167,6 +170,8 @@ __global__ void __launch_bounds__(256)
               T *__restrict__ fc, const T *__restrict__ inv, const T *__restrict__ mu_tab,
               long long S, const __grid_constant__ SpecCoefs<T> c,
               const __grid_constant__ ProlongCoefs<T> pc, T omega, int spp, long long ncoarse) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long mc = slab_index();
     if (k >= S || mc >= ncoarse) return;
@@ -221,6 +226,8 @@ __global__ void __launch_bounds__(256)
     k_lv_down0(T *__restrict__ uout, const T *__restrict__ f, T *__restrict__ fc,
                const T *__restrict__ inv, long long S, const __grid_constant__ ProlongCoefs<T> pc,
                T omega, int spp, long long ncoarse) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long mc0 = slab_index() * PP;
     if (k >= S || mc0 >= ncoarse) return;
@@ -275,6 +282,8 @@ __global__ void __launch_bounds__(256)
     k_lv_up(const T *__restrict__ ec, const T *__restrict__ uin, T *__restrict__ uout,
              const T *__restrict__ f, const T *__restrict__ inv, long long S,
              const __grid_constant__ ProlongCoefs<T> pc, T omega, int spp, long long ncoarse) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long mc0 = slab_index() * PP;
     if (k >= S || mc0 >= ncoarse) return;
@@ -336,6 +345,8 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(256)
     k_lv_coarse(T *__restrict__ u, const T *__restrict__ f, const T *__restrict__ inv, long long S,
                 int spp, long long nprob) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long q = slab_index();
     if (k >= S || q >= nprob) return;
@@ -359,6 +370,8 @@ __global__ void __launch_bounds__(256)
                       const T *__restrict__ mu_tab, long long S,
                       const __grid_constant__ SpecCoefs<T> c,
                       const __grid_constant__ ProlongCoefs<T> pc, int spp, long long ncoarse) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long mc = slab_index();
     if (k >= S || mc >= ncoarse) return;
@@ -383,6 +396,8 @@ __global__ void __launch_bounds__(256)
     k_lv_op(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out,
             const T *__restrict__ mu_tab, long long S, const __grid_constant__ SpecCoefs<T> c,
             int spp, long long nslabs, int res) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = slab_index();
     if (k >= S || n >= nslabs) return;
@@ -423,6 +438,8 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(128)
     k_lv_tail(const T *__restrict__ fin, T *__restrict__ uout, const __grid_constant__ TailArgs<T> ta,
               const __grid_constant__ ProlongCoefs<T> pc, long long S, int n0, T omega) {
+    griddep_wait();
+    griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long q = slab_index();  // right-hand side
     if (k >= S) return;
@@ -558,9 +575,10 @@ cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *inv, 
                                cudaStream_t s) {
     if (nslabs <= 0 || g.nxyz <= 0) return cudaSuccess;
     const ModeLaunch L = mode_launch(g.nxyz, nslabs);
-    ST_NT_DISPATCH(nt, (k_lv_smooth<T, NT><<<L.grid, L.block, 0, s>>>(
-                           uin, uout, f, inv, g.nxyz, omega, spp, nslabs, uin_zero)));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    ST_NT_DISPATCH(nt, (e = launch_pdl(k_lv_smooth<T, NT>, L.grid, L.block, 0, s, uin, uout, f,
+                                       inv, g.nxyz, omega, spp, nslabs, uin_zero)));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -570,15 +588,17 @@ cudaError_t launch_spec_down(const T *uin, T *uout, const T *f, T *fc, const T *
                              cudaStream_t s) {
     if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
     const ModeLaunch L = mode_launch(g.nxyz, ncoarse);
+    cudaError_t e = cudaSuccess;
     if (uin) {
-        ST_NT_DISPATCH(c.nt, (k_lv_down<T, NT><<<L.grid, L.block, 0, s>>>(
-                                 uin, uout, f, fc, inv, mu, g.nxyz, c, pc, omega, spp, ncoarse)));
+        ST_NT_DISPATCH(c.nt, (e = launch_pdl(k_lv_down<T, NT>, L.grid, L.block, 0, s, uin, uout,
+                                             f, fc, inv, mu, g.nxyz, c, pc, omega, spp,
+                                             ncoarse)));
     } else {  // from zero: two slab pairs per thread
         const ModeLaunch L2 = mode_launch(g.nxyz, (ncoarse + 1) / 2);
-        ST_NT_DISPATCH(c.nt, (k_lv_down0<T, NT, 2><<<L2.grid, L2.block, 0, s>>>(
-                                 uout, f, fc, inv, g.nxyz, pc, omega, spp, ncoarse)));
+        ST_NT_DISPATCH(c.nt, (e = launch_pdl(k_lv_down0<T, NT, 2>, L2.grid, L2.block, 0, s, uout,
+                                             f, fc, inv, g.nxyz, pc, omega, spp, ncoarse)));
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -587,9 +607,10 @@ cudaError_t launch_spec_up(const T *ec, const T *uin, T *uout, const T *f, const
                            long long ncoarse, cudaStream_t s) {
     if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
     const ModeLaunch L = mode_launch(g.nxyz, (ncoarse + 1) / 2);  // two slab pairs per thread
-    ST_NT_DISPATCH(pc.nt, (k_lv_up<T, NT, 2><<<L.grid, L.block, 0, s>>>(
-                              ec, uin, uout, f, inv, g.nxyz, pc, omega, spp, ncoarse)));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_up<T, NT, 2>, L.grid, L.block, 0, s, ec, uin, uout,
+                                          f, inv, g.nxyz, pc, omega, spp, ncoarse)));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -597,9 +618,10 @@ cudaError_t launch_spec_coarse(T *u, const T *f, const T *inv, const Grid &g, in
                                int nprob, cudaStream_t s) {
     if (nprob <= 0 || g.nxyz <= 0) return cudaSuccess;
     const ModeLaunch L = mode_launch(g.nxyz, nprob);
-    ST_NT_DISPATCH(nt, (k_lv_coarse<T, NT><<<L.grid, L.block, 0, s>>>(u, f, inv, g.nxyz, spp,
-                                                                       (long long)nprob)));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    ST_NT_DISPATCH(nt, (e = launch_pdl(k_lv_coarse<T, NT>, L.grid, L.block, 0, s, u, f, inv,
+                                       g.nxyz, spp, (long long)nprob)));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -608,9 +630,10 @@ cudaError_t launch_spec_res_restrict(const T *u, const T *f, T *fc, const T *mu,
                                      long long ncoarse, cudaStream_t s) {
     if (ncoarse <= 0 || g.nxyz <= 0) return cudaSuccess;
     const ModeLaunch L = mode_launch(g.nxyz, ncoarse);
-    ST_NT_DISPATCH(c.nt, (k_lv_res_restrict<T, NT><<<L.grid, L.block, 0, s>>>(
-                             u, f, fc, mu, g.nxyz, c, pc, spp, ncoarse)));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    ST_NT_DISPATCH(c.nt, (e = launch_pdl(k_lv_res_restrict<T, NT>, L.grid, L.block, 0, s, u, f,
+                                         fc, mu, g.nxyz, c, pc, spp, ncoarse)));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -619,9 +642,10 @@ cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *mu, const Gr
                            cudaStream_t s) {
     if (nslabs <= 0 || g.nxyz <= 0) return cudaSuccess;
     const ModeLaunch L = mode_launch(g.nxyz, nslabs);
-    ST_NT_DISPATCH(c.nt, (k_lv_op<T, NT><<<L.grid, L.block, 0, s>>>(u, f, out, mu, g.nxyz, c,
-                                                                      spp, nslabs, res)));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    ST_NT_DISPATCH(c.nt, (e = launch_pdl(k_lv_op<T, NT>, L.grid, L.block, 0, s, u, f, out, mu,
+                                         g.nxyz, c, spp, nslabs, res)));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 // the sub-cycle of levels l0 .. L in one launch; cudaErrorNotSupported when
 // n0 > TAIL_SLABS or more than 16 levels
@@ -639,9 +663,10 @@ cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nle
         L.block.x = 128;
         L.grid.x = (unsigned)((g.nxyz + 127) / 128);
     }
-    ST_NT_DISPATCH(pc.nt, (k_lv_tail<T, NT><<<L.grid, L.block, 0, s>>>(fin, uout, ta, pc, g.nxyz,
-                                                                        n0, omega)));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_tail<T, NT>, L.grid, L.block, 0, s, fin, uout, ta,
+                                          pc, g.nxyz, n0, omega)));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 #undef ST_NT_DISPATCH
 

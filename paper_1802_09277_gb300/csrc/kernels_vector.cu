@@ -2,6 +2,7 @@
 // of arXiv:1802.09277) and precision conversion for the mixed V-cycle.
 // Reductions are deterministic: fixed-size per-block partial sums, then one
 // fixed-order pass.
+#include "pdl.cuh"
 #include "st_internal.h"
 
 namespace st {
@@ -151,6 +152,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_multidot_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ w,
                        long long len, double *__restrict__ partial, int vec2) {
+    griddep_wait();
+    griddep_launch();
     using P2 = typename Pair<T>::V;
     __shared__ typename Red<T>::V red[8][4];
     const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
@@ -205,6 +208,8 @@ static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // one warp per output; lane-strided partial sums, then a fixed shuffle tree
 __global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, int count,
                                   double *__restrict__ out) {
+    griddep_wait();
+    griddep_launch();
     const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= count) return;
@@ -227,13 +232,13 @@ cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, 
         vl.v[i] = vecs[i];
         vec2 = vec2 && al(vecs[i]);
     }
-    k_multidot_partial<T><<<dim3(nblk, nrhs, (nv + 3) / 4), 256, 0, s>>>(nv, vl, w, len, partial,
-                                                                        vec2);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_multidot_partial<T>, dim3(nblk, nrhs, (nv + 3) / 4), dim3(256),
+                               0, s, nv, vl, w, len, partial, vec2);
     if (e != cudaSuccess) return e;
     const int count = nv * nrhs;
-    k_reduce_partials<<<(count + 3) / 4, 128, 0, s>>>(partial, nblk, count, out);
-    return cudaGetLastError();
+    e = launch_pdl(k_reduce_partials, dim3((count + 3) / 4), dim3(128), 0, s, partial, nblk,
+                   count, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // grid (blocks, nrhs): block row r handles right-hand side r (no index division)
@@ -241,6 +246,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_multiaxpy(int nv, const __grid_constant__ AxpyArgs<T> aa, long long len,
                 T *__restrict__ y, int vec2) {
+    griddep_wait();
+    griddep_launch();
     using P2 = typename Pair<T>::V;
     const int r = blockIdx.y;
     const long long off = (long long)r * len;
@@ -274,6 +281,8 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_axpy2(int nv, const __grid_constant__ Axpy2Args<T> aa, long long len, T *__restrict__ y1,
             T *__restrict__ y2, int write1) {
+    griddep_wait();
+    griddep_launch();
     const int r = blockIdx.y;
     const long long off = (long long)r * len;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -353,6 +362,8 @@ __global__ void __launch_bounds__(256)
     k_gram2_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ t1,
                     const T *__restrict__ t2, long long len, double *__restrict__ partial,
                     int vec4) {
+    griddep_wait();
+    griddep_launch();
     __shared__ typename Red<T>::V red[8][2 * GV];
     const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
     const int v0 = GV * blockIdx.z;
@@ -403,13 +414,13 @@ cudaError_t launch_gram2(int nv, const T *const *vecs, const T *t1, const T *t2,
         vec4 = vec4 && al4(vecs[i]);
     }
     constexpr int GV = 4;
-    k_gram2_partial<T, GV><<<dim3(nblk, nrhs, (nv + GV - 1) / GV), 256, 0, s>>>(
-        nv, vl, t1, t2, len, partial, vec4);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_gram2_partial<T, GV>, dim3(nblk, nrhs, (nv + GV - 1) / GV),
+                               dim3(256), 0, s, nv, vl, t1, t2, len, partial, vec4);
     if (e != cudaSuccess) return e;
     const int count = 2 * nv * nrhs;
-    k_reduce_partials<<<(count + 3) / 4, 128, 0, s>>>(partial, nblk, count, out);
-    return cudaGetLastError();
+    e = launch_pdl(k_reduce_partials, dim3((count + 3) / 4), dim3(128), 0, s, partial, nblk,
+                   count, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -434,8 +445,9 @@ cudaError_t launch_axpy2(int nv, const T *const *xs, const double *c1, const dou
     const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
     if (bx > cap) bx = cap;
     if (bx < 1) bx = 1;
-    k_axpy2<T><<<dim3((unsigned)bx, (unsigned)nrhs), 256, 0, s>>>(nv, aa, len, y1, y2, write1);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(k_axpy2<T>, dim3((unsigned)bx, (unsigned)nrhs), dim3(256), 0,
+                                     s, nv, aa, len, y1, y2, write1);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
@@ -458,8 +470,9 @@ cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int
     const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
     if (bx > cap) bx = cap;
     if (bx < 1) bx = 1;
-    k_multiaxpy<T><<<dim3((unsigned)bx, (unsigned)nrhs), 256, 0, s>>>(nv, aa, len, y, vec2);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(k_multiaxpy<T>, dim3((unsigned)bx, (unsigned)nrhs),
+                                     dim3(256), 0, s, nv, aa, len, y, vec2);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 struct ScaleArgs {
