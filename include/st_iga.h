@@ -440,6 +440,14 @@ int st_time_prolongation(st_handle h, int *nt, double *Pt);
  * by merging slab pairs (0; level 0: 0).  Any output may be NULL. */
 int st_level_shape(st_handle h, int lvl, int *slabs, int *spans, int *space_step);
 
+/* The 1D space prolongation of axis a used between level lvl and level
+ * lvl + 1 when the latter was obtained by halving the spans: P (n_f x n_c,
+ * row-major) expresses the interior B-splines of the coarse grid in those of
+ * level lvl's grid (knot insertion).  *nf, *nc receive the sizes; P may be
+ * NULL to query them.  ST_ERR_INVALID_ARG when level lvl + 1 is not a space
+ * step or a is not an axis of the domain. */
+int st_space_prolongation(st_handle h, int lvl, int axis, int *nf, int *nc, double *P);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *st_last_error(void);
 

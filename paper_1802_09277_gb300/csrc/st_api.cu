@@ -2775,6 +2775,18 @@ int st_time_prolongation(st_handle h, int *nt, double *Pt) {
     return ST_OK;
 }
 
+int st_space_prolongation(st_handle h, int lvl, int axis, int *nf, int *nc, double *P) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (lvl < 0 || lvl + 1 >= h->nlev || !h->lv[lvl + 1].xstep)
+        return fail(ST_ERR_INVALID_ARG, "level %d is not followed by a space step", lvl);
+    if (axis < 0 || axis >= h->dim) return fail(ST_ERR_INVALID_ARG, "bad axis %d", axis);
+    const LevelSpace &F = h->ls[h->lv[lvl].sp], &C = h->ls[h->lv[lvl + 1].sp];
+    if (nf) *nf = F.n[axis];
+    if (nc) *nc = C.n[axis];
+    if (P) std::memcpy(P, F.Pc[axis].data(), sizeof(double) * F.Pc[axis].size());
+    return ST_OK;
+}
+
 int st_level_shape(st_handle h, int lvl, int *slabs, int *spans, int *space_step) {
     if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
     if (lvl < 0 || lvl >= h->nlev) return fail(ST_ERR_INVALID_ARG, "level %d out of range", lvl);

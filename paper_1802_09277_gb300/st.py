@@ -30,7 +30,7 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_load_gaussians", "st_smooth",
            "st_smooth_static", "st_block_minres", "st_vcycle",
            "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
-           "st_time_prolongation", "st_level_shape", "st_last_error", "st_serve_opts_default", "st_serve_start",
+           "st_time_prolongation", "st_level_shape", "st_space_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_poll", "st_serve_wait", "st_serve_stop"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
                 "vector", "dot", "tc", "spec", "stencil_df", "minres"]
@@ -115,6 +115,7 @@ def load():
         "st_block_minres": (I, [P, D, D, D, P, P, I, D, I, ip, dp]),
         "st_vcycle": (I, [P, P, P]),
         "st_level_shape": (I, [P, I, ip, ip, ip]),
+        "st_space_prolongation": (I, [P, I, I, ip, ip, dp]),
         "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
         "st_autotune": (I, [P, ip, dp]),
         "st_profile": (I, [P, I]),
@@ -351,6 +352,18 @@ class Solver:
             _check(_lib.st_level_shape(self._h, lvl, ctypes.byref(n), sp, ctypes.byref(x)))
             out.append((n.value, tuple(sp[:self.dim]), "-" if lvl == 0 else ("x" if x.value else "t")))
         return out
+
+    def space_prolongation(self, level, axis):
+        """The 1D knot-insertion matrix (n_f x n_c) of axis `axis` between
+        level `level` and the space-coarsened level after it."""
+        import numpy as np
+        nf, nc = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.st_space_prolongation(self._h, int(level), int(axis), ctypes.byref(nf),
+                                          ctypes.byref(nc), None))
+        P = np.zeros((nf.value, nc.value))
+        _check(_lib.st_space_prolongation(self._h, int(level), int(axis), None, None,
+                                          P.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return P
 
     def time_prolongation(self):
         import numpy as np

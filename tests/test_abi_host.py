@@ -266,3 +266,29 @@ def test_space_ratio_option_errors(st):
     with pytest.raises(st.StError) as e:
         st.Solver(2, 2, (8, 8), 4, host_only=True, space_ratio=-1.0)
     assert e.value.code == st.ST_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("d,spans,p,N", [(1, (64,), 2, 16), (2, (16, 12), 3, 8), (3, (8, 8, 8), 1, 8),
+                                         (2, (36, 20), 2, 4)])
+def test_space_prolongation_matches_oracle(st, d, spans, p, N):
+    """The library's 1D knot-insertion matrices (collocation at the fine
+    Greville abscissae) equal the oracle's (L2 projection) on every space step
+    of the hierarchy; levels not followed by a space step are rejected."""
+    s = st.Solver(d, p, spans, N, host_only=True, space_ratio=1.0)
+    shapes = s.level_shapes()
+    steps = 0
+    for lvl in range(len(shapes) - 1):
+        if shapes[lvl + 1][2] != "x":
+            with pytest.raises(st.StError):
+                s.space_prolongation(lvl, 0)
+            continue
+        steps += 1
+        for a in range(d):
+            P = s.space_prolongation(lvl, a)
+            ref = S.space_prolongation_1d(shapes[lvl][1][a], p)
+            assert P.shape == ref.shape
+            assert np.abs(P - ref).max() <= 1e-12
+    assert steps >= 1
+    with pytest.raises(st.StError):
+        s.space_prolongation(0, d)
+    s.close()
