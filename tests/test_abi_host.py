@@ -122,6 +122,13 @@ def test_host_only_handle_rejects_device_calls(st):
     import ctypes
     rc = lib.st_apply(s._h, ctypes.c_void_p(8), ctypes.c_void_p(16))
     assert rc == -1
+    # the MinRes block solve needs device memory as well (no device call is made)
+    its = (ctypes.c_int * 1)()
+    rel = (ctypes.c_double * 1)()
+    rc = lib.st_block_minres(s._h, 5.0, 2.0, -3.0, ctypes.c_void_p(8), ctypes.c_void_p(16), 1,
+                             1e-8, 0, its, rel)
+    assert rc == st.ST_ERR_INVALID_ARG
+    assert "host-only" in lib.st_last_error().decode()
     s.close()
 
 
