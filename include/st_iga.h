@@ -434,10 +434,12 @@ int st_time_spectrum(st_handle h, int lvl, double *lam_re, double *lam_im, doubl
  * slab in the bases of the two fine slabs it merges (Sec. 3.1). */
 int st_time_prolongation(st_handle h, int *nt, double *Pt);
 
-/* Shape of multigrid level lvl (0 = finest): slabs per right-hand side,
- * knot spans per axis (spans[3], unused axes 1) and whether the level was
- * obtained from the previous one by halving the spans (*space_step = 1) or
- * by merging slab pairs (0; level 0: 0).  Any output may be NULL. */
+/* Shape of multigrid level lvl (0 = finest) of the space-time hierarchy
+ * (Sec. 3.1 coarsens in time and, with opt.space_ratio, in space): slabs
+ * per right-hand side, knot spans per axis (spans[3], unused axes 1) and
+ * whether the level was obtained from the previous one by halving the spans
+ * (*space_step = 1) or by merging slab pairs (0; level 0: 0).  Any output
+ * may be NULL; ST_ERR_INVALID_ARG for a level out of range. */
 int st_level_shape(st_handle h, int lvl, int *slabs, int *spans, int *space_step);
 
 /* The 1D space prolongation of axis a used between level lvl and level
