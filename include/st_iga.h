@@ -253,8 +253,11 @@ int st_smooth(st_handle h, double *u, const double *f, int nsteps);
  * ST_STATIC_SCRATCH_BYTES (about 9.7 MB) that every GPU which loads the
  * library holds until the process exits.  It calls no cudaMalloc, cudaFree
  * or other allocating routine.
- *   h      : any handle (st_setup or st_setup_host); only its host factors are
- *            read, its precision option is ignored (the steps run in FP64)
+ *   h      : a handle from st_setup or st_setup_host with variant ST_RSCHUR
+ *            and spatial_solver ST_SPATIAL_FD (any other variant or spatial
+ *            solver: ST_ERR_UNSUPPORTED before any copy or launch); only its
+ *            host factors are read, its precision option is ignored (the
+ *            steps run in FP64)
  *   u, f   : device, n_dofs doubles each (u in/out), must not alias
  *   stream : cudaStream_t for all work of this call (NULL = default stream)
  * Limits: n_dofs <= ST_STATIC_MAX_DOFS and at most ST_STATIC_MAX_N interior
@@ -361,6 +364,9 @@ typedef struct {
     int workers;          /* concurrent solves (default 4)                          */
     int max_batch;        /* right-hand sides per batched solve, 1..32 (default 8)  */
     st_options opt;       /* solver options for every request (nrhs is set per batch) */
+    int start_paused;     /* 1: workers take no request until st_serve_resume, so a
+                             whole mix can be queued before batches are formed
+                             (deterministic batching); default 0                */
 } st_server_opts;
 
 typedef struct {
@@ -374,6 +380,7 @@ typedef struct {
 } st_request;
 
 #define ST_ERR_NOT_READY -10  /* st_serve_poll: the request is still pending */
+#define ST_ERR_CANCELLED -11  /* st_serve_cancel removed the request before it ran */
 
 typedef struct {
     int status;           /* ST_OK or the solve's error code                      */
@@ -393,6 +400,14 @@ int st_serve_start(st_server *out, const st_server_opts *o);
 /* Queue a request (its rhs is copied before returning); *ticket identifies it.
  * Errors: INVALID_ARG (bad sizes), UNSUPPORTED. */
 int st_serve_submit(st_server s, const st_request *req, uint64_t *ticket);
+/* Let the workers of a server started with start_paused = 1 take requests
+ * (no effect otherwise).  Errors: INVALID_ARG (null server). */
+int st_serve_resume(st_server s);
+/* Withdraw a request that no worker has taken yet: its result becomes ready
+ * with status ST_ERR_CANCELLED and no solution.  Returns ST_OK when it was
+ * withdrawn, ST_ERR_NOT_READY when a worker is already solving it (it then
+ * completes normally), ST_ERR_INVALID_ARG for an unknown or finished ticket. */
+int st_serve_cancel(st_server s, uint64_t ticket);
 /* Non-blocking: ST_ERR_NOT_READY while pending; otherwise fills *res, copies
  * the solution (n_dofs doubles) into u_host if it is not NULL, releases the
  * request and returns ST_OK (the request's own status is res->status). */

@@ -2307,6 +2307,10 @@ constexpr size_t kStaticDoubles = 2 * (size_t)ST_STATIC_MAX_DOFS + 3 * kStaticFa
 // code must not use this name as an address: it only stands for the device
 // symbol; the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) double g_static_scratch[kStaticDoubles];
+// the public size constant hard-codes the band width 2 * PMAX + 1 = 7
+static_assert(2 * PMAX + 1 == 7, "ST_STATIC_SCRATCH_BYTES assumes PMAX = 3");
+static_assert(sizeof(g_static_scratch) == (size_t)ST_STATIC_SCRATCH_BYTES,
+              "static scratch array and ST_STATIC_SCRATCH_BYTES disagree");
 
 std::mutex g_static_mu;
 constexpr int kMaxDevices = 64;
@@ -2657,6 +2661,13 @@ int st_smooth_static(st_handle h, double *u, const double *f, int nsteps, void *
     if (!u || !f) return fail(ST_ERR_INVALID_ARG, "null vector pointer");
     if ((const void *)u == (const void *)f) return fail(ST_ERR_INVALID_ARG, "u and f alias");
     if (nsteps < 0) return fail(ST_ERR_INVALID_ARG, "nsteps < 0");
+    // only the real Schur form with exact spatial solves keeps everything it
+    // needs in the static array (the other variants need the per-mode shift
+    // table or the MinRes work space); refuse them before any upload or launch
+    if (h->opt.variant != ST_RSCHUR)
+        return fail(ST_ERR_UNSUPPORTED, "st_smooth_static supports only the real Schur variant");
+    if (h->opt.spatial_solver != ST_SPATIAL_FD)
+        return fail(ST_ERR_UNSUPPORTED, "st_smooth_static supports only exact spatial solves");
     const long long total = h->len * h->nrhs;
     if (total > ST_STATIC_MAX_DOFS)
         return fail(ST_ERR_INVALID_ARG, "%lld dofs exceed the static work space of %d dofs", total,

@@ -51,3 +51,19 @@ def test_smooth_static_rejects_oversize(st):
     with pytest.raises(st.StError) as e:
         host.smooth_static(u, torch.zeros_like(u), 1)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("opts", [dict(variant="eig"), dict(variant="cschur"),
+                                  dict(spatial_solver="minres")])
+def test_smooth_static_rejects_other_variants(st, opts):
+    # the diagonalisation, complex-Schur and MinRes smoothers need device
+    # tables the static array does not hold: refused before any copy or launch
+    host = st.Solver(2, 2, (12, 10), 4, host_only=True, **opts)
+    u = torch.zeros(host.ndofs, dtype=torch.float64, device="cuda")
+    f = torch.ones_like(u)
+    with pytest.raises(st.StError) as e:
+        host.smooth_static(u, f, 1)
+    assert e.value.code == -9
+    torch.cuda.synchronize()
+    assert float(u.abs().max()) == 0.0  # nothing ran
+    host.close()
