@@ -1,7 +1,11 @@
 // Serving loop with continuous batching (see st_serve_* in include/st_iga.h).
 //
 // Host-side scheduler only: every solve goes through st_setup / st_solve of
-// this library on the worker's own CUDA stream.
+// this library on the worker's own CUDA stream.  The server mutex guards the
+// queue, the result table, the setup cache and the budget accounting; it is
+// never held across a host factorisation, a device allocation or free, or a
+// solve, so submit / poll / wait and the other workers' admissions never wait
+// for one worker's setup.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,6 +19,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "../../include/st_iga.h"
@@ -37,6 +42,15 @@ struct Key {
     }
 };
 
+// a setup is shared by every request of the same problem (the tolerance and
+// the kind of right-hand side only matter to the solve)
+struct ShapeKey {
+    int geometry, degree, spans[3], slabs, nrhs;
+    bool operator<(const ShapeKey &o) const {
+        return std::memcmp(this, &o, sizeof(ShapeKey)) < 0;
+    }
+};
+
 struct Pending {
     uint64_t ticket;
     Key key;
@@ -46,6 +60,7 @@ struct Pending {
 
 struct Done {
     bool done = false;
+    bool running = false;
     st_result res{};
     std::vector<double> u;
     Clock::time_point submitted;
@@ -63,84 +78,107 @@ struct Entry {  // a cached setup for one configuration and batch size
 
 void zero_key(Key &k) { std::memset(&k, 0, sizeof k); }
 
+ShapeKey shape_of(const Key &k, int nrhs) {
+    ShapeKey s;
+    std::memset(&s, 0, sizeof s);
+    s.geometry = k.geometry;
+    s.degree = k.degree;
+    for (int a = 0; a < 3; ++a) s.spans[a] = k.spans[a];
+    s.slabs = k.slabs;
+    s.nrhs = nrhs;
+    return s;
+}
+
 }  // namespace
 
 struct st_server_s {
     st_server_opts o{};
     int device = 0;
-    size_t budget = 0, used = 0;
+    size_t budget = 0;
+    size_t used = 0;      // bytes held by cached setups plus reservations of setups being built
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Pending> pending;
     std::map<uint64_t, Done> results;
     std::vector<std::unique_ptr<Entry>> cache;
+    std::map<ShapeKey, size_t> footprint;  // measured device bytes of a setup + its two vectors
     std::vector<std::thread> threads;
     uint64_t next_ticket = 1, clock = 0;
-    int busy_workers = 0;
+    int busy_workers = 0;  // solving, building a setup or freeing one
+    bool paused = false;
     bool stop = false;
 };
 
 namespace {
 
-void destroy_entry(st_server_s *s, Entry *e) {
+// Frees an entry's device memory (st_destroy, cudaFree).  Called without the
+// server lock: cudaFree waits for the device.
+void free_entry(Entry *e) {
     if (e->h) st_destroy(e->h);
     if (e->f) cudaFree(e->f);
     if (e->u) cudaFree(e->u);
-    s->used -= e->bytes;
+    e->h = nullptr;
+    e->f = e->u = nullptr;
 }
 
-// Create a setup for (key, nrhs) within the remaining budget (lock held).
-int make_entry(st_server_s *s, const Key &key, int nrhs, Entry **out) {
+// First guess of a setup's device bytes before one of its shape was built:
+// the Krylov space and the level vectors dominate.  Deliberately generous; the
+// reservation is trimmed to the measured size once the setup exists.
+size_t guess_bytes(const st_server_s *s, const Key &k, int nrhs) {
+    int64_t nx = 1;
+    for (int a = 0; a < k.geometry; ++a) nx *= k.spans[a] + k.degree - 2;
+    const double n = (double)k.slabs * (s->o.opt.ne_per_slab + k.degree) * nx * nrhs;
+    const int m = s->o.opt.gmres_restart > 0 ? s->o.opt.gmres_restart : 20;
+    // 2m+1 Krylov vectors (counted as FP64), level vectors and work space
+    // (about 8 more), the request's two FP64 vectors, factors and tables
+    return (size_t)(8.0 * n * (2.0 * m + 1.0 + 8.0 + 2.0)) + ((size_t)32 << 20);
+}
+
+// Builds a setup for (key, nrhs) whose device memory stays within `limit`
+// bytes (setup, Krylov space and the two request vectors).  No lock held.
+int build_entry(st_server_s *s, const Key &key, int nrhs, size_t limit, Entry **out,
+                std::string *why) {
     st_options opt = s->o.opt;
     opt.nrhs = nrhs;
-    opt.hbm_budget = s->budget > s->used ? s->budget - s->used : 1;
-    st_handle h = nullptr;
-    int rc = st_setup(&h, key.geometry, key.degree, key.spans, key.slabs, &opt, nullptr);
-    if (rc != ST_OK) return rc;
-    rc = st::prepare_solve(h);
-    size_t hb = 0;
-    int64_t n = 0;
-    st_sizes(h, &n, nullptr, nullptr, nullptr, &hb);
-    const size_t vb = (size_t)n * sizeof(double);
-    if (rc == ST_OK && s->used + hb + 2 * vb > s->budget) rc = ST_ERR_OVER_BUDGET;
+    int64_t nx = 1;
+    for (int a = 0; a < key.geometry; ++a) nx *= key.spans[a] + key.degree - 2;
+    const size_t vb = (size_t)key.slabs * (opt.ne_per_slab + key.degree) * nx * nrhs * sizeof(double);
+    if (limit <= 2 * vb) {
+        *why = "the request's vectors alone exceed the reservation";
+        return ST_ERR_OVER_BUDGET;
+    }
+    opt.hbm_budget = limit - 2 * vb;
+    cudaSetDevice(s->device);
     std::unique_ptr<Entry> e(new Entry());
     e->key = key;
     e->nrhs = nrhs;
-    e->h = h;
-    if (rc == ST_OK && (cudaMalloc(&e->f, vb) != cudaSuccess || cudaMalloc(&e->u, vb) != cudaSuccess)) {
+    int rc = st_setup(&e->h, key.geometry, key.degree, key.spans, key.slabs, &opt, nullptr);
+    if (rc == ST_OK) rc = st::prepare_solve(e->h);
+    if (rc == ST_OK &&
+        (cudaMalloc(&e->f, vb) != cudaSuccess || cudaMalloc(&e->u, vb) != cudaSuccess)) {
         cudaGetLastError();
         rc = ST_ERR_OOM;
     }
     if (rc != ST_OK) {
-        e->bytes = 0;
-        destroy_entry(s, e.get());
+        *why = std::string("setup: ") + st_last_error();
+        free_entry(e.get());
         return rc;
     }
+    size_t hb = 0;
+    st_sizes(e->h, nullptr, nullptr, nullptr, nullptr, &hb);
     e->bytes = hb + 2 * vb;
-    s->used += e->bytes;
-    *out = e.get();
-    s->cache.push_back(std::move(e));
+    *out = e.release();
     return ST_OK;
 }
 
-bool evict_one(st_server_s *s) {
-    int best = -1;
-    for (int i = 0; i < (int)s->cache.size(); ++i)
-        if (!s->cache[i]->busy && (best < 0 || s->cache[i]->last_used < s->cache[best]->last_used))
-            best = i;
-    if (best < 0) return false;
-    destroy_entry(s, s->cache[best].get());
-    s->cache.erase(s->cache.begin() + best);
-    return true;
-}
-
 void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const st_solve_info *info,
-            Entry *e, Clock::time_point admitted, const std::vector<std::vector<double>> *u,
+            Clock::time_point admitted, const std::vector<std::vector<double>> *u,
             const std::string &msg = std::string()) {
     const auto now = Clock::now();
     for (size_t i = 0; i < batch.size(); ++i) {
         Done &d = s->results[batch[i].ticket];
         d.done = true;
+        d.running = false;
         d.res.status = status;
         d.res.iterations = info ? info->iterations : 0;
         d.res.refinements = info ? info->refinements : 0;
@@ -153,7 +191,94 @@ void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const
         std::snprintf(d.res.error, sizeof d.res.error, "%s", status == ST_OK ? "" : msg.c_str());
         if (u) d.u = (*u)[i];
     }
-    (void)e;
+}
+
+// Finds or builds a setup for the batch (lock held on entry and on return; it
+// is released while a setup is built or an evicted one is freed).  On success
+// the entry is marked busy.
+int acquire_entry(st_server_s *s, std::unique_lock<std::mutex> &lock, const Key &key, int R,
+                  Entry **out, std::string *why) {
+    const ShapeKey sk = shape_of(key, R);
+    for (;;) {
+        for (auto &c : s->cache)
+            if (!c->busy && c->nrhs == R && c->key.same_problem(key)) {
+                c->busy = true;
+                *out = c.get();
+                return ST_OK;
+            }
+        auto fp = s->footprint.find(sk);
+        size_t want = fp != s->footprint.end() ? fp->second : guess_bytes(s, key, R);
+        const size_t avail = s->budget > s->used ? s->budget - s->used : 0;
+        const bool idle = s->busy_workers == 0;
+        const bool any_free = std::any_of(s->cache.begin(), s->cache.end(),
+                                          [](const std::unique_ptr<Entry> &c) { return !c->busy; });
+        // an idle server with nothing to evict tries whatever is left (the
+        // guess may be too generous)
+        if (want > avail && idle && !any_free) want = avail;
+        if (want <= avail && want > 0) {
+            s->used += want;  // reserve, then build without the lock
+            ++s->busy_workers;
+            lock.unlock();
+            Entry *e = nullptr;
+            std::string msg;
+            const int rc = build_entry(s, key, R, want, &e, &msg);
+            lock.lock();
+            --s->busy_workers;
+            s->used -= want;
+            if (rc == ST_OK) {
+                s->used += e->bytes;
+                s->footprint[sk] = e->bytes;
+                e->busy = true;
+                s->cache.emplace_back(e);
+                *out = e;
+                s->cv.notify_all();
+                return ST_OK;
+            }
+            s->cv.notify_all();
+            if (rc != ST_ERR_OVER_BUDGET && rc != ST_ERR_OOM) {
+                *why = msg;
+                return rc;
+            }
+            if (want >= s->budget || (want == avail && idle && !any_free)) {
+                char buf[200];
+                std::snprintf(buf, sizeof buf, "does not fit the HBM budget (%zu bytes; %s)",
+                              s->budget, msg.c_str());
+                *why = buf;
+                return ST_ERR_OVER_BUDGET;
+            }
+            // the setup needed more than reserved: reserve more next time
+            s->footprint[sk] = std::min(s->budget, 2 * want);
+            continue;
+        }
+        // make room: evict the least recently used idle setup, freeing it
+        // without the lock (its bytes stay counted until they are freed)
+        int best = -1;
+        for (int i = 0; i < (int)s->cache.size(); ++i)
+            if (!s->cache[i]->busy &&
+                (best < 0 || s->cache[i]->last_used < s->cache[best]->last_used))
+                best = i;
+        if (best >= 0) {
+            std::unique_ptr<Entry> victim = std::move(s->cache[best]);
+            s->cache.erase(s->cache.begin() + best);
+            ++s->busy_workers;
+            lock.unlock();
+            free_entry(victim.get());
+            lock.lock();
+            --s->busy_workers;
+            s->used -= victim->bytes;
+            s->cv.notify_all();
+            continue;
+        }
+        if (s->busy_workers > 0) {  // wait for running work to release memory
+            s->cv.wait(lock);
+            continue;
+        }
+        char buf[200];
+        std::snprintf(buf, sizeof buf, "does not fit the HBM budget (%zu of %zu bytes held)", s->used,
+                      s->budget);
+        *why = buf;
+        return ST_ERR_OVER_BUDGET;
+    }
 }
 
 void worker(st_server_s *s) {
@@ -162,7 +287,7 @@ void worker(st_server_s *s) {
     if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) stream = nullptr;
     std::unique_lock<std::mutex> lock(s->mu);
     for (;;) {
-        s->cv.wait(lock, [s] { return s->stop || !s->pending.empty(); });
+        s->cv.wait(lock, [s] { return s->stop || (!s->paused && !s->pending.empty()); });
         if (s->pending.empty()) {
             if (s->stop) break;
             continue;
@@ -172,6 +297,7 @@ void worker(st_server_s *s) {
         std::vector<Pending> batch;
         for (auto it = s->pending.begin(); it != s->pending.end() && (int)batch.size() < s->o.max_batch;) {
             if (std::memcmp(&it->key, &key, sizeof(Key)) == 0) {
+                s->results[it->ticket].running = true;
                 batch.push_back(std::move(*it));
                 it = s->pending.erase(it);
             } else {
@@ -179,43 +305,14 @@ void worker(st_server_s *s) {
             }
         }
         const int R = (int)batch.size();
-        // find or create a setup
         Entry *e = nullptr;
-        int rc = ST_OK;
         std::string why;
-        for (;;) {
-            e = nullptr;
-            for (auto &c : s->cache)
-                if (!c->busy && c->nrhs == R && c->key.same_problem(key)) {
-                    e = c.get();
-                    break;
-                }
-            if (e) {  // a cached setup (possibly freed while this worker waited)
-                rc = ST_OK;
-                break;
-            }
-            rc = make_entry(s, key, R, &e);
-            if (rc == ST_OK) break;
-            why = std::string("setup: ") + st_last_error();
-            if (rc != ST_ERR_OVER_BUDGET && rc != ST_ERR_OOM) break;
-            if (evict_one(s)) continue;
-            if (s->busy_workers > 0) {  // wait for running solves to release memory
-                s->cv.wait(lock);
-                continue;
-            }
-            rc = ST_ERR_OVER_BUDGET;
-            char buf[200];
-            std::snprintf(buf, sizeof buf, "does not fit the HBM budget (%zu of %zu bytes held; %s)",
-                          s->used, s->budget, why.c_str());
-            why = buf;
-            break;
-        }
+        const int rc = acquire_entry(s, lock, key, R, &e, &why);
         if (rc != ST_OK) {
-            finish(s, batch, rc, nullptr, nullptr, Clock::now(), nullptr, why);
+            finish(s, batch, rc, nullptr, Clock::now(), nullptr, why);
             s->cv.notify_all();
             continue;
         }
-        e->busy = true;
         e->last_used = ++s->clock;
         ++s->busy_workers;
         const auto admitted = Clock::now();
@@ -244,7 +341,7 @@ void worker(st_server_s *s) {
 
         const std::string solve_msg = (st == ST_OK) ? std::string() : std::string(st_last_error());
         lock.lock();
-        finish(s, batch, st, &info, e, admitted, &u, solve_msg);
+        finish(s, batch, st, &info, admitted, &u, solve_msg);
         e->busy = false;
         --s->busy_workers;
         s->cv.notify_all();
@@ -262,6 +359,7 @@ void st_serve_opts_default(st_server_opts *o) {
     std::memset(o, 0, sizeof *o);
     o->workers = 4;
     o->max_batch = 8;
+    o->start_paused = 0;
     st_options_default(&o->opt);
 }
 
@@ -274,6 +372,7 @@ int st_serve_start(st_server *out, const st_server_opts *o) {
         return ST_ERR_INVALID_ARG;
     st_server_s *s = new st_server_s();
     s->o = oo;
+    s->paused = oo.start_paused != 0;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -288,6 +387,16 @@ int st_serve_start(st_server *out, const st_server_opts *o) {
     s->budget = oo.hbm_budget ? oo.hbm_budget : (size_t)(0.9 * (double)fr);
     for (int i = 0; i < oo.workers; ++i) s->threads.emplace_back(worker, s);
     *out = s;
+    return ST_OK;
+}
+
+int st_serve_resume(st_server s) {
+    if (!s) return ST_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->paused = false;
+    }
+    s->cv.notify_all();
     return ST_OK;
 }
 
@@ -329,6 +438,24 @@ int st_serve_submit(st_server s, const st_request *req, uint64_t *ticket) {
     return ST_OK;
 }
 
+int st_serve_cancel(st_server s, uint64_t ticket) {
+    if (!s) return ST_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto r = s->results.find(ticket);
+    if (r == s->results.end() || r->second.done) return ST_ERR_INVALID_ARG;
+    if (r->second.running) return ST_ERR_NOT_READY;
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+        if (it->ticket == ticket) {
+            std::vector<Pending> one;
+            one.push_back(std::move(*it));
+            s->pending.erase(it);
+            finish(s, one, ST_ERR_CANCELLED, nullptr, Clock::now(), nullptr, "cancelled");
+            s->cv.notify_all();
+            return ST_OK;
+        }
+    return ST_ERR_INVALID_ARG;
+}
+
 static int take_result(st_server s, uint64_t ticket, st_result *res, double *u_host) {
     auto it = s->results.find(ticket);
     if (it == s->results.end()) return ST_ERR_INVALID_ARG;
@@ -365,10 +492,11 @@ int st_serve_stop(st_server s) {
     {
         std::lock_guard<std::mutex> lock(s->mu);
         s->stop = true;
+        s->paused = false;  // queued work is finished before the workers exit
     }
     s->cv.notify_all();
     for (auto &t : s->threads) t.join();
-    for (auto &e : s->cache) destroy_entry(s, e.get());
+    for (auto &e : s->cache) free_entry(e.get());
     s->cache.clear();
     delete s;
     return ST_OK;

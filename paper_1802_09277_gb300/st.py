@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(PKG, "libst_iga.so")
 ST_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NOT_POSITIVE", -4: "ILL_CONDITIONED",
           -5: "NO_CONVERGENCE", -6: "TIMEOUT", -7: "CUDA", -8: "OVER_BUDGET",
-          -9: "UNSUPPORTED"}
+          -9: "UNSUPPORTED", -10: "NOT_READY", -11: "CANCELLED"}
 ST_ERR_INVALID_ARG = -1
 ST_ERR_NO_CONVERGENCE = -5
 ST_ERR_UNSUPPORTED = -9
@@ -31,7 +31,8 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_smooth_static", "st_block_minres", "st_vcycle",
            "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
            "st_time_prolongation", "st_level_shape", "st_space_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
-           "st_serve_submit", "st_serve_poll", "st_serve_wait", "st_serve_stop"]
+           "st_serve_submit", "st_serve_resume", "st_serve_cancel", "st_serve_poll", "st_serve_wait",
+           "st_serve_stop"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
                 "vector", "dot", "tc", "spec", "stencil_df", "minres"]
 
@@ -56,7 +57,7 @@ class StSolveInfo(ctypes.Structure):
 
 class StServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int),
-                ("max_batch", ctypes.c_int), ("opt", StOptions)]
+                ("max_batch", ctypes.c_int), ("opt", StOptions), ("start_paused", ctypes.c_int)]
 
 
 class StRequest(ctypes.Structure):
@@ -128,6 +129,8 @@ def load():
         "st_serve_opts_default": (V, [ctypes.POINTER(StServerOpts)]),
         "st_serve_start": (I, [ctypes.POINTER(P), ctypes.POINTER(StServerOpts)]),
         "st_serve_submit": (I, [P, ctypes.POINTER(StRequest), ctypes.POINTER(ctypes.c_uint64)]),
+        "st_serve_resume": (I, [P]),
+        "st_serve_cancel": (I, [P, ctypes.c_uint64]),
         "st_serve_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(StResult), dp]),
         "st_serve_wait": (I, [P, ctypes.c_uint64, D, ctypes.POINTER(StResult), dp]),
         "st_serve_stop": (I, [P]),
@@ -378,13 +381,14 @@ class Server:
     """Continuous-batching solve server (st_serve_*): submit host right-hand
     sides of any configuration, poll or wait for host solutions."""
 
-    def __init__(self, workers=4, max_batch=8, hbm_budget=0, **opts):
+    def __init__(self, workers=4, max_batch=8, hbm_budget=0, paused=False, **opts):
         lib = load()
         self.o = StServerOpts()
         lib.st_serve_opts_default(ctypes.byref(self.o))
         self.o.workers = int(workers)
         self.o.max_batch = int(max_batch)
         self.o.hbm_budget = int(hbm_budget)
+        self.o.start_paused = 1 if paused else 0
         self.o.opt = options(**opts)
         self._s = ctypes.c_void_p()
         _check(lib.st_serve_start(ctypes.byref(self._s), ctypes.byref(self.o)))
@@ -418,6 +422,19 @@ class Server:
         out = {k: getattr(res, k) for k, _ in StResult._fields_}
         out["error"] = res.error.decode(errors="replace")
         return out, u
+
+    def resume(self):
+        """Let the workers of a server started paused take requests."""
+        _check(_lib.st_serve_resume(self._s))
+
+    def cancel(self, ticket):
+        """True if the request was withdrawn before a worker took it, False
+        if it is already being solved."""
+        rc = _lib.st_serve_cancel(self._s, ctypes.c_uint64(ticket))
+        if rc == ST_ERR_NOT_READY:
+            return False
+        _check(rc)
+        return True
 
     def poll(self, ticket):
         """(result dict, solution) or None while pending."""

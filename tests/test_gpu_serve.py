@@ -52,12 +52,16 @@ def test_alone_vs_mix(st, prec, outer):
         assert res["status"] == 0 and res["batch_size"] == 1
         alone.append(u)
     srv.stop()
-    srv = st.Server(workers=3, max_batch=4, **opts)
+    # queue the whole mix before any worker starts, so that the repeated
+    # configurations are in the queue together and are batched
+    srv = st.Server(workers=3, max_batch=4, paused=True, **opts)
     tickets = [srv.submit(d, p, spans, N, c, tol=tol, coeffs=True) for d, spans, p, N, c in reqs]
+    srv.resume()
     mixed = [srv.wait(t, timeout=120.0) for t in tickets]
     srv.stop()
-    batched = max(res["batch_size"] for res, _ in mixed)
-    assert batched >= 2  # the repeated configurations were solved together
+    sizes = [res["batch_size"] for res, _ in mixed]
+    # every repeated configuration was solved as one batch
+    assert sizes == [MIX.count(m) for m in MIX], sizes
     for (d, spans, p, N, c), ua, (res, um) in zip(reqs, alone, mixed):
         assert res["status"] == 0
         # each right-hand side is refined on its own: same bits alone and in the mix
@@ -114,4 +118,23 @@ def test_poll_and_tickets(st):
     with pytest.raises(st.StError):
         srv.poll(t + 12345) if (t + 12345) in srv._n else st._check(
             st.load().st_serve_poll(srv._s, t + 12345, None, None))
+    srv.stop()
+
+
+def test_cancel_pending_request(st):
+    srv = st.Server(workers=1, max_batch=1, paused=True, precision="mixed_fp32", outer="ir")
+    d, spans, p, N = 1, (20,), 2, 4
+    pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+    t1 = srv.submit(d, p, spans, N, inputs.normal_coeffs(8, pr.ndofs), coeffs=True)
+    t2 = srv.submit(d, p, spans, N, inputs.normal_coeffs(9, pr.ndofs), coeffs=True)
+    assert srv.cancel(t2)  # nobody has taken it yet
+    res2, _ = srv.wait(t2, timeout=10.0)
+    assert res2["status"] == -11 and res2["error"] == "cancelled"
+    srv.resume()
+    res1, u1 = srv.wait(t1, timeout=60.0)
+    assert res1["status"] == 0
+    ud = S.forward_subst(pr, A.load_from_coeffs(pr, inputs.normal_coeffs(8, pr.ndofs)))
+    assert np.linalg.norm(u1 - ud) <= 1e-7 * np.linalg.norm(ud)
+    with pytest.raises(st.StError):  # finished and released: unknown ticket
+        srv.cancel(t1)
     srv.stop()
