@@ -416,3 +416,83 @@ def test_space_time_hierarchy_rule_and_convergence():
     assert np.linalg.norm(ux - ref) <= 1e-6 * np.linalg.norm(ref)
     assert it_x < it_t
     assert Hx.levels[-1].L.shape[0] * 10 < Ht.levels[-1].L.shape[0]
+
+
+# --------------------------------------------------------------------------
+# The V-cycle as a linear iteration (Sec. 3.1): one cycle maps the error
+# e = u* - u to E e with the multigrid error propagator written densely,
+#   two levels:  E_J = S^nu2 (I - P L_c^{-1} P^T L) S^nu1,
+#   more levels: E_l = S^nu2 (I - P (I - E_{l+1}) L_{l+1}^{-1} P^T L) S^nu1,
+# S = I - omega D^{-1} L, D = blockdiag(A_n) (inverted densely here), and
+# the coarsest level solved exactly.  A dropped smoothing loop, a restriction
+# of f instead of the residual, a missing coarse correction or a wrong
+# damping all change E.
+# --------------------------------------------------------------------------
+
+def _dense_propagator(H, lvl, nu1, nu2, omega):
+    L = H.levels[lvl].L.toarray()
+    n = L.shape[0]
+    if lvl == len(H.levels) - 1:
+        return np.zeros((n, n))  # exact coarsest solve: no error left
+    m = H.levels[lvl].m
+    Dinv = np.zeros_like(L)
+    for b in range(n // m):
+        sl_ = slice(b * m, (b + 1) * m)
+        Dinv[sl_, sl_] = np.linalg.inv(L[sl_, sl_])
+    Sm = np.eye(n) - omega * Dinv @ L
+    P = H.P[lvl].toarray()
+    Lc = H.levels[lvl + 1].L.toarray()
+    Ec = _dense_propagator(H, lvl + 1, nu1, nu2, omega)
+    # one cycle from zero on the coarse level returns (I - E_c) Lc^{-1} r_c
+    C = np.eye(n) - P @ (np.eye(Lc.shape[0]) - Ec) @ np.linalg.solve(Lc, P.T @ L)
+    return np.linalg.matrix_power(Sm, nu2) @ C @ np.linalg.matrix_power(Sm, nu1)
+
+
+@pytest.mark.parametrize("N,space_ratio", [(2, 0.0), (4, 0.0), (8, 0.0), (4, 1.0)])
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 1), (0, 1), (1, 0), (2, 2)])
+def test_vcycle_is_the_multigrid_error_propagator(N, space_ratio, nu1, nu2):
+    pr = A.Problem(1, (8,), 2, 2, N, theta=1.0)
+    H = S.Hierarchy(pr, space_ratio=space_ratio)
+    assert len(H.levels) >= 2
+    if space_ratio > 0:
+        assert "x" in H.kinds  # the space-coarsening branch is exercised too
+    rng = np.random.default_rng(100 * N + 10 * nu1 + nu2)
+    f = rng.standard_normal(pr.ndofs)
+    u0 = rng.standard_normal(pr.ndofs)
+    ustar = np.linalg.solve(H.levels[0].L.toarray(), f)
+    u1 = S.vcycle(H, f, nu1=nu1, nu2=nu2, omega=0.5, u=u0.copy())
+    E = _dense_propagator(H, 0, nu1, nu2, 0.5)
+    e1 = E @ (ustar - u0)
+    assert np.linalg.norm((ustar - u1) - e1) <= 1e-11 * np.linalg.norm(ustar - u0)
+    # and the cycle contracts the error (it is a convergent iteration)
+    assert np.max(np.abs(np.linalg.eigvals(E))) < 1.0
+
+
+def test_vcycle_propagator_rejects_planted_mistakes():
+    """The propagator check above catches the plausible mistakes: a cycle
+    without post-smoothing, one that restricts f instead of the residual,
+    and one without the coarse correction all move the error elsewhere."""
+    pr = A.Problem(1, (8,), 2, 2, 4, theta=1.0)
+    H = S.Hierarchy(pr)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal(pr.ndofs)
+    u0 = rng.standard_normal(pr.ndofs)
+    ustar = np.linalg.solve(H.levels[0].L.toarray(), f)
+    e1 = _dense_propagator(H, 0, 1, 1, 0.5) @ (ustar - u0)
+
+    def cycle(lvl, f, u, variant):
+        lev = H.levels[lvl]
+        if lvl == len(H.levels) - 1:
+            return H.coarse_lu.solve(f)
+        u = S.jacobi_step(lev, u, f, 0.5)
+        r = f - lev.L @ u
+        rc = H.P[lvl].T @ (f if variant == "restrict_f" else r)
+        if variant != "no_coarse":
+            u = u + H.P[lvl] @ cycle(lvl + 1, rc, np.zeros_like(rc), variant)
+        if variant != "no_post":
+            u = S.jacobi_step(lev, u, f, 0.5)
+        return u
+
+    for variant in ("no_post", "restrict_f", "no_coarse"):
+        ub = cycle(0, f, u0.copy(), variant)
+        assert np.linalg.norm((ustar - ub) - e1) > 1e-3 * np.linalg.norm(ustar - u0), variant
