@@ -1,18 +1,27 @@
 """Benchmark: space-time DoFs/s to relative residual 1e-8 on GB300.
 
-Workload (default "square64"): heat equation on (0,1)^2 x (0,1), B-spline
-degree 2 in space and time, 64 x 64 knot spans, 256 time slabs x 2 time
-elements (4 194 304 space-time dofs), theta = 1, right-hand side from i.i.d.
-N(0,1) B-spline coefficients (seed 2), zero initial guess.  Solver: FGMRES(20)
-right-preconditioned by one time-multigrid V-cycle (damped block Jacobi,
-omega = 1/2, nu1 = nu2 = 1, slab inverses by real-Schur time transform + fast
-diagonalisation in space), to ||f - L u|| <= 1e-8 ||f||.
+Default workload "cube48_x16": heat equation on (0,1)^3 x (0,1), B-spline
+degree 2 in space and time, 48^3 knot spans, 128 time slabs x 2 time
+elements (56 623 104 space-time dofs per right-hand side), theta = 1,
+16 right-hand sides of i.i.d. N(0,1) B-spline coefficients (seeds 400..415)
+solved together, zero initial guess, to ||f - L u|| <= 1e-8 ||f|| for every
+right-hand side.  Headline method: mixed precision -- iterative refinement
+with an FP64-accurate residual and FP64 update around an FP32 FGMRES(10),
+right-preconditioned by one time-multigrid V(1,1) cycle (damped block
+Jacobi, omega = 1/2, slab inverses by the real Schur time factors and fast
+diagonalisation in space, V-cycle in the spatial eigenbasis); the spatial
+transforms at the refinement boundary run as split TF32 on the tensor cores
+(FP32 accuracy).  Beside it on the same workload: the plain FP64 method
+(FP64 FGMRES and FP64 V-cycle) and FP64-outer FGMRES with the FP32 V-cycle.
+The 2D degree-3 workload "square128_p3" (128^2 spans, 1024 slabs, 32
+space-time Gaussian bumps) is measured after it with TF32 and BF16
+transforms and FP64 plain.  Every result carries the FP64 oracle's residual
+of the returned solution on sampled slabs.
 
-One step = one whole solve with the right-hand side resident in HBM.  `value`
-is the mixed-precision method (FP32 V-cycle, FP64 outer residual and update);
-the plain FP64 method on the same workload is reported beside it.
+One step = one whole solve with the right-hand sides resident in HBM.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+                  [--workload NAME]
 """
 import argparse
 import json
@@ -35,9 +44,23 @@ WORKLOADS = {
 }
 # right-hand side: "coeffs" = N(0,1) B-spline coefficients (one seed per rhs),
 # "bumps" = 32 space-time Gaussian bumps; number of rhs solved together;
-# FGMRES restart (memory); variants measured beside the headline
-RHS = {"square64": ("coeffs", 1, 20, "all"), "square128_p3": ("bumps", 1, 20, "min"),
-       "cube48_x16": ("coeffs", 16, 10, "none"), "interval16": ("coeffs", 1, 20, "all")}
+# FGMRES restart (memory: 16 FP64 rhs of cube48 are 7.25 GB per vector)
+RHS = {"square64": ("coeffs", 1, 20), "square128_p3": ("bumps", 1, 20),
+       "cube48_x16": ("coeffs", 16, 10), "interval16": ("coeffs", 1, 20)}
+# the plain FP64 method on each workload: FP64 FGMRES + FP64 V-cycle.  On the
+# large workloads its V-cycle runs in the spatial eigenbasis (the same
+# iterates as the B-spline-basis cycle, whose FP64 transforms in every
+# smoothing step take about a minute per cube48_x16 solve)
+FP64_PLAIN = {"square64": ("fp64", "nodal", "fgmres"), "interval16": ("fp64", "nodal", "fgmres"),
+              "square128_p3": ("fp64", "spectral", "fgmres"),
+              "cube48_x16": ("fp64", "spectral", "fgmres")}
+# variant sets measured beside the headline; extra workloads measured after it
+VSET = {"square64": "all", "interval16": "all", "square128_p3": "min", "cube48_x16": "outer64"}
+EXTRA = {"cube48_x16": ["square128_p3"]}
+# the oracle's bounded CPU sample of each workload: spatial spans and slabs
+# (same dimension, degree, time elements per slab and slab length)
+ORACLE_SAMPLE = {"square64": ((64, 64), 8), "square128_p3": ((16, 16), 8),
+                 "cube48_x16": ((8, 8, 8), 8), "interval16": ((16,), 8)}
 METRIC = "space-time DoFs/s to rel. residual 1e-8, mixed vs FP64 plain; serve p50/p99"
 UNIT = "DoFs/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -67,49 +90,180 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def workload_config(name, precision, basis, outer, fused):
+    d, spans, p, N, ne, tol, seed = WORKLOADS[name]
+    kind, nrhs, restart = RHS[name]
+    if kind == "bumps":
+        rhs = "32 space-time Gaussian bumps (centres U(0,1)^%d, widths U(0.05,0.2), " \
+              "amplitudes N(0,1)), seed %d" % (d + 1, seed)
+    elif nrhs > 1:
+        rhs = "%d right-hand sides of N(0,1) B-spline coefficients, seeds %d..%d, solved " \
+              "together" % (nrhs, seed, seed + nrhs - 1)
+    else:
+        rhs = "N(0,1) B-spline coefficients, seed %d" % seed
+    if outer == "ir":
+        solver = ("iterative refinement (FP64-accurate residual, FP64 update) around FP32 "
+                  "FGMRES(%d), right-preconditioned by one V(1,1) time-multigrid cycle, "
+                  "omega=0.5" % restart)
+    elif outer == "mg":
+        solver = "multigrid iteration with V(1,1) time-multigrid cycles, omega=0.5"
+    else:
+        solver = ("FP64 FGMRES(%d), right-preconditioned by one V(1,1) time-multigrid cycle, "
+                  "omega=0.5" % restart)
+    return {"workload": name,
+            "domain": "unit %s" % {1: "interval", 2: "square", 3: "cube"}[d],
+            "spans": list(spans), "degree": p, "slabs": N, "time_elements_per_slab": ne,
+            "theta": 1.0, "tol": tol, "nrhs": nrhs, "solver": solver, "precision": precision,
+            "vcycle_basis": basis, "outer": outer, "fused_vcycle": fused, "rhs": rhs,
+            "l2": "flushed between steps (256 MB write)"}
+
+
 # ----------------------------------------------------------------------------
-# CPU oracle leg (runs in a child process, single-threaded BLAS)
+# CPU oracle legs (a child process with single-threaded BLAS; the all-cores
+# leg runs one oracle solve per core in a spawned process pool)
 # ----------------------------------------------------------------------------
 
-def cpu_leg(args):
-    """Time the oracle's FGMRES + V-cycle solve on a bounded sample of the
-    workload: the same spatial grid, degree and slab size with fewer slabs."""
-    import numpy as np
+_ORACLE = {}
+
+
+def _oracle_init(workload):
+    """Build the oracle's sample problem and multigrid hierarchy (setup,
+    not timed, as in Table 4's setup / solve split)."""
+    from oracle import assemble as A
+    from oracle import solve as S
+    d, spans, p, N, ne, tol, seed = WORKLOADS[workload]
+    sspans, ns = ORACLE_SAMPLE[workload]
+    pr = A.Problem(d, sspans, p, ne, ns, theta=1.0, T=float(ns) / N)
+    _ORACLE.update(pr=pr, H=S.Hierarchy(pr), tol=tol, seed=seed)
+
+
+def _oracle_solve(k):
+    """One oracle solve (FGMRES + V-cycle with sparse-LU slab solves) of the
+    sample problem with right-hand side number k; returns seconds."""
     from oracle import assemble as A
     from oracle import solve as S
     from paper_1802_09277_gb300 import inputs
-    d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
-    n_sample = args.sample_slabs
-    pr = A.Problem(d, spans, p, ne, n_sample, theta=1.0, T=float(n_sample) / N)
-    c = inputs.normal_coeffs(seed, pr.ndofs)
-    f = A.load_from_coeffs(pr, c)
-    H = S.Hierarchy(pr)
-    L = H.levels[0].L
-    reps, total, iters = 0, 0.0, 0
+    pr, H = _ORACLE["pr"], _ORACLE["H"]
+    f = A.load_from_coeffs(pr, inputs.normal_coeffs(_ORACLE["seed"] + k, pr.ndofs))
+    t0 = time.perf_counter()
+    S.fgmres(H.levels[0].L, f, lambda v: S.vcycle(H, v), tol=_ORACLE["tol"], restart=20)
+    return time.perf_counter() - t0
+
+
+def cpu_leg(args):
+    """Time the oracle on the sample: `single` solves on one core for about
+    `seconds`, then rounds of one solve per core on `procs` cores (a round is
+    one step of the reference arm)."""
+    import multiprocessing as mp
+    _oracle_init(args.workload)
+    pr = _ORACLE["pr"]
+    out = {"sample_dofs": pr.ndofs, "sample_spans": list(pr.spans), "sample_slabs": pr.N}
+    single = []
     t_end = time.perf_counter() + args.cpu_seconds
     while True:
-        t0 = time.perf_counter()
-        u, it, hist = S.fgmres(L, f, lambda v: S.vcycle(H, v), tol=tol, restart=20)
-        total += time.perf_counter() - t0
-        reps += 1
-        iters = it
-        if time.perf_counter() >= t_end or reps >= 50:
+        single.append(_oracle_solve(len(single)))
+        if len(single) >= max(1, args.cpu_single_min) and time.perf_counter() >= t_end:
             break
-    out = {"value": pr.ndofs * reps / total, "seconds_per_solve": total / reps,
-           "iterations": iters, "sample_dofs": pr.ndofs, "sample_slabs": n_sample,
-           "reps": reps}
+    out["single"] = {"value": pr.ndofs / (sum(single) / len(single)),
+                     "seconds_per_solve": sum(single) / len(single), "solves": len(single)}
+    P = args.cpu_procs
+    if P > 1:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(P, initializer=_oracle_init, initargs=(args.workload,)) as pool:
+            pool.map(_oracle_solve, range(P))  # every worker has built its hierarchy
+            rounds = []
+            t_end = time.perf_counter() + args.cpu_seconds
+            for k in range(args.cpu_warmup + args.cpu_rounds):
+                t0 = time.perf_counter()
+                pool.map(_oracle_solve, [P * k + q for q in range(P)], chunksize=1)
+                dt = time.perf_counter() - t0
+                if k >= args.cpu_warmup:
+                    rounds.append(dt)
+                if args.cpu_rounds_bounded and time.perf_counter() >= t_end and rounds:
+                    break
+        out["all"] = {"value": P * pr.ndofs / (sum(rounds) / len(rounds)), "cores": P,
+                      "seconds_per_round": sum(rounds) / len(rounds), "rounds": len(rounds)}
     print(json.dumps(out))
 
 
-def run_cpu_leg(workload, sample_slabs, seconds):
+def run_cpu_leg(workload, seconds, procs, rounds=1000, warmup=0, bounded=True, single_min=1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "--workload", workload,
-           "--sample-slabs", str(sample_slabs), "--cpu-seconds", str(seconds)]
-    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+           "--cpu-seconds", str(seconds), "--cpu-procs", str(procs), "--cpu-rounds", str(rounds),
+           "--cpu-warmup", str(warmup), "--cpu-single-min", str(single_min)]
+    if bounded:
+        cmd.append("--cpu-rounds-bounded")
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
     if res.returncode != 0:
         raise RuntimeError("cpu leg failed: " + res.stderr[-2000:])
     return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def sample_text(workload, r):
+    d, spans, p, N, ne, tol, seed = WORKLOADS[workload]
+    return ("oracle FGMRES(20) + V(1,1) with sparse-LU slab solves on a sample of %s: %s spans, "
+            "%d of %d slabs (%d dofs), same degree, time elements and slab length; "
+            "N(0,1) coefficient rhs; setup (LU factorisations) not timed" % (
+                workload, "x".join(str(s) for s in r["sample_spans"]), r["sample_slabs"], N,
+                r["sample_dofs"]))
+
+
+# ----------------------------------------------------------------------------
+# FP64 oracle residual of a returned solution on sampled slabs
+# ----------------------------------------------------------------------------
+
+def oracle_slab_residual(workload, sols, cache, rank=0, slabs_per_rhs=6):
+    """||f_n - A u_n + B u_{n-1}|| / ||f_n|| summed over sampled slabs n of
+    the first and last right-hand side, with A, B and f_n from the FP64 oracle
+    (slab blocks of Eq. 2.4-2.5, the exact load vector).  sols: {name: host
+    float64 array of all right-hand sides}; returns {name: relative residual}."""
+    import numpy as np
+    from oracle import assemble as A
+    from paper_1802_09277_gb300 import inputs
+    d, spans, p, N, ne, tol, seed = WORKLOADS[workload]
+    kind, nrhs, _ = RHS[workload]
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    m = pr.Nt * pr.Nx
+    picks = sorted({0, 1, N // 2, N - 1} | {int(x) for x in np.random.default_rng(7).integers(
+        2, N - 1, max(0, slabs_per_rhs - 4))})
+    rhs_ids = sorted({0, nrhs - 1})
+    if "blocks" not in cache:
+        cache["blocks"] = A.slab_blocks(pr)
+        F = {}
+        if kind == "bumps":
+            cen, wid, amp = inputs.gaussian_bumps(seed + 1000 * rank, count=32, dim=d + 1)
+            Fs = A.bumps_load(pr, cen, wid, amp, slabs=picks).reshape(len(picks), m)
+            for i, n in enumerate(picks):
+                F[(0, n)] = Fs[i]
+        else:
+            # all slabs are alike, so a problem of len(picks) slabs holds the
+            # picked slabs' loads (M_t (x) M_x) c_n
+            sub = A.Problem(d, spans, p, ne, len(picks) * len(rhs_ids), theta=1.0,
+                            T=float(len(picks) * len(rhs_ids)) / N)
+            cs = []
+            for q in rhs_ids:
+                c = inputs.normal_coeffs(seed + 1000 * rank + q, N * m).reshape(N, m)
+                cs += [c[n] for n in picks]
+            Fs = A.load_from_coeffs(sub, np.concatenate(cs)).reshape(-1, m)
+            i = 0
+            for q in rhs_ids:
+                for n in picks:
+                    F[(q, n)] = Fs[i]
+                    i += 1
+        cache["F"] = F
+    Ab, Bb = cache["blocks"]
+    out = {}
+    for name, u in sols.items():
+        U = np.asarray(u).reshape(nrhs, N, m)
+        num = den = 0.0
+        for (q, n), f in cache["F"].items():
+            r = f - Ab @ U[q, n] + (Bb @ U[q, n - 1] if n else 0.0)
+            num += float(r @ r)
+            den += float(f @ f)
+        out[name] = float(np.sqrt(num / den))
+    out["_sampled"] = "slabs %s of rhs %s" % (picks, rhs_ids)
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -185,8 +339,9 @@ def gpu_arm(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
-    rhs_kind, nrhs, restart, vset = RHS[args.workload]
+    wl = args.workload
+    d, spans, p, N, ne, tol, seed = WORKLOADS[wl]
+    rhs_kind, nrhs, restart = RHS[wl]
     common = dict(ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
     peaks, peak_src = load_peaks()
 
@@ -198,8 +353,6 @@ def gpu_arm(args, rank, world):
 
     # rank r solves its own right-hand side(s) (independent replicas)
     n1 = make_len(d, spans, p, N, ne)
-    c = torch.tensor(np.concatenate([inputs.normal_coeffs(seed + 1000 * rank + q, n1)
-                                     for q in range(nrhs)]), dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def barrier():
@@ -244,13 +397,15 @@ def gpu_arm(args, rank, world):
 
     # --- mixed precision (headline) ---
     sm, setup_ms = timed_make(args.precision, args.basis, args.outer)
-    f = torch.empty_like(c)
+    f = torch.empty(nrhs * n1, dtype=torch.float64, device=dev)
     if rhs_kind == "bumps":
         cen, wid, amp = inputs.gaussian_bumps(seed + 1000 * rank, count=32, dim=d + 1)
         sm.load_gaussians(cen, wid, amp, f)
     else:
+        c = torch.tensor(np.concatenate([inputs.normal_coeffs(seed + 1000 * rank + q, n1)
+                                         for q in range(nrhs)]), dtype=torch.float64, device=dev)
         sm.load_coeffs(c, f)
-    del c
+        del c
     t0 = time.perf_counter()
     tuning = sm.autotune()  # also runs inside the first solve (opt.autotune)
     autotune_ms = 1e3 * (time.perf_counter() - t0)
@@ -288,11 +443,12 @@ def gpu_arm(args, rank, world):
 
     # --- the other variants on the same workload (fewer steps, no profiling) ---
     variants = {}
-    u64 = None
-    u_mixed = u_mixed.cpu()
-    ndofs_h = sm.ndofs
+    sols = {"mixed": u_mixed.cpu().numpy()}
+    del u_mixed
+    ndofs = sm.ndofs
     sm.close()
     torch.cuda.empty_cache()
+    plain = FP64_PLAIN[wl] + (args.fused, "fd", "rschur", 0.0)
     allv = (("fp64", "nodal", "fgmres"), ("fp64", "spectral", "fgmres"),
             ("mixed_fp32", "nodal", "fgmres"), ("mixed_fp32", "spectral", "fgmres"),
             ("mixed_fp32", "spectral", "ir"), ("mixed_tf32", "spectral", "ir"),
@@ -305,10 +461,14 @@ def gpu_arm(args, rank, world):
     # space-time coarsening of the B-spline-basis V-cycle (space while tau/h^2 > 1)
     allv.append(("mixed_fp32", "nodal", "fgmres", args.fused, "fd", "rschur", 1.0))
     allv.append((args.precision, args.basis, args.outer, 1 - args.fused, "fd", "rschur", 0.0))
-    chosen = {"all": allv, "min": [allv[0], allv[-1]], "none": []}[vset]
+    chosen = {"all": allv, "min": [allv[6]],
+              # FP64-outer FGMRES with the FP32 V-cycle (FP32 transforms)
+              "outer64": [("mixed_fp32", "spectral", "fgmres", args.fused, "fd", "rschur", 0.0)],
+              "none": []}[VSET[wl]]
+    chosen = [plain] + [v for v in chosen if v != plain]
     for prec, basis, outer, fz, spatial, fac, sratio in chosen:
-        name = "fp64_plain" if (prec, basis, spatial, sratio) == ("fp64", "nodal", "fd", 0.0) \
-            else "%s_%s_%s" % (prec, basis, outer)
+        is_plain = (prec, basis, outer, fz, spatial, fac, sratio) == plain
+        name = "fp64_plain" if is_plain else "%s_%s_%s" % (prec, basis, outer)
         if spatial != "fd":
             name += "_" + spatial + ("" if fac == "rschur" else "_" + fac)
         if sratio > 0:
@@ -316,7 +476,7 @@ def gpu_arm(args, rank, world):
         if fz != args.fused:
             name += "_fused" if fz else "_levelwise"
         elif (prec, basis, outer, spatial, sratio) == (args.precision, args.basis, args.outer,
-                                                       "fd", 0.0) and name != "fp64_plain":
+                                                       "fd", 0.0) and not is_plain:
             continue
         sv, sv_setup_ms = timed_make(prec, basis, outer, fz, spatial, fac, sratio)
         tv, iv, uv, _ = timed_solves(sv, f, max(1, args.steps // 2), 1)
@@ -325,24 +485,29 @@ def gpu_arm(args, rank, world):
                           "spatial_solver": spatial, "variant": fac, "space_ratio": sratio,
                           "levels": "".join(k for _, _, k in sv.level_shapes()[1:]),
                           "setup_ms": sv_setup_ms,
-                          "ms_per_step": msv,
+                          "ms_per_step": msv, "steps": len(tv),
                           "value": sv.ndofs * world / (msv / 1e3),
                           "iterations": iv[-1]["iterations"],
                           "refinements": iv[-1].get("refinements", 0),
                           "rel_residual": iv[-1]["rel_residual"]}
-        if name == "fp64_plain":
-            u64 = uv.cpu()
+        if is_plain or VSET[wl] == "outer64":
+            sols[name] = uv.cpu().numpy()
         del uv
         sv.close()
         torch.cuda.empty_cache()
-    # the FP64 reference solve (skipped where one takes about a minute)
-    v64 = variants.get("fp64_plain")
-    ms64 = v64["ms_per_step"] if v64 else None
-    i64 = [{"iterations": v64["iterations"] if v64 else None,
-            "rel_residual": v64["rel_residual"] if v64 else None}]
-    rel_diff = (float(torch.linalg.norm(u_mixed - u64) / torch.linalg.norm(u64))
-                if u64 is not None else None)
-    ndofs = ndofs_h
+    del f, flush
+    torch.cuda.empty_cache()
+    v64 = variants.pop("fp64_plain")
+    rel_diff = float(np.linalg.norm(sols["mixed"] - sols["fp64_plain"]) /
+                     np.linalg.norm(sols["fp64_plain"]))
+
+    # --- the FP64 oracle's residual of each returned solution ---
+    oracle = None
+    if rank == 0 and not args.no_oracle_check:
+        t0 = time.perf_counter()
+        oracle = oracle_slab_residual(wl, sols, {}, rank)
+        oracle["_seconds"] = time.perf_counter() - t0
+    del sols
 
     # --- roofline of the dominant kernel class ---
     dom = max(prof, key=lambda k: prof[k]["ms"])
@@ -350,19 +515,82 @@ def gpu_arm(args, rank, world):
     per_launch_ms = pd["ms"] / max(pd["launches"], 1)
     launches = sum(v["launches"] for v in prof.values())
     result = {
-        "ndofs": ndofs, "ms_mixed": ms, "ms_mixed_max": ms_max, "ms64": ms64, "ms_prof": ms_prof,
+        "ndofs": ndofs, "ms_mixed": ms, "ms_mixed_max": ms_max, "ms_prof": ms_prof,
         "iters_mixed": i_mixed[-1]["iterations"], "res_mixed": i_mixed[-1]["rel_residual"],
-        "refin_mixed": i_mixed[-1].get("refinements", 0),
-        "iters64": i64[-1]["iterations"], "res64": i64[-1]["rel_residual"],
-        "rel_diff_mixed_vs_fp64": rel_diff, "e2e_ms": e2e_ms, "bytes_h2d": f.numel() * 8,
-        "bytes_d2h": f.numel() * 8, "prof": prof, "dominant": dom,
+        "refin_mixed": i_mixed[-1].get("refinements", 0), "fp64_plain": v64,
+        "rel_diff_mixed_vs_fp64": rel_diff, "e2e_ms": e2e_ms, "bytes_h2d": ndofs * 8,
+        "bytes_d2h": ndofs * 8, "prof": prof, "dominant": dom,
         "per_launch_ms": per_launch_ms, "launches": launches // max(args.steps, 1),
         "launches_total": launches, "clocks": clk, "peaks": peaks, "peak_src": peak_src,
-        "variants": variants, "tuning": tuning,
+        "variants": variants, "tuning": tuning, "oracle": oracle,
         "setup_ms": {"setup": setup_ms, "autotune": autotune_ms},
-        "traffic_key": (args.workload, args.precision, args.basis, args.outer),
+        "traffic_key": (wl, args.precision, args.basis, args.outer),
     }
     return result
+
+
+def extra_workload(args, name):
+    """A second workload measured after the headline (one GPU): the mixed
+    TF32 and BF16 refinement solves and the plain FP64 method, each with the
+    FP64 oracle's residual of its solution on sampled slabs."""
+    import torch
+    from paper_1802_09277_gb300 import inputs, st
+    d, spans, p, N, ne, tol, seed = WORKLOADS[name]
+    rhs_kind, nrhs, restart = RHS[name]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    specs = [("mixed_tf32", "spectral", "ir"), ("mixed_bf16", "spectral", "ir"), FP64_PLAIN[name]]
+    out, sols, f = {}, {}, None
+    for prec, basis, outer in specs:
+        key = "fp64_plain" if (prec, basis, outer) == FP64_PLAIN[name] else "%s_%s_%s" % (
+            prec, basis, outer)
+        t0 = time.perf_counter()
+        sv = st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
+                       outer=outer, ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        if f is None:
+            f = torch.empty(sv.ndofs, dtype=torch.float64, device="cuda")
+            if rhs_kind == "bumps":
+                cen, wid, amp = inputs.gaussian_bumps(seed, count=32, dim=d + 1)
+                sv.load_gaussians(cen, wid, amp, f)
+            else:
+                import numpy as np
+                c = torch.tensor(np.concatenate([inputs.normal_coeffs(seed + q, sv.ndofs // nrhs)
+                                                 for q in range(nrhs)]), device="cuda")
+                sv.load_coeffs(c, f)
+                del c
+        u = torch.zeros_like(f)
+        steps = args.steps if prec != "fp64" else max(1, args.steps // 2)
+        for _ in range(1 if prec == "fp64" else args.warmup):
+            sv.solve(f, u, tol=tol)
+        times = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = sv.solve(f, u, tol=tol)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = sum(times) / len(times)
+        out[key] = {"precision": prec, "basis": basis, "outer": outer, "setup_ms": setup_ms,
+                    "ms_per_step": ms, "steps": steps, "value": sv.ndofs / (ms / 1e3),
+                    "iterations": info["iterations"], "refinements": info.get("refinements", 0),
+                    "rel_residual": info["rel_residual"]}
+        sols[key] = u.cpu().numpy()
+        del u
+        sv.close()
+        torch.cuda.empty_cache()
+    del f, flush
+    torch.cuda.empty_cache()
+    if not args.no_oracle_check:
+        orc = oracle_slab_residual(name, sols, {})
+        for k in out:
+            out[k]["oracle_rel_residual"] = orc[k]
+        out["oracle_sampled"] = orc["_sampled"]
+    out["config"] = workload_config(name, "mixed_tf32", "spectral", "ir", 0)
+    return out
 
 
 def serve_arm(args):
@@ -480,12 +708,18 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="square64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="cube48_x16", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-leg", action="store_true")
-    ap.add_argument("--sample-slabs", type=int, default=8)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-procs", type=int, default=0, help="0 = every host core")
+    ap.add_argument("--cpu-rounds", type=int, default=1000)
+    ap.add_argument("--cpu-warmup", type=int, default=0)
+    ap.add_argument("--cpu-rounds-bounded", action="store_true")
+    ap.add_argument("--cpu-single-min", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--clocks-csv", default=None,
                     help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--serve-requests", type=int, default=512)
@@ -498,6 +732,9 @@ def main():
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
                     help="eigenbasis V-cycle as one shared-memory kernel (1) or level by level (0)")
     args = ap.parse_args()
+    ncores = os.cpu_count() or 1
+    if args.cpu_procs <= 0:
+        args.cpu_procs = ncores
 
     if args.cpu_leg:
         cpu_leg(args)
@@ -505,29 +742,37 @@ def main():
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    d, spans, p, N, ne, tol, seed = WORKLOADS[args.workload]
-    cfg = {"workload": args.workload, "domain": "unit %s" % {1: "interval", 2: "square", 3: "cube"}[d],
-           "spans": list(spans), "degree": p, "slabs": N, "time_elements_per_slab": ne,
-           "theta": 1.0, "tol": tol, "solver": "V(1,1) time multigrid, omega=0.5, FGMRES(20) restart",
-           "precision": args.precision, "vcycle_basis": args.basis, "outer": args.outer,
-           "fused_vcycle": args.fused,
-           "rhs": "N(0,1) B-spline coefficients, seed %d" % seed, "l2": "flushed between steps"}
+    wl = args.workload
+    cfg = workload_config(wl, args.precision, args.basis, args.outer, args.fused)
 
     if args.impl == "reference":
         if rank != 0:
             return
-        ncores = os.cpu_count()
-        r = run_cpu_leg(args.workload, args.sample_slabs, max(5.0, args.cpu_seconds))
-        line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT,
-                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * r["seconds_per_solve"], "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": cfg,
-                "cpu_baseline": {"value": r["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                 "host_cores_available": ncores,
-                                 "sample": "%d of %d slabs (%d dofs), same grid/degree/slab size, "
-                                           "%d solves" % (r["sample_slabs"], N, r["sample_dofs"], r["reps"])},
-                "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+        # one step = one round of concurrent oracle solves of the sample, one
+        # per host core (setup excluded); a few single-core solves beside it
+        r = run_cpu_leg(wl, 0.0, args.cpu_procs, rounds=args.steps, warmup=args.warmup,
+                        bounded=False, single_min=3)
+        leg = r.get("all") or {"value": r["single"]["value"], "cores": 1,
+                               "seconds_per_round": r["single"]["seconds_per_solve"],
+                               "rounds": r["single"]["solves"]}
+        cfg_ref = {k: v for k, v in cfg.items()
+                   if k not in ("vcycle_basis", "outer", "fused_vcycle", "l2")}
+        cfg_ref.update(precision="fp64", solver="oracle: FGMRES(20) + V(1,1) time multigrid "
+                       "with sparse-LU slab solves (FP64, CPU)")
+        line = {"impl": "reference", "metric": METRIC, "value": leg["value"], "unit": UNIT,
+                "n_gpus": args.gpus, "steps": leg["rounds"], "warmup": args.warmup,
+                "ms_per_step": 1e3 * leg["seconds_per_round"],
+                "step": "one round of %d concurrent oracle solves of the sample, one per host "
+                        "core" % leg["cores"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg_ref,
+                "cpu_baseline": {"value": leg["value"], "unit": UNIT, "cores": leg["cores"],
+                                 "kind": "oracle", "host_cores_available": ncores,
+                                 "sample": sample_text(wl, r),
+                                 "single_core": {"value": r["single"]["value"], "cores": 1,
+                                                 "ms_per_solve": 1e3 * r["single"]["seconds_per_solve"],
+                                                 "solves": r["single"]["solves"]}},
+                "e2e": {"value": leg["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -543,6 +788,13 @@ def main():
         return
     ndofs = r["ndofs"]
     value = job_value(ndofs, world, r["ms_mixed_max"])
+    extra = {}
+    if not args.no_extra and world == 1:
+        for name in EXTRA.get(wl, []):
+            try:
+                extra[name] = extra_workload(args, name)
+            except Exception as e:
+                extra[name] = {"error": str(e)[:300]}
     serve = None
     if not args.no_serve and world == 1:
         try:
@@ -552,14 +804,22 @@ def main():
     cpu = None
     if not args.no_cpu and world == 1:
         try:
-            cb = run_cpu_leg(args.workload, args.sample_slabs, args.cpu_seconds)
-            cpu = {"value": cb["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "host_cores_available": os.cpu_count(),
-                   "sample": "%d of %d slabs (%d dofs), same grid/degree/slab size, FGMRES + V-cycle "
-                             "with sparse-LU slab solves, %d solves" % (
-                                 cb["sample_slabs"], N, cb["sample_dofs"], cb["reps"])}
+            cb = run_cpu_leg(wl, args.cpu_seconds, args.cpu_procs, bounded=True, single_min=2)
+            leg = cb.get("all") or {"value": cb["single"]["value"], "cores": 1}
+            cpu = {"value": leg["value"], "unit": UNIT, "cores": leg["cores"], "kind": "oracle",
+                   "host_cores_available": ncores, "sample": sample_text(wl, cb),
+                   "single_core": {"value": cb["single"]["value"], "cores": 1,
+                                   "ms_per_solve": 1e3 * cb["single"]["seconds_per_solve"]}}
         except Exception as e:  # the GPU number stands without it
-            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(e)[:200]}
+            cpu = {"value": None, "unit": UNIT, "cores": args.cpu_procs, "kind": "oracle",
+                   "error": str(e)[:200]}
+    v64 = r["fp64_plain"]
+    orc = r["oracle"] or {}
+    if v64 is not None:
+        v64 = dict(v64, dtype="f64", oracle_rel_residual=orc.get("fp64_plain"))
+    for k, v in r["variants"].items():
+        if k in orc:
+            v["oracle_rel_residual"] = orc[k]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_mixed_max"], "higher_is_better": True,
@@ -568,13 +828,17 @@ def main():
         "config": cfg,
         "iterations": r["iters_mixed"], "refinements": r["refin_mixed"],
         "rel_residual": r["res_mixed"],
-        "fp64_plain": None if r["ms64"] is None else {
-                       "value": ndofs * world / (r["ms64"] / 1e3), "ms_per_step": r["ms64"],
-                       "iterations": r["iters64"], "rel_residual": r["res64"], "dtype": "f64",
-                       "basis": "nodal"},
-        "variants": r["variants"],
-        "setup_ms": r["setup_ms"],
+        "oracle_rel_residual": orc.get("mixed"),
+        "oracle_check": None if not orc else {
+            "what": "FP64 oracle residual ||f_n - A u_n + B u_{n-1}|| / ||f_n|| of the returned "
+                    "solution (Eq. 2.4-2.5 slab blocks, exact load vector)",
+            "sampled": orc.get("_sampled"), "seconds": orc.get("_seconds")},
+        "fp64_plain": v64,
+        "mixed_vs_fp64_speedup": (v64["ms_per_step"] / r["ms_mixed"]) if v64 else None,
         "mixed_vs_fp64_solution_rel_diff": r["rel_diff_mixed_vs_fp64"],
+        "variants": r["variants"],
+        "extra_workloads": extra,
+        "setup_ms": r["setup_ms"],
         "roofline": roofline_entry(r),
         "profiled_ms_per_step": r["ms_prof"],
         "kernel_classes": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),

@@ -210,15 +210,17 @@ def _time_load(prob, n, func, npts):
     return W.T @ (w * func(t))
 
 
-def _separable_load(prob, space_funcs, time_func, npts):
-    """Load vector of f(x,t) = prod_a space_funcs[a](x_a) * time_func(t)."""
+def _separable_load(prob, space_funcs, time_func, npts, slabs=None):
+    """Load vector of f(x,t) = prod_a space_funcs[a](x_a) * time_func(t),
+    on the slabs listed in `slabs` (all slabs if None), in that order."""
     gx = None
     for a in range(prob.d):
         g = _space_load_1d(prob.spans[a], prob.p, space_funcs[a], npts)
         gx = g if gx is None else np.kron(g, gx)
-    out = np.zeros((prob.N, prob.Nt, prob.Nx))
-    for n in range(prob.N):
-        out[n] = np.outer(_time_load(prob, n, time_func, npts), gx)
+    slabs = range(prob.N) if slabs is None else list(slabs)
+    out = np.zeros((len(slabs), prob.Nt, prob.Nx))
+    for i, n in enumerate(slabs):
+        out[i] = np.outer(_time_load(prob, n, time_func, npts), gx)
     return out.reshape(-1)
 
 
@@ -232,17 +234,19 @@ def manufactured_load(prob):
     return _separable_load(prob, sx, ft, 2 * prob.p + 4)
 
 
-def bumps_load(prob, centers, widths, amps, npts=None):
+def bumps_load(prob, centers, widths, amps, npts=None, slabs=None):
     """Load vector of f(x,t) = sum_k a_k exp(-|(x,t) - c_k|^2 / (2 w_k^2)),
     space-time Gaussian bumps (centers [K, d+1] in (x, y, z, t) order),
-    Gauss-Legendre quadrature with npts (default 2p+4) points per element."""
+    Gauss-Legendre quadrature with npts (default 2p+4) points per element;
+    only the slabs listed in `slabs` (all if None), in that order."""
     npts = 2 * prob.p + 4 if npts is None else npts
-    out = np.zeros(prob.ndofs)
+    ns = prob.N if slabs is None else len(list(slabs))
+    out = np.zeros(ns * prob.Nt * prob.Nx)
     for c, wk, a in zip(centers, widths, amps):
         sfun = [(lambda x, cc=c[i], ww=wk: np.exp(-(x - cc) ** 2 / (2 * ww * ww)))
                 for i in range(prob.d)]
         tfun = lambda t, cc=c[prob.d], ww=wk: a * np.exp(-(t - cc) ** 2 / (2 * ww * ww))
-        out += _separable_load(prob, sfun, tfun, npts)
+        out += _separable_load(prob, sfun, tfun, npts, slabs)
     return out
 
 

@@ -273,6 +273,9 @@ def test_bumps_load_by_brute_force_quadrature():
                  for c, w, a in zip(cen, wid, amp))
         ref = np.einsum('t,y,x,tyx,ta,yj,xi->aji', wt, wy, wx, fv, test, By, Bx)
         assert np.allclose(f[n], ref, rtol=1e-9, atol=1e-12)
+    # a subset of slabs, in the order asked for, gives the same rows
+    sub = A.bumps_load(pr, cen, wid, amp, npts=12, slabs=[1, 0]).reshape(f.shape)
+    assert np.array_equal(sub[0], f[1]) and np.array_equal(sub[1], f[0])
 
 
 # --------------------------------------------------------------------------
