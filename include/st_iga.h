@@ -52,6 +52,7 @@ extern "C" {
 #define ST_ERR_CUDA            -7  /* a CUDA runtime call failed                 */
 #define ST_ERR_OVER_BUDGET     -8  /* request exceeds the HBM budget             */
 #define ST_ERR_UNSUPPORTED     -9  /* valid but not built (e.g. degree > 3)      */
+#define ST_ERR_COMM           -12  /* a communication callback of a partitioned handle failed */
 
 /* geometry: the spatial domain (0,1)^d */
 #define ST_INTERVAL 1
@@ -241,6 +242,15 @@ int st_load_gaussians(st_handle h, int nbumps, const double *centers, const doub
  * stay FP64 at the interface).  u: in/out, f: in, device, n_dofs each. */
 int st_smooth(st_handle h, double *u, const double *f, int nsteps);
 
+/* Bound on each device-side wait of the tensor-core transforms (the wait for
+ * an MMA group's completion signal), in seconds: 0 <= seconds <= 60, default
+ * 1.  When a wait runs out, the kernel records it, waits (bounded) for its
+ * MMAs in flight, frees its tensor memory and returns, and the next
+ * st_solve / st_vcycle returns ST_ERR_TIMEOUT; the handle stays usable.
+ * 0 makes every such wait a single test of the signal (for fault-handling
+ * tests).  Errors: INVALID_ARG (null handle, out of range). */
+int st_set_wait_limit(st_handle h, double seconds);
+
 /* Allocation-free smoothing steps.  The paper has no counterpart: this is a
  * deployment variant of st_smooth for callers that cannot allocate device
  * memory -- for example a host application whose memory pool already owns
@@ -349,13 +359,18 @@ int st_profile_read(st_handle h, int cls, int64_t *launches, double *ms,
  * GPU.  A free worker takes the oldest pending request together with up to
  * max_batch - 1 further pending requests of the same configuration
  * (geometry, degree, spans, slabs, tolerance) and solves them as one
- * multi-right-hand-side problem (opt.nrhs = batch size; every right-hand
- * side is refined independently, so its result does not depend on the
- * batch).  Setups (factors + work space, st_setup) are cached per
- * configuration and batch size and evicted least-recently-used.  A batch is
- * admitted only when its setup and vectors fit the HBM budget; otherwise it
- * waits for running solves to release memory (or fails with
- * ST_ERR_OVER_BUDGET if it cannot fit even on an idle server).
+ * multi-right-hand-side problem (opt.nrhs = the batch size rounded up to a
+ * power of two, the unused right-hand sides zero; every right-hand side is
+ * refined independently, so its result does not depend on the batch).
+ * Setups (factors + work space, st_setup) are cached per configuration and
+ * batch-size class and evicted least-recently-used; their device memory
+ * comes from a stream-ordered memory pool of the server, so building or
+ * releasing one never synchronises the device, and no lock is held while a
+ * setup is built or released.  A batch is admitted only when its setup and
+ * vectors fit the HBM budget; otherwise it waits for running solves to
+ * release memory (or fails with ST_ERR_OVER_BUDGET if it cannot fit even on
+ * an idle server).  st_serve_opts_default turns opt.autotune off (tuning
+ * would time kernels for every new configuration on the serving path).
  * ------------------------------------------------------------------------ */
 typedef struct st_server_s *st_server;
 
@@ -367,6 +382,10 @@ typedef struct {
     int start_paused;     /* 1: workers take no request until st_serve_resume, so a
                              whole mix can be queued before batches are formed
                              (deterministic batching); default 0                */
+    long long batch_dofs; /* a batch grows only while its total dofs stay within
+                             this (the oldest request always runs): large solves
+                             already saturate the GPU and only wait longer in a
+                             batch; 0 = no limit; default 8388608               */
 } st_server_opts;
 
 typedef struct {
@@ -416,6 +435,71 @@ int st_serve_poll(st_server s, uint64_t ticket, st_result *res, double *u_host);
 int st_serve_wait(st_server s, uint64_t ticket, double timeout_s, st_result *res, double *u_host);
 /* Finish queued work, stop the workers, free every device and host resource. */
 int st_serve_stop(st_server s);
+
+/* ------------------------------------------------------------------------
+ * Slab partition over several processes (one GPU each).  The smoother of
+ * Sec. 3.1 is block Jacobi over the time slabs, so every slab is smoothed on
+ * its own; the only coupling of the operator is B_n u_{n-1} = (N_t (x) M_x)
+ * u_{n-1} of Eq. 2.4, which reads the last time plane of the previous slab.
+ * A partitioned handle holds a contiguous range of slabs of every
+ * right-hand side: before each residual or smoothing step on a partitioned
+ * level it receives that one plane (N_x values per right-hand side) from the
+ * previous rank and sends its own last plane to the next.  The time
+ * coarsening merges slab pairs on each rank until a rank holds one slab; that
+ * level is gathered on every rank and the rest of the V-cycle runs there
+ * redundantly (the coarse levels are small), so a V-cycle gives the same bits
+ * as on one process.  The Krylov dot products are summed over the ranks.
+ * All entry points on a partitioned handle are collective: every rank calls
+ * them in the same order with its own slabs of u, f (layout as st_setup,
+ * n_dofs = the local slabs).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int rank, size;      /* this process and the number of processes         */
+    int host_buffers;    /* 1: the callbacks below take HOST buffers (the
+                            library stages device data through pinned host
+                            memory and synchronises its stream first); 0:
+                            DEVICE buffers, stream-ordered on `stream`      */
+    void *ctx;           /* passed to every callback                          */
+    /* send `bytes` bytes of `send` to rank dst and receive `bytes` bytes from
+     * rank src into `recv` (dst / src = -1: no send / receive); must not
+     * deadlock when every rank sends to rank + 1 and receives from rank - 1 */
+    int (*sendrecv)(void *ctx, const void *send, int dst, void *recv, int src, size_t bytes,
+                    void *stream);
+    /* recv (size * bytes bytes) = every rank's `send` block, in rank order   */
+    int (*allgather)(void *ctx, const void *send, void *recv, size_t bytes, void *stream);
+    /* in-place sum over the ranks of `count` HOST doubles (blocking); every
+     * rank must receive the same bits                                        */
+    int (*allreduce_sum)(void *ctx, double *vals, size_t count);
+} st_comm;
+/* Every callback returns 0 on success; anything else makes the calling entry
+ * point fail with ST_ERR_COMM. */
+
+/* Partitioned setup: rank r of `comm->size` holds slabs
+ * [r * slabs_global / size, (r + 1) * slabs_global / size) of every
+ * right-hand side.  slabs_global / size must be a power of two >= 2 (the
+ * local time coarsening ends at one slab per rank); opt as st_setup with
+ * basis ST_BASIS_NODAL, spatial_solver ST_SPATIAL_FD, space_ratio 0 and
+ * fused_vcycle 0 (else ST_ERR_UNSUPPORTED); CUDA graphs are not used (the
+ * exchanges run on the host).  The comm struct is copied; its ctx must stay
+ * valid until st_destroy.  Errors: as st_setup, INVALID_ARG for a bad comm
+ * or slab count. */
+int st_setup_partitioned(st_handle *out, int geometry, int degree, const int *spans,
+                         int slabs_global, const st_options *opt, const st_comm *comm,
+                         void *stream);
+/* The partition of slabs_global slabs over `size` ranks, as
+ * st_setup_partitioned makes it (host only): rank's first slab, its slab
+ * count and the first level that is gathered on every rank.  INVALID_ARG if
+ * it cannot be partitioned. */
+int st_partition_plan(int slabs_global, int size, int rank, int *slab_begin, int *slabs_local,
+                      int *gathered_level);
+/* NCCL communication for st_setup_partitioned: device buffers, stream-ordered
+ * NCCL send/receive, all-gather and all-reduce on `stream`.  libnccl.so.2 is
+ * loaded at run time (ST_ERR_UNSUPPORTED if it cannot be).  unique_id: 128
+ * bytes from st_comm_nccl_unique_id on one rank, given to every rank.
+ * st_comm_nccl_destroy releases the communicator. */
+int st_comm_nccl_unique_id(void *unique_id);
+int st_comm_nccl_create(st_comm *out, int size, int rank, const void *unique_id);
+void st_comm_nccl_destroy(st_comm *c);
 
 /* Host copies of the FP64 setup factors, for inspection and tests.
  * Time factors of level lvl (0 = finest), each nt x nt row-major, nt <= 8:

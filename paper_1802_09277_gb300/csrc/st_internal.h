@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "dfloat.h"
+#include "st_iga.h"
 
 #include <atomic>
 #include <cstdint>
@@ -30,6 +31,11 @@ inline cudaError_t smem_attr_once(const void *func, int bytes,
 // Allocate the outer iteration's Krylov space now (st_solve would do it on
 // first use); used by the server to account a setup's memory up front.
 int prepare_solve(st_handle_s *h);
+// st_setup with the handle's device memory taken from a stream-ordered pool
+// on `stream` (released by st_destroy with cudaFreeAsync on the handle's
+// stream at that time); used by the serving loop.
+int setup_pooled(st_handle_s **out, int geometry, int degree, const int *spans, int slabs,
+                 const st_options *opt, cudaStream_t stream, cudaMemPool_t pool);
 
 constexpr int NTMAX = 8;  // max time dofs per slab (ne + p)
 constexpr int PMAX = 3;   // max B-spline degree
@@ -56,6 +62,10 @@ struct TimeCoefs {
     int nt;
     int fuse_y;
     int mode;
+    // slab partition: the last time plane of the slab before the first slab
+    // of every problem ([problem][nxyz], data type of u), which then couples
+    // like an interior slab; nullptr: the first slab has no predecessor
+    const void *halo;
 };
 
 // Quasi-triangular Schur factor for the shift solve, plus X for the update
@@ -142,7 +152,8 @@ cudaError_t launch_add(T *y, const T *x, long long n, cudaStream_t s);
 // shape is not covered.
 cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, const float *wt,
                            int n_in, int n_out, long long ncols, long long inner, int *err,
-                           int nsm, cudaStream_t s, int ctas_per_sm = 0);
+                           int nsm, cudaStream_t s, int ctas_per_sm = 0,
+                           unsigned long long wait_ns = 1000000000ull);
 
 // ---- eigenbasis V-cycle kernels (kernels_spectral.cu) ----
 // ---- eigenbasis level kernels (kernels_modes.cu) ----

@@ -66,9 +66,9 @@ struct Done {
     Clock::time_point submitted;
 };
 
-struct Entry {  // a cached setup for one configuration and batch size
+struct Entry {  // a cached setup for one configuration and batch-size class
     Key key;
-    int nrhs = 1;
+    int nrhs = 1;  // a power of two: batches of nrhs/2 + 1 .. nrhs requests share it
     st_handle h = nullptr;
     double *f = nullptr, *u = nullptr;
     size_t bytes = 0;
@@ -94,6 +94,9 @@ ShapeKey shape_of(const Key &k, int nrhs) {
 struct st_server_s {
     st_server_opts o{};
     int device = 0;
+    // every setup's device memory comes from this stream-ordered pool, so that
+    // releasing a setup never synchronises the whole device (cudaFree would)
+    cudaMemPool_t pool = nullptr;
     size_t budget = 0;
     size_t used = 0;      // bytes held by cached setups plus reservations of setups being built
     std::mutex mu;
@@ -111,14 +114,25 @@ struct st_server_s {
 
 namespace {
 
-// Frees an entry's device memory (st_destroy, cudaFree).  Called without the
-// server lock: cudaFree waits for the device.
-void free_entry(Entry *e) {
-    if (e->h) st_destroy(e->h);
-    if (e->f) cudaFree(e->f);
-    if (e->u) cudaFree(e->u);
+// Returns an idle entry's device memory to the pool, stream-ordered on
+// `stream` (its last solve has completed: the worker synchronised its stream).
+void free_entry(Entry *e, cudaStream_t stream) {
+    if (e->h) {
+        st_set_stream(e->h, stream);
+        st_destroy(e->h);
+    }
+    if (e->f) cudaFreeAsync(e->f, stream);
+    if (e->u) cudaFreeAsync(e->u, stream);
     e->h = nullptr;
     e->f = e->u = nullptr;
+}
+
+// the batch-size class: the next power of two (setups are shared by the
+// batch sizes of one class; the unused right-hand sides are zero)
+int size_class(int R) {
+    int c = 1;
+    while (c < R) c *= 2;
+    return c;
 }
 
 // First guess of a setup's device bytes before one of its shape was built:
@@ -136,8 +150,8 @@ size_t guess_bytes(const st_server_s *s, const Key &k, int nrhs) {
 
 // Builds a setup for (key, nrhs) whose device memory stays within `limit`
 // bytes (setup, Krylov space and the two request vectors).  No lock held.
-int build_entry(st_server_s *s, const Key &key, int nrhs, size_t limit, Entry **out,
-                std::string *why) {
+int build_entry(st_server_s *s, const Key &key, int nrhs, size_t limit, cudaStream_t stream,
+                Entry **out, std::string *why) {
     st_options opt = s->o.opt;
     opt.nrhs = nrhs;
     int64_t nx = 1;
@@ -152,16 +166,24 @@ int build_entry(st_server_s *s, const Key &key, int nrhs, size_t limit, Entry **
     std::unique_ptr<Entry> e(new Entry());
     e->key = key;
     e->nrhs = nrhs;
-    int rc = st_setup(&e->h, key.geometry, key.degree, key.spans, key.slabs, &opt, nullptr);
+    int rc = st::setup_pooled(&e->h, key.geometry, key.degree, key.spans, key.slabs, &opt, stream,
+                              s->pool);
     if (rc == ST_OK) rc = st::prepare_solve(e->h);
-    if (rc == ST_OK &&
-        (cudaMalloc(&e->f, vb) != cudaSuccess || cudaMalloc(&e->u, vb) != cudaSuccess)) {
-        cudaGetLastError();
-        rc = ST_ERR_OOM;
+    if (rc == ST_OK) {
+        void *pf = nullptr, *pu = nullptr;
+        if (cudaMallocFromPoolAsync(&pf, vb, s->pool, stream) != cudaSuccess ||
+            cudaMallocFromPoolAsync(&pu, vb, s->pool, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess) {
+            cudaGetLastError();
+            rc = ST_ERR_OOM;
+        }
+        e->f = static_cast<double *>(pf);
+        e->u = static_cast<double *>(pu);
     }
     if (rc != ST_OK) {
         *why = std::string("setup: ") + st_last_error();
-        free_entry(e.get());
+        free_entry(e.get(), stream);
+        cudaStreamSynchronize(stream);
         return rc;
     }
     size_t hb = 0;
@@ -197,7 +219,7 @@ void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const
 // is released while a setup is built or an evicted one is freed).  On success
 // the entry is marked busy.
 int acquire_entry(st_server_s *s, std::unique_lock<std::mutex> &lock, const Key &key, int R,
-                  Entry **out, std::string *why) {
+                  cudaStream_t stream, Entry **out, std::string *why) {
     const ShapeKey sk = shape_of(key, R);
     for (;;) {
         for (auto &c : s->cache)
@@ -221,7 +243,7 @@ int acquire_entry(st_server_s *s, std::unique_lock<std::mutex> &lock, const Key 
             lock.unlock();
             Entry *e = nullptr;
             std::string msg;
-            const int rc = build_entry(s, key, R, want, &e, &msg);
+            const int rc = build_entry(s, key, R, want, stream, &e, &msg);
             lock.lock();
             --s->busy_workers;
             s->used -= want;
@@ -262,7 +284,7 @@ int acquire_entry(st_server_s *s, std::unique_lock<std::mutex> &lock, const Key 
             s->cache.erase(s->cache.begin() + best);
             ++s->busy_workers;
             lock.unlock();
-            free_entry(victim.get());
+            free_entry(victim.get(), stream);
             lock.lock();
             --s->busy_workers;
             s->used -= victim->bytes;
@@ -295,8 +317,12 @@ void worker(st_server_s *s) {
         // the oldest request and up to max_batch - 1 more of the same configuration
         const Key key = s->pending.front().key;
         std::vector<Pending> batch;
+        long long dofs = 0;
         for (auto it = s->pending.begin(); it != s->pending.end() && (int)batch.size() < s->o.max_batch;) {
-            if (std::memcmp(&it->key, &key, sizeof(Key)) == 0) {
+            const long long n = (long long)it->rhs.size();
+            if (std::memcmp(&it->key, &key, sizeof(Key)) == 0 &&
+                (batch.empty() || s->o.batch_dofs <= 0 || dofs + n <= s->o.batch_dofs)) {
+                dofs += n;
                 s->results[it->ticket].running = true;
                 batch.push_back(std::move(*it));
                 it = s->pending.erase(it);
@@ -305,9 +331,10 @@ void worker(st_server_s *s) {
             }
         }
         const int R = (int)batch.size();
+        const int RC = size_class(R);
         Entry *e = nullptr;
         std::string why;
-        const int rc = acquire_entry(s, lock, key, R, &e, &why);
+        const int rc = acquire_entry(s, lock, key, RC, stream, &e, &why);
         if (rc != ST_OK) {
             finish(s, batch, rc, nullptr, Clock::now(), nullptr, why);
             s->cv.notify_all();
@@ -328,6 +355,10 @@ void worker(st_server_s *s) {
             if (cudaMemcpyAsync(in + r * n1, batch[r].rhs.data(), n1 * sizeof(double),
                                 cudaMemcpyHostToDevice, stream) != cudaSuccess)
                 st = ST_ERR_CUDA;
+        if (st == ST_OK && RC > R &&
+            cudaMemsetAsync(in + R * n1, 0, (size_t)(RC - R) * n1 * sizeof(double), stream) !=
+                cudaSuccess)
+            st = ST_ERR_CUDA;
         if (st == ST_OK && key.coeffs) st = st_load_coeffs(e->h, e->u, e->f);
         if (st == ST_OK) st = st_solve(e->h, e->f, key.tol, e->u, 0, &info);
         if (st == ST_OK || st == ST_ERR_NO_CONVERGENCE) {
@@ -360,7 +391,11 @@ void st_serve_opts_default(st_server_opts *o) {
     o->workers = 4;
     o->max_batch = 8;
     o->start_paused = 0;
+    o->batch_dofs = 8388608;
     st_options_default(&o->opt);
+    // per-setup kernel tuning would time candidate kernels for every new
+    // configuration on the serving path
+    o->opt.autotune = 0;
 }
 
 int st_serve_start(st_server *out, const st_server_opts *o) {
@@ -385,6 +420,19 @@ int st_serve_start(st_server *out, const st_server_opts *o) {
         return ST_ERR_CUDA;
     }
     s->budget = oo.hbm_budget ? oo.hbm_budget : (size_t)(0.9 * (double)fr);
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = s->device;
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return ST_ERR_CUDA;
+    }
+    // keep released memory in the pool (no return to the driver between setups)
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     for (int i = 0; i < oo.workers; ++i) s->threads.emplace_back(worker, s);
     *out = s;
     return ST_OK;
@@ -496,8 +544,10 @@ int st_serve_stop(st_server s) {
     }
     s->cv.notify_all();
     for (auto &t : s->threads) t.join();
-    for (auto &e : s->cache) free_entry(e.get());
+    for (auto &e : s->cache) free_entry(e.get(), nullptr);
     s->cache.clear();
+    cudaStreamSynchronize(nullptr);
+    cudaMemPoolDestroy(s->pool);
     delete s;
     return ST_OK;
 }

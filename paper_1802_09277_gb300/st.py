@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(PKG, "libst_iga.so")
 ST_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "NOT_POSITIVE", -4: "ILL_CONDITIONED",
           -5: "NO_CONVERGENCE", -6: "TIMEOUT", -7: "CUDA", -8: "OVER_BUDGET",
-          -9: "UNSUPPORTED", -10: "NOT_READY", -11: "CANCELLED"}
+          -9: "UNSUPPORTED", -10: "NOT_READY", -11: "CANCELLED", -12: "COMM"}
 ST_ERR_INVALID_ARG = -1
 ST_ERR_NO_CONVERGENCE = -5
 ST_ERR_UNSUPPORTED = -9
@@ -28,11 +28,12 @@ SPATIAL = {"fd": 0, "minres": 1}
 # every symbol declared in include/st_iga.h
 SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",
            "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_load_gaussians", "st_smooth",
-           "st_smooth_static", "st_block_minres", "st_vcycle",
+           "st_smooth_static", "st_set_wait_limit", "st_block_minres", "st_vcycle",
            "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
            "st_time_prolongation", "st_level_shape", "st_space_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_resume", "st_serve_cancel", "st_serve_poll", "st_serve_wait",
-           "st_serve_stop"]
+           "st_serve_stop", "st_setup_partitioned", "st_partition_plan", "st_comm_nccl_unique_id",
+           "st_comm_nccl_create", "st_comm_nccl_destroy"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
                 "vector", "dot", "tc", "spec", "stencil_df", "minres"]
 
@@ -57,7 +58,8 @@ class StSolveInfo(ctypes.Structure):
 
 class StServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int),
-                ("max_batch", ctypes.c_int), ("opt", StOptions), ("start_paused", ctypes.c_int)]
+                ("max_batch", ctypes.c_int), ("opt", StOptions), ("start_paused", ctypes.c_int),
+                ("batch_dofs", ctypes.c_longlong)]
 
 
 class StRequest(ctypes.Structure):
@@ -76,6 +78,20 @@ class StResult(ctypes.Structure):
 
 
 ST_ERR_NOT_READY = -10
+
+# st_comm callbacks (slab-partitioned handles)
+SENDRECV_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                               ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p)
+ALLGATHER_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_size_t, ctypes.c_void_p)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                ctypes.c_size_t)
+
+
+class StComm(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int), ("size", ctypes.c_int), ("host_buffers", ctypes.c_int),
+                ("ctx", ctypes.c_void_p), ("sendrecv", SENDRECV_FN),
+                ("allgather", ALLGATHER_FN), ("allreduce_sum", ALLREDUCE_FN)]
 
 
 class StError(RuntimeError):
@@ -129,11 +145,18 @@ def load():
         "st_serve_opts_default": (V, [ctypes.POINTER(StServerOpts)]),
         "st_serve_start": (I, [ctypes.POINTER(P), ctypes.POINTER(StServerOpts)]),
         "st_serve_submit": (I, [P, ctypes.POINTER(StRequest), ctypes.POINTER(ctypes.c_uint64)]),
+        "st_set_wait_limit": (I, [P, D]),
         "st_serve_resume": (I, [P]),
         "st_serve_cancel": (I, [P, ctypes.c_uint64]),
         "st_serve_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(StResult), dp]),
         "st_serve_wait": (I, [P, ctypes.c_uint64, D, ctypes.POINTER(StResult), dp]),
         "st_serve_stop": (I, [P]),
+        "st_setup_partitioned": (I, [ctypes.POINTER(P), I, I, ip, I, ctypes.POINTER(StOptions),
+                                     ctypes.POINTER(StComm), P]),
+        "st_partition_plan": (I, [I, I, I, ip, ip, ip]),
+        "st_comm_nccl_unique_id": (I, [P]),
+        "st_comm_nccl_create": (I, [ctypes.POINTER(StComm), I, I, P]),
+        "st_comm_nccl_destroy": (V, [ctypes.POINTER(StComm)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -185,13 +208,23 @@ class Solver:
     degree p, spans per axis, slabs; keyword options as in st_options.
     host_only=True builds only the FP64 factors (no GPU needed)."""
 
-    def __init__(self, dim, degree, spans, slabs, host_only=False, stream=None, **opts):
+    def __init__(self, dim, degree, spans, slabs, host_only=False, stream=None, comm=None,
+                 **opts):
         lib = load()
         self.dim = int(dim)
         self.opt = options(**opts)
         self._h = ctypes.c_void_p()
+        self._comm = comm  # kept alive with the handle (its callbacks)
         sp = (ctypes.c_int * 3)(*([int(s) for s in spans] + [1] * (3 - len(spans))))
-        if host_only:
+        if comm is not None:
+            # slabs = the global slab count; this rank holds its own range
+            if stream is None:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream
+            rc = lib.st_setup_partitioned(ctypes.byref(self._h), self.dim, int(degree), sp,
+                                          int(slabs), ctypes.byref(self.opt),
+                                          ctypes.byref(comm.c), ctypes.c_void_p(stream))
+        elif host_only:
             rc = lib.st_setup_host(ctypes.byref(self._h), self.dim, int(degree), sp, int(slabs),
                                    ctypes.byref(self.opt))
         else:
@@ -290,6 +323,10 @@ class Solver:
                 "status": info.status,
                 "rel_residual": info.rel_residual, "seconds": info.seconds, "rc": rc}
 
+    def set_wait_limit(self, seconds):
+        """Bound of the tensor-core kernels' device-side waits (seconds)."""
+        _check(_lib.st_set_wait_limit(self._h, float(seconds)))
+
     def autotune(self):
         """Per axis: (choice, ms per pass); choice 0 = CUDA cores, k > 0 =
         tensor cores with k CTAs per SM."""
@@ -381,7 +418,8 @@ class Server:
     """Continuous-batching solve server (st_serve_*): submit host right-hand
     sides of any configuration, poll or wait for host solutions."""
 
-    def __init__(self, workers=4, max_batch=8, hbm_budget=0, paused=False, **opts):
+    def __init__(self, workers=4, max_batch=8, hbm_budget=0, paused=False, batch_dofs=None,
+                 **opts):
         lib = load()
         self.o = StServerOpts()
         lib.st_serve_opts_default(ctypes.byref(self.o))
@@ -389,6 +427,9 @@ class Server:
         self.o.max_batch = int(max_batch)
         self.o.hbm_budget = int(hbm_budget)
         self.o.start_paused = 1 if paused else 0
+        if batch_dofs is not None:
+            self.o.batch_dofs = int(batch_dofs)
+        opts.setdefault("autotune", 0)  # as st_serve_opts_default: no per-setup tuning
         self.o.opt = options(**opts)
         self._s = ctypes.c_void_p()
         _check(lib.st_serve_start(ctypes.byref(self._s), ctypes.byref(self.o)))
@@ -453,3 +494,94 @@ class Server:
             self.stop()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------------------
+# slab partition over several processes
+# ----------------------------------------------------------------------------
+
+def partition_plan(slabs_global, size, rank):
+    """(first slab, slab count, gathered level) of rank (st_partition_plan)."""
+    b, n, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().st_partition_plan(int(slabs_global), int(size), int(rank), ctypes.byref(b),
+                                    ctypes.byref(n), ctypes.byref(g)))
+    return b.value, n.value, g.value
+
+
+def _host_bytes(addr, nbytes):
+    """A uint8 CPU tensor over host memory at addr (no copy)."""
+    import torch
+    return torch.frombuffer((ctypes.c_char * int(nbytes)).from_address(addr), dtype=torch.uint8)
+
+
+class GlooComm:
+    """st_comm over the default torch.distributed process group with HOST
+    buffers (e.g. the gloo backend): the library stages its device data
+    through pinned host memory and calls these callbacks with host pointers.
+    Any exception inside a callback is reported to the library as a failure
+    (the entry point then returns ST_ERR_COMM)."""
+
+    def __init__(self):
+        import torch
+        import torch.distributed as dist
+        self.rank, self.size = dist.get_rank(), dist.get_world_size()
+
+        def sendrecv(ctx, send, dst, recv, src, nbytes, stream):
+            try:
+                req = dist.isend(_host_bytes(send, nbytes), dst) if dst >= 0 else None
+                if src >= 0:
+                    dist.recv(_host_bytes(recv, nbytes), src)
+                if req is not None:
+                    req.wait()
+                return 0
+            except Exception:
+                return 1
+
+        def allgather(ctx, send, recv, nbytes, stream):
+            try:
+                out = _host_bytes(recv, nbytes * self.size)
+                parts = [torch.empty(nbytes, dtype=torch.uint8) for _ in range(self.size)]
+                dist.all_gather(parts, _host_bytes(send, nbytes))
+                for q, t in enumerate(parts):
+                    out[q * nbytes:(q + 1) * nbytes].copy_(t)
+                return 0
+            except Exception:
+                return 1
+
+        def allreduce(ctx, vals, count):
+            try:
+                addr = ctypes.addressof(vals.contents)
+                t = torch.frombuffer((ctypes.c_double * int(count)).from_address(addr),
+                                     dtype=torch.float64)
+                dist.all_reduce(t)
+                return 0
+            except Exception:
+                return 1
+
+        self._fns = (SENDRECV_FN(sendrecv), ALLGATHER_FN(allgather), ALLREDUCE_FN(allreduce))
+        self.c = StComm(self.rank, self.size, 1, None, *self._fns)
+
+    def close(self):
+        pass
+
+
+class NcclComm:
+    """st_comm over an NCCL communicator that the library creates from a
+    unique id (st_comm_nccl_create): device buffers, stream-ordered."""
+
+    @staticmethod
+    def unique_id():
+        buf = (ctypes.c_char * 128)()
+        _check(load().st_comm_nccl_unique_id(buf))
+        return bytes(buf)
+
+    def __init__(self, size, rank, unique_id):
+        load()
+        self.c = StComm()
+        buf = (ctypes.c_char * 128).from_buffer_copy(bytes(unique_id))
+        _check(_lib.st_comm_nccl_create(ctypes.byref(self.c), int(size), int(rank), buf))
+        self.rank, self.size = int(rank), int(size)
+
+    def close(self):
+        if self.c.ctx:
+            _lib.st_comm_nccl_destroy(ctypes.byref(self.c))
