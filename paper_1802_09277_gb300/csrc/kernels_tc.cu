@@ -20,6 +20,9 @@
 // One CTA (128 threads) loops over 128-column tiles: all threads stage the
 // activation tile, thread 0 issues the MMAs and commits them to an
 // mbarrier, all threads wait (bounded) and drain TMEM with tcgen05.ld.
+// A wait that runs out is decided for the whole CTA at once (a CTA-wide
+// vote, so every thread takes the same barriers): the CTA records the error,
+// waits (bounded again) for its MMAs in flight, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "st_internal.h"
@@ -31,7 +34,7 @@ namespace {
 
 constexpr int TC_THREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lane quarter w % 4
 constexpr int TC_COLS = 128;  // columns (GEMM rows of the activation operand) per tile
-constexpr uint64_t TC_WAIT_NS = 1000000000ull;  // 1 s: far above any tile's MMA time
+constexpr uint64_t TC_DRAIN_NS = 1000000000ull;  // after a timeout: MMAs in flight finish
 constexpr int KIND_TF32X3 = 3;  // split TF32 (see above); MMA format TF32
 
 template <int KIND>
@@ -102,6 +105,7 @@ struct TcArgs {
     long long ncols;   // number of GEMM columns (input rows / (outer, inner) pairs)
     long long inner;   // MODE_S: stride of the contracted axis
     int *err;          // set to 1 if an mbarrier wait ran out
+    unsigned long long wait_ns;  // bound of each wait for the MMAs (0: test once)
 };
 
 // Stage 16-byte chunks [k0, k0 + kcs) of the weight operand (rows = output
@@ -246,7 +250,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
             }
             // the MMAs have read the chunk before it is overwritten or the
             // accumulator is read
-            if (!tc::mbar_wait_bounded(&mbar, phase, TC_WAIT_NS)) {
+            const bool ok = tc::mbar_wait_bounded(&mbar, phase, a.wait_ns);
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                // the MMAs still in flight complete before TMEM is released
+                tc::mbar_wait_bounded(&mbar, phase, TC_DRAIN_NS);
                 failed = true;
                 if (tid == 0) atomicExch(a.err, 1);
             }
@@ -349,8 +356,10 @@ static cudaError_t launch_tc_t(TcArgs a, cudaStream_t s, int nsm, int ctas_per_s
 // covers (the caller then uses the CUDA-core transform).
 cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, const float *wt,
                            int n_in, int n_out, long long ncols, long long inner, int *err,
-                           int nsm, cudaStream_t s, int ctas_per_sm) {
+                           int nsm, cudaStream_t s, int ctas_per_sm,
+                           unsigned long long wait_ns) {
     TcArgs a;
+    a.wait_ns = wait_ns;
     a.in = in;
     a.out = out;
     a.wt = wt;

@@ -126,9 +126,11 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Wall-clock bounded wait: returns false if the phase did not complete within
-// limit_ns nanoseconds (the caller then records an error and bails out).
+// limit_ns nanoseconds (the caller then records an error and bails out);
+// limit_ns = 0 tests the phase once without waiting.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity,
                                                   uint64_t limit_ns) {
+    if (limit_ns == 0) return mbar_test_wait(mbar, parity);
     const uint64_t t0 = global_ns();
     for (;;) {
         if (mbar_test_wait(mbar, parity)) return true;
