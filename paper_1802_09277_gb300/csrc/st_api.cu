@@ -141,6 +141,7 @@ struct st_handle_s {
     double tune_ms[3] = {0, 0, 0};
     bool tuned = false;
     int *tc_err = nullptr;  // device flag: a tensor-core kernel's bounded wait ran out
+    unsigned long long wait_ns = 1000000000ull;  // bound of each such wait (st_set_wait_limit)
     // host factors
     Mat M1[3], K1[3], U[3], Pt;
     std::vector<double> lam[3];
@@ -148,6 +149,20 @@ struct st_handle_s {
     // device
     std::vector<void *> allocs;
     size_t bytes = 0;
+    // device memory from this stream-ordered pool instead of cudaMalloc (the
+    // serving loop: releasing a setup then needs no device-wide synchronisation)
+    cudaMemPool_t pool = nullptr;
+    // slab partition (st_setup_partitioned): levels < gathered are split over
+    // the ranks (this rank: lv[l].nslab slabs starting at global slab
+    // slab_begin >> l), levels >= gathered hold every rank's slabs
+    bool part = false;
+    st_comm comm{};
+    int slab_begin = 0, N_global = 0, gathered = 0;
+    long long work_len = 0;              // largest level's dofs per rhs (work vectors)
+    void *send_plane = nullptr, *halo = nullptr;  // [rhs][nxyz], FP64-sized
+    void *agg_send = nullptr, *agg_recv = nullptr;  // gathered-level transfers
+    void *stage = nullptr;               // pinned host staging for host-buffer comms
+    size_t stage_bytes = 0;
     DevSpace<double> s64;
     DevSpace<float> s32;
     Work<double> w64;
@@ -196,10 +211,18 @@ int dalloc(st_handle h, size_t bytes, void **out) {
         return fail(ST_ERR_OVER_BUDGET, "allocation of %zu bytes exceeds the HBM budget (%zu of %zu used)",
                     bytes, h->bytes, h->opt.hbm_budget);
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    cudaError_t e;
+    if (h->pool) {
+        // complete before any other stream (or a synchronous copy) uses it
+        e = cudaMallocFromPoolAsync(&p, bytes ? bytes : 16, h->pool, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    } else {
+        e = cudaMalloc(&p, bytes ? bytes : 16);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(ST_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return fail(ST_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes,
+                    cudaGetErrorString(e));
     }
     h->allocs.push_back(p);
     h->bytes += bytes;
@@ -351,7 +374,7 @@ int build_space(st_handle h, const int spans[3], LevelSpace &S) {
 
 template <typename T>
 int alloc_work(st_handle h, Work<T> &w, bool level0) {
-    const size_t e0 = (size_t)h->len * h->nrhs;
+    const size_t e0 = (size_t)std::max(h->len, h->work_len) * h->nrhs;
     void *p;
     CKS(dalloc(h, e0 * sizeof(T), &p));
     w.w0 = (T *)p;
@@ -478,6 +501,73 @@ Work<double> &work<double>(st_handle h) { return h->w64; }
 template <>
 Work<float> &work<float>(st_handle h) { return h->w32; }
 
+// ---- slab partition: communication ----------------------------------------
+// Each call runs the comm callback (staging through pinned host memory for
+// host-buffer comms) and turns a failure into ST_ERR_COMM.
+int comm_sendrecv(st_handle h, const void *send, int dst, void *recv, int src, size_t bytes) {
+    const st_comm &c = h->comm;
+    if (!c.host_buffers) {
+        if (c.sendrecv(c.ctx, send, dst, recv, src, bytes, h->stream) != 0)
+            return fail(ST_ERR_COMM, "sendrecv callback failed");
+        return ST_OK;
+    }
+    char *hs = static_cast<char *>(h->stage), *hr = hs + bytes;
+    if (dst >= 0) CK(cudaMemcpyAsync(hs, send, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (c.sendrecv(c.ctx, hs, dst, hr, src, bytes, h->stream) != 0)
+        return fail(ST_ERR_COMM, "sendrecv callback failed");
+    if (src >= 0) {
+        CK(cudaMemcpyAsync(recv, hr, bytes, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));  // the staging buffer is reused
+    }
+    return ST_OK;
+}
+
+int comm_allgather(st_handle h, const void *send, void *recv, size_t bytes) {
+    const st_comm &c = h->comm;
+    if (!c.host_buffers) {
+        if (c.allgather(c.ctx, send, recv, bytes, h->stream) != 0)
+            return fail(ST_ERR_COMM, "allgather callback failed");
+        return ST_OK;
+    }
+    char *hs = static_cast<char *>(h->stage), *hr = hs + bytes;
+    CK(cudaMemcpyAsync(hs, send, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (c.allgather(c.ctx, hs, hr, bytes, h->stream) != 0)
+        return fail(ST_ERR_COMM, "allgather callback failed");
+    CK(cudaMemcpyAsync(recv, hr, bytes * c.size, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ST_OK;
+}
+
+int comm_allreduce(st_handle h, std::vector<double> &v) {
+    if (v.empty()) return ST_OK;
+    if (h->comm.allreduce_sum(h->comm.ctx, v.data(), v.size()) != 0)
+        return fail(ST_ERR_COMM, "allreduce callback failed");
+    return ST_OK;
+}
+
+// The coupling plane of a partitioned level: send the last time plane of this
+// rank's last slab (every rhs) to the next rank, receive the previous rank's
+// into the halo buffer; returns the halo pointer for the stencil (nullptr on
+// rank 0, whose first slab has no predecessor).
+template <typename T>
+int exchange_halo(st_handle h, int l, const T *u, const void **halo) {
+    *halo = nullptr;
+    if (!h->part || l >= h->gathered) return ST_OK;
+    const long long nxyz = h->g.nxyz, slab = (long long)h->nt * nxyz;
+    const int Nl = h->lv[l].nslab, R = h->nrhs, rank = h->comm.rank, size = h->comm.size;
+    T *sp = static_cast<T *>(h->send_plane), *hp = static_cast<T *>(h->halo);
+    if (rank + 1 < size)
+        CK(cudaMemcpy2DAsync(sp, nxyz * sizeof(T), u + (Nl - 1) * slab + (h->nt - 1) * nxyz,
+                             Nl * slab * sizeof(T), nxyz * sizeof(T), R, cudaMemcpyDeviceToDevice,
+                             h->stream));
+    CKS(comm_sendrecv(h, sp, rank + 1 < size ? rank + 1 : -1, hp, rank > 0 ? rank - 1 : -1,
+                      (size_t)R * nxyz * sizeof(T)));
+    if (rank > 0) *halo = hp;
+    return ST_OK;
+}
+
 // ---- operator pieces --------------------------------------------------------
 template <typename T>
 int stencil(st_handle h, int l, const T *u, const T *f, T *out, int mode, bool fuse_y, int slab0,
@@ -492,8 +582,10 @@ int stencil(st_handle h, int l, const T *u, const T *f, T *out, int mode, bool f
     const double bytes = sizeof(T) * (2.0 * E + (mode == MODE_RES ? E : 0.0) +
                                       (mode == MODE_MASS ? 0.0 : (double)nslabs * h->g.nxyz));
     const double flops = planes_pt * fsp + E * 4.0 * h->nt + (fuse_y ? E * 2.0 * h->nt : 0.0);
+    TimeCoefs<T> tcl = tc;
+    if (mode != MODE_MASS) CKS(exchange_halo<T>(h, l, u, &tcl.halo));
     KScope ks(h, cls_of<T>(ST_PROF_STENCIL64, ST_PROF_STENCIL32), bytes, flops);
-    CK(launch_stencil<T>(u, f, out, space<T>(h).bands, h->g, tc, h->lv[l].nslab, slab0, nslabs,
+    CK(launch_stencil<T>(u, f, out, space<T>(h).bands, h->g, tcl, h->lv[l].nslab, slab0, nslabs,
                          h->stream));
     return ST_OK;
 }
@@ -524,7 +616,8 @@ int axis_pass(st_handle h, int axis, const T *in, T *out, bool forward, long lon
                                              (float *)out, Wt, (int)n, (int)n, ncols, inner,
                                              h->tc_err, h->nsm, h->stream,
                                              full32 ? (h->tune3[axis] > 0 ? h->tune3[axis] : 0)
-                                                    : (h->tune[axis] > 0 ? h->tune[axis] : 0));
+                                                    : (h->tune[axis] > 0 ? h->tune[axis] : 0),
+                                             h->wait_ns);
         if (e == cudaSuccess) return ST_OK;
         if (e != cudaErrorNotSupported) CK(e);
         cudaGetLastError();
@@ -1131,6 +1224,31 @@ int vcycle(st_handle h, int l, T *u, const T *f, bool zero_init) {
         CKS(space_transfer<T>(h, l, w.u[l + 1], w.w1, xt, w.w0, false, planes));
         KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 3.0 * n_l, 1.0 * n_l);
         CK(launch_add<T>(u, w.w0, n_l, h->stream));
+    } else if (h->part && l + 1 == h->gathered) {
+        // the slab pair of this rank restricts to one coarse slab per rhs;
+        // every rank gathers all ranks' coarse slabs, runs the rest of the
+        // V-cycle on them and prolongates its own slab of the correction
+        const ProlongCoefs<T> pc = pack_prolong<T>(h);
+        const int R = h->nrhs, P = h->comm.size, rank = h->comm.rank;
+        const long long se = (long long)h->nt * h->g.nxyz;  // one slab
+        T *snd = static_cast<T *>(h->agg_send), *rcv = static_cast<T *>(h->agg_recv);
+        const double Ec = (double)R * se;
+        {
+            KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 3.0 * Ec, Ec * 4.0 * h->nt);
+            CK(launch_restrict<T>(w.w0, snd, pc, h->g, R, h->stream));
+        }
+        CKS(comm_allgather(h, snd, rcv, sizeof(T) * R * se));  // [rank][rhs][slab]
+        for (int q = 0; q < P; ++q)  // -> [rhs][rank's slab]
+            CK(cudaMemcpy2DAsync(w.f[l + 1] + q * se, P * se * sizeof(T), rcv + q * R * se,
+                                 se * sizeof(T), se * sizeof(T), R, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+        CKS(vcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], true));
+        CK(cudaMemcpy2DAsync(snd, se * sizeof(T), w.u[l + 1] + rank * se, P * se * sizeof(T),
+                             se * sizeof(T), R, cudaMemcpyDeviceToDevice, h->stream));
+        {
+            KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 5.0 * Ec, Ec * 4.0 * h->nt);
+            CK(launch_prolong_add<T>(snd, u, pc, h->g, R, h->stream));
+        }
     } else {
         const ProlongCoefs<T> pc = pack_prolong<T>(h);
         const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
@@ -1441,6 +1559,7 @@ int dots(st_handle h, int nv, const T *const *vecs, const T *w, std::vector<doub
                            sizeof(double) * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    if (h->part) CKS(comm_allreduce(h, out));
     if (h->recs.size() > 2048) prof_fold(h);
     return ST_OK;
 }
@@ -1451,7 +1570,9 @@ int norms(st_handle h, const T *x, std::vector<double> &nr) {
     const T *v[1] = {x};
     CKS(dots<T>(h, 1, v, x, d));
     nr.resize(h->nrhs);
-    for (int r = 0; r < h->nrhs; ++r) nr[r] = std::sqrt(std::max(0.0, d[r]));
+    // a NaN square sum stays NaN (std::max(0.0, NaN) would hide it as 0)
+    for (int r = 0; r < h->nrhs; ++r)
+        nr[r] = std::isnan(d[r]) ? d[r] : std::sqrt(std::max(0.0, d[r]));
     return ST_OK;
 }
 
@@ -1472,6 +1593,7 @@ int gram2s(st_handle h, int nv, const T *const *vecs, const T *t1, const T *t2,
                            sizeof(double) * 2 * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    if (h->part) CKS(comm_allreduce(h, out));
     if (h->recs.size() > 2048) prof_fold(h);
     return ST_OK;
 }
@@ -1484,7 +1606,8 @@ int residual64(st_handle h, const double *u, const double *f, double *r) {
 // double-float arithmetic (about 48 significant bits, far below the FP32
 // inner solve's error) instead of FP64, which runs at 1/64 of the FP32 rate.
 int residual_df(st_handle h, const double *u, const double *f, double *r) {
-    const TimeCoefs<dfloat> tc = pack_time<dfloat>(h, 0, MODE_RES, false);
+    TimeCoefs<dfloat> tc = pack_time<dfloat>(h, 0, MODE_RES, false);
+    CKS(exchange_halo<double>(h, 0, u, &tc.halo));
     const double E = (double)h->N * h->nrhs * h->nt * h->g.nxyz;
     const double planes_pt = (double)h->N * h->nrhs * (h->nt + 1) * h->g.nxyz;
     const int W = 2 * h->p + 1;
@@ -1496,11 +1619,21 @@ int residual_df(st_handle h, const double *u, const double *f, double *r) {
     return ST_OK;
 }
 
+// A right-hand side whose norm is not finite (NaN or Inf entries) is an
+// argument error: the iteration could never meet the tolerance.
+int check_finite_rhs(const std::vector<double> &nf) {
+    for (size_t q = 0; q < nf.size(); ++q)
+        if (!std::isfinite(nf[q]))
+            return fail(ST_ERR_INVALID_ARG, "right-hand side %zu is not finite", q);
+    return ST_OK;
+}
+
 int solve_mg(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
     CKS(ensure_krylov(h));
     double *r = h->V[0], *e = h->Zk[0];
     std::vector<double> nf, nr;
     CKS(norms<double>(h, rhs, nf));
+    CKS(check_finite_rhs(nf));
     int it = 0;
     double worst = 0.0;
     for (;;) {
@@ -1533,6 +1666,7 @@ int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vecto
     const int m = (int)Zk.size(), R = h->nrhs;
     std::vector<double> nb, beta, hcol;
     CKS(norms<T>(h, b, nb));
+    CKS(check_finite_rhs(nb));
     int total = 0;
     double worst = 0.0;
     std::vector<char> done(R, 0);
@@ -1686,6 +1820,7 @@ int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vect
     const size_t ld = (size_t)m + 1;
     std::vector<double> nb, beta, G;
     CKS(norms<T>(h, b, nb));
+    CKS(check_finite_rhs(nb));
     int total = 0;
     double worst = 0.0;
     std::vector<char> done(R, 0);
@@ -1942,9 +2077,11 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
     }
     bool u_zero = true;
     for (int q = 0; q < R; ++q) {
-        nf[q] = std::sqrt(std::max(0.0, g0[(size_t)0 * R + q]));
+        const double f2 = g0[(size_t)0 * R + q];
+        nf[q] = std::isfinite(f2) ? std::sqrt(std::max(0.0, f2)) : f2;
         u_zero = u_zero && g0[(size_t)3 * R + q] == 0.0;
     }
+    CKS(check_finite_rhs(nf));
     int total = 0, outer = 0;
     double worst = 0.0;
     const bool eig_basis = h->opt.basis == ST_BASIS_SPECTRAL;
@@ -2029,8 +2166,24 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
     return ST_OK;
 }
 
+// Slab partition plan: rank's first slab, its slab count, the first level
+// held by every rank (ST_OK or INVALID_ARG).
+int partition_plan(int slabs, int size, int rank, int *begin, int *local, int *gathered) {
+    if (size < 1 || rank < 0 || rank >= size || slabs < 1 || slabs % size != 0)
+        return fail(ST_ERR_INVALID_ARG, "%d slabs cannot be split evenly over %d ranks", slabs, size);
+    const int n = slabs / size;
+    if (n < 2 || (n & (n - 1)) != 0)
+        return fail(ST_ERR_INVALID_ARG, "slabs per rank (%d) must be a power of two >= 2", n);
+    int L = 0;
+    while ((1 << L) < n) ++L;
+    *begin = rank * n;
+    *local = n;
+    *gathered = L;
+    return ST_OK;
+}
+
 int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slabs,
-               const st_options *opt, void *stream) {
+               const st_options *opt, void *stream, const st_comm *comm = nullptr) {
     if (opt) h->opt = *opt; else st_options_default(&h->opt);
     st_options &o = h->opt;
     if (geometry < ST_INTERVAL || geometry > ST_CUBE) return fail(ST_ERR_INVALID_ARG, "geometry must be 1..3");
@@ -2217,6 +2370,27 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     }
     h->nlev = (int)h->lv.size();
     host::time_prolongation(tau0, o.ne_per_slab, degree, h->Pt);
+    h->work_len = h->len;
+    if (comm) {
+        // keep the global hierarchy's time factors (they depend on the slab
+        // length only); levels below the gathered one hold this rank's slabs
+        int begin = 0, local = 0, gathered = 0;
+        CKS(partition_plan(slabs, comm->size, comm->rank, &begin, &local, &gathered));
+        if (gathered >= h->nlev) return fail(ST_ERR_INVALID_ARG, "partition deeper than the hierarchy");
+        h->part = true;
+        h->comm = *comm;
+        h->slab_begin = begin;
+        h->N_global = slabs;
+        h->gathered = gathered;
+        h->N = local;
+        for (int l = 0; l < gathered; ++l) h->lv[l].nslab = local >> l;
+        h->len = (long long)local * h->nt * h->g.nxyz;
+        long long wl = 0;
+        for (int l = 0; l < h->nlev; ++l)
+            wl = std::max(wl, (long long)h->lv[l].nslab * h->nt * h->g.nxyz);
+        h->work_len = wl;
+        h->opt.use_graphs = 0;  // the exchanges run on the host
+    }
 
     if (h->host_only) return ST_OK;
 
@@ -2234,7 +2408,8 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         void *pe;
         CKS(dalloc(h, sizeof(int), &pe));
         h->tc_err = (int *)pe;
-        CK(cudaMemset(h->tc_err, 0, sizeof(int)));
+        CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
+        CK(cudaStreamSynchronize(h->stream));
     }
     for (size_t k = 0; k < h->ls.size(); ++k) {
         LevelSpace &S = h->ls[k];
@@ -2251,6 +2426,22 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
         void *px;
         CKS(dalloc(h, (size_t)h->len * h->nrhs * (h->mixed ? sizeof(float) : sizeof(double)), &px));
         h->xtmp = px;
+    }
+    if (h->part) {
+        const size_t plane = (size_t)h->nrhs * h->g.nxyz * sizeof(double);
+        const size_t slab = (size_t)h->nrhs * h->nt * h->g.nxyz * sizeof(double);
+        CKS(dalloc(h, plane, &h->send_plane));
+        CKS(dalloc(h, plane, &h->halo));
+        CKS(dalloc(h, slab, &h->agg_send));
+        CKS(dalloc(h, slab * h->comm.size, &h->agg_recv));
+        if (h->comm.host_buffers) {
+            h->stage_bytes = slab * (h->comm.size + 1);
+            if (cudaMallocHost(&h->stage, h->stage_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                h->stage = nullptr;
+                return fail(ST_ERR_OOM, "pinned staging buffer of %zu bytes", h->stage_bytes);
+            }
+        }
     }
     if (h->mixed) {
         CKS(alloc_work<float>(h, h->w32, true));
@@ -2337,6 +2528,22 @@ int static_scratch_addr(double **out) {
 
 }  // namespace
 
+namespace {
+// ST_ERR_TIMEOUT if a tensor-core kernel's bounded wait ran out since the
+// last check (the flag is cleared); synchronises the handle's stream.
+int check_waits(st_handle h) {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (err) {
+        CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
+        return fail(ST_ERR_TIMEOUT, "a tensor-core transform's bounded wait ran out");
+    }
+    return ST_OK;
+}
+int vcycle_entry(st_handle h, double *u, const double *f);
+}  // namespace
+
 int st::prepare_solve(st_handle_s *h) {
     if (!h || h->host_only) return ST_ERR_INVALID_ARG;
     if (h->opt.outer == ST_OUTER_IR && h->mixed) return ensure_krylov32(h);
@@ -2375,14 +2582,16 @@ void st_options_default(st_options *o) {
 const char *st_last_error(void) { return g_err.c_str(); }
 
 static int setup_entry(st_handle *out, int geometry, int degree, const int *spans, int slabs,
-                       const st_options *opt, void *stream, bool host_only) {
+                       const st_options *opt, void *stream, bool host_only,
+                       cudaMemPool_t pool = nullptr, const st_comm *comm = nullptr) {
     if (!out) return fail(ST_ERR_INVALID_ARG, "null output handle");
     *out = nullptr;
     st_handle h = nullptr;
     try {
         h = new st_handle_s();
         h->host_only = host_only;
-        const int rc = setup_impl(h, geometry, degree, spans, slabs, opt, stream);
+        h->pool = pool;
+        const int rc = setup_impl(h, geometry, degree, spans, slabs, opt, stream, comm);
         if (rc != ST_OK) {
             st_destroy(h);
             return rc;
@@ -2406,13 +2615,45 @@ int st_setup_host(st_handle *out, int geometry, int degree, const int *spans, in
     return setup_entry(out, geometry, degree, spans, slabs, opt, nullptr, true);
 }
 
+int st_setup_partitioned(st_handle *out, int geometry, int degree, const int *spans,
+                         int slabs_global, const st_options *opt, const st_comm *comm,
+                         void *stream) {
+    if (out) *out = nullptr;
+    if (!comm || !comm->sendrecv || !comm->allgather || !comm->allreduce_sum || comm->size < 1 ||
+        comm->rank < 0 || comm->rank >= comm->size)
+        return fail(ST_ERR_INVALID_ARG, "bad communicator");
+    st_options o;
+    if (opt) o = *opt; else st_options_default(&o);
+    if (o.basis != ST_BASIS_NODAL || o.spatial_solver != ST_SPATIAL_FD || o.space_ratio != 0 ||
+        o.fused_vcycle)
+        return fail(ST_ERR_UNSUPPORTED, "a partitioned handle runs the B-spline-basis V-cycle with "
+                    "exact spatial solves and time coarsening only");
+    return setup_entry(out, geometry, degree, spans, slabs_global, &o, stream, false, nullptr, comm);
+}
+
+int st_partition_plan(int slabs_global, int size, int rank, int *slab_begin, int *slabs_local,
+                      int *gathered_level) {
+    int b = 0, n = 0, g = 0;
+    CKS(partition_plan(slabs_global, size, rank, &b, &n, &g));
+    if (slab_begin) *slab_begin = b;
+    if (slabs_local) *slabs_local = n;
+    if (gathered_level) *gathered_level = g;
+    return ST_OK;
+}
+
 void st_destroy(st_handle h) {
     if (!h) return;
     for (auto &g : h->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    for (void *p : h->allocs) cudaFree(p);
+    for (void *p : h->allocs) {
+        if (h->pool)
+            cudaFreeAsync(p, h->stream);  // stream-ordered: no device-wide synchronisation
+        else
+            cudaFree(p);
+    }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->stage) cudaFreeHost(h->stage);
     delete h;
 }
 
@@ -2465,7 +2706,8 @@ int st_load_gaussians(st_handle h, int nbumps, const double *centers, const doub
     const long long per = nst + h->n[0] + h->n[1] + h->n[2];
     if ((long long)nbumps * per > h->len * h->nrhs)
         return fail(ST_ERR_INVALID_ARG, "too many bumps for the work space");
-    const double tau = h->opt.T / N, delta = h->opt.theta * tau / ne;
+    // slabs of a partitioned handle start at global slab slab_begin
+    const double tau = h->opt.T / (h->part ? h->N_global : N), delta = h->opt.theta * tau / ne;
     const int npts = 2 * p + 4;
     std::vector<double> g((size_t)nbumps * per, 0.0);
     for (int k = 0; k < nbumps; ++k) {
@@ -2475,7 +2717,8 @@ int st_load_gaussians(st_handle h, int nbumps, const double *centers, const doub
         const double ct = centers[k * (d + 1) + d];
         auto ft = [=](double t) { return a * std::exp(-(t - ct) * (t - ct) / (2 * w * w)); };
         for (int n = 0; n < N; ++n) {
-            const std::vector<double> gt = host::load_1d(n * tau, (n + 1) * tau, ne, p, delta, false, npts, ft);
+            const int ng = n + h->slab_begin;
+            const std::vector<double> gt = host::load_1d(ng * tau, (ng + 1) * tau, ne, p, delta, false, npts, ft);
             for (int j = 0; j < nt; ++j) gk[(size_t)n * nt + j] = gt[j];
         }
         long long off = nst;
@@ -2573,6 +2816,22 @@ int st_block_minres(st_handle h, double alpha, double beta1, double beta2, const
 int st_vcycle(st_handle h, double *u, const double *f) {
     CKS(check_ptr(h, u, "u"));
     CKS(check_ptr(h, f, "f"));
+    const int rc = vcycle_entry(h, u, f);
+    if (rc != ST_OK) return rc;
+    return check_waits(h);
+}
+
+int st_set_wait_limit(st_handle h, double seconds) {
+    if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
+    if (!(seconds >= 0) || seconds > 60) return fail(ST_ERR_INVALID_ARG, "wait limit must be in [0, 60] s");
+    h->wait_ns = (unsigned long long)(seconds * 1e9);
+    return ST_OK;
+}
+
+}  // extern "C"
+
+namespace {
+int vcycle_entry(st_handle h, double *u, const double *f) {
     if (h->opt.basis == ST_BASIS_SPECTRAL) {
         // the V-cycle is the affine iteration u + B (f - L u)
         CKS(ensure_krylov(h));
@@ -2592,6 +2851,9 @@ int st_vcycle(st_handle h, double *u, const double *f) {
     CK(launch_convert<float, double>(h->w32.u[0], u, n0, h->stream));
     return ST_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_guess,
              st_solve_info *info) {
@@ -2609,13 +2871,7 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
         if (h->opt.outer == ST_OUTER_MG) CKS(solve_mg(h, rhs, tol, u, info));
         else if (h->opt.outer == ST_OUTER_IR && h->mixed) CKS(solve_ir(h, rhs, tol, u, info));
         else CKS(solve_fgmres(h, rhs, tol, u, info));
-        CK(cudaStreamSynchronize(h->stream));
-        int tc_err = 0;
-        CK(cudaMemcpy(&tc_err, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (tc_err) {
-            CK(cudaMemset(h->tc_err, 0, sizeof(int)));
-            return fail(ST_ERR_TIMEOUT, "a tensor-core transform's bounded wait ran out");
-        }
+        CKS(check_waits(h));
     } catch (...) {
         return fail(ST_ERR_OOM, "host exception during solve");
     }
@@ -2810,3 +3066,8 @@ int st_level_shape(st_handle h, int lvl, int *slabs, int *spans, int *space_step
 }
 
 }  // extern "C"
+
+int st::setup_pooled(st_handle_s **out, int geometry, int degree, const int *spans, int slabs,
+                     const st_options *opt, cudaStream_t stream, cudaMemPool_t pool) {
+    return setup_entry(out, geometry, degree, spans, slabs, opt, stream, false, pool);
+}
