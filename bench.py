@@ -702,6 +702,91 @@ def roofline_entry(r):
     return base
 
 
+# ----------------------------------------------------------------------------
+# One library operation on a chosen problem (for profilers: ncu launch lists
+# and section captures); prints the mean CUDA-event time per call, no bench line
+# ----------------------------------------------------------------------------
+
+def case_mode(args):
+    """--case: run one operation (apply: FP64 operator; smooth: one damped
+    block-Jacobi step in the handle's precision; vcycle; solve to --case-tol;
+    table3: Table 3's experiment on this grid -- MinRes steps to reduce
+    ||r||_{P^-1} by --case-tol for every 2x2 block of the standardised real
+    Schur form of the level-0 time pencil and for its complex shifts) on
+    seeded synthetic vectors."""
+    import torch
+    from paper_1802_09277_gb300 import inputs, st
+    if args.case_op == "table3":
+        import numpy as np
+        s = st.Solver(args.case_dim, args.case_degree, args.case_spans, args.case_slabs,
+                      ne_per_slab=args.case_ne, theta=args.case_theta, spatial_solver="minres")
+        Z = s.time_factors(0)["Z"]
+        m = int(np.prod(s.nx))
+        f = torch.tensor(inputs.uniform_vector(5, 2 * m), dtype=torch.float64, device="cuda")
+        u = torch.zeros_like(f)
+        steps = {"rschur": 0, "complex": 0}
+        i = 0
+        while i < s.nt:
+            if i + 1 < s.nt and Z[i + 1, i] != 0.0:
+                a, b1, b2 = Z[i, i], Z[i, i + 1], Z[i + 1, i]
+                w = float(np.sqrt(abs(b1 * b2)))
+                for key, (c1, c2) in (("rschur", (b1, b2)), ("complex", (-w, w))):
+                    its, _, _ = s.block_minres(a, c1, c2, f, u, tol=args.case_tol)
+                    steps[key] = max(steps[key], int(its[0]))
+                i += 2
+            else:
+                i += 1
+        print("table3 dim=%d spans=%s p=%d nt=%d theta=%g tol=%g max_steps_rschur=%d "
+              "max_steps_complex=%d" % (args.case_dim, args.case_spans, args.case_degree, s.nt,
+                                        args.case_theta, args.case_tol, steps["rschur"],
+                                        steps["complex"]))
+        s.close()
+        return
+    s = st.Solver(args.case_dim, args.case_degree, args.case_spans, args.case_slabs,
+                  ne_per_slab=args.case_ne, precision=args.precision, basis=args.basis,
+                  outer=args.outer, fused_vcycle=args.fused,
+                  spatial_solver=args.case_spatial_solver, minres_tol=args.case_minres_tol,
+                  theta=args.case_theta, space_ratio=args.case_space_ratio,
+                  nrhs=args.case_nrhs)
+    n = s.ndofs
+    x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
+    f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    times = []
+    for _ in range(args.case_reps):
+        ev[0].record()
+        if args.case_op == "apply":
+            s.apply(x, y)
+        elif args.case_op == "smooth":
+            s.smooth(x, f, 1)
+        elif args.case_op == "vcycle":
+            s.vcycle(x, f)
+        else:
+            s.solve(f, y, tol=args.case_tol)
+        ev[1].record()
+        ev[1].synchronize()
+        times.append(ev[0].elapsed_time(ev[1]))
+    extra = ""
+    if args.case_op == "solve":
+        u = torch.zeros_like(f)
+        if args.case_profile:
+            s.profile(True)
+        info = s.solve(f, u, tol=args.case_tol)
+        if args.case_profile:
+            prof = s.profile_read()
+            s.profile(False)
+            for k, v in prof.items():
+                if v["launches"]:
+                    print("class=%s launches=%d ms=%.4f GB/s=%.1f" % (
+                        k, v["launches"], v["ms"], v["bytes"] / max(v["ms"], 1e-9) / 1e6))
+        levels = "".join(k for _, _, k in s.level_shapes()[1:])
+        extra = " iterations=%d levels=%s min_ms=%.4f" % (info["iterations"], levels, min(times))
+    print("op=%s dofs=%d precision=%s mean_ms=%.4f%s" % (args.case_op, n, args.precision,
+                                                        sum(times) / len(times), extra))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -731,8 +816,29 @@ def main():
                     choices=["mixed_fp32", "mixed_tf32", "mixed_bf16", "fp64"])
     ap.add_argument("--fused", type=int, default=0, choices=[0, 1],
                     help="eigenbasis V-cycle as one shared-memory kernel (1) or level by level (0)")
+    # --case: one library operation on a chosen problem (profiling driver)
+    ap.add_argument("--case", action="store_true")
+    ap.add_argument("--case-op", default="solve",
+                    choices=["apply", "smooth", "vcycle", "solve", "table3"])
+    ap.add_argument("--case-dim", type=int, default=2)
+    ap.add_argument("--case-spans", type=int, nargs="+", default=[64, 64])
+    ap.add_argument("--case-degree", type=int, default=2)
+    ap.add_argument("--case-slabs", type=int, default=256)
+    ap.add_argument("--case-ne", type=int, default=2)
+    ap.add_argument("--case-nrhs", type=int, default=1)
+    ap.add_argument("--case-reps", type=int, default=2)
+    ap.add_argument("--case-tol", type=float, default=1e-8)
+    ap.add_argument("--case-theta", type=float, default=1.0)
+    ap.add_argument("--case-space-ratio", type=float, default=0.0)
+    ap.add_argument("--case-spatial-solver", default="fd", choices=["fd", "minres"])
+    ap.add_argument("--case-minres-tol", type=float, default=1e-4)
+    ap.add_argument("--case-profile", action="store_true",
+                    help="print per-kernel-class CUDA-event times of one more solve")
     args = ap.parse_args()
     ncores = os.cpu_count() or 1
+    if args.case:
+        case_mode(args)
+        return
     if args.cpu_procs <= 0:
         args.cpu_procs = ncores
 
