@@ -45,6 +45,43 @@ __device__ __forceinline__ dfloat madd<dfloat>(dfloat acc, dfloat x, dfloat y) {
     return df_fma(acc, x, y);
 }
 
+// Accumulator of a sum of products: a plain FMA chain in FP32 / FP64.  In
+// double-float it is the compensated dot product Dot2 of Ogita, Rump and
+// Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005): the
+// leading products are summed by the error-free TwoSum into s, every
+// rounding error (TwoSum's, the leading product's exact error from FMA, the
+// cross terms with the operands' low parts) is summed in FP32 into t, and
+// s + t is renormalised once when the value is read -- about 12 FP32
+// instructions per term instead of 15, and one add on the loop-carried path
+// instead of a full renormalisation.
+template <typename C>
+struct Acc {
+    C v;
+    __device__ __forceinline__ Acc() : v(C(0)) {}
+    __device__ __forceinline__ void add(C c, C x) { v = madd(v, c, x); }
+    __device__ __forceinline__ C get() const { return v; }
+};
+template <>
+struct Acc<dfloat> {
+    float s, t;
+    __device__ __forceinline__ Acc() : s(0.f), t(0.f) {}
+    __device__ __forceinline__ void add(dfloat c, dfloat x) {
+        const float p = __fmul_rn(c.hi, x.hi);
+        float e = __fmaf_rn(c.hi, x.hi, -p);
+        e = __fmaf_rn(c.hi, x.lo, e);
+        e = __fmaf_rn(c.lo, x.hi, e);
+        const float s1 = __fadd_rn(s, p);
+        const float bb = __fsub_rn(s1, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+        t = __fadd_rn(t, __fadd_rn(err, e));
+        s = s1;
+    }
+    __device__ __forceinline__ dfloat get() const {
+        const float hi = __fadd_rn(s, t);
+        return dfloat(hi, __fsub_rn(t, __fsub_rn(hi, s)));
+    }
+};
+
 // FP64 data in double-float arithmetic: split and widen without FP64-rate
 // conversions (GB300 runs FP64 at 1/64 of the FP32 rate)
 template <>
@@ -145,20 +182,22 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
         }
 
     const int tx = tid % TX, ty = tid / TX;
-    C acc[TZ][NL];
+    Acc<C> acc[TZ][NL];
     C mprev[TZ];
 #pragma unroll
-    for (int a = 0; a < TZ; ++a) {
-        mprev[a] = C(0);
-#pragma unroll
-        for (int i = 0; i < NL; ++i) acc[a][i] = C(0);
-    }
+    for (int a = 0; a < TZ; ++a) mprev[a] = C(0);
 
     const T *uslab = u + (long long)slab * nt * nxyz;
-    const bool has_prev = (tc.mode != MODE_MASS) && (slab % slabs_per_prob) != 0;
+    const bool first = (slab % slabs_per_prob) == 0;
+    const bool has_prev = (tc.mode != MODE_MASS) && (!first || tc.halo != nullptr);
+    // the coupling plane: the previous slab's last time plane, or for the
+    // first slab of a partition the neighbour's plane in the halo buffer
+    const T *prev = !first ? uslab - nxyz
+                    : tc.halo ? static_cast<const T *>(tc.halo) + (long long)(slab / slabs_per_prob) * nxyz
+                              : nullptr;
 
     for (int jj = has_prev ? -1 : 0; jj < nt; ++jj) {
-        const T *plane = (jj < 0) ? uslab - nxyz : uslab + (long long)jj * nxyz;
+        const T *plane = (jj < 0) ? prev : uslab + (long long)jj * nxyz;
         __syncthreads();
         for (int e = tid; e < SZ * SY * SX; e += NTH) {
             const int sx = e % SX, sy = (e / SX) % SY, sz = e / (SX * SY);
@@ -174,20 +213,20 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
         for (int e = tid; e < SZ * SY * TX; e += NTH) {
             const int ex = e % TX, row = e / TX;  // row = sz*SY + sy
             const C *srow = S + row * SX + ex;
-            C a = C(0), b = C(0);
+            Acc<C> a, b;
             if (mass_only) {
 #pragma unroll
-                for (int o = 0; o < W; ++o) a = madd(a, bMx[ex * W + o], srow[o]);
+                for (int o = 0; o < W; ++o) a.add(bMx[ex * W + o], srow[o]);
             } else {
 #pragma unroll
                 for (int o = 0; o < W; ++o) {
                     const C sv = srow[o];
-                    a = madd(a, bMx[ex * W + o], sv);
-                    b = madd(b, bKx[ex * W + o], sv);
+                    a.add(bMx[ex * W + o], sv);
+                    b.add(bKx[ex * W + o], sv);
                 }
             }
-            A[e] = a;
-            B[e] = b;
+            A[e] = a.get();
+            B[e] = b.get();
         }
         __syncthreads();
         const C *pm;
@@ -196,23 +235,24 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
             // y-pass: AA = M1y A, SS = K1y A + M1y B
             for (int e = tid; e < SZ * TY * TX; e += NTH) {
                 const int ex = e % TX, ey = (e / TX) % TY, sz = e / (TX * TY);
-                C aa = C(0), ss = C(0);
+                Acc<C> aa, ss;
                 if (mass_only) {
 #pragma unroll
                     for (int o = 0; o < W; ++o)
-                        aa = madd(aa, bMy[ey * W + o], A[(sz * SY + ey + o) * TX + ex]);
+                        aa.add(bMy[ey * W + o], A[(sz * SY + ey + o) * TX + ex]);
                 } else {
 #pragma unroll
                     for (int o = 0; o < W; ++o) {
                         const int idx = (sz * SY + ey + o) * TX + ex;
                         const C av = A[idx], bv = B[idx];
                         const C my = bMy[ey * W + o], ky = bKy[ey * W + o];
-                        aa = madd(aa, my, av);
-                        ss = madd(madd(ss, ky, av), my, bv);
+                        aa.add(my, av);
+                        ss.add(ky, av);
+                        ss.add(my, bv);
                     }
                 }
-                AA[e] = aa;
-                SS[e] = ss;
+                AA[e] = aa.get();
+                SS[e] = ss.get();
             }
             __syncthreads();
             pm = AA;
@@ -226,15 +266,17 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
         for (int a = 0; a < TZ; ++a) {
             C m, k;
             if (DIM >= 3) {
-                m = C(0);
-                k = C(0);
+                Acc<C> am, ak;
 #pragma unroll
                 for (int o = 0; o < W; ++o) {
                     const int idx = ((a + o) * TY + ty) * TX + tx;
                     const C mz = bMz[a * W + o], kz = bKz[a * W + o];
-                    m = madd(m, mz, pm[idx]);
-                    k = madd(madd(k, kz, pm[idx]), mz, pk[idx]);
+                    am.add(mz, pm[idx]);
+                    ak.add(kz, pm[idx]);
+                    ak.add(mz, pk[idx]);
                 }
+                m = am.get();
+                k = ak.get();
             } else {
                 m = pm[ty * TX + tx];
                 k = pk[ty * TX + tx];
@@ -244,7 +286,10 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
             } else {
 #pragma unroll
                 for (int i = 0; i < NL; ++i)
-                    if (i < nt) acc[a][i] = madd(madd(acc[a][i], tc.CK[i * NTMAX + jj], m), tc.CM[i * NTMAX + jj], k);
+                    if (i < nt) {
+                        acc[a][i].add(tc.CK[i * NTMAX + jj], m);
+                        acc[a][i].add(tc.CM[i * NTMAX + jj], k);
+                    }
             }
         }
     }
@@ -265,7 +310,7 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
                 r[i] = C(0);
                 continue;
             }
-            C v = acc[a][i];
+            C v = acc[a][i].get();
             if (tc.mode == MODE_RES) {
                 v = to_c<C>(f[base + (long long)i * nxyz]) - v;
                 if (i == 0) v += mprev[a];
