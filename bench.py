@@ -747,7 +747,8 @@ def case_mode(args):
                   outer=args.outer, fused_vcycle=args.fused,
                   spatial_solver=args.case_spatial_solver, minres_tol=args.case_minres_tol,
                   theta=args.case_theta, space_ratio=args.case_space_ratio,
-                  nrhs=args.case_nrhs)
+                  nrhs=args.case_nrhs, nu1=args.case_nu[0], nu2=args.case_nu[1],
+                  inner_tol=args.case_inner_tol)
     n = s.ndofs
     x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
     f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")
@@ -832,6 +833,8 @@ def main():
     ap.add_argument("--case-space-ratio", type=float, default=0.0)
     ap.add_argument("--case-spatial-solver", default="fd", choices=["fd", "minres"])
     ap.add_argument("--case-minres-tol", type=float, default=1e-4)
+    ap.add_argument("--case-nu", type=int, nargs=2, default=[1, 1], help="nu1 nu2")
+    ap.add_argument("--case-inner-tol", type=float, default=1e-4)
     ap.add_argument("--case-profile", action="store_true",
                     help="print per-kernel-class CUDA-event times of one more solve")
     args = ap.parse_args()

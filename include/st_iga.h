@@ -323,6 +323,16 @@ int st_vcycle(st_handle h, double *u, const double *f);
 int st_solve(st_handle h, const double *rhs, double tol, double *u,
              int use_guess, st_solve_info *info);
 
+/* Residual history of the last st_solve on the handle: the FP64 relative
+ * residual ||f - L u||_2 / ||f||_2 (max over the right-hand sides) as the
+ * solver recomputes it -- at the start of every FGMRES cycle, every
+ * multigrid iteration, every refinement step of ST_OUTER_IR -- with the
+ * (inner) iteration count at which it was taken; the last entry is the
+ * final residual.  Copies up to cap entries into its / res (either may be
+ * NULL) and stores the number of entries in *n.  Host only, no device work.
+ * Errors: INVALID_ARG (null handle, cap < 0). */
+int st_solve_history(st_handle h, int cap, int *its, double *res, int *n);
+
 /* Per-kernel-class device timing for measurement.  While enabled, every
  * kernel launch of the handle is bracketed by CUDA events on the handle's
  * stream and its algorithmic bytes and flops (counted from the launch sizes:

@@ -202,6 +202,11 @@ struct st_handle_s {
     double *partial = nullptr, *dots = nullptr;
     int nblk_dot = 0;
     int krylov_m = 0;
+    // residual history of the last st_solve: (iterations so far, max over
+    // the rhs of the FP64 relative residual) at every restart, multigrid
+    // iteration or refinement step (st_solve_history)
+    std::vector<std::pair<int, double>> hist;
+    bool record_hist = false;  // set while the outer iteration runs
 };
 
 namespace {
@@ -1641,6 +1646,7 @@ int solve_mg(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
         CKS(norms<double>(h, r, nr));
         worst = 0.0;
         for (int q = 0; q < h->nrhs; ++q) worst = std::max(worst, nf[q] > 0 ? nr[q] / nf[q] : 0.0);
+        h->hist.emplace_back(it, worst);
         if (worst <= tol || it >= h->opt.max_it) break;
         CKS(precondition(h, r, e));
         std::vector<double> c(h->nrhs, 1.0);
@@ -1679,6 +1685,7 @@ int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vecto
             done[q] = skip[q] || !(nb[q] > 0) || rel <= tol;
             if (!skip[q]) worst = std::max(worst, rel);
         }
+        if (h->record_hist) h->hist.emplace_back(total, worst);
         if (worst <= tol || total >= maxit) break;
         std::vector<double> sc(R);
         for (int q = 0; q < R; ++q) sc[q] = (!done[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
@@ -1833,6 +1840,7 @@ int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vect
             done[q] = skip[q] || !(nb[q] > 0) || rel <= tol;
             if (!skip[q]) worst = std::max(worst, rel);
         }
+        if (h->record_hist) h->hist.emplace_back(total, worst);
         if (worst <= tol || total >= maxit) break;
         {
             std::vector<double> sc(R);
@@ -2129,6 +2137,7 @@ int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_inf
             sc[q] = skip[q] ? 0.0 : 1.0 / nr[q];
             back[q] = skip[q] ? 0.0 : nr[q];
         }
+        h->hist.emplace_back(total, worst);
         if (worst <= tol || total >= h->opt.max_it || outer >= 60) break;
         CKS((vconvert<double, float>(h, h->r64, h->rhs32)));
         CKS(vaxpy<float>(h, 0, nullptr, nullptr, h->rhs32, sc.data()));
@@ -2821,6 +2830,17 @@ int st_vcycle(st_handle h, double *u, const double *f) {
     return check_waits(h);
 }
 
+int st_solve_history(st_handle h, int cap, int *its, double *res, int *n) {
+    if (!h || cap < 0) return fail(ST_ERR_INVALID_ARG, "null handle or negative capacity");
+    const int k = std::min(cap, (int)h->hist.size());
+    for (int i = 0; i < k; ++i) {
+        if (its) its[i] = h->hist[i].first;
+        if (res) res[i] = h->hist[i].second;
+    }
+    if (n) *n = (int)h->hist.size();
+    return ST_OK;
+}
+
 int st_set_wait_limit(st_handle h, double seconds) {
     if (!h) return fail(ST_ERR_INVALID_ARG, "null handle");
     if (!(seconds >= 0) || seconds > 60) return fail(ST_ERR_INVALID_ARG, "wait limit must be in [0, 60] s");
@@ -2868,9 +2888,17 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
     const auto t0 = std::chrono::steady_clock::now();
     try {
         if (!use_guess) CK(launch_zero<double>(u, h->len * h->nrhs, h->stream));
-        if (h->opt.outer == ST_OUTER_MG) CKS(solve_mg(h, rhs, tol, u, info));
-        else if (h->opt.outer == ST_OUTER_IR && h->mixed) CKS(solve_ir(h, rhs, tol, u, info));
-        else CKS(solve_fgmres(h, rhs, tol, u, info));
+        h->hist.clear();
+        if (h->opt.outer == ST_OUTER_MG) {
+            CKS(solve_mg(h, rhs, tol, u, info));
+        } else if (h->opt.outer == ST_OUTER_IR && h->mixed) {
+            CKS(solve_ir(h, rhs, tol, u, info));  // records its refinement steps
+        } else {
+            h->record_hist = true;
+            const int rc = solve_fgmres(h, rhs, tol, u, info);
+            h->record_hist = false;
+            if (rc != ST_OK) return rc;
+        }
         CKS(check_waits(h));
     } catch (...) {
         return fail(ST_ERR_OOM, "host exception during solve");

@@ -33,7 +33,7 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_time_prolongation", "st_level_shape", "st_space_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_resume", "st_serve_cancel", "st_serve_poll", "st_serve_wait",
            "st_serve_stop", "st_setup_partitioned", "st_partition_plan", "st_comm_nccl_unique_id",
-           "st_comm_nccl_create", "st_comm_nccl_destroy"]
+           "st_comm_nccl_create", "st_comm_nccl_destroy", "st_solve_history"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
                 "vector", "dot", "tc", "spec", "stencil_df", "minres"]
 
@@ -151,6 +151,7 @@ def load():
         "st_serve_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(StResult), dp]),
         "st_serve_wait": (I, [P, ctypes.c_uint64, D, ctypes.POINTER(StResult), dp]),
         "st_serve_stop": (I, [P]),
+        "st_solve_history": (I, [P, I, ip, dp, ip]),
         "st_setup_partitioned": (I, [ctypes.POINTER(P), I, I, ip, I, ctypes.POINTER(StOptions),
                                      ctypes.POINTER(StComm), P]),
         "st_partition_plan": (I, [I, I, I, ip, ip, ip]),
@@ -326,6 +327,15 @@ class Solver:
     def set_wait_limit(self, seconds):
         """Bound of the tensor-core kernels' device-side waits (seconds)."""
         _check(_lib.st_set_wait_limit(self._h, float(seconds)))
+
+    def history(self):
+        """[(iterations, relative residual)] of the last solve."""
+        n = ctypes.c_int()
+        _check(_lib.st_solve_history(self._h, 0, None, None, ctypes.byref(n)))
+        its = (ctypes.c_int * max(n.value, 1))()
+        res = (ctypes.c_double * max(n.value, 1))()
+        _check(_lib.st_solve_history(self._h, n.value, its, res, ctypes.byref(n)))
+        return [(its[i], res[i]) for i in range(n.value)]
 
     def autotune(self):
         """Per axis: (choice, ms per pass); choice 0 = CUDA cores, k > 0 =

@@ -471,3 +471,24 @@ def test_fused_vcycle_matches_levelwise(st, prec, d, spans, p, N, ne):
         return
     ref = S.vcycle(hierarchy(pr), f)
     assert relerr(out[0], ref) <= (1e-11 if prec == "fp64" else 1e-4)
+
+
+@pytest.mark.parametrize("prec,outer,basis", [("fp64", "fgmres", "nodal"), ("fp64", "mg", "nodal"),
+                                              ("mixed_tf32", "ir", "spectral")])
+def test_solve_history(st, prec, outer, basis):
+    """st_solve_history: the FP64 relative residual at every restart /
+    multigrid iteration / refinement; it starts at 1 (zero initial guess),
+    ends at the solve's reported residual and decreases overall."""
+    d, spans, p, N = 2, (16, 12), 2, 8
+    pr = A.Problem(d, spans, p, 2, N, theta=1.0)
+    s = st.Solver(d, p, spans, N, precision=prec, outer=outer, basis=basis, gmres_restart=5)
+    f = dev(inputs.uniform_vector(77, pr.ndofs))
+    u = torch.zeros_like(f)
+    info = s.solve(f, u, tol=1e-10)
+    hist = s.history()
+    assert len(hist) >= 2
+    assert abs(hist[0][1] - 1.0) <= 1e-12 and hist[0][0] == 0
+    assert hist[-1][1] == info["rel_residual"] and hist[-1][0] == info["iterations"]
+    assert hist[-1][1] <= 1e-10 < hist[0][1]
+    assert all(b[0] >= a[0] for a, b in zip(hist, hist[1:]))
+    s.close()
