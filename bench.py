@@ -7,7 +7,7 @@ elements (56 623 104 space-time dofs per right-hand side), theta = 1,
 solved together, zero initial guess, to ||f - L u|| <= 1e-8 ||f|| for every
 right-hand side.  Headline method: mixed precision -- iterative refinement
 with an FP64-accurate residual and FP64 update around an FP32 FGMRES(10),
-right-preconditioned by one time-multigrid V(1,1) cycle (damped block
+right-preconditioned by one time-multigrid V(2,2) cycle (damped block
 Jacobi, omega = 1/2, slab inverses by the real Schur time factors and fast
 diagonalisation in space, V-cycle in the spatial eigenbasis); the spatial
 transforms at the refinement boundary run as split TF32 on the tensor cores
@@ -62,6 +62,10 @@ EXTRA = {"cube48_x16": ["square128_p3"]}
 ORACLE_SAMPLE = {"square64": ((64, 64), 8), "square128_p3": ((16, 16), 8),
                  "cube48_x16": ((8, 8, 8), 8), "interval16": ((16,), 8)}
 METRIC = "space-time DoFs/s to rel. residual 1e-8, mixed vs FP64 plain; serve p50/p99"
+# smoothing steps of every V-cycle in the bench (V(2,2): measured faster than
+# V(1,1) on cube48_x16 and square128_p3 -- fewer Krylov steps outweigh the
+# extra smoothing); the library default is V(1,1)
+NU = (2, 2)
 UNIT = "DoFs/s"
 L2_FLUSH_BYTES = 256 << 20
 
@@ -103,13 +107,13 @@ def workload_config(name, precision, basis, outer, fused):
         rhs = "N(0,1) B-spline coefficients, seed %d" % seed
     if outer == "ir":
         solver = ("iterative refinement (FP64-accurate residual, FP64 update) around FP32 "
-                  "FGMRES(%d), right-preconditioned by one V(1,1) time-multigrid cycle, "
-                  "omega=0.5" % restart)
+                  "FGMRES(%d), right-preconditioned by one V(%d,%d) time-multigrid cycle, "
+                  "omega=0.5" % ((restart,) + NU))
     elif outer == "mg":
-        solver = "multigrid iteration with V(1,1) time-multigrid cycles, omega=0.5"
+        solver = "multigrid iteration with V(%d,%d) time-multigrid cycles, omega=0.5" % NU
     else:
-        solver = ("FP64 FGMRES(%d), right-preconditioned by one V(1,1) time-multigrid cycle, "
-                  "omega=0.5" % restart)
+        solver = ("FP64 FGMRES(%d), right-preconditioned by one V(%d,%d) time-multigrid cycle, "
+                  "omega=0.5" % ((restart,) + NU))
     return {"workload": name,
             "domain": "unit %s" % {1: "interval", 2: "square", 3: "cube"}[d],
             "spans": list(spans), "degree": p, "slabs": N, "time_elements_per_slab": ne,
@@ -146,7 +150,8 @@ def _oracle_solve(k):
     pr, H = _ORACLE["pr"], _ORACLE["H"]
     f = A.load_from_coeffs(pr, inputs.normal_coeffs(_ORACLE["seed"] + k, pr.ndofs))
     t0 = time.perf_counter()
-    S.fgmres(H.levels[0].L, f, lambda v: S.vcycle(H, v), tol=_ORACLE["tol"], restart=20)
+    S.fgmres(H.levels[0].L, f, lambda v: S.vcycle(H, v, nu1=NU[0], nu2=NU[1]), tol=_ORACLE["tol"],
+             restart=20)
     return time.perf_counter() - t0
 
 
@@ -202,11 +207,11 @@ def run_cpu_leg(workload, seconds, procs, rounds=1000, warmup=0, bounded=True, s
 
 def sample_text(workload, r):
     d, spans, p, N, ne, tol, seed = WORKLOADS[workload]
-    return ("oracle FGMRES(20) + V(1,1) with sparse-LU slab solves on a sample of %s: %s spans, "
+    return ("oracle FGMRES(20) + V(%d,%d) with sparse-LU slab solves on a sample of %s: %s spans, "
             "%d of %d slabs (%d dofs), same degree, time elements and slab length; "
             "N(0,1) coefficient rhs; setup (LU factorisations) not timed" % (
-                workload, "x".join(str(s) for s in r["sample_spans"]), r["sample_slabs"], N,
-                r["sample_dofs"]))
+                NU[0], NU[1], workload, "x".join(str(s) for s in r["sample_spans"]),
+                r["sample_slabs"], N, r["sample_dofs"]))
 
 
 # ----------------------------------------------------------------------------
@@ -342,7 +347,8 @@ def gpu_arm(args, rank, world):
     wl = args.workload
     d, spans, p, N, ne, tol, seed = WORKLOADS[wl]
     rhs_kind, nrhs, restart = RHS[wl]
-    common = dict(ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
+    common = dict(ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs, nu1=NU[0],
+                  nu2=NU[1])
     peaks, peak_src = load_peaks()
 
     def make(prec, basis, outer, fused=None, spatial="fd", variant="rschur", space_ratio=0.0):
@@ -546,7 +552,8 @@ def extra_workload(args, name):
             prec, basis, outer)
         t0 = time.perf_counter()
         sv = st.Solver(d, p, spans, N, stream=stream.cuda_stream, precision=prec, basis=basis,
-                       outer=outer, ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs)
+                       outer=outer, ne_per_slab=ne, gmres_restart=restart, max_it=300, nrhs=nrhs,
+                       nu1=NU[0], nu2=NU[1])
         setup_ms = 1e3 * (time.perf_counter() - t0)
         if f is None:
             f = torch.empty(sv.ndofs, dtype=torch.float64, device="cuda")
@@ -608,7 +615,8 @@ def serve_arm(args):
         n = (sp + p - 2) ** 2 * N * (ne + p)
         reqs.append((sp, p, N, inputs.normal_coeffs(10000 + i, n)))
     srv = st.Server(workers=args.serve_workers, max_batch=8, precision=args.precision,
-                    basis="spectral", outer="ir", ne_per_slab=ne, gmres_restart=20, max_it=300)
+                    basis="spectral", outer="ir", ne_per_slab=ne, gmres_restart=20, max_it=300,
+                    nu1=NU[0], nu2=NU[1])
     tickets = [None] * nreq
     t0 = time.perf_counter()
 
@@ -866,8 +874,8 @@ def main():
                                "rounds": r["single"]["solves"]}
         cfg_ref = {k: v for k, v in cfg.items()
                    if k not in ("vcycle_basis", "outer", "fused_vcycle", "l2")}
-        cfg_ref.update(precision="fp64", solver="oracle: FGMRES(20) + V(1,1) time multigrid "
-                       "with sparse-LU slab solves (FP64, CPU)")
+        cfg_ref.update(precision="fp64", solver="oracle: FGMRES(20) + V(%d,%d) time multigrid "
+                       "with sparse-LU slab solves (FP64, CPU)" % NU)
         line = {"impl": "reference", "metric": METRIC, "value": leg["value"], "unit": UNIT,
                 "n_gpus": args.gpus, "steps": leg["rounds"], "warmup": args.warmup,
                 "ms_per_step": 1e3 * leg["seconds_per_round"],

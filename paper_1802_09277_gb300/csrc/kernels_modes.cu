@@ -432,6 +432,7 @@ template <typename T>
 struct TailArgs {
     const T *inv[16];  // per-mode inverses of levels l0 .. L
     int nlev;          // L - l0 + 1
+    int nu1, nu2;      // smoothing steps before / after the coarse correction
 };
 
 template <typename T, int NT>
@@ -455,34 +456,64 @@ __global__ void __launch_bounds__(128)
     }
     const long long gbase = q * n0 * NT * S + k;
     for (int e = 0; e < n0 * NT; ++e) f[e] = fin[gbase + (long long)e * S];
-    // down: the smoothing step from zero, residual, restriction
+    // down: nu1 smoothing steps from zero, the residual, restriction.  The
+    // first step from zero is u = w A^-1 f with residual (1 - w) f + e_0 p'
+    // (p' the new last entry of the slab before); each further Jacobi step
+    // u' = u + w A^-1 r carries the residual forward without A:
+    // r' = (1 - w) r + e_0 (p' - p), p / p' that entry before / after the step.
     for (int l = 0; l + 1 < ta.nlev; ++l) {
         const int N = n0 >> l;
         T m[NT * NT];
         load_inv<T, NT>(ta.inv[l], S, k, m);
         T *fl = f + off[l], *ul = u + off[l], *fc = f + off[l + 1];
-        T prev = T(0);  // new last entry of the slab before the pair
+        T r[TAIL_SLABS * NT];
+        if (ta.nu1 == 0) {
+            for (int e = 0; e < N * NT; ++e) {
+                ul[e] = T(0);
+                r[e] = fl[e];
+            }
+        } else {
+            T prev = T(0);  // new last entry of the slab before
+            for (int n = 0; n < N; ++n) {
+                T fa[NT], ua[NT];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) fa[i] = fl[n * NT + i];
+                matvec<T, NT>(m, fa, ua);
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    ua[i] *= omega;
+                    ul[n * NT + i] = ua[i];
+                    r[n * NT + i] = (T(1) - omega) * fa[i];
+                }
+                r[n * NT] += prev;
+                prev = ua[NT - 1];
+            }
+        }
+        for (int st = 1; st < ta.nu1; ++st) {
+            T old_prev = T(0), new_prev = T(0);
+            for (int n = 0; n < N; ++n) {
+                T ra[NT], d[NT];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) ra[i] = r[n * NT + i];
+                matvec<T, NT>(m, ra, d);
+                const T old_last = ul[n * NT + NT - 1];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    ul[n * NT + i] += omega * d[i];
+                    r[n * NT + i] = (T(1) - omega) * ra[i];
+                }
+                r[n * NT] += new_prev - old_prev;
+                old_prev = old_last;
+                new_prev = ul[n * NT + NT - 1];
+            }
+        }
         for (int mc = 0; mc < N / 2; ++mc) {
-            T fa[NT], fb[NT], ua[NT], ub[NT], ra[NT], rb[NT], out[NT];
+            T ra[NT], rb[NT], out[NT];
 #pragma unroll
             for (int i = 0; i < NT; ++i) {
-                fa[i] = fl[(2 * mc) * NT + i];
-                fb[i] = fl[(2 * mc + 1) * NT + i];
+                ra[i] = r[(2 * mc) * NT + i];
+                rb[i] = r[(2 * mc + 1) * NT + i];
             }
-            matvec<T, NT>(m, fa, ua);
-            matvec<T, NT>(m, fb, ub);
-#pragma unroll
-            for (int i = 0; i < NT; ++i) {
-                ua[i] *= omega;
-                ub[i] *= omega;
-                ra[i] = (T(1) - omega) * fa[i];
-                rb[i] = (T(1) - omega) * fb[i];
-                ul[(2 * mc) * NT + i] = ua[i];
-                ul[(2 * mc + 1) * NT + i] = ub[i];
-            }
-            ra[0] += prev;
-            rb[0] += ua[NT - 1];
-            prev = ub[NT - 1];
             restrict_pair<T, NT>(pc, ra, rb, out);
 #pragma unroll
             for (int i = 0; i < NT; ++i) fc[mc * NT + i] = out[i];
@@ -504,7 +535,9 @@ __global__ void __launch_bounds__(128)
             prev = v[NT - 1];
         }
     }
-    // up: prolongation of the coarse correction and the smoothing step
+    // up: prolongation of the coarse correction, then nu2 Jacobi steps
+    // u' = (1 - w) u + w A^-1 (f + e_0 p), p the previous slab's last entry
+    // before the step (the first step fused with the prolongation)
     for (int l = ta.nlev - 2; l >= 0; --l) {
         const int N = n0 >> l;
         T m[NT * NT];
@@ -527,6 +560,14 @@ __global__ void __launch_bounds__(128)
                 ua[j] = ul[(2 * mc) * NT + j] + pa;
                 ub[j] = ul[(2 * mc + 1) * NT + j] + pb;
             }
+            if (ta.nu2 == 0) {
+#pragma unroll
+                for (int i = 0; i < NT; ++i) {
+                    ul[(2 * mc) * NT + i] = ua[i];
+                    ul[(2 * mc + 1) * NT + i] = ub[i];
+                }
+                continue;
+            }
 #pragma unroll
             for (int i = 0; i < NT; ++i) r[i] = fl[(2 * mc) * NT + i];
             r[0] += prev;
@@ -542,6 +583,20 @@ __global__ void __launch_bounds__(128)
 #pragma unroll
             for (int i = 0; i < NT; ++i)
                 ul[(2 * mc + 1) * NT + i] = (T(1) - omega) * ub[i] + omega * v[i];
+        }
+        for (int st = 1; st < ta.nu2; ++st) {
+            T old_prev = T(0);
+            for (int n = 0; n < N; ++n) {
+                T r[NT], v[NT];
+#pragma unroll
+                for (int i = 0; i < NT; ++i) r[i] = fl[n * NT + i];
+                r[0] += old_prev;
+                matvec<T, NT>(m, r, v);
+                old_prev = ul[n * NT + NT - 1];
+#pragma unroll
+                for (int i = 0; i < NT; ++i)
+                    ul[n * NT + i] = (T(1) - omega) * ul[n * NT + i] + omega * v[i];
+            }
         }
     }
     for (int e = 0; e < n0 * NT; ++e) uout[gbase + (long long)e * S] = u[e];
@@ -652,12 +707,15 @@ cudaError_t launch_spec_op(const T *u, const T *f, T *out, const T *mu, const Gr
 template <typename T>
 cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nlev,
                              const Grid &g, const ProlongCoefs<T> &pc, T omega, int n0, int nrhs,
-                             cudaStream_t s) {
+                             int nu1, int nu2, cudaStream_t s) {
     if (n0 > TAIL_SLABS || nlev > 16 || nlev < 1 || (n0 >> (nlev - 1)) < 1) return cudaErrorNotSupported;
+    if (nu1 < 0 || nu2 < 0 || nu1 > 8 || nu2 > 8) return cudaErrorNotSupported;
     if (g.nxyz <= 0 || nrhs <= 0) return cudaSuccess;
     TailArgs<T> ta;
     for (int l = 0; l < nlev; ++l) ta.inv[l] = inv[l];
     ta.nlev = nlev;
+    ta.nu1 = nu1;
+    ta.nu2 = nu2;
     ModeLaunch L = mode_launch(g.nxyz, nrhs);
     if (L.block.x > 128) {  // smaller CTAs: more SMs share the few modes
         L.block.x = 128;
@@ -676,7 +734,8 @@ template cudaError_t launch_mode_inverse<float>(float *, const double *, const G
                                                 const SpecCoefs<double> &, cudaStream_t);
 #define ST_INST(T)                                                                              \
     template cudaError_t launch_spec_tail<T>(const T *, T *, const T *const *, int, const Grid &, \
-                                             const ProlongCoefs<T> &, T, int, int, cudaStream_t);   \
+                                             const ProlongCoefs<T> &, T, int, int, int, int,     \
+                                             cudaStream_t);                                      \
     template cudaError_t launch_spec_smooth<T>(const T *, T *, const T *, const T *,            \
                                                const Grid &, int, T, int, long long, int,       \
                                                cudaStream_t);                                   \

@@ -1342,11 +1342,12 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     CKS(ensure_inv<T>(h));
     const T *inv = inv_tabs<T>(h)[l];
     // the coarse end of the cycle (at most 16 slabs per problem) in one launch
-    if (zero_init && h->opt.nu1 == 1 && h->opt.nu2 == 1 && spp <= 16 && l < h->nlev - 1) {
-        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E, E * 2.0 * (6.0 * nt + 6.0));
+    if (zero_init && spp <= 16 && l < h->nlev - 1) {
+        const double nu = h->opt.nu1 + h->opt.nu2;
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E, E * nu * (6.0 * nt + 6.0));
         const cudaError_t e = launch_spec_tail<T>(f, u, inv_tabs<T>(h).data() + l, h->nlev - l, h->g,
                                                   pack_prolong<T>(h), (T)h->opt.omega, spp,
-                                                  h->nrhs, h->stream);
+                                                  h->nrhs, h->opt.nu1, h->opt.nu2, h->stream);
         if (e == cudaSuccess) return ST_OK;
         if (e != cudaErrorNotSupported) CK(e);
         cudaGetLastError();

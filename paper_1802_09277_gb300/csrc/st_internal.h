@@ -164,13 +164,13 @@ template <typename TO>
 cudaError_t launch_mode_inverse(TO *inv, const double *mu64, const Grid &g,
                                 const SpecCoefs<double> &c, cudaStream_t s);
 // the V-cycle's coarse levels l0 .. l0 + nlev - 1 (n0 slabs per problem on
-// level l0, nu1 = nu2 = 1, zero start) in one launch: fin = f on level l0,
-// uout = u on level l0; inv[i] = the per-mode inverses of level l0 + i.
-// cudaErrorNotSupported when n0 > 16 or nlev > 16
+// level l0, nu1 / nu2 smoothing steps, zero start) in one launch: fin = f on
+// level l0, uout = u on level l0; inv[i] = the per-mode inverses of level
+// l0 + i.  cudaErrorNotSupported when n0 > 16, nlev > 16 or nu > 8
 template <typename T>
 cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nlev,
                              const Grid &g, const ProlongCoefs<T> &pc, T omega, int n0, int nrhs,
-                             cudaStream_t s);
+                             int nu1, int nu2, cudaStream_t s);
 // uout = (1 - omega) uin + omega A^{-1} (f + e_0 uin_prev) (uin_zero: uin = 0)
 template <typename T>
 cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *inv, const Grid &g,
