@@ -756,7 +756,7 @@ def case_mode(args):
                   spatial_solver=args.case_spatial_solver, minres_tol=args.case_minres_tol,
                   theta=args.case_theta, space_ratio=args.case_space_ratio,
                   nrhs=args.case_nrhs, nu1=args.case_nu[0], nu2=args.case_nu[1],
-                  inner_tol=args.case_inner_tol)
+                  inner_tol=args.case_inner_tol, gmres_restart=args.case_restart)
     n = s.ndofs
     x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
     f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")
@@ -843,6 +843,7 @@ def main():
     ap.add_argument("--case-minres-tol", type=float, default=1e-4)
     ap.add_argument("--case-nu", type=int, nargs=2, default=[1, 1], help="nu1 nu2")
     ap.add_argument("--case-inner-tol", type=float, default=1e-4)
+    ap.add_argument("--case-restart", type=int, default=20, help="FGMRES restart (memory)")
     ap.add_argument("--case-profile", action="store_true",
                     help="print per-kernel-class CUDA-event times of one more solve")
     args = ap.parse_args()

@@ -23,7 +23,12 @@
 // A wait that runs out is decided for the whole CTA at once (a CTA-wide
 // vote, so every thread takes the same barriers): the CTA records the error,
 // waits (bounded again) for its MMAs in flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "st_internal.h"
 #include "tc_sm100.cuh"
@@ -106,6 +111,7 @@ struct TcArgs {
     long long inner;   // MODE_S: stride of the contracted axis
     int *err;          // set to 1 if an mbarrier wait ran out
     unsigned long long wait_ns;  // bound of each wait for the MMAs (0: test once)
+    int w_tma;         // pipelined kernel: the weight operand arrives by TMA (tensor map)
 };
 
 // Stage 16-byte chunks [k0, k0 + kcs) of the weight operand (rows = output
@@ -304,6 +310,378 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
 
 constexpr size_t TC_SMEM_MAX = 200 * 1024;
 
+// ---------------------------------------------------------------------------
+// Pipelined variant: each CTA keeps two tensor-memory accumulators and the
+// next column tile in registers, so that the MMAs of tile k, the global loads
+// of tile k + 1 and the epilogue of tile k - 1 overlap:
+//     wait MMA(k-1) -> convert tile k into shared memory -> issue MMA(k)
+//     -> load tile k+1 into registers -> drain accumulator of tile k-1.
+// The weight operand is staged once per CTA: a 2D TMA copy of the raw FP32
+// W^T (box n_pad x k_pad, zero-filled outside n_out x n_in) into the
+// activation area, converted there into the MMA layout.  Covers shapes whose
+// whole K fits in shared memory and whose tile fits the register prefetch
+// (K <= 80 for TF32 / split TF32, <= 96 for BF16); others use k_tc_axis.
+// The contiguous axis runs as MODE_XT: the activation tile (128 input rows)
+// is the 128-row operand and W the N = n_pad one, D[c][k] with lane = c, so
+// no MMA rows are spent on absent output modes (k_tc_axis's MODE_X makes W
+// the 128-row operand); each lane then writes its row out[c][0 .. n_out).
+// ---------------------------------------------------------------------------
+template <int EPC>
+struct PipeTraits {
+    static constexpr int PF = (EPC == 4) ? 10 : 6;  // 16-byte chunks per thread in flight
+};
+
+// Global -> registers: the 16-byte chunks of column tile c0 this thread
+// stages (the same mapping as k_tc_axis's staging loops).
+template <int KIND, int MODE>
+__device__ __forceinline__ void pipe_load(const TcArgs &a, long long c0, int KC,
+                                          float (&pre)[PipeTraits<16 / KindTraits<KIND>::ESZ>::PF]
+                                                      [16 / KindTraits<KIND>::ESZ]) {
+    constexpr int EPC = 16 / KindTraits<KIND>::ESZ;
+    constexpr int PF = PipeTraits<EPC>::PF;
+#pragma unroll
+    for (int it = 0; it < PF; ++it) {
+        const int t = threadIdx.x + it * TC_THREADS;
+        if (t >= TC_COLS * KC) break;
+        if (MODE != 1) {
+            const int grp = t / (8 * KC), rem = t % (8 * KC);
+            const int kc = rem / 8, r = grp * 8 + rem % 8;
+            const long long c = c0 + r;
+            const int i0 = kc * EPC;
+            if (a.vec4 && c < a.ncols && i0 + EPC <= a.n_in) {
+#pragma unroll
+                for (int j = 0; j < EPC; j += 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(a.in + c * a.n_in + i0 + j);
+                    pre[it][j] = q.x;
+                    pre[it][j + 1] = q.y;
+                    pre[it][j + 2] = q.z;
+                    pre[it][j + 3] = q.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < EPC; ++j) {
+                    const int i = i0 + j;
+                    pre[it][j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
+                }
+            }
+        } else {
+            const int kc = t / TC_COLS, r = t % TC_COLS;
+            const long long c = c0 + r;
+            const long long o = c / a.inner, ci = c % a.inner;
+            const float *src = a.in + o * a.n_in * a.inner + ci;
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) {
+                const int i = kc * EPC + j;
+                pre[it][j] = (c < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
+            }
+        }
+    }
+}
+
+// Registers -> the activation tile in the MMA layout (TF32 / BF16 / hi + lo).
+template <int KIND, int MODE>
+__device__ __forceinline__ void pipe_stage(unsigned char *xtile, size_t xbytes, int KC,
+                                           const float (&pre)[PipeTraits<16 / KindTraits<KIND>::ESZ>::PF]
+                                                             [16 / KindTraits<KIND>::ESZ]) {
+    constexpr int EPC = 16 / KindTraits<KIND>::ESZ;
+    constexpr int PF = PipeTraits<EPC>::PF;
+#pragma unroll
+    for (int it = 0; it < PF; ++it) {
+        const int t = threadIdx.x + it * TC_THREADS;
+        if (t >= TC_COLS * KC) break;
+        int kc, r;
+        if (MODE != 1) {
+            const int grp = t / (8 * KC), rem = t % (8 * KC);
+            kc = rem / 8;
+            r = grp * 8 + rem % 8;
+        } else {
+            kc = t / TC_COLS;
+            r = t % TC_COLS;
+        }
+        stage16<KIND>(xtile, TC_COLS, r, kc, pre[it], xbytes);
+    }
+}
+
+// One column tile's MMAs into the accumulator at `acc` (single thread).
+template <int KIND, int MODE>
+__device__ __forceinline__ void pipe_mma(const unsigned char *wtile, const unsigned char *xtile,
+                                         size_t wbytes, size_t xbytes, int wrows, int KC, int mh,
+                                         uint32_t acc, uint32_t idesc) {
+    using KT = KindTraits<KIND>;
+    const uint32_t wa = tc::smem_u32(wtile), xa = tc::smem_u32(xtile);
+    const uint32_t lbo_w = (uint32_t)wrows * 16, lbo_x = TC_COLS * 16;
+    constexpr int NPROD = (KT::NSPLIT == 2) ? 3 : 1;  // split: (hi, hi), (hi, lo), (lo, hi)
+    for (int st = 0; st < KC / 2; ++st) {
+#pragma unroll
+        for (int q = 0; q < NPROD; ++q) {
+            const uint32_t wo = (q == 2) ? (uint32_t)wbytes : 0u;
+            const uint32_t xo = (q == 1) ? (uint32_t)xbytes : 0u;
+            const uint64_t dx = tc::make_sdesc(xa + xo + 2 * st * lbo_x, lbo_x, 128);
+            const uint32_t accum = (st > 0 || q > 0) ? 1u : 0u;
+            if (MODE == 0) {
+                for (int h = 0; h < mh; ++h) {
+                    const uint64_t dw =
+                        tc::make_sdesc(wa + wo + 2 * st * lbo_w + (uint32_t)h * 2048u, lbo_w, 128);
+                    tc::mma<KT::FMT>(acc + (uint32_t)(h * TC_COLS), dw, dx, idesc, accum);
+                }
+            } else {
+                const uint64_t dw = tc::make_sdesc(wa + wo + 2 * st * lbo_w, lbo_w, 128);
+                tc::mma<KT::FMT>(acc, dx, dw, idesc, accum);
+            }
+        }
+    }
+}
+
+// Accumulator -> global for column tile c0 (all 8 warps; warp w reads TMEM
+// lanes 32 (w % 4) .., warps w and w + 4 split the columns).
+template <int MODE>
+__device__ __forceinline__ void pipe_epilogue(const TcArgs &a, long long c0, uint32_t acc, int mh) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wq = warp & 3, wh = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
+    if (MODE == 0) {
+        for (int h = 0; h < mh; ++h) {
+            const int k = 128 * h + 32 * wq + lane;
+            if (128 * h + 32 * wq >= a.n_out) continue;
+            for (int cc = wh * (TC_COLS / 2); cc < (wh + 1) * (TC_COLS / 2); cc += 16) {
+                float v[16];
+                tc::tmem_ld16(acc + lane_base + (uint32_t)(h * TC_COLS + cc), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const long long c = c0 + cc + j;
+                    if (k < a.n_out && c < a.ncols) a.out[c * a.n_out + k] = v[j];
+                }
+            }
+        }
+    } else if (MODE == 2) {
+        // lane = row c of the output; 16 consecutive modes per TMEM load
+        const long long c = c0 + 32 * wq + lane;
+        float *dst = a.out + c * a.n_out;
+        const bool v4 = a.vec4 && (a.n_out % 4 == 0);
+        const int nk = a.n_pad / 16;
+        for (int kk = 16 * ((nk * wh) / 2); kk < 16 * ((nk * (wh + 1)) / 2); kk += 16) {
+            float v[16];
+            tc::tmem_ld16(acc + lane_base + kk, v);
+            if (c >= a.ncols) continue;
+            if (v4 && kk + 16 <= a.n_out) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4 *>(dst + kk + j) =
+                        make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (kk + j < a.n_out) dst[kk + j] = v[j];
+            }
+        }
+    } else {
+        const long long c = c0 + 32 * wq + lane;
+        const long long o = c / a.inner, ci = c % a.inner;
+        float *dst = a.out + o * a.n_out * a.inner + ci;
+        const int nk = a.n_pad / 16;
+        for (int kk = 16 * ((nk * wh) / 2); kk < 16 * ((nk * (wh + 1)) / 2); kk += 16) {
+            float v[16];
+            tc::tmem_ld16(acc + lane_base + kk, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = kk + j;
+                if (k < a.n_out && c < a.ncols) dst[(long long)k * a.inner] = v[j];
+            }
+        }
+    }
+}
+
+__host__ __device__ inline uint32_t tc_acc_cols(int mode, int mh, int n_pad) {
+    return mode == 0 ? (uint32_t)(TC_COLS * mh)
+                     : (n_pad <= 32 ? 32u : n_pad <= 64 ? 64u : n_pad <= 128 ? 128u : 256u);
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(TC_THREADS)
+    k_tc_axis_pipe(const __grid_constant__ TcArgs a, const __grid_constant__ CUtensorMap wmap) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t mbar_w;
+    __shared__ uint32_t tmem_base;
+    using KT = KindTraits<KIND>;
+    constexpr int EPC = 16 / KT::ESZ;
+    constexpr int PF = PipeTraits<EPC>::PF;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int KC = a.k_pad / EPC;
+    const int mh = (MODE == 0) ? a.mh : 1;
+    const int wrows = (MODE == 0) ? 128 * mh : a.n_pad;
+    const size_t wbytes = (size_t)wrows * KC * 16, xbytes = (size_t)TC_COLS * KC * 16;
+    // operand area from the next 128-byte boundary (the launch adds 128 bytes):
+    // the TMA destination inside it must be 128-byte aligned
+    unsigned char *base = smem + ((128u - (tc::smem_u32(smem) & 127u)) & 127u);
+    unsigned char *wtile = base;
+    unsigned char *xtile = base + KT::NSPLIT * wbytes;  // wbytes is a multiple of 512
+    const uint32_t acc_cols = tc_acc_cols(MODE, mh, a.n_pad);
+    const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
+
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init(&mbar_w, 1);
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * acc_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    bool failed = false;
+
+    // ---- the weight operand, once per CTA ----
+    if (a.w_tma) {
+        float *raw = reinterpret_cast<float *>(xtile);  // free until the first tile
+        if (tid == 0) {
+            tc::mbar_expect_tx(&mbar_w, (uint32_t)(a.n_pad * a.k_pad * 4));
+            tc::tma_load_2d(raw, &wmap, 0, 0, &mbar_w);
+        }
+        const bool ok = tc::mbar_wait_bounded(&mbar_w, 0, TC_DRAIN_NS);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            tc::mbar_wait_bounded(&mbar_w, 0, TC_DRAIN_NS);  // the copy lands before exit
+            failed = true;
+            if (tid == 0) atomicExch(a.err, 1);
+        } else {
+            for (int t = tid; t < wrows * KC; t += TC_THREADS) {
+                const int kc = t / wrows, r = t % wrows;
+                float v[EPC];
+#pragma unroll
+                for (int j = 0; j < EPC; ++j)
+                    v[j] = (r < a.n_pad) ? raw[r * a.k_pad + kc * EPC + j] : 0.f;
+                stage16<KIND>(wtile, wrows, r, kc, v, wbytes);
+            }
+        }
+        __syncthreads();  // the raw weights are read before the first tile lands there
+    } else {
+        stage_w<KIND>(a, wtile, wrows, 0, KC, wbytes);
+    }
+    const uint32_t idesc = (MODE == 0) ? tc::make_idesc(KT::FMT, 128, TC_COLS)
+                                       : tc::make_idesc(KT::FMT, 128, a.n_pad);
+
+    float pre[PF][EPC];
+    long long tile = blockIdx.x, prev_tile = -1;
+    if (!failed && tile < ntiles) pipe_load<KIND, MODE>(a, tile * TC_COLS, KC, pre);
+    uint32_t ph[2] = {0u, 0u};
+    int k = 0;
+    while (!failed && tile < ntiles) {
+        const int b = k & 1;
+        if (k >= 1) {  // MMA(k-1) done: the activation tile is free, its accumulator ready
+            const bool ok = tc::mbar_wait_bounded(&mbar[b ^ 1], ph[b ^ 1], a.wait_ns);
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                tc::mbar_wait_bounded(&mbar[b ^ 1], ph[b ^ 1], TC_DRAIN_NS);
+                failed = true;
+                if (tid == 0) atomicExch(a.err, 1);
+                break;
+            }
+            ph[b ^ 1] ^= 1u;
+            tc::fence_after_sync();
+        }
+        pipe_stage<KIND, MODE>(xtile, xbytes, KC, pre);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            pipe_mma<KIND, MODE>(wtile, xtile, wbytes, xbytes, wrows, KC, mh, tmem + b * acc_cols,
+                                 idesc);
+            tc::commit(&mbar[b]);
+        }
+        const long long next = tile + gridDim.x;
+        if (next < ntiles) pipe_load<KIND, MODE>(a, next * TC_COLS, KC, pre);
+        if (k >= 1) pipe_epilogue<MODE>(a, prev_tile * TC_COLS, tmem + (b ^ 1) * acc_cols, mh);
+        // this epilogue's tensor-memory reads precede the next MMA into that accumulator
+        tc::fence_before_sync();
+        prev_tile = tile;
+        tile = next;
+        ++k;
+    }
+    if (!failed && k >= 1) {  // the last tile
+        const int b = (k - 1) & 1;
+        const bool ok = tc::mbar_wait_bounded(&mbar[b], ph[b], a.wait_ns);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            tc::mbar_wait_bounded(&mbar[b], ph[b], TC_DRAIN_NS);
+            if (tid == 0) atomicExch(a.err, 1);
+        } else {
+            tc::fence_after_sync();
+            pipe_epilogue<MODE>(a, prev_tile * TC_COLS, tmem + b * acc_cols, mh);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * acc_cols);
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); nullptr if unavailable.
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+template <int KIND, int MODE>
+static cudaError_t launch_tc_pipe(TcArgs a, cudaStream_t s, int nsm, int ctas_per_sm) {
+    using KT = KindTraits<KIND>;
+    constexpr int EPC = 16 / KT::ESZ;
+    const int KC = a.k_pad / EPC;
+    if (TC_COLS * KC > TC_THREADS * PipeTraits<EPC>::PF) return cudaErrorNotSupported;
+    const int mh = (MODE == 0) ? a.mh : 1;
+    const int wrows = (MODE == 0) ? 128 * mh : a.n_pad;
+    const size_t wbytes = (size_t)wrows * KC * 16, xbytes = (size_t)TC_COLS * KC * 16;
+    const size_t smem = KT::NSPLIT * (wbytes + xbytes) + 128;  // + alignment slack
+    if (smem > TC_SMEM_MAX) return cudaErrorNotSupported;
+    if (wbytes % 512 != 0) return cudaErrorNotSupported;  // keeps the TMA destination aligned
+    const uint32_t acc_cols = tc_acc_cols(MODE, mh, a.n_pad);
+    if (2 * acc_cols > 512) return cudaErrorNotSupported;
+    // the weights by TMA: row pitch a multiple of 16 bytes, the padded box
+    // within the activation area it is staged in
+    CUtensorMap wmap;
+    std::memset(&wmap, 0, sizeof wmap);
+    a.w_tma = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (enc && (a.n_in * 4) % 16 == 0 && (reinterpret_cast<uintptr_t>(a.wt) & 15u) == 0 &&
+        (size_t)a.n_pad * a.k_pad * 4 <= KT::NSPLIT * xbytes && a.k_pad <= 256 && a.n_pad <= 256) {
+        const cuuint64_t gdim[2] = {(cuuint64_t)a.n_in, (cuuint64_t)a.n_out};
+        const cuuint64_t gstride[1] = {(cuuint64_t)a.n_in * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)a.k_pad, (cuuint32_t)a.n_pad};
+        const cuuint32_t estride[2] = {1, 1};
+        if (enc(&wmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(a.wt), gdim,
+                gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+            a.w_tma = 1;
+    }
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e =
+            smem_attr_once((const void *)k_tc_axis_pipe<KIND, MODE>, (int)TC_SMEM_MAX, attr);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = (int)(512 / (2 * acc_cols));
+    const int by_smem = (int)((220 * 1024) / (smem + 1024));
+    if (by_smem < per_sm) per_sm = by_smem;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
+    long long grid = (long long)nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid <= 0) return cudaSuccess;
+    k_tc_axis_pipe<KIND, MODE><<<(unsigned)grid, TC_THREADS, smem, s>>>(a, wmap);
+    return cudaGetLastError();
+}
+
 template <int KIND, int MODE>
 static cudaError_t launch_tc_t(TcArgs a, cudaStream_t s, int nsm, int ctas_per_sm) {
     using KT = KindTraits<KIND>;
@@ -376,7 +754,23 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
     if (mode == 1 && a.n_pad > 256) return cudaErrorNotSupported;
     a.mh = (mode == 0 && n_out > 128) ? 2 : 1;
     a.kch = 0;
-    a.vec4 = (mode == 0 && n_in % 4 == 0 && (reinterpret_cast<uintptr_t>(in) & 15u) == 0) ? 1 : 0;
+    a.vec4 = (mode == 0 && n_in % 4 == 0 && (reinterpret_cast<uintptr_t>(in) & 15u) == 0 &&
+              (reinterpret_cast<uintptr_t>(out) & 15u) == 0) ? 1 : 0;
+    a.w_tma = 0;
+    // the pipelined kernel where the shape fits it, else the one-tile-at-a-time one
+    cudaError_t e;
+    // (the contiguous axis as MODE_XT = 2)
+    if (kind == KIND_TF32X3)
+        e = mode == 0 ? launch_tc_pipe<KIND_TF32X3, 2>(a, s, nsm, ctas_per_sm)
+                      : launch_tc_pipe<KIND_TF32X3, 1>(a, s, nsm, ctas_per_sm);
+    else if (kind == tc::FMT_TF32)
+        e = mode == 0 ? launch_tc_pipe<tc::FMT_TF32, 2>(a, s, nsm, ctas_per_sm)
+                      : launch_tc_pipe<tc::FMT_TF32, 1>(a, s, nsm, ctas_per_sm);
+    else
+        e = mode == 0 ? launch_tc_pipe<tc::FMT_BF16, 2>(a, s, nsm, ctas_per_sm)
+                      : launch_tc_pipe<tc::FMT_BF16, 1>(a, s, nsm, ctas_per_sm);
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
     if (kind == KIND_TF32X3)
         return mode == 0 ? launch_tc_t<KIND_TF32X3, 0>(a, s, nsm, ctas_per_sm)
                          : launch_tc_t<KIND_TF32X3, 1>(a, s, nsm, ctas_per_sm);

@@ -139,6 +139,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parit
     }
 }
 
+// ---- TMA (tensor memory accelerator) ----
+// Arm the mbarrier for one arrival plus `bytes` bytes of asynchronous copies.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+// 2D tiled TMA load of the box at element coordinates (x, y) of the tensor map
+// (a __grid_constant__ kernel parameter) into shared memory; completion is
+// signalled on the mbarrier as transferred bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y,
+                                            uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];"
+        :: "r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y),
+           "r"(smem_u32(mbar))
+        : "memory");
+}
+
 // ---- TMEM -> registers: 32 lanes x 32 bit, 16 consecutive columns ----
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
