@@ -756,7 +756,8 @@ def case_mode(args):
                   spatial_solver=args.case_spatial_solver, minres_tol=args.case_minres_tol,
                   theta=args.case_theta, space_ratio=args.case_space_ratio,
                   nrhs=args.case_nrhs, nu1=args.case_nu[0], nu2=args.case_nu[1],
-                  inner_tol=args.case_inner_tol, gmres_restart=args.case_restart)
+                  inner_tol=args.case_inner_tol, gmres_restart=args.case_restart,
+                  autotune=args.case_autotune)
     n = s.ndofs
     x = torch.tensor(inputs.uniform_vector(1, n), dtype=torch.float64, device="cuda")
     f = torch.tensor(inputs.uniform_vector(2, n), dtype=torch.float64, device="cuda")
@@ -818,7 +819,7 @@ def main():
                     help="keep the raw nvidia-smi clock samples of the timed region in this file")
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--basis", default="spectral", choices=["spectral", "nodal"])
     ap.add_argument("--outer", default="ir", choices=["ir", "fgmres", "mg"])
     ap.add_argument("--precision", default="mixed_tf32",
@@ -844,6 +845,7 @@ def main():
     ap.add_argument("--case-nu", type=int, nargs=2, default=[1, 1], help="nu1 nu2")
     ap.add_argument("--case-inner-tol", type=float, default=1e-4)
     ap.add_argument("--case-restart", type=int, default=20, help="FGMRES restart (memory)")
+    ap.add_argument("--case-autotune", type=int, default=1, choices=[0, 1])
     ap.add_argument("--case-profile", action="store_true",
                     help="print per-kernel-class CUDA-event times of one more solve")
     args = ap.parse_args()

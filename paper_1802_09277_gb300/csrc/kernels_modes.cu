@@ -420,6 +420,131 @@ __global__ void __launch_bounds__(256)
     store_col<T, NT>(out, base, S, r);
 }
 
+// Sweeping level kernels for nu >= 2 smoothing steps: one thread per
+// spatial mode and chunk of C consecutive slabs of one right-hand side walks
+// its slabs in time order.  A Jacobi step of slab n needs only the previous
+// slab's last entry from the step before, so all NU steps of a slab run in
+// registers as the sweep passes it (the previous slab's last entry after
+// each step is kept): every level is read and written once whatever NU.  A
+// chunk first recomputes the NU slabs before it (halo; their results are not
+// stored), after which its own slabs are exact.
+//
+// k_lv_sweep_down: from u = 0, NU steps, the residual of the result and its
+// restriction.  In residual form a step is u' = u + w A^-1 r and the residual
+// moves to r' = (1 - w) r + e_0 (p' - p), p / p' the previous slab's last
+// entry before / after the step, so only A^-1 is needed; r starts at f.
+template <typename T, int NT, int NU>
+__global__ void __launch_bounds__(256)
+    k_lv_sweep_down(const T *__restrict__ f, T *__restrict__ u, T *__restrict__ fc,
+                    const T *__restrict__ inv, long long S, const __grid_constant__ ProlongCoefs<T> pc,
+                    T omega, int N, int C, int nchunk, long long nwork) {
+    griddep_wait();
+    griddep_launch();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long w = slab_index();
+    if (k >= S || w >= nwork) return;
+    const long long q = w / nchunk;
+    const int n0 = (int)(w % nchunk) * C;
+    const int n1 = (n0 + C < N) ? n0 + C : N;
+    const int h = (n0 - NU > 0) ? n0 - NU : 0;
+    const long long slab = (long long)NT * S;
+    const long long fb = q * N * slab + k, cb = q * (N / 2) * slab + k;
+    T m[NT * NT];
+    load_inv<T, NT>(inv, S, k, m);
+    T last[NU + 1];  // previous slab's last entry after step s (s = 0: the zero start)
+#pragma unroll
+    for (int st = 0; st <= NU; ++st) last[st] = T(0);
+    T reven[NT];
+    for (int n = h; n < n1; ++n) {
+        T r[NT], x[NT];
+        load_col<T, NT>(f, fb + n * slab, S, r);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) x[i] = T(0);
+        T nl[NU + 1];
+        nl[0] = T(0);
+#pragma unroll
+        for (int st = 1; st <= NU; ++st) {
+            T d[NT];
+            matvec<T, NT>(m, r, d);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                x[i] += omega * d[i];
+                r[i] = (T(1) - omega) * r[i];
+            }
+            r[0] += last[st] - last[st - 1];
+            nl[st] = x[NT - 1];
+        }
+#pragma unroll
+        for (int st = 0; st <= NU; ++st) last[st] = nl[st];
+        if (n < n0) continue;
+        store_col<T, NT>(u, fb + n * slab, S, x);
+        if (((n - n0) & 1) == 0) {
+#pragma unroll
+            for (int i = 0; i < NT; ++i) reven[i] = r[i];
+        } else {
+            T out[NT];
+            restrict_pair<T, NT>(pc, reven, r, out);
+            store_col<T, NT>(fc, cb + (long long)(n / 2) * slab, S, out);
+        }
+    }
+}
+
+// k_lv_sweep_up: the prolongation u + P_t e and NU Jacobi steps
+// u' = (1 - w) u + w A^-1 (f + e_0 p), p the previous slab's last entry
+// before the step, out of place (uin -> uout: the next chunk's halo reads uin).
+template <typename T, int NT, int NU>
+__global__ void __launch_bounds__(256)
+    k_lv_sweep_up(const T *__restrict__ ec, const T *__restrict__ uin, T *__restrict__ uout,
+                  const T *__restrict__ f, const T *__restrict__ inv, long long S,
+                  const __grid_constant__ ProlongCoefs<T> pc, T omega, int N, int C, int nchunk,
+                  long long nwork) {
+    griddep_wait();
+    griddep_launch();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const long long w = slab_index();
+    if (k >= S || w >= nwork) return;
+    const long long q = w / nchunk;
+    const int n0 = (int)(w % nchunk) * C;
+    const int n1 = (n0 + C < N) ? n0 + C : N;
+    const int h = (n0 - NU > 0) ? n0 - NU : 0;
+    const long long slab = (long long)NT * S;
+    const long long fb = q * N * slab + k, cb = q * (N / 2) * slab + k;
+    T m[NT * NT];
+    load_inv<T, NT>(inv, S, k, m);
+    T last[NU];  // previous slab's last entry before step s + 1
+#pragma unroll
+    for (int st = 0; st < NU; ++st) last[st] = T(0);
+    for (int n = h; n < n1; ++n) {
+        T x[NT], e[NT], fr[NT];
+        load_col<T, NT>(uin, fb + n * slab, S, x);
+        load_col<T, NT>(ec, cb + (long long)(n / 2) * slab, S, e);
+        load_col<T, NT>(f, fb + n * slab, S, fr);
+        const int half = (n & 1) ? NT : 0;  // row block of P_t for this slab of the pair
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+            T pj = T(0);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) pj += pc.P[(half + j) * NTMAX + i] * e[i];
+            x[j] += pj;
+        }
+        T nl[NU];
+#pragma unroll
+        for (int st = 0; st < NU; ++st) {
+            T rr[NT], v[NT];
+#pragma unroll
+            for (int i = 0; i < NT; ++i) rr[i] = fr[i];
+            rr[0] += last[st];
+            nl[st] = x[NT - 1];
+            matvec<T, NT>(m, rr, v);
+#pragma unroll
+            for (int i = 0; i < NT; ++i) x[i] = (T(1) - omega) * x[i] + omega * v[i];
+        }
+#pragma unroll
+        for (int st = 0; st < NU; ++st) last[st] = nl[st];
+        if (n >= n0) store_col<T, NT>(uout, fb + n * slab, S, x);
+    }
+}
+
 // The coarse end of the V-cycle, levels l0 .. L (N_{l0} <= TAIL_SLABS slabs
 // per problem, nu1 = nu2 = 1, zero initial iterate on every level), in one
 // launch: one thread per (spatial mode, rhs) runs the sub-cycle sequentially
@@ -726,6 +851,61 @@ cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nle
                                           pc, g.nxyz, n0, omega)));
     return e != cudaSuccess ? e : cudaGetLastError();
 }
+// Chunk length of the sweeping kernels: enough (mode, chunk) threads to fill
+// the GPU, chunks even and at least 4 NU slabs long (halo overhead <= 1/4).
+static void sweep_chunks(long long S, int R, int N, int nu, int *C, int *nchunk) {
+    const long long want = 152LL * 2048;
+    long long nc = (want + S * R - 1) / (S * R);
+    const long long cmax = N / (4 * nu) > 1 ? N / (4 * nu) : 1;
+    if (nc > cmax) nc = cmax;
+    if (nc < 1) nc = 1;
+    int c = (int)((N + nc - 1) / nc);
+    c = (c + 1) & ~1;
+    *C = c;
+    *nchunk = (N + c - 1) / c;
+}
+
+template <typename T>
+cudaError_t launch_spec_sweep_down(const T *f, T *u, T *fc, const T *inv, const Grid &g,
+                                   const ProlongCoefs<T> &pc, T omega, int N, int nrhs, int nu,
+                                   cudaStream_t s) {
+    if (nu < 2 || nu > 4 || N % 2 != 0) return cudaErrorNotSupported;
+    if (g.nxyz <= 0 || nrhs <= 0) return cudaSuccess;
+    int C = 0, nch = 0;
+    sweep_chunks(g.nxyz, nrhs, N, nu, &C, &nch);
+    const long long nwork = (long long)nrhs * nch;
+    const ModeLaunch L = mode_launch(g.nxyz, nwork);
+    cudaError_t e = cudaSuccess;
+#define ST_SWEEP_D(NU)                                                                          \
+    if (nu == NU)                                                                               \
+        ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_sweep_down<T, NT, NU>, L.grid, L.block, 0, s, \
+                                              f, u, fc, inv, g.nxyz, pc, omega, N, C, nch,       \
+                                              nwork)));
+    ST_SWEEP_D(2) ST_SWEEP_D(3) ST_SWEEP_D(4)
+#undef ST_SWEEP_D
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spec_sweep_up(const T *ec, const T *uin, T *uout, const T *f, const T *inv,
+                                 const Grid &g, const ProlongCoefs<T> &pc, T omega, int N,
+                                 int nrhs, int nu, cudaStream_t s) {
+    if (nu < 2 || nu > 4 || N % 2 != 0) return cudaErrorNotSupported;
+    if (g.nxyz <= 0 || nrhs <= 0) return cudaSuccess;
+    int C = 0, nch = 0;
+    sweep_chunks(g.nxyz, nrhs, N, nu, &C, &nch);
+    const long long nwork = (long long)nrhs * nch;
+    const ModeLaunch L = mode_launch(g.nxyz, nwork);
+    cudaError_t e = cudaSuccess;
+#define ST_SWEEP_U(NU)                                                                          \
+    if (nu == NU)                                                                               \
+        ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_sweep_up<T, NT, NU>, L.grid, L.block, 0, s,   \
+                                              ec, uin, uout, f, inv, g.nxyz, pc, omega, N, C,    \
+                                              nch, nwork)));
+    ST_SWEEP_U(2) ST_SWEEP_U(3) ST_SWEEP_U(4)
+#undef ST_SWEEP_U
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
 #undef ST_NT_DISPATCH
 
 template cudaError_t launch_mode_inverse<double>(double *, const double *, const Grid &,
@@ -733,6 +913,12 @@ template cudaError_t launch_mode_inverse<double>(double *, const double *, const
 template cudaError_t launch_mode_inverse<float>(float *, const double *, const Grid &,
                                                 const SpecCoefs<double> &, cudaStream_t);
 #define ST_INST(T)                                                                              \
+    template cudaError_t launch_spec_sweep_down<T>(const T *, T *, T *, const T *, const Grid &, \
+                                                   const ProlongCoefs<T> &, T, int, int, int,    \
+                                                   cudaStream_t);                                \
+    template cudaError_t launch_spec_sweep_up<T>(const T *, const T *, T *, const T *,          \
+                                                 const T *, const Grid &, const ProlongCoefs<T> &, \
+                                                 T, int, int, int, cudaStream_t);                \
     template cudaError_t launch_spec_tail<T>(const T *, T *, const T *const *, int, const Grid &, \
                                              const ProlongCoefs<T> &, T, int, int, int, int,     \
                                              cudaStream_t);                                      \

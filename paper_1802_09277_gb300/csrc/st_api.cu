@@ -1364,17 +1364,36 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     bool zero = zero_init;
     const ProlongCoefs<T> pc = pack_prolong<T>(h);
     const long long nc = (long long)h->lv[l + 1].nslab * h->nrhs;
+    // nu1 = 2..4 from zero: all steps, the residual and the restriction in
+    // one sweeping pass over the level
+    bool swept = false;
+    if (zero && h->opt.nu1 >= 2 && h->opt.nu1 <= 4) {
+        const double nu = h->opt.nu1;
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.5 * E, E * nu * (2.0 * nt + 4.0));
+        const cudaError_t e = launch_spec_sweep_down<T>(f, oth, w.f[l + 1], inv, h->g, pc,
+                                                        omega, spp, h->nrhs, h->opt.nu1, h->stream);
+        if (e == cudaSuccess) {
+            std::swap(cur, oth);
+            zero = false;
+            swept = true;
+        } else {
+            if (e != cudaErrorNotSupported) CK(e);
+            cudaGetLastError();
+            ks.cancel();
+        }
+    }
     // pre-smoothing; the last step runs fused with the residual and the
     // restriction (k_spec_down), the first post-smoothing step with the
     // prolongation (k_spec_up)
-    for (int k = 0; k + 1 < h->opt.nu1; ++k) {
+    for (int k = 0; !swept && k + 1 < h->opt.nu1; ++k) {
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.0 : 3.0) * E, E * (2.0 * nt + 3.0));
         CK(launch_spec_smooth<T>(cur, oth, f, inv, h->g, nt, omega, spp, ns, zero ? 1 : 0,
                                  h->stream));
         std::swap(cur, oth);
         zero = false;
     }
-    if (h->opt.nu1 >= 1) {
+    if (swept) {
+    } else if (h->opt.nu1 >= 1) {
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * (zero ? 2.5 : 3.5) * E,
                   E * (zero ? 4.0 * nt + 4.0 : 8.0 * nt + 8.0));
         CK(launch_spec_down<T>(zero ? nullptr : cur, oth, f, w.f[l + 1], inv, lam, h->g, c, pc,
@@ -1386,7 +1405,23 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
         CK(launch_spec_res_restrict<T>(cur, f, w.f[l + 1], lam, h->g, c, pc, spp, nc, h->stream));
     }
     CKS(svcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], oth, true));
-    if (h->opt.nu2 >= 1) {
+    bool swept_up = false;
+    if (h->opt.nu2 >= 2 && h->opt.nu2 <= 4) {
+        const double nu = h->opt.nu2;
+        KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.5 * E, E * nu * (2.0 * nt + 3.0));
+        const cudaError_t e = launch_spec_sweep_up<T>(w.u[l + 1], cur, oth, f, inv, h->g, pc,
+                                                      omega, spp, h->nrhs, h->opt.nu2, h->stream);
+        if (e == cudaSuccess) {
+            std::swap(cur, oth);
+            swept_up = true;
+        } else {
+            if (e != cudaErrorNotSupported) CK(e);
+            cudaGetLastError();
+            ks.cancel();
+        }
+    }
+    if (swept_up) {
+    } else if (h->opt.nu2 >= 1) {
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.5 * E, E * (4.0 * nt + 4.0));
         CK(launch_spec_up<T>(w.u[l + 1], cur, oth, f, inv, h->g, pc, omega, spp, nc, h->stream));
         std::swap(cur, oth);
@@ -1395,7 +1430,7 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
         KScope ks(h, ST_PROF_TRANSFER, sizeof(T) * 5.0 * Ec, Ec * 4.0 * nt);
         CK(launch_prolong_add<T>(w.u[l + 1], cur, pc, h->g, nc, h->stream));
     }
-    for (int k = 1; k < h->opt.nu2; ++k) {
+    for (int k = 1; !swept_up && k < h->opt.nu2; ++k) {
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.0 * E, E * (2.0 * nt + 3.0));
         CK(launch_spec_smooth<T>(cur, oth, f, inv, h->g, nt, omega, spp, ns, 0, h->stream));
         std::swap(cur, oth);

@@ -171,6 +171,19 @@ template <typename T>
 cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nlev,
                              const Grid &g, const ProlongCoefs<T> &pc, T omega, int n0, int nrhs,
                              int nu1, int nu2, cudaStream_t s);
+// nu = 2..4 smoothing steps of a level in one pass (one thread per mode and
+// chunk of slabs, see kernels_modes.cu): down = from u = 0, nu steps, the
+// residual and its restriction into fc; up = prolongation of the coarse
+// correction ec and nu steps, uin -> uout (out of place).  N = slabs per
+// problem (even).  cudaErrorNotSupported outside nu = 2..4.
+template <typename T>
+cudaError_t launch_spec_sweep_down(const T *f, T *u, T *fc, const T *inv, const Grid &g,
+                                   const ProlongCoefs<T> &pc, T omega, int N, int nrhs, int nu,
+                                   cudaStream_t s);
+template <typename T>
+cudaError_t launch_spec_sweep_up(const T *ec, const T *uin, T *uout, const T *f, const T *inv,
+                                 const Grid &g, const ProlongCoefs<T> &pc, T omega, int N,
+                                 int nrhs, int nu, cudaStream_t s);
 // uout = (1 - omega) uin + omega A^{-1} (f + e_0 uin_prev) (uin_zero: uin = 0)
 template <typename T>
 cudaError_t launch_spec_smooth(const T *uin, T *uout, const T *f, const T *inv, const Grid &g,
