@@ -62,10 +62,11 @@ EXTRA = {"cube48_x16": ["square128_p3"]}
 ORACLE_SAMPLE = {"square64": ((64, 64), 8), "square128_p3": ((16, 16), 8),
                  "cube48_x16": ((8, 8, 8), 8), "interval16": ((16,), 8)}
 METRIC = "space-time DoFs/s to rel. residual 1e-8, mixed vs FP64 plain; serve p50/p99"
-# smoothing steps of every V-cycle in the bench (V(2,2): measured faster than
-# V(1,1) on cube48_x16 and square128_p3 -- fewer Krylov steps outweigh the
-# extra smoothing); the library default is V(1,1)
-NU = (2, 2)
+# smoothing steps of every V-cycle in the bench: V(4,4), measured best or
+# close to it on cube48_x16, square128_p3 and square64 (the sweeping level
+# kernels make every level one pass whatever nu, so more smoothing costs
+# arithmetic only and saves Krylov steps); the library default is V(1,1)
+NU = (4, 4)
 UNIT = "DoFs/s"
 L2_FLUSH_BYTES = 256 << 20
 

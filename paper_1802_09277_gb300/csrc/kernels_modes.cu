@@ -869,7 +869,7 @@ template <typename T>
 cudaError_t launch_spec_sweep_down(const T *f, T *u, T *fc, const T *inv, const Grid &g,
                                    const ProlongCoefs<T> &pc, T omega, int N, int nrhs, int nu,
                                    cudaStream_t s) {
-    if (nu < 2 || nu > 4 || N % 2 != 0) return cudaErrorNotSupported;
+    if (nu < 2 || nu > 6 || N % 2 != 0) return cudaErrorNotSupported;
     if (g.nxyz <= 0 || nrhs <= 0) return cudaSuccess;
     int C = 0, nch = 0;
     sweep_chunks(g.nxyz, nrhs, N, nu, &C, &nch);
@@ -881,7 +881,7 @@ cudaError_t launch_spec_sweep_down(const T *f, T *u, T *fc, const T *inv, const 
         ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_sweep_down<T, NT, NU>, L.grid, L.block, 0, s, \
                                               f, u, fc, inv, g.nxyz, pc, omega, N, C, nch,       \
                                               nwork)));
-    ST_SWEEP_D(2) ST_SWEEP_D(3) ST_SWEEP_D(4)
+    ST_SWEEP_D(2) ST_SWEEP_D(3) ST_SWEEP_D(4) ST_SWEEP_D(5) ST_SWEEP_D(6)
 #undef ST_SWEEP_D
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -890,7 +890,7 @@ template <typename T>
 cudaError_t launch_spec_sweep_up(const T *ec, const T *uin, T *uout, const T *f, const T *inv,
                                  const Grid &g, const ProlongCoefs<T> &pc, T omega, int N,
                                  int nrhs, int nu, cudaStream_t s) {
-    if (nu < 2 || nu > 4 || N % 2 != 0) return cudaErrorNotSupported;
+    if (nu < 2 || nu > 6 || N % 2 != 0) return cudaErrorNotSupported;
     if (g.nxyz <= 0 || nrhs <= 0) return cudaSuccess;
     int C = 0, nch = 0;
     sweep_chunks(g.nxyz, nrhs, N, nu, &C, &nch);
@@ -902,7 +902,7 @@ cudaError_t launch_spec_sweep_up(const T *ec, const T *uin, T *uout, const T *f,
         ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_sweep_up<T, NT, NU>, L.grid, L.block, 0, s,   \
                                               ec, uin, uout, f, inv, g.nxyz, pc, omega, N, C,    \
                                               nch, nwork)));
-    ST_SWEEP_U(2) ST_SWEEP_U(3) ST_SWEEP_U(4)
+    ST_SWEEP_U(2) ST_SWEEP_U(3) ST_SWEEP_U(4) ST_SWEEP_U(5) ST_SWEEP_U(6)
 #undef ST_SWEEP_U
     return e != cudaSuccess ? e : cudaGetLastError();
 }

@@ -1367,7 +1367,7 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     // nu1 = 2..4 from zero: all steps, the residual and the restriction in
     // one sweeping pass over the level
     bool swept = false;
-    if (zero && h->opt.nu1 >= 2 && h->opt.nu1 <= 4) {
+    if (zero && h->opt.nu1 >= 2 && h->opt.nu1 <= 6) {
         const double nu = h->opt.nu1;
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.5 * E, E * nu * (2.0 * nt + 4.0));
         const cudaError_t e = launch_spec_sweep_down<T>(f, oth, w.f[l + 1], inv, h->g, pc,
@@ -1406,7 +1406,7 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     }
     CKS(svcycle<T>(h, l + 1, w.u[l + 1], w.f[l + 1], oth, true));
     bool swept_up = false;
-    if (h->opt.nu2 >= 2 && h->opt.nu2 <= 4) {
+    if (h->opt.nu2 >= 2 && h->opt.nu2 <= 6) {
         const double nu = h->opt.nu2;
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 3.5 * E, E * nu * (2.0 * nt + 3.0));
         const cudaError_t e = launch_spec_sweep_up<T>(w.u[l + 1], cur, oth, f, inv, h->g, pc,

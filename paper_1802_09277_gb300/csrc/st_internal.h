@@ -171,11 +171,11 @@ template <typename T>
 cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nlev,
                              const Grid &g, const ProlongCoefs<T> &pc, T omega, int n0, int nrhs,
                              int nu1, int nu2, cudaStream_t s);
-// nu = 2..4 smoothing steps of a level in one pass (one thread per mode and
+// nu = 2..6 smoothing steps of a level in one pass (one thread per mode and
 // chunk of slabs, see kernels_modes.cu): down = from u = 0, nu steps, the
 // residual and its restriction into fc; up = prolongation of the coarse
 // correction ec and nu steps, uin -> uout (out of place).  N = slabs per
-// problem (even).  cudaErrorNotSupported outside nu = 2..4.
+// problem (even).  cudaErrorNotSupported outside nu = 2..6.
 template <typename T>
 cudaError_t launch_spec_sweep_down(const T *f, T *u, T *fc, const T *inv, const Grid &g,
                                    const ProlongCoefs<T> &pc, T omega, int N, int nrhs, int nu,

@@ -131,7 +131,7 @@ def test_vcycle_parity(st, basis, d, spans, p, N, ne):
     s.close()
 
 
-@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 2), (0, 1), (1, 0), (2, 1)])
+@pytest.mark.parametrize("nu1,nu2", [(1, 1), (2, 2), (0, 1), (1, 0), (2, 1), (3, 3), (4, 2), (6, 5)])
 @pytest.mark.parametrize("d,spans,p,N,ne", [(1, (16,), 2, 64, 2), (2, (6, 5), 2, 32, 2),
                                             (2, (7, 6), 3, 12, 2)])
 def test_vcycle_levels_and_tail_parity(st, nu1, nu2, d, spans, p, N, ne):
