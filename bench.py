@@ -663,10 +663,12 @@ def make_len(d, spans, p, N, ne):
 # over the class's launches in one solve, ncu with its default cache flush
 # between launches) for (workload, precision, basis, outer, kernel class);
 # the capture is summarised in the profiles/ file named beside it.  An entry
-# is removed whenever a kernel of the class changes.
+# is removed whenever a kernel of the class changes.  The cube48_x16 entry was
+# captured on one of its 16 right-hand sides and scaled by 16 (traffic grows
+# with the dofs).
 TRAFFIC = {
-    ("square64", "mixed_tf32", "spectral", "ir", "spec"):
-        (1.359e7, "profiles/traffic_square64_mixed_tf32_spectral_ir.md"),
+    ("cube48_x16", "mixed_tf32", "spectral", "ir", "stencil_df"):
+        (16 * (907353856 + 426703104), "profiles/traffic_cube48_stencil_dfloat_and_sweep.md"),
 }
 
 
@@ -691,12 +693,12 @@ def roofline_entry(r):
         base.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                     peak_note="FP32 CUDA-core FMA rate: unit counts x max SM clock")
         return base
-    if dom == "stencil_df":  # double-float on the FP32 pipe: 15 FP32 instructions per 2-flop FMA
-        peak = 152 * 128 * clk_max * 2 / 15 / 1e12
+    if dom == "stencil_df":  # double-float on the FP32 pipe: 12 FP32 instructions per 2-flop term
+        peak = 152 * 128 * clk_max * 2 / 12 / 1e12
         ach = pd["flops"] / secs / 1e12
         base.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                    peak_note="FP32 lane rate x max SM clock x 2 flops / 15 instructions per "
-                              "double-float multiply-add")
+                    peak_note="FP32 lane rate (152 SMs x 128 lanes) x max SM clock x 2 flops / "
+                              "12 FP32 instructions per compensated (Dot2) double-float term")
         return base
     if dom in ("stencil64", "gemm64"):  # FP64 pipe: GB300's 1.25 TFLOP/s dense FP64
         peak = 1.25
