@@ -7,7 +7,7 @@ elements (56 623 104 space-time dofs per right-hand side), theta = 1,
 solved together, zero initial guess, to ||f - L u|| <= 1e-8 ||f|| for every
 right-hand side.  Headline method: mixed precision -- iterative refinement
 with an FP64-accurate residual and FP64 update around an FP32 FGMRES(10),
-right-preconditioned by one time-multigrid V(2,2) cycle (damped block
+right-preconditioned by one time-multigrid V(4,4) cycle (damped block
 Jacobi, omega = 1/2, slab inverses by the real Schur time factors and fast
 diagonalisation in space, V-cycle in the spatial eigenbasis); the spatial
 transforms at the refinement boundary run as split TF32 on the tensor cores
@@ -432,20 +432,27 @@ def gpu_arm(args, rank, world):
     u_host = torch.empty_like(f_host).pin_memory()
     f_dev = torch.empty_like(f)
     u_dev = torch.zeros_like(f)
-    e2e_t = []
+    e2e_t, e2e_parts = [], []
     for k in range(args.warmup + max(2, args.steps // 2)):
         flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
         f_dev.copy_(f_host, non_blocking=True)
+        ev[1].record(stream)
         sm.solve(f_dev, u_dev, tol=tol)
+        ev[2].record(stream)
         u_host.copy_(u_dev, non_blocking=True)
-        e1.record(stream)
-        e1.synchronize()
+        ev[3].record(stream)
+        ev[3].synchronize()
         if k >= args.warmup:
-            e2e_t.append(e0.elapsed_time(e1))
+            e2e_t.append(ev[0].elapsed_time(ev[3]))
+            e2e_parts.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                              ev[2].elapsed_time(ev[3])])
     e2e_ms = sum(e2e_t) / len(e2e_t)
+    e2e_breakdown = {"h2d_ms": sum(p[0] for p in e2e_parts) / len(e2e_parts),
+                     "solve_ms": sum(p[1] for p in e2e_parts) / len(e2e_parts),
+                     "d2h_ms": sum(p[2] for p in e2e_parts) / len(e2e_parts),
+                     "pinned": bool(f_host.is_pinned() and u_host.is_pinned())}
     del f_host, u_host, f_dev, u_dev
 
     # --- the other variants on the same workload (fewer steps, no profiling) ---
@@ -525,7 +532,8 @@ def gpu_arm(args, rank, world):
         "ndofs": ndofs, "ms_mixed": ms, "ms_mixed_max": ms_max, "ms_prof": ms_prof,
         "iters_mixed": i_mixed[-1]["iterations"], "res_mixed": i_mixed[-1]["rel_residual"],
         "refin_mixed": i_mixed[-1].get("refinements", 0), "fp64_plain": v64,
-        "rel_diff_mixed_vs_fp64": rel_diff, "e2e_ms": e2e_ms, "bytes_h2d": ndofs * 8,
+        "rel_diff_mixed_vs_fp64": rel_diff, "e2e_ms": e2e_ms, "e2e_breakdown": e2e_breakdown,
+        "bytes_h2d": ndofs * 8,
         "bytes_d2h": ndofs * 8, "prof": prof, "dominant": dom,
         "per_launch_ms": per_launch_ms, "launches": launches // max(args.steps, 1),
         "launches_total": launches, "clocks": clk, "peaks": peaks, "peak_src": peak_src,
@@ -970,7 +978,8 @@ def main():
         "cpu_baseline": cpu,
         "serve": serve,
         "e2e": {"value": ndofs * world / (r["e2e_ms"] / 1e3), "unit": UNIT,
-                "h2d_bytes_per_step": r["bytes_h2d"], "d2h_bytes_per_step": r["bytes_d2h"]},
+                "h2d_bytes_per_step": r["bytes_h2d"], "d2h_bytes_per_step": r["bytes_d2h"],
+                "breakdown": r["e2e_breakdown"]},
         "gpu_launches": r["launches"],
         "transform_autotune": [{"axis": a, "choice": ("cuda_cores" if c == 0 else
                                                        "tensor_cores_%d_cta_per_sm" % c),
