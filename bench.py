@@ -610,8 +610,12 @@ def extra_workload(args, name):
 
 
 def serve_arm(args):
-    """Serving workload: Poisson arrivals of solve requests of mixed
-    configurations through st_serve (continuous batching)."""
+    """Serving workload: arrivals of solve requests of mixed configurations
+    through st_serve (continuous batching).  Three runs on one server: the
+    Poisson arrivals with an empty setup cache (the headline p50 / p99), the
+    same arrivals again (setups cached), and a burst with every request
+    submitted at once (a deep queue, where batches of equal configurations
+    form)."""
     import threading
     import numpy as np
     from paper_1802_09277_gb300 import inputs, st
@@ -626,38 +630,50 @@ def serve_arm(args):
     srv = st.Server(workers=args.serve_workers, max_batch=8, precision=args.precision,
                     basis="spectral", outer="ir", ne_per_slab=ne, gmres_restart=20, max_it=300,
                     nu1=NU[0], nu2=NU[1])
-    tickets = [None] * nreq
-    t0 = time.perf_counter()
 
-    def submitter():
-        for i, (sp, p, N, c) in enumerate(reqs):
-            dt = t0 + arrivals[i] - time.perf_counter()
-            if dt > 0:
-                time.sleep(dt)
-            tickets[i] = srv.submit(2, p, (sp, sp), N, c, tol=1e-8, coeffs=True)
+    def run(times):
+        tickets = [None] * nreq
+        t0 = time.perf_counter()
 
-    th = threading.Thread(target=submitter)
-    th.start()
-    lat, dofs, worst, batches, bad = [], 0, 0.0, [], 0
-    for i in range(nreq):
-        while tickets[i] is None:
-            time.sleep(1e-4)
-        res, u = srv.wait(tickets[i], timeout=600.0)
-        if res["status"] != 0:
-            bad += 1
-        lat.append(res["latency_seconds"])
-        dofs += res["n_dofs"]
-        worst = max(worst, res["rel_residual"])
-        batches.append(res["batch_size"])
-    makespan = time.perf_counter() - t0
-    th.join()
+        def submitter():
+            for i, (sp, p, N, c) in enumerate(reqs):
+                dt = t0 + times[i] - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[i] = srv.submit(2, p, (sp, sp), N, c, tol=1e-8, coeffs=True)
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat, dofs, worst, batches, bad = [], 0, 0.0, [], 0
+        for i in range(nreq):
+            while tickets[i] is None:
+                time.sleep(1e-4)
+            res, u = srv.wait(tickets[i], timeout=600.0)
+            if res["status"] != 0:
+                bad += 1
+            lat.append(res["latency_seconds"])
+            dofs += res["n_dofs"]
+            worst = max(worst, res["rel_residual"])
+            batches.append(res["batch_size"])
+        makespan = time.perf_counter() - t0
+        th.join()
+        lat = np.sort(np.array(lat))
+        return {"p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)),
+                "throughput_dofs_per_s": dofs / makespan, "makespan_s": makespan,
+                "total_dofs": int(dofs), "max_rel_residual": worst, "failed": bad,
+                "mean_batch": float(np.mean(batches))}
+
+    first = run(arrivals)
+    again = run(arrivals)
+    burst = run(np.zeros(nreq))
     srv.stop()
-    lat = np.sort(np.array(lat))
-    return {"requests": nreq, "arrival_rate_per_s": rate, "workers": args.serve_workers,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "throughput_dofs_per_s": dofs / makespan, "makespan_s": makespan, "total_dofs": int(dofs),
-            "max_rel_residual": worst, "failed": bad, "mean_batch": float(np.mean(batches)),
-            "precision": args.precision, "tol": 1e-8}
+    out = {"requests": nreq, "arrival_rate_per_s": rate, "workers": args.serve_workers,
+           "precision": args.precision, "tol": 1e-8, "setup_cache": "empty at start"}
+    out.update(first)
+    out["repeat_setups_cached"] = again
+    out["burst_all_at_once"] = burst
+    return out
 
 
 def make_len(d, spans, p, N, ne):

@@ -359,14 +359,238 @@ static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// z-marching variant (3D): a CTA owns a 16 x 8 column of (x, y) points of one
+// slab and walks its z range slice by slice.  For every slice and time plane
+// the slice (plus its x / y halo) is staged, the x-pass and the y-pass run
+// once, and each thread keeps the y-pass results of its own point for the
+// last 2p + 1 slices in a private ring in shared memory; when a slice
+// completes the window of an output slice, the thread runs the z-pass and
+// the time combination for that point and writes it.  Compared with the
+// tiled kernel, no x- or y-pass work is repeated on a z halo.  Each thread
+// reads and writes only its own ring entries, so the ring needs no barrier.
+// ---------------------------------------------------------------------------
+template <typename C, int P, int NT>
+struct ZmSmem {
+    static constexpr int TX = 16, TY = 8, W = 2 * P + 1;
+    static constexpr int SX = TX + 2 * P, SY = TY + 2 * P;
+    static constexpr int threads = TX * TY;
+    // S, A, B, x / y bands, ring (NT + 1 planes x W slices x {AA, SS} x threads)
+    static constexpr int nfix = SY * SX + 2 * SY * TX + 2 * W * (TX + TY) +
+                                (NT + 1) * W * 2 * threads;
+    static size_t bytes(int zc) { return sizeof(C) * ((size_t)nfix + 2 * (size_t)zc * W); }
+};
+
+template <typename T, typename C, int P, int NT>
+__global__ void __launch_bounds__(128)
+    k_stencil_zm(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out,
+                 Bands<T> bands, Grid g, const __grid_constant__ TimeCoefs<C> tc,
+                 int slabs_per_prob, int slab0, int tiles_x, int zc_len) {
+    using SM = ZmSmem<C, P, NT>;
+    constexpr int TX = SM::TX, TY = SM::TY, W = SM::W, SX = SM::SX, SY = SM::SY;
+    constexpr int NTH = SM::threads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *S = reinterpret_cast<C *>(smem_raw);
+    C *A = S + SY * SX;
+    C *B = A + SY * TX;
+    C *bMx = B + SY * TX;
+    C *bKx = bMx + TX * W;
+    C *bMy = bKx + TX * W;
+    C *bKy = bMy + TY * W;
+    C *ring = bKy + TY * W;                          // [NT + 1][W][2][NTH]
+    C *bMz = ring + (NT + 1) * W * 2 * NTH;           // [zc_len][W]
+    C *bKz = bMz + zc_len * W;
+
+    const int tid = threadIdx.x;
+    const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+    const int slab = slab0 + blockIdx.y;
+    const int zb = blockIdx.z * zc_len;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int ze = (zb + zc_len < nz) ? zb + zc_len : nz;
+    const long long nxyz = g.nxyz;
+
+    for (int e = tid; e < TX * W; e += NTH) {
+        const int gx = x0 + e / W;
+        bMx[e] = (gx < nx) ? to_c<C>(bands.M[0][(long long)gx * W + e % W]) : C(0);
+        bKx[e] = (gx < nx) ? to_c<C>(bands.K[0][(long long)gx * W + e % W]) : C(0);
+    }
+    for (int e = tid; e < TY * W; e += NTH) {
+        const int gy = y0 + e / W;
+        bMy[e] = (gy < ny) ? to_c<C>(bands.M[1][(long long)gy * W + e % W]) : C(0);
+        bKy[e] = (gy < ny) ? to_c<C>(bands.K[1][(long long)gy * W + e % W]) : C(0);
+    }
+    for (int e = tid; e < (ze - zb) * W; e += NTH) {
+        const long long gz = zb + e / W;
+        bMz[e] = to_c<C>(bands.M[2][gz * W + e % W]);
+        bKz[e] = to_c<C>(bands.K[2][gz * W + e % W]);
+    }
+
+    const int tx = tid % TX, ty = tid / TX;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const T *uslab = u + (long long)slab * NT * nxyz;
+    const bool first = (slab % slabs_per_prob) == 0;
+    const bool has_prev = (tc.mode != MODE_MASS) && (!first || tc.halo != nullptr);
+    const T *prev = !first ? uslab - nxyz
+                    : tc.halo ? static_cast<const T *>(tc.halo) + (long long)(slab / slabs_per_prob) * nxyz
+                              : nullptr;
+    const int j0 = has_prev ? -1 : 0;
+
+    for (int zs = zb - P; zs < ze + P; ++zs) {
+        const int slot = (zs - zb + P) % W;
+        const bool zin = zs >= 0 && zs < nz;
+        for (int jj = j0; jj < NT; ++jj) {
+            const T *plane = (jj < 0) ? prev : uslab + (long long)jj * nxyz;
+            // S is free (the previous x-pass is behind the last barrier)
+            for (int e = tid; e < SY * SX; e += NTH) {
+                const int sx = e % SX, sy = e / SX;
+                const int ggx = x0 + sx - P, ggy = y0 + sy - P;
+                C v = C(0);
+                if (zin && ggx >= 0 && ggx < nx && ggy >= 0 && ggy < ny)
+                    v = to_c<C>(plane[((long long)zs * ny + ggy) * nx + ggx]);
+                S[e] = v;
+            }
+            __syncthreads();  // S staged; the previous y-pass is done with A, B
+            const bool mass_only = jj < 0;
+            for (int e = tid; e < SY * TX; e += NTH) {
+                const int ex = e % TX, row = e / TX;
+                const C *srow = S + row * SX + ex;
+                Acc<C> a, b;
+                if (mass_only) {
+#pragma unroll
+                    for (int o = 0; o < W; ++o) a.add(bMx[ex * W + o], srow[o]);
+                } else {
+#pragma unroll
+                    for (int o = 0; o < W; ++o) {
+                        const C sv = srow[o];
+                        a.add(bMx[ex * W + o], sv);
+                        b.add(bKx[ex * W + o], sv);
+                    }
+                }
+                A[e] = a.get();
+                B[e] = b.get();
+            }
+            __syncthreads();  // A, B complete
+            {
+                Acc<C> aa, ss;
+                if (mass_only) {
+#pragma unroll
+                    for (int o = 0; o < W; ++o) aa.add(bMy[ty * W + o], A[(ty + o) * TX + tx]);
+                } else {
+#pragma unroll
+                    for (int o = 0; o < W; ++o) {
+                        const int idx = (ty + o) * TX + tx;
+                        const C av = A[idx], bv = B[idx];
+                        const C my = bMy[ty * W + o], ky = bKy[ty * W + o];
+                        aa.add(my, av);
+                        ss.add(ky, av);
+                        ss.add(my, bv);
+                    }
+                }
+                C *rp = ring + ((size_t)((jj + 1) * W + slot) * 2) * NTH + tid;
+                rp[0] = aa.get();
+                rp[NTH] = ss.get();
+            }
+        }
+        // output slice zc = zs - P: its window zc - P .. zc + P is in the ring
+        const int zc = zs - P;
+        if (zc < zb || zc >= ze) continue;
+        const int zr = zc - zb;
+        Acc<C> acc[NT];
+        C mprev = C(0);
+        for (int jj = j0; jj < NT; ++jj) {
+            Acc<C> am, ak;
+#pragma unroll
+            for (int o = 0; o < W; ++o) {
+                const int sl = (zc - P + o - zb + P) % W;  // slot of slice zc - P + o
+                const C *rp = ring + ((size_t)((jj + 1) * W + sl) * 2) * NTH + tid;
+                const C mz = bMz[zr * W + o], kz = bKz[zr * W + o];
+                am.add(mz, rp[0]);
+                if (jj >= 0) {
+                    ak.add(kz, rp[0]);
+                    ak.add(mz, rp[NTH]);
+                }
+            }
+            const C m = am.get();
+            if (jj < 0) {
+                mprev = m;
+                continue;
+            }
+            const C k = ak.get();
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                acc[i].add(tc.CK[i * NTMAX + jj], m);
+                acc[i].add(tc.CM[i * NTMAX + jj], k);
+            }
+        }
+        if (gx >= nx || gy >= ny) continue;
+        const long long base = (long long)slab * NT * nxyz + ((long long)zc * ny + gy) * nx + gx;
+        C r[NT];
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            C v = acc[i].get();
+            if (tc.mode == MODE_RES) {
+                v = to_c<C>(f[base + (long long)i * nxyz]) - v;
+                if (i == 0) v += mprev;
+            } else if (tc.mode == MODE_APPLY) {
+                if (i == 0) v -= mprev;
+            }
+            r[i] = v;
+        }
+        if (tc.fuse_y) {
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                C w = C(0);
+#pragma unroll
+                for (int j = 0; j < NT; ++j) w = madd(w, tc.Y[i * NTMAX + j], r[j]);
+                out[base + (long long)i * nxyz] = from_c<T>(w);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NT; ++i) out[base + (long long)i * nxyz] = from_c<T>(r[i]);
+        }
+    }
+}
+
+// cudaErrorNotSupported when the shared memory does not fit (the tiled
+// kernel is used then)
+template <typename T, typename C, int P, int NT>
+static cudaError_t launch_stencil_zm_t(const T *u, const T *f, T *out, const Bands<T> &bands,
+                                       const Grid &g, const TimeCoefs<C> &tc, int slabs_per_prob,
+                                       int slab0, int nslabs, cudaStream_t s) {
+    using SM = ZmSmem<C, P, NT>;
+    if (nslabs <= 0) return cudaSuccess;
+    if (nslabs > 65535) return cudaErrorInvalidValue;
+    const int zc = g.nz <= 64 ? g.nz : 32;  // z slices per CTA
+    const size_t bytes = SM::bytes(zc);
+    if (bytes > 200 * 1024) return cudaErrorNotSupported;
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e =
+            smem_attr_once((const void *)k_stencil_zm<T, C, P, NT>, (int)(200 * 1024), attr);
+        if (e != cudaSuccess) return e;
+    }
+    const int tx = (g.nx + SM::TX - 1) / SM::TX;
+    const int ty = (g.ny + SM::TY - 1) / SM::TY;
+    dim3 grid((unsigned)(tx * ty), (unsigned)nslabs, (unsigned)((g.nz + zc - 1) / zc));
+    k_stencil_zm<T, C, P, NT><<<grid, SM::threads, bytes, s>>>(u, f, out, bands, g, tc,
+                                                               slabs_per_prob, slab0, tx, zc);
+    return cudaGetLastError();
+}
+
 template <typename T, typename C>
 cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands, const Grid &g,
                            const TimeCoefs<C> &tc, int slabs_per_prob, int slab0, int nslabs,
                            cudaStream_t s) {
 #define ST_NT(PP, DD, N)                                                                        \
-    if (tc.nt == N)                                                                             \
+    if (tc.nt == N) {                                                                           \
+        if constexpr (DD == 3) {                                                                \
+            const cudaError_t ez = launch_stencil_zm_t<T, C, PP, N>(                            \
+                u, f, out, bands, g, tc, slabs_per_prob, slab0, nslabs, s);                     \
+            if (ez != cudaErrorNotSupported) return ez;                                         \
+        }                                                                                       \
         return launch_stencil_t<T, C, PP, DD, N>(u, f, out, bands, g, tc, slabs_per_prob, slab0, \
-                                                 nslabs, s);
+                                                 nslabs, s);                                    \
+    }
 #define ST_CASE(PP, DD)                                                                         \
     if (g.p == PP && g.dim == DD) {                                                             \
         if constexpr (std::is_same<C, dfloat>::value) {                                         \
