@@ -369,6 +369,9 @@ static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<
 // the time combination for that point and writes it.  Compared with the
 // tiled kernel, no x- or y-pass work is repeated on a z halo.  Each thread
 // reads and writes only its own ring entries, so the ring needs no barrier.
+// Used for the double-float residual at p = 3 (48^3, p = 3: 59 -> 47 ms per
+// solve); at p = 2 the ring's shared memory lowers the occupancy more than
+// the saved halo work gains (114 -> 118 ms), so the tiled kernel stays.
 // ---------------------------------------------------------------------------
 template <typename C, int P, int NT>
 struct ZmSmem {
@@ -583,7 +586,7 @@ cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands
                            cudaStream_t s) {
 #define ST_NT(PP, DD, N)                                                                        \
     if (tc.nt == N) {                                                                           \
-        if constexpr (DD == 3) {                                                                \
+        if constexpr (DD == 3 && PP >= 3) {                                                     \
             const cudaError_t ez = launch_stencil_zm_t<T, C, PP, N>(                            \
                 u, f, out, bands, g, tc, slabs_per_prob, slab0, nslabs, s);                     \
             if (ez != cudaErrorNotSupported) return ez;                                         \
