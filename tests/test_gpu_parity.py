@@ -496,9 +496,10 @@ def test_solve_history(st, prec, outer, basis):
 
 @pytest.mark.parametrize("spans,p", [((18, 5, 67), 2), ((9, 4, 70), 3)])
 def test_refinement_residual_3d_z_chunks(st, spans, p):
-    """The FP64-accurate refinement residual of the 3D mixed solve marches
-    along z in chunks of 32 planes when nz > 64 (ragged last chunk, ragged x
-    and y tiles): the refined solution matches the oracle's direct one."""
+    """The FP64-accurate refinement residual of the 3D mixed solve with more
+    than 64 z planes: at p = 3 the z-marching kernel in chunks of 32 planes
+    (ragged last chunk), at p = 2 the tiled kernel (ragged tiles in every
+    axis); the refined solution matches the oracle's direct one."""
     d, N, ne = 3, 2, 2
     pr = A.Problem(d, spans, p, ne, N, theta=1.0)
     c = inputs.normal_coeffs(91, pr.ndofs)
