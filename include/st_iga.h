@@ -323,6 +323,30 @@ int st_vcycle(st_handle h, double *u, const double *f);
 int st_solve(st_handle h, const double *rhs, double tol, double *u,
              int use_guess, st_solve_info *info);
 
+/* st_solve on HOST buffers for a stream of nbatch batches of the handle's
+ * systems (each batch: nrhs right-hand sides, st_solve's layout; batch k at
+ * offset k x n_dofs doubles).  Batch k solves on the handle's stream while
+ * batch k+1's right-hand sides are copied to the device and batch k-1's
+ * solutions back to the host, each on a stream of its own, so the transfers
+ * hide behind the solves but for the first copy in and the last copy out.
+ *   rhs  : host, nbatch x n_dofs doubles, not modified
+ *   u    : host, nbatch x n_dofs doubles: the solutions (output); the initial
+ *          guesses when use_guess != 0 (else zero guesses)
+ *   info : may be NULL; iterations, refinements and rel_residual are the
+ *          maxima over the batches, seconds the wall time of the whole call
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister) lets the copies
+ * overlap the solves; pageable memory works, each copy then blocks the host.
+ * On first use allocates two device staging slots per vector (4 x n_dofs
+ * doubles, counted against hbm_budget, kept until st_destroy) and two copy
+ * streams.  Returns after every copy has completed.  Errors: those of
+ * st_solve; INVALID_ARG (nbatch < 1, null, aliased or device pointers);
+ * OVER_BUDGET / OOM for the staging slots.  A batch that fails (e.g.
+ * ST_ERR_NO_CONVERGENCE) ends the call: the solutions of the batches before
+ * it are in u, its own and the later ones are not written.  st_solve_history
+ * then describes the last batch solved. */
+int st_solve_host(st_handle h, int nbatch, const double *rhs, double tol, double *u,
+                  int use_guess, st_solve_info *info);
+
 /* Residual history of the last st_solve on the handle: the FP64 relative
  * residual ||f - L u||_2 / ||f||_2 (max over the right-hand sides) as the
  * solver recomputes it -- at the start of every FGMRES cycle, every
@@ -429,9 +453,14 @@ int st_serve_start(st_server *out, const st_server_opts *o);
 /* Queue a request (its rhs is copied before returning); *ticket identifies it.
  * Errors: INVALID_ARG (bad sizes), UNSUPPORTED. */
 int st_serve_submit(st_server s, const st_request *req, uint64_t *ticket);
-/* Let the workers of a server started with start_paused = 1 take requests
- * (no effect otherwise).  Errors: INVALID_ARG (null server). */
+/* Let the workers take requests again after start_paused = 1 or
+ * st_serve_pause (no effect otherwise).  Errors: INVALID_ARG (null server). */
 int st_serve_resume(st_server s);
+/* Stop the workers from taking further requests until st_serve_resume:
+ * submitted requests queue (so batches of equal configurations can form
+ * from the whole queue); batches already taken run to the end.
+ * Errors: INVALID_ARG (null server). */
+int st_serve_pause(st_server s);
 /* Withdraw a request that no worker has taken yet: its result becomes ready
  * with status ST_ERR_CANCELLED and no solution.  Returns ST_OK when it was
  * withdrawn, ST_ERR_NOT_READY when a worker is already solving it (it then

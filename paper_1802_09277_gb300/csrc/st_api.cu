@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -199,7 +200,12 @@ struct st_handle_s {
     double *r64 = nullptr;
     float *rhs32 = nullptr, *e32 = nullptr;
     int krylov32_m = 0;
-    double *partial = nullptr, *dots = nullptr;
+    double *partial = nullptr;
+    // page-locked, mapped host buffer the final reduction of the dot products
+    // writes into directly: reading a Krylov step's dots then takes no copy
+    // engine, so it never waits behind a large transfer on another stream
+    double *dots_host = nullptr, *dots_host_dev = nullptr;
+    size_t dots_host_cap = 0;
     int nblk_dot = 0;
     int krylov_m = 0;
     // residual history of the last st_solve: (iterations so far, max over
@@ -207,6 +213,12 @@ struct st_handle_s {
     // iteration or refinement step (st_solve_history)
     std::vector<std::pair<int, double>> hist;
     bool record_hist = false;  // set while the outer iteration runs
+    // st_solve_host: two device staging slots per vector (allocated on first
+    // use), the copy-in and copy-out streams, and per slot the events "copied
+    // in", "solved" and "copied out"
+    double *hs_f[2] = {nullptr, nullptr}, *hs_u[2] = {nullptr, nullptr};
+    cudaStream_t cp_in = nullptr, cp_out = nullptr;
+    cudaEvent_t hs_in[2] = {}, hs_solved[2] = {}, hs_out[2] = {};
 };
 
 namespace {
@@ -1584,22 +1596,59 @@ int run_graphed(st_handle h, const void *in, void *out, Fn fn) {
     return ST_OK;
 }
 
+// Small page-locked, mapped host blocks, kept for reuse by later handles
+// instead of being freed (cudaFreeHost may wait for the whole device, which
+// would stall every other stream of a serving process)
+std::mutex g_mapped_mu;
+std::multimap<size_t, void *> g_mapped_free;  // capacity in bytes -> block
+
+void mapped_put(void *p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(g_mapped_mu);
+    g_mapped_free.emplace(bytes, p);
+}
+
+// the mapped host buffer for count reduced values (grown on demand; the
+// stream is idle whenever this runs, every reader synchronises it first)
+int host_dots(st_handle h, size_t count) {
+    if (count <= h->dots_host_cap) return ST_OK;
+    size_t bytes = 4096;
+    while (bytes < count * sizeof(double)) bytes <<= 1;
+    mapped_put(h->dots_host, h->dots_host_cap * sizeof(double));
+    h->dots_host = h->dots_host_dev = nullptr;
+    h->dots_host_cap = 0;
+    void *p = nullptr, *pd = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mapped_mu);
+        auto it = g_mapped_free.lower_bound(bytes);
+        if (it != g_mapped_free.end()) {
+            bytes = it->first;
+            p = it->second;
+            g_mapped_free.erase(it);
+        }
+    }
+    if (!p) CK(cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+    h->dots_host = (double *)p;
+    h->dots_host_cap = bytes / sizeof(double);
+    CK(cudaHostGetDevicePointer(&pd, p, 0));
+    h->dots_host_dev = (double *)pd;
+    return ST_OK;
+}
+
 // per-rhs dots of vecs[0..nv) with w -> host out[v*nrhs + r] (FP64 sums)
 template <typename T>
 int dots(st_handle h, int nv, const T *const *vecs, const T *w, std::vector<double> &out) {
-    out.assign((size_t)nv * h->nrhs, 0.0);
+    const size_t cnt_all = (size_t)nv * h->nrhs;
+    CKS(host_dots(h, cnt_all));
     for (int v0 = 0; v0 < nv; v0 += MAXV) {
         const int cnt = std::min(MAXV, nv - v0);
-        {
-            KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 1.0) * h->len * h->nrhs,
-                      2.0 * cnt * h->len * h->nrhs);
-            CK(launch_multidot<T>(cnt, vecs + v0, w, h->nrhs, h->len, h->partial, h->nblk_dot,
-                                  h->dots, h->stream));
-        }
-        CK(cudaMemcpyAsync(out.data() + (size_t)v0 * h->nrhs, h->dots,
-                           sizeof(double) * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
+        KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 1.0) * h->len * h->nrhs,
+                  2.0 * cnt * h->len * h->nrhs);
+        CK(launch_multidot<T>(cnt, vecs + v0, w, h->nrhs, h->len, h->partial, h->nblk_dot,
+                              h->dots_host_dev + (size_t)v0 * h->nrhs, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    out.assign(h->dots_host, h->dots_host + cnt_all);
     if (h->part) CKS(comm_allreduce(h, out));
     if (h->recs.size() > 2048) prof_fold(h);
     return ST_OK;
@@ -1621,19 +1670,17 @@ int norms(st_handle h, const T *x, std::vector<double> &nr) {
 template <typename T>
 int gram2s(st_handle h, int nv, const T *const *vecs, const T *t1, const T *t2,
            std::vector<double> &out) {
-    out.assign((size_t)2 * nv * h->nrhs, 0.0);
+    const size_t cnt_all = (size_t)2 * nv * h->nrhs;
+    CKS(host_dots(h, cnt_all));
     for (int v0 = 0; v0 < nv; v0 += MAXV) {
         const int cnt = std::min(MAXV, nv - v0);
-        {
-            KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 2.0) * h->len * h->nrhs,
-                      4.0 * cnt * h->len * h->nrhs);
-            CK(launch_gram2<T>(cnt, vecs + v0, t1, t2, h->nrhs, h->len, h->partial, h->nblk_dot,
-                               h->dots, h->stream));
-        }
-        CK(cudaMemcpyAsync(out.data() + (size_t)2 * v0 * h->nrhs, h->dots,
-                           sizeof(double) * 2 * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
+        KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 2.0) * h->len * h->nrhs,
+                  4.0 * cnt * h->len * h->nrhs);
+        CK(launch_gram2<T>(cnt, vecs + v0, t1, t2, h->nrhs, h->len, h->partial, h->nblk_dot,
+                           h->dots_host_dev + (size_t)2 * v0 * h->nrhs, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    out.assign(h->dots_host, h->dots_host + cnt_all);
     if (h->part) CKS(comm_allreduce(h, out));
     if (h->recs.size() > 2048) prof_fold(h);
     return ST_OK;
@@ -2521,8 +2568,7 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     void *p;
     CKS(dalloc(h, sizeof(double) * 2 * MAXV * h->nrhs * h->nblk_dot, &p));
     h->partial = (double *)p;
-    CKS(dalloc(h, sizeof(double) * 2 * MAXV * h->nrhs, &p));
-    h->dots = (double *)p;
+    CKS(host_dots(h, (size_t)2 * MAXV * h->nrhs));
     return ST_OK;
 }
 
@@ -2698,7 +2744,13 @@ void st_destroy(st_handle h) {
             cudaFree(p);
     }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (int s = 0; s < 2; ++s)
+        for (cudaEvent_t e : {h->hs_in[s], h->hs_solved[s], h->hs_out[s]})
+            if (e) cudaEventDestroy(e);
+    if (h->cp_in) cudaStreamDestroy(h->cp_in);
+    if (h->cp_out) cudaStreamDestroy(h->cp_out);
     if (h->stage) cudaFreeHost(h->stage);
+    mapped_put(h->dots_host, h->dots_host_cap * sizeof(double));
     delete h;
 }
 
@@ -2943,6 +2995,100 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
     if (info->status != ST_OK)
         return fail(info->status, "no convergence: rel. residual %.3e after %d iterations",
                     info->rel_residual, info->iterations);
+    return ST_OK;
+}
+
+int st_solve_host(st_handle h, int nbatch, const double *rhs, double tol, double *u,
+                  int use_guess, st_solve_info *info) {
+    CKS(check_ptr(h, rhs, "rhs"));
+    CKS(check_ptr(h, u, "u"));
+    if (nbatch < 1) return fail(ST_ERR_INVALID_ARG, "nbatch must be >= 1");
+    if ((const void *)rhs == (void *)u) return fail(ST_ERR_INVALID_ARG, "rhs and u alias");
+    if (!(tol > 0)) return fail(ST_ERR_INVALID_ARG, "tol must be > 0");
+    for (const void *p : {(const void *)rhs, (const void *)u}) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+        } else if (a.type == cudaMemoryTypeDevice) {
+            return fail(ST_ERR_INVALID_ARG, "st_solve_host takes host buffers (use st_solve)");
+        }
+    }
+    const size_t e = (size_t)h->len * h->nrhs;  // doubles per batch
+    if (!h->hs_f[0]) {
+        void *p;
+        for (int s = 0; s < 2; ++s) {
+            CKS(dalloc(h, e * sizeof(double), &p));
+            h->hs_f[s] = (double *)p;
+            CKS(dalloc(h, e * sizeof(double), &p));
+            h->hs_u[s] = (double *)p;
+        }
+    }
+    if (!h->cp_in) {
+        // non-blocking: no implicit ordering with a legacy-default compute stream
+        CK(cudaStreamCreateWithFlags(&h->cp_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->cp_out, cudaStreamNonBlocking));
+        for (int s = 0; s < 2; ++s) {
+            CK(cudaEventCreateWithFlags(&h->hs_in[s], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->hs_solved[s], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->hs_out[s], cudaEventDisableTiming));
+        }
+    }
+    st_solve_info local;
+    if (!info) info = &local;
+    std::memset(info, 0, sizeof *info);
+    const auto t0 = std::chrono::steady_clock::now();
+    // batch k uses slot k & 1; a slot is refilled only after the solve two
+    // batches back has finished with it and its solution has been copied out
+    auto copy_in = [&](int k) -> cudaError_t {
+        const int s = k & 1;
+        cudaError_t c = cudaStreamWaitEvent(h->cp_in, h->hs_solved[s], 0);
+        if (c == cudaSuccess && use_guess) c = cudaStreamWaitEvent(h->cp_in, h->hs_out[s], 0);
+        if (c == cudaSuccess)
+            c = cudaMemcpyAsync(h->hs_f[s], rhs + (size_t)k * e, e * sizeof(double),
+                                cudaMemcpyHostToDevice, h->cp_in);
+        if (c == cudaSuccess && use_guess)
+            c = cudaMemcpyAsync(h->hs_u[s], u + (size_t)k * e, e * sizeof(double),
+                                cudaMemcpyHostToDevice, h->cp_in);
+        if (c == cudaSuccess) c = cudaEventRecord(h->hs_in[s], h->cp_in);
+        return c;
+    };
+    // leave no copy in flight on the staging slots, whatever happened
+    auto drain = [&](int rc) {
+        cudaStreamSynchronize(h->cp_in);
+        cudaStreamSynchronize(h->cp_out);
+        cudaStreamSynchronize(h->stream);
+        return rc;
+    };
+    cudaError_t c = copy_in(0);
+    for (int k = 0; k < nbatch && c == cudaSuccess; ++k) {
+        const int s = k & 1;
+        if (k + 1 < nbatch) c = copy_in(k + 1);  // overlaps this batch's solve
+        if (c == cudaSuccess) c = cudaStreamWaitEvent(h->stream, h->hs_in[s], 0);
+        if (c == cudaSuccess) c = cudaStreamWaitEvent(h->stream, h->hs_out[s], 0);
+        if (c != cudaSuccess) break;
+        st_solve_info bi;
+        const int rc = st_solve(h, h->hs_f[s], tol, h->hs_u[s], use_guess, &bi);
+        info->iterations = std::max(info->iterations, bi.iterations);
+        info->refinements = std::max(info->refinements, bi.refinements);
+        info->rel_residual = std::max(info->rel_residual, bi.rel_residual);
+        if (rc != ST_OK) {
+            info->status = rc;
+            return drain(rc);
+        }
+        c = cudaEventRecord(h->hs_solved[s], h->stream);
+        if (c == cudaSuccess) c = cudaStreamWaitEvent(h->cp_out, h->hs_solved[s], 0);
+        if (c == cudaSuccess)
+            c = cudaMemcpyAsync(u + (size_t)k * e, h->hs_u[s], e * sizeof(double),
+                                cudaMemcpyDeviceToHost, h->cp_out);
+        if (c == cudaSuccess) c = cudaEventRecord(h->hs_out[s], h->cp_out);
+    }
+    if (c == cudaSuccess) c = cudaStreamSynchronize(h->cp_out);
+    if (c != cudaSuccess) {
+        cudaGetLastError();
+        return drain(fail(ST_ERR_CUDA, "st_solve_host: %s", cudaGetErrorString(c)));
+    }
+    CK(cudaStreamSynchronize(h->cp_in));
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return ST_OK;
 }
 

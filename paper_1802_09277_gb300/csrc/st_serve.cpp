@@ -438,6 +438,13 @@ int st_serve_start(st_server *out, const st_server_opts *o) {
     return ST_OK;
 }
 
+int st_serve_pause(st_server s) {
+    if (!s) return ST_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->paused = true;  // batches already taken run to the end
+    return ST_OK;
+}
+
 int st_serve_resume(st_server s) {
     if (!s) return ST_ERR_INVALID_ARG;
     {

@@ -31,9 +31,9 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_smooth_static", "st_set_wait_limit", "st_block_minres", "st_vcycle",
            "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
            "st_time_prolongation", "st_level_shape", "st_space_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
-           "st_serve_submit", "st_serve_resume", "st_serve_cancel", "st_serve_poll", "st_serve_wait",
+           "st_serve_submit", "st_serve_resume", "st_serve_pause", "st_serve_cancel", "st_serve_poll", "st_serve_wait",
            "st_serve_stop", "st_setup_partitioned", "st_partition_plan", "st_comm_nccl_unique_id",
-           "st_comm_nccl_create", "st_comm_nccl_destroy", "st_solve_history"]
+           "st_comm_nccl_create", "st_comm_nccl_destroy", "st_solve_history", "st_solve_host"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
                 "vector", "dot", "tc", "spec", "stencil_df", "minres"]
 
@@ -134,6 +134,7 @@ def load():
         "st_level_shape": (I, [P, I, ip, ip, ip]),
         "st_space_prolongation": (I, [P, I, I, ip, ip, dp]),
         "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
+        "st_solve_host": (I, [P, I, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
         "st_autotune": (I, [P, ip, dp]),
         "st_profile": (I, [P, I]),
         "st_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]),
@@ -147,6 +148,7 @@ def load():
         "st_serve_submit": (I, [P, ctypes.POINTER(StRequest), ctypes.POINTER(ctypes.c_uint64)]),
         "st_set_wait_limit": (I, [P, D]),
         "st_serve_resume": (I, [P]),
+        "st_serve_pause": (I, [P]),
         "st_serve_cancel": (I, [P, ctypes.c_uint64]),
         "st_serve_poll": (I, [P, ctypes.c_uint64, ctypes.POINTER(StResult), dp]),
         "st_serve_wait": (I, [P, ctypes.c_uint64, D, ctypes.POINTER(StResult), dp]),
@@ -324,6 +326,30 @@ class Solver:
                 "status": info.status,
                 "rel_residual": info.rel_residual, "seconds": info.seconds, "rc": rc}
 
+    def solve_host(self, rhs, u, tol=1e-8, use_guess=False, check=True):
+        """st_solve_host: rhs and u are contiguous float64 CPU tensors of
+        nbatch x ndofs values (pinned memory lets the copies overlap the
+        solves); nbatch = rhs.numel() // ndofs."""
+        import torch
+        for t, name in ((rhs, "rhs"), (u, "u")):
+            if not isinstance(t, torch.Tensor):
+                raise TypeError("%s must be a torch tensor" % name)
+            if t.dtype != torch.float64 or t.is_cuda or not t.is_contiguous():
+                raise ValueError("%s must be a contiguous float64 CPU tensor" % name)
+        if rhs.numel() == 0 or rhs.numel() % self.ndofs or u.numel() != rhs.numel():
+            raise ValueError("rhs and u must hold the same whole number of batches of %d values"
+                             % self.ndofs)
+        info = StSolveInfo()
+        rc = _lib.st_solve_host(self._h, rhs.numel() // self.ndofs,
+                                ctypes.c_void_p(rhs.data_ptr()), float(tol),
+                                ctypes.c_void_p(u.data_ptr()), int(bool(use_guess)),
+                                ctypes.byref(info))
+        if check:
+            _check(rc)
+        return {"iterations": info.iterations, "refinements": info.refinements,
+                "status": info.status, "rel_residual": info.rel_residual,
+                "seconds": info.seconds, "rc": rc}
+
     def set_wait_limit(self, seconds):
         """Bound of the tensor-core kernels' device-side waits (seconds)."""
         _check(_lib.st_set_wait_limit(self._h, float(seconds)))
@@ -475,8 +501,13 @@ class Server:
         return out, u
 
     def resume(self):
-        """Let the workers of a server started paused take requests."""
+        """Let the workers of a server started (or set) paused take requests."""
         _check(_lib.st_serve_resume(self._s))
+
+    def pause(self):
+        """Workers take no further request until resume(); running batches
+        finish."""
+        _check(_lib.st_serve_pause(self._s))
 
     def cancel(self, ticket):
         """True if the request was withdrawn before a worker took it, False

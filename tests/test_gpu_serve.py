@@ -138,3 +138,33 @@ def test_cancel_pending_request(st):
     with pytest.raises(st.StError):  # finished and released: unknown ticket
         srv.cancel(t1)
     srv.stop()
+
+
+def test_pause_queues_and_batches(st):
+    """A running server paused with st_serve_pause takes no request until
+    st_serve_resume; the queued repeats of one configuration then form one
+    batch, with the results of a fresh server."""
+    opts = dict(precision="mixed_tf32", outer="ir", basis="spectral")
+    reqs = _requests()
+    srv = st.Server(workers=2, max_batch=4, **opts)
+    d, spans, p, N, c = reqs[0]
+    first, _ = srv.wait(srv.submit(d, p, spans, N, c, tol=1e-10, coeffs=True), timeout=120.0)
+    assert first["status"] == 0  # the server runs before the pause
+    srv.pause()
+    tickets = [srv.submit(d, p, spans, N, c, tol=1e-10, coeffs=True)
+               for d, spans, p, N, c in reqs]
+    import time
+    time.sleep(0.5)
+    assert all(srv.poll(t) is None for t in tickets)  # nothing taken while paused
+    srv.resume()
+    got = [srv.wait(t, timeout=120.0) for t in tickets]
+    srv.stop()
+    assert [res["batch_size"] for res, _ in got] == [MIX.count(m) for m in MIX]
+    ref = st.Server(workers=1, max_batch=4, paused=True, **opts)
+    rt = [ref.submit(d, p, spans, N, c, tol=1e-10, coeffs=True) for d, spans, p, N, c in reqs]
+    ref.resume()
+    for (res, u), t in zip(got, rt):
+        r2, u2 = ref.wait(t, timeout=120.0)
+        assert res["status"] == 0 and r2["status"] == 0
+        assert np.array_equal(u, u2)
+    ref.stop()
