@@ -661,9 +661,12 @@ def serve_arm(args):
     for i, (sp, p, N) in enumerate(mix):
         n = (sp + p - 2) ** 2 * N * (ne + p)
         reqs.append((sp, p, N, inputs.normal_coeffs(10000 + i, n)))
-    srv = st.Server(workers=args.serve_workers, max_batch=8, precision=args.precision,
-                    basis="spectral", outer="ir", ne_per_slab=ne, gmres_restart=20, max_it=300,
-                    nu1=NU[0], nu2=NU[1])
+    def server(group_members):
+        return st.Server(workers=args.serve_workers, max_batch=8, precision=args.precision,
+                         basis="spectral", outer="ir", ne_per_slab=ne, gmres_restart=20,
+                         max_it=300, nu1=NU[0], nu2=NU[1], group_members=group_members)
+
+    srv = server(args.serve_group_members)
 
     def run(times, burst=False):
         tickets = [None] * nreq
@@ -687,6 +690,7 @@ def serve_arm(args):
         th = threading.Thread(target=submitter)
         th.start()
         lat, dofs, worst, batches, bad = [], 0, 0.0, [], 0
+        groups, syncs_pr, launches_pr = [], [], []
         for i in range(nreq):
             while tickets[i] is None:
                 time.sleep(1e-4)
@@ -698,6 +702,10 @@ def serve_arm(args):
             dofs += res["n_dofs"]
             worst = max(worst, res["rel_residual"])
             batches.append(res["batch_size"])
+            gq = max(1, res["group_requests"])
+            groups.append(gq)
+            syncs_pr.append(res["host_syncs"] / gq)  # the call's share per request
+            launches_pr.append(res["vector_launches"] / gq)
         makespan = time.perf_counter() - t0
         th.join()
         lat = np.sort(np.array(lat))
@@ -705,17 +713,29 @@ def serve_arm(args):
                 "p99_latency_s": float(np.percentile(lat, 99)),
                 "throughput_dofs_per_s": dofs / makespan, "makespan_s": makespan,
                 "total_dofs": int(dofs), "max_rel_residual": worst, "failed": bad,
-                "mean_batch": float(np.mean(batches))}
+                "mean_batch": float(np.mean(batches)),
+                "mean_group_requests": float(np.mean(groups)),
+                "host_syncs_per_request": float(np.mean(syncs_pr)),
+                "krylov_vector_launches_per_request": float(np.mean(launches_pr))}
 
     first = run(arrivals)
     again = run(arrivals)
+    run(None, burst=True)  # fills the setup cache with the burst's batch sizes
     burst = run(None, burst=True)
     srv.stop()
+    # the same burst with every configuration's batch solved alone (a second
+    # server; its first burst fills its setup cache)
+    srv = server(1)
+    run(None, burst=True)
+    alone = run(None, burst=True)
+    srv.stop()
     out = {"requests": nreq, "arrival_rate_per_s": rate, "workers": args.serve_workers,
+           "group_members": args.serve_group_members,
            "precision": args.precision, "tol": 1e-8, "setup_cache": "empty at start"}
     out.update(first)
     out["repeat_setups_cached"] = again
-    out["burst_all_at_once"] = burst
+    out["burst_all_at_once_setups_cached"] = burst
+    out["burst_groups_off_setups_cached"] = alone
     return out
 
 
@@ -892,6 +912,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=512)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-group-members", type=int, default=8,
+                    help="configurations per group solve call (1 = each batch alone)")
     ap.add_argument("--basis", default="spectral", choices=["spectral", "nodal"])
     ap.add_argument("--outer", default="ir", choices=["ir", "fgmres", "mg"])
     ap.add_argument("--precision", default="mixed_tf32",

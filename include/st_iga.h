@@ -172,6 +172,9 @@ typedef struct {
     int status;           /* ST_OK or ST_ERR_NO_CONVERGENCE                      */
     double rel_residual;  /* max over rhs of ||f - L u||_2 / ||f||_2 (FP64)       */
     double seconds;       /* wall time of the solve, host clock                 */
+    int host_syncs;       /* host synchronisations to read reductions back      */
+    int vector_launches;  /* Krylov vector-kernel launches (dots, updates); for
+                             st_solve_group both count the whole group's calls */
 } st_solve_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -323,12 +326,46 @@ int st_vcycle(st_handle h, double *u, const double *f);
 int st_solve(st_handle h, const double *rhs, double tol, double *u,
              int use_guess, st_solve_info *info);
 
+/* Solve the problems of n handles together (batching of uneven requests):
+ * the handles may differ in geometry, degree, spans, slabs and nrhs; each
+ * must be a mixed-precision handle with ST_OUTER_IR (the refinement of
+ * Sec. 3.1's outer solve around FP32 FGMRES, as st_solve runs it), not
+ * slab-partitioned, and all must share gmres_restart.  The members'
+ * refinement and Krylov iterations advance in lockstep: every Krylov vector
+ * operation of the members still iterating (Gram products and their
+ * reduction, the basis updates, the solution update) is ONE launch over all
+ * their right-hand sides, read back with one host synchronisation for the
+ * whole group, while each member's operator, V-cycle, transforms and FP64
+ * residual run on a stream of their own so that they overlap on the device.
+ * Every loop bound is kept per member and every decision per right-hand
+ * side, so each right-hand side gets exactly the result st_solve gives it on
+ * its own handle.
+ *   hs        : n distinct handles, 1 <= n <= 16, at most 32 right-hand sides
+ *               in all (the sum of their nrhs)
+ *   rhs, u    : n device pointers each, member k's n_dofs doubles (u: the
+ *               solution; the initial guess when use_guess != 0)
+ *   info      : n entries (may be NULL): member k's iterations, refinements,
+ *               residual and status; seconds = the group's wall time
+ * Work is queued on member 0's stream (and on internal streams ordered after
+ * it and after each member's own stream); the call returns with every
+ * member's work complete and its stream unchanged.  Errors: INVALID_ARG,
+ * UNSUPPORTED (a member of another kind), those of st_solve;
+ * NO_CONVERGENCE if any member stopped at max_it (its info says which; the
+ * others hold their solutions). */
+int st_solve_group(int n, const st_handle *hs, const double *const *rhs, double tol,
+                   double *const *u, int use_guess, st_solve_info *info);
+
 /* st_solve on HOST buffers for a stream of nbatch batches of the handle's
  * systems (each batch: nrhs right-hand sides, st_solve's layout; batch k at
  * offset k x n_dofs doubles).  Batch k solves on the handle's stream while
  * batch k+1's right-hand sides are copied to the device and batch k-1's
  * solutions back to the host, each on a stream of its own, so the transfers
  * hide behind the solves but for the first copy in and the last copy out.
+ * The copies back are issued in 256 MB chunks at the solve's host
+ * synchronisation points, one chunk in flight at a time: a bulk
+ * device-to-host transfer would hold up the solve's own small reads of its
+ * dot products (with use_guess the copy of a slot is issued in full before
+ * its guess is copied in).
  *   rhs  : host, nbatch x n_dofs doubles, not modified
  *   u    : host, nbatch x n_dofs doubles: the solutions (output); the initial
  *          guesses when use_guess != 0 (else zero guesses)
@@ -419,7 +456,17 @@ typedef struct {
     long long batch_dofs; /* a batch grows only while its total dofs stay within
                              this (the oldest request always runs): large solves
                              already saturate the GPU and only wait longer in a
-                             batch; 0 = no limit; default 8388608               */
+                             batch; 0 = no limit; default 8388608.  A group's
+                             total dofs stay within it too                      */
+    int group_members;    /* up to this many configurations (each with its batch,
+                             oldest first, none with more dofs per request than
+                             the oldest request's, so a group never delays it)
+                             are solved together by one st_solve_group call:
+                             one launch per Krylov vector operation and one host
+                             synchronisation per reduction for all of them, the
+                             members' V-cycles overlapping (at most 32 right-hand
+                             sides in all); 1 = every batch alone; default 8;
+                             used when opt is mixed precision with ST_OUTER_IR */
 } st_server_opts;
 
 typedef struct {
@@ -442,9 +489,12 @@ typedef struct {
     double queue_seconds; /* submit -> admitted                                   */
     double solve_seconds; /* admitted -> solution on the host                     */
     double latency_seconds; /* submit -> solution on the host                     */
-    int batch_size;       /* requests solved together with this one (incl. itself) */
+    int batch_size;       /* requests of this configuration solved with it (incl. itself) */
     int64_t n_dofs;
     char error[128];      /* message of a failure ("" on success)              */
+    int group_requests;   /* requests in the same solve call (all configurations) */
+    int host_syncs;       /* of that call (st_solve_info.host_syncs)             */
+    int vector_launches;  /* of that call (st_solve_info.vector_launches)        */
 } st_result;
 
 void st_serve_opts_default(st_server_opts *o);

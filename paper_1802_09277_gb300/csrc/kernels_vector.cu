@@ -9,28 +9,71 @@ namespace st {
 
 constexpr int NRHS_MAX = 32;
 
+// Device view of a group launch (see GLaunch): per member its length, rhs
+// count, wide-load flag and partial-sum buffer; per system its member and
+// rhs index and (multi-axpy) its vector count.
+struct GMemD {
+    long long len[GH];
+    int R[GH];
+    int vec[GH];
+    double *part[GH];
+};
+struct GSysD {
+    int m[NSYS_MAX], r[NSYS_MAX], nv[NSYS_MAX];
+};
+// vector v of member k
 template <typename T>
-struct VecList {
-    const T *v[MAXV];
+struct GVecD {
+    const T *v[MAXV][GH];
+};
+// one target vector per member
+template <typename T>
+struct GTgtD {
+    T *p[GH];
 };
 template <typename T>
-struct AxpyArgs {
-    const T *x[MAXV];
-    T coef[MAXV * NRHS_MAX];  // rounded to T on the host
-    T post[NRHS_MAX];         // y <- post_r * (y + sum_v coef x_v)
+struct GAxpyD {
+    T coef[MAXV * NSYS_MAX];  // rounded to T on the host
+    T post[NSYS_MAX];         // y <- post_s * (y + sum_v coef x_v)
+};
+// two outputs sharing the vectors x_v (the delayed Gram-Schmidt step):
+//   y1 <- post1_s * (y1 + sum_v c1 x_v)
+//   y2 <- post2_s * (y2 + c21_s * y1_old + sum_v c2 x_v)
+template <typename T>
+struct GAxpy2D {
+    T c1[MAXV * NSYS_MAX];
+    T c2[MAXV * NSYS_MAX];
+    T c21[NSYS_MAX];
+    T post1[NSYS_MAX], post2[NSYS_MAX];
+    int write1[NSYS_MAX];  // 0: y1 of system s is left untouched
 };
 
-// two outputs sharing the vectors x_v (the delayed Gram-Schmidt step):
-//   y1 <- post1_r * (y1 + sum_v c1 x_v)
-//   y2 <- post2_r * (y2 + c21_r * y1_old + sum_v c2 x_v)
-template <typename T>
-struct Axpy2Args {
-    const T *x[MAXV];
-    T c1[MAXV * NRHS_MAX];
-    T c2[MAXV * NRHS_MAX];
-    T c21[NRHS_MAX];
-    T post1[NRHS_MAX], post2[NRHS_MAX];
-};
+static GMemD mem_of(const GLaunch &g) {
+    GMemD m{};
+    for (int k = 0; k < g.nmem; ++k) {
+        m.len[k] = g.len[k];
+        m.R[k] = g.R[k];
+        m.part[k] = g.part[k];
+    }
+    return m;
+}
+static GSysD sys_of(const GLaunch &g) {
+    GSysD s{};
+    for (int i = 0; i < g.nsys; ++i) {
+        s.m[i] = g.sm[i];
+        s.r[i] = g.sr[i];
+        s.nv[i] = g.snv[i];
+    }
+    return s;
+}
+static bool group_ok(const GLaunch &g, int nv) {
+    if (g.nmem < 1 || g.nmem > GH || g.nsys < 1 || g.nsys > NSYS_MAX || nv < 0 || nv > MAXV)
+        return false;
+    for (int i = 0; i < g.nsys; ++i)
+        if (g.sm[i] < 0 || g.sm[i] >= g.nmem || g.sr[i] < 0 || g.sr[i] >= g.R[g.sm[i]])
+            return false;
+    return true;
+}
 
 // two consecutive elements as one 8- (float) or 16-byte (double) access
 template <typename T>
@@ -144,25 +187,30 @@ struct Red<float> {
     static __device__ __forceinline__ double out(V v) { return (double)v; }
 };
 
-// grid (nblk, nrhs, ceil(nv / 4)), 256 threads; partial[(v*nrhs + r)*nblk + blk].
-// Block (b, r, g) accumulates the dots of w with vectors 4g .. 4g+3 over a
-// grid-stride loop, two elements per load when vec2 is set.  w is re-read
-// by every group from L2.
+// grid (nblk, nsys, ceil(nv / 4)), 256 threads; member k's partial sums at
+// part[k][(v * R[k] + r) * nblk + blk].  Block (b, s, g) accumulates the dots
+// of system s's target with vectors 4g .. 4g+3 over a grid-stride loop, two
+// elements per load when the member allows it.  The target is re-read by
+// every group from L2.
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_multidot_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ w,
-                       long long len, double *__restrict__ partial, int vec2) {
+    k_gdot_partial(int nv, const __grid_constant__ GVecD<T> vl, const __grid_constant__ GTgtD<T> tw,
+                   const __grid_constant__ GMemD gm, const __grid_constant__ GSysD gs) {
     griddep_wait();
     griddep_launch();
     using P2 = typename Pair<T>::V;
     __shared__ typename Red<T>::V red[8][4];
-    const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
+    const int s = blockIdx.y, nblk = gridDim.x;
+    const int mk = gs.m[s], r = gs.r[s];
+    const long long len = gm.len[mk];
+    const long long off = (long long)r * len;
+    const int vec2 = gm.vec[mk];
+    const T *w = tw.p[mk];
     const int v0 = 4 * blockIdx.z;
     const int cnt = (nv - v0 < 4) ? nv - v0 : 4;
-    const long long off = (long long)r * len;
     const T *x[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0] + off;
+    for (int k = 0; k < 4; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0][mk] + off;
     DotAcc<T> acc[4];
     const long long stride = (long long)nblk * blockDim.x;
     if (vec2) {
@@ -199,68 +247,86 @@ __global__ void __launch_bounds__(256)
     if (threadIdx.x < cnt) {
         typename RD::V t = RD::zero();
         for (int q = 0; q < 8; ++q) t = RD::add(t, red[q][threadIdx.x]);
-        partial[((long long)(v0 + threadIdx.x) * nrhs + r) * nblk + blockIdx.x] = RD::out(t);
+        gm.part[mk][((long long)(v0 + threadIdx.x) * gm.R[mk] + r) * nblk + blockIdx.x] = RD::out(t);
     }
 }
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// one warp per output; lane-strided partial sums, then a fixed shuffle tree
-__global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, int count,
-                                  double *__restrict__ out) {
+// one warp per output out[row * nsys + s]: lane-strided partial sums of that
+// row and system, then a fixed shuffle tree
+__global__ void k_greduce(const __grid_constant__ GMemD gm, const __grid_constant__ GSysD gs,
+                          int nsys, int count, int nblk, double *__restrict__ out) {
     griddep_wait();
     griddep_launch();
     const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x & 31;
     if (i >= count) return;
+    const int row = i / nsys, s = i % nsys;
+    const int mk = gs.m[s];
+    const double *p = gm.part[mk] + ((long long)row * gm.R[mk] + gs.r[s]) * nblk;
     double t = 0.0;
-    for (int b = lane; b < nblk; b += 32) t += partial[(long long)i * nblk + b];
+    for (int b = lane; b < nblk; b += 32) t += p[b];
     t = warp_sum(t);
     if (lane == 0) out[i] = t;
 }
 
 template <typename T>
-cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, long long len,
-                            double *partial, int nblk, double *out, cudaStream_t s) {
-    if (nv > MAXV || nrhs > 65535 || nv <= 0) return cudaErrorInvalidValue;
-    VecList<T> vl;
-    auto al = [](const void *p) {
-        return sizeof(T) == 8 ? aligned16(p) : ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
-    };
-    int vec2 = (len % 2 == 0) && al(w);
-    for (int i = 0; i < nv; ++i) {
-        vl.v[i] = vecs[i];
-        vec2 = vec2 && al(vecs[i]);
+static bool al2(const void *p) {
+    return sizeof(T) == 8 ? aligned16(p) : ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
+}
+
+template <typename T>
+cudaError_t launch_gdot(const GLaunch &g, int nv, const T *const *xs, const T *const *w,
+                        double *out, cudaStream_t s) {
+    if (!group_ok(g, nv) || nv < 1) return cudaErrorInvalidValue;
+    GVecD<T> vl{};
+    GTgtD<T> tw{};
+    GMemD gm = mem_of(g);
+    for (int k = 0; k < g.nmem; ++k) {
+        tw.p[k] = const_cast<T *>(w[k]);
+        int vec2 = (g.len[k] % 2 == 0) && al2<T>(w[k]);
+        for (int v = 0; v < nv; ++v) {
+            vl.v[v][k] = xs[(size_t)v * g.nmem + k];
+            vec2 = vec2 && al2<T>(vl.v[v][k]);
+        }
+        gm.vec[k] = vec2;
     }
-    cudaError_t e = launch_pdl(k_multidot_partial<T>, dim3(nblk, nrhs, (nv + 3) / 4), dim3(256),
-                               0, s, nv, vl, w, len, partial, vec2);
+    const GSysD gs = sys_of(g);
+    cudaError_t e = launch_pdl(k_gdot_partial<T>, dim3(g.nblk, g.nsys, (nv + 3) / 4), dim3(256),
+                               0, s, nv, vl, tw, gm, gs);
     if (e != cudaSuccess) return e;
-    const int count = nv * nrhs;
-    e = launch_pdl(k_reduce_partials, dim3((count + 3) / 4), dim3(128), 0, s, partial, nblk,
-                   count, out);
+    const int count = nv * g.nsys;
+    e = launch_pdl(k_greduce, dim3((count + 3) / 4), dim3(128), 0, s, gm, gs, g.nsys, count,
+                   g.nblk, out);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// grid (blocks, nrhs): block row r handles right-hand side r (no index division)
+// grid (blocks, nsys): block row s updates system s (its member's vector at
+// offset r * len) with the first nv[s] vectors
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_multiaxpy(int nv, const __grid_constant__ AxpyArgs<T> aa, long long len,
-                T *__restrict__ y, int vec2) {
+    k_gaxpy(const __grid_constant__ GVecD<T> vl, const __grid_constant__ GTgtD<T> ty,
+            const __grid_constant__ GAxpyD<T> aa, const __grid_constant__ GMemD gm,
+            const __grid_constant__ GSysD gs) {
     griddep_wait();
     griddep_launch();
     using P2 = typename Pair<T>::V;
-    const int r = blockIdx.y;
-    const long long off = (long long)r * len;
+    const int s = blockIdx.y;
+    const int mk = gs.m[s], nv = gs.nv[s];
+    const long long len = gm.len[mk];
+    const long long off = (long long)gs.r[s] * len;
+    T *__restrict__ y = ty.p[mk];
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const T post = aa.post[r];
-    if (vec2) {  // off is even because len is
+    const T post = aa.post[s];
+    if (gm.vec[mk]) {  // off is even because len is
         const long long n = len / 2;
         P2 *y2 = reinterpret_cast<P2 *>(y + off);
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
             P2 acc = y2[i];
             for (int v = 0; v < nv; ++v) {
-                const T c = aa.coef[v * NRHS_MAX + r];
-                const P2 x = reinterpret_cast<const P2 *>(aa.x[v] + off)[i];
+                const T c = aa.coef[v * NSYS_MAX + s];
+                const P2 x = reinterpret_cast<const P2 *>(vl.v[v][mk] + off)[i];
                 acc.x += c * x.x;
                 acc.y += c * x.y;
             }
@@ -272,40 +338,40 @@ __global__ void __launch_bounds__(256)
     }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
         T acc = y[off + i];
-        for (int v = 0; v < nv; ++v) acc += aa.coef[v * NRHS_MAX + r] * aa.x[v][off + i];
+        for (int v = 0; v < nv; ++v) acc += aa.coef[v * NSYS_MAX + s] * vl.v[v][mk][off + i];
         y[off + i] = post * acc;
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256)
-    k_axpy2(int nv, const __grid_constant__ Axpy2Args<T> aa, long long len, T *__restrict__ y1,
-            T *__restrict__ y2, int write1) {
+    k_gaxpy2(int nv, const __grid_constant__ GVecD<T> vl, const __grid_constant__ GTgtD<T> t1,
+             const __grid_constant__ GTgtD<T> t2, const __grid_constant__ GAxpy2D<T> aa,
+             const __grid_constant__ GMemD gm, const __grid_constant__ GSysD gs) {
     griddep_wait();
     griddep_launch();
-    const int r = blockIdx.y;
-    const long long off = (long long)r * len;
+    const int s = blockIdx.y;
+    const int mk = gs.m[s];
+    const long long len = gm.len[mk];
+    const long long off = (long long)gs.r[s] * len;
+    T *__restrict__ y1 = t1.p[mk];
+    T *__restrict__ y2 = t2.p[mk];
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const T p1 = aa.post1[r], p2 = aa.post2[r], c21 = aa.c21[r];
+    const T p1 = aa.post1[s], p2 = aa.post2[s], c21 = aa.c21[s];
+    const int write1 = aa.write1[s];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
         const T a1o = y1[off + i];
         T a1 = a1o, a2 = y2[off + i] + c21 * a1o;
         for (int v = 0; v < nv; ++v) {
-            const T x = aa.x[v][off + i];
-            a1 += aa.c1[v * NRHS_MAX + r] * x;
-            a2 += aa.c2[v * NRHS_MAX + r] * x;
+            const T x = vl.v[v][mk][off + i];
+            a1 += aa.c1[v * NSYS_MAX + s] * x;
+            a2 += aa.c2[v * NSYS_MAX + s] * x;
         }
         if (write1) y1[off + i] = p1 * a1;
         y2[off + i] = p2 * a2;
     }
 }
 
-// grid (nblk, nrhs, ceil(nv / GV)): the dots of vectors GV g .. GV g + GV - 1
-// with two targets t1, t2 in one pass; partial[((v * 2 + t) * nrhs + r) * nblk + blk].
-// vec4: 16-byte loads (len a multiple of 4, 16-byte aligned vectors); each
-// thread forms the 4-term products of a chunk in T and adds them into its
-// accumulator (Kahan-compensated in FP32), so the compensation runs once per
-// 4 elements.
 template <typename T>
 struct Quad;
 template <>
@@ -357,28 +423,38 @@ __device__ __forceinline__ void gram2_body(const T *const *x, const T *__restric
     }
 }
 
+// grid (nblk, nsys, ceil(nv / GV)): the dots of vectors GV g .. GV g + GV - 1
+// with two targets t1, t2 in one pass; member k's partial sums at
+// part[k][((v * 2 + t) * R[k] + r) * nblk + blk].  vec4: 16-byte loads (len a
+// multiple of 4, 16-byte aligned vectors); each thread forms the 4-term
+// products of a chunk in T and adds them into its accumulator
+// (Kahan-compensated in FP32), so the compensation runs once per 4 elements.
 template <typename T, int GV>
 __global__ void __launch_bounds__(256)
-    k_gram2_partial(int nv, const __grid_constant__ VecList<T> vl, const T *__restrict__ t1,
-                    const T *__restrict__ t2, long long len, double *__restrict__ partial,
-                    int vec4) {
+    k_ggram2_partial(int nv, const __grid_constant__ GVecD<T> vl,
+                     const __grid_constant__ GTgtD<T> tt1, const __grid_constant__ GTgtD<T> tt2,
+                     const __grid_constant__ GMemD gm, const __grid_constant__ GSysD gs) {
     griddep_wait();
     griddep_launch();
     __shared__ typename Red<T>::V red[8][2 * GV];
-    const int r = blockIdx.y, nblk = gridDim.x, nrhs = gridDim.y;
+    const int s = blockIdx.y, nblk = gridDim.x;
+    const int mk = gs.m[s], r = gs.r[s];
+    const long long len = gm.len[mk];
+    const long long off = (long long)r * len;
+    const int vec4 = gm.vec[mk];
+    const T *t1 = tt1.p[mk] + off, *t2 = tt2.p[mk] + off;
     const int v0 = GV * blockIdx.z;
     const int cnt = (nv - v0 < GV) ? nv - v0 : GV;
-    const long long off = (long long)r * len;
     const T *x[GV];
 #pragma unroll
-    for (int k = 0; k < GV; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0] + off;
+    for (int k = 0; k < GV; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0][mk] + off;
     DotAcc<T> a1[GV], a2[GV];
     static_assert(GV == 4, "the count dispatch below covers GV = 4");
     switch (cnt) {  // uniform across the grid row
-        case 1: gram2_body<T, 1>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
-        case 2: gram2_body<T, 2>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
-        case 3: gram2_body<T, 3>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
-        default: gram2_body<T, 4>(x, t1 + off, t2 + off, len, vec4, a1, a2); break;
+        case 1: gram2_body<T, 1>(x, t1, t2, len, vec4, a1, a2); break;
+        case 2: gram2_body<T, 2>(x, t1, t2, len, vec4, a1, a2); break;
+        case 3: gram2_body<T, 3>(x, t1, t2, len, vec4, a1, a2); break;
+        default: gram2_body<T, 4>(x, t1, t2, len, vec4, a1, a2); break;
     }
     using RD = Red<T>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -396,82 +472,109 @@ __global__ void __launch_bounds__(256)
         typename RD::V t = RD::zero();
         for (int q = 0; q < 8; ++q) t = RD::add(t, red[q][threadIdx.x]);
         const int v = v0 + threadIdx.x / 2, which = threadIdx.x % 2;
-        partial[((long long)(2 * v + which) * nrhs + r) * nblk + blockIdx.x] = RD::out(t);
+        gm.part[mk][((long long)(2 * v + which) * gm.R[mk] + r) * nblk + blockIdx.x] = RD::out(t);
     }
 }
 
 template <typename T>
-cudaError_t launch_gram2(int nv, const T *const *vecs, const T *t1, const T *t2, int nrhs,
-                         long long len, double *partial, int nblk, double *out, cudaStream_t s) {
-    if (nv > MAXV || nrhs > 65535 || nv <= 0) return cudaErrorInvalidValue;
-    VecList<T> vl;
+cudaError_t launch_ggram2(const GLaunch &g, int nv, const T *const *xs, const T *const *t1,
+                          const T *const *t2, double *out, cudaStream_t s) {
+    if (!group_ok(g, nv) || nv < 1) return cudaErrorInvalidValue;
+    GVecD<T> vl{};
+    GTgtD<T> a{}, b{};
+    GMemD gm = mem_of(g);
     // 4-element loads need the vectors aligned to 4 elements (16 or 32 bytes)
     const uintptr_t am = 4 * sizeof(T) - 1;
     auto al4 = [am](const void *p) { return (reinterpret_cast<uintptr_t>(p) & am) == 0; };
-    int vec4 = (len % 4 == 0) && al4(t1) && al4(t2);
-    for (int i = 0; i < nv; ++i) {
-        vl.v[i] = vecs[i];
-        vec4 = vec4 && al4(vecs[i]);
-    }
-    constexpr int GV = 4;
-    cudaError_t e = launch_pdl(k_gram2_partial<T, GV>, dim3(nblk, nrhs, (nv + GV - 1) / GV),
-                               dim3(256), 0, s, nv, vl, t1, t2, len, partial, vec4);
-    if (e != cudaSuccess) return e;
-    const int count = 2 * nv * nrhs;
-    e = launch_pdl(k_reduce_partials, dim3((count + 3) / 4), dim3(128), 0, s, partial, nblk,
-                   count, out);
-    return e != cudaSuccess ? e : cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_axpy2(int nv, const T *const *xs, const double *c1, const double *c2,
-                         const double *c21, const double *post1, const double *post2, int nrhs,
-                         long long len, T *y1, T *y2, int write1, cudaStream_t s) {
-    if (nv > MAXV || nrhs > NRHS_MAX || nv < 0) return cudaErrorInvalidValue;
-    Axpy2Args<T> aa;
-    for (int v = 0; v < nv; ++v) {
-        aa.x[v] = xs[v];
-        for (int r = 0; r < nrhs; ++r) {
-            aa.c1[v * NRHS_MAX + r] = (T)c1[v * nrhs + r];
-            aa.c2[v * NRHS_MAX + r] = (T)c2[v * nrhs + r];
+    for (int k = 0; k < g.nmem; ++k) {
+        a.p[k] = const_cast<T *>(t1[k]);
+        b.p[k] = const_cast<T *>(t2[k]);
+        int vec4 = (g.len[k] % 4 == 0) && al4(t1[k]) && al4(t2[k]);
+        for (int v = 0; v < nv; ++v) {
+            vl.v[v][k] = xs[(size_t)v * g.nmem + k];
+            vec4 = vec4 && al4(vl.v[v][k]);
         }
+        gm.vec[k] = vec4;
     }
-    for (int r = 0; r < nrhs; ++r) {
-        aa.c21[r] = (T)c21[r];
-        aa.post1[r] = (T)post1[r];
-        aa.post2[r] = (T)post2[r];
-    }
-    long long bx = (len + 255) / 256;
-    const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
+    const GSysD gs = sys_of(g);
+    constexpr int GV = 4;
+    cudaError_t e = launch_pdl(k_ggram2_partial<T, GV>, dim3(g.nblk, g.nsys, (nv + GV - 1) / GV),
+                               dim3(256), 0, s, nv, vl, a, b, gm, gs);
+    if (e != cudaSuccess) return e;
+    const int count = 2 * nv * g.nsys;
+    e = launch_pdl(k_greduce, dim3((count + 3) / 4), dim3(128), 0, s, gm, gs, g.nsys, count,
+                   g.nblk, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+static unsigned axpy_blocks(const GLaunch &g, long long per_block) {
+    long long len = 1;
+    for (int k = 0; k < g.nmem; ++k) len = g.len[k] > len ? g.len[k] : len;
+    long long bx = (len + per_block - 1) / per_block;
+    const long long cap = (152LL * 16 + g.nsys - 1) / g.nsys;
     if (bx > cap) bx = cap;
     if (bx < 1) bx = 1;
-    const cudaError_t e = launch_pdl(k_axpy2<T>, dim3((unsigned)bx, (unsigned)nrhs), dim3(256), 0,
-                                     s, nv, aa, len, y1, y2, write1);
+    return (unsigned)bx;
+}
+
+template <typename T>
+cudaError_t launch_gaxpy2(const GLaunch &g, int nv, const T *const *xs, const double *c1,
+                          const double *c2, const double *c21, const double *post1,
+                          const double *post2, T *const *y1, T *const *y2, const int *write1,
+                          cudaStream_t s) {
+    if (!group_ok(g, nv)) return cudaErrorInvalidValue;
+    GVecD<T> vl{};
+    GTgtD<T> a{}, b{};
+    GAxpy2D<T> aa{};
+    for (int k = 0; k < g.nmem; ++k) {
+        a.p[k] = y1[k];
+        b.p[k] = y2[k];
+        for (int v = 0; v < nv; ++v) vl.v[v][k] = xs[(size_t)v * g.nmem + k];
+    }
+    for (int i = 0; i < g.nsys; ++i) {
+        for (int v = 0; v < nv; ++v) {
+            aa.c1[v * NSYS_MAX + i] = (T)c1[(size_t)v * g.nsys + i];
+            aa.c2[v * NSYS_MAX + i] = (T)c2[(size_t)v * g.nsys + i];
+        }
+        aa.c21[i] = (T)c21[i];
+        aa.post1[i] = (T)post1[i];
+        aa.post2[i] = (T)post2[i];
+        aa.write1[i] = write1[i];
+    }
+    const cudaError_t e = launch_pdl(k_gaxpy2<T>, dim3(axpy_blocks(g, 256), g.nsys), dim3(256), 0,
+                                     s, nv, vl, a, b, aa, mem_of(g), sys_of(g));
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int nrhs,
-                             long long len, T *y, cudaStream_t s, const double *post) {
-    if (nv > MAXV || nrhs > NRHS_MAX || nv < 0) return cudaErrorInvalidValue;
+cudaError_t launch_gaxpy(const GLaunch &g, int nv, const T *const *xs, const double *coef,
+                         T *const *y, const double *post, cudaStream_t s) {
+    if (!group_ok(g, nv)) return cudaErrorInvalidValue;
+    for (int i = 0; i < g.nsys; ++i)
+        if (g.snv[i] < 0 || g.snv[i] > nv) return cudaErrorInvalidValue;
     if (nv == 0 && !post) return cudaSuccess;
-    AxpyArgs<T> aa;
-    for (int v = 0; v < nv; ++v) {
-        aa.x[v] = xs[v];
-        for (int r = 0; r < nrhs; ++r) aa.coef[v * NRHS_MAX + r] = (T)coef[v * nrhs + r];
+    GVecD<T> vl{};
+    GTgtD<T> ty{};
+    GAxpyD<T> aa{};
+    GMemD gm = mem_of(g);
+    for (int k = 0; k < g.nmem; ++k) {
+        ty.p[k] = y[k];
+        int nvk = 0;  // vectors member k's systems use
+        for (int i = 0; i < g.nsys; ++i)
+            if (g.sm[i] == k && g.snv[i] > nvk) nvk = g.snv[i];
+        int vec2 = (g.len[k] % 2 == 0) && al2<T>(y[k]);
+        for (int v = 0; v < nv; ++v) {
+            vl.v[v][k] = xs[(size_t)v * g.nmem + k];
+            if (v < nvk) vec2 = vec2 && al2<T>(vl.v[v][k]);
+        }
+        gm.vec[k] = vec2;
     }
-    for (int r = 0; r < nrhs; ++r) aa.post[r] = post ? (T)post[r] : T(1);
-    const bool al = sizeof(T) == 8 ? aligned16(y) : ((reinterpret_cast<uintptr_t>(y) & 7u) == 0);
-    int vec2 = (len % 2 == 0) && al;
-    for (int v = 0; v < nv; ++v)
-        vec2 = vec2 && (sizeof(T) == 8 ? aligned16(xs[v])
-                                       : ((reinterpret_cast<uintptr_t>(xs[v]) & 7u) == 0));
-    long long bx = (len + 511) / 512;
-    const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
-    if (bx > cap) bx = cap;
-    if (bx < 1) bx = 1;
-    const cudaError_t e = launch_pdl(k_multiaxpy<T>, dim3((unsigned)bx, (unsigned)nrhs),
-                                     dim3(256), 0, s, nv, aa, len, y, vec2);
+    for (int i = 0; i < g.nsys; ++i) {
+        for (int v = 0; v < nv; ++v) aa.coef[v * NSYS_MAX + i] = (T)coef[(size_t)v * g.nsys + i];
+        aa.post[i] = post ? (T)post[i] : T(1);
+    }
+    const cudaError_t e = launch_pdl(k_gaxpy<T>, dim3(axpy_blocks(g, 512), g.nsys), dim3(256), 0,
+                                     s, vl, ty, aa, gm, sys_of(g));
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -550,27 +653,21 @@ template cudaError_t launch_convert<double, float>(const double *, float *, long
 template cudaError_t launch_convert<float, double>(const float *, double *, long long, cudaStream_t);
 template cudaError_t launch_convert<double, double>(const double *, double *, long long, cudaStream_t);
 template cudaError_t launch_zero<double>(double *, long long, cudaStream_t);
-template cudaError_t launch_multidot<double>(int, const double *const *, const double *, int,
-                                             long long, double *, int, double *, cudaStream_t);
-template cudaError_t launch_multidot<float>(int, const float *const *, const float *, int,
-                                            long long, double *, int, double *, cudaStream_t);
-template cudaError_t launch_multiaxpy<double>(int, const double *const *, const double *, int,
-                                              long long, double *, cudaStream_t, const double *);
-template cudaError_t launch_multiaxpy<float>(int, const float *const *, const double *, int,
-                                             long long, float *, cudaStream_t, const double *);
 template cudaError_t launch_zero<float>(float *, long long, cudaStream_t);
-template cudaError_t launch_gram2<float>(int, const float *const *, const float *, const float *,
-                                         int, long long, double *, int, double *, cudaStream_t);
-template cudaError_t launch_gram2<double>(int, const double *const *, const double *,
-                                          const double *, int, long long, double *, int,
-                                          double *, cudaStream_t);
-template cudaError_t launch_axpy2<float>(int, const float *const *, const double *,
-                                         const double *, const double *, const double *,
-                                         const double *, int, long long, float *, float *, int,
-                                         cudaStream_t);
-template cudaError_t launch_axpy2<double>(int, const double *const *, const double *,
-                                          const double *, const double *, const double *,
-                                          const double *, int, long long, double *, double *,
-                                          int, cudaStream_t);
+#define ST_GVEC(T)                                                                             \
+    template cudaError_t launch_gdot<T>(const GLaunch &, int, const T *const *, const T *const *, \
+                                        double *, cudaStream_t);                                  \
+    template cudaError_t launch_ggram2<T>(const GLaunch &, int, const T *const *,                \
+                                          const T *const *, const T *const *, double *,           \
+                                          cudaStream_t);                                          \
+    template cudaError_t launch_gaxpy<T>(const GLaunch &, int, const T *const *, const double *,  \
+                                         T *const *, const double *, cudaStream_t);               \
+    template cudaError_t launch_gaxpy2<T>(const GLaunch &, int, const T *const *, const double *, \
+                                          const double *, const double *, const double *,         \
+                                          const double *, T *const *, T *const *, const int *,    \
+                                          cudaStream_t);
+ST_GVEC(float)
+ST_GVEC(double)
+#undef ST_GVEC
 
 }  // namespace st

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -200,11 +201,10 @@ struct st_handle_s {
     double *r64 = nullptr;
     float *rhs32 = nullptr, *e32 = nullptr;
     int krylov32_m = 0;
-    double *partial = nullptr;
-    // page-locked, mapped host buffer the final reduction of the dot products
-    // writes into directly: reading a Krylov step's dots then takes no copy
-    // engine, so it never waits behind a large transfer on another stream
-    double *dots_host = nullptr, *dots_host_dev = nullptr;
+    double *partial = nullptr, *dots = nullptr;
+    // page-locked host block the reduced dot products are copied into (one
+    // DMA, no staging through pageable memory)
+    double *dots_host = nullptr;
     size_t dots_host_cap = 0;
     int nblk_dot = 0;
     int krylov_m = 0;
@@ -213,12 +213,27 @@ struct st_handle_s {
     // iteration or refinement step (st_solve_history)
     std::vector<std::pair<int, double>> hist;
     bool record_hist = false;  // set while the outer iteration runs
+    // host synchronisations for reductions and Krylov vector-kernel launches
+    // of the current solve (a group's operations count on its first member)
+    long long n_sync = 0, n_vl = 0;
     // st_solve_host: two device staging slots per vector (allocated on first
     // use), the copy-in and copy-out streams, and per slot the events "copied
     // in", "solved" and "copied out"
     double *hs_f[2] = {nullptr, nullptr}, *hs_u[2] = {nullptr, nullptr};
     cudaStream_t cp_in = nullptr, cp_out = nullptr;
     cudaEvent_t hs_in[2] = {}, hs_solved[2] = {}, hs_out[2] = {};
+    // solutions still to be copied back to the host: issued in chunks at the
+    // solve's host synchronisation points, one chunk in flight at a time (a
+    // device-to-host transfer delays the solve's own small reads behind it)
+    struct BgCopy {
+        double *dst;
+        const double *src;
+        size_t n, done;
+        int slot;
+    };
+    std::deque<BgCopy> bg;
+    cudaEvent_t bg_ev = nullptr;  // the last chunk issued
+    cudaError_t bg_err = cudaSuccess;
 };
 
 namespace {
@@ -1285,25 +1300,25 @@ int vcycle(st_handle h, int l, T *u, const T *f, bool zero_init) {
 }
 
 // y_r = post_r (y_r + sum_v coef[v*R + r] x_v), in chunks of MAXV vectors
+GLaunch solo_launch(st_handle h);
+
 template <typename T>
 int vaxpy(st_handle h, int nv, const T *const *xs, const double *coef, T *y,
           const double *post = nullptr) {
     const int R = h->nrhs;
+    GLaunch g = solo_launch(h);
+    T *const y1[1] = {y};
     int v0 = 0;
     do {
         const int cnt = std::min(MAXV, nv - v0);
         const bool last = v0 + cnt >= nv;
+        for (int r = 0; r < R; ++r) g.snv[r] = cnt;
         KScope ks(h, ST_PROF_VECTOR, sizeof(T) * (cnt + 2.0) * h->len * R, 2.0 * cnt * h->len * R);
-        CK(launch_multiaxpy<T>(cnt, xs ? xs + v0 : nullptr, coef ? coef + (size_t)v0 * R : nullptr,
-                               R, h->len, y, h->stream, last ? post : nullptr));
+        CK(launch_gaxpy<T>(g, cnt, xs ? xs + v0 : nullptr, coef ? coef + (size_t)v0 * R : nullptr,
+                           y1, last ? post : nullptr, h->stream));
+        ++h->n_vl;
         v0 += cnt;
     } while (v0 < nv);
-    return ST_OK;
-}
-
-int vscale(st_handle h, const double *x, double *y, const double *a) {
-    KScope ks(h, ST_PROF_VECTOR, 16.0 * h->len * h->nrhs, 1.0 * h->len * h->nrhs);
-    CK(launch_scale(x, y, a, h->nrhs, h->len, h->stream));
     return ST_OK;
 }
 
@@ -1486,7 +1501,6 @@ int precondition_spectral(st_handle h, const double *v, double *z);
 template <>
 int precondition_spectral<double>(st_handle h, const double *v, double *z) {
     Work<double> &w = h->w64;
-    DevSpace<double> &ds = h->s64;
     const long long planes = (long long)h->N * h->nrhs * h->nt;
     double *fh = nullptr, *e = nullptr;
     CKS(spatial<double>(h, v, w.w0, w.w1, true, planes, &fh));
@@ -1501,7 +1515,6 @@ int precondition_spectral<double>(st_handle h, const double *v, double *z) {
 // z = V-cycle(v) with zero initial guess, FP64 at the interface
 int precondition_spectral_f32(st_handle h, const double *v, double *z) {
     Work<float> &w = h->w32;
-    DevSpace<float> &ds = h->s32;
     const long long planes = (long long)h->N * h->nrhs * h->nt;
     CKS((vconvert<double, float>(h, v, w.w0)));
     float *fh = nullptr, *e = nullptr;
@@ -1596,43 +1609,88 @@ int run_graphed(st_handle h, const void *in, void *out, Fn fn) {
     return ST_OK;
 }
 
-// Small page-locked, mapped host blocks, kept for reuse by later handles
-// instead of being freed (cudaFreeHost may wait for the whole device, which
-// would stall every other stream of a serving process)
-std::mutex g_mapped_mu;
-std::multimap<size_t, void *> g_mapped_free;  // capacity in bytes -> block
+// Small page-locked host blocks, kept for reuse by later handles instead of
+// being freed (cudaFreeHost may wait for the whole device, which would stall
+// every other stream of a serving process)
+std::mutex g_pinned_mu;
+std::multimap<size_t, void *> g_pinned_free;  // capacity in bytes -> block
 
-void mapped_put(void *p, size_t bytes) {
+void pinned_put(void *p, size_t bytes) {
     if (!p) return;
-    std::lock_guard<std::mutex> lock(g_mapped_mu);
-    g_mapped_free.emplace(bytes, p);
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    g_pinned_free.emplace(bytes, p);
 }
 
-// the mapped host buffer for count reduced values (grown on demand; the
+// the page-locked host buffer for count reduced values (grown on demand; the
 // stream is idle whenever this runs, every reader synchronises it first)
 int host_dots(st_handle h, size_t count) {
     if (count <= h->dots_host_cap) return ST_OK;
     size_t bytes = 4096;
     while (bytes < count * sizeof(double)) bytes <<= 1;
-    mapped_put(h->dots_host, h->dots_host_cap * sizeof(double));
-    h->dots_host = h->dots_host_dev = nullptr;
+    pinned_put(h->dots_host, h->dots_host_cap * sizeof(double));
+    h->dots_host = nullptr;
     h->dots_host_cap = 0;
-    void *p = nullptr, *pd = nullptr;
+    void *p = nullptr;
     {
-        std::lock_guard<std::mutex> lock(g_mapped_mu);
-        auto it = g_mapped_free.lower_bound(bytes);
-        if (it != g_mapped_free.end()) {
+        std::lock_guard<std::mutex> lock(g_pinned_mu);
+        auto it = g_pinned_free.lower_bound(bytes);
+        if (it != g_pinned_free.end()) {
             bytes = it->first;
             p = it->second;
-            g_mapped_free.erase(it);
+            g_pinned_free.erase(it);
         }
     }
-    if (!p) CK(cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable));
+    if (!p) CK(cudaHostAlloc(&p, bytes, cudaHostAllocPortable));
     h->dots_host = (double *)p;
     h->dots_host_cap = bytes / sizeof(double);
-    CK(cudaHostGetDevicePointer(&pd, p, 0));
-    h->dots_host_dev = (double *)pd;
     return ST_OK;
+}
+
+// the handle's right-hand sides as a group launch of one member: every
+// Krylov vector kernel of a single handle runs the group kernels, so a system
+// gets the same arithmetic alone and in a group (st_solve_group)
+GLaunch solo_launch(st_handle h) {
+    GLaunch g;
+    g.nmem = 1;
+    g.nsys = h->nrhs;
+    g.nblk = h->nblk_dot;
+    g.len[0] = h->len;
+    g.R[0] = h->nrhs;
+    g.part[0] = h->partial;
+    for (int r = 0; r < h->nrhs; ++r) g.sr[r] = r;
+    return g;
+}
+
+// doubles per chunk of a solution copied back by st_solve_host (256 MB:
+// about 1.3 ms of the host link, under one Krylov step of a large solve)
+constexpr size_t kBgChunk = (size_t)32 << 20;
+
+// Issue the next chunk of the pending solution copies if the previous one
+// has completed (all: issue everything now).  Errors are kept for the caller
+// of st_solve_host.
+void bg_pump(st_handle h, bool all = false) {
+    while (!h->bg.empty() && h->bg_err == cudaSuccess) {
+        if (!all) {
+            const cudaError_t q = cudaEventQuery(h->bg_ev);
+            if (q == cudaErrorNotReady) return;
+            if (q != cudaSuccess) {
+                h->bg_err = q;
+                return;
+            }
+        }
+        auto &c = h->bg.front();
+        const size_t n = all ? c.n - c.done : std::min(kBgChunk, c.n - c.done);
+        cudaError_t e = cudaMemcpyAsync(c.dst + c.done, c.src + c.done, n * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->cp_out);
+        if (e == cudaSuccess) e = cudaEventRecord(h->bg_ev, h->cp_out);
+        c.done += n;
+        if (e == cudaSuccess && c.done == c.n) {
+            e = cudaEventRecord(h->hs_out[c.slot], h->cp_out);
+            h->bg.pop_front();
+        }
+        if (e != cudaSuccess) h->bg_err = e;
+        if (!all) return;
+    }
 }
 
 // per-rhs dots of vecs[0..nv) with w -> host out[v*nrhs + r] (FP64 sums)
@@ -1640,15 +1698,23 @@ template <typename T>
 int dots(st_handle h, int nv, const T *const *vecs, const T *w, std::vector<double> &out) {
     const size_t cnt_all = (size_t)nv * h->nrhs;
     CKS(host_dots(h, cnt_all));
+    const GLaunch g = solo_launch(h);
+    const T *const w1[1] = {w};
     for (int v0 = 0; v0 < nv; v0 += MAXV) {
         const int cnt = std::min(MAXV, nv - v0);
-        KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 1.0) * h->len * h->nrhs,
-                  2.0 * cnt * h->len * h->nrhs);
-        CK(launch_multidot<T>(cnt, vecs + v0, w, h->nrhs, h->len, h->partial, h->nblk_dot,
-                              h->dots_host_dev + (size_t)v0 * h->nrhs, h->stream));
+        {
+            KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 1.0) * h->len * h->nrhs,
+                      2.0 * cnt * h->len * h->nrhs);
+            CK(launch_gdot<T>(g, cnt, vecs + v0, w1, h->dots, h->stream));
+        }
+        ++h->n_vl;
+        CK(cudaMemcpyAsync(h->dots_host + (size_t)v0 * h->nrhs, h->dots,
+                           sizeof(double) * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    ++h->n_sync;
     out.assign(h->dots_host, h->dots_host + cnt_all);
+    bg_pump(h);
     if (h->part) CKS(comm_allreduce(h, out));
     if (h->recs.size() > 2048) prof_fold(h);
     return ST_OK;
@@ -1672,15 +1738,23 @@ int gram2s(st_handle h, int nv, const T *const *vecs, const T *t1, const T *t2,
            std::vector<double> &out) {
     const size_t cnt_all = (size_t)2 * nv * h->nrhs;
     CKS(host_dots(h, cnt_all));
+    const GLaunch g = solo_launch(h);
+    const T *const a1[1] = {t1}, *const a2[1] = {t2};
     for (int v0 = 0; v0 < nv; v0 += MAXV) {
         const int cnt = std::min(MAXV, nv - v0);
-        KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 2.0) * h->len * h->nrhs,
-                  4.0 * cnt * h->len * h->nrhs);
-        CK(launch_gram2<T>(cnt, vecs + v0, t1, t2, h->nrhs, h->len, h->partial, h->nblk_dot,
-                           h->dots_host_dev + (size_t)2 * v0 * h->nrhs, h->stream));
+        {
+            KScope ks(h, ST_PROF_DOT, sizeof(T) * (cnt + 2.0) * h->len * h->nrhs,
+                      4.0 * cnt * h->len * h->nrhs);
+            CK(launch_ggram2<T>(g, cnt, vecs + v0, a1, a2, h->dots, h->stream));
+        }
+        ++h->n_vl;
+        CK(cudaMemcpyAsync(h->dots_host + (size_t)2 * v0 * h->nrhs, h->dots,
+                           sizeof(double) * 2 * cnt * h->nrhs, cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    ++h->n_sync;
     out.assign(h->dots_host, h->dots_host + cnt_all);
+    bg_pump(h);
     if (h->part) CKS(comm_allreduce(h, out));
     if (h->recs.size() > 2048) prof_fold(h);
     return ST_OK;
@@ -1885,11 +1959,311 @@ int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vecto
     return ST_OK;
 }
 
+// ---- groups of handles (st_solve_group; one handle = a group of one) -------
+//
+// Members keep their own vectors, operators and preconditioner graphs; the
+// group runs their Krylov iterations in lockstep.  Per-member work (operator,
+// V-cycle, transforms, residual) is issued on the member's stream; each
+// Krylov vector operation of the members taking part is one group launch on
+// the group stream (member 0's), ordered after the members' work by events;
+// a reduction is read back once for the whole group.
+struct Grp {
+    std::vector<st_handle> hs;
+    std::vector<int> first;            // first system of member k
+    int S = 0;                         // systems (right-hand sides) in all
+    cudaStream_t G = nullptr;          // group stream
+    std::vector<cudaStream_t> own;     // members' streams before the call
+    std::vector<cudaEvent_t> ev;       // member k's last work
+    cudaEvent_t evg = nullptr;         // the group stream's last work
+    bool forked = false;               // members 1.. run on streams of their own
+};
+
+// Streams and events the group fans out on, per host thread and device
+// (created once, kept for the thread's later groups)
+struct ForkPool {
+    int dev = -1;
+    std::vector<cudaStream_t> s;
+    std::vector<cudaEvent_t> e;
+};
+thread_local ForkPool t_fork;
+
+int fork_pool(int nstreams, int nevents) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (t_fork.dev != dev) {  // the old device's objects stay with it
+        t_fork = ForkPool();
+        t_fork.dev = dev;
+    }
+    while ((int)t_fork.s.size() < nstreams) {
+        cudaStream_t st;
+        CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        t_fork.s.push_back(st);
+    }
+    while ((int)t_fork.e.size() < nevents) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        t_fork.e.push_back(e);
+    }
+    return ST_OK;
+}
+
+// Members 1.. move to streams of their own (after the work already queued on
+// their own and the group stream); a single member stays on its stream.
+int grp_begin(Grp &g, bool fork) {
+    const int M = (int)g.hs.size();
+    g.first.assign(M, 0);
+    g.S = 0;
+    for (int k = 0; k < M; ++k) {
+        g.first[k] = g.S;
+        g.S += g.hs[k]->nrhs;
+    }
+    g.G = g.hs[0]->stream;
+    g.own.resize(M);
+    for (int k = 0; k < M; ++k) g.own[k] = g.hs[k]->stream;
+    g.forked = fork && M > 1;
+    if (!g.forked) return ST_OK;
+    CKS(fork_pool(M - 1, M + 1));
+    g.ev.assign(t_fork.e.begin(), t_fork.e.begin() + M);
+    g.evg = t_fork.e[M];
+    CK(cudaEventRecord(g.evg, g.G));
+    for (int k = 1; k < M; ++k) {
+        cudaStream_t st = t_fork.s[k - 1];
+        CK(cudaStreamWaitEvent(st, g.evg, 0));
+        CK(cudaEventRecord(g.ev[k], g.own[k]));
+        CK(cudaStreamWaitEvent(st, g.ev[k], 0));
+        g.hs[k]->stream = st;
+    }
+    return ST_OK;
+}
+
+// the group stream waits for the work of the members in mask
+int grp_join(Grp &g, const std::vector<char> &mask) {
+    if (!g.forked) return ST_OK;
+    for (size_t k = 1; k < g.hs.size(); ++k)
+        if (mask[k]) {
+            CK(cudaEventRecord(g.ev[k], g.hs[k]->stream));
+            CK(cudaStreamWaitEvent(g.G, g.ev[k], 0));
+        }
+    return ST_OK;
+}
+
+// the members in mask wait for the group stream's work
+int grp_fork(Grp &g, const std::vector<char> &mask) {
+    if (!g.forked) return ST_OK;
+    CK(cudaEventRecord(g.evg, g.G));
+    for (size_t k = 1; k < g.hs.size(); ++k)
+        if (mask[k]) CK(cudaStreamWaitEvent(g.hs[k]->stream, g.evg, 0));
+    return ST_OK;
+}
+
+// every member's work done, streams handed back, group stream synchronised
+int grp_end(Grp &g) {
+    std::vector<char> all(g.hs.size(), 1);
+    const int rc = grp_join(g, all);
+    for (size_t k = 0; k < g.hs.size(); ++k) g.hs[k]->stream = g.own[k];
+    if (rc != ST_OK) return rc;
+    CK(cudaStreamSynchronize(g.G));
+    return ST_OK;
+}
+
+// the launch over the systems of the members in mask; sys[i] = the group
+// system index of launch system i
+GLaunch grp_launch(const Grp &g, const std::vector<char> &mask, std::vector<int> &sys) {
+    GLaunch L;
+    sys.clear();
+    L.nblk = g.hs[0]->nblk_dot;
+    for (size_t k = 0; k < g.hs.size(); ++k) {
+        if (!mask[k]) continue;
+        st_handle h = g.hs[k];
+        const int kk = L.nmem++;
+        L.len[kk] = h->len;
+        L.R[kk] = h->nrhs;
+        L.part[kk] = h->partial;
+        for (int r = 0; r < h->nrhs; ++r) {
+            L.sm[L.nsys] = kk;
+            L.sr[L.nsys] = r;
+            ++L.nsys;
+            sys.push_back(g.first[k] + r);
+        }
+    }
+    return L;
+}
+
+// Vector v of member k: vec(v, k).  Members outside mask get no entry.
+template <typename T, class Vec>
+std::vector<const T *> grp_vecs(const Grp &g, const std::vector<char> &mask, int v0, int nv,
+                                Vec vec) {
+    std::vector<const T *> out;
+    int nm = 0;
+    for (size_t k = 0; k < g.hs.size(); ++k) nm += mask[k] ? 1 : 0;
+    out.resize((size_t)nv * nm);
+    int kk = 0;
+    for (size_t k = 0; k < g.hs.size(); ++k) {
+        if (!mask[k]) continue;
+        for (int v = 0; v < nv; ++v) out[(size_t)v * nm + kk] = vec(v0 + v, (int)k);
+        ++kk;
+    }
+    return out;
+}
+
+// out[v * S + s] (group systems; zero for members outside mask) = dot of
+// vector v with the target over system s, or with rows = 2 the Gram pairs
+// out[(2 v + t) * S + s] with targets t1, t2
+template <typename T, class Vec, class Tgt1, class Tgt2>
+int grp_reduce(Grp &g, const std::vector<char> &mask, int nv, Vec vec, Tgt1 t1, Tgt2 t2, int rows,
+               std::vector<double> &out) {
+    st_handle h0 = g.hs[0];
+    std::vector<int> sys;
+    const GLaunch L = grp_launch(g, mask, sys);
+    out.assign((size_t)rows * nv * g.S, 0.0);
+    if (L.nsys == 0) return ST_OK;
+    CKS(grp_join(g, mask));
+    CKS(host_dots(h0, (size_t)rows * nv * L.nsys));
+    std::vector<const T *> a, b;
+    for (size_t k = 0; k < g.hs.size(); ++k)
+        if (mask[k]) {
+            a.push_back(t1((int)k));
+            b.push_back(t2((int)k));
+        }
+    double bytes = 0.0;
+    for (size_t k = 0; k < g.hs.size(); ++k)
+        if (mask[k]) bytes += (double)g.hs[k]->len * g.hs[k]->nrhs;
+    for (int v0 = 0; v0 < nv; v0 += MAXV) {
+        const int cnt = std::min(MAXV, nv - v0);
+        const std::vector<const T *> xs = grp_vecs<T>(g, mask, v0, cnt, vec);
+        {
+            KScope ks(h0, ST_PROF_DOT, sizeof(T) * (cnt + rows) * bytes, 2.0 * rows * cnt * bytes);
+            if (rows == 1)
+                CK(launch_gdot<T>(L, cnt, xs.data(), a.data(), h0->dots, g.G));
+            else
+                CK(launch_ggram2<T>(L, cnt, xs.data(), a.data(), b.data(), h0->dots, g.G));
+        }
+        ++h0->n_vl;
+        CK(cudaMemcpyAsync(h0->dots_host + (size_t)rows * v0 * L.nsys, h0->dots,
+                           sizeof(double) * rows * cnt * L.nsys, cudaMemcpyDeviceToHost, g.G));
+    }
+    CK(cudaStreamSynchronize(g.G));
+    ++h0->n_sync;
+    for (int row = 0; row < rows * nv; ++row)
+        for (int i = 0; i < L.nsys; ++i)
+            out[(size_t)row * g.S + sys[i]] = h0->dots_host[(size_t)row * L.nsys + i];
+    bg_pump(h0);
+    // a slab-partitioned handle (only ever alone in its group): sum the
+    // ranks' partial dots, as the single-handle reductions do
+    if (h0->part) CKS(comm_allreduce(h0, out));
+    if (h0->recs.size() > 2048) prof_fold(h0);
+    return ST_OK;
+}
+
+// per-system norms of vector vec(0, k) (group systems of members in mask)
+template <typename T, class Vec>
+int grp_norms(Grp &g, const std::vector<char> &mask, Vec vec, std::vector<double> &nr) {
+    std::vector<double> d;
+    auto tgt = [&](int k) { return vec(0, k); };
+    CKS((grp_reduce<T>(g, mask, 1, vec, tgt, tgt, 1, d)));
+    nr.assign(g.S, 0.0);
+    for (int q = 0; q < g.S; ++q) nr[q] = std::isnan(d[q]) ? d[q] : std::sqrt(std::max(0.0, d[q]));
+    return ST_OK;
+}
+
+// y_s <- post_s (y_s + sum_{v < nvm[k]} coef[v * S + s] x_v) for the members
+// in mask (nvm: vectors per member, <= nv; post may be NULL)
+template <typename T, class Vec, class Tgt>
+int grp_axpy(Grp &g, const std::vector<char> &mask, int nv, const std::vector<int> &nvm, Vec vec,
+             const double *coef, Tgt y, const double *post) {
+    st_handle h0 = g.hs[0];
+    std::vector<int> sys;
+    GLaunch L = grp_launch(g, mask, sys);
+    if (L.nsys == 0) return ST_OK;
+    CKS(grp_join(g, mask));
+    std::vector<T *> ys;
+    double bytes = 0.0;
+    for (size_t k = 0; k < g.hs.size(); ++k)
+        if (mask[k]) {
+            ys.push_back(y((int)k));
+            bytes += (double)g.hs[k]->len * g.hs[k]->nrhs;
+        }
+    std::vector<int> mk;  // group member of launch member kk
+    for (size_t k = 0; k < g.hs.size(); ++k)
+        if (mask[k]) mk.push_back((int)k);
+    int v0 = 0;
+    do {
+        const int cnt = std::min(MAXV, nv - v0);
+        const bool last = v0 + cnt >= nv;
+        std::vector<double> c((size_t)std::max(cnt, 1) * L.nsys, 0.0), p(L.nsys, 1.0);
+        for (int i = 0; i < L.nsys; ++i) {
+            const int k = mk[L.sm[i]];
+            L.snv[i] = std::max(0, std::min(cnt, nvm[k] - v0));
+            for (int v = 0; v < L.snv[i]; ++v)
+                c[(size_t)v * L.nsys + i] = coef[(size_t)(v0 + v) * g.S + sys[i]];
+            if (post) p[i] = post[sys[i]];
+        }
+        const std::vector<const T *> xs = grp_vecs<T>(g, mask, v0, cnt, vec);
+        {
+            KScope ks(h0, ST_PROF_VECTOR, sizeof(T) * (cnt + 2.0) * bytes, 2.0 * cnt * bytes);
+            CK(launch_gaxpy<T>(L, cnt, xs.data(), c.data(), ys.data(),
+                               (last && post) ? p.data() : nullptr, g.G));
+        }
+        ++h0->n_vl;
+        v0 += cnt;
+    } while (v0 < nv);
+    return grp_fork(g, mask);
+}
+
+// the delayed Gram-Schmidt two-output update for the members in mask
+// (coefficients [v * S + s], scalars [s], group system order)
+template <typename T, class Vec, class Tgt1, class Tgt2>
+int grp_axpy2(Grp &g, const std::vector<char> &mask, int nv, Vec vec, const std::vector<double> &c1,
+              const std::vector<double> &c2, const std::vector<double> &c21,
+              const std::vector<double> &p1, const std::vector<double> &p2,
+              const std::vector<int> &write1, Tgt1 y1, Tgt2 y2) {
+    st_handle h0 = g.hs[0];
+    std::vector<int> sys;
+    const GLaunch L = grp_launch(g, mask, sys);
+    if (L.nsys == 0) return ST_OK;
+    CKS(grp_join(g, mask));
+    std::vector<T *> a, b;
+    double bytes = 0.0;
+    for (size_t k = 0; k < g.hs.size(); ++k)
+        if (mask[k]) {
+            a.push_back(y1((int)k));
+            b.push_back(y2((int)k));
+            bytes += (double)g.hs[k]->len * g.hs[k]->nrhs;
+        }
+    const int n = L.nsys;
+    std::vector<double> d1((size_t)std::max(nv, 1) * n), d2((size_t)std::max(nv, 1) * n), d21(n),
+        q1(n), q2(n);
+    std::vector<int> w1(n);
+    for (int i = 0; i < n; ++i) {
+        const int s = sys[i];
+        for (int v = 0; v < nv; ++v) {
+            d1[(size_t)v * n + i] = c1[(size_t)v * g.S + s];
+            d2[(size_t)v * n + i] = c2[(size_t)v * g.S + s];
+        }
+        d21[i] = c21[s];
+        q1[i] = p1[s];
+        q2[i] = p2[s];
+    }
+    std::vector<int> mk;
+    for (size_t k = 0; k < g.hs.size(); ++k)
+        if (mask[k]) mk.push_back((int)k);
+    for (int i = 0; i < n; ++i) w1[i] = write1[mk[L.sm[i]]];
+    const std::vector<const T *> xs = grp_vecs<T>(g, mask, 0, nv, vec);
+    {
+        KScope ks(h0, ST_PROF_VECTOR, sizeof(T) * (nv + 4.0) * bytes, 4.0 * (nv + 1) * bytes);
+        CK(launch_gaxpy2<T>(L, nv, xs.data(), d1.data(), d2.data(), d21.data(), q1.data(),
+                            q2.data(), a.data(), b.data(), w1.data(), g.G));
+    }
+    ++h0->n_vl;
+    return grp_fork(g, mask);
+}
+
 // Flexible GMRES(m) with classical Gram-Schmidt and DELAYED
 // reorthogonalisation (the low-synchronisation scheme of Swirydowicz et al.,
 // "Low synchronization Gram-Schmidt and GMRES algorithms", and Bielich et
 // al., "Low-synch Gram-Schmidt with delayed reorthogonalization for Krylov
-// solvers"): basis vector j enters step j once-orthogonalised (q~_j); one
+// solvers") on T vectors for every member k in mem, right-preconditioned by
+// prec(k, v, z): basis vector j enters step j once-orthogonalised (q~_j); one
 // Gram pass over [q_0 .. q_{j-1}, q~_j, w] with the two targets q~_j and
 // w = A M^{-1} q~_j gives both the second pass of q~_j (a = Q^T q~_j,
 // rho = sqrt(q~_j.q~_j - |a|^2), q_j = (q~_j - Q a) / rho) and the first pass
@@ -1901,41 +2275,68 @@ int fgmres_core(st_handle h, const T *b, T *x, double tol, int maxit, std::vecto
 // z actually used), so preconditioning q~_j instead of q_j is exact.  One
 // host synchronisation and two passes over the basis per step (CGS2 takes
 // two synchronisations and four passes).  Every decision is taken per
-// right-hand side, so a batch gives each rhs its single-rhs result.
-template <typename T, class Apply, class Res, class Prec>
-int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vector<T *> &V,
-                 std::vector<T *> &Zk, Apply apply, Res resid, Prec prec,
-                 const std::vector<char> &skip, int *its, double *worst_out) {
-    const int m = (int)Zk.size(), R = h->nrhs;
+// right-hand side and every loop bound per member, so each system gets its
+// single-handle (and single-rhs) result; a member that is done waits for the
+// others without further work.  b(k), x(k): member k's right-hand side and
+// iterate; V(j, k), Z(j, k): its basis; tol, maxit, its, worst per member;
+// skip per group system.
+template <typename T, class VB, class VX, class VV, class VZ, class Apply, class Res, class Prec>
+int fgmres_group(Grp &g, const std::vector<char> &mem, VB b, VX x, VV V, VZ Zk, int m,
+                 const std::vector<double> &tolm, const std::vector<int> &maxit, Apply apply,
+                 Res resid, Prec prec, const std::vector<char> &skip, std::vector<int> &its,
+                 std::vector<double> &worst) {
+    const int M = (int)g.hs.size(), S = g.S;
     const size_t ld = (size_t)m + 1;
+    std::vector<int> mq(S);
+    for (int k = 0; k < M; ++k)
+        for (int r = 0; r < g.hs[k]->nrhs; ++r) mq[g.first[k] + r] = k;
+    auto V0 = [&](int, int k) { return (const T *)V(0, k); };
+    auto Bv = [&](int, int k) { return (const T *)b(k); };
     std::vector<double> nb, beta, G;
-    CKS(norms<T>(h, b, nb));
-    CKS(check_finite_rhs(nb));
-    int total = 0;
-    double worst = 0.0;
-    std::vector<char> done(R, 0);
+    CKS(grp_norms<T>(g, mem, Bv, nb));
+    {
+        std::vector<double> chk;
+        for (int q = 0; q < S; ++q)
+            if (mem[mq[q]]) chk.push_back(nb[q]);
+        CKS(check_finite_rhs(chk));
+    }
+    std::vector<int> total(M, 0);
+    worst.assign(M, 0.0);
+    std::vector<char> live = mem, done(S, 0);
     while (true) {
-        CKS(resid(x, b, V[0]));
-        CKS(norms<T>(h, V[0], beta));
-        worst = 0.0;
-        for (int q = 0; q < R; ++q) {
-            const double rel = nb[q] > 0 ? beta[q] / nb[q] : 0.0;
-            done[q] = skip[q] || !(nb[q] > 0) || rel <= tol;
-            if (!skip[q]) worst = std::max(worst, rel);
+        for (int k = 0; k < M; ++k)
+            if (live[k]) CKS(resid(k, x(k), b(k), V(0, k)));
+        CKS(grp_norms<T>(g, live, V0, beta));
+        for (int k = 0; k < M; ++k) {
+            if (!live[k]) continue;
+            double wk = 0.0;
+            for (int q = g.first[k]; q < g.first[k] + g.hs[k]->nrhs; ++q) {
+                const double rel = nb[q] > 0 ? beta[q] / nb[q] : 0.0;
+                done[q] = skip[q] || !(nb[q] > 0) || rel <= tolm[k];
+                if (!skip[q]) wk = std::max(wk, rel);
+            }
+            worst[k] = wk;
+            if (g.hs[k]->record_hist) g.hs[k]->hist.emplace_back(total[k], wk);
+            if (wk <= tolm[k] || total[k] >= maxit[k]) live[k] = 0;
         }
-        if (h->record_hist) h->hist.emplace_back(total, worst);
-        if (worst <= tol || total >= maxit) break;
+        bool anylive = false;
+        for (int k = 0; k < M; ++k) anylive = anylive || live[k];
+        if (!anylive) break;
         {
-            std::vector<double> sc(R);
-            for (int q = 0; q < R; ++q) sc[q] = (!done[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
-            CKS(vaxpy<T>(h, 0, nullptr, nullptr, V[0], sc.data()));
+            std::vector<double> sc(S, 0.0);
+            for (int q = 0; q < S; ++q)
+                if (live[mq[q]]) sc[q] = (!done[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
+            std::vector<int> nv0(M, 0);
+            auto Vw = [&](int k) { return V(0, k); };
+            CKS((grp_axpy<T>(g, live, 0, nv0, V0, nullptr, Vw, sc.data())));
         }
-        std::vector<double> H((size_t)R * ld * m, 0.0), cs((size_t)R * m), sn((size_t)R * m),
-            g((size_t)R * ld, 0.0), nu(R, 0.0);
-        std::vector<int> kq(R, 0);
-        std::vector<char> act(R), pend(R, 0);
-        for (int q = 0; q < R; ++q) {
-            g[(size_t)q * ld] = done[q] ? 0.0 : beta[q];
+        std::vector<double> H((size_t)S * ld * m, 0.0), cs((size_t)S * m), sn((size_t)S * m),
+            gv((size_t)S * ld, 0.0), nu(S, 0.0);
+        std::vector<int> kq(S, 0);
+        std::vector<char> act(S, 0), pend(S, 0);
+        for (int q = 0; q < S; ++q) {
+            if (!live[mq[q]]) continue;
+            gv[(size_t)q * ld] = done[q] ? 0.0 : beta[q];
             act[q] = !done[q];
         }
         // complete column col of rhs q with the second pass (a, rho) of the
@@ -1944,7 +2345,7 @@ int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vect
             double *c = &H[(size_t)q * ld * m + (size_t)col * ld];
             for (int i = 0; i <= col; ++i) c[i] += nu[q] * a[i];
             c[col + 1] = nu[q] * rho;
-            double *cq = &cs[(size_t)q * m], *sq = &sn[(size_t)q * m], *gq = &g[(size_t)q * ld];
+            double *cq = &cs[(size_t)q * m], *sq = &sn[(size_t)q * m], *gq = &gv[(size_t)q * ld];
             for (int i = 0; i < col; ++i) {
                 const double x0 = c[i], x1 = c[i + 1];
                 c[i] = cq[i] * x0 + sq[i] * x1;
@@ -1959,7 +2360,7 @@ int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vect
             gq[col] = cq[col] * gq[col];
             kq[q] = col + 1;
             pend[q] = 0;
-            if (std::fabs(gq[col + 1]) <= tol * nb[q] || rho == 0.0) act[q] = 0;
+            if (std::fabs(gq[col + 1]) <= tolm[mq[q]] * nb[q] || rho == 0.0) act[q] = 0;
         };
         // residual estimate if the pending column were completed with a = 0, rho = 1
         auto provisional = [&](int q, int col) {
@@ -1974,70 +2375,94 @@ int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vect
             }
             const double rad = std::hypot(c[col], c[col + 1]);
             const double s = rad > 0 ? c[col + 1] / rad : 0.0;
-            return std::fabs(s * g[(size_t)q * ld + col]);
+            return std::fabs(s * gv[(size_t)q * ld + col]);
         };
+        std::vector<char> cyc = live;  // members still in this cycle
         for (int j = 0;; ++j) {
             // (A) rhs whose pending column already meets the tolerance (or
-            // every pending rhs at the end of the cycle): second pass only
-            const bool last = (j == m) || total >= maxit;
-            std::vector<char> fin(R, 0);
+            // every pending rhs at the end of its member's cycle): second pass only
+            std::vector<char> last(M, 0), fm(M, 0), fin(S, 0);
+            for (int k = 0; k < M; ++k) last[k] = cyc[k] && ((j == m) || total[k] >= maxit[k]);
             bool anyfin = false;
-            for (int q = 0; q < R; ++q)
-                if (act[q] && pend[q] && (last || provisional(q, j - 1) <= tol * nb[q])) {
+            for (int q = 0; q < S; ++q) {
+                const int k = mq[q];
+                if (cyc[k] && act[q] && pend[q] &&
+                    (last[k] || provisional(q, j - 1) <= tolm[k] * nb[q])) {
                     fin[q] = 1;
+                    fm[k] = 1;
                     anyfin = true;
                 }
+            }
             if (anyfin) {
-                std::vector<const T *> vw(V.begin(), V.begin() + j + 1);
-                CKS(dots<T>(h, j + 1, vw.data(), V[j], G));
-                std::vector<double> c1((size_t)j * R, 0.0), p1(R, 1.0), a(j);
-                for (int q = 0; q < R; ++q) {
+                auto Vj = [&](int, int k) { return (const T *)V(j, k); };
+                auto Vi = [&](int i, int k) { return (const T *)V(i, k); };
+                CKS((grp_reduce<T>(g, fm, j + 1, Vi, [&](int k) { return Vj(0, k); },
+                                   [&](int k) { return Vj(0, k); }, 1, G)));
+                std::vector<double> c1((size_t)std::max(j, 1) * S, 0.0), p1(S, 1.0), a(j);
+                for (int q = 0; q < S; ++q) {
                     if (!fin[q]) continue;
                     double aa = 0.0;
                     for (int i = 0; i < j; ++i) {
-                        a[i] = G[(size_t)i * R + q];
+                        a[i] = G[(size_t)i * S + q];
                         aa += a[i] * a[i];
                     }
-                    const double rho = std::sqrt(std::max(G[(size_t)j * R + q] - aa, 0.0));
+                    const double rho = std::sqrt(std::max(G[(size_t)j * S + q] - aa, 0.0));
                     finish_col(q, j - 1, a.data(), rho);
                     if (act[q] && rho > 0) {  // continues: q~_j becomes q_j
-                        for (int i = 0; i < j; ++i) c1[(size_t)i * R + q] = -a[i];
+                        for (int i = 0; i < j; ++i) c1[(size_t)i * S + q] = -a[i];
                         p1[q] = 1.0 / rho;
                     }
                 }
-                CKS(vaxpy<T>(h, j, V.data(), c1.data(), V[j], p1.data()));
+                std::vector<int> nvj(M, j);
+                auto Vw = [&](int k) { return V(j, k); };
+                CKS((grp_axpy<T>(g, fm, j, nvj, Vi, c1.data(), Vw, p1.data())));
             }
-            bool any = false;
-            for (int q = 0; q < R; ++q) any = any || act[q];
-            if (!any || last) break;
+            bool anycyc = false;
+            for (int k = 0; k < M; ++k) {
+                if (!cyc[k]) continue;
+                bool any = false;
+                for (int q = g.first[k]; q < g.first[k] + g.hs[k]->nrhs; ++q) any = any || act[q];
+                if (!any || last[k]) cyc[k] = 0;
+                anycyc = anycyc || cyc[k];
+            }
+            if (!anycyc) break;
             // (B) the step: z_j = M^{-1} q~_j, w = A z_j
-            CKS(prec(V[j], Zk[j]));
-            CKS(apply(Zk[j], V[j + 1]));
+            for (int k = 0; k < M; ++k) {
+                if (!cyc[k]) continue;
+                CKS(prec(k, V(j, k), Zk(j, k)));
+                CKS(apply(k, Zk(j, k), V(j + 1, k)));
+            }
             // (C) one Gram pass, targets q~_j and w
-            CKS(gram2s<T>(h, j + 2, V.data(), V[j], V[j + 1], G));
-            std::vector<double> c1((size_t)j * R, 0.0), c2((size_t)j * R, 0.0), c21(R, 0.0),
-                p1(R, 1.0), p2(R, 1.0), a(j), bb(j);
-            int write1 = 0;
-            for (int q = 0; q < R; ++q) {
-                if (!act[q]) continue;
+            {
+                auto Vi = [&](int i, int k) { return (const T *)V(i, k); };
+                CKS((grp_reduce<T>(g, cyc, j + 2, Vi, [&](int k) { return (const T *)V(j, k); },
+                                   [&](int k) { return (const T *)V(j + 1, k); }, 2, G)));
+            }
+            std::vector<double> c1((size_t)std::max(j, 1) * S, 0.0),
+                c2((size_t)std::max(j, 1) * S, 0.0), c21(S, 0.0), p1(S, 1.0), p2(S, 1.0), a(j),
+                bb(j);
+            std::vector<int> write1(M, 0);
+            for (int q = 0; q < S; ++q) {
+                const int k = mq[q];
+                if (!cyc[k] || !act[q]) continue;
                 double aa = 0.0, ab = 0.0, b2 = 0.0;
                 for (int i = 0; i < j; ++i) {
-                    a[i] = pend[q] ? G[((size_t)2 * i) * R + q] : 0.0;
-                    bb[i] = G[((size_t)2 * i + 1) * R + q];
+                    a[i] = pend[q] ? G[((size_t)2 * i) * S + q] : 0.0;
+                    bb[i] = G[((size_t)2 * i + 1) * S + q];
                     aa += a[i] * a[i];
                     ab += a[i] * bb[i];
                     b2 += bb[i] * bb[i];
                 }
-                const double d = G[((size_t)2 * j) * R + q];
-                const double cw = G[((size_t)2 * j + 1) * R + q];
-                const double e = G[((size_t)2 * (j + 1) + 1) * R + q];
+                const double d = G[((size_t)2 * j) * S + q];
+                const double cw = G[((size_t)2 * j + 1) * S + q];
+                const double e = G[((size_t)2 * (j + 1) + 1) * S + q];
                 double rho = 1.0;
                 if (pend[q]) {
                     rho = std::sqrt(std::max(d - aa, 0.0));
                     finish_col(q, j - 1, a.data(), rho);
                     if (!act[q]) continue;  // converged at column j - 1
-                    write1 = 1;
-                    for (int i = 0; i < j; ++i) c1[(size_t)i * R + q] = -a[i];
+                    write1[k] = 1;
+                    for (int i = 0; i < j; ++i) c1[(size_t)i * S + q] = -a[i];
                     p1[q] = 1.0 / rho;
                 }
                 const double sj = (cw - ab) / rho;
@@ -2054,39 +2479,51 @@ int fgmres_dcgs2(st_handle h, const T *b, T *x, double tol, int maxit, std::vect
                     continue;
                 }
                 const double nq = std::sqrt(std::max(r2, 1e-10 * e));
-                for (int i = 0; i < j; ++i) c2[(size_t)i * R + q] = -(bb[i] - a[i] * sj / rho);
+                for (int i = 0; i < j; ++i) c2[(size_t)i * S + q] = -(bb[i] - a[i] * sj / rho);
                 c21[q] = -sj / rho;
                 p2[q] = 1.0 / nq;
                 nu[q] = nq;
                 pend[q] = 1;
             }
             {
-                KScope ks(h, ST_PROF_VECTOR, sizeof(T) * (j + 2.0 + 2.0) * h->len * R,
-                          4.0 * (j + 1) * h->len * R);
-                CK(launch_axpy2<T>(j, V.data(), c1.data(), c2.data(), c21.data(), p1.data(),
-                                   p2.data(), R, h->len, V[j], V[j + 1], write1, h->stream));
+                auto Vi = [&](int i, int k) { return (const T *)V(i, k); };
+                auto Y1 = [&](int k) { return V(j, k); };
+                auto Y2 = [&](int k) { return V(j + 1, k); };
+                CKS((grp_axpy2<T>(g, cyc, j, Vi, c1, c2, c21, p1, p2, write1, Y1, Y2)));
             }
-            ++total;
+            for (int k = 0; k < M; ++k) total[k] += cyc[k] ? 1 : 0;
         }
-        // x += Z y per rhs
-        const int kmax = *std::max_element(kq.begin(), kq.end());
-        std::vector<double> coef((size_t)std::max(kmax, 1) * R, 0.0);
-        for (int q = 0; q < R; ++q) {
+        // x += Z y per rhs, over the members of this cycle
+        std::vector<int> kmax(M, 0);
+        for (int q = 0; q < S; ++q)
+            if (live[mq[q]]) kmax[mq[q]] = std::max(kmax[mq[q]], kq[q]);
+        int kall = 0;
+        std::vector<char> upd(M, 0);
+        for (int k = 0; k < M; ++k) {
+            upd[k] = live[k] && kmax[k] > 0;
+            kall = std::max(kall, upd[k] ? kmax[k] : 0);
+        }
+        std::vector<double> coef((size_t)std::max(kall, 1) * S, 0.0);
+        for (int q = 0; q < S; ++q) {
+            if (!upd[mq[q]]) continue;
             const int k = kq[q];
             const double *Hq = &H[(size_t)q * ld * m];
-            const double *gq = &g[(size_t)q * ld];
+            const double *gq = &gv[(size_t)q * ld];
             std::vector<double> y(k);
             for (int i = k - 1; i >= 0; --i) {
                 double sacc = gq[i];
                 for (int c2i = i + 1; c2i < k; ++c2i) sacc -= Hq[(size_t)c2i * ld + i] * y[c2i];
                 y[i] = sacc / Hq[(size_t)i * ld + i];
             }
-            for (int i = 0; i < k; ++i) coef[(size_t)i * R + q] = y[i];
+            for (int i = 0; i < k; ++i) coef[(size_t)i * S + q] = y[i];
         }
-        if (kmax > 0) CKS(vaxpy<T>(h, kmax, Zk.data(), coef.data(), x));
+        if (kall > 0) {
+            auto Zi = [&](int i, int k) { return (const T *)Zk(i, k); };
+            auto Xw = [&](int k) { return x(k); };
+            CKS((grp_axpy<T>(g, upd, kall, kmax, Zi, coef.data(), Xw, nullptr)));
+        }
     }
-    *its = total;
-    *worst_out = worst;
+    its = total;
     return ST_OK;
 }
 
@@ -2156,106 +2593,178 @@ int ensure_krylov32(st_handle h) {
 // Mixed-precision iterative refinement: FP64 residual r = f - L u and FP64
 // update u += ||r|| e, where e solves L e = r / ||r|| approximately by FGMRES
 // on FP32 vectors (FP32 operator, FP32 V-cycle) to inner_tol.
-int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
-    CKS(ensure_krylov32(h));
-    const int R = h->nrhs;
-    std::vector<double> nf(R), nr(R), g0;
+// Mixed-precision iterative refinement over a group of members (a single
+// handle is the group of one): the refinement steps, FP64 residuals,
+// transforms and updates run per member on its stream, the norms and the
+// inner FGMRES's vector kernels as group launches.  Each member's loop
+// bounds and each system's decisions are the single-handle ones, so every
+// right-hand side gets the result st_solve gives it.
+int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *u,
+                   st_solve_info *info) {
+    const int M = (int)g.hs.size(), S = g.S;
+    for (st_handle h : g.hs) CKS(ensure_krylov32(h));
+    std::vector<char> all(M, 1);
+    std::vector<double> nf(S), nr(S), g0;
     // ||f|| and ||u|| in one pass: from a zero initial guess the first
     // residual is f itself
     {
-        const double *fu[2] = {rhs, u};
-        CKS(gram2s<double>(h, 2, fu, rhs, u, g0));
+        auto FU = [&](int v, int k) { return v == 0 ? rhs[k] : (const double *)u[k]; };
+        auto F = [&](int k) { return rhs[k]; };
+        auto U = [&](int k) { return (const double *)u[k]; };
+        CKS((grp_reduce<double>(g, all, 2, FU, F, U, 2, g0)));
     }
-    bool u_zero = true;
-    for (int q = 0; q < R; ++q) {
-        const double f2 = g0[(size_t)0 * R + q];
-        nf[q] = std::isfinite(f2) ? std::sqrt(std::max(0.0, f2)) : f2;
-        u_zero = u_zero && g0[(size_t)3 * R + q] == 0.0;
-    }
+    std::vector<char> u_zero(M, 1);
+    for (int k = 0; k < M; ++k)
+        for (int q = g.first[k]; q < g.first[k] + g.hs[k]->nrhs; ++q) {
+            const double f2 = g0[(size_t)0 * S + q];
+            nf[q] = std::isfinite(f2) ? std::sqrt(std::max(0.0, f2)) : f2;
+            u_zero[k] = u_zero[k] && g0[(size_t)3 * S + q] == 0.0;
+        }
     CKS(check_finite_rhs(nf));
-    int total = 0, outer = 0;
-    double worst = 0.0;
-    const bool eig_basis = h->opt.basis == ST_BASIS_SPECTRAL;
-    const SpecCoefs<float> c0 = pack_spec<float>(h, 0);
-    const long long nsl = (long long)h->N * R;
+    std::vector<int> total(M, 0), outer(M, 0);
+    std::vector<double> worst(M, 0.0);
+    std::vector<char> eig(M);
+    std::vector<SpecCoefs<float>> c0(M);
+    std::vector<long long> nsl(M);
+    for (int k = 0; k < M; ++k) {
+        eig[k] = g.hs[k]->opt.basis == ST_BASIS_SPECTRAL;
+        c0[k] = pack_spec<float>(g.hs[k], 0);
+        nsl[k] = (long long)g.hs[k]->N * g.hs[k]->nrhs;
+    }
     // B-spline basis: FP32 stencil operator, V-cycle with its transforms;
     // eigenbasis: pointwise operator L^, V-cycle without transforms
-    auto apply = [h, eig_basis, c0, nsl](const float *z, float *w) {
-        if (!eig_basis)
-            return stencil<float>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, (int)nsl);
-        const double E = (double)nsl * h->nt * h->g.nxyz;
+    auto apply = [&](int k, const float *z, float *w) {
+        st_handle h = g.hs[k];
+        if (!eig[k]) return stencil<float>(h, 0, z, nullptr, w, MODE_APPLY, false, 0, (int)nsl[k]);
+        const double E = (double)nsl[k] * h->nt * h->g.nxyz;
         KScope ks(h, ST_PROF_SPEC, 4.0 * 2.25 * E, E * (4.0 * h->nt + 2.0));
-        CK(launch_spec_op<float>(z, nullptr, w, h->s32.mu, h->g, c0, h->N, nsl, 0, h->stream));
+        CK(launch_spec_op<float>(z, nullptr, w, h->s32.mu, h->g, c0[k], h->N, nsl[k], 0,
+                                 h->stream));
         return (int)ST_OK;
     };
-    auto resid = [h, eig_basis, c0, nsl](const float *x, const float *b, float *r) {
-        if (!eig_basis) return stencil<float>(h, 0, x, b, r, MODE_RES, false, 0, (int)nsl);
-        const double E = (double)nsl * h->nt * h->g.nxyz;
+    auto resid = [&](int k, const float *x, const float *b, float *r) {
+        st_handle h = g.hs[k];
+        if (!eig[k]) return stencil<float>(h, 0, x, b, r, MODE_RES, false, 0, (int)nsl[k]);
+        const double E = (double)nsl[k] * h->nt * h->g.nxyz;
         KScope ks(h, ST_PROF_SPEC, 4.0 * 3.25 * E, E * (4.0 * h->nt + 2.0));
-        CK(launch_spec_op<float>(x, b, r, h->s32.mu, h->g, c0, h->N, nsl, 1, h->stream));
+        CK(launch_spec_op<float>(x, b, r, h->s32.mu, h->g, c0[k], h->N, nsl[k], 1, h->stream));
         return (int)ST_OK;
     };
-    auto prec = [h, eig_basis](const float *v, float *z) {
-        if (!eig_basis)
+    auto prec = [&](int k, const float *v, float *z) {
+        st_handle h = g.hs[k];
+        if (!eig[k])
             return run_graphed(h, v, z, [h, v, z] { return precondition32(h, v, z); });
         return run_graphed(h, v, z, [h, v, z] { return svcycle_top<float>(h, z, v, h->w32.w0); });
     };
-    const long long n0 = h->len * R;
+    auto R64 = [&](int, int k) { return (const double *)g.hs[k]->r64; };
+    auto B32 = [&](int k) { return (const float *)g.hs[k]->rhs32; };
+    auto X32 = [&](int k) { return g.hs[k]->e32; };
+    auto VV = [&](int j, int k) { return g.hs[k]->V32[j]; };
+    auto ZZ = [&](int j, int k) { return g.hs[k]->Z32[j]; };
+    std::vector<char> run(M, 1);  // members still refining
     for (bool first = true;; first = false) {
-        if (first && u_zero) {
-            CK(cudaMemcpyAsync(h->r64, rhs, sizeof(double) * h->len * R, cudaMemcpyDeviceToDevice,
-                               h->stream));
-            nr = nf;
-        } else {
-            CKS(residual_df(h, u, rhs, h->r64));
-            CKS(norms<double>(h, h->r64, nr));
-        }
-        worst = 0.0;
-        std::vector<char> skip(R, 0);
-        std::vector<double> sc(R), back(R);
-        for (int q = 0; q < R; ++q) {
-            const double rel = nf[q] > 0 ? nr[q] / nf[q] : 0.0;
-            worst = std::max(worst, rel);
-            skip[q] = !(nf[q] > 0) || rel <= tol || !(nr[q] > 0);
-            sc[q] = skip[q] ? 0.0 : 1.0 / nr[q];
-            back[q] = skip[q] ? 0.0 : nr[q];
-        }
-        h->hist.emplace_back(total, worst);
-        if (worst <= tol || total >= h->opt.max_it || outer >= 60) break;
-        CKS((vconvert<double, float>(h, h->r64, h->rhs32)));
-        CKS(vaxpy<float>(h, 0, nullptr, nullptr, h->rhs32, sc.data()));
-        const long long planes = (long long)h->N * R * h->nt;
-        // the two transforms around each inner solve run at full FP32
-        // accuracy: their error bounds what one refinement step can gain
-        if (eig_basis) {  // r^ = (I (x) U^T) r, into rhs32
-            float *rh = nullptr;
-            CKS(spatial<float>(h, h->rhs32, h->w32.w0, h->w32.w1, true, planes, &rh, true));
-            CK(cudaMemcpyAsync(h->rhs32, rh, sizeof(float) * n0, cudaMemcpyDeviceToDevice, h->stream));
-        }
-        CK(launch_zero<float>(h->e32, n0, h->stream));
-        int its = 0;
-        double w32 = 0.0;
-        const double itol = std::max(h->opt.inner_tol, 1e-6);
-        CKS(fgmres_dcgs2<float>(h, h->rhs32, h->e32, itol, h->opt.max_it - total, h->V32,
-                                h->Z32, apply, resid, prec, skip, &its, &w32));
-        total += its;
-        ++outer;
-        const float *corr = h->e32;
-        if (eig_basis) {  // e = (I (x) U) e^
-            float *eb = nullptr;
-            CKS(spatial<float>(h, h->e32, h->w32.w0, h->w32.w1, false, planes, &eb, true));
-            corr = eb;
+        std::vector<char> need(M, 0);
+        for (int k = 0; k < M; ++k) {
+            if (!run[k]) continue;
+            st_handle h = g.hs[k];
+            if (first && u_zero[k]) {
+                CK(cudaMemcpyAsync(h->r64, rhs[k], sizeof(double) * h->len * h->nrhs,
+                                   cudaMemcpyDeviceToDevice, h->stream));
+                for (int q = g.first[k]; q < g.first[k] + h->nrhs; ++q) nr[q] = nf[q];
+            } else {
+                CKS(residual_df(h, u[k], rhs[k], h->r64));
+                need[k] = 1;
+            }
         }
         {
+            std::vector<double> nn;
+            CKS(grp_norms<double>(g, need, R64, nn));
+            for (int k = 0; k < M; ++k)
+                if (need[k])
+                    for (int q = g.first[k]; q < g.first[k] + g.hs[k]->nrhs; ++q) nr[q] = nn[q];
+        }
+        std::vector<char> skip(S, 0);
+        std::vector<double> sc(S, 0.0), back(S, 0.0);
+        bool any = false;
+        for (int k = 0; k < M; ++k) {
+            if (!run[k]) continue;
+            st_handle h = g.hs[k];
+            double wk = 0.0;
+            for (int q = g.first[k]; q < g.first[k] + h->nrhs; ++q) {
+                const double rel = nf[q] > 0 ? nr[q] / nf[q] : 0.0;
+                wk = std::max(wk, rel);
+                skip[q] = !(nf[q] > 0) || rel <= tol || !(nr[q] > 0);
+                sc[q] = skip[q] ? 0.0 : 1.0 / nr[q];
+                back[q] = skip[q] ? 0.0 : nr[q];
+            }
+            worst[k] = wk;
+            h->hist.emplace_back(total[k], wk);
+            if (wk <= tol || total[k] >= h->opt.max_it || outer[k] >= 60) run[k] = 0;
+            any = any || run[k];
+        }
+        if (!any) break;
+        for (int k = 0; k < M; ++k)
+            if (run[k]) CKS((vconvert<double, float>(g.hs[k], g.hs[k]->r64, g.hs[k]->rhs32)));
+        {
+            std::vector<int> nv0(M, 0);
+            auto B32w = [&](int k) { return g.hs[k]->rhs32; };
+            auto none = [&](int, int) { return (const float *)nullptr; };
+            CKS((grp_axpy<float>(g, run, 0, nv0, none, nullptr, B32w, sc.data())));
+        }
+        std::vector<double> itol(M, 0.0);
+        std::vector<int> maxit(M, 0);
+        for (int k = 0; k < M; ++k) {
+            if (!run[k]) continue;
+            st_handle h = g.hs[k];
+            const long long n0 = h->len * h->nrhs;
+            const long long planes = (long long)h->N * h->nrhs * h->nt;
+            // the two transforms around each inner solve run at full FP32
+            // accuracy: their error bounds what one refinement step can gain
+            if (eig[k]) {  // r^ = (I (x) U^T) r, into rhs32
+                float *rh = nullptr;
+                CKS(spatial<float>(h, h->rhs32, h->w32.w0, h->w32.w1, true, planes, &rh, true));
+                CK(cudaMemcpyAsync(h->rhs32, rh, sizeof(float) * n0, cudaMemcpyDeviceToDevice,
+                                   h->stream));
+            }
+            CK(launch_zero<float>(h->e32, n0, h->stream));
+            itol[k] = std::max(h->opt.inner_tol, 1e-6);
+            maxit[k] = h->opt.max_it - total[k];
+        }
+        std::vector<int> its;
+        std::vector<double> w32;
+        CKS((fgmres_group<float>(g, run, B32, X32, VV, ZZ, g.hs[0]->opt.gmres_restart, itol, maxit,
+                                 apply, resid, prec, skip, its, w32)));
+        for (int k = 0; k < M; ++k) {
+            if (!run[k]) continue;
+            st_handle h = g.hs[k];
+            const long long n0 = h->len * h->nrhs;
+            const long long planes = (long long)h->N * h->nrhs * h->nt;
+            total[k] += its[k];
+            ++outer[k];
+            const float *corr = h->e32;
+            if (eig[k]) {  // e = (I (x) U) e^
+                float *eb = nullptr;
+                CKS(spatial<float>(h, h->e32, h->w32.w0, h->w32.w1, false, planes, &eb, true));
+                corr = eb;
+            }
             KScope ks(h, ST_PROF_VECTOR, 12.0 * n0, 2.0 * n0);
-            CK(launch_axpy_f32_f64(corr, u, back.data(), R, h->len, h->stream));
+            CK(launch_axpy_f32_f64(corr, u[k], &back[g.first[k]], h->nrhs, h->len, h->stream));
         }
     }
-    info->iterations = total;
-    info->refinements = outer;
-    info->rel_residual = worst;
-    info->status = (worst <= tol) ? ST_OK : ST_ERR_NO_CONVERGENCE;
+    for (int k = 0; k < M; ++k) {
+        info[k].iterations = total[k];
+        info[k].refinements = outer[k];
+        info[k].rel_residual = worst[k];
+        info[k].status = (worst[k] <= tol) ? ST_OK : ST_ERR_NO_CONVERGENCE;
+    }
     return ST_OK;
+}
+
+int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
+    Grp g;
+    g.hs = {h};
+    CKS(grp_begin(g, false));
+    return solve_ir_group(g, &rhs, tol, &u, info);
 }
 
 // Slab partition plan: rank's first slab, its slab count, the first level
@@ -2568,7 +3077,10 @@ int setup_impl(st_handle h, int geometry, int degree, const int *spans, int slab
     void *p;
     CKS(dalloc(h, sizeof(double) * 2 * MAXV * h->nrhs * h->nblk_dot, &p));
     h->partial = (double *)p;
-    CKS(host_dots(h, (size_t)2 * MAXV * h->nrhs));
+    // room for a group launch of up to NSYS_MAX systems (st_solve_group)
+    CKS(dalloc(h, sizeof(double) * 2 * MAXV * NSYS_MAX, &p));
+    h->dots = (double *)p;
+    CKS(host_dots(h, (size_t)2 * MAXV * NSYS_MAX));
     return ST_OK;
 }
 
@@ -2747,10 +3259,11 @@ void st_destroy(st_handle h) {
     for (int s = 0; s < 2; ++s)
         for (cudaEvent_t e : {h->hs_in[s], h->hs_solved[s], h->hs_out[s]})
             if (e) cudaEventDestroy(e);
+    if (h->bg_ev) cudaEventDestroy(h->bg_ev);
     if (h->cp_in) cudaStreamDestroy(h->cp_in);
     if (h->cp_out) cudaStreamDestroy(h->cp_out);
     if (h->stage) cudaFreeHost(h->stage);
-    mapped_put(h->dots_host, h->dots_host_cap * sizeof(double));
+    pinned_put(h->dots_host, h->dots_host_cap * sizeof(double));
     delete h;
 }
 
@@ -2977,6 +3490,7 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
     try {
         if (!use_guess) CK(launch_zero<double>(u, h->len * h->nrhs, h->stream));
         h->hist.clear();
+        h->n_sync = h->n_vl = 0;
         if (h->opt.outer == ST_OUTER_MG) {
             CKS(solve_mg(h, rhs, tol, u, info));
         } else if (h->opt.outer == ST_OUTER_IR && h->mixed) {
@@ -2992,9 +3506,79 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
         return fail(ST_ERR_OOM, "host exception during solve");
     }
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    info->host_syncs = (int)h->n_sync;
+    info->vector_launches = (int)h->n_vl;
     if (info->status != ST_OK)
         return fail(info->status, "no convergence: rel. residual %.3e after %d iterations",
                     info->rel_residual, info->iterations);
+    return ST_OK;
+}
+
+int st_solve_group(int n, const st_handle *hs, const double *const *rhs, double tol,
+                   double *const *u, int use_guess, st_solve_info *info) {
+    if (n < 1 || n > GH) return fail(ST_ERR_INVALID_ARG, "a group has 1 to %d handles", GH);
+    if (!hs || !rhs || !u) return fail(ST_ERR_INVALID_ARG, "null array");
+    if (!(tol > 0)) return fail(ST_ERR_INVALID_ARG, "tol must be > 0");
+    int S = 0;
+    for (int k = 0; k < n; ++k) {
+        st_handle h = hs[k];
+        CKS(check_ptr(h, rhs[k], "rhs"));
+        CKS(check_ptr(h, u[k], "u"));
+        if ((const void *)rhs[k] == (void *)u[k])
+            return fail(ST_ERR_INVALID_ARG, "rhs and u of member %d alias", k);
+        for (int j = 0; j < k; ++j)
+            if (hs[j] == h) return fail(ST_ERR_INVALID_ARG, "handle %d appears twice", k);
+        if (h->part) return fail(ST_ERR_UNSUPPORTED, "member %d is slab-partitioned", k);
+        if (!h->mixed || h->opt.outer != ST_OUTER_IR)
+            return fail(ST_ERR_UNSUPPORTED,
+                        "st_solve_group solves mixed-precision handles with ST_OUTER_IR");
+        if (h->opt.gmres_restart != hs[0]->opt.gmres_restart)
+            return fail(ST_ERR_INVALID_ARG, "members differ in gmres_restart");
+        S += h->nrhs;
+    }
+    if (S > NSYS_MAX)
+        return fail(ST_ERR_INVALID_ARG, "%d right-hand sides in the group (at most %d)", S, NSYS_MAX);
+    std::vector<st_solve_info> local(n);
+    if (!info) info = local.data();
+    std::memset(info, 0, sizeof(st_solve_info) * n);
+    for (int k = 0; k < n; ++k)
+        if (hs[k]->opt.autotune && !hs[k]->tuned) CKS(autotune(hs[k]));
+    const auto t0 = std::chrono::steady_clock::now();
+    Grp g;
+    g.hs.assign(hs, hs + n);
+    CKS(grp_begin(g, true));
+    int rc = ST_OK;
+    try {
+        for (int k = 0; k < n && rc == ST_OK; ++k) {
+            st_handle h = hs[k];
+            if (!use_guess && launch_zero<double>(u[k], h->len * h->nrhs, h->stream) != cudaSuccess)
+                rc = fail(ST_ERR_CUDA, "zeroing the initial guess failed");
+            h->hist.clear();
+            h->n_sync = h->n_vl = 0;
+        }
+        if (rc == ST_OK) rc = solve_ir_group(g, rhs, tol, u, info);
+    } catch (...) {
+        rc = fail(ST_ERR_OOM, "host exception during solve");
+    }
+    const int rc_end = grp_end(g);  // the members' streams handed back in every case
+    if (rc != ST_OK) return rc;
+    if (rc_end != ST_OK) return rc_end;
+    for (int k = 0; k < n; ++k) CKS(check_waits(hs[k]));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    long long ns = 0, nl = 0;
+    for (int k = 0; k < n; ++k) {
+        ns += hs[k]->n_sync;
+        nl += hs[k]->n_vl;
+    }
+    for (int k = 0; k < n; ++k) {
+        info[k].seconds = secs;
+        info[k].host_syncs = (int)ns;
+        info[k].vector_launches = (int)nl;
+    }
+    for (int k = 0; k < n; ++k)
+        if (info[k].status != ST_OK)
+            return fail(info[k].status, "member %d: no convergence: rel. residual %.3e after %d iterations",
+                        k, info[k].rel_residual, info[k].iterations);
     return ST_OK;
 }
 
@@ -3032,15 +3616,31 @@ int st_solve_host(st_handle h, int nbatch, const double *rhs, double tol, double
             CK(cudaEventCreateWithFlags(&h->hs_solved[s], cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&h->hs_out[s], cudaEventDisableTiming));
         }
+        CK(cudaEventCreateWithFlags(&h->bg_ev, cudaEventDisableTiming));
     }
     st_solve_info local;
     if (!info) info = &local;
     std::memset(info, 0, sizeof *info);
     const auto t0 = std::chrono::steady_clock::now();
+    h->bg.clear();
+    h->bg_err = cudaSuccess;
+    // the pending copy of slot s (two batches back) issued in full
+    auto flush_slot = [&](int s) {
+        if (h->bg.empty() || h->bg.front().slot != s) return;
+        auto &c = h->bg.front();
+        cudaError_t e = cudaMemcpyAsync(c.dst + c.done, c.src + c.done,
+                                        (c.n - c.done) * sizeof(double), cudaMemcpyDeviceToHost,
+                                        h->cp_out);
+        if (e == cudaSuccess) e = cudaEventRecord(h->bg_ev, h->cp_out);
+        if (e == cudaSuccess) e = cudaEventRecord(h->hs_out[s], h->cp_out);
+        if (e != cudaSuccess && h->bg_err == cudaSuccess) h->bg_err = e;
+        h->bg.pop_front();
+    };
     // batch k uses slot k & 1; a slot is refilled only after the solve two
     // batches back has finished with it and its solution has been copied out
     auto copy_in = [&](int k) -> cudaError_t {
         const int s = k & 1;
+        if (use_guess) flush_slot(s);
         cudaError_t c = cudaStreamWaitEvent(h->cp_in, h->hs_solved[s], 0);
         if (c == cudaSuccess && use_guess) c = cudaStreamWaitEvent(h->cp_in, h->hs_out[s], 0);
         if (c == cudaSuccess)
@@ -3052,35 +3652,46 @@ int st_solve_host(st_handle h, int nbatch, const double *rhs, double tol, double
         if (c == cudaSuccess) c = cudaEventRecord(h->hs_in[s], h->cp_in);
         return c;
     };
-    // leave no copy in flight on the staging slots, whatever happened
+    // every solution of the batches solved so far issued, and no copy left in
+    // flight on the staging slots, whatever happened
     auto drain = [&](int rc) {
+        bg_pump(h, true);
         cudaStreamSynchronize(h->cp_in);
         cudaStreamSynchronize(h->cp_out);
         cudaStreamSynchronize(h->stream);
+        h->bg.clear();
         return rc;
     };
     cudaError_t c = copy_in(0);
     for (int k = 0; k < nbatch && c == cudaSuccess; ++k) {
         const int s = k & 1;
         if (k + 1 < nbatch) c = copy_in(k + 1);  // overlaps this batch's solve
+        flush_slot(s);
         if (c == cudaSuccess) c = cudaStreamWaitEvent(h->stream, h->hs_in[s], 0);
         if (c == cudaSuccess) c = cudaStreamWaitEvent(h->stream, h->hs_out[s], 0);
         if (c != cudaSuccess) break;
         st_solve_info bi;
+        // batch k - 1's solution is copied back in chunks during this solve
         const int rc = st_solve(h, h->hs_f[s], tol, h->hs_u[s], use_guess, &bi);
         info->iterations = std::max(info->iterations, bi.iterations);
         info->refinements = std::max(info->refinements, bi.refinements);
         info->rel_residual = std::max(info->rel_residual, bi.rel_residual);
+        info->host_syncs += bi.host_syncs;
+        info->vector_launches += bi.vector_launches;
         if (rc != ST_OK) {
             info->status = rc;
             return drain(rc);
         }
         c = cudaEventRecord(h->hs_solved[s], h->stream);
         if (c == cudaSuccess) c = cudaStreamWaitEvent(h->cp_out, h->hs_solved[s], 0);
-        if (c == cudaSuccess)
-            c = cudaMemcpyAsync(u + (size_t)k * e, h->hs_u[s], e * sizeof(double),
-                                cudaMemcpyDeviceToHost, h->cp_out);
-        if (c == cudaSuccess) c = cudaEventRecord(h->hs_out[s], h->cp_out);
+        if (c == cudaSuccess) {
+            h->bg.push_back({u + (size_t)k * e, h->hs_u[s], e, 0, s});
+            bg_pump(h);
+        }
+    }
+    if (c == cudaSuccess) {
+        bg_pump(h, true);
+        c = h->bg_err;
     }
     if (c == cudaSuccess) c = cudaStreamSynchronize(h->cp_out);
     if (c != cudaSuccess) {

@@ -234,26 +234,44 @@ cudaError_t launch_mode_solve(T *w, const T *mu, const Grid &g, const SpecCoefs<
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin *x, Tout *y, long long n, cudaStream_t s);
 
-// out[v*nrhs + r] = dot of vecs[v] and w over rhs r (FP64 accumulation);
-// partial: nv * nrhs * nblk doubles of scratch
-template <typename T>
-cudaError_t launch_multidot(int nv, const T *const *vecs, const T *w, int nrhs, long long len,
-                            double *partial, int nblk, double *out, cudaStream_t s);
+// Krylov vector kernels over a group of members (handles) whose vectors hold
+// different numbers of right-hand sides of different lengths.  A launch
+// covers the systems s < nsys; system s is right-hand side sr[s] of member
+// sm[s] (len[k] values at offset sr[s] * len[k] of member k's vectors).
+// Vector v of member k is xs[v * nmem + k]; a target of member k is t[k].
+// A single handle is the group of one member with systems r = 0 .. R-1, so
+// every system gets the same arithmetic whatever else is in its launch.
+constexpr int GH = 16;        // members of one group launch
+constexpr int NSYS_MAX = 32;  // systems of one group launch
+struct GLaunch {
+    int nmem = 0, nsys = 0, nblk = 0;  // nblk: partial sums per system and dot
+    long long len[GH] = {};
+    int R[GH] = {};                    // right-hand sides of member k
+    double *part[GH] = {};             // member k's partial sums: rows x R[k] x nblk
+    int sm[NSYS_MAX] = {}, sr[NSYS_MAX] = {};
+    int snv[NSYS_MAX] = {};            // launch_gaxpy: vectors system s uses (<= nv)
+};
 
-// y_r = post_r * (y_r + sum_v coef[v][r] x_v)  (per rhs r; post NULL = 1)
-// out[(v * 2 + t) * nrhs + r] = dot of vecs[v] with target t (t1, t2) over rhs r
+// out[v * nsys + s] = dot of vector v with target w over system s (FP64 sums)
 template <typename T>
-cudaError_t launch_gram2(int nv, const T *const *vecs, const T *t1, const T *t2, int nrhs,
-                         long long len, double *partial, int nblk, double *out, cudaStream_t s);
-// y1 <- post1 (y1 + sum_v c1[v] x_v);  y2 <- post2 (y2 + c21 y1_old + sum_v c2[v] x_v)
-// (coefficients [v * nrhs + r], per rhs r); write1 = 0 leaves y1 untouched
+cudaError_t launch_gdot(const GLaunch &g, int nv, const T *const *xs, const T *const *w,
+                        double *out, cudaStream_t s);
+// out[(v * 2 + t) * nsys + s] = dot of vector v with target t (t1, t2) over system s
 template <typename T>
-cudaError_t launch_axpy2(int nv, const T *const *xs, const double *c1, const double *c2,
-                         const double *c21, const double *post1, const double *post2, int nrhs,
-                         long long len, T *y1, T *y2, int write1, cudaStream_t s);
+cudaError_t launch_ggram2(const GLaunch &g, int nv, const T *const *xs, const T *const *t1,
+                          const T *const *t2, double *out, cudaStream_t s);
+// y_s = post_s (y_s + sum_{v < snv[s]} coef[v * nsys + s] x_v)  (post NULL = 1)
 template <typename T>
-cudaError_t launch_multiaxpy(int nv, const T *const *xs, const double *coef, int nrhs,
-                             long long len, T *y, cudaStream_t s, const double *post = nullptr);
+cudaError_t launch_gaxpy(const GLaunch &g, int nv, const T *const *xs, const double *coef,
+                         T *const *y, const double *post, cudaStream_t s);
+// y1 <- post1 (y1 + sum_v c1 x_v);  y2 <- post2 (y2 + c21 y1_old + sum_v c2 x_v)
+// (coefficients [v * nsys + s], scalars [s]); write1[s] = 0 leaves system
+// s's y1 untouched
+template <typename T>
+cudaError_t launch_gaxpy2(const GLaunch &g, int nv, const T *const *xs, const double *c1,
+                          const double *c2, const double *c21, const double *post1,
+                          const double *post2, T *const *y1, T *const *y2, const int *write1,
+                          cudaStream_t s);
 
 // f = sum_k gt_k (x) gz_k (x) gy_k (x) gx_k, g packed per k as
 // [nslab_t | nx | ny | nz] doubles

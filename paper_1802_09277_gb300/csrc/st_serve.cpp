@@ -195,7 +195,7 @@ int build_entry(st_server_s *s, const Key &key, int nrhs, size_t limit, cudaStre
 
 void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const st_solve_info *info,
             Clock::time_point admitted, const std::vector<std::vector<double>> *u,
-            const std::string &msg = std::string()) {
+            const std::string &msg = std::string(), int group_requests = 0) {
     const auto now = Clock::now();
     for (size_t i = 0; i < batch.size(); ++i) {
         Done &d = s->results[batch[i].ticket];
@@ -210,6 +210,9 @@ void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const
         d.res.latency_seconds = std::chrono::duration<double>(now - batch[i].submitted).count();
         d.res.batch_size = (int)batch.size();
         d.res.n_dofs = (int64_t)batch[i].rhs.size();
+        d.res.group_requests = group_requests > 0 ? group_requests : (int)batch.size();
+        d.res.host_syncs = info ? info->host_syncs : 0;
+        d.res.vector_launches = info ? info->vector_launches : 0;
         std::snprintf(d.res.error, sizeof d.res.error, "%s", status == ST_OK ? "" : msg.c_str());
         if (u) d.u = (*u)[i];
     }
@@ -219,7 +222,7 @@ void finish(st_server_s *s, const std::vector<Pending> &batch, int status, const
 // is released while a setup is built or an evicted one is freed).  On success
 // the entry is marked busy.
 int acquire_entry(st_server_s *s, std::unique_lock<std::mutex> &lock, const Key &key, int R,
-                  cudaStream_t stream, Entry **out, std::string *why) {
+                  cudaStream_t stream, Entry **out, std::string *why, bool may_wait = true) {
     const ShapeKey sk = shape_of(key, R);
     for (;;) {
         for (auto &c : s->cache)
@@ -292,6 +295,10 @@ int acquire_entry(st_server_s *s, std::unique_lock<std::mutex> &lock, const Key 
             continue;
         }
         if (s->busy_workers > 0) {  // wait for running work to release memory
+            if (!may_wait) {
+                *why = "no room now";
+                return ST_ERR_NOT_READY;
+            }
             s->cv.wait(lock);
             continue;
         }
@@ -301,6 +308,32 @@ int acquire_entry(st_server_s *s, std::unique_lock<std::mutex> &lock, const Key 
         *why = buf;
         return ST_ERR_OVER_BUDGET;
     }
+}
+
+// one configuration's share of a solve call: its requests and its setup
+struct Member {
+    Key key;
+    std::vector<Pending> batch;
+    int R = 0, RC = 0;
+    Entry *e = nullptr;
+};
+
+// back into the queue in submission order (lock held)
+void requeue(st_server_s *s, std::vector<Pending> &batch) {
+    for (Pending &p : batch) {
+        s->results[p.ticket].running = false;
+        auto at = std::upper_bound(s->pending.begin(), s->pending.end(), p.ticket,
+                                   [](uint64_t t, const Pending &q) { return t < q.ticket; });
+        s->pending.insert(at, std::move(p));
+    }
+    batch.clear();
+}
+
+// configurations are solved together (st_solve_group) when the server's
+// solver is the mixed-precision refinement
+bool grouping(const st_server_s *s) {
+    return s->o.group_members > 1 && s->o.opt.precision != ST_FP64 &&
+           s->o.opt.outer == ST_OUTER_IR;
 }
 
 void worker(st_server_s *s) {
@@ -314,66 +347,147 @@ void worker(st_server_s *s) {
             if (s->stop) break;
             continue;
         }
-        // the oldest request and up to max_batch - 1 more of the same configuration
-        const Key key = s->pending.front().key;
-        std::vector<Pending> batch;
-        long long dofs = 0;
-        for (auto it = s->pending.begin(); it != s->pending.end() && (int)batch.size() < s->o.max_batch;) {
-            const long long n = (long long)it->rhs.size();
-            if (std::memcmp(&it->key, &key, sizeof(Key)) == 0 &&
-                (batch.empty() || s->o.batch_dofs <= 0 || dofs + n <= s->o.batch_dofs)) {
-                dofs += n;
-                s->results[it->ticket].running = true;
-                batch.push_back(std::move(*it));
-                it = s->pending.erase(it);
-            } else {
-                ++it;
+        // the oldest request and up to max_batch - 1 more of the same
+        // configuration; for a group solve, then the same for further
+        // configurations (oldest first) while the group stays within its
+        // right-hand-side and dofs limits
+        std::vector<Member> mem;
+        std::vector<Key> tried;
+        const int gmax = grouping(s) ? std::min(s->o.group_members, st::GH) : 1;
+        const double tol0 = s->pending.front().key.tol;
+        const long long n0 = (long long)s->pending.front().rhs.size();
+        long long gdofs = 0;
+        int gsys = 0;
+        // takes the requests of the oldest configuration not yet tried into
+        // m (false: none left)
+        auto form = [&](Member &m) {
+            for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+                const Key key = it->key;
+                // a group never waits for a larger problem than its oldest
+                // request's (it runs at the pace of its slowest member)
+                bool skip = !mem.empty() && (key.tol != tol0 || (long long)it->rhs.size() > n0);
+                for (const Member &o : mem) skip = skip || o.key.same_problem(key);
+                for (const Key &k : tried) skip = skip || std::memcmp(&k, &key, sizeof(Key)) == 0;
+                if (skip) continue;
+                tried.push_back(key);
+                m = Member();
+                m.key = key;
+                long long dofs = 0;
+                for (auto jt = s->pending.begin();
+                     jt != s->pending.end() && (int)m.batch.size() < s->o.max_batch;) {
+                    const long long n = (long long)jt->rhs.size();
+                    bool take = std::memcmp(&jt->key, &key, sizeof(Key)) == 0;
+                    if (take && !(mem.empty() && m.batch.empty()))  // the oldest always runs
+                        take = (s->o.batch_dofs <= 0 || gdofs + dofs + n <= s->o.batch_dofs) &&
+                               gsys + size_class((int)m.batch.size() + 1) <= st::NSYS_MAX;
+                    if (take) {
+                        dofs += n;
+                        s->results[jt->ticket].running = true;
+                        m.batch.push_back(std::move(*jt));
+                        jt = s->pending.erase(jt);
+                    } else {
+                        ++jt;
+                    }
+                }
+                if (m.batch.empty()) continue;  // its oldest request does not fit
+                m.R = (int)m.batch.size();
+                m.RC = size_class(m.R);
+                return true;
             }
+            return false;
+        };
+        // the first configuration may wait for memory; the others join only
+        // if their setup is at hand now, else they go back to the queue
+        bool failed0 = false;
+        for (;;) {
+            if ((int)mem.size() >= gmax) break;
+            Member m;
+            if (!form(m)) break;
+            std::string why;
+            const bool first = mem.empty();
+            const int rc = acquire_entry(s, lock, m.key, m.RC, stream, &m.e, &why, first);
+            if (rc != ST_OK) {
+                if (first) {
+                    finish(s, m.batch, rc, nullptr, Clock::now(), nullptr, why);
+                    failed0 = true;
+                    break;
+                }
+                requeue(s, m.batch);
+                continue;
+            }
+            m.e->last_used = ++s->clock;
+            for (const Pending &p : m.batch) gdofs += (long long)p.rhs.size();
+            gsys += m.RC;
+            mem.push_back(std::move(m));
         }
-        const int R = (int)batch.size();
-        const int RC = size_class(R);
-        Entry *e = nullptr;
-        std::string why;
-        const int rc = acquire_entry(s, lock, key, RC, stream, &e, &why);
-        if (rc != ST_OK) {
-            finish(s, batch, rc, nullptr, Clock::now(), nullptr, why);
+        if (failed0 || mem.empty()) {
             s->cv.notify_all();
             continue;
         }
-        e->last_used = ++s->clock;
         ++s->busy_workers;
         const auto admitted = Clock::now();
         lock.unlock();
 
         // ---- solve (no lock held) ----
-        const int64_t n1 = (int64_t)batch[0].rhs.size();
-        st_solve_info info{};
-        std::vector<std::vector<double>> u(R, std::vector<double>(n1));
-        int st = st_set_stream(e->h, stream);
-        double *in = key.coeffs ? e->u : e->f;
-        for (int r = 0; r < R && st == ST_OK; ++r)
-            if (cudaMemcpyAsync(in + r * n1, batch[r].rhs.data(), n1 * sizeof(double),
-                                cudaMemcpyHostToDevice, stream) != cudaSuccess)
-                st = ST_ERR_CUDA;
-        if (st == ST_OK && RC > R &&
-            cudaMemsetAsync(in + R * n1, 0, (size_t)(RC - R) * n1 * sizeof(double), stream) !=
-                cudaSuccess)
-            st = ST_ERR_CUDA;
-        if (st == ST_OK && key.coeffs) st = st_load_coeffs(e->h, e->u, e->f);
-        if (st == ST_OK) st = st_solve(e->h, e->f, key.tol, e->u, 0, &info);
-        if (st == ST_OK || st == ST_ERR_NO_CONVERGENCE) {
-            for (int r = 0; r < R; ++r)
-                if (cudaMemcpyAsync(u[r].data(), e->u + r * n1, n1 * sizeof(double),
-                                    cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        const int nm = (int)mem.size();
+        std::vector<st_solve_info> infos(nm);
+        std::vector<std::vector<std::vector<double>>> us(nm);
+        int st = ST_OK;
+        for (int i = 0; i < nm && st == ST_OK; ++i) {
+            Member &m = mem[i];
+            Entry *e = m.e;
+            const int64_t n1 = (int64_t)m.batch[0].rhs.size();
+            us[i].assign(m.R, std::vector<double>(n1));
+            st = st_set_stream(e->h, stream);
+            double *in = m.key.coeffs ? e->u : e->f;
+            for (int r = 0; r < m.R && st == ST_OK; ++r)
+                if (cudaMemcpyAsync(in + r * n1, m.batch[r].rhs.data(), n1 * sizeof(double),
+                                    cudaMemcpyHostToDevice, stream) != cudaSuccess)
                     st = ST_ERR_CUDA;
+            if (st == ST_OK && m.RC > m.R &&
+                cudaMemsetAsync(in + m.R * n1, 0, (size_t)(m.RC - m.R) * n1 * sizeof(double),
+                                stream) != cudaSuccess)
+                st = ST_ERR_CUDA;
+            if (st == ST_OK && m.key.coeffs) st = st_load_coeffs(e->h, e->u, e->f);
+        }
+        if (st == ST_OK) {
+            if (nm == 1) {
+                st = st_solve(mem[0].e->h, mem[0].e->f, tol0, mem[0].e->u, 0, &infos[0]);
+            } else {
+                std::vector<st_handle> hs(nm);
+                std::vector<const double *> fs(nm);
+                std::vector<double *> uu(nm);
+                for (int i = 0; i < nm; ++i) {
+                    hs[i] = mem[i].e->h;
+                    fs[i] = mem[i].e->f;
+                    uu[i] = mem[i].e->u;
+                }
+                st = st_solve_group(nm, hs.data(), fs.data(), tol0, uu.data(), 0, infos.data());
+            }
+        }
+        if (st == ST_OK || st == ST_ERR_NO_CONVERGENCE) {
+            for (int i = 0; i < nm; ++i) {
+                const int64_t n1 = (int64_t)mem[i].batch[0].rhs.size();
+                for (int r = 0; r < mem[i].R; ++r)
+                    if (cudaMemcpyAsync(us[i][r].data(), mem[i].e->u + r * n1, n1 * sizeof(double),
+                                        cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+                        st = ST_ERR_CUDA;
+            }
             if (cudaStreamSynchronize(stream) != cudaSuccess) st = ST_ERR_CUDA;
         }
         if (st == ST_ERR_CUDA) cudaGetLastError();
 
         const std::string solve_msg = (st == ST_OK) ? std::string() : std::string(st_last_error());
+        int greq = 0;
+        for (const Member &m : mem) greq += m.R;
         lock.lock();
-        finish(s, batch, st, &info, admitted, &u, solve_msg);
-        e->busy = false;
+        for (int i = 0; i < nm; ++i) {
+            const bool ran = st == ST_OK || st == ST_ERR_NO_CONVERGENCE;
+            const int status = ran ? infos[i].status : st;
+            finish(s, mem[i].batch, status, &infos[i], admitted, &us[i],
+                   status == ST_OK ? std::string() : solve_msg, greq);
+            mem[i].e->busy = false;
+        }
         --s->busy_workers;
         s->cv.notify_all();
     }
@@ -392,6 +506,7 @@ void st_serve_opts_default(st_server_opts *o) {
     o->max_batch = 8;
     o->start_paused = 0;
     o->batch_dofs = 8388608;
+    o->group_members = 8;
     st_options_default(&o->opt);
     // per-setup kernel tuning would time candidate kernels for every new
     // configuration on the serving path
@@ -403,7 +518,8 @@ int st_serve_start(st_server *out, const st_server_opts *o) {
     *out = nullptr;
     st_server_opts oo;
     if (o) oo = *o; else st_serve_opts_default(&oo);
-    if (oo.workers < 1 || oo.workers > 64 || oo.max_batch < 1 || oo.max_batch > 32)
+    if (oo.workers < 1 || oo.workers > 64 || oo.max_batch < 1 || oo.max_batch > 32 ||
+        oo.group_members < 0)
         return ST_ERR_INVALID_ARG;
     st_server_s *s = new st_server_s();
     s->o = oo;

@@ -33,7 +33,8 @@ SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_
            "st_time_prolongation", "st_level_shape", "st_space_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
            "st_serve_submit", "st_serve_resume", "st_serve_pause", "st_serve_cancel", "st_serve_poll", "st_serve_wait",
            "st_serve_stop", "st_setup_partitioned", "st_partition_plan", "st_comm_nccl_unique_id",
-           "st_comm_nccl_create", "st_comm_nccl_destroy", "st_solve_history", "st_solve_host"]
+           "st_comm_nccl_create", "st_comm_nccl_destroy", "st_solve_history", "st_solve_host",
+           "st_solve_group"]
 PROF_CLASSES = ["stencil64", "stencil32", "gemm64", "gemm32", "shift", "update", "transfer",
                 "vector", "dot", "tc", "spec", "stencil_df", "minres"]
 
@@ -53,13 +54,14 @@ class StOptions(ctypes.Structure):
 
 class StSolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("refinements", ctypes.c_int), ("status", ctypes.c_int),
-                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("host_syncs", ctypes.c_int), ("vector_launches", ctypes.c_int)]
 
 
 class StServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int),
                 ("max_batch", ctypes.c_int), ("opt", StOptions), ("start_paused", ctypes.c_int),
-                ("batch_dofs", ctypes.c_longlong)]
+                ("batch_dofs", ctypes.c_longlong), ("group_members", ctypes.c_int)]
 
 
 class StRequest(ctypes.Structure):
@@ -74,7 +76,9 @@ class StResult(ctypes.Structure):
                 ("refinements", ctypes.c_int), ("rel_residual", ctypes.c_double),
                 ("queue_seconds", ctypes.c_double), ("solve_seconds", ctypes.c_double),
                 ("latency_seconds", ctypes.c_double), ("batch_size", ctypes.c_int),
-                ("n_dofs", ctypes.c_int64), ("error", ctypes.c_char * 128)]
+                ("n_dofs", ctypes.c_int64), ("error", ctypes.c_char * 128),
+                ("group_requests", ctypes.c_int), ("host_syncs", ctypes.c_int),
+                ("vector_launches", ctypes.c_int)]
 
 
 ST_ERR_NOT_READY = -10
@@ -135,6 +139,8 @@ def load():
         "st_space_prolongation": (I, [P, I, I, ip, ip, dp]),
         "st_solve": (I, [P, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
         "st_solve_host": (I, [P, I, P, D, P, I, ctypes.POINTER(StSolveInfo)]),
+        "st_solve_group": (I, [I, ctypes.POINTER(P), ctypes.POINTER(P), D, ctypes.POINTER(P), I,
+                               ctypes.POINTER(StSolveInfo)]),
         "st_autotune": (I, [P, ip, dp]),
         "st_profile": (I, [P, I]),
         "st_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_int64), dp, dp, dp]),
@@ -324,7 +330,8 @@ class Solver:
             _check(rc)
         return {"iterations": info.iterations, "refinements": info.refinements,
                 "status": info.status,
-                "rel_residual": info.rel_residual, "seconds": info.seconds, "rc": rc}
+                "rel_residual": info.rel_residual, "seconds": info.seconds,
+                "host_syncs": info.host_syncs, "vector_launches": info.vector_launches, "rc": rc}
 
     def solve_host(self, rhs, u, tol=1e-8, use_guess=False, check=True):
         """st_solve_host: rhs and u are contiguous float64 CPU tensors of
@@ -348,7 +355,8 @@ class Solver:
             _check(rc)
         return {"iterations": info.iterations, "refinements": info.refinements,
                 "status": info.status, "rel_residual": info.rel_residual,
-                "seconds": info.seconds, "rc": rc}
+                "seconds": info.seconds, "host_syncs": info.host_syncs,
+                "vector_launches": info.vector_launches, "rc": rc}
 
     def set_wait_limit(self, seconds):
         """Bound of the tensor-core kernels' device-side waits (seconds)."""
@@ -450,12 +458,33 @@ class Solver:
         return P
 
 
+def solve_group(solvers, rhs, u, tol=1e-8, use_guess=False, check=True):
+    """st_solve_group: solve the problems of several Solver handles together
+    (one launch per Krylov vector operation over all their right-hand sides);
+    rhs[k], u[k] are member k's device vectors.  Returns one info dict per
+    member."""
+    n = len(solvers)
+    if n == 0 or len(rhs) != n or len(u) != n:
+        raise ValueError("one rhs and one u per solver")
+    P = ctypes.c_void_p
+    hs = (P * n)(*[s._h for s in solvers])
+    rp = (P * n)(*[_dptr(r, s.ndofs, "rhs") for s, r in zip(solvers, rhs)])
+    up = (P * n)(*[_dptr(x, s.ndofs, "u") for s, x in zip(solvers, u)])
+    infos = (StSolveInfo * n)()
+    rc = _lib.st_solve_group(n, hs, rp, float(tol), up, int(bool(use_guess)), infos)
+    if check:
+        _check(rc)
+    return [{"iterations": i.iterations, "refinements": i.refinements, "status": i.status,
+             "rel_residual": i.rel_residual, "seconds": i.seconds, "host_syncs": i.host_syncs,
+             "vector_launches": i.vector_launches, "rc": rc} for i in infos]
+
+
 class Server:
     """Continuous-batching solve server (st_serve_*): submit host right-hand
     sides of any configuration, poll or wait for host solutions."""
 
     def __init__(self, workers=4, max_batch=8, hbm_budget=0, paused=False, batch_dofs=None,
-                 **opts):
+                 group_members=None, **opts):
         lib = load()
         self.o = StServerOpts()
         lib.st_serve_opts_default(ctypes.byref(self.o))
@@ -465,6 +494,8 @@ class Server:
         self.o.start_paused = 1 if paused else 0
         if batch_dofs is not None:
             self.o.batch_dofs = int(batch_dofs)
+        if group_members is not None:
+            self.o.group_members = int(group_members)
         opts.setdefault("autotune", 0)  # as st_serve_opts_default: no per-setup tuning
         self.o.opt = options(**opts)
         self._s = ctypes.c_void_p()

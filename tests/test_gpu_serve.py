@@ -62,6 +62,12 @@ def test_alone_vs_mix(st, prec, outer):
     sizes = [res["batch_size"] for res, _ in mixed]
     # every repeated configuration was solved as one batch
     assert sizes == [MIX.count(m) for m in MIX], sizes
+    groups = [res["group_requests"] for res, _ in mixed]
+    if outer == "ir":  # the refinement server groups configurations (how many per call
+        # depends on which worker builds which setup first: the lock is released meanwhile)
+        assert all(g >= b for g, b in zip(groups, sizes)), groups
+    else:  # other solvers: each configuration's batch alone
+        assert groups == sizes, groups
     for (d, spans, p, N, c), ua, (res, um) in zip(reqs, alone, mixed):
         assert res["status"] == 0
         # each right-hand side is refined on its own: same bits alone and in the mix
@@ -168,3 +174,41 @@ def test_pause_queues_and_batches(st):
         assert res["status"] == 0 and r2["status"] == 0
         assert np.array_equal(u, u2)
     ref.stop()
+
+
+def test_group_members_off(st):
+    """group_members = 1: every configuration's batch is solved alone, with
+    the same bits as in a group."""
+    opts = dict(precision="mixed_tf32", outer="ir", basis="spectral")
+    reqs = _requests()
+    out = {}
+    for gm in (1, 8):
+        srv = st.Server(workers=1, max_batch=4, paused=True, group_members=gm, **opts)
+        tickets = [srv.submit(d, p, spans, N, c, tol=1e-10, coeffs=True)
+                   for d, spans, p, N, c in reqs]
+        srv.resume()
+        out[gm] = [srv.wait(t, timeout=120.0) for t in tickets]
+        srv.stop()
+    # one worker: the oldest configuration first, then (oldest first) every
+    # other configuration with no more dofs per request; then the rest
+    ndofs = [A.Problem(d, spans, p, 2, N, theta=1.0).ndofs for d, spans, p, N in MIX]
+    expect, left = [0] * len(MIX), list(range(len(MIX)))
+    while left:
+        lead = left[0]
+        members = {MIX[i] for i in left if ndofs[i] <= ndofs[lead]}
+        group = [i for i in left if MIX[i] in members]
+        for i in group:
+            expect[i] = len(group)
+        left = [i for i in left if i not in group]
+    for (r1, u1), (r8, u8), e in zip(out[1], out[8], expect):
+        assert r1["status"] == 0 and r8["status"] == 0
+        assert r1["group_requests"] == r1["batch_size"]
+        assert r8["group_requests"] == e, ([r["group_requests"] for r, _ in out[8]], expect)
+        assert np.array_equal(u1, u8)
+    # one group call reads its reductions back fewer times than the batches
+    # alone (one solve call per configuration; the MIX configurations differ
+    # in their dof counts)
+    calls1 = {r["n_dofs"]: r["host_syncs"] for r, _ in out[1]}
+    assert len(calls1) == len(set(MIX))
+    first_group = [i for i in range(len(MIX)) if expect[i] == expect[0]]
+    assert out[8][0][0]["host_syncs"] < sum(calls1[ndofs[i]] for i in set(first_group))
