@@ -93,25 +93,36 @@ __device__ __forceinline__ double from_c<double, dfloat>(dfloat x) {
     return df_to_double(x);
 }
 
-template <int DIM>
+// Spatial tile of one CTA: TX x TY x TZ output points, ZS threads per (x, y)
+// column (each owning TZ / ZS of its z points).  The double-float 3D tile is
+// twice as deep with two threads per column: the x- and y-passes are redone
+// on a z halo of 2p slices, which costs 1.5x instead of 2x over the outputs
+// (68 instead of 83 multiply-adds per output and time plane at p = 2), with
+// the same accumulators per thread.
+template <int DIM, bool DF>
 struct TileShape;
-template <>
-struct TileShape<1> {
-    static constexpr int TX = 128, TY = 1, TZ = 1;
+template <bool DF>
+struct TileShape<1, DF> {
+    static constexpr int TX = 128, TY = 1, TZ = 1, ZS = 1;
+};
+template <bool DF>
+struct TileShape<2, DF> {
+    static constexpr int TX = 32, TY = 16, TZ = 1, ZS = 1;
 };
 template <>
-struct TileShape<2> {
-    static constexpr int TX = 32, TY = 16, TZ = 1;
+struct TileShape<3, false> {
+    static constexpr int TX = 16, TY = 8, TZ = 4, ZS = 1;
 };
 template <>
-struct TileShape<3> {
-    static constexpr int TX = 16, TY = 8, TZ = 4;
+struct TileShape<3, true> {
+    static constexpr int TX = 16, TY = 8, TZ = 8, ZS = 2;
 };
 
 template <typename T, int P, int DIM>  // T: compute type
 struct StencilSmem {
-    using TS = TileShape<DIM>;
-    static constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ;
+    using TS = TileShape<DIM, std::is_same<T, dfloat>::value>;
+    static constexpr int TX = TS::TX, TY = TS::TY, TZ = TS::TZ, ZS = TS::ZS;
+    static constexpr int TZL = TZ / ZS;  // z points per thread
     static constexpr int HX = P, HY = (DIM >= 2) ? P : 0, HZ = (DIM >= 3) ? P : 0;
     static constexpr int SX = TX + 2 * HX, SY = TY + 2 * HY, SZ = TZ + 2 * HZ;
     static constexpr int W = 2 * P + 1;
@@ -123,17 +134,21 @@ struct StencilSmem {
     // same time (a barrier separates the z-pass reads from the next staging)
     static constexpr int nR1 = (nS > 2 * nAA) ? nS : 2 * nAA;
     static constexpr size_t bytes = sizeof(T) * (nR1 + 2 * nA + nBand);
-    static constexpr int threads = TX * TY;
+    static constexpr int threads = TX * TY * ZS;
+    // the deep tile (64 KB): three CTAs per SM (24 warps) where N_t <= 4 lets
+    // the accumulators fit 80 registers, else two
+    static constexpr int min_blocks(int ntc) { return ZS > 1 ? ((ntc > 0 && ntc <= 4) ? 3 : 2) : 1; }
 };
 
 // NTC > 0: N_t fixed at compile time (exact-length loops, fewer registers
 // for the N_t x TZ accumulators); NTC = 0: N_t from tc.nt, loops over NTMAX
 template <typename T, typename C, int P, int DIM, int NTC = 0>
-__global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
+__global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads,
+                                  StencilSmem<C, P, DIM>::min_blocks(NTC))
     k_stencil(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out, Bands<T> bands,
               Grid g, const __grid_constant__ TimeCoefs<C> tc, int slabs_per_prob, int slab0, int tiles_x, int tiles_y) {
     using SM = StencilSmem<C, P, DIM>;
-    constexpr int TX = SM::TX, TY = SM::TY, TZ = SM::TZ;
+    constexpr int TX = SM::TX, TY = SM::TY, TZ = SM::TZ, TZL = SM::TZL;
     constexpr int HX = SM::HX, HY = SM::HY, HZ = SM::HZ;
     constexpr int SX = SM::SX, SY = SM::SY, SZ = SM::SZ, W = SM::W;
     constexpr int NTH = SM::threads;
@@ -181,11 +196,12 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
             bKz[e] = (gz < nz) ? to_c<C>(bands.K[2][(long long)gz * W + e % W]) : C(0);
         }
 
-    const int tx = tid % TX, ty = tid / TX;
-    Acc<C> acc[TZ][NL];
-    C mprev[TZ];
+    const int tx = tid % TX, ty = (tid / TX) % TY;
+    const int za = (tid / (TX * TY)) * TZL;  // this thread's first z point in the tile
+    Acc<C> acc[TZL][NL];
+    C mprev[TZL];
 #pragma unroll
-    for (int a = 0; a < TZ; ++a) mprev[a] = C(0);
+    for (int a = 0; a < TZL; ++a) mprev[a] = C(0);
 
     const T *uslab = u + (long long)slab * nt * nxyz;
     const bool first = (slab % slabs_per_prob) == 0;
@@ -263,7 +279,8 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
         }
         // z-pass and accumulation into this thread's output points
 #pragma unroll
-        for (int a = 0; a < TZ; ++a) {
+        for (int al = 0; al < TZL; ++al) {
+            const int a = za + al;
             C m, k;
             if (DIM >= 3) {
                 Acc<C> am, ak;
@@ -282,13 +299,13 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
                 k = pk[ty * TX + tx];
             }
             if (jj < 0) {
-                mprev[a] = m;
+                mprev[al] = m;
             } else {
 #pragma unroll
                 for (int i = 0; i < NL; ++i)
                     if (i < nt) {
-                        acc[a][i].add(tc.CK[i * NTMAX + jj], m);
-                        acc[a][i].add(tc.CM[i * NTMAX + jj], k);
+                        acc[al][i].add(tc.CK[i * NTMAX + jj], m);
+                        acc[al][i].add(tc.CM[i * NTMAX + jj], k);
                     }
             }
         }
@@ -298,8 +315,9 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads)
     const int gx = x0 + tx, gy = y0 + ty;
     if (gx >= nx || gy >= ny) return;
 #pragma unroll
-    for (int a = 0; a < TZ; ++a) {
-        const int gz = z0 + a;
+    for (int al = 0; al < TZL; ++al) {
+        const int a = al;  // accumulator index; the z point is za + al
+        const int gz = z0 + za + al;
         if (gz >= nz) break;
         const long long sp = ((long long)gz * ny + gy) * nx + gx;
         const long long base = (long long)slab * nt * nxyz + sp;
