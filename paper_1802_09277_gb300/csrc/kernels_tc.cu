@@ -682,6 +682,270 @@ static cudaError_t launch_tc_pipe(TcArgs a, cudaStream_t s, int nsm, int ctas_pe
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// K-streamed pipelined variant, for contractions whose K is too long for the
+// register prefetch of k_tc_axis_pipe (the n = 129 axes of a 128-span p = 3
+// grid): the weight operand (N = n_pad <= 256 rows, all of K, zero padded)
+// stays in shared memory for the CTA's life; each 128-column tile streams its
+// activation rows in steps of PK_KB 16-byte K chunks through two
+// shared-memory buffers, with the next two steps held in registers, and its
+// MMAs chain into one of two TMEM accumulators:
+//     wait MMA(s-2) -> stage step s -> MMA(s) -> load step s+2
+//     -> (last step of a tile) drain the previous tile's accumulator.
+// Strided axis (MODE_S) and the contiguous axis as MODE_XT only (the weight
+// is the N operand).  Step s completes on mbarrier s & 1 with parity
+// (s >> 1) & 1, tile t on the accumulator barrier t & 1 with parity
+// (t >> 1) & 1.
+// ---------------------------------------------------------------------------
+constexpr int PK_KB = 6;  // 16-byte K chunks per step: three MMA K steps
+constexpr size_t PK_SMEM_MAX = 225 * 1024;
+
+template <int KIND>
+struct PkTraits {
+    static constexpr int EPC = 16 / KindTraits<KIND>::ESZ;
+    static constexpr int PF = TC_COLS * PK_KB / TC_THREADS;  // chunks per thread and step
+    static_assert(TC_COLS * PK_KB % TC_THREADS == 0, "whole chunks per thread");
+};
+
+// Global -> registers: step chunks [kc0, kc0 + PK_KB) of column tile c0.
+template <int KIND, int MODE>
+__device__ __forceinline__ void pk_load(const TcArgs &a, long long c0, int kc0,
+                                        float (&pre)[PkTraits<KIND>::PF][PkTraits<KIND>::EPC]) {
+    constexpr int EPC = PkTraits<KIND>::EPC, PF = PkTraits<KIND>::PF;
+#pragma unroll
+    for (int it = 0; it < PF; ++it) {
+        const int t = threadIdx.x + it * TC_THREADS;
+        if (MODE != 1) {
+            const int grp = t / (8 * PK_KB), rem = t % (8 * PK_KB);
+            const int kc = rem / 8, r = grp * 8 + rem % 8;
+            const long long c = c0 + r;
+            const int i0 = (kc0 + kc) * EPC;
+            if (a.vec4 && c < a.ncols && i0 + EPC <= a.n_in) {
+#pragma unroll
+                for (int j = 0; j < EPC; j += 4) {
+                    const float4 q = *reinterpret_cast<const float4 *>(a.in + c * a.n_in + i0 + j);
+                    pre[it][j] = q.x;
+                    pre[it][j + 1] = q.y;
+                    pre[it][j + 2] = q.z;
+                    pre[it][j + 3] = q.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < EPC; ++j) {
+                    const int i = i0 + j;
+                    pre[it][j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
+                }
+            }
+        } else {
+            const int kc = t / TC_COLS, r = t % TC_COLS;
+            const long long c = c0 + r;
+            const long long o = c / a.inner, ci = c % a.inner;
+#pragma unroll
+            for (int j = 0; j < EPC; ++j) {
+                const int i = (kc0 + kc) * EPC + j;
+                pre[it][j] = (c < a.ncols && i < a.n_in)
+                                 ? a.in[(o * a.n_in + i) * a.inner + ci]
+                                 : 0.f;
+            }
+        }
+    }
+}
+
+// Registers -> one step buffer (PK_KB chunks of 128 rows, MMA layout).
+template <int KIND, int MODE>
+__device__ __forceinline__ void pk_stage(unsigned char *xbuf, size_t xb,
+                                         const float (&pre)[PkTraits<KIND>::PF][PkTraits<KIND>::EPC]) {
+    constexpr int PF = PkTraits<KIND>::PF;
+#pragma unroll
+    for (int it = 0; it < PF; ++it) {
+        const int t = threadIdx.x + it * TC_THREADS;
+        int kc, r;
+        if (MODE != 1) {
+            const int grp = t / (8 * PK_KB), rem = t % (8 * PK_KB);
+            kc = rem / 8;
+            r = grp * 8 + rem % 8;
+        } else {
+            kc = t / TC_COLS;
+            r = t % TC_COLS;
+        }
+        stage16<KIND>(xbuf, TC_COLS, r, kc, pre[it], xb);
+    }
+}
+
+// One step's MMAs (single thread): K chunks kc0 .. kc0 + PK_KB of the
+// resident weight against the step buffer.
+template <int KIND>
+__device__ __forceinline__ void pk_mma(uint32_t wa, uint32_t xa, size_t wbytes, size_t xb,
+                                       int wrows, int kc0, bool first, uint32_t acc,
+                                       uint32_t idesc) {
+    using KT = KindTraits<KIND>;
+    const uint32_t lbo_w = (uint32_t)wrows * 16, lbo_x = TC_COLS * 16;
+    constexpr int NPROD = (KT::NSPLIT == 2) ? 3 : 1;  // split: (hi, hi), (hi, lo), (lo, hi)
+#pragma unroll
+    for (int st = 0; st < PK_KB / 2; ++st) {
+#pragma unroll
+        for (int q = 0; q < NPROD; ++q) {
+            const uint32_t wo = (q == 2) ? (uint32_t)wbytes : 0u;
+            const uint32_t xo = (q == 1) ? (uint32_t)xb : 0u;
+            const uint64_t dx = tc::make_sdesc(xa + xo + 2 * st * lbo_x, lbo_x, 128);
+            const uint64_t dw =
+                tc::make_sdesc(wa + wo + (uint32_t)(kc0 + 2 * st) * lbo_w, lbo_w, 128);
+            const uint32_t accum = (!first || st > 0 || q > 0) ? 1u : 0u;
+            tc::mma<KT::FMT>(acc, dx, dw, idesc, accum);
+        }
+    }
+}
+
+template <int KIND, int MODE>
+__global__ void __launch_bounds__(TC_THREADS) k_tc_axis_pipek(const __grid_constant__ TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar_x[2], mbar_acc[2];
+    __shared__ uint32_t tmem_base;
+    using KT = KindTraits<KIND>;
+    constexpr int EPC = PkTraits<KIND>::EPC, PF = PkTraits<KIND>::PF;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int KC = a.k_pad / EPC;  // a multiple of PK_KB
+    const int NC = KC / PK_KB;     // steps per tile
+    const int wrows = a.n_pad;
+    const size_t wbytes = (size_t)wrows * KC * 16, xb = (size_t)TC_COLS * PK_KB * 16;
+    unsigned char *base = smem + ((128u - (tc::smem_u32(smem) & 127u)) & 127u);
+    unsigned char *wtile = base;
+    unsigned char *xbuf0 = base + KT::NSPLIT * wbytes;  // two buffers of NSPLIT * xb
+    const uint32_t acc_cols = tc_acc_cols(1, 1, a.n_pad);
+    const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
+    const long long my_tiles =
+        (blockIdx.x < ntiles) ? (ntiles - 1 - (long long)blockIdx.x) / gridDim.x + 1 : 0;
+    const long long S = my_tiles * NC;  // steps of this CTA
+
+    if (tid == 0) {
+        tc::mbar_init(&mbar_x[0], 1);
+        tc::mbar_init(&mbar_x[1], 1);
+        tc::mbar_init(&mbar_acc[0], 1);
+        tc::mbar_init(&mbar_acc[1], 1);
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * acc_cols);
+    stage_w<KIND>(a, wtile, wrows, 0, KC, wbytes);  // made visible by the first step's fence
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = tc::make_idesc(KT::FMT, 128, a.n_pad);
+    auto tile_of = [&](long long ti) { return (long long)blockIdx.x + ti * gridDim.x; };
+
+    // after a wait ran out: record it, let the MMAs of step `last` (and so all
+    // before it) finish, bounded, before the tensor memory is released
+    auto give_up = [&](long long last) {
+        if (last >= 0)
+            tc::mbar_wait_bounded(&mbar_x[last & 1], (uint32_t)((last >> 1) & 1), TC_DRAIN_NS);
+        if (tid == 0) atomicExch(a.err, 1);
+    };
+    // step s with its data in `cur`; the step s + 2 is loaded into `cur`.  False if
+    // a wait ran out (the CTA gives up).
+    auto body = [&](long long s, float (&cur)[PF][EPC]) -> bool {
+        const int b = (int)(s & 1);
+        const long long ti = s / NC;
+        const int ch = (int)(s % NC);
+        unsigned char *xbuf = xbuf0 + (size_t)b * KT::NSPLIT * xb;
+        if (s >= 2) {  // the MMAs of step s - 2 have read this buffer
+            const bool ok =
+                tc::mbar_wait_bounded(&mbar_x[b], (uint32_t)(((s - 2) >> 1) & 1), a.wait_ns);
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                give_up(s - 1);
+                return false;
+            }
+            tc::fence_after_sync();
+        }
+        pk_stage<KIND, MODE>(xbuf, xb, cur);
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            pk_mma<KIND>(tc::smem_u32(wtile), tc::smem_u32(xbuf), wbytes, xb, wrows, ch * PK_KB,
+                         ch == 0, tmem + (uint32_t)(ti & 1) * acc_cols, idesc);
+            tc::commit(&mbar_x[b]);
+            if (ch == NC - 1) tc::commit(&mbar_acc[ti & 1]);
+        }
+        if (s + 2 < S)
+            pk_load<KIND, MODE>(a, tile_of((s + 2) / NC) * TC_COLS, (int)((s + 2) % NC) * PK_KB, cur);
+        if (ch == NC - 1 && ti >= 1) {  // drain the previous tile while this one's MMAs run
+            const int pb = (int)((ti - 1) & 1);
+            const bool ok = tc::mbar_wait_bounded(&mbar_acc[pb], (uint32_t)(((ti - 1) >> 1) & 1),
+                                                  a.wait_ns);
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                give_up(s);
+                return false;
+            }
+            tc::fence_after_sync();
+            pipe_epilogue<MODE>(a, tile_of(ti - 1) * TC_COLS, tmem + (uint32_t)pb * acc_cols, 1);
+            // these tensor-memory reads precede the next MMA into that accumulator
+            tc::fence_before_sync();
+        }
+        return true;
+    };
+
+    float pre0[PF][EPC], pre1[PF][EPC];
+    if (S > 0) pk_load<KIND, MODE>(a, tile_of(0) * TC_COLS, 0, pre0);
+    if (S > 1) pk_load<KIND, MODE>(a, tile_of(1 / NC) * TC_COLS, (1 % NC) * PK_KB, pre1);
+    bool failed = false;
+    long long s = 0;
+    for (; s + 1 < S; s += 2) {
+        if (!body(s, pre0) || !body(s + 1, pre1)) {
+            failed = true;
+            break;
+        }
+    }
+    if (!failed && s < S && !body(s, pre0)) failed = true;
+    if (!failed && S > 0) {  // the last tile
+        const long long tl = my_tiles - 1;
+        const bool ok = tc::mbar_wait_bounded(&mbar_acc[tl & 1], (uint32_t)((tl >> 1) & 1),
+                                              a.wait_ns);
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            give_up(S - 1);
+        } else {
+            tc::fence_after_sync();
+            pipe_epilogue<MODE>(a, tile_of(tl) * TC_COLS, tmem + (uint32_t)(tl & 1) * acc_cols, 1);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 2 * acc_cols);
+}
+
+template <int KIND, int MODE>
+static cudaError_t launch_tc_pipek(TcArgs a, cudaStream_t s, int nsm, int ctas_per_sm) {
+    using KT = KindTraits<KIND>;
+    constexpr int EPC = PkTraits<KIND>::EPC;
+    if (MODE == 0 || a.n_pad > 256) return cudaErrorNotSupported;
+    const int kstep = PK_KB * EPC;  // K per step
+    a.k_pad = (a.n_in + kstep - 1) / kstep * kstep;
+    const int KC = a.k_pad / EPC;
+    const size_t wbytes = (size_t)a.n_pad * KC * 16, xb = (size_t)TC_COLS * PK_KB * 16;
+    const size_t smem = KT::NSPLIT * (wbytes + 2 * xb) + 128;  // + alignment slack
+    if (smem > PK_SMEM_MAX) return cudaErrorNotSupported;
+    // descriptor addresses (14 bits of address / 16) cover the shared memory
+    const uint32_t acc_cols = tc_acc_cols(1, 1, a.n_pad);
+    static std::atomic<unsigned long long> attr{0};
+    {
+        const cudaError_t e =
+            smem_attr_once((const void *)k_tc_axis_pipek<KIND, MODE>, (int)PK_SMEM_MAX, attr);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = (int)(512 / (2 * acc_cols));
+    const int by_smem = (int)((228 * 1024) / (smem + 1024));
+    if (by_smem < per_sm) per_sm = by_smem;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
+    long long grid = (long long)nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    if (grid <= 0) return cudaSuccess;
+    k_tc_axis_pipek<KIND, MODE><<<(unsigned)grid, TC_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int KIND, int MODE>
 static cudaError_t launch_tc_t(TcArgs a, cudaStream_t s, int nsm, int ctas_per_sm) {
     using KT = KindTraits<KIND>;
@@ -769,6 +1033,18 @@ cudaError_t launch_tc_axis(int kind, int mode, const float *in, float *out, cons
     else
         e = mode == 0 ? launch_tc_pipe<tc::FMT_BF16, 2>(a, s, nsm, ctas_per_sm)
                       : launch_tc_pipe<tc::FMT_BF16, 1>(a, s, nsm, ctas_per_sm);
+    if (e != cudaErrorNotSupported) return e;
+    cudaGetLastError();
+    // K too long for the register prefetch: the K-streamed pipeline
+    if (kind == KIND_TF32X3)
+        e = mode == 0 ? launch_tc_pipek<KIND_TF32X3, 2>(a, s, nsm, ctas_per_sm)
+                      : launch_tc_pipek<KIND_TF32X3, 1>(a, s, nsm, ctas_per_sm);
+    else if (kind == tc::FMT_TF32)
+        e = mode == 0 ? launch_tc_pipek<tc::FMT_TF32, 2>(a, s, nsm, ctas_per_sm)
+                      : launch_tc_pipek<tc::FMT_TF32, 1>(a, s, nsm, ctas_per_sm);
+    else
+        e = mode == 0 ? launch_tc_pipek<tc::FMT_BF16, 2>(a, s, nsm, ctas_per_sm)
+                      : launch_tc_pipek<tc::FMT_BF16, 1>(a, s, nsm, ctas_per_sm);
     if (e != cudaErrorNotSupported) return e;
     cudaGetLastError();
     if (kind == KIND_TF32X3)
