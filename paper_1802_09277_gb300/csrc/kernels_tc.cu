@@ -39,6 +39,7 @@ namespace {
 
 constexpr int TC_THREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lane quarter w % 4
 constexpr int TC_COLS = 128;  // columns (GEMM rows of the activation operand) per tile
+static_assert(TC_THREADS % TC_COLS == 0, "a thread stages one column of every tile");
 constexpr uint64_t TC_DRAIN_NS = 1000000000ull;  // after a timeout: MMAs in flight finish
 constexpr int KIND_TF32X3 = 3;  // split TF32 (see above); MMA format TF32
 
@@ -113,6 +114,21 @@ struct TcArgs {
     unsigned long long wait_ns;  // bound of each wait for the MMAs (0: test once)
     int w_tma;         // pipelined kernel: the weight operand arrives by TMA (tensor map)
 };
+
+// A strided-axis column c = (outer o, inner index ci): src = in + o n_in inner + ci.
+// One division per column (32-bit when the operands fit), not per chunk.
+__device__ __forceinline__ const float *col_src(const TcArgs &a, long long c) {
+    long long o, ci;
+    if (c < 0x7fffffffLL && a.inner < 0x7fffffffLL) {
+        const unsigned q = (unsigned)c / (unsigned)a.inner;
+        o = q;
+        ci = c - (long long)q * a.inner;
+    } else {
+        o = c / a.inner;
+        ci = c - o * a.inner;
+    }
+    return a.in + o * a.n_in * a.inner + ci;
+}
 
 // Stage 16-byte chunks [k0, k0 + kcs) of the weight operand (rows = output
 // modes, zero padded) as a K-major tile of wrows rows.
@@ -204,12 +220,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis(const __grid_constant__ 
                     stage16<KIND>(xtile, TC_COLS, r, kc, v, xbytes);
                 }
             } else {
-                // lanes: consecutive columns (consecutive inner index), same chunk
+                // lanes: consecutive columns (consecutive inner index), same chunk;
+                // a thread's column is the same for all its chunks
+                const int r = tid % TC_COLS;
+                const long long c = c0 + r;
+                const float *src = col_src(a, c);
                 for (int t = tid; t < TC_COLS * kcs; t += TC_THREADS) {
-                    const int kc = t / TC_COLS, r = t % TC_COLS;
-                    const long long c = c0 + r;
-                    const long long o = c / a.inner, ci = c % a.inner;
-                    const float *src = a.in + o * a.n_in * a.inner + ci;
+                    const int kc = t / TC_COLS;
                     float v[8];
 #pragma unroll
                     for (int j = 0; j < EPC; ++j) {
@@ -339,6 +356,9 @@ __device__ __forceinline__ void pipe_load(const TcArgs &a, long long c0, int KC,
                                                       [16 / KindTraits<KIND>::ESZ]) {
     constexpr int EPC = 16 / KindTraits<KIND>::ESZ;
     constexpr int PF = PipeTraits<EPC>::PF;
+    // MODE_S: a thread's column is the same for all its chunks
+    const long long cs = c0 + threadIdx.x % TC_COLS;
+    const float *src = (MODE == 1) ? col_src(a, cs) : nullptr;
 #pragma unroll
     for (int it = 0; it < PF; ++it) {
         const int t = threadIdx.x + it * TC_THREADS;
@@ -365,14 +385,11 @@ __device__ __forceinline__ void pipe_load(const TcArgs &a, long long c0, int KC,
                 }
             }
         } else {
-            const int kc = t / TC_COLS, r = t % TC_COLS;
-            const long long c = c0 + r;
-            const long long o = c / a.inner, ci = c % a.inner;
-            const float *src = a.in + o * a.n_in * a.inner + ci;
+            const int kc = t / TC_COLS;
 #pragma unroll
             for (int j = 0; j < EPC; ++j) {
                 const int i = kc * EPC + j;
-                pre[it][j] = (c < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
+                pre[it][j] = (cs < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
             }
         }
     }
@@ -705,71 +722,81 @@ template <int KIND>
 struct PkTraits {
     static constexpr int EPC = 16 / KindTraits<KIND>::ESZ;
     static constexpr int PF = TC_COLS * PK_KB / TC_THREADS;  // chunks per thread and step
+    static constexpr int NPT = PF * EPC;                     // values per thread and step
+    static constexpr int W = PK_KB * EPC;                    // K values per step
+    static constexpr int RP = W + 4;  // raw row pitch (floats): conflict-free 16-byte reads
     static_assert(TC_COLS * PK_KB % TC_THREADS == 0, "whole chunks per thread");
 };
 
-// Global -> registers: step chunks [kc0, kc0 + PK_KB) of column tile c0.
+// Global -> registers: K values [kc0 EPC, kc0 EPC + W) of column tile c0.
+// MODE_S: a thread loads its column's chunks (lanes: consecutive columns);
+// MODE_XT: lanes take consecutive values of a row (rows of n_in values need
+// not be 16-byte aligned), and the step is regrouped into chunks through
+// shared memory (pk_stage).
 template <int KIND, int MODE>
 __device__ __forceinline__ void pk_load(const TcArgs &a, long long c0, int kc0,
-                                        float (&pre)[PkTraits<KIND>::PF][PkTraits<KIND>::EPC]) {
-    constexpr int EPC = PkTraits<KIND>::EPC, PF = PkTraits<KIND>::PF;
+                                        float (&pre)[PkTraits<KIND>::NPT]) {
+    using PT = PkTraits<KIND>;
+    constexpr int EPC = PT::EPC;
+    if (MODE == 1) {
+        const long long c = c0 + threadIdx.x % TC_COLS;
+        const float *src = col_src(a, c);
 #pragma unroll
-    for (int it = 0; it < PF; ++it) {
-        const int t = threadIdx.x + it * TC_THREADS;
-        if (MODE != 1) {
-            const int grp = t / (8 * PK_KB), rem = t % (8 * PK_KB);
-            const int kc = rem / 8, r = grp * 8 + rem % 8;
-            const long long c = c0 + r;
-            const int i0 = (kc0 + kc) * EPC;
-            if (a.vec4 && c < a.ncols && i0 + EPC <= a.n_in) {
-#pragma unroll
-                for (int j = 0; j < EPC; j += 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(a.in + c * a.n_in + i0 + j);
-                    pre[it][j] = q.x;
-                    pre[it][j + 1] = q.y;
-                    pre[it][j + 2] = q.z;
-                    pre[it][j + 3] = q.w;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < EPC; ++j) {
-                    const int i = i0 + j;
-                    pre[it][j] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
-                }
-            }
-        } else {
-            const int kc = t / TC_COLS, r = t % TC_COLS;
-            const long long c = c0 + r;
-            const long long o = c / a.inner, ci = c % a.inner;
+        for (int it = 0; it < PT::PF; ++it) {
+            const int kc = threadIdx.x / TC_COLS + it * (TC_THREADS / TC_COLS);
 #pragma unroll
             for (int j = 0; j < EPC; ++j) {
                 const int i = (kc0 + kc) * EPC + j;
-                pre[it][j] = (c < a.ncols && i < a.n_in)
-                                 ? a.in[(o * a.n_in + i) * a.inner + ci]
-                                 : 0.f;
+                pre[it * EPC + j] = (c < a.ncols && i < a.n_in) ? src[(long long)i * a.inner] : 0.f;
             }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < PT::NPT; ++k) {
+            const int e = threadIdx.x + k * TC_THREADS;
+            const int r = e / PT::W, i = kc0 * EPC + e % PT::W;
+            const long long c = c0 + r;
+            pre[k] = (c < a.ncols && i < a.n_in) ? a.in[c * a.n_in + i] : 0.f;
         }
     }
 }
 
-// Registers -> one step buffer (PK_KB chunks of 128 rows, MMA layout).
+// Registers -> one step buffer (PK_KB chunks of 128 rows, MMA layout); MODE_XT
+// through the raw buffer (one barrier).  Lanes store consecutive rows of a
+// chunk (contiguous in the core-matrix layout).
 template <int KIND, int MODE>
-__device__ __forceinline__ void pk_stage(unsigned char *xbuf, size_t xb,
-                                         const float (&pre)[PkTraits<KIND>::PF][PkTraits<KIND>::EPC]) {
-    constexpr int PF = PkTraits<KIND>::PF;
+__device__ __forceinline__ void pk_stage(unsigned char *xbuf, size_t xb, float *raw,
+                                         const float (&pre)[PkTraits<KIND>::NPT]) {
+    using PT = PkTraits<KIND>;
+    constexpr int EPC = PT::EPC;
+    if (MODE == 1) {
 #pragma unroll
-    for (int it = 0; it < PF; ++it) {
-        const int t = threadIdx.x + it * TC_THREADS;
-        int kc, r;
-        if (MODE != 1) {
-            const int grp = t / (8 * PK_KB), rem = t % (8 * PK_KB);
-            kc = rem / 8;
-            r = grp * 8 + rem % 8;
-        } else {
-            kc = t / TC_COLS;
-            r = t % TC_COLS;
+        for (int it = 0; it < PT::PF; ++it) {
+            const int kc = threadIdx.x / TC_COLS + it * (TC_THREADS / TC_COLS);
+            stage16<KIND>(xbuf, TC_COLS, threadIdx.x % TC_COLS, kc, &pre[it * EPC], xb);
         }
-        stage16<KIND>(xbuf, TC_COLS, r, kc, pre[it], xb);
+    } else {
+#pragma unroll
+        for (int k = 0; k < PT::NPT; ++k) {
+            const int e = threadIdx.x + k * TC_THREADS;
+            raw[(e / PT::W) * PT::RP + e % PT::W] = pre[k];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < PT::PF; ++it) {
+            const int t = threadIdx.x + it * TC_THREADS;
+            const int kc = t / TC_COLS, r = t % TC_COLS;
+            float v[EPC];
+#pragma unroll
+            for (int j = 0; j < EPC; j += 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(raw + r * PT::RP + kc * EPC + j);
+                v[j] = q.x;
+                v[j + 1] = q.y;
+                v[j + 2] = q.z;
+                v[j + 3] = q.w;
+            }
+            stage16<KIND>(xbuf, TC_COLS, r, kc, v, xb);
+        }
     }
 }
 
@@ -803,7 +830,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis_pipek(const __grid_const
     __shared__ uint64_t mbar_x[2], mbar_acc[2];
     __shared__ uint32_t tmem_base;
     using KT = KindTraits<KIND>;
-    constexpr int EPC = PkTraits<KIND>::EPC, PF = PkTraits<KIND>::PF;
+    constexpr int EPC = PkTraits<KIND>::EPC, NPT = PkTraits<KIND>::NPT;
     const int tid = threadIdx.x, warp = tid >> 5;
     const int KC = a.k_pad / EPC;  // a multiple of PK_KB
     const int NC = KC / PK_KB;     // steps per tile
@@ -812,6 +839,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis_pipek(const __grid_const
     unsigned char *base = smem + ((128u - (tc::smem_u32(smem) & 127u)) & 127u);
     unsigned char *wtile = base;
     unsigned char *xbuf0 = base + KT::NSPLIT * wbytes;  // two buffers of NSPLIT * xb
+    float *raw = reinterpret_cast<float *>(xbuf0 + 2 * KT::NSPLIT * xb);  // MODE_XT regrouping
     const uint32_t acc_cols = tc_acc_cols(1, 1, a.n_pad);
     const long long ntiles = (a.ncols + TC_COLS - 1) / TC_COLS;
     const long long my_tiles =
@@ -842,7 +870,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis_pipek(const __grid_const
     };
     // step s with its data in `cur`; the step s + 2 is loaded into `cur`.  False if
     // a wait ran out (the CTA gives up).
-    auto body = [&](long long s, float (&cur)[PF][EPC]) -> bool {
+    auto body = [&](long long s, float (&cur)[NPT]) -> bool {
         const int b = (int)(s & 1);
         const long long ti = s / NC;
         const int ch = (int)(s % NC);
@@ -856,7 +884,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis_pipek(const __grid_const
             }
             tc::fence_after_sync();
         }
-        pk_stage<KIND, MODE>(xbuf, xb, cur);
+        pk_stage<KIND, MODE>(xbuf, xb, raw, cur);
         tc::fence_proxy_async_smem();
         tc::fence_before_sync();
         __syncthreads();
@@ -885,7 +913,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_tc_axis_pipek(const __grid_const
         return true;
     };
 
-    float pre0[PF][EPC], pre1[PF][EPC];
+    float pre0[NPT], pre1[NPT];
     if (S > 0) pk_load<KIND, MODE>(a, tile_of(0) * TC_COLS, 0, pre0);
     if (S > 1) pk_load<KIND, MODE>(a, tile_of(1 / NC) * TC_COLS, (1 % NC) * PK_KB, pre1);
     bool failed = false;
@@ -923,9 +951,9 @@ static cudaError_t launch_tc_pipek(TcArgs a, cudaStream_t s, int nsm, int ctas_p
     a.k_pad = (a.n_in + kstep - 1) / kstep * kstep;
     const int KC = a.k_pad / EPC;
     const size_t wbytes = (size_t)a.n_pad * KC * 16, xb = (size_t)TC_COLS * PK_KB * 16;
-    const size_t smem = KT::NSPLIT * (wbytes + 2 * xb) + 128;  // + alignment slack
+    const size_t rawb = (MODE == 2) ? (size_t)TC_COLS * PkTraits<KIND>::RP * 4 : 0;
+    const size_t smem = KT::NSPLIT * (wbytes + 2 * xb) + rawb + 128;  // + alignment slack
     if (smem > PK_SMEM_MAX) return cudaErrorNotSupported;
-    // descriptor addresses (14 bits of address / 16) cover the shared memory
     const uint32_t acc_cols = tc_acc_cols(1, 1, a.n_pad);
     static std::atomic<unsigned long long> attr{0};
     {
