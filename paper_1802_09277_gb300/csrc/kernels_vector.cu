@@ -623,6 +623,46 @@ cudaError_t launch_scale(const double *x, double *y, const double *a, int nrhs, 
     return cudaGetLastError();
 }
 
+struct ScaleArgsF {
+    float a[NRHS_MAX];
+};
+
+// y (FP32) = float(x) * s_r per rhs r: the refinement's scaled FP32 right-hand
+// side in one pass (the rounding of a conversion followed by an FP32 scaling)
+__global__ void k_convert_scale(const double *__restrict__ x, float *__restrict__ y,
+                                const __grid_constant__ ScaleArgsF sa, long long len, int vec2) {
+    const int r = blockIdx.y;
+    const long long off = (long long)r * len;
+    const float s = sa.a[r];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    if (vec2) {  // off is even because len is
+        const double2 *x2 = reinterpret_cast<const double2 *>(x + off);
+        float2 *y2 = reinterpret_cast<float2 *>(y + off);
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len / 2; i += stride) {
+            const double2 v = x2[i];
+            y2[i] = make_float2(__fmul_rn((float)v.x, s), __fmul_rn((float)v.y, s));
+        }
+        return;
+    }
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride)
+        y[off + i] = __fmul_rn((float)x[off + i], s);
+}
+
+cudaError_t launch_convert_scale(const double *x, float *y, const double *scale, int nrhs,
+                                 long long len, cudaStream_t s) {
+    if (nrhs > NRHS_MAX || nrhs < 1) return cudaErrorInvalidValue;
+    if (len <= 0) return cudaSuccess;
+    ScaleArgsF sa;
+    for (int r = 0; r < nrhs; ++r) sa.a[r] = (float)scale[r];
+    const int vec2 = (len % 2 == 0) && aligned16(x) && ((reinterpret_cast<uintptr_t>(y) & 7u) == 0);
+    long long bx = (len / 2 + 255) / 256;
+    const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
+    if (bx > cap) bx = cap;
+    if (bx < 1) bx = 1;
+    k_convert_scale<<<dim3((unsigned)bx, (unsigned)nrhs), 256, 0, s>>>(x, y, sa, len, vec2);
+    return cudaGetLastError();
+}
+
 // f[slab][t][z][y][x] = sum_k gt[k][slab][t] gz[k][z] gy[k][y] gx[k][x]
 __global__ void k_separable_sum(double *__restrict__ f, const double *__restrict__ g, int K,
                                 long long nslab_t, int nx, int ny, int nz, long long total) {

@@ -2667,9 +2667,7 @@ int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *
         for (int k = 0; k < M; ++k) {
             if (!run[k]) continue;
             st_handle h = g.hs[k];
-            if (first && u_zero[k]) {
-                CK(cudaMemcpyAsync(h->r64, rhs[k], sizeof(double) * h->len * h->nrhs,
-                                   cudaMemcpyDeviceToDevice, h->stream));
+            if (first && u_zero[k]) {  // the residual is f itself (read from f below)
                 for (int q = g.first[k]; q < g.first[k] + h->nrhs; ++q) nr[q] = nf[q];
             } else {
                 CKS(residual_df(h, u[k], rhs[k], h->r64));
@@ -2703,14 +2701,6 @@ int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *
             any = any || run[k];
         }
         if (!any) break;
-        for (int k = 0; k < M; ++k)
-            if (run[k]) CKS((vconvert<double, float>(g.hs[k], g.hs[k]->r64, g.hs[k]->rhs32)));
-        {
-            std::vector<int> nv0(M, 0);
-            auto B32w = [&](int k) { return g.hs[k]->rhs32; };
-            auto none = [&](int, int) { return (const float *)nullptr; };
-            CKS((grp_axpy<float>(g, run, 0, nv0, none, nullptr, B32w, sc.data())));
-        }
         std::vector<double> itol(M, 0.0);
         std::vector<int> maxit(M, 0);
         for (int k = 0; k < M; ++k) {
@@ -2718,13 +2708,25 @@ int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *
             st_handle h = g.hs[k];
             const long long n0 = h->len * h->nrhs;
             const long long planes = (long long)h->N * h->nrhs * h->nt;
+            // FP32 right-hand side r / ||r|| in one pass (from f itself on the
+            // first step from zero), straight into the buffer the forward
+            // transform starts from: it ends in rhs32 (odd axis counts start in
+            // w1, even ones in rhs32; no pass is in place)
+            const double *src = (first && u_zero[k]) ? rhs[k] : h->r64;
+            float *cv = (eig[k] && h->dim % 2 == 1) ? h->w32.w1 : h->rhs32;
+            {
+                KScope ks(h, ST_PROF_VECTOR, 12.0 * n0, 1.0 * n0);
+                CK(launch_convert_scale(src, cv, &sc[g.first[k]], h->nrhs, h->len, h->stream));
+            }
             // the two transforms around each inner solve run at full FP32
             // accuracy: their error bounds what one refinement step can gain
             if (eig[k]) {  // r^ = (I (x) U^T) r, into rhs32
                 float *rh = nullptr;
-                CKS(spatial<float>(h, h->rhs32, h->w32.w0, h->w32.w1, true, planes, &rh, true));
-                CK(cudaMemcpyAsync(h->rhs32, rh, sizeof(float) * n0, cudaMemcpyDeviceToDevice,
-                                   h->stream));
+                if (h->dim % 2 == 1)
+                    CKS(spatial<float>(h, h->w32.w1, h->rhs32, h->w32.w0, true, planes, &rh, true));
+                else
+                    CKS(spatial<float>(h, h->rhs32, h->w32.w0, h->rhs32, true, planes, &rh, true));
+                if (rh != h->rhs32) return fail(ST_ERR_CUDA, "forward transform landed elsewhere");
             }
             CK(launch_zero<float>(h->e32, n0, h->stream));
             itol[k] = std::max(h->opt.inner_tol, 1e-6);

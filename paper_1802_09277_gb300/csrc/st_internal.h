@@ -233,6 +233,10 @@ cudaError_t launch_mode_solve(T *w, const T *mu, const Grid &g, const SpecCoefs<
 // ---- vector kernels (kernels_vector.cu) ----
 template <typename Tin, typename Tout>
 cudaError_t launch_convert(const Tin *x, Tout *y, long long n, cudaStream_t s);
+// y = float(x) * float(scale[r]) over rhs r of len values each (one FP32 rounding
+// of the conversion, one of the product)
+cudaError_t launch_convert_scale(const double *x, float *y, const double *scale, int nrhs,
+                                 long long len, cudaStream_t s);
 
 // Krylov vector kernels over a group of members (handles) whose vectors hold
 // different numbers of right-hand sides of different lengths.  A launch
