@@ -31,6 +31,8 @@
 //                     u_n = A^{-1} (f_n + e_0 u_{n-1, last}) over its slabs
 //  k_lv_res_restrict  residual and restriction without smoothing (nu1 = 0)
 //  k_lv_op            the eigenbasis operator L^ (or f - L^ u) pointwise
+#include <type_traits>
+
 #include "pdl.cuh"
 #include "spec_common.cuh"
 
@@ -546,12 +548,14 @@ __global__ void __launch_bounds__(256)
 }
 
 // The coarse end of the V-cycle, levels l0 .. L (N_{l0} <= TAIL_SLABS slabs
-// per problem, nu1 = nu2 = 1, zero initial iterate on every level), in one
-// launch: one thread per (spatial mode, rhs) runs the sub-cycle sequentially
-// over its slabs with the level vectors in thread-local memory (an
-// interleaved, L1-resident per-thread array), the same steps as k_lv_down0 /
+// per problem, nu1, nu2 <= 8 smoothing steps, zero initial iterate on every
+// level), in one launch: one thread per (spatial mode, rhs) runs the
+// sub-cycle sequentially over its slabs, the same steps as k_lv_down0 /
 // k_lv_coarse / k_lv_up: the Jacobi steps see the previous slab's iterate
-// from before the step, which the sequential sweep keeps in a register.
+// from before the step, which the sequential sweep keeps in a register.  The
+// level vectors are thread-local arrays: in local memory for a run-time slab
+// count (L1-resident only while few threads run), in registers for the small
+// tails whose slab and level counts are compile-time constants.
 constexpr int TAIL_SLABS = 16;
 template <typename T>
 struct TailArgs {
@@ -560,46 +564,63 @@ struct TailArgs {
     int nu1, nu2;      // smoothing steps before / after the coarse correction
 };
 
-template <typename T, int NT>
+// N0C > 0: the top level's slab count N0C and the level count NLC fixed at
+// compile time, so that every loop unrolls and the level vectors live in
+// registers (a few slabs); N0C = 0: both at run time, the vectors in local
+// memory (up to TAIL_SLABS slabs).
+template <typename T, int NT, int N0C = 0, int NLC = 0>
 __global__ void __launch_bounds__(128)
     k_lv_tail(const T *__restrict__ fin, T *__restrict__ uout, const __grid_constant__ TailArgs<T> ta,
-              const __grid_constant__ ProlongCoefs<T> pc, long long S, int n0, T omega) {
+              const __grid_constant__ ProlongCoefs<T> pc, long long S, int n0_arg, T omega) {
     griddep_wait();
     griddep_launch();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const long long q = slab_index();  // right-hand side
     if (k >= S) return;
-    constexpr int CAP = 2 * TAIL_SLABS * NT;  // slabs of all tail levels, per vector
+    constexpr int NMAX = N0C > 0 ? N0C : TAIL_SLABS;
+    constexpr int CAP = 2 * NMAX * NT;  // slabs of all tail levels, per vector
+    const int n0 = N0C > 0 ? N0C : n0_arg;
+    const int nlev = NLC > 0 ? NLC : ta.nlev;
     T f[CAP], u[CAP];
     int off[16];
     {
         int o = 0;
-        for (int l = 0; l < ta.nlev; ++l) {
+#pragma unroll
+        for (int l = 0; l < (NLC > 0 ? NLC : 16); ++l) {
+            if (l >= nlev) break;
             off[l] = o;
             o += (n0 >> l) * NT;
         }
     }
     const long long gbase = q * n0 * NT * S + k;
-    for (int e = 0; e < n0 * NT; ++e) f[e] = fin[gbase + (long long)e * S];
+#pragma unroll
+    for (int e = 0; e < NMAX * NT; ++e)
+        if (e < n0 * NT) f[e] = fin[gbase + (long long)e * S];
     // down: nu1 smoothing steps from zero, the residual, restriction.  The
     // first step from zero is u = w A^-1 f with residual (1 - w) f + e_0 p'
     // (p' the new last entry of the slab before); each further Jacobi step
     // u' = u + w A^-1 r carries the residual forward without A:
     // r' = (1 - w) r + e_0 (p' - p), p / p' that entry before / after the step.
-    for (int l = 0; l + 1 < ta.nlev; ++l) {
+#pragma unroll
+    for (int l = 0; l + 1 < (NLC > 0 ? NLC : 16); ++l) {
+        if (l + 1 >= nlev) break;
         const int N = n0 >> l;
         T m[NT * NT];
         load_inv<T, NT>(ta.inv[l], S, k, m);
         T *fl = f + off[l], *ul = u + off[l], *fc = f + off[l + 1];
-        T r[TAIL_SLABS * NT];
+        T r[NMAX * NT];
         if (ta.nu1 == 0) {
-            for (int e = 0; e < N * NT; ++e) {
+            #pragma unroll
+            for (int e = 0; e < (N0C > 0 ? NMAX * NT : N * NT); ++e) {
+                if (e >= N * NT) break;
                 ul[e] = T(0);
                 r[e] = fl[e];
             }
         } else {
             T prev = T(0);  // new last entry of the slab before
-            for (int n = 0; n < N; ++n) {
+            #pragma unroll
+            for (int n = 0; n < (N0C > 0 ? NMAX : N); ++n) {
+                if (n >= N) break;
                 T fa[NT], ua[NT];
 #pragma unroll
                 for (int i = 0; i < NT; ++i) fa[i] = fl[n * NT + i];
@@ -616,7 +637,9 @@ __global__ void __launch_bounds__(128)
         }
         for (int st = 1; st < ta.nu1; ++st) {
             T old_prev = T(0), new_prev = T(0);
-            for (int n = 0; n < N; ++n) {
+            #pragma unroll
+            for (int n = 0; n < (N0C > 0 ? NMAX : N); ++n) {
+                if (n >= N) break;
                 T ra[NT], d[NT];
 #pragma unroll
                 for (int i = 0; i < NT; ++i) ra[i] = r[n * NT + i];
@@ -632,7 +655,9 @@ __global__ void __launch_bounds__(128)
                 new_prev = ul[n * NT + NT - 1];
             }
         }
-        for (int mc = 0; mc < N / 2; ++mc) {
+        #pragma unroll
+        for (int mc = 0; mc < (N0C > 0 ? NMAX / 2 : N / 2); ++mc) {
+            if (mc >= N / 2) break;
             T ra[NT], rb[NT], out[NT];
 #pragma unroll
             for (int i = 0; i < NT; ++i) {
@@ -645,11 +670,13 @@ __global__ void __launch_bounds__(128)
         }
     }
     {  // coarsest level: forward substitution
-        const int l = ta.nlev - 1, N = n0 >> l;
+        const int l = nlev - 1, N = n0 >> l;
         T m[NT * NT];
         load_inv<T, NT>(ta.inv[l], S, k, m);
         T prev = T(0);
-        for (int n = 0; n < N; ++n) {
+        #pragma unroll
+            for (int n = 0; n < (N0C > 0 ? NMAX : N); ++n) {
+                if (n >= N) break;
             T r[NT], v[NT];
 #pragma unroll
             for (int i = 0; i < NT; ++i) r[i] = f[off[l] + n * NT + i];
@@ -663,14 +690,18 @@ __global__ void __launch_bounds__(128)
     // up: prolongation of the coarse correction, then nu2 Jacobi steps
     // u' = (1 - w) u + w A^-1 (f + e_0 p), p the previous slab's last entry
     // before the step (the first step fused with the prolongation)
-    for (int l = ta.nlev - 2; l >= 0; --l) {
+    #pragma unroll
+    for (int l = (NLC > 0 ? NLC : 16) - 2; l >= 0; --l) {
+        if (l > nlev - 2) continue;
         const int N = n0 >> l;
         T m[NT * NT];
         load_inv<T, NT>(ta.inv[l], S, k, m);
         const T *fl = f + off[l], *uc = u + off[l + 1];
         T *ul = u + off[l];
         T prev = T(0);  // corrected (not yet smoothed) last entry of the slab before
-        for (int mc = 0; mc < N / 2; ++mc) {
+        #pragma unroll
+        for (int mc = 0; mc < (N0C > 0 ? NMAX / 2 : N / 2); ++mc) {
+            if (mc >= N / 2) break;
             T e[NT], ua[NT], ub[NT], r[NT], v[NT];
 #pragma unroll
             for (int i = 0; i < NT; ++i) e[i] = uc[mc * NT + i];
@@ -711,7 +742,9 @@ __global__ void __launch_bounds__(128)
         }
         for (int st = 1; st < ta.nu2; ++st) {
             T old_prev = T(0);
-            for (int n = 0; n < N; ++n) {
+            #pragma unroll
+            for (int n = 0; n < (N0C > 0 ? NMAX : N); ++n) {
+                if (n >= N) break;
                 T r[NT], v[NT];
 #pragma unroll
                 for (int i = 0; i < NT; ++i) r[i] = fl[n * NT + i];
@@ -724,7 +757,9 @@ __global__ void __launch_bounds__(128)
             }
         }
     }
-    for (int e = 0; e < n0 * NT; ++e) uout[gbase + (long long)e * S] = u[e];
+#pragma unroll
+    for (int e = 0; e < NMAX * NT; ++e)
+        if (e < n0 * NT) uout[gbase + (long long)e * S] = u[e];
 }
 
 // ---- launchers: dispatch on N_t ----
@@ -847,6 +882,17 @@ cudaError_t launch_spec_tail(const T *fin, T *uout, const T *const *inv, int nle
         L.grid.x = (unsigned)((g.nxyz + 127) / 128);
     }
     cudaError_t e = cudaSuccess;
+    // the complete power-of-two tails of at most 4 slabs in registers (FP32)
+    if (std::is_same<T, float>::value && n0 == 4 && nlev == 3) {
+        ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_tail<T, NT, 4, 3>, L.grid, L.block, 0, s, fin,
+                                              uout, ta, pc, g.nxyz, n0, omega)));
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
+    if (std::is_same<T, float>::value && n0 == 2 && nlev == 2) {
+        ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_tail<T, NT, 2, 2>, L.grid, L.block, 0, s, fin,
+                                              uout, ta, pc, g.nxyz, n0, omega)));
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     ST_NT_DISPATCH(pc.nt, (e = launch_pdl(k_lv_tail<T, NT>, L.grid, L.block, 0, s, fin, uout, ta,
                                           pc, g.nxyz, n0, omega)));
     return e != cudaSuccess ? e : cudaGetLastError();

@@ -1368,8 +1368,16 @@ int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
     const int nt = h->nt;
     CKS(ensure_inv<T>(h));
     const T *inv = inv_tabs<T>(h)[l];
-    // the coarse end of the cycle (at most 16 slabs per problem) in one launch
-    if (zero_init && spp <= 16 && l < h->nlev - 1) {
+    // the coarse end of the cycle in one launch: up to 16 slabs per problem
+    // (its level vectors in local memory) for a problem with few modes or
+    // when no sweeping kernel applies; otherwise the sweeps go on down to 4
+    // slabs and the tail's vectors fit in registers (with many modes the
+    // local-memory tail spills out of L1: 2.3 ms per cycle for 48^3 x 16
+    // right-hand sides at 16 slabs)
+    const bool sweeps = h->opt.nu1 >= 2 && h->opt.nu1 <= 6 && h->opt.nu2 >= 2 && h->opt.nu2 <= 6;
+    const bool many = (long long)h->g.nxyz * h->nrhs > 152LL * 256;
+    const int tail_max = (sweeps && many) ? 4 : 16;
+    if (zero_init && spp <= tail_max && l < h->nlev - 1) {
         const double nu = h->opt.nu1 + h->opt.nu2;
         KScope ks(h, ST_PROF_SPEC, sizeof(T) * 2.0 * E, E * nu * (6.0 * nt + 6.0));
         const cudaError_t e = launch_spec_tail<T>(f, u, inv_tabs<T>(h).data() + l, h->nlev - l, h->g,

@@ -513,3 +513,34 @@ def test_refinement_residual_3d_z_chunks(st, spans, p):
     err = np.linalg.norm(host(u) - ud) / np.linalg.norm(ud)
     assert info["rel_residual"] <= 1e-10 and err <= 1e-8, (err, info)
     s.close()
+
+
+def test_refinement_many_modes_register_tail(st):
+    """With many (mode, right-hand side) pairs and V(4,4) the eigenbasis
+    V-cycle sweeps down to 4 slabs and ends in the register-resident tail
+    (a 16-slab tail would spill its vectors out of L1): 16 right-hand sides
+    of a 64 x 64, p = 2 problem on 16 slabs reach the oracle's solution to
+    1e-8, and match the solves of one right-hand side each (which end in
+    the 16-slab tail) to the same tolerance."""
+    d, spans, p, N, ne, R = 2, (64, 64), 2, 16, 2, 16
+    pr = A.Problem(d, spans, p, ne, N, theta=1.0)
+    cs = [inputs.normal_coeffs(90 + r, pr.ndofs) for r in range(R)]
+    F = [A.load_from_coeffs(pr, c) for c in cs]
+    s = st.Solver(d, p, spans, N, ne_per_slab=ne, nrhs=R, precision="mixed_tf32",
+                  basis="spectral", outer="ir", nu1=4, nu2=4)
+    u = torch.zeros(R * pr.ndofs, dtype=torch.float64, device="cuda")
+    info = s.solve(dev(np.concatenate(F)), u, tol=1e-10)
+    assert info["rel_residual"] <= 1e-10
+    got = host(u).reshape(R, pr.ndofs)
+    for r in (0, R - 1):
+        ud = exact(pr, F[r])
+        assert np.linalg.norm(got[r] - ud) <= 1e-8 * np.linalg.norm(ud), r
+    s.close()
+    one = st.Solver(d, p, spans, N, ne_per_slab=ne, nrhs=1, precision="mixed_tf32",
+                    basis="spectral", outer="ir", nu1=4, nu2=4)
+    for r in range(R):
+        u1 = torch.zeros(pr.ndofs, dtype=torch.float64, device="cuda")
+        one.solve(dev(F[r]), u1, tol=1e-10)
+        v = host(u1)
+        assert np.linalg.norm(got[r] - v) <= 1e-8 * np.linalg.norm(v), r
+    one.close()
