@@ -115,7 +115,7 @@ struct TileShape<3, false> {
 };
 template <>
 struct TileShape<3, true> {
-    static constexpr int TX = 8, TY = 16, TZ = 8, ZS = 2;
+    static constexpr int TX = 8, TY = 8, TZ = 16, ZS = 4;
 };
 
 template <typename T, int P, int DIM>  // T: compute type
