@@ -755,7 +755,7 @@ def make_len(d, spans, p, N, ne):
 # with the dofs).
 TRAFFIC = {
     ("cube48_x16", "mixed_tf32", "spectral", "ir", "stencil_df"):
-        (16 * (906198016 + 426818816), "profiles/traffic_cube48_stencil_dfloat_and_sweep.md"),
+        (16 * (906206720 + 429370112), "profiles/traffic_cube48_stencil_dfloat_and_sweep.md"),
 }
 
 
