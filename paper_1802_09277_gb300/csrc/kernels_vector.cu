@@ -187,58 +187,115 @@ struct Red<float> {
     static __device__ __forceinline__ double out(V v) { return (double)v; }
 };
 
-// grid (nblk, nsys, ceil(nv / 4)), 256 threads; member k's partial sums at
+// One thread's share of the dots of CNT vectors with the target w (SELF: of
+// each vector with itself, w unused), elements in grid-stride order.  The
+// count is a compile-time constant and the loop takes two strides at a time,
+// so every load of both is issued before the products that use them: with
+// the count a run-time value (predicated loads) the loads of the next stride
+// waited for the arithmetic of this one, and the FP64 dots ran at a sixth of
+// HBM bandwidth.  Each accumulator sees its elements in the order of the
+// plain grid-stride loop.
+template <typename T, int CNT, bool SELF>
+__device__ __forceinline__ void gdot_body(const T *const *x, const T *__restrict__ w,
+                                          long long len, int vec2, DotAcc<T> *acc) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (vec2) {
+        using P2 = typename Pair<T>::V;
+        const long long np = len / 2;
+        const P2 *w2 = reinterpret_cast<const P2 *>(w);
+        long long i = i0;
+        for (; i + stride < np; i += 2 * stride) {
+            P2 a[2][CNT], b[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (!SELF) b[u] = w2[i + u * stride];
+#pragma unroll
+                for (int k = 0; k < CNT; ++k)
+                    a[u][k] = reinterpret_cast<const P2 *>(x[k])[i + u * stride];
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int k = 0; k < CNT; ++k) {
+                    const P2 c = SELF ? a[u][k] : b[u];
+                    acc[k].add(a[u][k].x, c.x);
+                    acc[k].add(a[u][k].y, c.y);
+                }
+        }
+        if (i < np) {
+            P2 a[CNT], b;
+            if (!SELF) b = w2[i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) a[k] = reinterpret_cast<const P2 *>(x[k])[i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) {
+                const P2 c = SELF ? a[k] : b;
+                acc[k].add(a[k].x, c.x);
+                acc[k].add(a[k].y, c.y);
+            }
+        }
+    } else {
+        long long i = i0;
+        for (; i + stride < len; i += 2 * stride) {
+            T a[2][CNT], b[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                if (!SELF) b[u] = w[i + u * stride];
+#pragma unroll
+                for (int k = 0; k < CNT; ++k) a[u][k] = x[k][i + u * stride];
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int k = 0; k < CNT; ++k) acc[k].add(a[u][k], SELF ? a[u][k] : b[u]);
+        }
+        if (i < len) {
+            T a[CNT], b = T(0);
+            if (!SELF) b = w[i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) a[k] = x[k][i];
+#pragma unroll
+            for (int k = 0; k < CNT; ++k) acc[k].add(a[k], SELF ? a[k] : b);
+        }
+    }
+}
+
+// grid (nblk, nsys, ceil(nv / GV)), 256 threads; member k's partial sums at
 // part[k][(v * R[k] + r) * nblk + blk].  Block (b, s, g) accumulates the dots
-// of system s's target with vectors 4g .. 4g+3 over a grid-stride loop, two
-// elements per load when the member allows it.  The target is re-read by
-// every group from L2.
-template <typename T>
+// of vectors GV g .. GV g + GV - 1 of system s with its target (SELF: with
+// themselves) over a grid-stride loop, two elements per load when the member
+// allows it.  The target is re-read by every group from L2.
+template <typename T, int GV, bool SELF>
 __global__ void __launch_bounds__(256)
     k_gdot_partial(int nv, const __grid_constant__ GVecD<T> vl, const __grid_constant__ GTgtD<T> tw,
                    const __grid_constant__ GMemD gm, const __grid_constant__ GSysD gs) {
     griddep_wait();
     griddep_launch();
-    using P2 = typename Pair<T>::V;
-    __shared__ typename Red<T>::V red[8][4];
+    __shared__ typename Red<T>::V red[8][GV];
     const int s = blockIdx.y, nblk = gridDim.x;
     const int mk = gs.m[s], r = gs.r[s];
     const long long len = gm.len[mk];
     const long long off = (long long)r * len;
     const int vec2 = gm.vec[mk];
-    const T *w = tw.p[mk];
-    const int v0 = 4 * blockIdx.z;
-    const int cnt = (nv - v0 < 4) ? nv - v0 : 4;
-    const T *x[4];
+    const T *w = SELF ? nullptr : tw.p[mk] + off;
+    const int v0 = GV * blockIdx.z;
+    const int cnt = (nv - v0 < GV) ? nv - v0 : GV;
+    const T *x[GV];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0][mk] + off;
-    DotAcc<T> acc[4];
-    const long long stride = (long long)nblk * blockDim.x;
-    if (vec2) {
-        const P2 *w2 = reinterpret_cast<const P2 *>(w + off);
-        const long long np = len / 2;
-#pragma unroll 2
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
-            const P2 wi = w2[i];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k < cnt) {
-                    const P2 a = reinterpret_cast<const P2 *>(x[k])[i];
-                    acc[k].add(a.x, wi.x);
-                    acc[k].add(a.y, wi.y);
-                }
-        }
-    } else {
-        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
-            const T wi = w[off + i];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (k < cnt) acc[k].add(x[k][i], wi);
-        }
+    for (int k = 0; k < GV; ++k) x[k] = vl.v[(k < cnt) ? v0 + k : v0][mk] + off;
+    DotAcc<T> acc[GV];
+    static_assert(GV == 2 || GV == 4, "the count dispatch below covers GV = 2 and 4");
+    switch (cnt) {  // uniform across the grid row
+        case 1: gdot_body<T, 1, SELF>(x, w, len, vec2, acc); break;
+        case 2: gdot_body<T, 2, SELF>(x, w, len, vec2, acc); break;
+        case 3: gdot_body<T, (GV > 2 ? 3 : 2), SELF>(x, w, len, vec2, acc); break;
+        default: gdot_body<T, GV, SELF>(x, w, len, vec2, acc); break;
     }
     using RD = Red<T>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < GV; ++k) {
         if (k >= cnt) break;
         const typename RD::V t = RD::warp(RD::of(acc[k]));
         if (lane == 0) red[warp][k] = t;
@@ -276,16 +333,17 @@ static bool al2(const void *p) {
     return sizeof(T) == 8 ? aligned16(p) : ((reinterpret_cast<uintptr_t>(p) & 7u) == 0);
 }
 
+// shared by launch_gdot and launch_gnorm2 (self = 1: w unused)
 template <typename T>
-cudaError_t launch_gdot(const GLaunch &g, int nv, const T *const *xs, const T *const *w,
-                        double *out, cudaStream_t s) {
+static cudaError_t gdot_run(const GLaunch &g, int nv, const T *const *xs, const T *const *w,
+                            bool self, double *out, cudaStream_t s) {
     if (!group_ok(g, nv) || nv < 1) return cudaErrorInvalidValue;
     GVecD<T> vl{};
     GTgtD<T> tw{};
     GMemD gm = mem_of(g);
     for (int k = 0; k < g.nmem; ++k) {
-        tw.p[k] = const_cast<T *>(w[k]);
-        int vec2 = (g.len[k] % 2 == 0) && al2<T>(w[k]);
+        tw.p[k] = self ? nullptr : const_cast<T *>(w[k]);
+        int vec2 = (g.len[k] % 2 == 0) && (self || al2<T>(w[k]));
         for (int v = 0; v < nv; ++v) {
             vl.v[v][k] = xs[(size_t)v * g.nmem + k];
             vec2 = vec2 && al2<T>(vl.v[v][k]);
@@ -293,13 +351,32 @@ cudaError_t launch_gdot(const GLaunch &g, int nv, const T *const *xs, const T *c
         gm.vec[k] = vec2;
     }
     const GSysD gs = sys_of(g);
-    cudaError_t e = launch_pdl(k_gdot_partial<T>, dim3(g.nblk, g.nsys, (nv + 3) / 4), dim3(256),
-                               0, s, nv, vl, tw, gm, gs);
+    cudaError_t e;
+    if (self)  // norms come one or two at a time: the two-vector kernel keeps its registers low
+        e = launch_pdl(k_gdot_partial<T, 2, true>, dim3(g.nblk, g.nsys, (nv + 1) / 2), dim3(256),
+                       0, s, nv, vl, tw, gm, gs);
+    else
+        e = launch_pdl(k_gdot_partial<T, 4, false>, dim3(g.nblk, g.nsys, (nv + 3) / 4), dim3(256),
+                       0, s, nv, vl, tw, gm, gs);
     if (e != cudaSuccess) return e;
     const int count = nv * g.nsys;
     e = launch_pdl(k_greduce, dim3((count + 3) / 4), dim3(128), 0, s, gm, gs, g.nsys, count,
                    g.nblk, out);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gdot(const GLaunch &g, int nv, const T *const *xs, const T *const *w,
+                        double *out, cudaStream_t s) {
+    bool self = nv == 1;  // a vector with itself: one load per element
+    for (int k = 0; self && k < g.nmem; ++k) self = xs[k] == w[k];
+    return gdot_run<T>(g, nv, xs, w, self, out, s);
+}
+
+template <typename T>
+cudaError_t launch_gnorm2(const GLaunch &g, int nv, const T *const *xs, double *out,
+                          cudaStream_t s) {
+    return gdot_run<T>(g, nv, xs, nullptr, true, out, s);
 }
 
 // grid (blocks, nsys): block row s updates system s (its member's vector at
@@ -308,7 +385,7 @@ template <typename T>
 __global__ void __launch_bounds__(256)
     k_gaxpy(const __grid_constant__ GVecD<T> vl, const __grid_constant__ GTgtD<T> ty,
             const __grid_constant__ GAxpyD<T> aa, const __grid_constant__ GMemD gm,
-            const __grid_constant__ GSysD gs) {
+            const __grid_constant__ GSysD gs, int yz) {
     griddep_wait();
     griddep_launch();
     using P2 = typename Pair<T>::V;
@@ -323,7 +400,13 @@ __global__ void __launch_bounds__(256)
         const long long n = len / 2;
         P2 *y2 = reinterpret_cast<P2 *>(y + off);
         for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-            P2 acc = y2[i];
+            P2 acc;
+            if (yz) {  // -0 + p = p for every p, signed zeros included
+                acc.x = -T(0);
+                acc.y = -T(0);
+            } else {
+                acc = y2[i];
+            }
             for (int v = 0; v < nv; ++v) {
                 const T c = aa.coef[v * NSYS_MAX + s];
                 const P2 x = reinterpret_cast<const P2 *>(vl.v[v][mk] + off)[i];
@@ -337,7 +420,7 @@ __global__ void __launch_bounds__(256)
         return;
     }
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
-        T acc = y[off + i];
+        T acc = yz ? -T(0) : y[off + i];
         for (int v = 0; v < nv; ++v) acc += aa.coef[v * NSYS_MAX + s] * vl.v[v][mk][off + i];
         y[off + i] = post * acc;
     }
@@ -548,7 +631,7 @@ cudaError_t launch_gaxpy2(const GLaunch &g, int nv, const T *const *xs, const do
 
 template <typename T>
 cudaError_t launch_gaxpy(const GLaunch &g, int nv, const T *const *xs, const double *coef,
-                         T *const *y, const double *post, cudaStream_t s) {
+                         T *const *y, const double *post, cudaStream_t s, bool y_zero) {
     if (!group_ok(g, nv)) return cudaErrorInvalidValue;
     for (int i = 0; i < g.nsys; ++i)
         if (g.snv[i] < 0 || g.snv[i] > nv) return cudaErrorInvalidValue;
@@ -574,7 +657,7 @@ cudaError_t launch_gaxpy(const GLaunch &g, int nv, const T *const *xs, const dou
         aa.post[i] = post ? (T)post[i] : T(1);
     }
     const cudaError_t e = launch_pdl(k_gaxpy<T>, dim3(axpy_blocks(g, 512), g.nsys), dim3(256), 0,
-                                     s, vl, ty, aa, gm, sys_of(g));
+                                     s, vl, ty, aa, gm, sys_of(g), y_zero ? 1 : 0);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -583,23 +666,27 @@ struct ScaleArgs {
 };
 
 // y (FP64) += a_r * x (FP32), per rhs r: the refinement update
+// y_r += a_r x_r (store: y_r = 0 + a_r x_r, y not read), one grid row per
+// right-hand side r
 __global__ void k_axpy_f32_f64(const float *__restrict__ x, double *__restrict__ y,
-                               const __grid_constant__ ScaleArgs sa, long long len, int nrhs) {
-    const long long n = (long long)nrhs * len;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+                               const __grid_constant__ ScaleArgs sa, long long len, int store) {
+    const long long off = (long long)blockIdx.y * len;
+    const double a = sa.a[blockIdx.y];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
          i += (long long)gridDim.x * blockDim.x)
-        y[i] += sa.a[i / len] * (double)x[i];
+        y[off + i] = (store ? 0.0 : y[off + i]) + a * (double)x[off + i];
 }
 
 cudaError_t launch_axpy_f32_f64(const float *x, double *y, const double *a, int nrhs,
-                                long long len, cudaStream_t s) {
+                                long long len, cudaStream_t s, bool store) {
     if (nrhs > NRHS_MAX) return cudaErrorInvalidValue;
+    if (nrhs <= 0 || len <= 0) return cudaSuccess;
     ScaleArgs sa;
     for (int r = 0; r < nrhs; ++r) sa.a[r] = a[r];
-    long long blocks = ((long long)nrhs * len + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    if (blocks <= 0) return cudaSuccess;
-    k_axpy_f32_f64<<<(unsigned)blocks, 256, 0, s>>>(x, y, sa, len, nrhs);
+    long long bx = (len + 255) / 256;
+    const long long cap = (152LL * 16 + nrhs - 1) / nrhs;
+    if (bx > cap) bx = cap;
+    k_axpy_f32_f64<<<dim3((unsigned)bx, (unsigned)nrhs), 256, 0, s>>>(x, y, sa, len, store ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -697,11 +784,13 @@ template cudaError_t launch_zero<float>(float *, long long, cudaStream_t);
 #define ST_GVEC(T)                                                                             \
     template cudaError_t launch_gdot<T>(const GLaunch &, int, const T *const *, const T *const *, \
                                         double *, cudaStream_t);                                  \
+    template cudaError_t launch_gnorm2<T>(const GLaunch &, int, const T *const *, double *,       \
+                                          cudaStream_t);                                          \
     template cudaError_t launch_ggram2<T>(const GLaunch &, int, const T *const *,                \
                                           const T *const *, const T *const *, double *,           \
                                           cudaStream_t);                                          \
     template cudaError_t launch_gaxpy<T>(const GLaunch &, int, const T *const *, const double *,  \
-                                         T *const *, const double *, cudaStream_t);               \
+                                         T *const *, const double *, cudaStream_t, bool);         \
     template cudaError_t launch_gaxpy2<T>(const GLaunch &, int, const T *const *, const double *, \
                                           const double *, const double *, const double *,         \
                                           const double *, T *const *, T *const *, const int *,    \

@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/st_iga.h"
 #include "host_setup.h"
 #include "st_internal.h"
@@ -291,6 +293,26 @@ void prof_fold(st_handle h) {
     }
     h->recs.clear();
     h->ev_next = 0;
+}
+
+// A named host range for timeline profilers (NVTX): one per API call,
+// refinement step, Krylov cycle, preconditioner application and V-cycle
+// level.  A replayed CUDA graph shows as its preconditioner range (the level
+// ranges appear where the cycle is launched directly).  Without an attached
+// tool a range costs two calls through no-op function pointers.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+const char *level_range_name(int l) {
+    static const char *const names[] = {
+        "V-cycle level 0",  "V-cycle level 1",  "V-cycle level 2",  "V-cycle level 3",
+        "V-cycle level 4",  "V-cycle level 5",  "V-cycle level 6",  "V-cycle level 7",
+        "V-cycle level 8",  "V-cycle level 9",  "V-cycle level 10", "V-cycle level 11",
+        "V-cycle level 12", "V-cycle level 13", "V-cycle level 14", "V-cycle level >= 15"};
+    return names[l < 0 ? 0 : (l > 15 ? 15 : l)];
 }
 
 // Records [start, stop) events around one launch when profiling is on.
@@ -1360,6 +1382,7 @@ int ensure_inv(st_handle h) {
 // the transforms (I (x) U^T) on the residual and (I (x) U) on the result.
 template <typename T>
 int svcycle(st_handle h, int l, T *u, const T *f, T *tmp, bool zero_init) {
+    NvtxRange range(level_range_name(l));
     const int spp = h->lv[l].nslab;
     const long long ns = (long long)spp * h->nrhs;
     const double E = (double)ns * h->nt * h->g.nxyz;
@@ -1580,6 +1603,7 @@ int ensure_krylov(st_handle h) {
 // a private stream, later uses launch it.  Eager while profiling is on.
 template <typename Fn>
 int run_graphed(st_handle h, const void *in, void *out, Fn fn) {
+    NvtxRange range("preconditioner");
     if (h->prof_on || !h->opt.use_graphs) return fn();
     st_handle_s::GraphRec *g = nullptr;
     for (auto &r : h->graphs)
@@ -1776,6 +1800,7 @@ int residual64(st_handle h, const double *u, const double *f, double *r) {
 // double-float arithmetic (about 48 significant bits, far below the FP32
 // inner solve's error) instead of FP64, which runs at 1/64 of the FP32 rate.
 int residual_df(st_handle h, const double *u, const double *f, double *r) {
+    NvtxRange range("FP64 residual");
     TimeCoefs<dfloat> tc = pack_time<dfloat>(h, 0, MODE_RES, false);
     CKS(exchange_halo<double>(h, 0, u, &tc.halo));
     const double E = (double)h->N * h->nrhs * h->nt * h->g.nxyz;
@@ -2115,12 +2140,15 @@ std::vector<const T *> grp_vecs(const Grp &g, const std::vector<char> &mask, int
 }
 
 // out[v * S + s] (group systems; zero for members outside mask) = dot of
-// vector v with the target over system s, or with rows = 2 the Gram pairs
+// vector v with the target over system s (rows = 1), of vector v with itself
+// (rows = 0: the targets are unused), or with rows = 2 the Gram pairs
 // out[(2 v + t) * S + s] with targets t1, t2
 template <typename T, class Vec, class Tgt1, class Tgt2>
-int grp_reduce(Grp &g, const std::vector<char> &mask, int nv, Vec vec, Tgt1 t1, Tgt2 t2, int rows,
-               std::vector<double> &out) {
+int grp_reduce(Grp &g, const std::vector<char> &mask, int nv, Vec vec, Tgt1 t1, Tgt2 t2,
+               int rows_in, std::vector<double> &out) {
     st_handle h0 = g.hs[0];
+    const bool self = rows_in == 0;
+    const int rows = self ? 1 : rows_in;  // output rows per vector
     std::vector<int> sys;
     const GLaunch L = grp_launch(g, mask, sys);
     out.assign((size_t)rows * nv * g.S, 0.0);
@@ -2129,7 +2157,7 @@ int grp_reduce(Grp &g, const std::vector<char> &mask, int nv, Vec vec, Tgt1 t1, 
     CKS(host_dots(h0, (size_t)rows * nv * L.nsys));
     std::vector<const T *> a, b;
     for (size_t k = 0; k < g.hs.size(); ++k)
-        if (mask[k]) {
+        if (mask[k] && !self) {
             a.push_back(t1((int)k));
             b.push_back(t2((int)k));
         }
@@ -2140,8 +2168,11 @@ int grp_reduce(Grp &g, const std::vector<char> &mask, int nv, Vec vec, Tgt1 t1, 
         const int cnt = std::min(MAXV, nv - v0);
         const std::vector<const T *> xs = grp_vecs<T>(g, mask, v0, cnt, vec);
         {
-            KScope ks(h0, ST_PROF_DOT, sizeof(T) * (cnt + rows) * bytes, 2.0 * rows * cnt * bytes);
-            if (rows == 1)
+            KScope ks(h0, ST_PROF_DOT, sizeof(T) * (cnt + (self ? 0 : rows)) * bytes,
+                      2.0 * rows * cnt * bytes);
+            if (self)
+                CK(launch_gnorm2<T>(L, cnt, xs.data(), h0->dots, g.G));
+            else if (rows == 1)
                 CK(launch_gdot<T>(L, cnt, xs.data(), a.data(), h0->dots, g.G));
             else
                 CK(launch_ggram2<T>(L, cnt, xs.data(), a.data(), b.data(), h0->dots, g.G));
@@ -2168,17 +2199,18 @@ template <typename T, class Vec>
 int grp_norms(Grp &g, const std::vector<char> &mask, Vec vec, std::vector<double> &nr) {
     std::vector<double> d;
     auto tgt = [&](int k) { return vec(0, k); };
-    CKS((grp_reduce<T>(g, mask, 1, vec, tgt, tgt, 1, d)));
+    CKS((grp_reduce<T>(g, mask, 1, vec, tgt, tgt, 0, d)));
     nr.assign(g.S, 0.0);
     for (int q = 0; q < g.S; ++q) nr[q] = std::isnan(d[q]) ? d[q] : std::sqrt(std::max(0.0, d[q]));
     return ST_OK;
 }
 
 // y_s <- post_s (y_s + sum_{v < nvm[k]} coef[v * S + s] x_v) for the members
-// in mask (nvm: vectors per member, <= nv; post may be NULL)
+// in mask (nvm: vectors per member, <= nv; post may be NULL; y_zero: y_s is
+// taken as zero and not read, nv <= MAXV)
 template <typename T, class Vec, class Tgt>
 int grp_axpy(Grp &g, const std::vector<char> &mask, int nv, const std::vector<int> &nvm, Vec vec,
-             const double *coef, Tgt y, const double *post) {
+             const double *coef, Tgt y, const double *post, bool y_zero = false) {
     st_handle h0 = g.hs[0];
     std::vector<int> sys;
     GLaunch L = grp_launch(g, mask, sys);
@@ -2210,7 +2242,7 @@ int grp_axpy(Grp &g, const std::vector<char> &mask, int nv, const std::vector<in
         {
             KScope ks(h0, ST_PROF_VECTOR, sizeof(T) * (cnt + 2.0) * bytes, 2.0 * cnt * bytes);
             CK(launch_gaxpy<T>(L, cnt, xs.data(), c.data(), ys.data(),
-                               (last && post) ? p.data() : nullptr, g.G));
+                               (last && post) ? p.data() : nullptr, g.G, y_zero && v0 == 0));
         }
         ++h0->n_vl;
         v0 += cnt;
@@ -2286,8 +2318,8 @@ int grp_axpy2(Grp &g, const std::vector<char> &mask, int nv, Vec vec, const std:
 // right-hand side and every loop bound per member, so each system gets its
 // single-handle (and single-rhs) result; a member that is done waits for the
 // others without further work.  b(k), x(k): member k's right-hand side and
-// iterate; V(j, k), Z(j, k): its basis; tol, maxit, its, worst per member;
-// skip per group system.
+// iterate, x zero on entry; V(j, k), Z(j, k): its basis; tol, maxit, its,
+// worst per member; skip per group system.
 template <typename T, class VB, class VX, class VV, class VZ, class Apply, class Res, class Prec>
 int fgmres_group(Grp &g, const std::vector<char> &mem, VB b, VX x, VV V, VZ Zk, int m,
                  const std::vector<double> &tolm, const std::vector<int> &maxit, Apply apply,
@@ -2311,10 +2343,18 @@ int fgmres_group(Grp &g, const std::vector<char> &mem, VB b, VX x, VV V, VZ Zk, 
     std::vector<int> total(M, 0);
     worst.assign(M, 0.0);
     std::vector<char> live = mem, done(S, 0);
-    while (true) {
-        for (int k = 0; k < M; ++k)
-            if (live[k]) CKS(resid(k, x(k), b(k), V(0, k)));
-        CKS(grp_norms<T>(g, live, V0, beta));
+    // x is zero on entry: the first cycle's residual is b itself (b - L 0
+    // has b's bits), so its norm is ||b|| and V_0 = b / ||b|| is formed from
+    // b without the operator pass and the second norm
+    for (bool first = true;; first = false) {
+        NvtxRange range("FGMRES cycle");
+        if (first) {
+            beta = nb;
+        } else {
+            for (int k = 0; k < M; ++k)
+                if (live[k]) CKS(resid(k, x(k), b(k), V(0, k)));
+            CKS(grp_norms<T>(g, live, V0, beta));
+        }
         for (int k = 0; k < M; ++k) {
             if (!live[k]) continue;
             double wk = 0.0;
@@ -2334,9 +2374,14 @@ int fgmres_group(Grp &g, const std::vector<char> &mem, VB b, VX x, VV V, VZ Zk, 
             std::vector<double> sc(S, 0.0);
             for (int q = 0; q < S; ++q)
                 if (live[mq[q]]) sc[q] = (!done[q] && beta[q] > 0) ? 1.0 / beta[q] : 0.0;
-            std::vector<int> nv0(M, 0);
             auto Vw = [&](int k) { return V(0, k); };
-            CKS((grp_axpy<T>(g, live, 0, nv0, V0, nullptr, Vw, sc.data())));
+            if (first) {  // V_0 = sc b, V_0 not read
+                std::vector<int> nv1(M, 1);
+                CKS((grp_axpy<T>(g, live, 1, nv1, Bv, sc.data(), Vw, nullptr, true)));
+            } else {
+                std::vector<int> nv0(M, 0);
+                CKS((grp_axpy<T>(g, live, 0, nv0, V0, nullptr, Vw, sc.data())));
+            }
         }
         std::vector<double> H((size_t)S * ld * m, 0.0), cs((size_t)S * m), sn((size_t)S * m),
             gv((size_t)S * ld, 0.0), nu(S, 0.0);
@@ -2407,6 +2452,8 @@ int fgmres_group(Grp &g, const std::vector<char> &mem, VB b, VX x, VV V, VZ Zk, 
                 CKS((grp_reduce<T>(g, fm, j + 1, Vi, [&](int k) { return Vj(0, k); },
                                    [&](int k) { return Vj(0, k); }, 1, G)));
                 std::vector<double> c1((size_t)std::max(j, 1) * S, 0.0), p1(S, 1.0), a(j);
+                std::vector<char> cont(M, 0);  // members with a system that continues
+                bool anycont = false;
                 for (int q = 0; q < S; ++q) {
                     if (!fin[q]) continue;
                     double aa = 0.0;
@@ -2419,11 +2466,18 @@ int fgmres_group(Grp &g, const std::vector<char> &mem, VB b, VX x, VV V, VZ Zk, 
                     if (act[q] && rho > 0) {  // continues: q~_j becomes q_j
                         for (int i = 0; i < j; ++i) c1[(size_t)i * S + q] = -a[i];
                         p1[q] = 1.0 / rho;
+                        cont[mq[q]] = 1;
+                        anycont = true;
                     }
                 }
-                std::vector<int> nvj(M, j);
-                auto Vw = [&](int k) { return V(j, k); };
-                CKS((grp_axpy<T>(g, fm, j, nvj, Vi, c1.data(), Vw, p1.data())));
+                // a system that stops here never reads q~_j again (x is
+                // updated from the z vectors, a restart rebuilds q_0), so its
+                // member's update is left out when none of its systems continues
+                if (anycont) {
+                    std::vector<int> nvj(M, j);
+                    auto Vw = [&](int k) { return V(j, k); };
+                    CKS((grp_axpy<T>(g, cont, j, nvj, Vi, c1.data(), Vw, p1.data())));
+                }
             }
             bool anycyc = false;
             for (int k = 0; k < M; ++k) {
@@ -2608,25 +2662,24 @@ int ensure_krylov32(st_handle h) {
 // bounds and each system's decisions are the single-handle ones, so every
 // right-hand side gets the result st_solve gives it.
 int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *u,
-                   st_solve_info *info) {
+                   bool guess, st_solve_info *info) {
     const int M = (int)g.hs.size(), S = g.S;
     for (st_handle h : g.hs) CKS(ensure_krylov32(h));
     std::vector<char> all(M, 1);
     std::vector<double> nf(S), nr(S), g0;
-    // ||f|| and ||u|| in one pass: from a zero initial guess the first
-    // residual is f itself
+    // ||f||, and ||u|| of an initial guess, in one pass: from a zero initial
+    // guess the first residual is f itself (without a guess u is not read)
     {
         auto FU = [&](int v, int k) { return v == 0 ? rhs[k] : (const double *)u[k]; };
-        auto F = [&](int k) { return rhs[k]; };
-        auto U = [&](int k) { return (const double *)u[k]; };
-        CKS((grp_reduce<double>(g, all, 2, FU, F, U, 2, g0)));
+        auto F = [&](int k) { return rhs[k]; };  // unused by the self dots
+        CKS((grp_reduce<double>(g, all, guess ? 2 : 1, FU, F, F, 0, g0)));
     }
     std::vector<char> u_zero(M, 1);
     for (int k = 0; k < M; ++k)
         for (int q = g.first[k]; q < g.first[k] + g.hs[k]->nrhs; ++q) {
             const double f2 = g0[(size_t)0 * S + q];
             nf[q] = std::isfinite(f2) ? std::sqrt(std::max(0.0, f2)) : f2;
-            u_zero[k] = u_zero[k] && g0[(size_t)3 * S + q] == 0.0;
+            if (guess) u_zero[k] = u_zero[k] && g0[(size_t)1 * S + q] == 0.0;
         }
     CKS(check_finite_rhs(nf));
     std::vector<int> total(M, 0), outer(M, 0);
@@ -2669,8 +2722,22 @@ int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *
     auto X32 = [&](int k) { return g.hs[k]->e32; };
     auto VV = [&](int j, int k) { return g.hs[k]->V32[j]; };
     auto ZZ = [&](int j, int k) { return g.hs[k]->Z32[j]; };
+    // without a guess u is not zeroed beforehand: a member's first update
+    // stores u = 0 + ||r|| e (the bits of an update of a zero u), and a member
+    // that never updates (or a solve that fails first) is zeroed on the way out
+    struct ZeroUnset {
+        Grp &g;
+        double *const *u;
+        std::vector<char> set;
+        ~ZeroUnset() {
+            for (size_t k = 0; k < set.size(); ++k)
+                if (!set[k])
+                    (void)launch_zero<double>(u[k], g.hs[k]->len * g.hs[k]->nrhs, g.hs[k]->stream);
+        }
+    } u_set{g, u, std::vector<char>(M, guess ? 1 : 0)};
     std::vector<char> run(M, 1);  // members still refining
     for (bool first = true;; first = false) {
+        NvtxRange range("refinement step");
         std::vector<char> need(M, 0);
         for (int k = 0; k < M; ++k) {
             if (!run[k]) continue;
@@ -2758,7 +2825,9 @@ int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *
                 corr = eb;
             }
             KScope ks(h, ST_PROF_VECTOR, 12.0 * n0, 2.0 * n0);
-            CK(launch_axpy_f32_f64(corr, u[k], &back[g.first[k]], h->nrhs, h->len, h->stream));
+            CK(launch_axpy_f32_f64(corr, u[k], &back[g.first[k]], h->nrhs, h->len, h->stream,
+                                   !u_set.set[k]));
+            u_set.set[k] = 1;
         }
     }
     for (int k = 0; k < M; ++k) {
@@ -2770,11 +2839,12 @@ int solve_ir_group(Grp &g, const double *const *rhs, double tol, double *const *
     return ST_OK;
 }
 
-int solve_ir(st_handle h, const double *rhs, double tol, double *u, st_solve_info *info) {
+int solve_ir(st_handle h, const double *rhs, double tol, double *u, bool guess,
+             st_solve_info *info) {
     Grp g;
     g.hs = {h};
     CKS(grp_begin(g, false));
-    return solve_ir_group(g, &rhs, tol, &u, info);
+    return solve_ir_group(g, &rhs, tol, &u, guess, info);
 }
 
 // Slab partition plan: rank's first slab, its slab count, the first level
@@ -3220,17 +3290,20 @@ static int setup_entry(st_handle *out, int geometry, int degree, const int *span
 
 int st_setup(st_handle *out, int geometry, int degree, const int *spans, int slabs,
              const st_options *opt, void *stream) {
+    NvtxRange range("st_setup");
     return setup_entry(out, geometry, degree, spans, slabs, opt, stream, false);
 }
 
 int st_setup_host(st_handle *out, int geometry, int degree, const int *spans, int slabs,
                   const st_options *opt) {
+    NvtxRange range("st_setup_host");
     return setup_entry(out, geometry, degree, spans, slabs, opt, nullptr, true);
 }
 
 int st_setup_partitioned(st_handle *out, int geometry, int degree, const int *spans,
                          int slabs_global, const st_options *opt, const st_comm *comm,
                          void *stream) {
+    NvtxRange range("st_setup_partitioned");
     if (out) *out = nullptr;
     if (!comm || !comm->sendrecv || !comm->allgather || !comm->allreduce_sum || comm->size < 1 ||
         comm->rank < 0 || comm->rank >= comm->size)
@@ -3295,6 +3368,7 @@ int st_sizes(st_handle h, int64_t *n_dofs, int *n_t, int *n_x, int *n_levels, si
 }
 
 int st_apply(st_handle h, const double *x, double *y) {
+    NvtxRange range("st_apply");
     CKS(check_ptr(h, x, "x"));
     CKS(check_ptr(h, y, "y"));
     if ((const void *)x == (void *)y) return fail(ST_ERR_INVALID_ARG, "x and y alias");
@@ -3367,6 +3441,7 @@ int st_load_gaussians(st_handle h, int nbumps, const double *centers, const doub
 }
 
 int st_smooth(st_handle h, double *u, const double *f, int nsteps) {
+    NvtxRange range("st_smooth");
     CKS(check_ptr(h, u, "u"));
     CKS(check_ptr(h, f, "f"));
     if (nsteps < 0) return fail(ST_ERR_INVALID_ARG, "nsteps < 0");
@@ -3434,6 +3509,7 @@ int st_block_minres(st_handle h, double alpha, double beta1, double beta2, const
 }
 
 int st_vcycle(st_handle h, double *u, const double *f) {
+    NvtxRange range("st_vcycle");
     CKS(check_ptr(h, u, "u"));
     CKS(check_ptr(h, f, "f"));
     const int rc = vcycle_entry(h, u, f);
@@ -3488,6 +3564,7 @@ extern "C" {
 
 int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_guess,
              st_solve_info *info) {
+    NvtxRange range("st_solve");
     CKS(check_ptr(h, rhs, "rhs"));
     CKS(check_ptr(h, u, "u"));
     if ((const void *)rhs == (void *)u) return fail(ST_ERR_INVALID_ARG, "rhs and u alias");
@@ -3498,13 +3575,14 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
     if (h->opt.autotune && !h->tuned) CKS(autotune(h));
     const auto t0 = std::chrono::steady_clock::now();
     try {
-        if (!use_guess) CK(launch_zero<double>(u, h->len * h->nrhs, h->stream));
+        const bool ir = h->opt.outer == ST_OUTER_IR && h->mixed;
+        if (!use_guess && !ir) CK(launch_zero<double>(u, h->len * h->nrhs, h->stream));
         h->hist.clear();
         h->n_sync = h->n_vl = 0;
         if (h->opt.outer == ST_OUTER_MG) {
             CKS(solve_mg(h, rhs, tol, u, info));
-        } else if (h->opt.outer == ST_OUTER_IR && h->mixed) {
-            CKS(solve_ir(h, rhs, tol, u, info));  // records its refinement steps
+        } else if (ir) {  // writes u itself without a guess; records its refinement steps
+            CKS(solve_ir(h, rhs, tol, u, use_guess != 0, info));
         } else {
             h->record_hist = true;
             const int rc = solve_fgmres(h, rhs, tol, u, info);
@@ -3526,6 +3604,7 @@ int st_solve(st_handle h, const double *rhs, double tol, double *u, int use_gues
 
 int st_solve_group(int n, const st_handle *hs, const double *const *rhs, double tol,
                    double *const *u, int use_guess, st_solve_info *info) {
+    NvtxRange range("st_solve_group");
     if (n < 1 || n > GH) return fail(ST_ERR_INVALID_ARG, "a group has 1 to %d handles", GH);
     if (!hs || !rhs || !u) return fail(ST_ERR_INVALID_ARG, "null array");
     if (!(tol > 0)) return fail(ST_ERR_INVALID_ARG, "tol must be > 0");
@@ -3560,13 +3639,11 @@ int st_solve_group(int n, const st_handle *hs, const double *const *rhs, double 
     int rc = ST_OK;
     try {
         for (int k = 0; k < n && rc == ST_OK; ++k) {
-            st_handle h = hs[k];
-            if (!use_guess && launch_zero<double>(u[k], h->len * h->nrhs, h->stream) != cudaSuccess)
-                rc = fail(ST_ERR_CUDA, "zeroing the initial guess failed");
+            st_handle h = hs[k];  // the refinement writes u itself without a guess
             h->hist.clear();
             h->n_sync = h->n_vl = 0;
         }
-        if (rc == ST_OK) rc = solve_ir_group(g, rhs, tol, u, info);
+        if (rc == ST_OK) rc = solve_ir_group(g, rhs, tol, u, use_guess != 0, info);
     } catch (...) {
         rc = fail(ST_ERR_OOM, "host exception during solve");
     }
@@ -3594,6 +3671,7 @@ int st_solve_group(int n, const st_handle *hs, const double *const *rhs, double 
 
 int st_solve_host(st_handle h, int nbatch, const double *rhs, double tol, double *u,
                   int use_guess, st_solve_info *info) {
+    NvtxRange range("st_solve_host");
     CKS(check_ptr(h, rhs, "rhs"));
     CKS(check_ptr(h, u, "u"));
     if (nbatch < 1) return fail(ST_ERR_INVALID_ARG, "nbatch must be >= 1");

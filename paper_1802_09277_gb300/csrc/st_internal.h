@@ -260,14 +260,19 @@ struct GLaunch {
 template <typename T>
 cudaError_t launch_gdot(const GLaunch &g, int nv, const T *const *xs, const T *const *w,
                         double *out, cudaStream_t s);
+// out[v * nsys + s] = dot of vector v with itself over system s (FP64 sums)
+template <typename T>
+cudaError_t launch_gnorm2(const GLaunch &g, int nv, const T *const *xs, double *out,
+                          cudaStream_t s);
 // out[(v * 2 + t) * nsys + s] = dot of vector v with target t (t1, t2) over system s
 template <typename T>
 cudaError_t launch_ggram2(const GLaunch &g, int nv, const T *const *xs, const T *const *t1,
                           const T *const *t2, double *out, cudaStream_t s);
-// y_s = post_s (y_s + sum_{v < snv[s]} coef[v * nsys + s] x_v)  (post NULL = 1)
+// y_s = post_s (y_s + sum_{v < snv[s]} coef[v * nsys + s] x_v)  (post NULL = 1;
+// y_zero: y_s is taken as zero and not read)
 template <typename T>
 cudaError_t launch_gaxpy(const GLaunch &g, int nv, const T *const *xs, const double *coef,
-                         T *const *y, const double *post, cudaStream_t s);
+                         T *const *y, const double *post, cudaStream_t s, bool y_zero = false);
 // y1 <- post1 (y1 + sum_v c1 x_v);  y2 <- post2 (y2 + c21 y1_old + sum_v c2 x_v)
 // (coefficients [v * nsys + s], scalars [s]); write1[s] = 0 leaves system
 // s's y1 untouched
@@ -282,9 +287,9 @@ cudaError_t launch_gaxpy2(const GLaunch &g, int nv, const T *const *xs, const do
 cudaError_t launch_separable_sum(double *f, const double *g, int K, long long nslab_t, int nx,
                                  int ny, int nz, cudaStream_t s);
 
-// y (FP64) += a_r * x (FP32) per rhs r
+// y (FP64) += a_r * x (FP32) per rhs r (store: y = 0 + a_r * x, y not read)
 cudaError_t launch_axpy_f32_f64(const float *x, double *y, const double *a, int nrhs,
-                                long long len, cudaStream_t s);
+                                long long len, cudaStream_t s, bool store = false);
 
 // y = a_r * x (per rhs), y may alias x
 cudaError_t launch_scale(const double *x, double *y, const double *a, int nrhs, long long len,
