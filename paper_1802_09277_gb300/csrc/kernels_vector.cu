@@ -426,7 +426,12 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <typename T>
+// Two-output update of system s, CNT vectors fixed at compile time (CNT < 0:
+// the run-time count nv).  With a fixed count the coefficients sit in
+// registers and every load of an element pair (y1, y2, the vectors) is
+// issued before its arithmetic; each output sees the same operations in the
+// same order in every instance.
+template <typename T, int CNT>
 __global__ void __launch_bounds__(256)
     k_gaxpy2(int nv, const __grid_constant__ GVecD<T> vl, const __grid_constant__ GTgtD<T> t1,
              const __grid_constant__ GTgtD<T> t2, const __grid_constant__ GAxpy2D<T> aa,
@@ -440,18 +445,76 @@ __global__ void __launch_bounds__(256)
     T *__restrict__ y1 = t1.p[mk];
     T *__restrict__ y2 = t2.p[mk];
     const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const T p1 = aa.post1[s], p2 = aa.post2[s], c21 = aa.c21[s];
     const int write1 = aa.write1[s];
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
-        const T a1o = y1[off + i];
-        T a1 = a1o, a2 = y2[off + i] + c21 * a1o;
-        for (int v = 0; v < nv; ++v) {
-            const T x = vl.v[v][mk][off + i];
-            a1 += aa.c1[v * NSYS_MAX + s] * x;
-            a2 += aa.c2[v * NSYS_MAX + s] * x;
+    if constexpr (CNT < 0) {
+        for (long long i = i0; i < len; i += stride) {
+            const T a1o = y1[off + i];
+            T a1 = a1o, a2 = y2[off + i] + c21 * a1o;
+            for (int v = 0; v < nv; ++v) {
+                const T x = vl.v[v][mk][off + i];
+                a1 += aa.c1[v * NSYS_MAX + s] * x;
+                a2 += aa.c2[v * NSYS_MAX + s] * x;
+            }
+            if (write1) y1[off + i] = p1 * a1;
+            y2[off + i] = p2 * a2;
         }
-        if (write1) y1[off + i] = p1 * a1;
-        y2[off + i] = p2 * a2;
+    } else {
+        constexpr int NV = CNT > 0 ? CNT : 1;
+        T k1[NV], k2[NV];
+        const T *x[NV];
+#pragma unroll
+        for (int v = 0; v < CNT; ++v) {
+            k1[v] = aa.c1[v * NSYS_MAX + s];
+            k2[v] = aa.c2[v * NSYS_MAX + s];
+            x[v] = vl.v[v][mk] + off;
+        }
+        if (gm.vec[mk]) {  // off is even because len is
+            using P2 = typename Pair<T>::V;
+            const long long np = len / 2;
+            P2 *q1 = reinterpret_cast<P2 *>(y1 + off);
+            P2 *q2 = reinterpret_cast<P2 *>(y2 + off);
+            for (long long i = i0; i < np; i += stride) {
+                const P2 u1 = q1[i], u2 = q2[i];
+                P2 xv[NV];
+#pragma unroll
+                for (int v = 0; v < CNT; ++v) xv[v] = reinterpret_cast<const P2 *>(x[v])[i];
+                T a1x = u1.x, a1y = u1.y, a2x = u2.x + c21 * u1.x, a2y = u2.y + c21 * u1.y;
+#pragma unroll
+                for (int v = 0; v < CNT; ++v) {
+                    a1x += k1[v] * xv[v].x;
+                    a2x += k2[v] * xv[v].x;
+                    a1y += k1[v] * xv[v].y;
+                    a2y += k2[v] * xv[v].y;
+                }
+                if (write1) {
+                    P2 o1;
+                    o1.x = p1 * a1x;
+                    o1.y = p1 * a1y;
+                    q1[i] = o1;
+                }
+                P2 o2;
+                o2.x = p2 * a2x;
+                o2.y = p2 * a2y;
+                q2[i] = o2;
+            }
+        } else {
+            for (long long i = i0; i < len; i += stride) {
+                const T a1o = y1[off + i], b2 = y2[off + i];
+                T xv[NV];
+#pragma unroll
+                for (int v = 0; v < CNT; ++v) xv[v] = x[v][i];
+                T a1 = a1o, a2 = b2 + c21 * a1o;
+#pragma unroll
+                for (int v = 0; v < CNT; ++v) {
+                    a1 += k1[v] * xv[v];
+                    a2 += k2[v] * xv[v];
+                }
+                if (write1) y1[off + i] = p1 * a1;
+                y2[off + i] = p2 * a2;
+            }
+        }
     }
 }
 
@@ -624,8 +687,30 @@ cudaError_t launch_gaxpy2(const GLaunch &g, int nv, const T *const *xs, const do
         aa.post2[i] = (T)post2[i];
         aa.write1[i] = write1[i];
     }
-    const cudaError_t e = launch_pdl(k_gaxpy2<T>, dim3(axpy_blocks(g, 256), g.nsys), dim3(256), 0,
-                                     s, nv, vl, a, b, aa, mem_of(g), sys_of(g));
+    GMemD gm = mem_of(g);
+    for (int k = 0; k < g.nmem; ++k) {  // pair loads: every vector aligned to two elements
+        int vec2 = (g.len[k] % 2 == 0) && al2<T>(y1[k]) && al2<T>(y2[k]);
+        for (int v = 0; v < nv; ++v) vec2 = vec2 && al2<T>(vl.v[v][k]);
+        gm.vec[k] = vec2;
+    }
+    const dim3 grid(axpy_blocks(g, 256), g.nsys);
+    const GSysD gs = sys_of(g);
+    cudaError_t e;
+    switch (nv) {
+#define ST_GAXPY2_CASE(C) \
+    case C: e = launch_pdl(k_gaxpy2<T, C>, grid, dim3(256), 0, s, nv, vl, a, b, aa, gm, gs); break;
+        ST_GAXPY2_CASE(0)
+        ST_GAXPY2_CASE(1)
+        ST_GAXPY2_CASE(2)
+        ST_GAXPY2_CASE(3)
+        ST_GAXPY2_CASE(4)
+        ST_GAXPY2_CASE(5)
+        ST_GAXPY2_CASE(6)
+        ST_GAXPY2_CASE(7)
+        ST_GAXPY2_CASE(8)
+#undef ST_GAXPY2_CASE
+        default: e = launch_pdl(k_gaxpy2<T, -1>, grid, dim3(256), 0, s, nv, vl, a, b, aa, gm, gs);
+    }
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
