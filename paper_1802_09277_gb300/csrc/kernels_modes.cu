@@ -457,9 +457,16 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int st = 0; st <= NU; ++st) last[st] = T(0);
     T reven[NT];
+    // the next slab's column is loaded while this one is computed: two
+    // slabs' loads in flight per thread (one alone left the kernel
+    // latency-bound at about 5 TB/s)
+    T rn[NT];
+    if (h < n1) load_col<T, NT>(f, fb + h * slab, S, rn);
     for (int n = h; n < n1; ++n) {
         T r[NT], x[NT];
-        load_col<T, NT>(f, fb + n * slab, S, r);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) r[i] = rn[i];
+        if (n + 1 < n1) load_col<T, NT>(f, fb + (n + 1) * slab, S, rn);
 #pragma unroll
         for (int i = 0; i < NT; ++i) x[i] = T(0);
         T nl[NU + 1];
@@ -516,11 +523,27 @@ __global__ void __launch_bounds__(256)
     T last[NU];  // previous slab's last entry before step s + 1
 #pragma unroll
     for (int st = 0; st < NU; ++st) last[st] = T(0);
+    // the next slab's columns are loaded while this one is computed (the
+    // coarse column once per slab pair)
+    T xn[NT], en[NT], fn[NT];
+    if (h < n1) {
+        load_col<T, NT>(uin, fb + h * slab, S, xn);
+        load_col<T, NT>(ec, cb + (long long)(h / 2) * slab, S, en);
+        load_col<T, NT>(f, fb + h * slab, S, fn);
+    }
     for (int n = h; n < n1; ++n) {
         T x[NT], e[NT], fr[NT];
-        load_col<T, NT>(uin, fb + n * slab, S, x);
-        load_col<T, NT>(ec, cb + (long long)(n / 2) * slab, S, e);
-        load_col<T, NT>(f, fb + n * slab, S, fr);
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            x[i] = xn[i];
+            e[i] = en[i];
+            fr[i] = fn[i];
+        }
+        if (n + 1 < n1) {
+            load_col<T, NT>(uin, fb + (n + 1) * slab, S, xn);
+            if (((n + 1) & 1) == 0) load_col<T, NT>(ec, cb + (long long)((n + 1) / 2) * slab, S, en);
+            load_col<T, NT>(f, fb + (n + 1) * slab, S, fn);
+        }
         const int half = (n & 1) ? NT : 0;  // row block of P_t for this slab of the pair
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
