@@ -435,8 +435,17 @@ __global__ void __launch_bounds__(256)
 // restriction.  In residual form a step is u' = u + w A^-1 r and the residual
 // moves to r' = (1 - w) r + e_0 (p' - p), p / p' the previous slab's last
 // entry before / after the step, so only A^-1 is needed; r starts at f.
+// CTAs per SM the down sweep is compiled for: five (48 registers) where its
+// prefetching loop fits them without spilling (FP32, N_t <= 3, or N_t = 4
+// with up to four steps); there the prefetch at 61 registers lost a CTA per
+// SM and more time than it saved
 template <typename T, int NT, int NU>
-__global__ void __launch_bounds__(256)
+constexpr int sweep_down_min_blocks() {
+    return (sizeof(T) == 4 && (NT <= 3 || (NT == 4 && NU <= 4))) ? 5 : 1;
+}
+
+template <typename T, int NT, int NU>
+__global__ void __launch_bounds__(256, sweep_down_min_blocks<T, NT, NU>())
     k_lv_sweep_down(const T *__restrict__ f, T *__restrict__ u, T *__restrict__ fc,
                     const T *__restrict__ inv, long long S, const __grid_constant__ ProlongCoefs<T> pc,
                     T omega, int N, int C, int nchunk, long long nwork) {
