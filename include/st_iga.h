@@ -225,6 +225,22 @@ int st_apply(st_handle h, const double *x, double *y);
 /* r = f - L_h u (FP64).  u, f, r: device, n_dofs each; r must not alias u. */
 int st_residual(st_handle h, const double *u, const double *f, double *r);
 
+/* r = f - L_h u (Eq. 2.4, through the Kronecker factors of Eq. 2.5) on FP64
+ * data in double-float arithmetic: every value a pair of FP32 numbers
+ * hi + lo (about 48 significant bits), products summed by compensated Dot2
+ * sums.  This is the residual the ST_OUTER_IR refinement takes at every step
+ * of a mixed-precision handle, here on any handle; it agrees with
+ * st_residual to about 1e-14 relative.  u, f, r: device, n_dofs each; r must
+ * not alias u.  slabs_per_cta: 0 lets the library choose how many
+ * consecutive slabs one CTA of the tiled kernel handles (several on large
+ * grids: the coupling plane B_n u_{n-1} of a CTA's later slabs is then taken
+ * from the slab before instead of recomputed); 1, 2, 4 or 8 sets it.  The
+ * result has the same bits for every value.  The 3D p = 3 residual marches
+ * in z, one slab per CTA, and ignores it.  Errors: ST_ERR_INVALID_ARG for a
+ * null or host-only handle, a null pointer, aliasing or another
+ * slabs_per_cta; ST_ERR_CUDA if a launch fails. */
+int st_residual_df(st_handle h, const double *u, const double *f, double *r, int slabs_per_cta);
+
 /* Load vector of a source given by its B-spline coefficients in the trial
  * basis of every slab: f = (M_t (x) M_x) c, which is l_h(phi_i) of Sec. 2.3
  * exactly (u0 = 0).  c, f: device, n_dofs each, must not alias. */

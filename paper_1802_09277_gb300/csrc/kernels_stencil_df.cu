@@ -8,6 +8,6 @@ namespace st {
 template cudaError_t launch_stencil<double, dfloat>(const double *, const double *, double *,
                                                     const Bands<double> &, const Grid &,
                                                     const TimeCoefs<dfloat> &, int, int, int,
-                                                    cudaStream_t);
+                                                    cudaStream_t, int);
 
 }  // namespace st

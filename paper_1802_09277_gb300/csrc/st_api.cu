@@ -1799,7 +1799,7 @@ int residual64(st_handle h, const double *u, const double *f, double *r) {
 // The refinement residual r = f - L u of the mixed modes on FP64 data in
 // double-float arithmetic (about 48 significant bits, far below the FP32
 // inner solve's error) instead of FP64, which runs at 1/64 of the FP32 rate.
-int residual_df(st_handle h, const double *u, const double *f, double *r) {
+int residual_df(st_handle h, const double *u, const double *f, double *r, int sch = 0) {
     NvtxRange range("FP64 residual");
     TimeCoefs<dfloat> tc = pack_time<dfloat>(h, 0, MODE_RES, false);
     CKS(exchange_halo<double>(h, 0, u, &tc.halo));
@@ -1810,7 +1810,7 @@ int residual_df(st_handle h, const double *u, const double *f, double *r) {
     KScope ks(h, ST_PROF_STENCILDF, 8.0 * (3.0 * E + (double)h->N * h->nrhs * h->g.nxyz),
               planes_pt * fsp + E * 4.0 * h->nt);
     CK((launch_stencil<double, dfloat>(u, f, r, space<double>(h).bands, h->g, tc, h->lv[0].nslab,
-                                       0, h->N * h->nrhs, h->stream)));
+                                       0, h->N * h->nrhs, h->stream, sch)));
     return ST_OK;
 }
 
@@ -3381,6 +3381,17 @@ int st_residual(st_handle h, const double *u, const double *f, double *r) {
     CKS(check_ptr(h, r, "r"));
     if ((const void *)u == (void *)r) return fail(ST_ERR_INVALID_ARG, "u and r alias");
     return residual64(h, u, f, r);
+}
+
+int st_residual_df(st_handle h, const double *u, const double *f, double *r, int slabs_per_cta) {
+    CKS(check_ptr(h, u, "u"));
+    CKS(check_ptr(h, f, "f"));
+    CKS(check_ptr(h, r, "r"));
+    if ((const void *)u == (void *)r) return fail(ST_ERR_INVALID_ARG, "u and r alias");
+    if (slabs_per_cta != 0 && slabs_per_cta != 1 && slabs_per_cta != 2 && slabs_per_cta != 4 &&
+        slabs_per_cta != 8)
+        return fail(ST_ERR_INVALID_ARG, "slabs_per_cta must be 0, 1, 2, 4 or 8");
+    return residual_df(h, u, f, r, slabs_per_cta);
 }
 
 int st_load_coeffs(st_handle h, const double *c, double *f) {

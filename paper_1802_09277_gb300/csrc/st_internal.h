@@ -112,11 +112,13 @@ struct Bands {
 };
 
 // ---- launchers (kernels_stencil.cu) ----
-// T: data type in HBM; C: arithmetic (T itself, or dfloat on FP64 data)
+// T: data type in HBM; C: arithmetic (T itself, or dfloat on FP64 data).
+// sch: slabs per CTA of the double-float kernel (0: chosen from the grid
+// size; 1, 2, 4 or 8); one slab per CTA otherwise
 template <typename T, typename C = T>
 cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands, const Grid &g,
                            const TimeCoefs<C> &tc, int slabs_per_prob, int slab0, int nslabs,
-                           cudaStream_t s);
+                           cudaStream_t s, int sch = 0);
 
 // ---- launchers (kernels_transform.cu) ----
 // C[b][m][n] = sum_k A(b,m,k) B(b,k,n) with arbitrary strides

@@ -11,10 +11,20 @@
 // optionally followed by the forward time transform w = Y r (the first step
 // of applying A_n^{-1} through Eq. 3.1).
 //
-// One CTA owns one slab and one spatial tile (all time planes).  Each plane
-// tile plus a halo of p is staged in shared memory, then reduced axis by
-// axis: x-pass (M1x, K1x), y-pass, z-pass; the 2p+1 band coefficients of the
-// tile's rows are staged once per CTA.
+// One CTA owns one spatial tile (all time planes) of `sch` consecutive slabs.
+// Each plane tile plus a halo of p is staged in shared memory, then reduced
+// axis by axis: x-pass (M1x, K1x), y-pass, z-pass; the 2p+1 band
+// coefficients of the tile's rows are staged once per CTA.
+//
+// In double-float the coupling term enters the accumulator of time plane 0
+// as one more Dot2 term (-m_prev), ahead of the slab's own terms, and a CTA
+// with several slabs keeps M_x u of each slab's last time plane for the next
+// one: B_n u_{n-1} is then never recomputed inside a CTA (one mass-only plane
+// of staging and three passes saved per slab; 8 % of the multiply-adds at
+// N_t = 4).  The carried value has the bits a recomputation would give (the
+// mass passes are the same operation sequence), so the result does not
+// depend on `sch`.  FP64 and FP32 run one slab per CTA and add the coupling
+// term in the epilogue.
 //
 // Storage type T (FP64 or FP32 in HBM) and compute type C are separate: the
 // FP64-accurate residual of the mixed-precision refinement computes in
@@ -146,8 +156,10 @@ template <typename T, typename C, int P, int DIM, int NTC = 0>
 __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads,
                                   StencilSmem<C, P, DIM>::min_blocks(NTC))
     k_stencil(const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ out, Bands<T> bands,
-              Grid g, const __grid_constant__ TimeCoefs<C> tc, int slabs_per_prob, int slab0, int tiles_x, int tiles_y) {
+              Grid g, const __grid_constant__ TimeCoefs<C> tc, int slabs_per_prob, int slab0,
+              int slab_end, int sch, int tiles_x, int tiles_y) {
     using SM = StencilSmem<C, P, DIM>;
+    constexpr bool DF = std::is_same<C, dfloat>::value;
     constexpr int TX = SM::TX, TY = SM::TY, TZ = SM::TZ, TZL = SM::TZL;
     constexpr int HX = SM::HX, HY = SM::HY, HZ = SM::HZ;
     constexpr int SX = SM::SX, SY = SM::SY, SZ = SM::SZ, W = SM::W;
@@ -171,7 +183,6 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads,
     const int x0 = (tile % tiles_x) * TX;
     const int y0 = ((tile / tiles_x) % tiles_y) * TY;
     const int z0 = (tile / (tiles_x * tiles_y)) * TZ;
-    const int slab = slab0 + blockIdx.y;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const long long nxyz = g.nxyz;
     constexpr int NL = NTC > 0 ? NTC : NTMAX;
@@ -198,159 +209,176 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads,
 
     const int tx = tid % TX, ty = (tid / TX) % TY;
     const int za = (tid / (TX * TY)) * TZL;  // this thread's first z point in the tile
-    Acc<C> acc[TZL][NL];
     C mprev[TZL];
 #pragma unroll
     for (int a = 0; a < TZL; ++a) mprev[a] = C(0);
 
-    const T *uslab = u + (long long)slab * nt * nxyz;
-    const bool first = (slab % slabs_per_prob) == 0;
-    const bool has_prev = (tc.mode != MODE_MASS) && (!first || tc.halo != nullptr);
-    // the coupling plane: the previous slab's last time plane, or for the
-    // first slab of a partition the neighbour's plane in the halo buffer
-    const T *prev = !first ? uslab - nxyz
-                    : tc.halo ? static_cast<const T *>(tc.halo) + (long long)(slab / slabs_per_prob) * nxyz
-                              : nullptr;
+    // one slab per CTA (a single trip, known to the compiler) unless double-float
+    const int sbeg = slab0 + (int)blockIdx.y * (DF ? sch : 1);
+    const int send = DF ? min(sbeg + sch, slab_end) : sbeg + 1;
+    for (int slab = sbeg; slab < send; ++slab) {
+        Acc<C> acc[TZL][NL];
+        const T *uslab = u + (long long)slab * nt * nxyz;
+        const bool first = (slab % slabs_per_prob) == 0;
+        const bool has_prev = (tc.mode != MODE_MASS) && (!first || tc.halo != nullptr);
+        // double-float, not the CTA's first slab: M_x u of the coupling plane is
+        // the previous slab's last time plane, kept from that slab's z-pass
+        const bool carried = DF && has_prev && !first && slab > sbeg;
+        if (carried) {
+#pragma unroll
+            for (int al = 0; al < TZL; ++al) acc[al][0].add(C(-1), mprev[al]);
+        }
+        // the coupling plane: the previous slab's last time plane, or for the
+        // first slab of a partition the neighbour's plane in the halo buffer
+        const T *prev = !first ? uslab - nxyz
+                        : tc.halo ? static_cast<const T *>(tc.halo) + (long long)(slab / slabs_per_prob) * nxyz
+                                  : nullptr;
 
-    for (int jj = has_prev ? -1 : 0; jj < nt; ++jj) {
-        const T *plane = (jj < 0) ? prev : uslab + (long long)jj * nxyz;
-        __syncthreads();
-        for (int e = tid; e < SZ * SY * SX; e += NTH) {
-            const int sx = e % SX, sy = (e / SX) % SY, sz = e / (SX * SY);
-            const int gx = x0 + sx - HX, gy = y0 + sy - HY, gz = z0 + sz - HZ;
-            C v = C(0);
-            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-                v = to_c<C>(plane[((long long)gz * ny + gy) * nx + gx]);
-            S[e] = v;
-        }
-        __syncthreads();
-        // x-pass: A = M1x u, B = K1x u (the coupling plane needs only M_x u)
-        const bool mass_only = jj < 0;
-        for (int e = tid; e < SZ * SY * TX; e += NTH) {
-            const int ex = e % TX, row = e / TX;  // row = sz*SY + sy
-            const C *srow = S + row * SX + ex;
-            Acc<C> a, b;
-            if (mass_only) {
-#pragma unroll
-                for (int o = 0; o < W; ++o) a.add(bMx[ex * W + o], srow[o]);
-            } else {
-#pragma unroll
-                for (int o = 0; o < W; ++o) {
-                    const C sv = srow[o];
-                    a.add(bMx[ex * W + o], sv);
-                    b.add(bKx[ex * W + o], sv);
-                }
+        for (int jj = (has_prev && !carried) ? -1 : 0; jj < nt; ++jj) {
+            const T *plane = (jj < 0) ? prev : uslab + (long long)jj * nxyz;
+            __syncthreads();
+            for (int e = tid; e < SZ * SY * SX; e += NTH) {
+                const int sx = e % SX, sy = (e / SX) % SY, sz = e / (SX * SY);
+                const int gx = x0 + sx - HX, gy = y0 + sy - HY, gz = z0 + sz - HZ;
+                C v = C(0);
+                if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+                    v = to_c<C>(plane[((long long)gz * ny + gy) * nx + gx]);
+                S[e] = v;
             }
-            A[e] = a.get();
-            B[e] = b.get();
-        }
-        __syncthreads();
-        const C *pm;
-        const C *pk;
-        if (DIM >= 2) {
-            // y-pass: AA = M1y A, SS = K1y A + M1y B
-            for (int e = tid; e < SZ * TY * TX; e += NTH) {
-                const int ex = e % TX, ey = (e / TX) % TY, sz = e / (TX * TY);
-                Acc<C> aa, ss;
+            __syncthreads();
+            // x-pass: A = M1x u, B = K1x u (the coupling plane needs only M_x u)
+            const bool mass_only = jj < 0;
+            for (int e = tid; e < SZ * SY * TX; e += NTH) {
+                const int ex = e % TX, row = e / TX;  // row = sz*SY + sy
+                const C *srow = S + row * SX + ex;
+                Acc<C> a, b;
                 if (mass_only) {
 #pragma unroll
-                    for (int o = 0; o < W; ++o)
-                        aa.add(bMy[ey * W + o], A[(sz * SY + ey + o) * TX + ex]);
+                    for (int o = 0; o < W; ++o) a.add(bMx[ex * W + o], srow[o]);
                 } else {
 #pragma unroll
                     for (int o = 0; o < W; ++o) {
-                        const int idx = (sz * SY + ey + o) * TX + ex;
-                        const C av = A[idx], bv = B[idx];
-                        const C my = bMy[ey * W + o], ky = bKy[ey * W + o];
-                        aa.add(my, av);
-                        ss.add(ky, av);
-                        ss.add(my, bv);
+                        const C sv = srow[o];
+                        a.add(bMx[ex * W + o], sv);
+                        b.add(bKx[ex * W + o], sv);
                     }
                 }
-                AA[e] = aa.get();
-                SS[e] = ss.get();
+                A[e] = a.get();
+                B[e] = b.get();
             }
             __syncthreads();
-            pm = AA;
-            pk = SS;
-        } else {
-            pm = A;
-            pk = B;
-        }
-        // z-pass and accumulation into this thread's output points
+            const C *pm;
+            const C *pk;
+            if (DIM >= 2) {
+                // y-pass: AA = M1y A, SS = K1y A + M1y B
+                for (int e = tid; e < SZ * TY * TX; e += NTH) {
+                    const int ex = e % TX, ey = (e / TX) % TY, sz = e / (TX * TY);
+                    Acc<C> aa, ss;
+                    if (mass_only) {
 #pragma unroll
-        for (int al = 0; al < TZL; ++al) {
-            const int a = za + al;
-            C m, k;
-            if (DIM >= 3) {
-                Acc<C> am, ak;
+                        for (int o = 0; o < W; ++o)
+                            aa.add(bMy[ey * W + o], A[(sz * SY + ey + o) * TX + ex]);
+                    } else {
 #pragma unroll
-                for (int o = 0; o < W; ++o) {
-                    const int idx = ((a + o) * TY + ty) * TX + tx;
-                    const C mz = bMz[a * W + o], kz = bKz[a * W + o];
-                    am.add(mz, pm[idx]);
-                    ak.add(kz, pm[idx]);
-                    ak.add(mz, pk[idx]);
-                }
-                m = am.get();
-                k = ak.get();
-            } else {
-                m = pm[ty * TX + tx];
-                k = pk[ty * TX + tx];
-            }
-            if (jj < 0) {
-                mprev[al] = m;
-            } else {
-#pragma unroll
-                for (int i = 0; i < NL; ++i)
-                    if (i < nt) {
-                        acc[al][i].add(tc.CK[i * NTMAX + jj], m);
-                        acc[al][i].add(tc.CM[i * NTMAX + jj], k);
+                        for (int o = 0; o < W; ++o) {
+                            const int idx = (sz * SY + ey + o) * TX + ex;
+                            const C av = A[idx], bv = B[idx];
+                            const C my = bMy[ey * W + o], ky = bKy[ey * W + o];
+                            aa.add(my, av);
+                            ss.add(ky, av);
+                            ss.add(my, bv);
+                        }
                     }
+                    AA[e] = aa.get();
+                    SS[e] = ss.get();
+                }
+                __syncthreads();
+                pm = AA;
+                pk = SS;
+            } else {
+                pm = A;
+                pk = B;
+            }
+            // z-pass and accumulation into this thread's output points
+#pragma unroll
+            for (int al = 0; al < TZL; ++al) {
+                const int a = za + al;
+                C m, k;
+                if (DIM >= 3) {
+                    Acc<C> am, ak;
+#pragma unroll
+                    for (int o = 0; o < W; ++o) {
+                        const int idx = ((a + o) * TY + ty) * TX + tx;
+                        const C mz = bMz[a * W + o], kz = bKz[a * W + o];
+                        am.add(mz, pm[idx]);
+                        ak.add(kz, pm[idx]);
+                        ak.add(mz, pk[idx]);
+                    }
+                    m = am.get();
+                    k = ak.get();
+                } else {
+                    m = pm[ty * TX + tx];
+                    k = pk[ty * TX + tx];
+                }
+                if (jj < 0) {
+                    if constexpr (DF)
+                        acc[al][0].add(C(-1), m);
+                    else
+                        mprev[al] = m;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NL; ++i)
+                        if (i < nt) {
+                            acc[al][i].add(tc.CK[i * NTMAX + jj], m);
+                            acc[al][i].add(tc.CM[i * NTMAX + jj], k);
+                        }
+                    if (DF && jj == nt - 1) mprev[al] = m;  // the next slab's coupling plane
+                }
             }
         }
-    }
 
-    // epilogue
-    const int gx = x0 + tx, gy = y0 + ty;
-    if (gx >= nx || gy >= ny) return;
+        // epilogue (no barrier below: threads outside the grid skip it)
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx < nx && gy < ny) {
 #pragma unroll
-    for (int al = 0; al < TZL; ++al) {
-        const int a = al;  // accumulator index; the z point is za + al
-        const int gz = z0 + za + al;
-        if (gz >= nz) break;
-        const long long sp = ((long long)gz * ny + gy) * nx + gx;
-        const long long base = (long long)slab * nt * nxyz + sp;
-        C r[NL];
+            for (int al = 0; al < TZL; ++al) {
+                const int a = al;  // accumulator index; the z point is za + al
+                const int gz = z0 + za + al;
+                if (gz >= nz) break;
+                const long long sp = ((long long)gz * ny + gy) * nx + gx;
+                const long long base = (long long)slab * nt * nxyz + sp;
+                C r[NL];
 #pragma unroll
-        for (int i = 0; i < NL; ++i) {
-            if (i >= nt) {
-                r[i] = C(0);
-                continue;
+                for (int i = 0; i < NL; ++i) {
+                    if (i >= nt) {
+                        r[i] = C(0);
+                        continue;
+                    }
+                    C v = acc[a][i].get();
+                    if (tc.mode == MODE_RES) {
+                        v = to_c<C>(f[base + (long long)i * nxyz]) - v;
+                        if (!DF && i == 0) v += mprev[a];
+                    } else if (tc.mode == MODE_APPLY) {
+                        if (!DF && i == 0) v -= mprev[a];
+                    }
+                    r[i] = v;
+                }
+                if (tc.fuse_y) {
+#pragma unroll
+                    for (int i = 0; i < NL; ++i) {
+                        if (i >= nt) break;
+                        C w = C(0);
+#pragma unroll
+                        for (int j = 0; j < NL; ++j)
+                            if (j < nt) w = madd(w, tc.Y[i * NTMAX + j], r[j]);
+                        out[base + (long long)i * nxyz] = from_c<T>(w);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NL; ++i)
+                        if (i < nt) out[base + (long long)i * nxyz] = from_c<T>(r[i]);
+                }
             }
-            C v = acc[a][i].get();
-            if (tc.mode == MODE_RES) {
-                v = to_c<C>(f[base + (long long)i * nxyz]) - v;
-                if (i == 0) v += mprev[a];
-            } else if (tc.mode == MODE_APPLY) {
-                if (i == 0) v -= mprev[a];
-            }
-            r[i] = v;
-        }
-        if (tc.fuse_y) {
-#pragma unroll
-            for (int i = 0; i < NL; ++i) {
-                if (i >= nt) break;
-                C w = C(0);
-#pragma unroll
-                for (int j = 0; j < NL; ++j)
-                    if (j < nt) w = madd(w, tc.Y[i * NTMAX + j], r[j]);
-                out[base + (long long)i * nxyz] = from_c<T>(w);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < NL; ++i)
-                if (i < nt) out[base + (long long)i * nxyz] = from_c<T>(r[i]);
         }
     }
 }
@@ -358,7 +386,7 @@ __global__ void __launch_bounds__(StencilSmem<C, P, DIM>::threads,
 template <typename T, typename C, int P, int DIM, int NTC = 0>
 static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<T> &bands,
                                     const Grid &g, const TimeCoefs<C> &tc, int slabs_per_prob,
-                                    int slab0, int nslabs, cudaStream_t s) {
+                                    int slab0, int nslabs, cudaStream_t s, int sch_req) {
     using SM = StencilSmem<C, P, DIM>;
     static std::atomic<unsigned long long> attr{0};
     {
@@ -370,10 +398,23 @@ static cudaError_t launch_stencil_t(const T *u, const T *f, T *out, const Bands<
     const int ty = (g.ny + SM::TY - 1) / SM::TY;
     const int tz = (g.nz + SM::TZ - 1) / SM::TZ;
     if (nslabs <= 0) return cudaSuccess;
-    if (nslabs > 65535) return cudaErrorInvalidValue;
-    dim3 grid((unsigned)(tx * ty * tz), (unsigned)nslabs);
-    k_stencil<T, C, P, DIM, NTC><<<grid, SM::threads, SM::bytes, s>>>(u, f, out, bands, g, tc,
-                                                                      slabs_per_prob, slab0, tx, ty);
+    // double-float: up to 8 slabs per CTA while at least 8192 CTAs remain
+    // (many waves of the GPU's resident CTAs), or the count asked for;
+    // FP64 / FP32: one
+    int sch = 1;
+    if constexpr (std::is_same<C, dfloat>::value) {
+        if (sch_req > 0) {
+            sch = sch_req;
+        } else {
+            const long long tiles = (long long)tx * ty * tz;
+            while (sch < 8 && tiles * ((nslabs + 2 * sch - 1) / (2 * sch)) >= 8192) sch *= 2;
+        }
+    }
+    const int gy = (nslabs + sch - 1) / sch;
+    if (gy > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)(tx * ty * tz), (unsigned)gy);
+    k_stencil<T, C, P, DIM, NTC><<<grid, SM::threads, SM::bytes, s>>>(
+        u, f, out, bands, g, tc, slabs_per_prob, slab0, slab0 + nslabs, sch, tx, ty);
     return cudaGetLastError();
 }
 
@@ -601,7 +642,8 @@ static cudaError_t launch_stencil_zm_t(const T *u, const T *f, T *out, const Ban
 template <typename T, typename C>
 cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands, const Grid &g,
                            const TimeCoefs<C> &tc, int slabs_per_prob, int slab0, int nslabs,
-                           cudaStream_t s) {
+                           cudaStream_t s, int sch) {
+    if (sch < 0 || sch > 8 || (sch & (sch - 1)) != 0) return cudaErrorInvalidValue;
 #define ST_NT(PP, DD, N)                                                                        \
     if (tc.nt == N) {                                                                           \
         if constexpr (DD == 3 && PP >= 3) {                                                     \
@@ -610,7 +652,7 @@ cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands
             if (ez != cudaErrorNotSupported) return ez;                                         \
         }                                                                                       \
         return launch_stencil_t<T, C, PP, DD, N>(u, f, out, bands, g, tc, slabs_per_prob, slab0, \
-                                                 nslabs, s);                                    \
+                                                 nslabs, s, sch);                               \
     }
 #define ST_CASE(PP, DD)                                                                         \
     if (g.p == PP && g.dim == DD) {                                                             \
@@ -618,7 +660,7 @@ cudaError_t launch_stencil(const T *u, const T *f, T *out, const Bands<T> &bands
             ST_NT(PP, DD, 3) ST_NT(PP, DD, 4) ST_NT(PP, DD, 5) ST_NT(PP, DD, 6)                  \
         }                                                                                       \
         return launch_stencil_t<T, C, PP, DD>(u, f, out, bands, g, tc, slabs_per_prob, slab0,   \
-                                              nslabs, s);                                       \
+                                              nslabs, s, sch);                                  \
     }
     ST_CASE(1, 1)
     ST_CASE(2, 1)

@@ -27,7 +27,7 @@ SPATIAL = {"fd": 0, "minres": 1}
 
 # every symbol declared in include/st_iga.h
 SYMBOLS = ["st_options_default", "st_setup", "st_setup_host", "st_destroy", "st_set_stream",
-           "st_sizes", "st_apply", "st_residual", "st_load_coeffs", "st_load_gaussians", "st_smooth",
+           "st_sizes", "st_apply", "st_residual", "st_residual_df", "st_load_coeffs", "st_load_gaussians", "st_smooth",
            "st_smooth_static", "st_set_wait_limit", "st_block_minres", "st_vcycle",
            "st_solve", "st_autotune", "st_profile", "st_profile_read", "st_time_factors", "st_time_spectrum", "st_space_factors",
            "st_time_prolongation", "st_level_shape", "st_space_prolongation", "st_last_error", "st_serve_opts_default", "st_serve_start",
@@ -129,6 +129,7 @@ def load():
                          ctypes.POINTER(ctypes.c_size_t)]),
         "st_apply": (I, [P, P, P]),
         "st_residual": (I, [P, P, P, P]),
+        "st_residual_df": (I, [P, P, P, P, I]),
         "st_load_coeffs": (I, [P, P, P]),
         "st_load_gaussians": (I, [P, I, dp, dp, dp, P]),
         "st_smooth": (I, [P, P, P, I]),
@@ -273,6 +274,12 @@ class Solver:
     def residual(self, u, f, r):
         _check(_lib.st_residual(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f"),
                                 _dptr(r, self.ndofs, "r")))
+
+    def residual_df(self, u, f, r, slabs_per_cta=0):
+        """The refinement's double-float residual r = f - L u (FP64 data);
+        slabs_per_cta 0 (library's choice), 1, 2, 4 or 8."""
+        _check(_lib.st_residual_df(self._h, _dptr(u, self.ndofs, "u"), _dptr(f, self.ndofs, "f"),
+                                   _dptr(r, self.ndofs, "r"), int(slabs_per_cta)))
 
     def load_coeffs(self, c, f):
         _check(_lib.st_load_coeffs(self._h, _dptr(c, self.ndofs, "c"), _dptr(f, self.ndofs, "f")))
