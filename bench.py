@@ -750,13 +750,11 @@ def make_len(d, spans, p, N, ne):
 # over the class's launches in one solve, ncu with its default cache flush
 # between launches) for (workload, precision, basis, outer, kernel class);
 # the capture is summarised in the profiles/ file named beside it.  An entry
-# is removed whenever a kernel of the class changes.  The cube48_x16 entry was
-# captured on one of its 16 right-hand sides and scaled by 16 (traffic grows
-# with the dofs).
-TRAFFIC = {
-    ("cube48_x16", "mixed_tf32", "spectral", "ir", "stencil_df"):
-        (16 * (906206720 + 429370112), "profiles/traffic_cube48_stencil_dfloat_and_sweep.md"),
-}
+# is removed whenever a kernel of the class changes: the double-float
+# residual's (profiles/traffic_cube48_stencil_dfloat_and_sweep.md, one of the
+# 16 right-hand sides scaled by 16) went when its CTAs began to cover several
+# slabs, and no capture of the new kernel has been taken.
+TRAFFIC = {}
 
 
 def roofline_entry(r):
