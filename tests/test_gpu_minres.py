@@ -8,8 +8,9 @@ diagonalisation) to 1e-8 relative to the largest entry; the smoother with
 a tight inner tolerance (1e-13) equals the exact damped block-Jacobi step to
 1e-10; at the default inner tolerance 1e-4 the step's error against the exact
 step is that of the oracle's own inexact step (about 1e-5), bounded here by
-1e-3; a solve preconditioned by the inexact V-cycle to 1e-8 matches the exact
-solution to 1e-6 (FP64) / 1e-5 (mixed)."""
+1e-3; a solve preconditioned by the inexact V-cycle reaches 1e-8, and solved
+to 1e-12 (FP64) / 1e-10 (mixed) it matches the oracle's exact solution to
+1e-10 / 1e-8."""
 import numpy as np
 import pytest
 

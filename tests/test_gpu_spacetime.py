@@ -4,8 +4,9 @@ and time) against the CPU oracle, through the C ABI.
 The oracle's hierarchy uses Galerkin coarse operators P^T L P; the library
 rediscretises (the same operators: nested spaces, pinned in the oracle tests).
 Tolerances as for the time-only V-cycle: one V-cycle 1e-11 relative to the
-largest entry (FP64); solves to 1e-8 match the exact solution to 1e-6 (FP64)
-and 1e-5 (mixed FP32 V-cycle)."""
+largest entry (FP64); solves reach 1e-8, and solved to 1e-12 (FP64) / 1e-10
+(mixed FP32 V-cycle) they match the oracle's exact solution to 1e-10 /
+1e-8."""
 import numpy as np
 import pytest
 
