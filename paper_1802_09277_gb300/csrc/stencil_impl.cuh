@@ -147,7 +147,10 @@ struct StencilSmem {
     static constexpr int threads = TX * TY * ZS;
     // the deep tile (64 KB): three CTAs per SM (24 warps) where N_t <= 4 lets
     // the accumulators fit 80 registers, else two
-    static constexpr int min_blocks(int ntc) { return ZS > 1 ? ((ntc > 0 && ntc <= 4) ? 3 : 2) : 1; }
+    static constexpr int min_blocks(int ntc) {
+        return ZS > 1 ? ((ntc > 0 && ntc <= 4) ? 3 : 2)
+                      : (DIM == 2 && !std::is_same<T, dfloat>::value) ? 2 : 1;
+    }
 };
 
 // NTC > 0: N_t fixed at compile time (exact-length loops, fewer registers
