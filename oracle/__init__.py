@@ -10,7 +10,9 @@ What it computes (Hofer, Langer, Neumueller, arXiv:1802.09277):
 * ``assemble`` -- the 1D space matrices M1, K1, the SUPG-weighted time matrices
   K_t, M_t, the jump coupling N_t (Eq. 2.6 and the text after it), the global
   block lower-bidiagonal space-time matrix L_h (Eq. 2.4, Eq. 2.5) as a scipy
-  CSR matrix, load vectors, and the dG error norm (Sec. 2.2).
+  CSR matrix, one block row of it applied factor by factor without assembly
+  (for grids too large to assemble), load vectors, and the dG error norm
+  (Sec. 2.2).
 * ``solve``    -- the exact solution of L_h u = f (sparse LU), the damped
   block-Jacobi smoother of Sec. 3.1 with sparse-LU slab solves, a time-only
   V-cycle that merges slab pairs with Galerkin coarse operators, the

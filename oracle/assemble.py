@@ -165,6 +165,60 @@ def slab_blocks(prob):
     return A, B
 
 
+def _apply_axis(mat, v, axis):
+    """Apply a dense 1D matrix along one axis of v (shape (N_t, n_z, n_y, n_x)
+    trimmed to the problem's dimension; spatial axis 0 is x, the last)."""
+    ax = v.ndim - 1 - axis
+    return np.moveaxis(np.tensordot(mat, v, axes=([1], [ax])), 0, ax)
+
+
+def slab_residual_kron(prob, f_n, u_n, u_prev, magnitude=False):
+    """One block row of Eq. 2.4 without assembling it: the slab residual
+    r_n = f_n - (K_t (x) M_x + M_t (x) K_x) u_n + (N_t (x) M_x) u_{n-1}
+    (Eq. 2.5), each Kronecker factor applied along its own axis, M_x as the
+    product of the 1D mass matrices and K_x as the sum over axes of the 1D
+    stiffness in one slot.  u_prev = None for the first slab (no coupling).
+
+    With magnitude=True every factor and vector is replaced by its entry-wise
+    absolute value and the three terms are added: the size of the terms the
+    residual sums, |f_n| + (|K_t| (x) |M_x| + |M_t| (x) |K_x|) |u_n| +
+    (|N_t| (x) |M_x|) |u_{n-1}|, the scale of a rounding-error bound."""
+    facs = [space_matrices(s, prob.p) for s in prob.spans]
+    Kt, Mt = time_matrices(prob.tau, prob.ne, prob.p, prob.delta)
+    Nt = coupling_matrix(prob.tau, prob.ne, prob.p)
+    ab = np.abs if magnitude else (lambda a: a)
+    shape = (prob.Nt,) + tuple(reversed(prob.n_axis))
+
+    def mass(v):
+        for a in range(prob.d):
+            v = _apply_axis(ab(facs[a][0]), v, a)
+        return v
+
+    def stiff(v):
+        out = 0.0
+        for a in range(prob.d):
+            w = v
+            for b in range(prob.d):
+                w = _apply_axis(ab(facs[b][1] if b == a else facs[b][0]), w, b)
+            out = out + w
+        return out
+
+    def time(mat, v):
+        return np.tensordot(ab(mat), v, axes=([1], [0]))
+
+    u = ab(np.asarray(u_n, dtype=np.float64).reshape(shape))
+    Lu = time(Kt, mass(u)) + time(Mt, stiff(u))
+    f = ab(np.asarray(f_n, dtype=np.float64).reshape(shape))
+    if magnitude:
+        r = f + Lu
+    else:
+        r = f - Lu
+    if u_prev is not None:
+        c = time(Nt, mass(ab(np.asarray(u_prev, dtype=np.float64).reshape(shape))))
+        r = r + c
+    return r.reshape(-1)
+
+
 def assemble_L(prob):
     """The block lower-bidiagonal system matrix of Eq. 2.4: A on the
     diagonal, -B on the first sub-diagonal."""

@@ -117,3 +117,4 @@ def test_residual_df_on_mixed_handle_and_errors(st):
             assert e.value.code == st.ST_ERR_INVALID_ARG
         s.close()
     assert np.array_equal(outs[0], outs[1])
+
