@@ -19,6 +19,17 @@ def uniform_vector(seed, n, lo=-1.0, hi=1.0):
     return np.random.default_rng(seed).uniform(lo, hi, int(n))
 
 
+def uniform_vectors_on_device(seed, n, count, device, lo=-1.0, hi=1.0):
+    """`count` i.i.d. U(lo, hi) float64 vectors of length n drawn on `device`
+    by one seeded torch generator, for sizes too large to draw on the host
+    and copy (a test copies back only the parts an oracle checks)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return [torch.empty(int(n), dtype=torch.float64, device=device).uniform_(lo, hi, generator=g)
+            for _ in range(count)]
+
+
 def gaussian_bumps(seed, count=32, dim=3, wmin=0.05, wmax=0.2):
     """Space-time Gaussian bump parameters: centers U(0,1)^dim in
     (x, y, z, t) order, widths U(wmin, wmax), amplitudes N(0,1)."""

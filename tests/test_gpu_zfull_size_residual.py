@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from oracle import assemble as A
+from paper_1802_09277_gb300 import inputs
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,10 +58,7 @@ def test_residual_df_full_size_sampled(st):
     s = st.Solver(d, p, spans, N, ne_per_slab=ne, nrhs=R, precision="mixed_tf32",
                   basis="spectral", outer="ir")
     assert s.ndofs == R * pr.ndofs
-    g = torch.Generator(device="cuda")
-    g.manual_seed(77)
-    x = torch.empty(s.ndofs, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
-    f = torch.empty_like(x).uniform_(-1.0, 1.0, generator=g)
+    x, f = inputs.uniform_vectors_on_device(77, s.ndofs, 2, "cuda")
     r = torch.empty_like(x)
     s.residual_df(x, f, r)
     torch.cuda.synchronize()
