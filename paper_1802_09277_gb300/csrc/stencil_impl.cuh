@@ -146,7 +146,8 @@ struct StencilSmem {
     static constexpr size_t bytes = sizeof(T) * (nR1 + 2 * nA + nBand);
     static constexpr int threads = TX * TY * ZS;
     // the deep tile (64 KB): three CTAs per SM (24 warps) where N_t <= 4 lets
-    // the accumulators fit 80 registers, else two
+    // the accumulators fit 80 registers, else two; the FP64 / FP32 2D tile
+    // (512 threads): two CTAs per SM, at most 64 registers
     static constexpr int min_blocks(int ntc) {
         return ZS > 1 ? ((ntc > 0 && ntc <= 4) ? 3 : 2)
                       : (DIM == 2 && !std::is_same<T, dfloat>::value) ? 2 : 1;
